@@ -1,0 +1,397 @@
+"""Benchmark: local stencils/sec of the stencil setup (steps a1-a7) on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload helm2d_n1024]
+                    [--policy local] [--impl ours|reference]
+
+One step = one pass of the whole hot path over the workload's potential, resident in HBM:
+lsp_set_potential (a1: device copy + v_min/v_max/mean) and lsp_build_stencils (a2-a7: shift
+list, per-shift kernel vectors, Gram matrix, near-null vector, and the Q, C, P rows of every
+point). The value is points / second (one stencil = the finished Q, C, P rows of one point).
+L2 is flushed (256 MiB write) before every timed step, outside the step's events.
+
+Under torchrun each rank builds the stencils of its own potential (a different seed): the
+per-point problems are independent, so ranks share nothing (weak scaling, no collective on
+the data path); the step time is the maximum over ranks.
+
+--impl reference times the CPU oracle (numpy/scipy FP64) on a bounded sample of the same
+workload on the host cores and extrapolates to the whole workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD_TEXT = {
+    "helm2d_n1024": "2D Helmholtz n=1024 (1,048,576 points), 3x3 neighbourhoods, omega=2*pi*256, "
+                    "c(x)=1+sum of 64 seeded Gaussians (seed 3)",
+    "helm2d_n256": "2D Helmholtz n=256 (65,536 points), 3x3 neighbourhoods, omega=2*pi*64, "
+                   "c(x)=1+sum of 16 seeded Gaussians (seed 2)",
+    "schr3d_n64": "3D Schroedinger-type n=64 (262,144 points), 3x3x3 neighbourhoods, 8 seeded "
+                  "Gaussian wells (seed 4), max|v|h^2=0.6",
+    "helm2d_n32": "2D Helmholtz n=32 (1,024 points), 3x3 neighbourhoods, omega=2*pi*8, "
+                  "one centred Gaussian bump",
+}
+
+
+def dist_info():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.gpu = gpu_index
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names[1:], parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def lattice_domain_sizes(m_list: np.ndarray, n: int, d: int) -> list[int]:
+    """|E_k| of the lattice-separable stages (host recomputation from the shift list)."""
+    p2 = (np.arange(n // 2 + 1, dtype=np.int64)) ** 2
+    sizes = [len(m_list)]
+    cur = np.asarray(m_list, dtype=np.int64)
+    for _ in range(d - 1):
+        lo, hi = int(cur.min()), int(cur.max() + p2[-1])
+        flags = np.zeros(hi - lo + 1, dtype=bool)
+        for p in p2:
+            flags[cur + p - lo] = True
+        cur = np.nonzero(flags)[0].astype(np.int64) + lo
+        sizes.append(len(cur))
+    return sizes  # [|E_d| = shifts, |E_{d-1}|, ..., |E_1|]
+
+
+def kernel_work(name: str, n: int, d: int, N: int, mu: int, sizes: list[int]):
+    """Algorithmic (flops or bytes, unit) of one launch of a kernel, or None."""
+    P = n // 2 + 1
+    ncls = {1: 3, 2: 6, 3: 10}
+    if name.startswith("stage"):
+        k = int(name[-1])
+        # stage k runs over E_k; sizes lists E_d, E_{d-1}, ..., so E_k = sizes[d - k]
+        count = sizes[d - k]
+        per = 2 * 2 * ncls[k] + (1 if k == 1 else 0)  # 2 functions x FMA, + w^2 in stage 1
+        return count * P * per, "flop"
+    if name == "rows":
+        return N * (8 + 3 * mu * 8), "byte"
+    if name == "stats":
+        return N * 8, "byte"
+    return None
+
+
+def measure_fp64_peak(torch) -> float:
+    """FP64 GEMM throughput (TFLOP/s) of the library matmul, best of 5, 4096^3."""
+    a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    b = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
+    best = 0.0
+    for _ in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * 4096 ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return best
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_info()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from lsp_inputs import make_workload
+    from paper_1607_02560_gb300 import Context
+    from paper_1607_02560_gb300 import build as B
+
+    B.build()
+    seed = None if rank == 0 else 1000 + rank
+    v_host = make_workload(args.workload, seed=seed)
+    d, n = v_host.ndim, v_host.shape[0]
+    N = v_host.size
+    stream = torch.cuda.Stream()
+    ctx = Context(d, n, stream=stream)
+    mu = ctx.mu
+    v_dev = torch.from_numpy(v_host).to("cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def step():
+        ctx.set_potential(v_dev)
+        ctx.build_stencils(policy=args.policy, use_graph=True)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        ctx.synchronize()
+        tab = ctx.get_shift_table(with_sidx=False)
+        ns = len(tab["s"])
+        m_list = np.round((tab["s"] / (np.pi ** 2) - 2) / 4).astype(np.int64)
+
+        # ---- timed region: K steps, graph replay, L2 flushed before each ----
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = Clocks(local)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        clk = clocks.stop()
+        step_ms = [a.elapsed_time(b) for a, b in evs]
+        total_ms = float(np.sum(step_ms))
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+            dist.barrier()
+
+        # ---- per-kernel timing over K more steps (events around every launch) ----
+        ctx.kernel_timing(True)
+        for k in range(args.steps):
+            flush.zero_()
+            step()
+        ctx.synchronize()
+        ktimes = ctx.kernel_times()
+        ctx.kernel_timing(False)
+
+        # ---- end to end through the public API with host buffers ----
+        v_pin = torch.empty(v_host.shape, dtype=torch.float64, pin_memory=True)
+        v_pin.copy_(torch.from_numpy(v_host))
+        outs = [torch.empty((N, mu), dtype=torch.float64, pin_memory=True).numpy()
+                for _ in range(3)]
+        e2e_ms = []
+        for k in range(max(3, args.steps // 2) + 1):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ctx.set_potential(v_pin.numpy())
+            ctx.build_stencils(policy=args.policy, use_graph=True)
+            for which, o in zip("QCP", outs):
+                ctx.get_rows(which, o)
+            e2e_ms.append((time.perf_counter() - t1) * 1e3)
+        e2e_ms = e2e_ms[1:]
+
+    if rank != 0:
+        if ws > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    value = N * args.steps * ws / (total_ms * 1e-3)
+    peaks, peak_src = load_peaks()
+    sizes = lattice_domain_sizes(m_list, n, d)
+    launches = int(sum(c for _, c in ktimes.values()))
+    kern = {}
+    for name, (ms, cnt) in ktimes.items():
+        w = kernel_work(name, n, d, N, mu, sizes)
+        kern[name] = {"ms_per_launch": ms / max(cnt, 1), "launches": cnt}
+        if w:
+            per = w[0] / (ms / max(cnt, 1) * 1e-3)
+            kern[name]["achieved"] = per / (1e12 if w[1] == "flop" else 1e9)
+            kern[name]["unit"] = "TFLOP/s" if w[1] == "flop" else "GB/s"
+    dom = max(ktimes.items(), key=lambda kv: kv[1][0])[0]
+    fp64_peak = measure_fp64_peak(torch)
+    w = kernel_work(dom, n, d, N, mu, sizes)
+    if w and w[1] == "flop":
+        roof = {"bound": "alu", "kernel": dom, "achieved": kern[dom]["achieved"],
+                "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": kern[dom]["achieved"] / fp64_peak, "traffic": None,
+                "peak_source": "FP64 DGEMM (torch.matmul 4096^3, best of 6) measured in this "
+                               "run; FP64 ALU, nominal 1.25 TFLOP/s on GB300",
+                "work_per_launch": w[0]}
+    elif w:
+        roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved"],
+                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": kern[dom]["achieved"] / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                "work_per_launch": w[0]}
+    else:
+        roof = None
+    rows_k = kern.get("rows")
+    out = {
+        "metric": "local stencils/sec (Q, C, P rows of every grid point, steps a1-a7)",
+        "value": value, "unit": "stencils/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "text": WORKLOAD_TEXT.get(args.workload, ""),
+                   "policy": args.policy, "mode": "fp64", "d": d, "n": n, "points": N,
+                   "shifts": ns, "lattice_domains": sizes,
+                   "l2": "flushed before every timed step (256 MiB write), outside the step events",
+                   "parallelism": f"replicas x{ws} (independent potentials)"},
+        "roofline": roof,
+        "hbm_roofline_rows": ({"achieved": rows_k["achieved"], "peak": peaks["hbm_gbs"],
+                               "frac": rows_k["achieved"] / peaks["hbm_gbs"], "unit": "GB/s"}
+                              if rows_k and "achieved" in rows_k else None),
+        "kernels": kern,
+        "gpu_launches": launches,
+        "wall_s_timed_region": wall,
+        "clocks": clk,
+        "e2e": {"value": N / (float(np.median(e2e_ms)) * 1e-3), "unit": "stencils/s",
+                "h2d_bytes_per_step": int(N * 8), "d2h_bytes_per_step": int(3 * N * mu * 8),
+                "ms_per_step": float(np.median(e2e_ms))},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.workload, args.policy, budget_s=args.cpu_budget)
+    print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def cpu_baseline(workload: str, policy: str, budget_s: float = 20.0, step_index: int = 0):
+    """The oracle, as it stands, on the host cores: a sample of shifts plus the row assembly
+    of every point, extrapolated to the workload's full shift list."""
+    import oracle as O
+    from lsp_inputs import make_workload
+
+    v = make_workload(workload)
+    n, d = v.shape[0], v.ndim
+    t0 = time.perf_counter()
+    st = O.build_stencils(v, policy, shift_subset=[0])  # shift list + s_j + row assembly
+    t_rows = time.perf_counter() - t0
+    ns = len(st["S"])
+    rng = np.random.default_rng(100 + step_index)
+    order = rng.permutation(ns)
+    done, t_sh = 0, 0.0
+    while done < ns and (t_sh + t_rows) < budget_s:
+        t1 = time.perf_counter()
+        O.stencil_for_shift(n, d, float(st["S"][order[done]]))
+        t_sh += time.perf_counter() - t1
+        done += 1
+    per_shift = t_sh / max(done, 1)
+    total = t_rows + per_shift * ns
+    return {"value": v.size / total, "unit": "stencils/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {ns} shifts (seeded) timed at {per_shift:.3f} s each + "
+                      f"shift assignment and row assembly of all {v.size} points "
+                      f"({t_rows:.2f} s); extrapolated to all shifts"
+                      + ("" if done == ns else " (extrapolated)"),
+            "seconds": t_sh + t_rows}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_info()
+    if rank != 0:
+        return
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    vals = []
+    budget = max(2.0, args.ref_step_s)
+    for k in range(args.warmup + args.steps):
+        cb = cpu_baseline(args.workload, args.policy, budget_s=budget, step_index=k)
+        if k >= args.warmup:
+            vals.append(cb)
+    value = float(np.median([c["value"] for c in vals]))
+    last = vals[-1]
+    out = {"impl": "reference", "metric": "local stencils/sec (Q, C, P rows of every grid "
+                                          "point, steps a1-a7)",
+           "value": value, "unit": "stencils/s", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": float(np.mean([c["seconds"] for c in vals])) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic",
+           "config": {"workload": args.workload, "text": WORKLOAD_TEXT.get(args.workload, ""),
+                      "policy": args.policy, "mode": "fp64"},
+           "cpu_baseline": {"value": value, "unit": "stencils/s", "cores": 1, "kind": "oracle",
+                            "sample": "per step: " + last["sample"]},
+           "e2e": {"value": value, "unit": "stencils/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="helm2d_n1024")
+    ap.add_argument("--policy", default="local", choices=["local", "paper", "mean"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--ref-step-s", type=float, default=4.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,175 @@
+/*
+ * lsp.h -- C ABI of the GB300 stencil-setup library for the localized sparsifying
+ * preconditioner (Liu & Ying, "Localized sparsifying preconditioner for periodic indefinite
+ * systems").
+ *
+ * Problem (Sec. 1, Eq. model; Sec. 2, Eq. dmodel): (-Laplace + v) u = f on the periodic unit
+ * cube [0,1)^d, discretised pseudospectrally on the n^d grid hJ, h = 1/n:
+ *     (L + diag(v)) u = f,   L = F^-1 diag(4 pi^2 |k|^2) F,  k in K = [-n/2, n/2)^d.
+ * For every grid point j the library builds the sparse rows Q[j, mu_j], C[j, mu_j] and
+ * P[j, mu_j] of the preconditioner P^-1 C (Sec. 4.1, Eq. PC), mu_j = {i : |i - j|_inf <= t}.
+ *
+ * Conventions shared by every call:
+ *  - Grid arrays are float64, row-major, last axis fastest, n^d entries.
+ *  - Offsets o of mu_0 are in lexicographic order (o_1..o_d in [-t, t], last fastest);
+ *    row j of Q, C, P holds |mu| = (2t+1)^d values, column (j + o) mod n for the o-th value.
+ *  - Shifts live on the resonance-free lattice s = (4m + 2) pi^2 (Sec. 4.1); m is an integer
+ *    "lattice index".
+ *  - Every call returns an lsp_status; no call throws or aborts. On failure the context keeps a
+ *    message readable with lsp_last_error().
+ *  - Device work is issued on the CUDA stream given to lsp_create() and is stream ordered.
+ *    Calls that return data to host memory synchronise that stream before returning.
+ *  - Pointers passed in are borrowed for the duration of the call; output buffers are owned
+ *    by the caller. The context owns all device scratch it allocates.
+ */
+#ifndef LSP_H
+#define LSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lsp_ctx lsp_ctx;
+
+typedef enum {
+  LSP_OK = 0,
+  LSP_ERR_ARG = 1,             /* invalid argument (sizes, NaN/Inf in v, off-lattice shift) */
+  LSP_ERR_STATE = 2,           /* call out of order (e.g. build before set_potential)        */
+  LSP_ERR_RESONANT_SHIFT = 3,  /* a requested shift makes L + s singular (s = -4 pi^2 |k|^2) */
+  LSP_ERR_CUDA = 4,            /* a CUDA runtime call or kernel launch failed                */
+  LSP_ERR_OOM = 5,             /* device or pinned host allocation failed                    */
+  LSP_ERR_TIMEOUT = 6,         /* a bounded device-side wait gave up                         */
+  LSP_ERR_DEGENERATE = 7,      /* reserved: degenerate near-null spaces are flagged per shift */
+  LSP_ERR_UNSUPPORTED = 8      /* valid request that this build does not implement           */
+} lsp_status;
+
+typedef enum { LSP_FP64 = 0, LSP_MIXED = 1, LSP_LEARNED = 2 } lsp_mode;
+
+typedef enum {
+  LSP_SHIFT_PAPER = 0,  /* |S| shifts spread evenly over [v_min, v_max], snapped (Sec. 4.1)   */
+  LSP_SHIFT_LOCAL = 1,  /* each point's own shift G_{v_j} of Sec. 4.1, snapped to the lattice */
+  LSP_SHIFT_LIST = 2,   /* caller-given shift values (must lie on the lattice)               */
+  LSP_SHIFT_MEAN = 3    /* the single shift snap(mean v) of Sec. 3                           */
+} lsp_shift_policy;
+
+typedef enum {
+  LSP_EIG_SYMMETRIC = 0, /* block-diagonalise A by the cube symmetry of mu_0, solve the blocks */
+  LSP_EIG_FULL = 1       /* cyclic Jacobi on the whole |mu| x |mu| matrix A                    */
+} lsp_eig_method;
+
+/* Per-shift flag bits (lsp_get_shift_table). */
+#define LSP_FLAG_DEGENERATE 1    /* lambda_2 - lambda_1 < 1e-8 max|lambda|                    */
+#define LSP_FLAG_NONSYMMETRIC 2  /* the smallest eigenvalue is not in the fully symmetric block */
+#define LSP_FLAG_NOT_CONVERGED 4 /* Jacobi hit its sweep limit                                 */
+
+typedef struct {
+  int t;               /* neighbourhood radius; this build supports t = 1 (|mu| = 3^d)         */
+  int policy;          /* lsp_shift_policy                                                     */
+  int nshifts;         /* PAPER: |S| before de-duplication; 0 selects n/16 (2D) or n/4 (3D)   */
+  const double* shifts;/* LIST: nshifts shift values in host memory, each (4m+2) pi^2          */
+  int mode;            /* lsp_mode; this build implements LSP_FP64                             */
+  int refine_steps;    /* inverse-iteration steps applied to each near-null vector (0 or 1)   */
+  int eig_method;      /* lsp_eig_method                                                       */
+  int use_graph;       /* 1: record the launch sequence once per configuration, replay it     */
+} lsp_stencil_opts;
+
+/* Fill *opts with the defaults: t=1, LOCAL policy, FP64, symmetric eigen-solve, no graph. */
+void lsp_default_opts(lsp_stencil_opts* opts);
+
+/*
+ * Create a context for the d-dimensional n^d grid (Sec. 2). d in {2, 3}; n a power of two,
+ * 8 <= n <= 4096 (2D) or 8 <= n <= 256 (3D), so that the offsets of mu_0 - mu_0 stay distinct
+ * mod n. cuda_stream is a cudaStream_t (NULL = the legacy default stream) that every device
+ * operation of the context is issued on. The current CUDA device at this call is the one used.
+ * On success *out receives the context; release it with lsp_destroy().
+ */
+lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out);
+
+/* Release a context and all device memory it owns. NULL is accepted. */
+lsp_status lsp_destroy(lsp_ctx* ctx);
+
+/*
+ * Step a1: ingest the potential v (Sec. 2: v_j = v(h j)), n^d float64 values, row-major.
+ * v_on_device = 1: v is a device pointer (copied device-to-device); 0: host pointer (copied
+ * host-to-device). The call computes v_min, v_max and the mean (Sec. 3, Sec. 4.1) on the
+ * device and waits for them (one small device-to-host read). Fails with LSP_ERR_ARG if v holds
+ * NaN or Inf, or if the shifts it implies fall outside the supported lattice range |m| < 2^30.
+ */
+lsp_status lsp_set_potential(lsp_ctx* ctx, const double* v, int v_on_device);
+
+/*
+ * Steps a2-a7: build every stencil row (Sec. 4.1, Sec. 4.2).
+ *   a2 shift list S and per-point shift s_j (arg-min of |s - v_j|, ties to the smaller s);
+ *   a3 kernel vectors g_s = G_s[:, 0] and g_s * g_s at the offsets mu_0 - mu_0 (Sec. 4.2);
+ *   a4 Gram matrix A = A1 - A2 of Eq. A;  a5 eigenvector alpha_s of its smallest eigenvalue,
+ *      ||alpha|| = 1, alpha[centre] > 0;  a6 c_s = alpha_s^T G_s[mu_0, mu_0];
+ *   a7 Q[j, mu_j] = alpha_{s_j}, C[j, mu_j] = c_{s_j},
+ *      P[j, mu_j] = alpha_{s_j} + c_{s_j} .* (v[mu_j] - s_j).
+ * Asynchronous on the context stream (except LIST/PAPER/MEAN, which upload a small shift list
+ * from pinned host memory). Results stay on the device until read with lsp_get_rows(),
+ * lsp_export_sparse_rows() or lsp_get_shift_table(). opts = NULL uses lsp_default_opts().
+ * Errors: LSP_ERR_STATE without a potential; LSP_ERR_ARG for bad options or an off-lattice
+ * LIST shift; LSP_ERR_RESONANT_SHIFT for a LIST shift equal to -4 pi^2 |k|^2 for a k in K.
+ */
+lsp_status lsp_build_stencils(lsp_ctx* ctx, const lsp_stencil_opts* opts);
+
+/*
+ * y = (L + diag(v)) u (Sec. 2, Eq. dmodel) for the context's current potential. u and y are
+ * device pointers to n^d float64 values (real input; L maps real arrays to real arrays);
+ * they may alias. Asynchronous on the context stream. LSP_ERR_STATE without a potential.
+ */
+lsp_status lsp_apply_operator(lsp_ctx* ctx, const double* u_dev, double* y_dev);
+
+/*
+ * Copy the dense row block of Q, C or P (which = 'Q', 'C', 'P'): n^d x |mu| float64,
+ * row j at rows[j * |mu| ...], in mu_0 offset order. on_device = 1: rows is a device pointer
+ * (asynchronous copy); 0: host pointer (the call waits for the copy).
+ */
+lsp_status lsp_get_rows(lsp_ctx* ctx, char which, double* rows, int on_device);
+
+/*
+ * Export Q, C or P as CSR in host memory: rowptr[n^d + 1] (int64), colidx[nnz] (int32),
+ * vals[nnz] (float64), nnz = n^d |mu|. Column indices of a row follow the mu_0 offset order,
+ * so they are not sorted where the neighbourhood wraps around the periodic boundary.
+ * With rowptr, colidx and vals all NULL only *nnz_out is written (size query). Waits for the
+ * copies before returning.
+ */
+lsp_status lsp_export_sparse_rows(lsp_ctx* ctx, char which, int64_t* rowptr, int32_t* colidx,
+                                  double* vals, int64_t* nnz_out);
+
+/*
+ * Read the per-shift table of the last build into host memory (Sec. 4.1: "only needs to be
+ * computed once for different locations sharing the same shift"). *nshifts_out receives |S|.
+ * Any output pointer may be NULL. s[|S|] shift values (increasing), alpha[|S| x |mu|],
+ * c[|S| x |mu|], lam[|S| x 2] = (lambda_1, lambda_2) of A, flags[|S|] (LSP_FLAG_* bits),
+ * s_idx[n^d] = index into s of each point's shift s_j. Waits before returning.
+ */
+lsp_status lsp_get_shift_table(lsp_ctx* ctx, int64_t* nshifts_out, double* s, double* alpha,
+                               double* c, double* lam, int32_t* flags, int32_t* s_idx);
+
+/* |mu| = (2t+1)^d for t = 1 and the number of grid points n^d. */
+lsp_status lsp_get_sizes(const lsp_ctx* ctx, int64_t* npoints, int* mu);
+
+/* Block until all work issued by the context has finished. */
+lsp_status lsp_synchronize(lsp_ctx* ctx);
+
+/*
+ * Per-kernel timing with CUDA events on the context stream. enable = 1 starts recording
+ * (graph replay is bypassed while enabled), 0 stops. lsp_kernel_times() copies, for up to
+ * cap kernels, the name (NUL-terminated, up to 31 chars), the summed milliseconds and the
+ * launch count since the last enable, and returns the number of kernels seen in *count.
+ */
+lsp_status lsp_kernel_timing(lsp_ctx* ctx, int enable);
+lsp_status lsp_kernel_times(lsp_ctx* ctx, int cap, char (*names)[32], double* ms,
+                            int64_t* launches, int* count);
+
+/* Message of the last failed call on this context ("" if none). Never NULL. */
+const char* lsp_last_error(const lsp_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSP_H */

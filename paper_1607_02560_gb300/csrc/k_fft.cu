@@ -1,0 +1,130 @@
+// y = (L + diag(v)) u with L = F^-1 diag(4 pi^2 |k|^2) F (Sec. 2, Eq. dmodel).
+//
+// A d-dimensional complex FP64 FFT done one axis at a time: every block transforms whole
+// lines of the chosen axis in shared memory (iterative radix-2, bit-reversed load, twiddles
+// from a table computed on the host in extended precision). Passes:
+//   2D: [fwd axis0 from real u] -> [fwd axis1, * 4 pi^2 |k|^2, inv axis1] -> [inv axis0, y = Re/N + v u]
+//   3D: [fwd 0] -> [fwd 1] -> [fwd 2, * symbol, inv 2] -> [inv 1] -> [inv 0, output]
+// The unitary factors n^{-d/2} of F and F^-1 combine into the single 1/N of the output pass.
+#include "lsp_internal.h"
+
+namespace lsp {
+namespace {
+
+enum Mode { kPlain = 0, kLoadReal = 1, kSymbol = 2, kOutput = 3 };
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ void fft_line(double2* x, int n, int logn, const double2* __restrict__ tw,
+                                         bool inverse) {
+  for (int s = 1; s <= logn; ++s) {
+    const int m = 1 << s, half = m >> 1, tstride = n >> s;
+    for (int b = threadIdx.x; b < n / 2; b += blockDim.x) {
+      const int grp = b / half, k = b - grp * half;
+      const int i = grp * m + k, j = i + half;
+      double2 w = __ldg(tw + k * tstride);
+      if (inverse) w.y = -w.y;
+      const double2 a = x[i], t = cmul(x[j], w);
+      x[i] = make_double2(a.x + t.x, a.y + t.y);
+      x[j] = make_double2(a.x - t.x, a.y - t.y);
+    }
+    __syncthreads();
+  }
+}
+
+// Lines along `axis` (stride S = n^(d-1-axis) between elements); one line per block.
+__global__ void k_fft_axis(double2* __restrict__ Z, const double* __restrict__ u,
+                           const double* __restrict__ v, double* __restrict__ y, int d, int n,
+                           int logn, int axis, int64_t nlines, const double2* __restrict__ tw,
+                           int mode, int fwd_first) {
+  extern __shared__ double2 line[];
+  int64_t S = 1;
+  for (int a = axis + 1; a < d; ++a) S *= n;
+  for (int64_t l = blockIdx.x; l < nlines; l += gridDim.x) {
+    const int64_t inner = l % S, outer = l / S;
+    const int64_t base = outer * S * n + inner;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int r = __brev(i) >> (32 - logn);
+      const int64_t g = base + (int64_t)i * S;
+      line[r] = (mode == kLoadReal) ? make_double2(u[g], 0.0) : Z[g];
+    }
+    __syncthreads();
+    fft_line(line, n, logn, tw, !fwd_first);
+    if (mode == kSymbol) {
+      // multiply by 4 pi^2 |k|^2 (k in FFT order), then transform back along this axis
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int64_t g = base + (int64_t)i * S;
+        double k2 = 0.0;
+        for (int a = d - 1; a >= 0; --a) {
+          const int ka = (int)(g % n);
+          g /= n;
+          const double kk = ka < n / 2 ? (double)ka : (double)(ka - n);
+          k2 += kk * kk;
+        }
+        const double lam = 4.0 * kPi2 * k2;
+        line[i].x *= lam;
+        line[i].y *= lam;
+      }
+      __syncthreads();
+      // bit-reverse again in place for the inverse transform
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int r = __brev(i) >> (32 - logn);
+        if (r > i) {
+          const double2 t = line[i];
+          line[i] = line[r];
+          line[r] = t;
+        }
+      }
+      __syncthreads();
+      fft_line(line, n, logn, tw, true);
+    }
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const int64_t g = base + (int64_t)i * S;
+      if (mode == kOutput) {
+        const double inv_n = 1.0 / (double)nlines / (double)n;  // 1/N (exact, power of two)
+        y[g] = fma(v[g], u[g], line[i].x * inv_n);
+      } else {
+        Z[g] = line[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_apply(lsp_ctx* c, const double* u, double* y) {
+  const int d = c->geo.d, n = c->geo.n;
+  int logn = 0;
+  while ((1 << logn) < n) ++logn;
+  const int64_t nlines = c->geo.N / n;
+  const size_t smem = sizeof(double2) * n;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_fft_axis, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int threads = n / 2 < 256 ? (n / 2 < 32 ? 32 : n / 2) : 256;
+  int64_t blocks = nlines < 152 * 32 ? nlines : 152 * 32;
+  double2* Z = (double2*)c->fftbuf.p;
+  const double2* tw = (const double2*)c->twiddle.p;
+  const double* v = (const double*)c->v.p;
+  int t = timer_begin(c, "apply_fft");
+  // forward passes on axes 0..d-2
+  for (int axis = 0; axis < d - 1; ++axis)
+    k_fft_axis<<<(int)blocks, threads, smem, c->stream>>>(Z, u, v, y, d, n, logn, axis, nlines, tw,
+                                                          axis == 0 ? kLoadReal : kPlain, 1);
+  // last axis: forward, symbol, inverse
+  k_fft_axis<<<(int)blocks, threads, smem, c->stream>>>(Z, u, v, y, d, n, logn, d - 1, nlines, tw,
+                                                        kSymbol, 1);
+  // inverse passes on axes d-2..0; the last one writes y
+  for (int axis = d - 2; axis >= 0; --axis)
+    k_fft_axis<<<(int)blocks, threads, smem, c->stream>>>(Z, u, v, y, d, n, logn, axis, nlines, tw,
+                                                          axis == 0 ? kOutput : kPlain, 0);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+}  // namespace lsp

@@ -1,0 +1,187 @@
+// Step a7: the rows of Q, C and P for every grid point (Sec. 4.1):
+//   Q[j, mu_j] = alpha_{s_j},  C[j, mu_j] = c_{s_j},  P[j, mu_j] = alpha_{s_j} + c_{s_j} .* (v[mu_j] - s_j),
+// with s_j the shift of S nearest to v_j (ties to the smaller shift) and mu_j = j + mu_0 taken
+// periodically. Also the per-point shift index alone (for the shift table) and the CSR column
+// indices of the common sparsity pattern.
+//
+// HBM-bound: per point 8 bytes of v are read and 3 |mu| doubles are written. A block handles
+// 256 consecutive points, whose rows form one contiguous span of every output array, so
+// consecutive threads store consecutive doubles (fully coalesced, streaming stores).
+#include "lsp_internal.h"
+
+namespace lsp {
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ int64_t snap_m(double x) {
+  double y = __dmul_rn(__dsub_rn(__ddiv_rn(x, kPi2), 2.0), 0.25);
+  return (int64_t)round(y);
+}
+__device__ __forceinline__ double shift_of(int64_t m) {
+  return __dmul_rn((double)(4 * m + 2), kPi2);
+}
+
+// Index in the sorted list S (given by lattice indices) of the shift nearest to x; ties go to
+// the smaller shift. |s - x| is monotone on each side of x, so only the two shifts around the
+// insertion point can win.
+__device__ __forceinline__ int nearest_shift(const int32_t* __restrict__ m, int ns, double x) {
+  int lo = 0, hi = ns;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (shift_of(__ldg(m + mid)) < x)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  if (lo == 0) return 0;
+  if (lo == ns) return ns - 1;
+  const double d1 = fabs(__dsub_rn(shift_of(__ldg(m + lo - 1)), x));
+  const double d2 = fabs(__dsub_rn(shift_of(__ldg(m + lo)), x));
+  return d1 <= d2 ? lo - 1 : lo;
+}
+
+template <int D>
+__device__ __forceinline__ int64_t neighbour(int64_t j, int o, int logn, int64_t mask) {
+  if (D == 2) {
+    const int64_t x1 = j & mask, x0 = j >> logn;
+    const int64_t y0 = (x0 + (o / 3) - 1) & mask, y1 = (x1 + (o % 3) - 1) & mask;
+    return (y0 << logn) | y1;
+  } else {
+    const int64_t x2 = j & mask, x1 = (j >> logn) & mask, x0 = j >> (2 * logn);
+    const int64_t y0 = (x0 + (o / 9) - 1) & mask, y1 = (x1 + ((o / 3) % 3) - 1) & mask,
+                  y2 = (x2 + (o % 3) - 1) & mask;
+    return (y0 << (2 * logn)) | (y1 << logn) | y2;
+  }
+}
+
+template <int D, bool LOCAL, bool ROWS, bool SIDX>
+__global__ void __launch_bounds__(kThreads) k_rows(
+    const double* __restrict__ v, int64_t N, int logn, const int32_t* __restrict__ idx_of,
+    int64_t mlo, int64_t R, int32_t* __restrict__ err, const int32_t* __restrict__ shift_m,
+    const int32_t* __restrict__ count,
+    const double* __restrict__ alpha, const double* __restrict__ cst, double* __restrict__ Q,
+    double* __restrict__ C, double* __restrict__ P, int32_t* __restrict__ sidx_out) {
+  constexpr int MU = D == 2 ? 9 : 27;
+  __shared__ int s_idx[kThreads];
+  __shared__ double s_val[kThreads];
+  const int64_t mask = ((int64_t)1 << logn) - 1;
+  const int ns = *count;
+  for (int64_t j0 = (int64_t)blockIdx.x * kThreads; j0 < N; j0 += (int64_t)gridDim.x * kThreads) {
+    const int npts = (int)min((int64_t)kThreads, N - j0);
+    const int t = threadIdx.x;
+    if (t < npts) {
+      const double x = __ldg(v + j0 + t);
+      int idx;
+      if (LOCAL) {
+        const int64_t r = snap_m(x) - mlo;
+        idx = (r >= 0 && r < R) ? __ldg(idx_of + r) : -1;
+        if (idx < 0) {  // cannot happen when host and device snap alike; recorded, row set to 0
+          atomicOr(err, 2);
+          idx = 0;
+        }
+      } else
+        idx = nearest_shift(shift_m, ns, x);
+      s_idx[t] = idx;
+      s_val[t] = shift_of(__ldg(shift_m + idx));
+      if (SIDX) sidx_out[j0 + t] = idx;
+    }
+    __syncthreads();
+    if (ROWS) {
+      const int64_t obase = j0 * MU;
+      for (int e = t; e < npts * MU; e += kThreads) {
+        const int p = e / MU, o = e - p * MU;
+        const int idx = s_idx[p];
+        const double a = __ldg(alpha + (int64_t)idx * MU + o);
+        const double cc = __ldg(cst + (int64_t)idx * MU + o);
+        const double vn = __ldg(v + neighbour<D>(j0 + p, o, logn, mask));
+        __stcs(Q + obase + e, a);
+        __stcs(C + obase + e, cc);
+        __stcs(P + obase + e, fma(cc, vn - s_val[p], a));
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kThreads) k_colidx(int64_t N, int logn, int32_t* __restrict__ col,
+                                                     int64_t* __restrict__ rowptr) {
+  constexpr int MU = D == 2 ? 9 : 27;
+  const int64_t mask = ((int64_t)1 << logn) - 1;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < N * MU;
+       e += (int64_t)gridDim.x * kThreads) {
+    const int64_t j = e / MU;
+    const int o = (int)(e - j * MU);
+    col[e] = (int32_t)neighbour<D>(j, o, logn, mask);
+  }
+  for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j <= N;
+       j += (int64_t)gridDim.x * kThreads)
+    rowptr[j] = j * MU;
+}
+
+int log2i(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+template <int D, bool LOCAL, bool ROWS, bool SIDX>
+void launch_rows_t(lsp_ctx* c, const int32_t* count) {
+  const int64_t N = c->geo.N;
+  int64_t b = (N + kThreads - 1) / kThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  k_rows<D, LOCAL, ROWS, SIDX><<<(int)b, kThreads, 0, c->stream>>>(
+      (const double*)c->v.p, N, log2i(c->geo.n), (const int32_t*)c->idx_of.p, c->mrange.lo,
+      c->mrange.size(), (int32_t*)c->counts.p + kErrWord, (const int32_t*)c->shift_m.p, count, (const double*)c->alpha.p, (const double*)c->cst.p,
+      (double*)c->Q.p, (double*)c->C.p, (double*)c->P.p, (int32_t*)c->sidx.p);
+}
+
+template <bool ROWS, bool SIDX>
+void dispatch_rows(lsp_ctx* c, int policy, const int32_t* count) {
+  const bool local = policy == LSP_SHIFT_LOCAL;
+  if (c->geo.d == 2) {
+    if (local)
+      launch_rows_t<2, true, ROWS, SIDX>(c, count);
+    else
+      launch_rows_t<2, false, ROWS, SIDX>(c, count);
+  } else {
+    if (local)
+      launch_rows_t<3, true, ROWS, SIDX>(c, count);
+    else
+      launch_rows_t<3, false, ROWS, SIDX>(c, count);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count) {
+  int t = timer_begin(c, "rows");
+  dispatch_rows<true, false>(c, policy, count);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sidx(lsp_ctx* c, int policy, const int32_t* count) {
+  int t = timer_begin(c, "sidx");
+  dispatch_rows<false, true>(c, policy, count);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colidx(lsp_ctx* c) {
+  const int64_t work = c->geo.N * c->geo.mu;
+  int64_t b = (work + kThreads - 1) / kThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  int t = timer_begin(c, "colidx");
+  if (c->geo.d == 2)
+    k_colidx<2><<<(int)b, kThreads, 0, c->stream>>>(c->geo.N, log2i(c->geo.n),
+                                                     (int32_t*)c->colidx.p, (int64_t*)c->rowptr.p);
+  else
+    k_colidx<3><<<(int)b, kThreads, 0, c->stream>>>(c->geo.N, log2i(c->geo.n),
+                                                     (int32_t*)c->colidx.p, (int64_t*)c->rowptr.p);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+}  // namespace lsp

@@ -1,0 +1,320 @@
+// Steps a1-a2 and the domain bookkeeping of a3:
+//  * potential statistics v_min, v_max, mean (Sec. 3 mean shift; Sec. 4.1 range of S),
+//  * per-point lattice shift m_j = snap(v_j) for the per-point policy (Sec. 4.1, G_{v_j}),
+//  * stream compaction of flag arrays into sorted index lists,
+//  * marking of the integer domains E_k of the lattice-separable kernel-vector stages,
+//  * the reciprocal table w(l) = 1 / (pi^2 (4 l + 2)) (Sec. 3 definition of G_s on the lattice).
+#include <float.h>
+
+#include "lsp_internal.h"
+
+namespace lsp {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kTileFlags = kThreads * 16;  // flags per compaction tile (one uint4 per thread)
+
+__device__ __forceinline__ double warp_min(double x) {
+  for (int o = 16; o > 0; o >>= 1) x = fmin(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+__device__ __forceinline__ double warp_max(double x) {
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+__device__ __forceinline__ double warp_sum(double x) {
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+// Per-block partial min / max / sum / count of non-finite values, 4 doubles per block.
+__global__ void __launch_bounds__(kThreads) k_stats_partial(const double* __restrict__ v,
+                                                            int64_t N, double* __restrict__ part) {
+  double mn = DBL_MAX, mx = -DBL_MAX, sm = 0.0, bad = 0.0;
+  for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * kThreads) {
+    double x = __ldg(v + j);
+    if (!isfinite(x)) {
+      bad += 1.0;
+      continue;
+    }
+    mn = fmin(mn, x);
+    mx = fmax(mx, x);
+    sm += x;
+  }
+  __shared__ double red[4][kThreads / 32];
+  mn = warp_min(mn);
+  mx = warp_max(mx);
+  sm = warp_sum(sm);
+  bad = warp_sum(bad);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[0][w] = mn;
+    red[1][w] = mx;
+    red[2][w] = sm;
+    red[3][w] = bad;
+  }
+  __syncthreads();
+  if (w == 0) {
+    mn = l < kThreads / 32 ? red[0][l] : DBL_MAX;
+    mx = l < kThreads / 32 ? red[1][l] : -DBL_MAX;
+    sm = l < kThreads / 32 ? red[2][l] : 0.0;
+    bad = l < kThreads / 32 ? red[3][l] : 0.0;
+    mn = warp_min(mn);
+    mx = warp_max(mx);
+    sm = warp_sum(sm);
+    bad = warp_sum(bad);
+    if (l == 0) {
+      part[4 * blockIdx.x + 0] = mn;
+      part[4 * blockIdx.x + 1] = mx;
+      part[4 * blockIdx.x + 2] = sm;
+      part[4 * blockIdx.x + 3] = bad;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_stats_final(const double* __restrict__ part, int nb,
+                                                          double* __restrict__ out) {
+  double mn = DBL_MAX, mx = -DBL_MAX, sm = 0.0, bad = 0.0;
+  for (int b = threadIdx.x; b < nb; b += kThreads) {
+    mn = fmin(mn, part[4 * b + 0]);
+    mx = fmax(mx, part[4 * b + 1]);
+    sm += part[4 * b + 2];
+    bad += part[4 * b + 3];
+  }
+  __shared__ double red[4][kThreads / 32];
+  mn = warp_min(mn);
+  mx = warp_max(mx);
+  sm = warp_sum(sm);
+  bad = warp_sum(bad);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[0][w] = mn;
+    red[1][w] = mx;
+    red[2][w] = sm;
+    red[3][w] = bad;
+  }
+  __syncthreads();
+  if (w == 0) {
+    mn = l < kThreads / 32 ? red[0][l] : DBL_MAX;
+    mx = l < kThreads / 32 ? red[1][l] : -DBL_MAX;
+    sm = l < kThreads / 32 ? red[2][l] : 0.0;
+    bad = l < kThreads / 32 ? red[3][l] : 0.0;
+    mn = warp_min(mn);
+    mx = warp_max(mx);
+    sm = warp_sum(sm);
+    bad = warp_sum(bad);
+    if (l == 0) {
+      out[0] = mn;
+      out[1] = mx;
+      out[2] = sm;
+      out[3] = bad;
+    }
+  }
+}
+
+// Lattice index of the resonance-free shift (4m+2) pi^2 nearest to x (Sec. 4.1); halves away
+// from zero. Explicit round-to-nearest intrinsics keep the decision identical to a plain
+// IEEE evaluation of (x / pi^2 - 2) / 4 (no contraction into fused operations).
+__device__ __forceinline__ int64_t snap_m(double x) {
+  double y = __dmul_rn(__dsub_rn(__ddiv_rn(x, kPi2), 2.0), 0.25);
+  return (int64_t)round(y);
+}
+
+// The host derived [mlo, mlo + R) from snap(v_min) and snap(v_max) with the same IEEE
+// operations; an index outside it would mean the two disagree, and is recorded in *err.
+__global__ void __launch_bounds__(kThreads) k_mark_local(const double* __restrict__ v, int64_t N,
+                                                         int64_t mlo, int64_t R,
+                                                         uint8_t* __restrict__ flag,
+                                                         int32_t* __restrict__ err) {
+  for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * kThreads) {
+    const int64_t r = snap_m(__ldg(v + j)) - mlo;
+    if (r >= 0 && r < R)
+      flag[r] = 1;
+    else
+      atomicOr(err, 1);
+  }
+}
+
+// E_{k-1} gets every l + p^2 for l in the list of E_k and p in [0, P).
+__global__ void __launch_bounds__(kThreads) k_mark_stage(const int32_t* __restrict__ list,
+                                                         const int32_t* __restrict__ count, int P,
+                                                         int64_t lo_prev,
+                                                         uint8_t* __restrict__ flag_prev) {
+  const int64_t cnt = *count;
+  for (int p = blockIdx.y; p < P; p += gridDim.y) {
+    const int64_t p2 = (int64_t)p * p;
+    for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * kThreads) {
+      flag_prev[(int64_t)__ldg(list + i) + p2 - lo_prev] = 1;
+    }
+  }
+}
+
+__device__ __forceinline__ int count16(uint4 q) {
+  return __popc(q.x & 0x01010101u) + __popc(q.y & 0x01010101u) + __popc(q.z & 0x01010101u) +
+         __popc(q.w & 0x01010101u);
+}
+
+// Compaction pass 1: number of set flags in each tile of kTileFlags.
+__global__ void __launch_bounds__(kThreads) k_compact_count(const uint8_t* __restrict__ flag,
+                                                            int32_t* __restrict__ tilecnt) {
+  const uint4 q = reinterpret_cast<const uint4*>(flag)[(int64_t)blockIdx.x * kThreads + threadIdx.x];
+  int c = count16(q);
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ int red[kThreads / 32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+    tilecnt[blockIdx.x] = s;
+  }
+}
+
+// Compaction pass 2: exclusive scan of the tile counts (one block), total into *count.
+__global__ void __launch_bounds__(1024) k_compact_scan(int32_t* __restrict__ tilecnt, int ntiles,
+                                                       int32_t* __restrict__ count) {
+  __shared__ int part[1024];
+  const int per = (ntiles + 1023) / 1024;
+  const int b0 = threadIdx.x * per;
+  int s = 0;
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < ntiles) s += tilecnt[b0 + i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < 1024; off <<= 1) {
+    int add = threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;  // exclusive
+  for (int i = 0; i < per; ++i) {
+    if (b0 + i < ntiles) {
+      int c = tilecnt[b0 + i];
+      tilecnt[b0 + i] = run;
+      run += c;
+    }
+  }
+  if (threadIdx.x == 1023) *count = part[1023];
+}
+
+// Compaction pass 3: write list[pos] = lo + r for every set flag r (in increasing r), and
+// idx_of[r] = pos (or -1) when idx_of is given.
+__global__ void __launch_bounds__(kThreads) k_compact_write(const uint8_t* __restrict__ flag,
+                                                            const int32_t* __restrict__ tileoff,
+                                                            int64_t lo, int64_t range,
+                                                            int32_t* __restrict__ list,
+                                                            int32_t* __restrict__ idx_of) {
+  const int64_t base = (int64_t)blockIdx.x * kTileFlags + (int64_t)threadIdx.x * 16;
+  const uint4 q = reinterpret_cast<const uint4*>(flag)[(int64_t)blockIdx.x * kThreads + threadIdx.x];
+  const int c = count16(q);
+  int incl = c;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  __shared__ int wsum[kThreads / 32];
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  int woff = 0;
+  for (int i = 0; i < w; ++i) woff += wsum[i];
+  int pos = tileoff[blockIdx.x] + woff + incl - c;
+  const uint32_t words[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int64_t r = base + k;
+    const bool set = (words[k >> 2] >> (8 * (k & 3))) & 1u;
+    if (r < range) {
+      if (set) {
+        list[pos] = (int32_t)(lo + r);
+        if (idx_of) idx_of[r] = pos;
+        ++pos;
+      } else if (idx_of) {
+        idx_of[r] = -1;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_wtable(int64_t lo, int64_t range, double* __restrict__ w) {
+  for (int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x; r < range;
+       r += (int64_t)gridDim.x * kThreads) {
+    const double l4 = (double)(4 * (lo + r) + 2);  // exact integer
+    w[r] = 1.0 / __dmul_rn(kPi2, l4);
+  }
+}
+
+int grid_for(int64_t work, int per_block = kThreads) {
+  int64_t b = (work + per_block - 1) / per_block;
+  const int64_t cap = 152 * 32;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks) {
+  int t = timer_begin(c, "stats");
+  k_stats_partial<<<nblocks, kThreads, 0, c->stream>>>((const double*)c->v.p, c->geo.N,
+                                                        (double*)c->stats_part.p);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats_final(lsp_ctx* c, int nblocks) {
+  int t = timer_begin(c, "stats_final");
+  k_stats_final<<<1, kThreads, 0, c->stream>>>((const double*)c->stats_part.p, nblocks,
+                                                (double*)c->stats.p);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark_local(lsp_ctx* c) {
+  int t = timer_begin(c, "mark_local");
+  k_mark_local<<<grid_for(c->geo.N), kThreads, 0, c->stream>>>(
+      (const double*)c->v.p, c->geo.N, c->mrange.lo, c->mrange.size(), (uint8_t*)c->shift_flag.p,
+      (int32_t*)c->counts.p + kErrWord);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+// flags must hold a multiple of kTileFlags bytes (zero beyond `range`); tile scratch lives in
+// the context's `counts` buffer after its first 16 entries.
+cudaError_t launch_compact(lsp_ctx* c, const uint8_t* flags, int64_t lo, int64_t range,
+                           int32_t* list, int32_t* count, int32_t* idx_of) {
+  const int ntiles = (int)((range + kTileFlags - 1) / kTileFlags);
+  int32_t* tiles = (int32_t*)c->counts.p + 16;
+  int t = timer_begin(c, "compact");
+  k_compact_count<<<ntiles, kThreads, 0, c->stream>>>(flags, tiles);
+  k_compact_scan<<<1, 1024, 0, c->stream>>>(tiles, ntiles, count);
+  k_compact_write<<<ntiles, kThreads, 0, c->stream>>>(flags, tiles, lo, range, list, idx_of);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark_stage(lsp_ctx* c, const int32_t* list, const int32_t* count, int64_t cap,
+                              int64_t lo_prev, uint8_t* flag_prev) {
+  const int P = c->geo.P;
+  int gx = (int)((cap + kThreads - 1) / kThreads);
+  if (gx > 1024) gx = 1024;
+  if (gx < 1) gx = 1;
+  dim3 grid(gx, P < 4096 ? P : 4096);
+  int t = timer_begin(c, "mark_stage");
+  k_mark_stage<<<grid, kThreads, 0, c->stream>>>(list, count, P, lo_prev, flag_prev);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, double* w) {
+  int t = timer_begin(c, "wtable");
+  k_wtable<<<grid_for(range), kThreads, 0, c->stream>>>(lo, range, w);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+}  // namespace lsp

@@ -1,0 +1,709 @@
+// Host side of the C ABI declared in include/lsp.h: context life cycle, buffer management,
+// the launch sequence of build_stencils (steps a1-a7), CUDA-graph replay, per-kernel timing,
+// and the copy-out calls.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "lsp_internal.h"
+
+using namespace lsp;
+
+namespace {
+
+lsp_status fail(lsp_ctx* c, lsp_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return st;
+}
+
+#define CUDA_OK(ctx, expr)                                                               \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      return fail(ctx, _e == cudaErrorMemoryAllocation ? LSP_ERR_OOM : LSP_ERR_CUDA,     \
+                  "%s failed: %s", #expr, cudaGetErrorString(_e));                       \
+  } while (0)
+
+// Lattice index of the shift (4m+2) pi^2 nearest to x, halves away from zero (Sec. 4.1).
+// Host code is compiled without floating-point contraction, so this is the plain IEEE
+// evaluation, identical to the device version.
+int64_t snap_host(double x) {
+  volatile double q = x / kPi2;
+  volatile double r = (q - 2.0) * 0.25;
+  return (int64_t)round(r);
+}
+double shift_host(int64_t m) {
+  volatile double a = (double)(4 * m + 2);
+  return a * kPi2;
+}
+
+int ncls_stage(int k) { return k == 1 ? 3 : (k == 2 ? 6 : 10); }
+
+// Is r = |k|^2 for some k in K = [-n/2, n/2)^d ?  (the eigenvalues of L are 4 pi^2 |k|^2)
+bool is_norm(int64_t r, int d, int half) {
+  for (int64_t a = 0; a <= half; ++a) {
+    const int64_t ra = r - a * a;
+    if (ra < 0) break;
+    if (d == 1) {
+      if (ra == 0) return true;
+      continue;
+    }
+    for (int64_t b = 0; b <= half; ++b) {
+      const int64_t rb = ra - b * b;
+      if (rb < 0) break;
+      if (d == 2) {
+        if (rb == 0) return true;
+        continue;
+      }
+      const int64_t c = (int64_t)llround(sqrt((double)rb));
+      if (c <= half && c * c == rb) return true;
+    }
+  }
+  return false;
+}
+
+// ---- geometry and symmetry basis ------------------------------------------------------
+
+int pair_index(int a, int b) {  // a <= b in {0,1,2}
+  static const int t[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+  return t[a][b];
+}
+int triple_index(int a, int b, int c) {  // a <= b <= c
+  int idx = 0;
+  for (int x = 0; x < 3; ++x)
+    for (int y = x; y < 3; ++y)
+      for (int z = y; z < 3; ++z) {
+        if (x == a && y == b && z == c) return idx;
+        ++idx;
+      }
+  return -1;
+}
+
+void build_geometry(Geometry& g, int d, int n) {
+  memset(&g, 0, sizeof g);
+  g.d = d;
+  g.n = n;
+  g.mu = d == 2 ? 9 : 27;
+  g.ncls = d == 2 ? 6 : 10;
+  g.centre = g.mu / 2;
+  g.N = 1;
+  for (int i = 0; i < d; ++i) g.N *= n;
+  g.P = n / 2 + 1;
+  for (int a = 0; a < g.mu; ++a) {
+    int rem = a;
+    for (int i = d - 1; i >= 0; --i) {
+      g.off[a][i] = rem % 3 - 1;
+      rem /= 3;
+    }
+  }
+  for (int a = 0; a < g.mu; ++a)
+    for (int b = 0; b < g.mu; ++b) {
+      int v[3] = {0, 0, 0};
+      for (int i = 0; i < d; ++i) v[i] = abs(g.off[a][i] - g.off[b][i]);
+      std::sort(v, v + d);
+      g.cls_of[a][b] = (uint8_t)(d == 2 ? pair_index(v[0], v[1]) : triple_index(v[0], v[1], v[2]));
+    }
+}
+
+// Symmetry-adapted vectors: block = one row of an irreducible representation of the signed
+// permutation group; vector = a polynomial pattern restricted to one orbit of mu_0 (the points
+// with exactly k nonzero offsets).
+enum Pat { kOne, kX, kX2mY2, kXY, kXY2mZ2, kXYZ };
+double pattern(int kind, const int* o) {
+  const double x = o[0], y = o[1], z = o[2];
+  switch (kind) {
+    case kOne: return 1.0;
+    case kX: return x;
+    case kX2mY2: return x * x - y * y;
+    case kXY: return x * y;
+    case kXY2mZ2: return x * (y * y - z * z);
+    default: return x * y * z;
+  }
+}
+
+bool build_sym(SymBasis& s, const Geometry& g) {
+  memset(&s, 0, sizeof s);
+  struct Blk { int copies; int nv; int orbit[4]; int kind[4]; };
+  std::vector<Blk> blks;
+  if (g.d == 2) {
+    blks = {{1, 3, {0, 1, 2}, {kOne, kOne, kOne}},
+            {1, 1, {1}, {kX2mY2}},
+            {1, 1, {2}, {kXY}},
+            {2, 2, {1, 2}, {kX, kX}}};
+  } else {
+    blks = {{1, 4, {0, 1, 2, 3}, {kOne, kOne, kOne, kOne}},
+            {3, 3, {1, 2, 3}, {kX, kX, kX}},
+            {2, 2, {1, 2}, {kX2mY2, kX2mY2}},
+            {3, 2, {2, 3}, {kXY, kXY}},
+            {3, 1, {2}, {kXY2mZ2}},
+            {1, 1, {3}, {kXYZ}}};
+  }
+  s.nblk = (int)blks.size();
+  int total = 0;
+  for (int b = 0; b < s.nblk; ++b) {
+    s.dim[b] = blks[b].nv;
+    s.copies[b] = blks[b].copies;
+    s.first[b] = s.nvec;
+    total += blks[b].nv * blks[b].copies;
+    for (int i = 0; i < blks[b].nv; ++i) {
+      double* u = s.u[s.nvec++];
+      double nrm = 0.0;
+      for (int a = 0; a < g.mu; ++a) {
+        int o[3] = {0, 0, 0}, nz = 0;
+        for (int k = 0; k < g.d; ++k) {
+          o[k] = g.off[a][k];
+          nz += o[k] != 0;
+        }
+        u[a] = nz == blks[b].orbit[i] ? pattern(blks[b].kind[i], o) : 0.0;
+        nrm += u[a] * u[a];
+      }
+      if (nrm == 0.0) return false;
+      nrm = sqrt(nrm);
+      for (int a = 0; a < g.mu; ++a) u[a] /= nrm;
+    }
+  }
+  if (total != g.mu) return false;
+  for (int i = 0; i < s.nvec; ++i)
+    for (int j = 0; j < s.nvec; ++j) {
+      double dot = 0.0;
+      for (int a = 0; a < g.mu; ++a) dot += s.u[i][a] * s.u[j][a];
+      if (fabs(dot - (i == j ? 1.0 : 0.0)) > 1e-14) return false;
+    }
+  return true;
+}
+
+size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+
+}  // namespace
+
+namespace lsp {
+
+bool ensure(lsp_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (b.bytes >= bytes) return true;
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.bytes = 0;
+  size_t want = round_up(bytes, 256);
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();
+    b.p = nullptr;
+    c->err = "device allocation of " + std::to_string(want) + " bytes failed";
+    return false;
+  }
+  b.bytes = want;
+  return true;
+}
+
+int timer_begin(lsp_ctx* c, const char* name) {
+  if (!c->timing) return -1;
+  int slot = -1;
+  for (size_t i = 0; i < c->timers.size(); ++i)
+    if (c->timers[i].name == name) slot = (int)i;
+  if (slot < 0) {
+    c->timers.push_back({name, 0.0, 0});
+    slot = (int)c->timers.size() - 1;
+  }
+  if (c->ev_next + 2 > c->ev_pool.size()) {
+    for (int k = 0; k < 64; ++k) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      c->ev_pool.push_back(e);
+    }
+  }
+  cudaEvent_t e0 = c->ev_pool[c->ev_next++], e1 = c->ev_pool[c->ev_next++];
+  cudaEventRecord(e0, c->stream);
+  c->ev_pending.push_back({slot, {e0, e1}});
+  return (int)c->ev_pending.size() - 1;
+}
+
+void timer_end(lsp_ctx* c, int t) {
+  if (t < 0 || !c->timing) return;
+  cudaEventRecord(c->ev_pending[t].second.second, c->stream);
+}
+
+}  // namespace lsp
+
+namespace {
+
+lsp_status flush_timers(lsp_ctx* c) {
+  if (c->ev_pending.empty()) return LSP_OK;
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  for (auto& pe : c->ev_pending) {
+    float ms = 0;
+    CUDA_OK(c, cudaEventElapsedTime(&ms, pe.second.first, pe.second.second));
+    c->timers[pe.first].ms += ms;
+    c->timers[pe.first].launches += 1;
+  }
+  c->ev_pending.clear();
+  c->ev_next = 0;
+  return LSP_OK;
+}
+
+// The launch sequence of steps a2-a7 for the sizes already prepared in the context.
+lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, bool upload) {
+  const int d = c->geo.d;
+  int32_t* counts = (int32_t*)c->counts.p;
+  CUDA_OK(c, cudaMemsetAsync(counts + kErrWord, 0, sizeof(int32_t), c->stream));
+  if (o.policy == LSP_SHIFT_LOCAL) {
+    const int64_t R = c->mrange.size();
+    CUDA_OK(c, cudaMemsetAsync(c->shift_flag.p, 0, round_up(R, 4096), c->stream));
+    CUDA_OK(c, launch_mark_local(c));
+    CUDA_OK(c, launch_compact(c, (const uint8_t*)c->shift_flag.p, c->mrange.lo, R,
+                              (int32_t*)c->shift_m.p, counts + 0, (int32_t*)c->idx_of.p));
+  } else if (upload) {
+    CUDA_OK(c, cudaMemcpyAsync(c->shift_m.p, c->h_list, sizeof(int32_t) * cap_s,
+                               cudaMemcpyHostToDevice, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(counts, c->h_list + cap_s, sizeof(int32_t),
+                               cudaMemcpyHostToDevice, c->stream));
+  }
+  const int32_t* list = (const int32_t*)c->shift_m.p;
+  const int32_t* count = counts + 0;
+  int64_t cap = cap_s;
+  for (int k = d - 1; k >= 1; --k) {
+    const int64_t sz = c->erange[k].size();
+    CUDA_OK(c, cudaMemsetAsync(c->eflag[k].p, 0, round_up(sz, 4096), c->stream));
+    CUDA_OK(c, launch_mark_stage(c, list, count, cap, c->erange[k].lo, (uint8_t*)c->eflag[k].p));
+    CUDA_OK(c, launch_compact(c, (const uint8_t*)c->eflag[k].p, c->erange[k].lo, sz,
+                              (int32_t*)c->elist[k].p, counts + (d - k), nullptr));
+    list = (const int32_t*)c->elist[k].p;
+    count = counts + (d - k);
+    cap = sz;
+  }
+  CUDA_OK(c, launch_wtable(c, c->erange[0].lo, c->erange[0].size(), (double*)c->wtab.p));
+  for (int k = 1; k <= d; ++k) {
+    const double* prev = k == 1 ? (const double*)c->wtab.p : (const double*)c->T[k - 1].p;
+    const int64_t lo_prev = c->erange[k - 1].lo, stride_prev = c->erange[k - 1].size();
+    if (k < d) {
+      CUDA_OK(c, launch_stage(c, d, k, (const int32_t*)c->elist[k].p, counts + (d - k),
+                              c->erange[k].size(), prev, lo_prev, stride_prev, (double*)c->T[k].p,
+                              c->erange[k].lo, c->erange[k].size(), false));
+    } else {
+      CUDA_OK(c, launch_stage(c, d, k, (const int32_t*)c->shift_m.p, counts + 0, cap_s, prev,
+                              lo_prev, stride_prev, (double*)c->gvals.p, 0, cap_s, true));
+    }
+  }
+  CUDA_OK(c, launch_eig(c, counts + 0, cap_s, o.eig_method, o.refine_steps));
+  CUDA_OK(c, launch_rows(c, o.policy, counts + 0));
+  return LSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void lsp_default_opts(lsp_stencil_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->t = 1;
+  o->policy = LSP_SHIFT_LOCAL;
+  o->mode = LSP_FP64;
+  o->eig_method = LSP_EIG_SYMMETRIC;
+}
+
+lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
+  if (!out) return LSP_ERR_ARG;
+  *out = nullptr;
+  if (d != 2 && d != 3) return LSP_ERR_ARG;
+  if (n < 8 || (n & (n - 1)) != 0 || n > (d == 2 ? 4096 : 256)) return LSP_ERR_ARG;
+  lsp_ctx* c = new (std::nothrow) lsp_ctx();
+  if (!c) return LSP_ERR_OOM;
+  c->stream = (cudaStream_t)cuda_stream;
+  build_geometry(c->geo, d, n);
+  if (!build_sym(c->sym, c->geo)) {
+    delete c;
+    return LSP_ERR_STATE;
+  }
+  lsp_status st = LSP_OK;
+  do {
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+      st = LSP_ERR_CUDA;
+      break;
+    }
+    if (cudaMallocHost(&c->h_stats, 8 * sizeof(double)) != cudaSuccess) {
+      st = LSP_ERR_OOM;
+      break;
+    }
+    if (upload_sym(c) != cudaSuccess) {
+      st = LSP_ERR_CUDA;
+      break;
+    }
+    // X_a(p) = w_p cos(2 pi a p / n), w_p = 1 at p = 0 and p = n/2, else 2
+    const int P = c->geo.P;
+    std::vector<double> X(3 * P);
+    const long double two_pi = 6.283185307179586476925286766559005768L;
+    for (int a = 0; a < 3; ++a)
+      for (int p = 0; p < P; ++p) {
+        const long double wgt = (p == 0 || p == n / 2) ? 1.0L : 2.0L;
+        const long double ang = two_pi * (long double)((a * p) % n) / (long double)n;
+        X[a * P + p] = (double)(wgt * cosl(ang));
+      }
+    // twiddles exp(-2 pi i j / n), j < n/2
+    std::vector<double> tw(n);
+    for (int j = 0; j < n / 2; ++j) {
+      const long double ang = two_pi * (long double)j / (long double)n;
+      tw[2 * j] = (double)cosl(ang);
+      tw[2 * j + 1] = (double)(-sinl(ang));
+    }
+    if (!ensure(c, c->xtab, sizeof(double) * X.size()) ||
+        !ensure(c, c->twiddle, sizeof(double) * tw.size()) ||
+        !ensure(c, c->stats, 8 * sizeof(double))) {
+      st = LSP_ERR_OOM;
+      break;
+    }
+    if (cudaMemcpy(c->xtab.p, X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(c->twiddle.p, tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      st = LSP_ERR_CUDA;
+      break;
+    }
+  } while (0);
+  if (st != LSP_OK) {
+    lsp_destroy(c);
+    return st;
+  }
+  *out = c;
+  return LSP_OK;
+}
+
+lsp_status lsp_destroy(lsp_ctx* c) {
+  if (!c) return LSP_OK;
+  cudaStreamSynchronize(c->stream);
+  DevBuf* bufs[] = {&c->v, &c->stats_part, &c->stats, &c->xtab, &c->shift_m, &c->shift_flag,
+                    &c->idx_of, &c->counts, &c->wtab, &c->gvals, &c->alpha, &c->cst, &c->lam,
+                    &c->sflags, &c->Q, &c->C, &c->P, &c->sidx, &c->colidx, &c->rowptr,
+                    &c->fftbuf, &c->twiddle};
+  for (DevBuf* b : bufs)
+    if (b->p) cudaFree(b->p);
+  for (int k = 0; k < kMaxD; ++k) {
+    if (c->eflag[k].p) cudaFree(c->eflag[k].p);
+    if (c->elist[k].p) cudaFree(c->elist[k].p);
+    if (c->T[k].p) cudaFree(c->T[k].p);
+  }
+  if (c->h_stats) cudaFreeHost(c->h_stats);
+  if (c->h_list) cudaFreeHost(c->h_list);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  delete c;
+  return LSP_OK;
+}
+
+lsp_status lsp_set_potential(lsp_ctx* c, const double* v, int v_on_device) {
+  if (!c) return LSP_ERR_ARG;
+  if (!v) return fail(c, LSP_ERR_ARG, "v is NULL");
+  const int64_t N = c->geo.N;
+  if (!ensure(c, c->v, sizeof(double) * N)) return LSP_ERR_OOM;
+  CUDA_OK(c, cudaMemcpyAsync(c->v.p, v, sizeof(double) * N,
+                             v_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                             c->stream));
+  int nb = (int)std::min<int64_t>(152 * 4, (N + 255) / 256);
+  if (!ensure(c, c->stats_part, sizeof(double) * 4 * nb)) return LSP_ERR_OOM;
+  CUDA_OK(c, launch_stats_partial(c, nb));
+  CUDA_OK(c, launch_stats_final(c, nb));
+  CUDA_OK(c, cudaMemcpyAsync(c->h_stats, c->stats.p, 4 * sizeof(double), cudaMemcpyDeviceToHost,
+                             c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  c->have_v = false;
+  c->built = false;
+  if (c->h_stats[3] > 0)
+    return fail(c, LSP_ERR_ARG, "v holds %.0f NaN/Inf values", c->h_stats[3]);
+  c->vmin = c->h_stats[0];
+  c->vmax = c->h_stats[1];
+  c->vmean = c->h_stats[2] / (double)N;
+  const double half = (double)(c->geo.n / 2);
+  const double lim = 1073741824.0 - c->geo.d * half * half - 16;
+  if (fabs((double)snap_host(c->vmin)) > lim || fabs((double)snap_host(c->vmax)) > lim)
+    return fail(c, LSP_ERR_ARG, "potential range [%g, %g] exceeds the lattice index range",
+                c->vmin, c->vmax);
+  c->have_v = true;
+  return LSP_OK;
+}
+
+lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
+  if (!c) return LSP_ERR_ARG;
+  lsp_stencil_opts o;
+  if (opts)
+    o = *opts;
+  else
+    lsp_default_opts(&o);
+  if (!c->have_v) return fail(c, LSP_ERR_STATE, "build_stencils before set_potential");
+  if (o.t != 1) return fail(c, LSP_ERR_UNSUPPORTED, "only t = 1 neighbourhoods are built");
+  if (o.mode != LSP_FP64) return fail(c, LSP_ERR_UNSUPPORTED, "mode %d not built", o.mode);
+  if (o.policy < 0 || o.policy > 3) return fail(c, LSP_ERR_ARG, "bad policy %d", o.policy);
+  if (o.eig_method != LSP_EIG_SYMMETRIC && o.eig_method != LSP_EIG_FULL)
+    return fail(c, LSP_ERR_ARG, "bad eig_method %d", o.eig_method);
+  if (o.refine_steps < 0 || o.refine_steps > 4)
+    return fail(c, LSP_ERR_ARG, "refine_steps must be in [0, 4]");
+  const int d = c->geo.d, n = c->geo.n;
+  const int64_t N = c->geo.N;
+  const int mu = c->geo.mu;
+  c->built = false;
+
+  // ---- a2: the shift set ----
+  std::vector<int64_t> ms;
+  int64_t cap_s = 0;
+  if (o.policy == LSP_SHIFT_LOCAL) {
+    c->mrange.lo = snap_host(c->vmin);
+    c->mrange.hi = snap_host(c->vmax);
+    cap_s = c->mrange.size();
+  } else {
+    if (o.policy == LSP_SHIFT_PAPER) {
+      int K = o.nshifts > 0 ? o.nshifts : std::max(2, d == 2 ? n / 16 : n / 4);
+      if (K == 1) {
+        ms.push_back(snap_host(c->vmin));
+      } else {
+        volatile double step = (c->vmax - c->vmin) / (double)(K - 1);
+        for (int i = 0; i < K - 1; ++i) {
+          volatile double prod = (double)i * step;
+          volatile double x = c->vmin + prod;
+          ms.push_back(snap_host(x));
+        }
+        ms.push_back(snap_host(c->vmax));
+      }
+    } else if (o.policy == LSP_SHIFT_MEAN) {
+      ms.push_back(snap_host(c->vmean));
+    } else {
+      if (!o.shifts || o.nshifts < 1) return fail(c, LSP_ERR_ARG, "LIST policy needs shifts");
+      for (int i = 0; i < o.nshifts; ++i) {
+        const double s = o.shifts[i];
+        if (!isfinite(s)) return fail(c, LSP_ERR_ARG, "shift %d is not finite", i);
+        // resonance: s = -4 pi^2 |k|^2 for some k in K makes L + s singular (Sec. 3)
+        const double r = -s / (4.0 * kPi2);
+        const double rr = round(r);
+        if (rr >= 0 && rr <= d * (double)(n / 2) * (n / 2) && fabs(r - rr) < 1e-12 * (1 + rr) &&
+            is_norm((int64_t)rr, d, n / 2))
+          return fail(c, LSP_ERR_RESONANT_SHIFT, "shift %.17g is an eigenvalue of -L", s);
+        const int64_t m = snap_host(s);
+        if (shift_host(m) != s)
+          return fail(c, LSP_ERR_ARG, "shift %.17g is not on the lattice (4m+2) pi^2", s);
+        ms.push_back(m);
+      }
+    }
+    std::sort(ms.begin(), ms.end());
+    ms.erase(std::unique(ms.begin(), ms.end()), ms.end());
+    c->mrange.lo = ms.front();
+    c->mrange.hi = ms.back();
+    cap_s = (int64_t)ms.size();
+  }
+  const int64_t half2 = (int64_t)(n / 2) * (n / 2);
+  c->erange[d] = c->mrange;
+  for (int k = d - 1; k >= 0; --k) {
+    c->erange[k].lo = c->erange[k + 1].lo;
+    c->erange[k].hi = c->erange[k + 1].hi + half2;
+  }
+  if (c->erange[0].hi > 2147483000LL || c->erange[0].lo < -2147483000LL)
+    return fail(c, LSP_ERR_ARG, "shift range too large for 32-bit lattice indices");
+
+  // ---- buffers (all allocation happens before any capture) ----
+  const int64_t R = c->mrange.size();
+  bool ok = ensure(c, c->shift_m, sizeof(int32_t) * cap_s) &&
+            ensure(c, c->counts, sizeof(int32_t) * (16 + 2 + c->erange[0].size() / 4096 + 16)) &&
+            ensure(c, c->gvals, sizeof(double) * 2 * c->geo.ncls * cap_s) &&
+            ensure(c, c->alpha, sizeof(double) * mu * cap_s) &&
+            ensure(c, c->cst, sizeof(double) * mu * cap_s) &&
+            ensure(c, c->lam, sizeof(double) * 2 * cap_s) &&
+            ensure(c, c->sflags, sizeof(int32_t) * cap_s) &&
+            ensure(c, c->wtab, sizeof(double) * c->erange[0].size()) &&
+            ensure(c, c->Q, sizeof(double) * mu * N) && ensure(c, c->C, sizeof(double) * mu * N) &&
+            ensure(c, c->P, sizeof(double) * mu * N);
+  if (ok && o.policy == LSP_SHIFT_LOCAL)
+    ok = ensure(c, c->shift_flag, round_up(R, 4096)) && ensure(c, c->idx_of, sizeof(int32_t) * R);
+  for (int k = 1; ok && k < d; ++k) {
+    const int64_t sz = c->erange[k].size();
+    ok = ensure(c, c->eflag[k], round_up(sz, 4096)) && ensure(c, c->elist[k], sizeof(int32_t) * sz) &&
+         ensure(c, c->T[k], sizeof(double) * 2 * ncls_stage(k) * sz);
+  }
+  if (!ok) return LSP_ERR_OOM;
+  if (o.policy != LSP_SHIFT_LOCAL) {
+    if (c->h_list_cap < cap_s + 1) {
+      if (c->h_list) cudaFreeHost(c->h_list);
+      c->h_list = nullptr;
+      c->h_list_cap = 0;
+      if (cudaMallocHost(&c->h_list, sizeof(int32_t) * (cap_s + 1)) != cudaSuccess)
+        return fail(c, LSP_ERR_OOM, "pinned allocation failed");
+      c->h_list_cap = cap_s + 1;
+    }
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));  // the staging buffer may still be in use
+    for (int64_t i = 0; i < cap_s; ++i) c->h_list[i] = (int32_t)ms[i];
+    c->h_list[cap_s] = (int32_t)cap_s;
+    CUDA_OK(c, cudaMemcpyAsync(c->shift_m.p, c->h_list, sizeof(int32_t) * cap_s,
+                               cudaMemcpyHostToDevice, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(c->counts.p, c->h_list + cap_s, sizeof(int32_t),
+                               cudaMemcpyHostToDevice, c->stream));
+  }
+  c->ns_host = o.policy == LSP_SHIFT_LOCAL ? -1 : cap_s;
+  c->last_policy = o.policy;
+
+  lsp_status st;
+  if (o.use_graph && !c->timing) {
+    std::vector<int64_t> key = {o.policy, o.eig_method, o.refine_steps, cap_s, c->mrange.lo,
+                                c->mrange.hi, (int64_t)(intptr_t)c->v.p,
+                                (int64_t)(intptr_t)c->Q.p};
+    for (int k = 0; k <= d; ++k) key.push_back(c->erange[k].lo);
+    if (!c->graph || key != c->graph_key) {
+      if (c->graph) cudaGraphExecDestroy(c->graph);
+      c->graph = nullptr;
+      cudaGraph_t g;
+      CUDA_OK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+      st = issue_build(c, o, cap_s, false);
+      cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+      if (st != LSP_OK) return st;
+      CUDA_OK(c, ce);
+      ce = cudaGraphInstantiate(&c->graph, g, 0);
+      cudaGraphDestroy(g);
+      CUDA_OK(c, ce);
+      c->graph_key = key;
+    }
+    CUDA_OK(c, cudaGraphLaunch(c->graph, c->stream));
+    st = LSP_OK;
+  } else {
+    st = issue_build(c, o, cap_s, false);
+  }
+  if (st == LSP_OK) c->built = true;
+  return st;
+}
+
+lsp_status lsp_apply_operator(lsp_ctx* c, const double* u, double* y) {
+  if (!c) return LSP_ERR_ARG;
+  if (!u || !y) return fail(c, LSP_ERR_ARG, "u or y is NULL");
+  if (!c->have_v) return fail(c, LSP_ERR_STATE, "apply_operator before set_potential");
+  if (!ensure(c, c->fftbuf, sizeof(double) * 2 * c->geo.N)) return LSP_ERR_OOM;
+  CUDA_OK(c, launch_apply(c, u, y));
+  return LSP_OK;
+}
+
+static lsp_status rows_of(lsp_ctx* c, char which, const double** out) {
+  if (!c->built) return fail(c, LSP_ERR_STATE, "no stencils built");
+  switch (which) {
+    case 'Q': *out = (const double*)c->Q.p; return LSP_OK;
+    case 'C': *out = (const double*)c->C.p; return LSP_OK;
+    case 'P': *out = (const double*)c->P.p; return LSP_OK;
+    default: return fail(c, LSP_ERR_ARG, "which must be 'Q', 'C' or 'P'");
+  }
+}
+
+lsp_status lsp_get_rows(lsp_ctx* c, char which, double* rows, int on_device) {
+  if (!c) return LSP_ERR_ARG;
+  if (!rows) return fail(c, LSP_ERR_ARG, "rows is NULL");
+  const double* src;
+  lsp_status st = rows_of(c, which, &src);
+  if (st != LSP_OK) return st;
+  const size_t bytes = sizeof(double) * c->geo.mu * c->geo.N;
+  CUDA_OK(c, cudaMemcpyAsync(rows, src, bytes,
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             c->stream));
+  if (!on_device) CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return LSP_OK;
+}
+
+lsp_status lsp_export_sparse_rows(lsp_ctx* c, char which, int64_t* rowptr, int32_t* colidx,
+                                  double* vals, int64_t* nnz_out) {
+  if (!c) return LSP_ERR_ARG;
+  const int64_t nnz = c->geo.N * c->geo.mu;
+  if (nnz_out) *nnz_out = nnz;
+  if (!rowptr && !colidx && !vals) return LSP_OK;
+  if (!rowptr || !colidx || !vals)
+    return fail(c, LSP_ERR_ARG, "rowptr, colidx and vals must all be given");
+  const double* src;
+  lsp_status st = rows_of(c, which, &src);
+  if (st != LSP_OK) return st;
+  if (!ensure(c, c->colidx, sizeof(int32_t) * nnz) ||
+      !ensure(c, c->rowptr, sizeof(int64_t) * (c->geo.N + 1)))
+    return LSP_ERR_OOM;
+  CUDA_OK(c, launch_colidx(c));
+  CUDA_OK(c, cudaMemcpyAsync(colidx, c->colidx.p, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost,
+                             c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(rowptr, c->rowptr.p, sizeof(int64_t) * (c->geo.N + 1),
+                             cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaMemcpyAsync(vals, src, sizeof(double) * nnz, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return LSP_OK;
+}
+
+lsp_status lsp_get_shift_table(lsp_ctx* c, int64_t* nshifts_out, double* s, double* alpha,
+                               double* cst, double* lam, int32_t* flags, int32_t* s_idx) {
+  if (!c) return LSP_ERR_ARG;
+  if (!c->built) return fail(c, LSP_ERR_STATE, "no stencils built");
+  int32_t head[16];
+  CUDA_OK(c, cudaMemcpyAsync(head, c->counts.p, sizeof(head), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  const int32_t ns = head[0];
+  if (head[kErrWord] != 0)
+    return fail(c, LSP_ERR_STATE, "device lattice snap disagreed with the host (bits %d)",
+                head[kErrWord]);
+  if (nshifts_out) *nshifts_out = ns;
+  const int mu = c->geo.mu;
+  if (s) {
+    std::vector<int32_t> m(ns);
+    CUDA_OK(c, cudaMemcpy(m.data(), c->shift_m.p, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < ns; ++i) s[i] = shift_host(m[i]);
+  }
+  if (alpha)
+    CUDA_OK(c, cudaMemcpy(alpha, c->alpha.p, sizeof(double) * mu * ns, cudaMemcpyDeviceToHost));
+  if (cst) CUDA_OK(c, cudaMemcpy(cst, c->cst.p, sizeof(double) * mu * ns, cudaMemcpyDeviceToHost));
+  if (lam) CUDA_OK(c, cudaMemcpy(lam, c->lam.p, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost));
+  if (flags)
+    CUDA_OK(c, cudaMemcpy(flags, c->sflags.p, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost));
+  if (s_idx) {
+    if (!ensure(c, c->sidx, sizeof(int32_t) * c->geo.N)) return LSP_ERR_OOM;
+    CUDA_OK(c, launch_sidx(c, c->last_policy, (const int32_t*)c->counts.p));
+    CUDA_OK(c, cudaMemcpyAsync(s_idx, c->sidx.p, sizeof(int32_t) * c->geo.N,
+                               cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  }
+  return LSP_OK;
+}
+
+lsp_status lsp_get_sizes(const lsp_ctx* c, int64_t* npoints, int* mu) {
+  if (!c) return LSP_ERR_ARG;
+  if (npoints) *npoints = c->geo.N;
+  if (mu) *mu = c->geo.mu;
+  return LSP_OK;
+}
+
+lsp_status lsp_synchronize(lsp_ctx* c) {
+  if (!c) return LSP_ERR_ARG;
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  CUDA_OK(c, cudaGetLastError());
+  return LSP_OK;
+}
+
+lsp_status lsp_kernel_timing(lsp_ctx* c, int enable) {
+  if (!c) return LSP_ERR_ARG;
+  lsp_status st = flush_timers(c);
+  if (st != LSP_OK) return st;
+  if (enable) c->timers.clear();
+  c->timing = enable != 0;
+  return LSP_OK;
+}
+
+lsp_status lsp_kernel_times(lsp_ctx* c, int cap, char (*names)[32], double* ms, int64_t* launches,
+                            int* count) {
+  if (!c) return LSP_ERR_ARG;
+  lsp_status st = flush_timers(c);
+  if (st != LSP_OK) return st;
+  if (count) *count = (int)c->timers.size();
+  for (int i = 0; i < cap && i < (int)c->timers.size(); ++i) {
+    if (names) {
+      strncpy(names[i], c->timers[i].name.c_str(), 31);
+      names[i][31] = 0;
+    }
+    if (ms) ms[i] = c->timers[i].ms;
+    if (launches) launches[i] = c->timers[i].launches;
+  }
+  return LSP_OK;
+}
+
+const char* lsp_last_error(const lsp_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+}  // extern "C"

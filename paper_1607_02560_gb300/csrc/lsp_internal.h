@@ -1,0 +1,145 @@
+// Internal declarations shared by the translation units of liblsp.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lsp.h"
+
+namespace lsp {
+
+// pi^2 as the correctly rounded product of the double nearest pi. Kept identical on host and
+// device so that lattice snapping takes bit-identical decisions everywhere.
+constexpr double kPi = 3.141592653589793;
+constexpr double kPi2 = kPi * kPi;
+
+constexpr int kMaxD = 3;
+constexpr int kMaxMu = 27;      // (2t+1)^d for t = 1, d = 3
+constexpr int kMaxCls = 10;     // sorted |offset| tuples over {0,1,2}^d, d = 3
+constexpr int kMaxSymVec = 13;  // symmetry-adapted basis vectors (3D)
+constexpr int kMaxSymBlk = 6;
+// counts[] layout: [0] |S|, [1], [2] sizes of the compacted stage domains, [kErrWord] device
+// error bits, [16...] compaction tile scratch.
+constexpr int kErrWord = 15;
+
+// Symmetry-adapted basis of R^{|mu|} for the hyperoctahedral group acting on mu_0 (t = 1):
+// one row of every irreducible representation that occurs. Block b has `dim` basis vectors
+// (its multiplicity in mu_0) and stands for `copies` identical blocks (the irrep dimension).
+struct SymBasis {
+  int nblk;
+  int dim[kMaxSymBlk];
+  int copies[kMaxSymBlk];
+  int first[kMaxSymBlk];          // index of its first vector
+  int nvec;
+  double u[kMaxSymVec][kMaxMu];   // orthonormal vectors, dense over mu_0
+};
+
+// Offset tables for t = 1.
+struct Geometry {
+  int d, n, mu, ncls, centre;
+  int64_t N;
+  int P;                           // n/2 + 1 frequencies per axis in [0, n/2]
+  int off[kMaxMu][kMaxD];          // mu_0 offsets, lexicographic
+  uint8_t cls_of[kMaxMu][kMaxMu];  // class of o_a - o_b (sorted |components|)
+};
+
+struct Range {
+  int64_t lo = 0, hi = -1;  // inclusive
+  int64_t size() const { return hi >= lo ? hi - lo + 1 : 0; }
+};
+
+// Device buffer that only grows.
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct KernelTimer {
+  std::string name;
+  double ms = 0;
+  int64_t launches = 0;
+};
+
+}  // namespace lsp
+
+struct lsp_ctx {
+  lsp::Geometry geo;
+  lsp::SymBasis sym;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // potential and its statistics (a1)
+  bool have_v = false;
+  double vmin = 0, vmax = 0, vmean = 0;
+  lsp::DevBuf v, stats_part, stats;
+  double* h_stats = nullptr;  // pinned
+
+  // cos table X_a(p) = w_p cos(2 pi a p / n), a = 0..2, p = 0..n/2
+  lsp::DevBuf xtab;
+
+  // shift list (a2)
+  bool built = false;
+  int last_policy = -1;
+  int64_t ns_host = -1;          // |S| when known on the host, else -1
+  lsp::Range mrange;             // lattice index range covering S
+  lsp::DevBuf shift_m, shift_flag, idx_of, counts;
+  int32_t* h_list = nullptr;     // pinned staging for host-made shift lists
+  int64_t h_list_cap = 0;
+
+  // lattice-separable stages (a3)
+  lsp::Range erange[lsp::kMaxD + 1];  // E_k ranges; E_d = shifts, E_0 = table domain
+  lsp::DevBuf eflag[lsp::kMaxD], elist[lsp::kMaxD], T[lsp::kMaxD], wtab;
+
+  // per-shift results (a3-a6)
+  lsp::DevBuf gvals, alpha, cst, lam, sflags;
+
+  // rows (a7) and export
+  lsp::DevBuf Q, C, P, sidx, colidx, rowptr;
+
+  // FFT (apply_operator)
+  lsp::DevBuf fftbuf, twiddle;
+
+  // timing
+  bool timing = false;
+  std::vector<lsp::KernelTimer> timers;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  size_t ev_next = 0;
+
+  // graph cache
+  cudaGraphExec_t graph = nullptr;
+  std::vector<int64_t> graph_key;
+};
+
+namespace lsp {
+
+// ---- host helpers (lsp_api.cu) ----
+bool ensure(lsp_ctx* ctx, DevBuf& b, size_t bytes);
+int timer_begin(lsp_ctx* ctx, const char* name);
+void timer_end(lsp_ctx* ctx, int slot);
+
+// ---- launchers; each returns cudaGetLastError() after the launch ----
+cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks);
+cudaError_t launch_stats_final(lsp_ctx* c, int nblocks);
+cudaError_t launch_mark_local(lsp_ctx* c);
+cudaError_t launch_compact(lsp_ctx* c, const uint8_t* flags, int64_t lo, int64_t range,
+                           int32_t* list, int32_t* count, int32_t* idx_of);
+cudaError_t launch_mark_stage(lsp_ctx* c, const int32_t* list, const int32_t* count,
+                              int64_t cap, int64_t lo_prev, uint8_t* flag_prev);
+cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, double* w);
+cudaError_t launch_stage(lsp_ctx* c, int d, int k, const int32_t* list, const int32_t* count,
+                         int64_t cap, const double* Tprev, int64_t lo_prev, int64_t stride_prev,
+                         double* Tout, int64_t lo_out, int64_t stride_out, bool by_index);
+cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int eig_method,
+                       int refine_steps);
+cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count);
+cudaError_t launch_sidx(lsp_ctx* c, int policy, const int32_t* count);
+cudaError_t launch_colidx(lsp_ctx* c);
+cudaError_t launch_apply(lsp_ctx* c, const double* u, double* y);
+cudaError_t upload_sym(lsp_ctx* c);
+
+}  // namespace lsp

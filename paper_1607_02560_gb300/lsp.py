@@ -1,0 +1,235 @@
+"""Thin Python binding of the C ABI in include/lsp.h (argument marshalling only).
+
+Every step of the stencil setup runs in liblsp.so's CUDA kernels; this module only converts
+arrays to pointers and status codes to exceptions. Device buffers are torch CUDA tensors
+(PyTorch provides device memory and the stream); host buffers are numpy arrays. There is no
+CPU fallback: without liblsp.so or a CUDA device the calls raise.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblsp.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "lsp.h")
+
+LSP_OK = 0
+STATUS = {0: "LSP_OK", 1: "LSP_ERR_ARG", 2: "LSP_ERR_STATE", 3: "LSP_ERR_RESONANT_SHIFT",
+          4: "LSP_ERR_CUDA", 5: "LSP_ERR_OOM", 6: "LSP_ERR_TIMEOUT", 7: "LSP_ERR_DEGENERATE",
+          8: "LSP_ERR_UNSUPPORTED"}
+POLICY = {"paper": 0, "local": 1, "list": 2, "mean": 3}
+MODE = {"fp64": 0, "mixed": 1, "learned": 2}
+EIG = {"symmetric": 0, "full": 1}
+FLAG_DEGENERATE, FLAG_NONSYMMETRIC, FLAG_NOT_CONVERGED = 1, 2, 4
+
+
+class LspError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class StencilOpts(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_int), ("policy", ctypes.c_int), ("nshifts", ctypes.c_int),
+                ("shifts", ctypes.POINTER(ctypes.c_double)), ("mode", ctypes.c_int),
+                ("refine_steps", ctypes.c_int), ("eig_method", ctypes.c_int),
+                ("use_graph", ctypes.c_int)]
+
+
+_lib = None
+
+
+def declared_symbols() -> list[str]:
+    """Names of the functions declared in include/lsp.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsp_[a-z_0-9]+)\s*\(", text)))
+
+
+def lib() -> ctypes.CDLL:
+    """Load liblsp.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_1607_02560_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "lsp_default_opts": (None, [ctypes.POINTER(StencilOpts)]),
+        "lsp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+        "lsp_destroy": (ctypes.c_int, [vp]),
+        "lsp_set_potential": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "lsp_build_stencils": (ctypes.c_int, [vp, ctypes.POINTER(StencilOpts)]),
+        "lsp_apply_operator": (ctypes.c_int, [vp, vp, vp]),
+        "lsp_get_rows": (ctypes.c_int, [vp, ctypes.c_char, vp, ctypes.c_int]),
+        "lsp_export_sparse_rows": (ctypes.c_int, [vp, ctypes.c_char, vp, vp, vp, i64p]),
+        "lsp_get_shift_table": (ctypes.c_int, [vp, i64p, vp, vp, vp, vp, vp, vp]),
+        "lsp_get_sizes": (ctypes.c_int, [vp, i64p, ctypes.POINTER(ctypes.c_int)]),
+        "lsp_synchronize": (ctypes.c_int, [vp]),
+        "lsp_kernel_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lsp_kernel_times": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp,
+                                             ctypes.POINTER(ctypes.c_int)]),
+        "lsp_last_error": (ctypes.c_char_p, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _ptr(a) -> int | None:
+    """Address of a torch tensor's or numpy array's storage (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(type(a))
+
+
+def _on_device(a) -> int:
+    return int(hasattr(a, "is_cuda") and a.is_cuda)
+
+
+def default_opts() -> StencilOpts:
+    o = StencilOpts()
+    lib().lsp_default_opts(ctypes.byref(o))
+    return o
+
+
+class Context:
+    """An lsp_ctx: one grid (d, n) on one CUDA stream."""
+
+    def __init__(self, d: int, n: int, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = lib().lsp_create(d, n, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if st != LSP_OK:
+            raise LspError(st, f"lsp_create(d={d}, n={n}) failed")
+        self.h = h
+        self.d, self.n = d, n
+        N = ctypes.c_int64()
+        mu = ctypes.c_int()
+        lib().lsp_get_sizes(self.h, ctypes.byref(N), ctypes.byref(mu))
+        self.N, self.mu = N.value, mu.value
+        self._keep = None
+
+    def _check(self, st: int, what: str):
+        if st != LSP_OK:
+            msg = lib().lsp_last_error(self.h)
+            raise LspError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lsp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- the calls of include/lsp.h ----
+    def set_potential(self, v):
+        """v: torch CUDA tensor or numpy array, n^d float64 (a1)."""
+        if getattr(v, "dtype", None) not in (np.float64,) and str(getattr(v, "dtype", "")) != "torch.float64":
+            raise TypeError("v must be float64")
+        if int(np.prod(v.shape)) != self.N:
+            raise ValueError("v has the wrong size")
+        self._check(lib().lsp_set_potential(self.h, _ptr(v), _on_device(v)), "set_potential")
+
+    def build_stencils(self, policy="local", nshifts=0, shifts=None, mode="fp64",
+                       refine_steps=0, eig_method="symmetric", use_graph=False, t=1):
+        """Steps a2-a7 (asynchronous on the context stream)."""
+        o = StencilOpts()
+        o.t = t
+        o.policy = POLICY[policy] if isinstance(policy, str) else int(policy)
+        o.mode = MODE[mode] if isinstance(mode, str) else int(mode)
+        o.refine_steps = refine_steps
+        o.eig_method = EIG[eig_method] if isinstance(eig_method, str) else int(eig_method)
+        o.use_graph = int(bool(use_graph))
+        o.nshifts = int(nshifts)
+        if shifts is not None:
+            arr = np.ascontiguousarray(shifts, dtype=np.float64)
+            self._keep = arr
+            o.shifts = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            o.nshifts = len(arr)
+        self._check(lib().lsp_build_stencils(self.h, ctypes.byref(o)), "build_stencils")
+
+    def apply_operator(self, u, y):
+        """y = (L + diag v) u for torch CUDA tensors u, y (n^d float64)."""
+        if not (_on_device(u) and _on_device(y)):
+            raise ValueError("apply_operator takes device tensors")
+        self._check(lib().lsp_apply_operator(self.h, _ptr(u), _ptr(y)), "apply_operator")
+
+    def get_rows(self, which: str, out=None):
+        """Dense [n^d, |mu|] rows of Q, C or P into `out` (torch CUDA tensor or numpy array)."""
+        if out is None:
+            out = np.empty((self.N, self.mu), dtype=np.float64)
+        self._check(lib().lsp_get_rows(self.h, which.encode(), _ptr(out), _on_device(out)),
+                    "get_rows")
+        return out
+
+    def export_sparse_rows(self, which: str):
+        """(rowptr int64, colidx int32, vals float64) in host memory."""
+        nnz = ctypes.c_int64()
+        self._check(lib().lsp_export_sparse_rows(self.h, which.encode(), None, None, None,
+                                                 ctypes.byref(nnz)), "export size")
+        rowptr = np.empty(self.N + 1, dtype=np.int64)
+        colidx = np.empty(nnz.value, dtype=np.int32)
+        vals = np.empty(nnz.value, dtype=np.float64)
+        self._check(lib().lsp_export_sparse_rows(self.h, which.encode(), _ptr(rowptr),
+                                                 _ptr(colidx), _ptr(vals), ctypes.byref(nnz)),
+                    "export_sparse_rows")
+        return rowptr, colidx, vals
+
+    def get_shift_table(self, with_sidx=True):
+        ns = ctypes.c_int64()
+        self._check(lib().lsp_get_shift_table(self.h, ctypes.byref(ns), None, None, None, None,
+                                              None, None), "shift table size")
+        k = ns.value
+        out = dict(s=np.empty(k), alpha=np.empty((k, self.mu)), c=np.empty((k, self.mu)),
+                   lam=np.empty((k, 2)), flags=np.empty(k, dtype=np.int32),
+                   s_idx=np.empty(self.N, dtype=np.int32) if with_sidx else None)
+        self._check(lib().lsp_get_shift_table(self.h, ctypes.byref(ns), _ptr(out["s"]),
+                                              _ptr(out["alpha"]), _ptr(out["c"]),
+                                              _ptr(out["lam"]), _ptr(out["flags"]),
+                                              _ptr(out["s_idx"])), "get_shift_table")
+        return out
+
+    def synchronize(self):
+        self._check(lib().lsp_synchronize(self.h), "synchronize")
+
+    def kernel_timing(self, enable: bool):
+        self._check(lib().lsp_kernel_timing(self.h, int(bool(enable))), "kernel_timing")
+
+    def kernel_times(self) -> dict:
+        cap = 64
+        names = (ctypes.c_char * 32 * cap)()
+        ms = np.zeros(cap)
+        launches = np.zeros(cap, dtype=np.int64)
+        cnt = ctypes.c_int()
+        self._check(lib().lsp_kernel_times(self.h, cap, names, _ptr(ms), _ptr(launches),
+                                           ctypes.byref(cnt)), "kernel_times")
+        return {names[i].value.decode(): (float(ms[i]), int(launches[i]))
+                for i in range(min(cnt.value, cap))}

@@ -1,0 +1,271 @@
+"""GPU path (liblsp.so through the C ABI) against the CPU oracle.
+
+Tolerances. The near-null vector alpha of A = A1 - A2 (Eq. A) moves by about u * kappa under
+a rounding-level change of A, with kappa = max|lambda| / (lambda_2 - lambda_1) and u = 2^-53;
+the oracle itself shows this spread when its inverse-FFT kernel vectors are replaced by
+long-double direct sums. So alpha is compared entrywise with
+    tol_alpha = max(1e-10, 16 u kappa)
+(kappa <= ~600 in 2D, so 1e-10 there; ~2e6 in 3D), and c = G alpha and the P rows inherit
+the bound through their formulas:
+    tol_c = tol_alpha * max_b sum_a |G[a, b]| + 1e-13 max|c|,
+    tol_P = tol_alpha + tol_c * max|v[mu_j] - s_j| + 1e-13 max|P|.
+Shift lists, per-point shift indices and CSR patterns are integer results: compared exactly.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from lsp_inputs import gaussian_source, make_workload
+
+pytestmark = pytest.mark.gpu
+
+U = 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1607_02560_gb300 import build as B
+    B.build()
+
+
+def ctx_for(v):
+    from paper_1607_02560_gb300 import Context
+    return Context(v.ndim, v.shape[0])
+
+
+def shift_tols(n, d, s):
+    st = O.stencil_for_shift(n, d, float(s))
+    w = np.linalg.eigvalsh(st["A"])
+    kappa = np.abs(w).max() / max(w[1] - w[0], 1e-300)
+    ta = max(1e-10, 16 * U * kappa)
+    offs = O.neighbourhood_offsets(d)
+    Gm = O._gather(st["g"], offs, n)
+    tc = ta * np.abs(Gm).sum(axis=0).max() + 1e-13 * np.abs(st["c"]).max()
+    return st, ta, tc
+
+
+def check_shift_table(tab, v, policy, nshifts=None, m_list=None, sample=None):
+    n, d = v.shape[0], v.ndim
+    ref = O.build_stencils(v, policy, nshifts=nshifts, m_list=m_list, shift_subset=[])
+    assert np.array_equal(tab["s"], ref["S"]), "shift list differs"
+    assert np.array_equal(tab["s_idx"].reshape(v.shape), ref["s_idx"]), "s_j differs"
+    idx = range(len(ref["S"])) if sample is None else sample
+    tols = {}
+    for i in idx:
+        st, ta, tc = shift_tols(n, d, ref["S"][i])
+        ea = np.abs(tab["alpha"][i] - st["alpha"]).max()
+        ec = np.abs(tab["c"][i] - st["c"]).max()
+        assert ea <= ta, (i, ea, ta)
+        assert ec <= tc, (i, ec, tc)
+        assert abs(tab["lam"][i, 0] - st["lam1"]) <= 1e-9 * np.abs(st["A"]).max()
+        tols[i] = (ta, tc)
+    return ref, tols
+
+
+def check_rows(ctx, v, ref, tols):
+    """Rows at every point whose shift has an oracle stencil in `tols`."""
+    d = v.ndim
+    offs = O.neighbourhood_offsets(d)
+    Q, C, P = (ctx.get_rows(k) for k in "QCP")
+    sidx = ref["s_idx"].reshape(-1)
+    vnb = np.stack([np.roll(v, tuple(-o for o in off), axis=tuple(range(d))) for off in offs],
+                   axis=-1).reshape(-1, len(offs))
+    checked = 0
+    for i, (ta, tc) in tols.items():
+        pts = np.nonzero(sidx == i)[0]
+        if len(pts) == 0:
+            continue
+        st = O.stencil_for_shift(v.shape[0], d, float(ref["S"][i]))
+        s = ref["S"][i]
+        eP = st["alpha"][None, :] + st["c"][None, :] * (vnb[pts] - s)
+        tp = ta + tc * np.abs(vnb[pts] - s).max() + 1e-13 * np.abs(eP).max()
+        assert np.abs(Q[pts] - st["alpha"]).max() <= ta
+        assert np.abs(C[pts] - st["c"]).max() <= tc
+        assert np.abs(P[pts] - eP).max() <= tp
+        checked += len(pts)
+    return checked
+
+
+def rows_consistent_with_table(ctx, v, tab):
+    """Every row equals the formula of Sec. 4.1 applied to the GPU's own shift table."""
+    d = v.ndim
+    offs = O.neighbourhood_offsets(d)
+    Q, C, P = (ctx.get_rows(k) for k in "QCP")
+    sidx = tab["s_idx"].astype(np.int64)
+    assert np.array_equal(Q, tab["alpha"][sidx])
+    assert np.array_equal(C, tab["c"][sidx])
+    vnb = np.stack([np.roll(v, tuple(-o for o in off), axis=tuple(range(d))) for off in offs],
+                   axis=-1).reshape(-1, len(offs))
+    eP = tab["alpha"][sidx] + tab["c"][sidx] * (vnb - tab["s"][sidx][:, None])
+    assert np.abs(P - eP).max() <= 4e-16 * (np.abs(eP).max() + np.abs(tab["c"]).max()
+                                             * np.abs(vnb).max())
+
+
+SMALL = [("helm2d_n32", 8), ("helm2d_n32", 16), ("helm2d_n32", 32), ("helm2d_n256", 64),
+         ("schr3d_n64", 8), ("schr3d_n64", 16)]
+
+
+@pytest.mark.parametrize("name,n", SMALL)
+@pytest.mark.parametrize("policy", ["local", "paper", "mean"])
+def test_small_parity(name, n, policy):
+    v = make_workload(name, n=n)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy=policy)
+    tab = ctx.get_shift_table()
+    ref, tols = check_shift_table(tab, v, policy)
+    assert check_rows(ctx, v, ref, tols) == v.size
+    rows_consistent_with_table(ctx, v, tab)
+
+
+@pytest.mark.parametrize("name,n", [("helm2d_n256", 64), ("schr3d_n64", 16)])
+def test_full_jacobi_and_refinement_match(name, n):
+    v = make_workload(name, n=n)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    for kw in (dict(eig_method="full"), dict(refine_steps=1),
+               dict(eig_method="full", refine_steps=1)):
+        ctx.build_stencils(policy="local", **kw)
+        tab = ctx.get_shift_table()
+        check_shift_table(tab, v, "local")
+        assert not np.any(tab["flags"] & 4)
+
+
+def test_list_policy_and_errors():
+    import torch
+    from paper_1607_02560_gb300 import LspError
+    v = make_workload("helm2d_n32", n=16)
+    ctx = ctx_for(v)
+    with pytest.raises(LspError) as e:
+        ctx.build_stencils()
+    assert e.value.status == 2  # build before set_potential
+    bad = v.copy()
+    bad[3, 4] = np.nan
+    with pytest.raises(LspError) as e:
+        ctx.set_potential(bad)
+    assert e.value.status == 1
+    ctx.set_potential(torch.from_numpy(v).cuda())
+    m = np.array([-20, -15, -9])
+    ctx.build_stencils(policy="list", shifts=O.shift_value(m))
+    tab = ctx.get_shift_table()
+    ref, tols = check_shift_table(tab, v, "list", m_list=m)
+    assert check_rows(ctx, v, ref, tols) == v.size
+    with pytest.raises(LspError) as e:  # -4 pi^2 * 5 = -4 pi^2 |(1, 2)|^2: resonant
+        ctx.build_stencils(policy="list", shifts=[-20 * O.PI2])
+    assert e.value.status == 3
+    with pytest.raises(LspError) as e:
+        ctx.build_stencils(policy="list", shifts=[-21.5 * O.PI2])
+    assert e.value.status == 1
+
+
+def test_graph_replay_is_bit_identical():
+    v = make_workload("helm2d_n256", n=64)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="local")
+    ref = [ctx.get_rows(k).copy() for k in "QCP"]
+    for _ in range(3):
+        ctx.build_stencils(policy="local", use_graph=True)
+        for k, r in zip("QCP", ref):
+            assert np.array_equal(ctx.get_rows(k), r)
+
+
+@pytest.mark.parametrize("name,n", [("helm2d_n32", 32), ("helm2d_n256", 256),
+                                    ("schr3d_n64", 16), ("schr3d_n64", 32)])
+def test_apply_operator(name, n):
+    import torch
+    v = make_workload(name, n=n)
+    d = v.ndim
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    rng = np.random.default_rng(7)
+    u = rng.standard_normal(v.shape)
+    y = torch.empty(v.shape, dtype=torch.float64, device="cuda")
+    ctx.apply_operator(torch.from_numpy(u).cuda(), y)
+    ref = O.apply_operator(v, u)
+    scale = (4 * O.PI2 * d * (n / 2) ** 2 + np.abs(v).max()) * np.abs(u).max()
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-13 * scale
+    # plane wave with constant v: eigenvalue 4 pi^2 |k|^2 + v
+    vc = np.full(v.shape, -321.5)
+    ctx.set_potential(vc)
+    x = np.meshgrid(*([np.arange(n) / n] * d), indexing="ij")
+    k = np.arange(1, d + 1) * 3
+    uw = np.cos(2 * np.pi * sum(ki * xi for ki, xi in zip(k, x)))
+    ctx.apply_operator(torch.from_numpy(uw).cuda(), y)
+    lam = 4 * O.PI2 * float((k ** 2).sum()) - 321.5
+    assert np.abs(y.cpu().numpy() - lam * uw).max() <= 1e-12 * abs(lam)
+
+
+@pytest.mark.parametrize("name,n,policy", [("helm2d_n32", 32, "local"), ("schr3d_n64", 8, "paper")])
+def test_export_csr(name, n, policy):
+    v = make_workload(name, n=n)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy=policy)
+    for which in "QCP":
+        rowptr, colidx, vals = ctx.export_sparse_rows(which)
+        rows = ctx.get_rows(which)
+        ref = O.rows_to_csr(rows, n, v.ndim)
+        assert np.array_equal(rowptr, ref.indptr)
+        assert np.array_equal(colidx, ref.indices)
+        assert np.array_equal(vals, rows.reshape(-1))
+
+
+def test_gmres_counts_unchanged_with_gpu_stencils():
+    import json
+    import os
+    import scipy.sparse
+    with open(os.path.join(os.path.dirname(__file__), "golden", "gmres_helm2d_n32.json")) as fh:
+        gold = json.load(fh)["iterations"]
+    v = make_workload("helm2d_n32")
+    n = 32
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    for pol in ("local", "paper", "mean"):
+        ctx.build_stencils(policy=pol)
+        mats = {}
+        for which in "CP":
+            rowptr, colidx, vals = ctx.export_sparse_rows(which)
+            mats[which] = scipy.sparse.csr_matrix((vals, colidx, rowptr), shape=(n * n, n * n))
+        _, it, res, info = O.gmres_solve(v, gaussian_source(n, 2, 2.0), mats["P"], mats["C"])
+        assert info == 0 and it == gold[f"{pol}/2.0"], (pol, it)
+
+
+# ---- full sizes, in the launch configuration of the benchmark (graph replay) -------------
+
+def test_full_size_2d_n1024_sampled():
+    v = make_workload("helm2d_n1024")
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    for _ in range(2):
+        ctx.build_stencils(policy="local", use_graph=True)
+    tab = ctx.get_shift_table()
+    rng = np.random.default_rng(11)
+    sample = sorted(rng.choice(len(tab["s"]), 6, replace=False).tolist()) + [0, len(tab["s"]) - 1]
+    ref, tols = check_shift_table(tab, v, "local", sample=sample)
+    assert check_rows(ctx, v, ref, tols) > 0
+    rows_consistent_with_table(ctx, v, tab)
+    assert not np.any(tab["flags"] & 4)
+
+
+def test_full_size_2d_n1024_paper_policy():
+    v = make_workload("helm2d_n1024")
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="paper", use_graph=True)
+    tab = ctx.get_shift_table()
+    sample = [0, len(tab["s"]) // 2, len(tab["s"]) - 1]
+    ref, tols = check_shift_table(tab, v, "paper", sample=sample)
+    assert check_rows(ctx, v, ref, tols) > 0
+    rows_consistent_with_table(ctx, v, tab)
+
+
+def test_full_size_3d_n64_all_shifts():
+    v = make_workload("schr3d_n64")
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="local", use_graph=True)
+    tab = ctx.get_shift_table()
+    ref, tols = check_shift_table(tab, v, "local")
+    assert check_rows(ctx, v, ref, tols) == v.size
