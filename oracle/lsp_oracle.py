@@ -41,7 +41,7 @@ __all__ = [
     "neighbourhood_offsets", "kernel_vectors", "gram_matrix", "near_null",
     "stencil_for_shift", "build_stencils", "rows_to_csr", "sparse_matrices",
     "gmres_solve", "dense_green_matrix", "brute_force_stencil", "sign_fix",
-    "local_shift_indices",
+    "local_shift_indices", "gather_offsets",
 ]
 
 PI2 = math.pi * math.pi  # pi^2 as one correctly rounded product of the float64 pi
@@ -170,10 +170,13 @@ def kernel_vectors(n: int, d: int, s: float):
     return g, g2
 
 
-def _gather(vec: np.ndarray, offs: np.ndarray, n: int) -> np.ndarray:
+def gather_offsets(vec: np.ndarray, offs: np.ndarray, n: int) -> np.ndarray:
     """M[a, b] = vec[(o_a - o_b) mod n]  (translation invariance, Sec. 4.2)."""
     diff = (offs[:, None, :] - offs[None, :, :]) % n
     return vec[tuple(diff[..., i] for i in range(offs.shape[1]))]
+
+
+_gather = gather_offsets
 
 
 def gram_matrix(g: np.ndarray, g2: np.ndarray, offs: np.ndarray):

@@ -13,6 +13,7 @@
 // on the whole |mu| x |mu| matrix. Both give every eigenvalue, so lambda_2 and the degeneracy
 // flag are exact in either method.
 #include <float.h>
+#include <string.h>
 
 #include "lsp_internal.h"
 
@@ -359,6 +360,229 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
   }
 }
 
+// ---- 2D, one thread per shift ------------------------------------------------------------
+// In 2D the symmetry-adapted vectors are u_0..u_2 (fully symmetric: centre, edges, corners),
+// u_3 (edges, x^2 - y^2), u_4 (corners, xy) and u_5, u_6 (x-odd on edges and corners). With
+// W_i = G_s[mu, mu] u_i (linear in g) and the A1 part u_i^T A1 u_j (linear in g * g), every
+// block entry is  B_ij = u_i^T A1 u_j - W_i . W_j, so the 9 x 9 matrix A is never formed.
+__constant__ double c_W2[7][9][6];   // W_i[k] = sum_c c_W2[i][k][c] g[c]
+__constant__ double c_B2[7][7][6];   // u_i^T A1 u_j = sum_c c_B2[i][j][c] (g*g)[c]
+
+template <int I>
+__device__ __forceinline__ void w_vec(const double (&g)[6], double (&w)[9]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s = fma(c_W2[I][k][c], g[c], s);
+    w[k] = s;
+  }
+}
+template <int I, int J>
+__device__ __forceinline__ double b_entry(const double (&g2)[6], const double (&wi)[9],
+                                          const double (&wj)[9]) {
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) s = fma(c_B2[I][J][c], g2[c], s);
+  double t = 0.0;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) t = fma(wi[k], wj[k], t);
+  return s - t;
+}
+
+// Eigenvalues of the symmetric 2 x 2 [[a, b], [b, c]], smaller one first; the small one as
+// det / large avoids cancellation.
+__device__ __forceinline__ void eig2(double a, double b, double c, double& lo, double& hi) {
+  const double m = 0.5 * (a + c), h = 0.5 * (a - c);
+  const double r = sqrt(fma(h, h, b * b));
+  hi = m + r;
+  lo = (hi != 0.0) ? (a * c - b * b) / hi : m - r;
+  if (lo > hi) {
+    const double t = lo;
+    lo = hi;
+    hi = t;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals, int64_t cap,
+                                               const int32_t* __restrict__ count,
+                                               double* __restrict__ alpha_out,
+                                               double* __restrict__ c_out,
+                                               double* __restrict__ lam_out,
+                                               int32_t* __restrict__ flags_out) {
+  const int64_t cnt = *count;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double g[6], g2[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      g[c] = __ldg(gvals + (int64_t)(2 * c) * cap + i);
+      g2[c] = __ldg(gvals + (int64_t)(2 * c + 1) * cap + i);
+    }
+    // fully symmetric block (3 x 3)
+    double w0[9], w1[9], w2[9];
+    w_vec<0>(g, w0);
+    w_vec<1>(g, w1);
+    w_vec<2>(g, w2);
+    double b00 = b_entry<0, 0>(g2, w0, w0), b01 = b_entry<0, 1>(g2, w0, w1),
+           b02 = b_entry<0, 2>(g2, w0, w2), b11 = b_entry<1, 1>(g2, w1, w1),
+           b12 = b_entry<1, 2>(g2, w1, w2), b22 = b_entry<2, 2>(g2, w2, w2);
+    // the other blocks: two 1 x 1 and one 2 x 2 (two copies)
+    double e00, e01, e11, bb1, bb2;
+    {
+      double u[9], v[9];
+      w_vec<3>(g, u);
+      bb1 = b_entry<3, 3>(g2, u, u);
+      w_vec<4>(g, u);
+      bb2 = b_entry<4, 4>(g2, u, u);
+      w_vec<5>(g, u);
+      w_vec<6>(g, v);
+      e00 = b_entry<5, 5>(g2, u, u);
+      e01 = b_entry<5, 6>(g2, u, v);
+      e11 = b_entry<6, 6>(g2, v, v);
+    }
+    // smallest eigenpair of the 3 x 3 block: scale to unit max entry, then repeated products
+    // with the adjugate (= det * inverse: inverse iteration without divisions), starting from
+    // the adjugate column with the largest diagonal entry.
+    const double sc = fmax(fmax(fmax(fabs(b00), fabs(b01)), fmax(fabs(b02), fabs(b11))),
+                           fmax(fabs(b12), fabs(b22)));
+    const double isc = sc > 0 ? 1.0 / sc : 0.0;
+    const double s00 = b00 * isc, s01 = b01 * isc, s02 = b02 * isc, s11 = b11 * isc,
+                 s12 = b12 * isc, s22 = b22 * isc;
+    const double a00 = s11 * s22 - s12 * s12, a01 = s02 * s12 - s01 * s22,
+                 a02 = s01 * s12 - s02 * s11, a11 = s00 * s22 - s02 * s02,
+                 a12 = s01 * s02 - s00 * s12, a22 = s00 * s11 - s01 * s01;
+    double x0, x1, x2;
+    if (a00 >= a11 && a00 >= a22) {
+      x0 = a00; x1 = a01; x2 = a02;
+    } else if (a11 >= a22) {
+      x0 = a01; x1 = a11; x2 = a12;
+    } else {
+      x0 = a02; x1 = a12; x2 = a22;
+    }
+#pragma unroll
+    for (int it = 0; it < 5; ++it) {
+      const double y0 = a00 * x0 + a01 * x1 + a02 * x2;
+      const double y1 = a01 * x0 + a11 * x1 + a12 * x2;
+      const double y2 = a02 * x0 + a12 * x1 + a22 * x2;
+      // renormalise by a power of two (exact) to stay clear of under/overflow
+      const double mx = fmax(fabs(y0), fmax(fabs(y1), fabs(y2)));
+      const double p2 = mx > 0 ? exp2((double)(-ilogb(mx))) : 1.0;
+      x0 = y0 * p2;
+      x1 = y1 * p2;
+      x2 = y2 * p2;
+    }
+    const double inrm = rsqrt(x0 * x0 + x1 * x1 + x2 * x2);
+    double y[3] = {x0 * inrm, x1 * inrm, x2 * inrm};
+    // one Newton correction of the normalisation (rsqrt is approximate)
+    {
+      const double n2 = y[0] * y[0] + y[1] * y[1] + y[2] * y[2];
+      const double f = 1.5 - 0.5 * n2;
+      y[0] *= f;
+      y[1] *= f;
+      y[2] *= f;
+    }
+    const double r0 = s00 * y[0] + s01 * y[1] + s02 * y[2];
+    const double r1 = s01 * y[0] + s11 * y[1] + s12 * y[2];
+    const double r2 = s02 * y[0] + s12 * y[1] + s22 * y[2];
+    const double ls = y[0] * r0 + y[1] * r1 + y[2] * r2;  // Rayleigh quotient (scaled)
+    const double res = fmax(fabs(r0 - ls * y[0]), fmax(fabs(r1 - ls * y[1]), fabs(r2 - ls * y[2])));
+    int flags = 0;
+    double l1s = ls;
+    // remaining eigenvalues of the 3 x 3 block from its trace and principal minors
+    const double tr = s00 + s11 + s22, m2 = a00 + a11 + a22;
+    if (!(res <= 64 * 2.2e-16) || !(ls > 0)) {
+      // not converged (tiny gap or a non-positive block): cyclic Jacobi on the block
+      double a[4][4] = {{s00, s01, s02, 0}, {s01, s11, s12, 0}, {s02, s12, s22, 0}, {0, 0, 0, 0}};
+      double vv[4][4];
+      if (!jacobi_small(a, vv, 3)) flags |= LSP_FLAG_NOT_CONVERGED;
+      int k = 0;
+      if (a[1][1] < a[k][k]) k = 1;
+      if (a[2][2] < a[k][k]) k = 2;
+      l1s = a[k][k];
+      y[0] = vv[0][k];
+      y[1] = vv[1][k];
+      y[2] = vv[2][k];
+    }
+    const double S = tr - l1s, Pp = m2 - l1s * S;
+    const double disc = fmax(0.25 * S * S - Pp, 0.0);
+    const double l3s = 0.5 * S + sqrt(disc);
+    const double l2s = l3s > 0 ? Pp / l3s : 0.0;
+    double lam1 = l1s * sc, lamA2 = l2s * sc, lamA3 = l3s * sc;
+    double eLo, eHi;
+    eig2(e00, e01, e11, eLo, eHi);
+    // winner over the blocks; lambda_2 counts the 2 x 2 block twice (two irrep copies)
+    int win = 0;
+    double best = lam1;
+    if (bb1 < best) { best = bb1; win = 1; }
+    if (bb2 < best) { best = bb2; win = 2; }
+    if (eLo < best) { best = eLo; win = 3; }
+    double lam2;
+    if (win == 0)
+      lam2 = fmin(fmin(lamA2, bb1), fmin(bb2, eLo));
+    else if (win == 3)
+      lam2 = eLo;  // second copy of the same eigenvalue
+    else
+      lam2 = fmin(fmin(lam1, win == 1 ? bb2 : bb1), eLo);
+    const double lmax = fmax(fmax(fabs(lamA3), fabs(eHi)), fmax(fabs(bb1), fabs(bb2)));
+    if (lam2 - best < 1e-8 * lmax) flags |= LSP_FLAG_DEGENERATE;
+    if (win != 0) flags |= LSP_FLAG_NONSYMMETRIC;
+    double al[9], cv[9];
+    if (win == 0) {
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        al[a] = y[0] * c_sym.u[0][a] + y[1] * c_sym.u[1][a] + y[2] * c_sym.u[2][a];
+        cv[a] = y[0] * w0[a] + y[1] * w1[a] + y[2] * w2[a];
+      }
+    } else if (win == 1 || win == 2) {
+      const int vi = win == 1 ? 3 : 4;
+      double u[9];
+      if (win == 1) w_vec<3>(g, u); else w_vec<4>(g, u);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        al[a] = c_sym.u[vi][a];
+        cv[a] = u[a];
+      }
+    } else {
+      // eigenvector of the 2 x 2 block for eLo
+      double p = e01, q = eLo - e00;
+      if (fabs(e00 - eLo) < fabs(e11 - eLo)) {
+        p = eLo - e11;
+        q = e01;
+      }
+      double nr = sqrt(p * p + q * q);
+      if (nr == 0) { p = 1; q = 0; nr = 1; }
+      p /= nr;
+      q /= nr;
+      double u[9], v[9];
+      w_vec<5>(g, u);
+      w_vec<6>(g, v);
+#pragma unroll
+      for (int a = 0; a < 9; ++a) {
+        al[a] = p * c_sym.u[5][a] + q * c_sym.u[6][a];
+        cv[a] = p * u[a] + q * v[a];
+      }
+    }
+    // sign: alpha[centre] > 0, else the first entry above 1e-12 in magnitude
+    double ref = al[4];
+    if (!(fabs(ref) > 1e-12)) {
+      ref = 0.0;
+#pragma unroll
+      for (int a = 0; a < 9; ++a)
+        if (ref == 0.0 && fabs(al[a]) > 1e-12) ref = al[a];
+    }
+    const double sg = ref < 0 ? -1.0 : 1.0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+      alpha_out[i * 9 + a] = sg * al[a];
+      c_out[i * 9 + a] = sg * cv[a];
+    }
+    lam_out[2 * i + 0] = best;
+    lam_out[2 * i + 1] = lam2;
+    flags_out[i] = flags;
+  }
+}
+
 template <int MU, int NCLS, int WARPS>
 cudaError_t launch_eig_t(lsp_ctx* c, const int32_t* count, int64_t cap, int method, int refine) {
   const size_t smem = sizeof(WarpSmem<MU>) * WARPS;
@@ -395,13 +619,40 @@ cudaError_t upload_sym(lsp_ctx* c) {
       }
   e = cudaMemcpyToSymbol(c_ent, ent, sizeof(ent));
   if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_nent, &n, sizeof(int));
+  e = cudaMemcpyToSymbol(c_nent, &n, sizeof(int));
+  if (e != cudaSuccess || c->geo.d != 2) return e;
+  // W_i[k] = sum_a G[k, a] u_i[a] = sum_a g[cls(k, a)] u_i[a];  u_i^T A1 u_j = sum g2[cls(a,b)] u_i[a] u_j[b]
+  static double W2[7][9][6], B2[7][7][6];
+  memset(W2, 0, sizeof W2);
+  memset(B2, 0, sizeof B2);
+  for (int i = 0; i < 7; ++i)
+    for (int k = 0; k < 9; ++k)
+      for (int a = 0; a < 9; ++a) W2[i][k][c->geo.cls_of[k][a]] += c->sym.u[i][a];
+  for (int i = 0; i < 7; ++i)
+    for (int j = 0; j < 7; ++j)
+      for (int a = 0; a < 9; ++a)
+        for (int b = 0; b < 9; ++b)
+          B2[i][j][c->geo.cls_of[a][b]] += c->sym.u[i][a] * c->sym.u[j][b];
+  e = cudaMemcpyToSymbol(c_W2, W2, sizeof W2);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_B2, B2, sizeof B2);
 }
 
 cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int method, int refine) {
   int t = timer_begin(c, "eig");
-  cudaError_t e = c->geo.d == 2 ? launch_eig_t<9, 6, 8>(c, count, cap, method, refine)
-                                : launch_eig_t<27, 10, 2>(c, count, cap, method, refine);
+  cudaError_t e;
+  if (c->geo.d == 2 && method == LSP_EIG_SYMMETRIC && refine == 0) {
+    int64_t b = (cap + 127) / 128;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    k_eig2d<<<(int)b, 128, 0, c->stream>>>((const double*)c->gvals.p, cap, count,
+                                           (double*)c->alpha.p, (double*)c->cst.p,
+                                           (double*)c->lam.p, (int32_t*)c->sflags.p);
+    e = cudaGetLastError();
+  } else {
+    e = c->geo.d == 2 ? launch_eig_t<9, 6, 8>(c, count, cap, method, refine)
+                      : launch_eig_t<27, 10, 2>(c, count, cap, method, refine);
+  }
   timer_end(c, t);
   return e;
 }

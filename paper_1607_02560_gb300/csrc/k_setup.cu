@@ -117,7 +117,12 @@ __global__ void __launch_bounds__(kThreads) k_stats_final(const double* __restri
 // from zero. Explicit round-to-nearest intrinsics keep the decision identical to a plain
 // IEEE evaluation of (x / pi^2 - 2) / 4 (no contraction into fused operations).
 __device__ __forceinline__ int64_t snap_m(double x) {
-  double y = __dmul_rn(__dsub_rn(__ddiv_rn(x, kPi2), 2.0), 0.25);
+  // Fast path: fma(x, 1/(4 pi^2), -1/2) is within a few ulp of the exact (x/pi^2 - 2)/4, so
+  // its nearest integer is the exact one unless it lies next to a half-integer.
+  const double yf = fma(x, kQuarterInvPi2, -0.5);
+  const double r = rint(yf);
+  if (0.5 - fabs(yf - r) > 1e-14 * fabs(yf) + 1e-14) return (int64_t)r;
+  const double y = __dmul_rn(__dsub_rn(__ddiv_rn(x, kPi2), 2.0), 0.25);
   return (int64_t)round(y);
 }
 

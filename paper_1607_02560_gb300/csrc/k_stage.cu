@@ -71,10 +71,11 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
   extern __shared__ double xs[];  // [3][P]
   for (int i = threadIdx.x; i < 3 * P; i += kThreads) xs[i] = X[i];
   __syncthreads();
-  const int64_t cnt = *count_ptr;
+  // list == nullptr: the domain is the whole range [lo_out, lo_out + stride_out)
+  const int64_t cnt = list ? (int64_t)*count_ptr : stride_out;
   for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < cnt;
        idx += (int64_t)gridDim.x * kThreads) {
-    const int64_t l = __ldg(list + idx);
+    const int64_t l = list ? (int64_t)__ldg(list + idx) : lo_out + idx;
     double acc[M::NCO][2];
 #pragma unroll
     for (int c = 0; c < M::NCO; ++c) acc[c][0] = acc[c][1] = 0.0;

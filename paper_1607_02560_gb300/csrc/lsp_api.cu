@@ -271,6 +271,13 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
   int64_t cap = cap_s;
   for (int k = d - 1; k >= 1; --k) {
     const int64_t sz = c->erange[k].size();
+    if (c->edense[k]) {
+      // every l of the range is evaluated: no marking or compaction needed
+      list = nullptr;
+      count = nullptr;
+      cap = sz;
+      continue;
+    }
     CUDA_OK(c, cudaMemsetAsync(c->eflag[k].p, 0, round_up(sz, 4096), c->stream));
     CUDA_OK(c, launch_mark_stage(c, list, count, cap, c->erange[k].lo, (uint8_t*)c->eflag[k].p));
     CUDA_OK(c, launch_compact(c, (const uint8_t*)c->eflag[k].p, c->erange[k].lo, sz,
@@ -284,9 +291,11 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
     const double* prev = k == 1 ? (const double*)c->wtab.p : (const double*)c->T[k - 1].p;
     const int64_t lo_prev = c->erange[k - 1].lo, stride_prev = c->erange[k - 1].size();
     if (k < d) {
-      CUDA_OK(c, launch_stage(c, d, k, (const int32_t*)c->elist[k].p, counts + (d - k),
-                              c->erange[k].size(), prev, lo_prev, stride_prev, (double*)c->T[k].p,
-                              c->erange[k].lo, c->erange[k].size(), false));
+      const bool dense = c->edense[k];
+      CUDA_OK(c, launch_stage(c, d, k, dense ? nullptr : (const int32_t*)c->elist[k].p,
+                              dense ? nullptr : counts + (d - k), c->erange[k].size(), prev,
+                              lo_prev, stride_prev, (double*)c->T[k].p, c->erange[k].lo,
+                              c->erange[k].size(), false));
     } else {
       CUDA_OK(c, launch_stage(c, d, k, (const int32_t*)c->shift_m.p, counts + 0, cap_s, prev,
                               lo_prev, stride_prev, (double*)c->gvals.p, 0, cap_s, true));
@@ -400,6 +409,7 @@ lsp_status lsp_destroy(lsp_ctx* c) {
 
 lsp_status lsp_set_potential(lsp_ctx* c, const double* v, int v_on_device) {
   if (!c) return LSP_ERR_ARG;
+  cudaGetLastError();  // a launch check below must not report an earlier, unrelated error
   if (!v) return fail(c, LSP_ERR_ARG, "v is NULL");
   const int64_t N = c->geo.N;
   if (!ensure(c, c->v, sizeof(double) * N)) return LSP_ERR_OOM;
@@ -431,6 +441,7 @@ lsp_status lsp_set_potential(lsp_ctx* c, const double* v, int v_on_device) {
 
 lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   if (!c) return LSP_ERR_ARG;
+  cudaGetLastError();
   lsp_stencil_opts o;
   if (opts)
     o = *opts;
@@ -503,6 +514,17 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   }
   if (c->erange[0].hi > 2147483000LL || c->erange[0].lo < -2147483000LL)
     return fail(c, LSP_ERR_ARG, "shift range too large for 32-bit lattice indices");
+  // A stage domain E_k = {l + p^2} is evaluated over its whole range when the list it is built
+  // from could cover it (upper bound of its size times n/2+1 offsets >= twice the range):
+  // marking and compacting would then cost more than the few extra points.
+  {
+    int64_t ub = cap_s;
+    for (int k = d - 1; k >= 1; --k) {
+      const int64_t sz = c->erange[k].size();
+      c->edense[k] = (k < d - 1 && c->edense[k + 1]) || ub * (int64_t)c->geo.P >= 2 * sz;
+      ub = c->edense[k] ? sz : std::min<int64_t>(sz, ub * (int64_t)c->geo.P);
+    }
+  }
 
   // ---- buffers (all allocation happens before any capture) ----
   const int64_t R = c->mrange.size();
@@ -545,11 +567,14 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   c->last_policy = o.policy;
 
   lsp_status st;
-  if (o.use_graph && !c->timing) {
+  const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy &&
+                          c->stream != cudaStreamPerThread;
+  if (o.use_graph && !c->timing && capturable) {
     std::vector<int64_t> key = {o.policy, o.eig_method, o.refine_steps, cap_s, c->mrange.lo,
                                 c->mrange.hi, (int64_t)(intptr_t)c->v.p,
                                 (int64_t)(intptr_t)c->Q.p};
     for (int k = 0; k <= d; ++k) key.push_back(c->erange[k].lo);
+    for (int k = 0; k < kMaxD; ++k) key.push_back(c->edense[k]);
     if (!c->graph || key != c->graph_key) {
       if (c->graph) cudaGraphExecDestroy(c->graph);
       c->graph = nullptr;
@@ -575,6 +600,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
 
 lsp_status lsp_apply_operator(lsp_ctx* c, const double* u, double* y) {
   if (!c) return LSP_ERR_ARG;
+  cudaGetLastError();
   if (!u || !y) return fail(c, LSP_ERR_ARG, "u or y is NULL");
   if (!c->have_v) return fail(c, LSP_ERR_STATE, "apply_operator before set_potential");
   if (!ensure(c, c->fftbuf, sizeof(double) * 2 * c->geo.N)) return LSP_ERR_OOM;
@@ -609,6 +635,7 @@ lsp_status lsp_get_rows(lsp_ctx* c, char which, double* rows, int on_device) {
 lsp_status lsp_export_sparse_rows(lsp_ctx* c, char which, int64_t* rowptr, int32_t* colidx,
                                   double* vals, int64_t* nnz_out) {
   if (!c) return LSP_ERR_ARG;
+  cudaGetLastError();
   const int64_t nnz = c->geo.N * c->geo.mu;
   if (nnz_out) *nnz_out = nnz;
   if (!rowptr && !colidx && !vals) return LSP_OK;
@@ -634,6 +661,7 @@ lsp_status lsp_get_shift_table(lsp_ctx* c, int64_t* nshifts_out, double* s, doub
                                double* cst, double* lam, int32_t* flags, int32_t* s_idx) {
   if (!c) return LSP_ERR_ARG;
   if (!c->built) return fail(c, LSP_ERR_STATE, "no stencils built");
+  cudaGetLastError();
   int32_t head[16];
   CUDA_OK(c, cudaMemcpyAsync(head, c->counts.p, sizeof(head), cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));

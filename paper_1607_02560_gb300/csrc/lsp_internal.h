@@ -15,6 +15,7 @@ namespace lsp {
 // device so that lattice snapping takes bit-identical decisions everywhere.
 constexpr double kPi = 3.141592653589793;
 constexpr double kPi2 = kPi * kPi;
+constexpr double kQuarterInvPi2 = 0.25 / kPi2;  // for the fast path of the lattice snap
 
 constexpr int kMaxD = 3;
 constexpr int kMaxMu = 27;      // (2t+1)^d for t = 1, d = 3
@@ -93,6 +94,7 @@ struct lsp_ctx {
   // lattice-separable stages (a3)
   lsp::Range erange[lsp::kMaxD + 1];  // E_k ranges; E_d = shifts, E_0 = table domain
   lsp::DevBuf eflag[lsp::kMaxD], elist[lsp::kMaxD], T[lsp::kMaxD], wtab;
+  bool edense[lsp::kMaxD] = {false, false, false};  // E_k evaluated over its whole range
 
   // per-shift results (a3-a6)
   lsp::DevBuf gvals, alpha, cst, lam, sflags;

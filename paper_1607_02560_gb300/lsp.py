@@ -177,7 +177,11 @@ class Context:
         self._check(lib().lsp_build_stencils(self.h, ctypes.byref(o)), "build_stencils")
 
     def apply_operator(self, u, y):
-        """y = (L + diag v) u for torch CUDA tensors u, y (n^d float64)."""
+        """y = (L + diag v) u for torch CUDA tensors u, y (n^d float64).
+
+        Asynchronous on the context's stream: order it after the producer of u and before any
+        reader of y (e.g. with synchronize()).
+        """
         if not (_on_device(u) and _on_device(y)):
             raise ValueError("apply_operator takes device tensors")
         self._check(lib().lsp_apply_operator(self.h, _ptr(u), _ptr(y)), "apply_operator")

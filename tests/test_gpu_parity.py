@@ -29,9 +29,16 @@ def built():
     B.build()
 
 
+_STREAM = []
+
+
 def ctx_for(v):
+    """A context on a dedicated (non-default) stream, as the benchmark uses."""
+    import torch
     from paper_1607_02560_gb300 import Context
-    return Context(v.ndim, v.shape[0])
+    if not _STREAM:
+        _STREAM.append(torch.cuda.Stream())
+    return Context(v.ndim, v.shape[0], stream=_STREAM[0])
 
 
 def shift_tols(n, d, s):
@@ -40,7 +47,7 @@ def shift_tols(n, d, s):
     kappa = np.abs(w).max() / max(w[1] - w[0], 1e-300)
     ta = max(1e-10, 16 * U * kappa)
     offs = O.neighbourhood_offsets(d)
-    Gm = O._gather(st["g"], offs, n)
+    Gm = O.gather_offsets(st["g"], offs, n)
     tc = ta * np.abs(Gm).sum(axis=0).max() + 1e-13 * np.abs(st["c"]).max()
     return st, ta, tc
 
@@ -182,7 +189,9 @@ def test_apply_operator(name, n):
     rng = np.random.default_rng(7)
     u = rng.standard_normal(v.shape)
     y = torch.empty(v.shape, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
     ctx.apply_operator(torch.from_numpy(u).cuda(), y)
+    ctx.synchronize()  # the context works on its own stream
     ref = O.apply_operator(v, u)
     scale = (4 * O.PI2 * d * (n / 2) ** 2 + np.abs(v).max()) * np.abs(u).max()
     assert np.abs(y.cpu().numpy() - ref).max() <= 1e-13 * scale
@@ -192,7 +201,9 @@ def test_apply_operator(name, n):
     x = np.meshgrid(*([np.arange(n) / n] * d), indexing="ij")
     k = np.arange(1, d + 1) * 3
     uw = np.cos(2 * np.pi * sum(ki * xi for ki, xi in zip(k, x)))
+    torch.cuda.synchronize()
     ctx.apply_operator(torch.from_numpy(uw).cuda(), y)
+    ctx.synchronize()
     lam = 4 * O.PI2 * float((k ** 2).sum()) - 321.5
     assert np.abs(y.cpu().numpy() - lam * uw).max() <= 1e-12 * abs(lam)
 
