@@ -136,8 +136,10 @@ def kernel_work(name: str, n: int, d: int, N: int, mu: int, sizes: list[int]):
         k = int(name[-1])
         # stage k runs over E_k; sizes lists E_d, E_{d-1}, ..., so E_k = sizes[d - k]
         count = sizes[d - k]
-        per = 2 * 2 * ncls[k] + (1 if k == 1 else 0)  # 2 functions x FMA, + w^2 in stage 1
-        return count * P * per, "flop"
+        if k == 1:
+            # mirror-paired: per pair 4 add/sub + 6 FMA (16 flops), plus the middle term (12)
+            return count * ((n // 4) * 16 + 12), "flop"
+        return count * P * 2 * 2 * ncls[k], "flop"  # 2 functions x one FMA per class
     if name == "rows":
         return N * (8 + 3 * mu * 8), "byte"
     if name == "stats":
@@ -174,7 +176,7 @@ def run_ours(args):
 
     B.build()
     seed = None if rank == 0 else 1000 + rank
-    v_host = make_workload(args.workload, seed=seed)
+    v_host = make_workload(args.workload, seed=seed, n=args.n)
     d, n = v_host.ndim, v_host.shape[0]
     N = v_host.size
     stream = torch.cuda.Stream()
@@ -185,7 +187,7 @@ def run_ours(args):
 
     def step():
         ctx.set_potential(v_dev)
-        ctx.build_stencils(policy=args.policy, use_graph=True)
+        ctx.build_stencils(policy=args.policy, mode=args.mode, use_graph=True)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -241,7 +243,7 @@ def run_ours(args):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             ctx.set_potential(v_pin.numpy())
-            ctx.build_stencils(policy=args.policy, use_graph=True)
+            ctx.build_stencils(policy=args.policy, mode=args.mode, use_graph=True)
             for which, o in zip("QCP", outs):
                 ctx.get_rows(which, o)
             e2e_ms.append((time.perf_counter() - t1) * 1e3)
@@ -288,10 +290,10 @@ def run_ours(args):
         "metric": "local stencils/sec (Q, C, P rows of every grid point, steps a1-a7)",
         "value": value, "unit": "stencils/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": args.workload, "text": WORKLOAD_TEXT.get(args.workload, ""),
-                   "policy": args.policy, "mode": "fp64", "d": d, "n": n, "points": N,
+                   "policy": args.policy, "mode": args.mode, "d": d, "n": n, "points": N,
                    "shifts": ns, "lattice_domains": sizes,
                    "l2": "flushed before every timed step (256 MiB write), outside the step events",
                    "parallelism": f"replicas x{ws} (independent potentials)"},
@@ -307,12 +309,70 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(N * 8), "d2h_bytes_per_step": int(3 * N * mu * 8),
                 "ms_per_step": float(np.median(e2e_ms))},
     }
+    if not args.no_variants:
+        out["variants"] = variants(args, torch)
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.policy, budget_s=args.cpu_budget)
     print(json.dumps(out))
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup: int):
+    """stencils/s of one configuration (same step, L2 flush and events as the main line)."""
+    from lsp_inputs import make_workload
+    from paper_1607_02560_gb300 import Context
+
+    v = make_workload(workload)
+    stream = torch.cuda.Stream()
+    ctx = Context(v.ndim, v.shape[0], stream=stream)
+    v_dev = torch.from_numpy(v).to("cuda")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            ctx.set_potential(v_dev)
+            ctx.build_stencils(policy=policy, mode=mode, use_graph=True)
+        ctx.synchronize()
+        tot = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ctx.set_potential(v_dev)
+            ctx.build_stencils(policy=policy, mode=mode, use_graph=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        ns = len(ctx.get_shift_table(with_sidx=False)["s"])
+        ctx.kernel_timing(True)
+        for _ in range(5):
+            flush.zero_()
+            ctx.set_potential(v_dev)
+            ctx.build_stencils(policy=policy, mode=mode, use_graph=True)
+        ctx.synchronize()
+        kt = {k: round(ms / max(cnt, 1), 4) for k, (ms, cnt) in ctx.kernel_times().items()}
+        ctx.kernel_timing(False)
+    ctx.close()
+    return {"workload": workload, "policy": policy, "mode": mode, "value": v.size * steps / (tot * 1e-3),
+            "unit": "stencils/s", "ms_per_step": tot / steps, "shifts": ns,
+            "kernel_ms_per_launch": kt}
+
+
+def variants(args, torch):
+    """The metric's other forms on the same GPU: FP64 vs mixed, 2D n=1024 vs 3D n=64, and the
+    paper's shift policy."""
+    out = []
+    for wl, pol, mode in [("helm2d_n1024", "local", "mixed"), ("schr3d_n64", "local", "fp64"),
+                          ("schr3d_n64", "local", "mixed"), ("helm2d_n1024", "paper", "fp64"),
+                          ("helm2d_n1024", "paper", "mixed")]:
+        if (wl, pol, mode) == (args.workload, args.policy, args.mode):
+            continue
+        try:
+            out.append(time_config(torch, wl, pol, mode, steps=20, warmup=3))
+        except Exception as exc:  # a variant must not hide the main line
+            out.append({"workload": wl, "policy": pol, "mode": mode, "error": str(exc)[:200]})
+    return out
 
 
 def cpu_baseline(workload: str, policy: str, budget_s: float = 20.0, step_index: int = 0):
@@ -380,6 +440,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="helm2d_n1024")
     ap.add_argument("--policy", default="local", choices=["local", "paper", "mean"])
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="rescale the workload's grid (small cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

@@ -367,24 +367,39 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
 // block entry is  B_ij = u_i^T A1 u_j - W_i . W_j, so the 9 x 9 matrix A is never formed.
 __constant__ double c_W2[7][9][6];   // W_i[k] = sum_c c_W2[i][k][c] g[c]
 __constant__ double c_B2[7][7][6];   // u_i^T A1 u_j = sum_c c_B2[i][j][c] (g*g)[c]
+__constant__ float c_W2f[7][9][6];   // the same tables in FP32 (mixed mode)
+__constant__ float c_B2f[7][7][6];
 
-template <int I>
-__device__ __forceinline__ void w_vec(const double (&g)[6], double (&w)[9]) {
+template <typename GT>
+__device__ __forceinline__ GT coefW(int i, int k, int c);
+template <>
+__device__ __forceinline__ double coefW<double>(int i, int k, int c) { return c_W2[i][k][c]; }
+template <>
+__device__ __forceinline__ float coefW<float>(int i, int k, int c) { return c_W2f[i][k][c]; }
+template <typename GT>
+__device__ __forceinline__ GT coefB(int i, int j, int c);
+template <>
+__device__ __forceinline__ double coefB<double>(int i, int j, int c) { return c_B2[i][j][c]; }
+template <>
+__device__ __forceinline__ float coefB<float>(int i, int j, int c) { return c_B2f[i][j][c]; }
+
+// GT is the arithmetic of the Gram assembly: double (FP64 mode) or float (mixed mode).
+template <int I, typename GT>
+__device__ __forceinline__ void w_vec(const GT (&g)[6], GT (&w)[9]) {
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    double s = 0.0;
+    GT s = GT(0);
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s = fma(c_W2[I][k][c], g[c], s);
+    for (int c = 0; c < 6; ++c) s = fma(coefW<GT>(I, k, c), g[c], s);
     w[k] = s;
   }
 }
-template <int I, int J>
-__device__ __forceinline__ double b_entry(const double (&g2)[6], const double (&wi)[9],
-                                          const double (&wj)[9]) {
-  double s = 0.0;
+template <int I, int J, typename GT>
+__device__ __forceinline__ GT b_entry(const GT (&g2)[6], const GT (&wi)[9], const GT (&wj)[9]) {
+  GT s = GT(0);
 #pragma unroll
-  for (int c = 0; c < 6; ++c) s = fma(c_B2[I][J][c], g2[c], s);
-  double t = 0.0;
+  for (int c = 0; c < 6; ++c) s = fma(coefB<GT>(I, J, c), g2[c], s);
+  GT t = GT(0);
 #pragma unroll
   for (int k = 0; k < 9; ++k) t = fma(wi[k], wj[k], t);
   return s - t;
@@ -404,6 +419,7 @@ __device__ __forceinline__ void eig2(double a, double b, double c, double& lo, d
   }
 }
 
+template <typename GT>
 __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals, int64_t cap,
                                                const int32_t* __restrict__ count,
                                                double* __restrict__ alpha_out,
@@ -413,14 +429,14 @@ __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals,
   const int64_t cnt = *count;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double g[6], g2[6];
+    GT g[6], g2[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
-      g[c] = __ldg(gvals + (int64_t)(2 * c) * cap + i);
-      g2[c] = __ldg(gvals + (int64_t)(2 * c + 1) * cap + i);
+      g[c] = (GT)__ldg(gvals + (int64_t)(2 * c) * cap + i);
+      g2[c] = (GT)__ldg(gvals + (int64_t)(2 * c + 1) * cap + i);
     }
     // fully symmetric block (3 x 3)
-    double w0[9], w1[9], w2[9];
+    GT w0[9], w1[9], w2[9];
     w_vec<0>(g, w0);
     w_vec<1>(g, w1);
     w_vec<2>(g, w2);
@@ -430,7 +446,7 @@ __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals,
     // the other blocks: two 1 x 1 and one 2 x 2 (two copies)
     double e00, e01, e11, bb1, bb2;
     {
-      double u[9], v[9];
+      GT u[9], v[9];
       w_vec<3>(g, u);
       bb1 = b_entry<3, 3>(g2, u, u);
       w_vec<4>(g, u);
@@ -536,7 +552,7 @@ __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals,
       }
     } else if (win == 1 || win == 2) {
       const int vi = win == 1 ? 3 : 4;
-      double u[9];
+      GT u[9];
       if (win == 1) w_vec<3>(g, u); else w_vec<4>(g, u);
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
@@ -554,7 +570,7 @@ __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals,
       if (nr == 0) { p = 1; q = 0; nr = 1; }
       p /= nr;
       q /= nr;
-      double u[9], v[9];
+      GT u[9], v[9];
       w_vec<5>(g, u);
       w_vec<6>(g, v);
 #pragma unroll
@@ -633,21 +649,38 @@ cudaError_t upload_sym(lsp_ctx* c) {
       for (int a = 0; a < 9; ++a)
         for (int b = 0; b < 9; ++b)
           B2[i][j][c->geo.cls_of[a][b]] += c->sym.u[i][a] * c->sym.u[j][b];
+  static float W2f[7][9][6], B2f[7][7][6];
+  for (int i = 0; i < 7; ++i)
+    for (int k = 0; k < 9; ++k)
+      for (int q = 0; q < 6; ++q) W2f[i][k][q] = (float)W2[i][k][q];
+  for (int i = 0; i < 7; ++i)
+    for (int j = 0; j < 7; ++j)
+      for (int q = 0; q < 6; ++q) B2f[i][j][q] = (float)B2[i][j][q];
   e = cudaMemcpyToSymbol(c_W2, W2, sizeof W2);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_W2f, W2f, sizeof W2f);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_B2f, B2f, sizeof B2f);
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_B2, B2, sizeof B2);
 }
 
-cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int method, int refine) {
+cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int method, int refine,
+                       bool fp32_gram) {
   int t = timer_begin(c, "eig");
   cudaError_t e;
   if (c->geo.d == 2 && method == LSP_EIG_SYMMETRIC && refine == 0) {
     int64_t b = (cap + 127) / 128;
     if (b > 152 * 16) b = 152 * 16;
     if (b < 1) b = 1;
-    k_eig2d<<<(int)b, 128, 0, c->stream>>>((const double*)c->gvals.p, cap, count,
-                                           (double*)c->alpha.p, (double*)c->cst.p,
-                                           (double*)c->lam.p, (int32_t*)c->sflags.p);
+    if (fp32_gram)
+      k_eig2d<float><<<(int)b, 128, 0, c->stream>>>((const double*)c->gvals.p, cap, count,
+                                                    (double*)c->alpha.p, (double*)c->cst.p,
+                                                    (double*)c->lam.p, (int32_t*)c->sflags.p);
+    else
+      k_eig2d<double><<<(int)b, 128, 0, c->stream>>>((const double*)c->gvals.p, cap, count,
+                                                     (double*)c->alpha.p, (double*)c->cst.p,
+                                                     (double*)c->lam.p, (int32_t*)c->sflags.p);
     e = cudaGetLastError();
   } else {
     e = c->geo.d == 2 ? launch_eig_t<9, 6, 8>(c, count, cap, method, refine)

@@ -245,11 +245,22 @@ __global__ void __launch_bounds__(kThreads) k_compact_write(const uint8_t* __res
   }
 }
 
-__global__ void __launch_bounds__(kThreads) k_wtable(int64_t lo, int64_t range, double* __restrict__ w) {
+// w(l) = 1 / (pi^2 (4 l + 2)): FP64 interleaved with w^2, or w alone rounded to FP32.
+__global__ void __launch_bounds__(kThreads) k_wtable64(int64_t lo, int64_t range,
+                                                       double2* __restrict__ w) {
   for (int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x; r < range;
        r += (int64_t)gridDim.x * kThreads) {
     const double l4 = (double)(4 * (lo + r) + 2);  // exact integer
-    w[r] = 1.0 / __dmul_rn(kPi2, l4);
+    const double x = 1.0 / __dmul_rn(kPi2, l4);
+    w[r] = make_double2(x, x * x);
+  }
+}
+__global__ void __launch_bounds__(kThreads) k_wtable32(int64_t lo, int64_t range,
+                                                       float* __restrict__ w) {
+  for (int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x; r < range;
+       r += (int64_t)gridDim.x * kThreads) {
+    const double l4 = (double)(4 * (lo + r) + 2);
+    w[r] = (float)(1.0 / __dmul_rn(kPi2, l4));
   }
 }
 
@@ -315,9 +326,12 @@ cudaError_t launch_mark_stage(lsp_ctx* c, const int32_t* list, const int32_t* co
   return cudaGetLastError();
 }
 
-cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, double* w) {
+cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, void* w, bool fp32) {
   int t = timer_begin(c, "wtable");
-  k_wtable<<<grid_for(range), kThreads, 0, c->stream>>>(lo, range, w);
+  if (fp32)
+    k_wtable32<<<grid_for(range), kThreads, 0, c->stream>>>(lo, range, (float*)w);
+  else
+    k_wtable64<<<grid_for(range), kThreads, 0, c->stream>>>(lo, range, (double2*)w);
   timer_end(c, t);
   return cudaGetLastError();
 }

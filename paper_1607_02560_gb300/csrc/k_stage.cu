@@ -55,102 +55,175 @@ struct StageMap<3> {
   }
 };
 
-// One thread per domain point l. For stage 1 the input is the w table and w^2 is formed in
-// registers; later stages read both functions of every input class. Output layout is
-// structure-of-arrays: Tout[(c * 2 + f) * stride_out + pos].
-template <int K>
+// One thread per domain point l; structure-of-arrays output Tout[(c * 2 + f) * stride_out + pos].
+//
+// Stage 1 reads the interleaved table (w, w^2) and pairs every p < n/4 with its mirror
+// q = n/2 - p: X_a(q) = (-1)^a X_a(p) (w_q = w_p, cos(pi a - t) = (-1)^a cos t), so
+//   sum_p X_a(p) w(p^2 + l) = sum_{p < n/4} X_a(p) [w(p^2 + l) + (-1)^a w(q^2 + l)] + X_a(n/4) w(n^2/16 + l),
+// i.e. 5 FP64 operations per frequency instead of 7 (the host table satisfies the mirror
+// identity exactly). Later stages read both functions of every input class.
+// R is the arithmetic type: double for the FP64 mode, float for the mixed mode. OUT is the
+// type of the output table (the last stage always writes double g values).
+template <typename R>
+struct Vec2;
+template <>
+struct Vec2<double> { using type = double2; };
+template <>
+struct Vec2<float> { using type = float2; };
+
+template <int K, typename R, typename OUT>
 __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ list,
                                                     const int32_t* __restrict__ count_ptr, int P,
-                                                    const double* __restrict__ X,
-                                                    const double* __restrict__ Tprev,
+                                                    const R* __restrict__ X,
+                                                    const R* __restrict__ Tprev,
                                                     int64_t lo_prev, int64_t stride_prev,
-                                                    double* __restrict__ Tout, int64_t lo_out,
+                                                    OUT* __restrict__ Tout, int64_t lo_out,
                                                     int64_t stride_out, int by_index,
                                                     double scale) {
   using M = StageMap<K>;
-  extern __shared__ double xs[];  // [3][P]
+  using R2 = typename Vec2<R>::type;
+  extern __shared__ __align__(16) unsigned char xs_raw[];
+  R* xs = reinterpret_cast<R*>(xs_raw);  // [3][P]
   for (int i = threadIdx.x; i < 3 * P; i += kThreads) xs[i] = X[i];
   __syncthreads();
   // list == nullptr: the domain is the whole range [lo_out, lo_out + stride_out)
   const int64_t cnt = list ? (int64_t)*count_ptr : stride_out;
+  const int half = P - 1;  // n/2
   for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < cnt;
        idx += (int64_t)gridDim.x * kThreads) {
     const int64_t l = list ? (int64_t)__ldg(list + idx) : lo_out + idx;
-    double acc[M::NCO][2];
+    R acc[M::NCO][2];
 #pragma unroll
-    for (int c = 0; c < M::NCO; ++c) acc[c][0] = acc[c][1] = 0.0;
-    const double* base = Tprev + (l - lo_prev);
-    for (int p = 0; p < P; ++p) {
-      const int64_t off = (int64_t)p * p;
-      double in[M::NCP][2];
-      if (K == 1) {
-        const double w = __ldg(base + off);
-        in[0][0] = w;
-        in[0][1] = w * w;
-      } else {
+    for (int c = 0; c < M::NCO; ++c) acc[c][0] = acc[c][1] = R(0);
+    if (K == 1) {
+      // FP64: interleaved (w, w^2) table, one 16-byte load per term (the FP64 pipe is the
+      // bound, so the square is read rather than computed). FP32: plain w table, the square
+      // formed in registers (there the L2 bandwidth is the bound).
+      const R2* tab = reinterpret_cast<const R2*>(Tprev) + (l - lo_prev);
+      const R* tab1 = Tprev + (l - lo_prev);
+      constexpr bool kPair = sizeof(R) == 8;
+      const int quarter = half / 2;  // n/4
+      for (int p = 0; p < quarter; ++p) {
+        const int q = half - p;
+        R2 wa, wb;
+        if (kPair) {
+          wa = __ldg(tab + (int64_t)p * p);
+          wb = __ldg(tab + (int64_t)q * q);
+        } else {
+          wa.x = __ldg(tab1 + (int64_t)p * p);
+          wb.x = __ldg(tab1 + (int64_t)q * q);
+          wa.y = wa.x * wa.x;
+          wb.y = wb.x * wb.x;
+        }
+        const R s1 = wa.x + wb.x, d1 = wa.x - wb.x;
+        const R s2 = wa.y + wb.y, d2 = wa.y - wb.y;
+        const R x0 = xs[p], x1 = xs[P + p], x2 = xs[2 * P + p];
+        acc[0][0] = fma(x0, s1, acc[0][0]);
+        acc[1][0] = fma(x1, d1, acc[1][0]);
+        acc[2][0] = fma(x2, s1, acc[2][0]);
+        acc[0][1] = fma(x0, s2, acc[0][1]);
+        acc[1][1] = fma(x1, d2, acc[1][1]);
+        acc[2][1] = fma(x2, s2, acc[2][1]);
+      }
+      {
+        R2 wm;
+        if (kPair) {
+          wm = __ldg(tab + (int64_t)quarter * quarter);
+        } else {
+          wm.x = __ldg(tab1 + (int64_t)quarter * quarter);
+          wm.y = wm.x * wm.x;
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          acc[c][0] = fma(xs[c * P + quarter], wm.x, acc[c][0]);
+          acc[c][1] = fma(xs[c * P + quarter], wm.y, acc[c][1]);
+        }
+      }
+    } else {
+      const R* base = Tprev + (l - lo_prev);
+      for (int p = 0; p < P; ++p) {
+        const int64_t off = (int64_t)p * p;
+        R in[M::NCP][2];
 #pragma unroll
         for (int c = 0; c < M::NCP; ++c) {
           in[c][0] = __ldg(base + (2 * c + 0) * stride_prev + off);
           in[c][1] = __ldg(base + (2 * c + 1) * stride_prev + off);
         }
-      }
-      const double x[3] = {xs[p], xs[P + p], xs[2 * P + p]};
+        const R x[3] = {xs[p], xs[P + p], xs[2 * P + p]};
 #pragma unroll
-      for (int c = 0; c < M::NCO; ++c) {
-        acc[c][0] = fma(x[M::a(c)], in[M::r(c)][0], acc[c][0]);
-        acc[c][1] = fma(x[M::a(c)], in[M::r(c)][1], acc[c][1]);
+        for (int c = 0; c < M::NCO; ++c) {
+          acc[c][0] = fma(x[M::a(c)], in[M::r(c)][0], acc[c][0]);
+          acc[c][1] = fma(x[M::a(c)], in[M::r(c)][1], acc[c][1]);
+        }
       }
     }
     const int64_t pos = by_index ? idx : (l - lo_out);
 #pragma unroll
     for (int c = 0; c < M::NCO; ++c) {
-      Tout[(2 * c + 0) * stride_out + pos] = acc[c][0] * scale;
-      Tout[(2 * c + 1) * stride_out + pos] = acc[c][1] * scale;
+      Tout[(2 * c + 0) * stride_out + pos] = (OUT)((double)acc[c][0] * scale);
+      Tout[(2 * c + 1) * stride_out + pos] = (OUT)((double)acc[c][1] * scale);
     }
   }
 }
 
-template <int K>
+template <int K, typename R, typename OUT>
 cudaError_t launch_k(lsp_ctx* c, const int32_t* list, const int32_t* count, int64_t cap,
-                     const double* Tprev, int64_t lo_prev, int64_t stride_prev, double* Tout,
+                     const R* X, const R* Tprev, int64_t lo_prev, int64_t stride_prev, OUT* Tout,
                      int64_t lo_out, int64_t stride_out, bool by_index, double scale) {
   const int P = c->geo.P;
-  const size_t smem = sizeof(double) * 3 * P;
+  const size_t smem = sizeof(R) * 3 * P;
   if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_stage<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_stage<K, R, OUT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
   int64_t b = (cap + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
   if (b > 152 * 16) b = 152 * 16;
-  k_stage<K><<<(int)b, kThreads, smem, c->stream>>>(list, count, P, (const double*)c->xtab.p,
-                                                     Tprev, lo_prev, stride_prev, Tout, lo_out,
-                                                     stride_out, by_index ? 1 : 0, scale);
+  k_stage<K, R, OUT><<<(int)b, kThreads, smem, c->stream>>>(list, count, P, X, Tprev, lo_prev,
+                                                            stride_prev, Tout, lo_out, stride_out,
+                                                            by_index ? 1 : 0, scale);
   return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_typed(lsp_ctx* c, int d, int k, const int32_t* list, const int32_t* count,
+                         int64_t cap, const void* Tprev, int64_t lo_prev, int64_t stride_prev,
+                         void* Tout, int64_t lo_out, int64_t stride_out, bool by_index,
+                         double scale, const R* X) {
+  const R* prev = (const R*)Tprev;
+  if (k == d) {  // last stage: double g values for the eigen step
+    double* out = (double*)Tout;
+    if (k == 2)
+      return launch_k<2, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev, out,
+                                    lo_out, stride_out, by_index, scale);
+    return launch_k<3, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev, out, lo_out,
+                                  stride_out, by_index, scale);
+  }
+  R* out = (R*)Tout;
+  if (k == 1)
+    return launch_k<1, R, R>(c, list, count, cap, X, prev, lo_prev, stride_prev, out, lo_out,
+                             stride_out, by_index, scale);
+  return launch_k<2, R, R>(c, list, count, cap, X, prev, lo_prev, stride_prev, out, lo_out,
+                           stride_out, by_index, scale);
 }
 
 }  // namespace
 
 cudaError_t launch_stage(lsp_ctx* c, int d, int k, const int32_t* list, const int32_t* count,
-                         int64_t cap, const double* Tprev, int64_t lo_prev, int64_t stride_prev,
-                         double* Tout, int64_t lo_out, int64_t stride_out, bool by_index) {
+                         int64_t cap, const void* Tprev, int64_t lo_prev, int64_t stride_prev,
+                         void* Tout, int64_t lo_out, int64_t stride_out, bool by_index,
+                         bool fp32) {
   // The final stage carries the 1/N of the inverse transform (N a power of two: exact).
   const double scale = (k == d) ? 1.0 / (double)c->geo.N : 1.0;
   static const char* names[4] = {"", "stage1", "stage2", "stage3"};
   int t = timer_begin(c, names[k]);
-  cudaError_t e;
-  if (k == 1)
-    e = launch_k<1>(c, list, count, cap, Tprev, lo_prev, stride_prev, Tout, lo_out, stride_out,
-                    by_index, scale);
-  else if (k == 2)
-    e = launch_k<2>(c, list, count, cap, Tprev, lo_prev, stride_prev, Tout, lo_out, stride_out,
-                    by_index, scale);
-  else
-    e = launch_k<3>(c, list, count, cap, Tprev, lo_prev, stride_prev, Tout, lo_out, stride_out,
-                    by_index, scale);
+  cudaError_t e =
+      fp32 ? launch_typed<float>(c, d, k, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
+                                 lo_out, stride_out, by_index, scale, (const float*)c->xtab32.p)
+           : launch_typed<double>(c, d, k, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
+                                  lo_out, stride_out, by_index, scale, (const double*)c->xtab.p);
   timer_end(c, t);
-  (void)d;
   return e;
 }
 

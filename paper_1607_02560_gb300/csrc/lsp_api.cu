@@ -186,10 +186,24 @@ size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
 }  // namespace
 
 namespace lsp {
+bool ensure(lsp_ctx* c, DevBuf& b, size_t bytes);
+}
+namespace {
+// ensure() that also forgets a cached content key when the buffer is reallocated.
+bool ensure_tracked(lsp_ctx* c, lsp::DevBuf& b, size_t bytes, int64_t* key) {
+  void* before = b.p;
+  if (!lsp::ensure(c, b, bytes)) return false;
+  if (b.p != before) *key = -1;
+  return true;
+}
+}  // namespace
+
+namespace lsp {
 
 bool ensure(lsp_ctx* c, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return true;
+  ++c->alloc_gen;
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
@@ -286,22 +300,22 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
     count = counts + (d - k);
     cap = sz;
   }
-  CUDA_OK(c, launch_wtable(c, c->erange[0].lo, c->erange[0].size(), (double*)c->wtab.p));
+  const bool fp32 = o.mode == LSP_MIXED;  // the w table is refreshed by the caller
   for (int k = 1; k <= d; ++k) {
-    const double* prev = k == 1 ? (const double*)c->wtab.p : (const double*)c->T[k - 1].p;
+    const void* prev = k == 1 ? c->wtab.p : c->T[k - 1].p;
     const int64_t lo_prev = c->erange[k - 1].lo, stride_prev = c->erange[k - 1].size();
     if (k < d) {
       const bool dense = c->edense[k];
       CUDA_OK(c, launch_stage(c, d, k, dense ? nullptr : (const int32_t*)c->elist[k].p,
                               dense ? nullptr : counts + (d - k), c->erange[k].size(), prev,
-                              lo_prev, stride_prev, (double*)c->T[k].p, c->erange[k].lo,
-                              c->erange[k].size(), false));
+                              lo_prev, stride_prev, c->T[k].p, c->erange[k].lo,
+                              c->erange[k].size(), false, fp32));
     } else {
       CUDA_OK(c, launch_stage(c, d, k, (const int32_t*)c->shift_m.p, counts + 0, cap_s, prev,
-                              lo_prev, stride_prev, (double*)c->gvals.p, 0, cap_s, true));
+                              lo_prev, stride_prev, c->gvals.p, 0, cap_s, true, fp32));
     }
   }
-  CUDA_OK(c, launch_eig(c, counts + 0, cap_s, o.eig_method, o.refine_steps));
+  CUDA_OK(c, launch_eig(c, counts + 0, cap_s, o.eig_method, o.refine_steps, fp32));
   CUDA_OK(c, launch_rows(c, o.policy, counts + 0));
   return LSP_OK;
 }
@@ -346,15 +360,35 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
       st = LSP_ERR_CUDA;
       break;
     }
-    // X_a(p) = w_p cos(2 pi a p / n), w_p = 1 at p = 0 and p = n/2, else 2
+    // X_a(p) = w_p cos(2 pi a p / n), w_p = 1 at p = 0 and p = n/2, else 2. The cosine of
+    // 2 pi r / n is taken from the first octant by exact symmetries, so the table satisfies
+    // cos(pi a - t) = (-1)^a cos(t) (used by the mirror pairing of stage 1) bit for bit.
     const int P = c->geo.P;
     std::vector<double> X(3 * P);
     const long double two_pi = 6.283185307179586476925286766559005768L;
+    auto cos_r = [&](int r) -> long double {  // cos(2 pi r / n), r in [0, n)
+      r %= n;
+      int sign = 1;
+      if (r > n / 2) r = n - r;            // cos(2 pi - t) = cos t
+      if (r > n / 4) {                     // cos(pi - t) = -cos t
+        r = n / 2 - r;
+        sign = -1;
+      }
+      long double val;
+      if (r == 0)
+        val = 1.0L;
+      else if (4 * r == n)
+        val = 0.0L;
+      else if (8 * r > n)                   // cos t = sin(pi/2 - t)
+        val = sinl(two_pi * (long double)(n / 4 - r) / (long double)n);
+      else
+        val = cosl(two_pi * (long double)r / (long double)n);
+      return sign * val;
+    };
     for (int a = 0; a < 3; ++a)
       for (int p = 0; p < P; ++p) {
         const long double wgt = (p == 0 || p == n / 2) ? 1.0L : 2.0L;
-        const long double ang = two_pi * (long double)((a * p) % n) / (long double)n;
-        X[a * P + p] = (double)(wgt * cosl(ang));
+        X[a * P + p] = (double)(wgt * cos_r(a * p));
       }
     // twiddles exp(-2 pi i j / n), j < n/2
     std::vector<double> tw(n);
@@ -362,6 +396,13 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
       const long double ang = two_pi * (long double)j / (long double)n;
       tw[2 * j] = (double)cosl(ang);
       tw[2 * j + 1] = (double)(-sinl(ang));
+    }
+    std::vector<float> X32(X.begin(), X.end());
+    if (!ensure(c, c->xtab32, sizeof(float) * X32.size()) ||
+        cudaMemcpy(c->xtab32.p, X32.data(), sizeof(float) * X32.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      st = LSP_ERR_CUDA;
+      break;
     }
     if (!ensure(c, c->xtab, sizeof(double) * X.size()) ||
         !ensure(c, c->twiddle, sizeof(double) * tw.size()) ||
@@ -388,7 +429,7 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
 lsp_status lsp_destroy(lsp_ctx* c) {
   if (!c) return LSP_OK;
   cudaStreamSynchronize(c->stream);
-  DevBuf* bufs[] = {&c->v, &c->stats_part, &c->stats, &c->xtab, &c->shift_m, &c->shift_flag,
+  DevBuf* bufs[] = {&c->v, &c->stats_part, &c->stats, &c->xtab, &c->xtab32, &c->shift_m, &c->shift_flag,
                     &c->idx_of, &c->counts, &c->wtab, &c->gvals, &c->alpha, &c->cst, &c->lam,
                     &c->sflags, &c->Q, &c->C, &c->P, &c->sidx, &c->colidx, &c->rowptr,
                     &c->fftbuf, &c->twiddle};
@@ -449,7 +490,8 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     lsp_default_opts(&o);
   if (!c->have_v) return fail(c, LSP_ERR_STATE, "build_stencils before set_potential");
   if (o.t != 1) return fail(c, LSP_ERR_UNSUPPORTED, "only t = 1 neighbourhoods are built");
-  if (o.mode != LSP_FP64) return fail(c, LSP_ERR_UNSUPPORTED, "mode %d not built", o.mode);
+  if (o.mode != LSP_FP64 && o.mode != LSP_MIXED)
+    return fail(c, LSP_ERR_UNSUPPORTED, "mode %d is not built by lsp_build_stencils", o.mode);
   if (o.policy < 0 || o.policy > 3) return fail(c, LSP_ERR_ARG, "bad policy %d", o.policy);
   if (o.eig_method != LSP_EIG_SYMMETRIC && o.eig_method != LSP_EIG_FULL)
     return fail(c, LSP_ERR_ARG, "bad eig_method %d", o.eig_method);
@@ -535,7 +577,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
             ensure(c, c->cst, sizeof(double) * mu * cap_s) &&
             ensure(c, c->lam, sizeof(double) * 2 * cap_s) &&
             ensure(c, c->sflags, sizeof(int32_t) * cap_s) &&
-            ensure(c, c->wtab, sizeof(double) * c->erange[0].size()) &&
+            ensure_tracked(c, c->wtab, sizeof(double) * 2 * c->erange[0].size(), &c->wtab_size) &&
             ensure(c, c->Q, sizeof(double) * mu * N) && ensure(c, c->C, sizeof(double) * mu * N) &&
             ensure(c, c->P, sizeof(double) * mu * N);
   if (ok && o.policy == LSP_SHIFT_LOCAL)
@@ -566,15 +608,28 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   c->ns_host = o.policy == LSP_SHIFT_LOCAL ? -1 : cap_s;
   c->last_policy = o.policy;
 
+  // w depends only on its index range and precision: refreshed (outside any graph) only when
+  // those change, so a replayed graph always finds the table it was recorded with.
+  {
+    const bool fp32 = o.mode == LSP_MIXED;
+    if (!(c->wtab_lo == c->erange[0].lo && c->wtab_size == c->erange[0].size() &&
+          c->wtab_fp32 == (int)fp32)) {
+      CUDA_OK(c, launch_wtable(c, c->erange[0].lo, c->erange[0].size(), c->wtab.p, fp32));
+      c->wtab_lo = c->erange[0].lo;
+      c->wtab_size = c->erange[0].size();
+      c->wtab_fp32 = (int)fp32;
+    }
+  }
   lsp_status st;
   const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy &&
                           c->stream != cudaStreamPerThread;
   if (o.use_graph && !c->timing && capturable) {
-    std::vector<int64_t> key = {o.policy, o.eig_method, o.refine_steps, cap_s, c->mrange.lo,
+    std::vector<int64_t> key = {o.policy, o.mode, o.eig_method, o.refine_steps, cap_s, c->mrange.lo,
                                 c->mrange.hi, (int64_t)(intptr_t)c->v.p,
                                 (int64_t)(intptr_t)c->Q.p};
     for (int k = 0; k <= d; ++k) key.push_back(c->erange[k].lo);
     for (int k = 0; k < kMaxD; ++k) key.push_back(c->edense[k]);
+    key.push_back(c->alloc_gen);  // any reallocation invalidates recorded pointers
     if (!c->graph || key != c->graph_key) {
       if (c->graph) cudaGraphExecDestroy(c->graph);
       c->graph = nullptr;

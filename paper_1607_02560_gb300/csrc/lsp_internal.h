@@ -79,8 +79,8 @@ struct lsp_ctx {
   lsp::DevBuf v, stats_part, stats;
   double* h_stats = nullptr;  // pinned
 
-  // cos table X_a(p) = w_p cos(2 pi a p / n), a = 0..2, p = 0..n/2
-  lsp::DevBuf xtab;
+  // cos table X_a(p) = w_p cos(2 pi a p / n), a = 0..2, p = 0..n/2 (FP64 and FP32 copies)
+  lsp::DevBuf xtab, xtab32;
 
   // shift list (a2)
   bool built = false;
@@ -95,6 +95,9 @@ struct lsp_ctx {
   lsp::Range erange[lsp::kMaxD + 1];  // E_k ranges; E_d = shifts, E_0 = table domain
   lsp::DevBuf eflag[lsp::kMaxD], elist[lsp::kMaxD], T[lsp::kMaxD], wtab;
   bool edense[lsp::kMaxD] = {false, false, false};  // E_k evaluated over its whole range
+  int64_t wtab_lo = 0, wtab_size = -1;  // range held by wtab (-1: none)
+  int wtab_fp32 = -1;
+  int64_t alloc_gen = 0;  // bumped whenever a device buffer is (re)allocated
 
   // per-shift results (a3-a6)
   lsp::DevBuf gvals, alpha, cst, lam, sflags;
@@ -132,12 +135,13 @@ cudaError_t launch_compact(lsp_ctx* c, const uint8_t* flags, int64_t lo, int64_t
                            int32_t* list, int32_t* count, int32_t* idx_of);
 cudaError_t launch_mark_stage(lsp_ctx* c, const int32_t* list, const int32_t* count,
                               int64_t cap, int64_t lo_prev, uint8_t* flag_prev);
-cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, double* w);
+cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, void* w, bool fp32);
 cudaError_t launch_stage(lsp_ctx* c, int d, int k, const int32_t* list, const int32_t* count,
-                         int64_t cap, const double* Tprev, int64_t lo_prev, int64_t stride_prev,
-                         double* Tout, int64_t lo_out, int64_t stride_out, bool by_index);
+                         int64_t cap, const void* Tprev, int64_t lo_prev, int64_t stride_prev,
+                         void* Tout, int64_t lo_out, int64_t stride_out, bool by_index,
+                         bool fp32);
 cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int eig_method,
-                       int refine_steps);
+                       int refine_steps, bool fp32_gram);
 cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count);
 cudaError_t launch_sidx(lsp_ctx* c, int policy, const int32_t* count);
 cudaError_t launch_colidx(lsp_ctx* c);
