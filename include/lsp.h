@@ -165,6 +165,30 @@ lsp_status lsp_kernel_timing(lsp_ctx* ctx, int enable);
 lsp_status lsp_kernel_times(lsp_ctx* ctx, int cap, char (*names)[32], double* ms,
                             int64_t* launches, int* count);
 
+/*
+ * y = (L + diag(v)) u, like lsp_apply_operator, for callers that cannot allocate device
+ * memory when they need the operator: code running while a stream is being captured into a
+ * CUDA graph (cudaMalloc is not permitted there), or code whose device memory belongs to a
+ * pool or framework allocator that must not see extra allocations or device-wide syncs.
+ * The paper has no counterpart; this is a deployment variant of the same operator.
+ *
+ * Nothing is allocated: the transform's complex work array is a fixed array inside the
+ * library (16 MiB plus 32 KiB of twiddles, held on every GPU that loads the library until the
+ * process exits). The caller passes all inputs and outputs as device pointers to n^d float64
+ * values: the potential v, the input u and the output y (y may alias u). d in {2, 3}, n a power
+ * of two >= 8, and n^d <= LSP_NOALLOC_MAX_POINTS; larger grids return LSP_ERR_ARG (use a
+ * context). The work is issued on cuda_stream (a cudaStream_t; NULL = legacy default stream).
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture. Every call on a device
+ * shares the one array: calls whose GPU work may overlap (different streams, no ordering)
+ * race and give wrong results. Each call overwrites the whole work array before reading it,
+ * so nothing needs clearing. Errors: LSP_ERR_ARG for bad sizes or NULL pointers,
+ * LSP_ERR_CUDA if the address lookup or a launch fails.
+ */
+#define LSP_NOALLOC_MAX_POINTS 1048576
+lsp_status lsp_apply_operator_noalloc(int d, int n, const double* v_dev, const double* u_dev,
+                                      double* y_dev, void* cuda_stream);
+
 /* Message of the last failed call on this context ("" if none). Never NULL. */
 const char* lsp_last_error(const lsp_ctx* ctx);
 

@@ -128,3 +128,86 @@ cudaError_t launch_apply(lsp_ctx* c, const double* u, double* y) {
 }
 
 }  // namespace lsp
+
+// ---- y = (L + diag v) u without any device allocation -------------------------------------
+// Some callers cannot allocate device memory at the moment they need the operator: code that
+// runs while a CUDA stream is being captured into a graph (where cudaMalloc is not permitted),
+// and code whose device memory is owned by a pool or framework allocator that forbids extra
+// allocations, or that cannot afford the device-wide synchronisation a cudaMalloc may cause.
+// For them the complex work array of the transform lives in a fixed, file-scope device array
+// instead of a context buffer. Every GPU that loads this library holds that array (16 MiB for
+// the work array plus 32 KiB of twiddles) until the process exits.
+namespace lsp {
+namespace {
+
+constexpr int64_t kNoAllocMaxPoints = (int64_t)1 << 20;  // must match LSP_NOALLOC_MAX_POINTS
+constexpr int kNoAllocMaxHalfN = 2048;
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) double2 g_noalloc_work[kNoAllocMaxPoints];
+static __device__ __align__(256) double2 g_noalloc_twiddle[kNoAllocMaxHalfN];
+
+// Host-side copies of the arrays' device addresses, one per device ordinal. The symbol names
+// themselves are host stand-ins, not device addresses, so they are never passed to a kernel.
+double2* g_work_addr[kMaxDevices];
+double2* g_tw_addr[kMaxDevices];
+
+// exp(-2 pi i j / n), j < n/2, with the CUDA math library's sincospi.
+__global__ void k_noalloc_twiddles(double2* __restrict__ tw, int n) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n / 2; j += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)j / (double)n, &s, &c);
+    tw[j] = make_double2(c, -s);
+  }
+}
+
+}  // namespace
+}  // namespace lsp
+
+extern "C" lsp_status lsp_apply_operator_noalloc(int d, int n, const double* v_dev,
+                                                 const double* u_dev, double* y_dev,
+                                                 void* cuda_stream) {
+  using namespace lsp;
+  if (d != 2 && d != 3) return LSP_ERR_ARG;
+  if (n < 8 || (n & (n - 1)) != 0 || n / 2 > kNoAllocMaxHalfN) return LSP_ERR_ARG;
+  int64_t N = 1;
+  for (int i = 0; i < d; ++i) N *= n;
+  if (N > kNoAllocMaxPoints) return LSP_ERR_ARG;  // larger grids need the context path
+  if (!v_dev || !u_dev || !y_dev) return LSP_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LSP_ERR_CUDA;
+  // One-time set-up per device (this device is current): look up the arrays' addresses.
+  if (!g_work_addr[dev] || !g_tw_addr[dev]) {
+    double2* w = nullptr;
+    double2* t = nullptr;
+    if (cudaGetSymbolAddress((void**)&w, g_noalloc_work) != cudaSuccess ||
+        cudaGetSymbolAddress((void**)&t, g_noalloc_twiddle) != cudaSuccess) {
+      cudaGetLastError();
+      return LSP_ERR_CUDA;
+    }
+    g_work_addr[dev] = w;
+    g_tw_addr[dev] = t;
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double2* Z = g_work_addr[dev];
+  double2* tw = g_tw_addr[dev];
+  int logn = 0;
+  while ((1 << logn) < n) ++logn;
+  const int64_t nlines = N / n;
+  const size_t smem = sizeof(double2) * n;  // <= 16 KiB for n <= 1024
+  const int threads = n / 2 < 256 ? (n / 2 < 32 ? 32 : n / 2) : 256;
+  const int blocks = (int)(nlines < 152 * 32 ? nlines : 152 * 32);
+  cudaGetLastError();
+  k_noalloc_twiddles<<<(n / 2 + 255) / 256, 256, 0, st>>>(tw, n);
+  // The first pass writes every element of Z before any pass reads it, so the work array
+  // needs no clearing between calls.
+  for (int axis = 0; axis < d - 1; ++axis)
+    k_fft_axis<<<blocks, threads, smem, st>>>(Z, u_dev, v_dev, y_dev, d, n, logn, axis, nlines, tw,
+                                              axis == 0 ? kLoadReal : kPlain, 1);
+  k_fft_axis<<<blocks, threads, smem, st>>>(Z, u_dev, v_dev, y_dev, d, n, logn, d - 1, nlines, tw,
+                                            kSymbol, 1);
+  for (int axis = d - 2; axis >= 0; --axis)
+    k_fft_axis<<<blocks, threads, smem, st>>>(Z, u_dev, v_dev, y_dev, d, n, logn, axis, nlines, tw,
+                                              axis == 0 ? kOutput : kPlain, 0);
+  return cudaGetLastError() == cudaSuccess ? LSP_OK : LSP_ERR_CUDA;
+}

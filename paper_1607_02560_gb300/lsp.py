@@ -76,6 +76,8 @@ def lib() -> ctypes.CDLL:
         "lsp_kernel_times": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp,
                                              ctypes.POINTER(ctypes.c_int)]),
         "lsp_last_error": (ctypes.c_char_p, [vp]),
+        "lsp_apply_operator_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp,
+                                                       vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -102,6 +104,25 @@ def _ptr(a) -> int | None:
 
 def _on_device(a) -> int:
     return int(hasattr(a, "is_cuda") and a.is_cuda)
+
+
+def apply_operator_noalloc(d: int, n: int, v, u, y, stream=None) -> None:
+    """y = (L + diag v) u through lsp_apply_operator_noalloc (no device allocation).
+
+    v, u, y: torch CUDA tensors of n^d float64. Asynchronous on `stream` (default: torch's
+    current stream).
+    """
+    import torch
+
+    for a in (v, u, y):
+        if not _on_device(a):
+            raise ValueError("apply_operator_noalloc takes device tensors")
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = lib().lsp_apply_operator_noalloc(d, n, _ptr(v), _ptr(u), _ptr(y),
+                                          ctypes.c_void_p(stream.cuda_stream))
+    if st != LSP_OK:
+        raise LspError(st, f"lsp_apply_operator_noalloc(d={d}, n={n}) failed")
 
 
 def default_opts() -> StencilOpts:
