@@ -51,6 +51,28 @@ def dist_info():
     return ws, rank, local
 
 
+def rank_seed(rank: int):
+    """Each rank builds the stencils of its own potential: the workload's seed on rank 0,
+    seed 1000 + rank elsewhere (independent problems, no data exchange)."""
+    return None if rank == 0 else 1000 + rank
+
+
+def max_over_ranks(value: float, device: str = "cpu") -> float:
+    """The slowest rank's time (the job's time); identity without torch.distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(points_per_rank: int, steps: int, world: int, total_ms: float) -> float:
+    """Whole-job stencils/s: all ranks' points over the slowest rank's time."""
+    return points_per_rank * steps * world / (total_ms * 1e-3)
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -175,8 +197,7 @@ def run_ours(args):
     from paper_1607_02560_gb300 import build as B
 
     B.build()
-    seed = None if rank == 0 else 1000 + rank
-    v_host = make_workload(args.workload, seed=seed, n=args.n)
+    v_host = make_workload(args.workload, seed=rank_seed(rank), n=args.n)
     d, n = v_host.ndim, v_host.shape[0]
     N = v_host.size
     stream = torch.cuda.Stream()
@@ -218,9 +239,7 @@ def run_ours(args):
         total_ms = float(np.sum(step_ms))
         if ws > 1:
             import torch.distributed as dist
-            t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+            total_ms = max_over_ranks(total_ms, device="cuda")
             dist.barrier()
 
         # ---- per-kernel timing over K more steps (events around every launch) ----
@@ -255,7 +274,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
-    value = N * args.steps * ws / (total_ms * 1e-3)
+    value = job_throughput(N, args.steps, ws, total_ms)
     peaks, peak_src = load_peaks()
     sizes = lattice_domain_sizes(m_list, n, d)
     launches = int(sum(c for _, c in ktimes.values()))
@@ -319,14 +338,17 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup: int):
+def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup: int,
+                mlp=None, stream=None):
     """stencils/s of one configuration (same step, L2 flush and events as the main line)."""
     from lsp_inputs import make_workload
     from paper_1607_02560_gb300 import Context
 
     v = make_workload(workload)
-    stream = torch.cuda.Stream()
+    stream = stream or torch.cuda.Stream()
     ctx = Context(v.ndim, v.shape[0], stream=stream)
+    if mlp is not None:
+        ctx.set_mlp(mlp)
     v_dev = torch.from_numpy(v).to("cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     with torch.cuda.stream(stream):
@@ -344,7 +366,14 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
             e1.record(stream)
             torch.cuda.synchronize()
             tot += e0.elapsed_time(e1)
-        ns = len(ctx.get_shift_table(with_sidx=False)["s"])
+        used = ctx.mode_used()
+        ns = len(ctx.get_shift_table(with_sidx=False)["s"]) if used != "learned" else None
+        extra = {}
+        if used == "learned":
+            q_learned = ctx.get_rows("Q").copy()
+            ctx.build_stencils(policy=policy, mode="fp64")
+            extra["max_abs_dalpha_vs_fp64"] = float(np.abs(q_learned - ctx.get_rows("Q")).max())
+            ctx.build_stencils(policy=policy, mode=mode, use_graph=True)
         ctx.kernel_timing(True)
         for _ in range(5):
             flush.zero_()
@@ -354,9 +383,33 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
         kt = {k: round(ms / max(cnt, 1), 4) for k, (ms, cnt) in ctx.kernel_times().items()}
         ctx.kernel_timing(False)
     ctx.close()
-    return {"workload": workload, "policy": policy, "mode": mode, "value": v.size * steps / (tot * 1e-3),
-            "unit": "stencils/s", "ms_per_step": tot / steps, "shifts": ns,
-            "kernel_ms_per_launch": kt}
+    out = {"workload": workload, "policy": policy, "mode": mode, "mode_used": used,
+           "value": v.size * steps / (tot * 1e-3), "unit": "stencils/s",
+           "ms_per_step": tot / steps, "shifts": ns, "kernel_ms_per_launch": kt}
+    out.update(extra)
+    return out
+
+
+def learned_variant(torch, workload: str, steps: int = 3000):
+    """Train the surrogate on 16 other seeds of the workload, then time the learned build."""
+    from lsp_inputs import make_workload
+    from paper_1607_02560_gb300.learned import train_surrogate
+
+    stream = torch.cuda.Stream()
+    pots = [make_workload(workload, seed=s) for s in range(100, 116)]
+    t0 = time.time()
+    with torch.cuda.stream(stream):
+        mlp, losses = train_surrogate(pots[0].ndim, pots, samples_per_potential=65536,
+                                      steps=steps, batch=4096, lr=2e-3, stream=stream)
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    out = time_config(torch, workload, "local", "learned", steps=20, warmup=3, mlp=mlp,
+                      stream=stream)
+    out["training"] = {"potentials": len(pots), "pairs": 16 * 65536, "steps": steps,
+                       "batch": 4096, "seconds": round(t_train, 2),
+                       "final_loss": float(np.mean(losses[-50:]))}
+    mlp.close()
+    return out
 
 
 def variants(args, torch):
@@ -372,6 +425,12 @@ def variants(args, torch):
             out.append(time_config(torch, wl, pol, mode, steps=20, warmup=3))
         except Exception as exc:  # a variant must not hide the main line
             out.append({"workload": wl, "policy": pol, "mode": mode, "error": str(exc)[:200]})
+    if not args.no_learned:
+        for wl in ("helm2d_n1024", "schr3d_n64"):
+            try:
+                out.append(learned_variant(torch, wl))
+            except Exception as exc:
+                out.append({"workload": wl, "mode": "learned", "error": str(exc)[:300]})
     return out
 
 
@@ -442,6 +501,7 @@ def main():
     ap.add_argument("--policy", default="local", choices=["local", "paper", "mean"])
     ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip training the surrogate")
     ap.add_argument("--n", type=int, default=None, help="rescale the workload's grid (small cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

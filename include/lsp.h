@@ -69,7 +69,7 @@ typedef struct {
   int policy;          /* lsp_shift_policy                                                     */
   int nshifts;         /* PAPER: |S| before de-duplication; 0 selects n/16 (2D) or n/4 (3D)   */
   const double* shifts;/* LIST: nshifts shift values in host memory, each (4m+2) pi^2          */
-  int mode;            /* lsp_mode; this build implements LSP_FP64                             */
+  int mode;            /* lsp_mode: FP64, MIXED (FP32 contractions/Gram, FP64 solve), LEARNED  */
   int refine_steps;    /* inverse-iteration steps applied to each near-null vector (0 or 1)   */
   int eig_method;      /* lsp_eig_method                                                       */
   int use_graph;       /* 1: record the launch sequence once per configuration, replay it     */
@@ -164,6 +164,58 @@ lsp_status lsp_synchronize(lsp_ctx* ctx);
 lsp_status lsp_kernel_timing(lsp_ctx* ctx, int enable);
 lsp_status lsp_kernel_times(lsp_ctx* ctx, int cap, char (*names)[32], double* ms,
                             int64_t* launches, int* count);
+
+/*
+ * ---- Learned stencils (no counterpart in the paper: a surrogate for steps a3-a6) ----
+ * A multilayer perceptron maps the 5^d patch of h^2 v around a point and the point's snapped
+ * shift h^2 s_j (normalised) to that point's (alpha, c); it is trained on the stencils the
+ * eigen path (Sec. 4.1-4.2) produces.
+ * Layers: (5^d -> 256) SiLU, (256 -> 256) SiLU, (256 -> 256) SiLU, (256 -> 2|mu|); bf16 weights,
+ * fp32 accumulation on the tensor cores, fp32 master weights and Adam. In a LEARNED build the
+ * rows are Q = alpha / |alpha|, C = c / |alpha|, P = Q + C .* (v[mu_j] - s_j), s_j = snap(v_j).
+ */
+typedef struct lsp_mlp lsp_mlp;
+
+/* New network for d in {2, 3}, initialised from `seed`, working on cuda_stream. */
+lsp_status lsp_mlp_create(int d, uint64_t seed, void* cuda_stream, lsp_mlp** out);
+lsp_status lsp_mlp_destroy(lsp_mlp* m);
+/* Length of the flat fp32 parameter vector (*total) and how many of them are trainable. */
+lsp_status lsp_mlp_param_count(const lsp_mlp* m, int64_t* total, int64_t* nweights);
+/*
+ * Copy the flat fp32 parameter vector to / from host memory. Layout: W1 [256 x K0], b1 [256],
+ * W2 [256 x 256], b2, W3, b3, W4 [OUTP x 256], b4 [OUTP], then mu_x, sigma_x, mu_y[OUTP],
+ * sigma_y[OUTP], and the trained input range [lo, hi] of h^2 v. K0 = 32 (2D) / 128 (3D) with
+ * the 5^d + 1 real inputs first; OUTP = 32 / 64 with the 2|mu| real outputs first (alpha, c).
+ */
+lsp_status lsp_mlp_get_params(lsp_mlp* m, float* host);
+lsp_status lsp_mlp_set_params(lsp_mlp* m, const float* host);
+/*
+ * Training pairs from the context's last FP64 or MIXED build: for nsamples pseudo-random
+ * points (a hash of (seed, i)), X_dev[i] = the 5^d raw h^2 v features and h^2 s_j (fp32) and
+ * T_dev[i] = (alpha, c) of the point (fp32, 2|mu| values). Device pointers, caller-owned.
+ */
+lsp_status lsp_mlp_training_pairs(lsp_ctx* ctx, lsp_mlp* m, int64_t nsamples, uint64_t seed,
+                                  float* X_dev, float* T_dev);
+/* Set the input / output normalisation and the trained input range from n raw pairs. */
+lsp_status lsp_mlp_fit_normalization(lsp_mlp* m, const float* X_dev, const float* T_dev, int64_t n);
+/* Y_dev[i] (OUTP fp32, normalised output space) for raw inputs X_dev[i], i < batch. */
+lsp_status lsp_mlp_forward(lsp_mlp* m, const float* X_dev, int64_t batch, float* Y_dev);
+/*
+ * One training step on raw pairs (batch a multiple of 128): loss = mean over the batch and
+ * the 2|mu| outputs of (y - t_normalised)^2. apply = 1 takes an Adam step with rate lr.
+ * *loss_out (host) receives the loss; grads_host (optional, host, nweights floats) receives
+ * the gradient of the trainable parameters before the update.
+ */
+lsp_status lsp_mlp_train_step(lsp_mlp* m, const float* X_dev, const float* T_dev, int64_t batch,
+                              float lr, int apply, float* loss_out, float* grads_host);
+const char* lsp_mlp_last_error(const lsp_mlp* m);
+/* Attach a network to a context for LSP_LEARNED builds (NULL detaches). Same d required. */
+lsp_status lsp_set_mlp(lsp_ctx* ctx, lsp_mlp* m);
+/*
+ * Mode the last build actually used: a LEARNED build whose potential leaves the network's
+ * trained input range falls back to LSP_FP64 (the eigen path).
+ */
+lsp_status lsp_get_mode_used(const lsp_ctx* ctx, int* mode);
 
 /*
  * y = (L + diag(v)) u, like lsp_apply_operator, for callers that cannot allocate device

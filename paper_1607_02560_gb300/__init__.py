@@ -6,5 +6,5 @@ thin Python binding. Build the library with `paper_1607_02560_gb300.build.build(
 
 from .lsp import (  # noqa: F401
     EIG, FLAG_DEGENERATE, FLAG_NONSYMMETRIC, FLAG_NOT_CONVERGED, MODE, POLICY, Context,
-    LspError, declared_symbols, default_opts, lib,
+    LspError, Mlp, declared_symbols, default_opts, lib,
 )

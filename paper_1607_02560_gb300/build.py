@@ -49,7 +49,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     extra = list(extra or [])
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "lsp.h"))
     newest = max(os.path.getmtime(p) for p in srcs + headers + [__file__])
     if os.path.exists(LIB) and os.path.getmtime(LIB) >= newest and not extra:

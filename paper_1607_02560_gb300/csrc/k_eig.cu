@@ -74,6 +74,14 @@ __device__ int jacobi_small(double a[4][4], double v[4][4], int dim) {
   return 0;
 }
 
+// Per-block copies of the class table and the symmetry-adapted vectors: the warp kernel
+// indexes them with lane-dependent indices, which constant memory would serialise.
+template <int MU>
+struct __align__(16) BlockTables {
+  double u[kMaxSymVec][MU];
+  uint8_t cls[MU][MU];
+};
+
 template <int MU>
 struct __align__(16) WarpSmem {
   double A[MU * MU];
@@ -154,13 +162,13 @@ __device__ int jacobi_full(WarpSmem<MU>& sm, int lane) {
 // Rayleigh quotient of alpha. A0 is rebuilt from g (A may have been overwritten). Gaussian
 // elimination with partial pivoting, lanes own columns. A zero pivot leaves alpha unchanged.
 template <int MU>
-__device__ void refine_step(WarpSmem<MU>& sm, int lane, int centre) {
+__device__ void refine_step(WarpSmem<MU>& sm, const BlockTables<MU>& tb, int lane, int centre) {
   double* M = sm.V;  // the matrix (A0 - sigma I); the right-hand side lives in sm.work
   for (int e = lane; e < MU * MU; e += 32) {
     const int a = e / MU, b = e % MU;
     double s = 0.0;
-    for (int k = 0; k < MU; ++k) s = fma(sm.g[2 * c_cls[a][k]], sm.g[2 * c_cls[b][k]], s);
-    M[e] = sm.g[2 * c_cls[a][b] + 1] - s;
+    for (int k = 0; k < MU; ++k) s = fma(sm.g[2 * tb.cls[a][k]], sm.g[2 * tb.cls[b][k]], s);
+    M[e] = sm.g[2 * tb.cls[a][b] + 1] - s;
   }
   __syncwarp();
   // Rayleigh quotient
@@ -243,7 +251,13 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
                                                     int32_t* __restrict__ flags_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  WarpSmem<MU>& sm = reinterpret_cast<WarpSmem<MU>*>(smraw)[w];
+  BlockTables<MU>& tb = *reinterpret_cast<BlockTables<MU>*>(smraw);
+  WarpSmem<MU>& sm =
+      reinterpret_cast<WarpSmem<MU>*>(smraw + ((sizeof(BlockTables<MU>) + 15) / 16) * 16)[w];
+  for (int e = threadIdx.x; e < kMaxSymVec * MU; e += WARPS * 32)
+    tb.u[e / MU][e % MU] = c_sym.u[e / MU][e % MU];
+  for (int e = threadIdx.x; e < MU * MU; e += WARPS * 32) tb.cls[e / MU][e % MU] = c_cls[e / MU][e % MU];
+  __syncthreads();
   const int64_t cnt = *count;
   const int centre = MU / 2;
   for (int64_t i = (int64_t)blockIdx.x * WARPS + w; i < cnt; i += (int64_t)gridDim.x * WARPS) {
@@ -253,8 +267,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
     for (int e = lane; e < MU * MU; e += 32) {
       const int a = e / MU, b = e % MU;
       double s = 0.0;
-      for (int k = 0; k < MU; ++k) s = fma(sm.g[2 * c_cls[a][k]], sm.g[2 * c_cls[b][k]], s);
-      sm.A[e] = sm.g[2 * c_cls[a][b] + 1] - s;
+      for (int k = 0; k < MU; ++k) s = fma(sm.g[2 * tb.cls[a][k]], sm.g[2 * tb.cls[b][k]], s);
+      sm.A[e] = sm.g[2 * tb.cls[a][b] + 1] - s;
     }
     __syncwarp();
     double lam1 = 0, lam2 = 0, lmax = 0;
@@ -279,8 +293,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
       // projections B_b[i][j] = u_i^T A u_j
       for (int ent = lane; ent < c_nent; ent += 32) {
         const int b = c_ent[ent][0], ii = c_ent[ent][1], jj = c_ent[ent][2];
-        const double* ui = c_sym.u[c_sym.first[b] + ii];
-        const double* uj = c_sym.u[c_sym.first[b] + jj];
+        const double* ui = tb.u[c_sym.first[b] + ii];
+        const double* uj = tb.u[c_sym.first[b] + jj];
         double s = 0.0;
         for (int a = 0; a < MU; ++a) {
           if (ui[a] == 0.0) continue;
@@ -333,7 +347,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
         for (int a = 0; a < MU; ++a) {
           double s = 0.0;
           for (int r = 0; r < c_sym.dim[bstar]; ++r)
-            s = fma(sm.y[bstar][r], c_sym.u[c_sym.first[bstar] + r][a], s);
+            s = fma(sm.y[bstar][r], tb.u[c_sym.first[bstar] + r][a], s);
           sm.alpha[a] = s;
         }
       }
@@ -343,11 +357,11 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
       sign_fix<MU>(sm.alpha, centre);
     }
     __syncwarp();
-    for (int r = 0; r < refine; ++r) refine_step<MU>(sm, lane, centre);
+    for (int r = 0; r < refine; ++r) refine_step<MU>(sm, tb, lane, centre);
     // a6: c[b] = sum_a alpha[a] G[a, b]
     if (lane < MU) {
       double s = 0.0;
-      for (int a = 0; a < MU; ++a) s = fma(sm.g[2 * c_cls[a][lane]], sm.alpha[a], s);
+      for (int a = 0; a < MU; ++a) s = fma(sm.g[2 * tb.cls[a][lane]], sm.alpha[a], s);
       alpha_out[i * MU + lane] = sm.alpha[lane];
       c_out[i * MU + lane] = s;
     }
@@ -507,8 +521,14 @@ __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals,
     double l1s = ls;
     // remaining eigenvalues of the 3 x 3 block from its trace and principal minors
     const double tr = s00 + s11 + s22, m2 = a00 + a11 + a22;
-    if (!(res <= 64 * 2.2e-16) || !(ls > 0)) {
-      // not converged (tiny gap or a non-positive block): cyclic Jacobi on the block
+    double S = tr - l1s, Pp = m2 - l1s * S;
+    double disc = fmax(0.25 * S * S - Pp, 0.0);
+    double l3s = 0.5 * S + sqrt(disc);
+    double l2s = l3s > 0 ? Pp / l3s : 0.0;
+    // The adjugate iteration converges to the eigenvalue of smallest magnitude. Accept it when
+    // the residual is at rounding level and it is also the algebraically smallest (it can be
+    // slightly negative when the block was assembled in FP32); otherwise run cyclic Jacobi.
+    if (!(res <= 64 * 2.2e-16) || !(l1s <= l2s)) {
       double a[4][4] = {{s00, s01, s02, 0}, {s01, s11, s12, 0}, {s02, s12, s22, 0}, {0, 0, 0, 0}};
       double vv[4][4];
       if (!jacobi_small(a, vv, 3)) flags |= LSP_FLAG_NOT_CONVERGED;
@@ -519,11 +539,12 @@ __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals,
       y[0] = vv[0][k];
       y[1] = vv[1][k];
       y[2] = vv[2][k];
+      S = tr - l1s;
+      Pp = m2 - l1s * S;
+      disc = fmax(0.25 * S * S - Pp, 0.0);
+      l3s = 0.5 * S + sqrt(disc);
+      l2s = l3s > 0 ? Pp / l3s : 0.0;
     }
-    const double S = tr - l1s, Pp = m2 - l1s * S;
-    const double disc = fmax(0.25 * S * S - Pp, 0.0);
-    const double l3s = 0.5 * S + sqrt(disc);
-    const double l2s = l3s > 0 ? Pp / l3s : 0.0;
     double lam1 = l1s * sc, lamA2 = l2s * sc, lamA3 = l3s * sc;
     double eLo, eHi;
     eig2(e00, e01, e11, eLo, eHi);
@@ -601,7 +622,8 @@ __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals,
 
 template <int MU, int NCLS, int WARPS>
 cudaError_t launch_eig_t(lsp_ctx* c, const int32_t* count, int64_t cap, int method, int refine) {
-  const size_t smem = sizeof(WarpSmem<MU>) * WARPS;
+  const size_t smem =
+      ((sizeof(BlockTables<MU>) + 15) / 16) * 16 + sizeof(WarpSmem<MU>) * WARPS;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(k_eig<MU, NCLS, WARPS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -55,13 +55,6 @@ struct StageMap<3> {
   }
 };
 
-// One thread per domain point l; structure-of-arrays output Tout[(c * 2 + f) * stride_out + pos].
-//
-// Stage 1 reads the interleaved table (w, w^2) and pairs every p < n/4 with its mirror
-// q = n/2 - p: X_a(q) = (-1)^a X_a(p) (w_q = w_p, cos(pi a - t) = (-1)^a cos t), so
-//   sum_p X_a(p) w(p^2 + l) = sum_{p < n/4} X_a(p) [w(p^2 + l) + (-1)^a w(q^2 + l)] + X_a(n/4) w(n^2/16 + l),
-// i.e. 5 FP64 operations per frequency instead of 7 (the host table satisfies the mirror
-// identity exactly). Later stages read both functions of every input class.
 // R is the arithmetic type: double for the FP64 mode, float for the mixed mode. OUT is the
 // type of the output table (the last stage always writes double g values).
 template <typename R>
@@ -71,7 +64,92 @@ struct Vec2<double> { using type = double2; };
 template <>
 struct Vec2<float> { using type = float2; };
 
-template <int K, typename R, typename OUT>
+// Accumulate the stage-K sums of one domain point l over the frequencies p = first, first +
+// step, ... (all of them for step = 1). Structure-of-arrays tables: Tprev[(c * 2 + f) *
+// stride_prev + (l + p^2 - lo_prev)].
+//
+// Stage 1 reads the w table and pairs every p < n/4 with its mirror q = n/2 - p:
+// X_a(q) = (-1)^a X_a(p) (w_q = w_p, cos(pi a - t) = (-1)^a cos t), so
+//   sum_p X_a(p) w(p^2 + l) = sum_{p < n/4} X_a(p) [w(p^2 + l) + (-1)^a w(q^2 + l)] + X_a(n/4) w(n^2/16 + l),
+// 5 arithmetic operations per frequency instead of 7 (the host table satisfies the mirror
+// identity exactly). In FP64 the table interleaves (w, w^2) and is read with one 16-byte load
+// (the FP64 pipe is the bound); in FP32 it holds w alone and the square is formed in registers
+// (the L2 bandwidth is the bound).
+template <int K, typename R>
+__device__ __forceinline__ void stage_accumulate(const R* __restrict__ xs, int P, int64_t l,
+                                                 const R* __restrict__ Tprev, int64_t lo_prev,
+                                                 int64_t stride_prev, int first, int step,
+                                                 R (&acc)[StageMap<K>::NCO][2]) {
+  using M = StageMap<K>;
+  using R2 = typename Vec2<R>::type;
+  const int half = P - 1;  // n/2
+  if (K == 1) {
+    const R2* tab = reinterpret_cast<const R2*>(Tprev) + (l - lo_prev);
+    const R* tab1 = Tprev + (l - lo_prev);
+    constexpr bool kPair = sizeof(R) == 8;
+    const int quarter = half / 2;  // n/4
+#pragma unroll 4
+    for (int p = first; p < quarter; p += step) {
+      const int q = half - p;
+      R2 wa, wb;
+      if (kPair) {
+        wa = __ldg(tab + (int64_t)p * p);
+        wb = __ldg(tab + (int64_t)q * q);
+      } else {
+        wa.x = __ldg(tab1 + (int64_t)p * p);
+        wb.x = __ldg(tab1 + (int64_t)q * q);
+        wa.y = wa.x * wa.x;
+        wb.y = wb.x * wb.x;
+      }
+      const R s1 = wa.x + wb.x, d1 = wa.x - wb.x;
+      const R s2 = wa.y + wb.y, d2 = wa.y - wb.y;
+      const R x0 = xs[p], x1 = xs[P + p], x2 = xs[2 * P + p];
+      acc[0][0] = fma(x0, s1, acc[0][0]);
+      acc[1][0] = fma(x1, d1, acc[1][0]);
+      acc[2][0] = fma(x2, s1, acc[2][0]);
+      acc[0][1] = fma(x0, s2, acc[0][1]);
+      acc[1][1] = fma(x1, d2, acc[1][1]);
+      acc[2][1] = fma(x2, s2, acc[2][1]);
+    }
+    if (first == 0) {
+      R2 wm;
+      if (kPair) {
+        wm = __ldg(tab + (int64_t)quarter * quarter);
+      } else {
+        wm.x = __ldg(tab1 + (int64_t)quarter * quarter);
+        wm.y = wm.x * wm.x;
+      }
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        acc[c][0] = fma(xs[c * P + quarter], wm.x, acc[c][0]);
+        acc[c][1] = fma(xs[c * P + quarter], wm.y, acc[c][1]);
+      }
+    }
+  } else {
+    const R* base = Tprev + (l - lo_prev);
+    for (int p = first; p < P; p += step) {
+      const int64_t off = (int64_t)p * p;
+      R in[M::NCP][2];
+#pragma unroll
+      for (int c = 0; c < M::NCP; ++c) {
+        in[c][0] = __ldg(base + (2 * c + 0) * stride_prev + off);
+        in[c][1] = __ldg(base + (2 * c + 1) * stride_prev + off);
+      }
+      const R x[3] = {xs[p], xs[P + p], xs[2 * P + p]};
+#pragma unroll
+      for (int c = 0; c < M::NCO; ++c) {
+        acc[c][0] = fma(x[M::a(c)], in[M::r(c)][0], acc[c][0]);
+        acc[c][1] = fma(x[M::a(c)], in[M::r(c)][1], acc[c][1]);
+      }
+    }
+  }
+}
+
+// One thread per domain point (SPLIT = false), or one warp per domain point with the lanes
+// splitting the frequencies and a shuffle reduction at the end (SPLIT = true, used when the
+// domain is too small to fill the GPU, e.g. a few dozen shifts). Output: Tout[(c * 2 + f) *
+// stride_out + pos], pos = index in the list (by_index) or l - lo_out.
+template <int K, typename R, typename OUT, bool SPLIT>
 __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ list,
                                                     const int32_t* __restrict__ count_ptr, int P,
                                                     const R* __restrict__ X,
@@ -81,81 +159,31 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
                                                     int64_t stride_out, int by_index,
                                                     double scale) {
   using M = StageMap<K>;
-  using R2 = typename Vec2<R>::type;
   extern __shared__ __align__(16) unsigned char xs_raw[];
   R* xs = reinterpret_cast<R*>(xs_raw);  // [3][P]
   for (int i = threadIdx.x; i < 3 * P; i += kThreads) xs[i] = X[i];
   __syncthreads();
   // list == nullptr: the domain is the whole range [lo_out, lo_out + stride_out)
   const int64_t cnt = list ? (int64_t)*count_ptr : stride_out;
-  const int half = P - 1;  // n/2
-  for (int64_t idx = (int64_t)blockIdx.x * kThreads + threadIdx.x; idx < cnt;
-       idx += (int64_t)gridDim.x * kThreads) {
+  const int lane = threadIdx.x & 31;
+  const int64_t per_block = SPLIT ? kThreads / 32 : kThreads;
+  const int64_t sub = SPLIT ? (threadIdx.x >> 5) : threadIdx.x;
+  for (int64_t idx = (int64_t)blockIdx.x * per_block + sub; idx < cnt;
+       idx += (int64_t)gridDim.x * per_block) {
     const int64_t l = list ? (int64_t)__ldg(list + idx) : lo_out + idx;
     R acc[M::NCO][2];
 #pragma unroll
     for (int c = 0; c < M::NCO; ++c) acc[c][0] = acc[c][1] = R(0);
-    if (K == 1) {
-      // FP64: interleaved (w, w^2) table, one 16-byte load per term (the FP64 pipe is the
-      // bound, so the square is read rather than computed). FP32: plain w table, the square
-      // formed in registers (there the L2 bandwidth is the bound).
-      const R2* tab = reinterpret_cast<const R2*>(Tprev) + (l - lo_prev);
-      const R* tab1 = Tprev + (l - lo_prev);
-      constexpr bool kPair = sizeof(R) == 8;
-      const int quarter = half / 2;  // n/4
-      for (int p = 0; p < quarter; ++p) {
-        const int q = half - p;
-        R2 wa, wb;
-        if (kPair) {
-          wa = __ldg(tab + (int64_t)p * p);
-          wb = __ldg(tab + (int64_t)q * q);
-        } else {
-          wa.x = __ldg(tab1 + (int64_t)p * p);
-          wb.x = __ldg(tab1 + (int64_t)q * q);
-          wa.y = wa.x * wa.x;
-          wb.y = wb.x * wb.x;
-        }
-        const R s1 = wa.x + wb.x, d1 = wa.x - wb.x;
-        const R s2 = wa.y + wb.y, d2 = wa.y - wb.y;
-        const R x0 = xs[p], x1 = xs[P + p], x2 = xs[2 * P + p];
-        acc[0][0] = fma(x0, s1, acc[0][0]);
-        acc[1][0] = fma(x1, d1, acc[1][0]);
-        acc[2][0] = fma(x2, s1, acc[2][0]);
-        acc[0][1] = fma(x0, s2, acc[0][1]);
-        acc[1][1] = fma(x1, d2, acc[1][1]);
-        acc[2][1] = fma(x2, s2, acc[2][1]);
-      }
-      {
-        R2 wm;
-        if (kPair) {
-          wm = __ldg(tab + (int64_t)quarter * quarter);
-        } else {
-          wm.x = __ldg(tab1 + (int64_t)quarter * quarter);
-          wm.y = wm.x * wm.x;
-        }
+    stage_accumulate<K, R>(xs, P, l, Tprev, lo_prev, stride_prev, SPLIT ? lane : 0,
+                           SPLIT ? 32 : 1, acc);
+    if (SPLIT) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          acc[c][0] = fma(xs[c * P + quarter], wm.x, acc[c][0]);
-          acc[c][1] = fma(xs[c * P + quarter], wm.y, acc[c][1]);
-        }
-      }
-    } else {
-      const R* base = Tprev + (l - lo_prev);
-      for (int p = 0; p < P; ++p) {
-        const int64_t off = (int64_t)p * p;
-        R in[M::NCP][2];
+      for (int c = 0; c < M::NCO; ++c)
 #pragma unroll
-        for (int c = 0; c < M::NCP; ++c) {
-          in[c][0] = __ldg(base + (2 * c + 0) * stride_prev + off);
-          in[c][1] = __ldg(base + (2 * c + 1) * stride_prev + off);
-        }
-        const R x[3] = {xs[p], xs[P + p], xs[2 * P + p]};
+        for (int f = 0; f < 2; ++f)
 #pragma unroll
-        for (int c = 0; c < M::NCO; ++c) {
-          acc[c][0] = fma(x[M::a(c)], in[M::r(c)][0], acc[c][0]);
-          acc[c][1] = fma(x[M::a(c)], in[M::r(c)][1], acc[c][1]);
-        }
-      }
+          for (int o = 16; o > 0; o >>= 1) acc[c][f] += __shfl_xor_sync(0xffffffffu, acc[c][f], o);
+      if (lane != 0) continue;
     }
     const int64_t pos = by_index ? idx : (l - lo_out);
 #pragma unroll
@@ -166,24 +194,39 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
   }
 }
 
+template <int K, typename R, typename OUT, bool SPLIT>
+cudaError_t launch_kk(lsp_ctx* c, const int32_t* list, const int32_t* count, int64_t cap,
+                      const R* X, const R* Tprev, int64_t lo_prev, int64_t stride_prev, OUT* Tout,
+                      int64_t lo_out, int64_t stride_out, bool by_index, double scale) {
+  const int P = c->geo.P;
+  const size_t smem = sizeof(R) * 3 * P;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_stage<K, R, OUT, SPLIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t per_block = SPLIT ? kThreads / 32 : kThreads;
+  int64_t b = (cap + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > 152 * 16) b = 152 * 16;
+  k_stage<K, R, OUT, SPLIT><<<(int)b, kThreads, smem, c->stream>>>(
+      list, count, P, X, Tprev, lo_prev, stride_prev, Tout, lo_out, stride_out, by_index ? 1 : 0,
+      scale);
+  return cudaGetLastError();
+}
+
+// Domains below about two threads per SM-lane slot are spread over warps instead.
+constexpr int64_t kSplitBelow = 152 * 256;
+
 template <int K, typename R, typename OUT>
 cudaError_t launch_k(lsp_ctx* c, const int32_t* list, const int32_t* count, int64_t cap,
                      const R* X, const R* Tprev, int64_t lo_prev, int64_t stride_prev, OUT* Tout,
                      int64_t lo_out, int64_t stride_out, bool by_index, double scale) {
-  const int P = c->geo.P;
-  const size_t smem = sizeof(R) * 3 * P;
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_stage<K, R, OUT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  int64_t b = (cap + kThreads - 1) / kThreads;
-  if (b < 1) b = 1;
-  if (b > 152 * 16) b = 152 * 16;
-  k_stage<K, R, OUT><<<(int)b, kThreads, smem, c->stream>>>(list, count, P, X, Tprev, lo_prev,
-                                                            stride_prev, Tout, lo_out, stride_out,
-                                                            by_index ? 1 : 0, scale);
-  return cudaGetLastError();
+  if (cap < kSplitBelow)
+    return launch_kk<K, R, OUT, true>(c, list, count, cap, X, Tprev, lo_prev, stride_prev, Tout,
+                                      lo_out, stride_out, by_index, scale);
+  return launch_kk<K, R, OUT, false>(c, list, count, cap, X, Tprev, lo_prev, stride_prev, Tout,
+                                     lo_out, stride_out, by_index, scale);
 }
 
 template <typename R>

@@ -490,8 +490,33 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     lsp_default_opts(&o);
   if (!c->have_v) return fail(c, LSP_ERR_STATE, "build_stencils before set_potential");
   if (o.t != 1) return fail(c, LSP_ERR_UNSUPPORTED, "only t = 1 neighbourhoods are built");
-  if (o.mode != LSP_FP64 && o.mode != LSP_MIXED)
-    return fail(c, LSP_ERR_UNSUPPORTED, "mode %d is not built by lsp_build_stencils", o.mode);
+  if (o.mode != LSP_FP64 && o.mode != LSP_MIXED && o.mode != LSP_LEARNED)
+    return fail(c, LSP_ERR_ARG, "bad mode %d", o.mode);
+  if (o.mode == LSP_LEARNED) {
+    if (!c->mlp) return fail(c, LSP_ERR_STATE, "LEARNED build without a network (lsp_set_mlp)");
+    // Gate: the network answers only inside the h^2 v range it was trained on; outside it
+    // the FP64 eigen path builds the stencils instead.
+    float lo = 0, hi = 0;
+    if (!mlp_input_range(c->mlp, &lo, &hi)) return fail(c, LSP_ERR_CUDA, "reading the network");
+    const double h2 = 1.0 / ((double)c->geo.n * c->geo.n);
+    const double margin = 0.02 * ((double)hi - (double)lo);
+    if (c->vmin * h2 >= (double)lo - margin && c->vmax * h2 <= (double)hi + margin) {
+      const int64_t N = c->geo.N;
+      const int mu = c->geo.mu;
+      if (!ensure(c, c->Q, sizeof(double) * mu * N) || !ensure(c, c->C, sizeof(double) * mu * N) ||
+          !ensure(c, c->P, sizeof(double) * mu * N) ||
+          !ensure(c, c->counts, sizeof(int32_t) * 64))
+        return LSP_ERR_OOM;
+      c->built = false;
+      CUDA_OK(c, cudaMemsetAsync((int32_t*)c->counts.p + kErrWord, 0, sizeof(int32_t), c->stream));
+      CUDA_OK(c, launch_learned_rows(c, c->mlp));
+      c->built = true;
+      c->built_learned = true;
+      c->mode_used = LSP_LEARNED;
+      return LSP_OK;
+    }
+    o.mode = LSP_FP64;  // fallback
+  }
   if (o.policy < 0 || o.policy > 3) return fail(c, LSP_ERR_ARG, "bad policy %d", o.policy);
   if (o.eig_method != LSP_EIG_SYMMETRIC && o.eig_method != LSP_EIG_FULL)
     return fail(c, LSP_ERR_ARG, "bad eig_method %d", o.eig_method);
@@ -649,7 +674,11 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   } else {
     st = issue_build(c, o, cap_s, false);
   }
-  if (st == LSP_OK) c->built = true;
+  if (st == LSP_OK) {
+    c->built = true;
+    c->built_learned = false;
+    c->mode_used = o.mode;
+  }
   return st;
 }
 
@@ -716,6 +745,8 @@ lsp_status lsp_get_shift_table(lsp_ctx* c, int64_t* nshifts_out, double* s, doub
                                double* cst, double* lam, int32_t* flags, int32_t* s_idx) {
   if (!c) return LSP_ERR_ARG;
   if (!c->built) return fail(c, LSP_ERR_STATE, "no stencils built");
+  if (c->built_learned)
+    return fail(c, LSP_ERR_STATE, "a learned build has no shift table (rows only)");
   cudaGetLastError();
   int32_t head[16];
   CUDA_OK(c, cudaMemcpyAsync(head, c->counts.p, sizeof(head), cudaMemcpyDeviceToHost, c->stream));
@@ -758,6 +789,25 @@ lsp_status lsp_synchronize(lsp_ctx* c) {
   if (!c) return LSP_ERR_ARG;
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   CUDA_OK(c, cudaGetLastError());
+  if (c->built_learned && c->counts.p) {
+    int32_t e = 0;
+    CUDA_OK(c, cudaMemcpy(&e, (int32_t*)c->counts.p + kErrWord, sizeof e, cudaMemcpyDeviceToHost));
+    if (e) return fail(c, LSP_ERR_TIMEOUT, "a tensor-core wait gave up (bits %d)", e);
+  }
+  return LSP_OK;
+}
+
+lsp_status lsp_set_mlp(lsp_ctx* c, lsp_mlp* m) {
+  if (!c) return LSP_ERR_ARG;
+  if (m && mlp_dim(m) != c->geo.d) return fail(c, LSP_ERR_ARG, "network dimension mismatch");
+  if (m) CUDA_OK(c, mlp_sync(m));
+  c->mlp = m;
+  return LSP_OK;
+}
+
+lsp_status lsp_get_mode_used(const lsp_ctx* c, int* mode) {
+  if (!c || !mode) return LSP_ERR_ARG;
+  *mode = c->mode_used;
   return LSP_OK;
 }
 

@@ -9,6 +9,8 @@
 
 #include "../../include/lsp.h"
 
+struct lsp_mlp;
+
 namespace lsp {
 
 // pi^2 as the correctly rounded product of the double nearest pi. Kept identical on host and
@@ -115,6 +117,11 @@ struct lsp_ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   size_t ev_next = 0;
 
+  // learned surrogate (LSP_LEARNED builds)
+  lsp_mlp* mlp = nullptr;
+  bool built_learned = false;
+  int mode_used = -1;
+
   // graph cache
   cudaGraphExec_t graph = nullptr;
   std::vector<int64_t> graph_key;
@@ -147,5 +154,9 @@ cudaError_t launch_sidx(lsp_ctx* c, int policy, const int32_t* count);
 cudaError_t launch_colidx(lsp_ctx* c);
 cudaError_t launch_apply(lsp_ctx* c, const double* u, double* y);
 cudaError_t upload_sym(lsp_ctx* c);
+cudaError_t launch_learned_rows(lsp_ctx* c, lsp_mlp* m);
+bool mlp_input_range(lsp_mlp* m, float* lo, float* hi);
+int mlp_dim(const lsp_mlp* m);
+cudaError_t mlp_sync(lsp_mlp* m);
 
 }  // namespace lsp

@@ -78,6 +78,20 @@ def lib() -> ctypes.CDLL:
         "lsp_last_error": (ctypes.c_char_p, [vp]),
         "lsp_apply_operator_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp,
                                                        vp]),
+        "lsp_mlp_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, vp, ctypes.POINTER(vp)]),
+        "lsp_mlp_destroy": (ctypes.c_int, [vp]),
+        "lsp_mlp_param_count": (ctypes.c_int, [vp, i64p, i64p]),
+        "lsp_mlp_get_params": (ctypes.c_int, [vp, vp]),
+        "lsp_mlp_set_params": (ctypes.c_int, [vp, vp]),
+        "lsp_mlp_training_pairs": (ctypes.c_int, [vp, vp, ctypes.c_int64, ctypes.c_uint64, vp,
+                                                   vp]),
+        "lsp_mlp_fit_normalization": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64]),
+        "lsp_mlp_forward": (ctypes.c_int, [vp, vp, ctypes.c_int64, vp]),
+        "lsp_mlp_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, ctypes.c_float,
+                                               ctypes.c_int, ctypes.POINTER(ctypes.c_float), vp]),
+        "lsp_mlp_last_error": (ctypes.c_char_p, [vp]),
+        "lsp_set_mlp": (ctypes.c_int, [vp, vp]),
+        "lsp_get_mode_used": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -245,6 +259,17 @@ class Context:
     def synchronize(self):
         self._check(lib().lsp_synchronize(self.h), "synchronize")
 
+    def set_mlp(self, mlp):
+        """Attach a trained Mlp for mode="learned" builds (None detaches)."""
+        self._mlp = mlp
+        self._check(lib().lsp_set_mlp(self.h, mlp.h if mlp is not None else None), "set_mlp")
+
+    def mode_used(self) -> str:
+        """Mode the last build actually ran ("learned" falls back to "fp64" out of range)."""
+        m = ctypes.c_int()
+        self._check(lib().lsp_get_mode_used(self.h, ctypes.byref(m)), "get_mode_used")
+        return {v: k for k, v in MODE.items()}.get(m.value, str(m.value))
+
     def kernel_timing(self, enable: bool):
         self._check(lib().lsp_kernel_timing(self.h, int(bool(enable))), "kernel_timing")
 
@@ -258,3 +283,81 @@ class Context:
                                            ctypes.byref(cnt)), "kernel_times")
         return {names[i].value.decode(): (float(ms[i]), int(launches[i]))
                 for i in range(min(cnt.value, cap))}
+
+
+class Mlp:
+    """An lsp_mlp: the learned-stencil network (see include/lsp.h)."""
+
+    def __init__(self, d: int, seed: int = 0, stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required (no CPU fallback)")
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = lib().lsp_mlp_create(d, seed, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h))
+        if st != LSP_OK:
+            raise LspError(st, f"lsp_mlp_create(d={d}) failed")
+        self.h = h
+        self.d = d
+        self.mu = 9 if d == 2 else 27
+        self.nf = 26 if d == 2 else 126  # 5^d patch of h^2 v + the snapped shift h^2 s_j
+        self.out = 2 * self.mu
+        self.outp = 32 if d == 2 else 64
+        self.k0 = 32 if d == 2 else 128
+        tot, nw = ctypes.c_int64(), ctypes.c_int64()
+        lib().lsp_mlp_param_count(self.h, ctypes.byref(tot), ctypes.byref(nw))
+        self.nparams_total, self.nweights = tot.value, nw.value
+
+    def _check(self, st: int, what: str):
+        if st != LSP_OK:
+            msg = lib().lsp_mlp_last_error(self.h)
+            raise LspError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().lsp_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.nparams_total, dtype=np.float32)
+        self._check(lib().lsp_mlp_get_params(self.h, _ptr(out)), "get_params")
+        return out
+
+    def set_params(self, flat: np.ndarray):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        if flat.size != self.nparams_total:
+            raise ValueError("wrong parameter count")
+        self._check(lib().lsp_mlp_set_params(self.h, _ptr(flat)), "set_params")
+
+    def training_pairs(self, ctx: Context, n: int, seed: int, X, T):
+        """Raw (features, targets) of n random points of ctx's last eigen-path build."""
+        self._check(lib().lsp_mlp_training_pairs(ctx.h, self.h, n, seed, _ptr(X), _ptr(T)),
+                    "training_pairs")
+
+    def fit_normalization(self, X, T, n: int):
+        self._check(lib().lsp_mlp_fit_normalization(self.h, _ptr(X), _ptr(T), n),
+                    "fit_normalization")
+
+    def forward(self, X, n: int, Y):
+        self._check(lib().lsp_mlp_forward(self.h, _ptr(X), n, _ptr(Y)), "forward")
+
+    def train_step(self, X, T, batch: int, lr: float, apply: bool = True, grads=None) -> float:
+        loss = ctypes.c_float()
+        self._check(lib().lsp_mlp_train_step(self.h, _ptr(X), _ptr(T), batch, lr, int(apply),
+                                             ctypes.byref(loss), _ptr(grads)), "train_step")
+        return loss.value
+
+    def save(self, path: str):
+        np.save(path, self.get_params())
+
+    def load(self, path: str):
+        self.set_params(np.load(path))

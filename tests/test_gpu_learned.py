@@ -1,0 +1,210 @@
+"""Learned stencils on the GPU (tcgen05 forward/backward, Adam) against the CPU oracles.
+
+* forward and gradients of the network against the numpy FP64 definition (oracle/mlp_oracle),
+  with the same bf16-rounded weights; tolerance set by bf16 activations (about 1e-2 relative);
+* training lowers the loss;
+* a network trained on eigen-path stencils reproduces them: alpha close to the FP64 path, the
+  sparsification residual ||alpha^T G[mu, mu^c]|| within a small factor of the optimum
+  sqrt(lambda_1) (the eigen-path judge), and the oracle GMRES count within +1;
+* a potential outside the trained range falls back to the eigen path;
+* the gain: the learned build is faster than the FP64 eigen build on the same GPU.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from lsp_inputs import gaussian_source, helmholtz_random_bumps, make_workload
+from oracle import mlp_oracle as MO
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+    from paper_1607_02560_gb300 import build
+    build.build()
+    return torch.cuda.Stream()
+
+
+def unpack(flat, d):
+    """Weights and biases (float64 of the bf16-rounded weights) and normalisation."""
+    import torch
+    K0, OUTP = (32, 32) if d == 2 else (128, 64)
+    shapes = [(256, K0), (256, 256), (256, 256), (OUTP, 256)]
+    W, b, off = [], [], 0
+    for (n, k) in shapes:
+        w = flat[off:off + n * k].reshape(n, k)
+        W.append(torch.from_numpy(w.copy()).to(torch.bfloat16).to(torch.float64).numpy())
+        off += n * k
+        b.append(flat[off:off + n].astype(np.float64))
+        off += n
+    norm = flat[off:off + 2 + 2 * OUTP].astype(np.float64)
+    return W, b, norm, K0, OUTP
+
+
+def normalised_inputs(X, norm, K0):
+    import torch
+    x = (X.astype(np.float64) - norm[0]) / norm[1]
+    x = torch.from_numpy(x).to(torch.float32).to(torch.bfloat16).to(torch.float64).numpy()
+    out = np.zeros((X.shape[0], K0))
+    out[:, :X.shape[1]] = x
+    return out
+
+
+def pool_2d(mlp, stream, n=64, seeds=(100, 101), samples=8192):
+    from paper_1607_02560_gb300.learned import make_pool
+    pots = [helmholtz_random_bumps(n, 2 * np.pi * n / 4, 16, s) for s in seeds]
+    return make_pool(mlp, pots, samples, stream)
+
+
+def test_forward_and_gradients_match_oracle(stream):
+    import torch
+    from paper_1607_02560_gb300 import Mlp
+    mlp = Mlp(2, seed=5, stream=stream)
+    X, T = pool_2d(mlp, stream)
+    torch.cuda.synchronize()
+    mlp.fit_normalization(X, T, X.shape[0])
+    B = 256
+    Y = torch.empty((B, mlp.outp), dtype=torch.float32, device="cuda")
+    mlp.forward(X[:B], B, Y)
+    torch.cuda.synchronize()
+    W, b, norm, K0, OUTP = unpack(mlp.get_params(), 2)
+    x = normalised_inputs(X[:B].cpu().numpy(), norm, K0)
+    y_ref, _ = MO.mlp_forward(x, W, b)
+    y = Y.cpu().numpy()
+    assert np.abs(y - y_ref).max() <= 2e-2 * max(1.0, np.abs(y_ref).max())
+    # gradients of mean((y - t_norm)^2) over the real outputs
+    grads = np.empty(mlp.nweights, dtype=np.float32)
+    loss = mlp.train_step(X[:B], T[:B], B, 0.0, apply=False, grads=grads)
+    t = (T[:B].cpu().numpy().astype(np.float64) - norm[2:2 + 18]) / norm[2 + OUTP:2 + OUTP + 18]
+    tp = np.zeros((B, OUTP))
+    tp[:, :18] = t
+    # the oracle's loss averages over OUTP columns; rescale to the 18 real outputs
+    loss_ref, dW, db = MO.mlp_backward(x, tp, W, b)
+    loss_ref *= OUTP / 18
+    assert abs(loss - loss_ref) <= 3e-2 * loss_ref
+    off = 0
+    for layer, (n, k) in enumerate([(256, K0), (256, 256), (256, 256), (OUTP, 256)]):
+        g = grads[off:off + n * k].reshape(n, k)
+        ref = dW[layer] * OUTP / 18
+        rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+        assert rel < 5e-2, (layer, rel)
+        off += n * k
+        gb = grads[off:off + n]
+        rb = db[layer] * OUTP / 18
+        assert np.linalg.norm(gb - rb) / np.linalg.norm(rb) < 5e-2, layer
+        off += n
+
+
+def test_training_lowers_the_loss(stream):
+    import torch
+    from paper_1607_02560_gb300 import Mlp
+    from paper_1607_02560_gb300.learned import train
+    mlp = Mlp(2, seed=1, stream=stream)
+    X, T = pool_2d(mlp, stream)
+    torch.cuda.synchronize()
+    mlp.fit_normalization(X, T, X.shape[0])
+    losses = train(mlp, X, T, steps=300, batch=1024, lr=2e-3)
+    assert np.mean(losses[-20:]) < 0.1 * np.mean(losses[:5]), (losses[:5], losses[-5:])
+
+
+@pytest.fixture(scope="module")
+def trained_2d_n32(stream):
+    """A network trained on eigen-path stencils of 2D n = 32 Helmholtz potentials."""
+    from paper_1607_02560_gb300.learned import train_surrogate
+    pots = [helmholtz_random_bumps(32, 2 * np.pi * 8, 16, s) for s in range(100, 132)]
+    mlp, losses = train_surrogate(2, pots, samples_per_potential=8192, steps=4000, batch=2048,
+                                  lr=2e-3, seed=3, stream=stream)
+    return mlp, losses
+
+
+def test_learned_stencils_are_judged_by_the_eigen_path(stream, trained_2d_n32):
+    from paper_1607_02560_gb300 import Context
+    mlp, losses = trained_2d_n32
+    v = make_workload("helm2d_n32")
+    n, d = 32, 2
+    ctx = Context(d, n, stream=stream)
+    ctx.set_mlp(mlp)
+    ctx.set_potential(v)
+    ctx.build_stencils(mode="learned")
+    assert ctx.mode_used() == "learned"
+    Ql, Cl, Pl = (ctx.get_rows(k).copy() for k in "QCP")
+    ref = O.build_stencils(v, "local")
+    err = np.abs(Ql - ref["Q"]).max()
+    # judge: sparsification residual alpha^T A alpha against lambda_1 for every shift
+    sidx = ref["s_idx"].reshape(-1)
+    worst = 0.0
+    for i, s in enumerate(ref["S"]):
+        st = O.stencil_for_shift(n, d, float(s))
+        pts = np.nonzero(sidx == i)[0]
+        a = Ql[pts]
+        ratio = np.sqrt(np.einsum("pi,ij,pj->p", a, st["A"], a) / st["lam1"])
+        worst = max(worst, float(ratio.max()))
+    print(f"learned: max |d alpha| = {err:.3g}, worst residual / optimum = {worst:.3f}, "
+          f"final loss {np.mean(losses[-50:]):.3g}")
+    assert err < 5e-2
+    assert worst < 3.0
+    # GMRES with the learned P, C
+    import scipy.sparse
+    mats = {}
+    for which in "CP":
+        rowptr, colidx, vals = ctx.export_sparse_rows(which)
+        mats[which] = scipy.sparse.csr_matrix((vals, colidx, rowptr), shape=(n * n, n * n))
+    with open(os.path.join(GOLDEN, "gmres_helm2d_n32.json")) as fh:
+        gold = json.load(fh)["iterations"]["local/2.0"]
+    _, it, res, info = O.gmres_solve(v, gaussian_source(n, 2, 2.0), mats["P"], mats["C"])
+    assert info == 0 and it <= gold + 1, (it, gold)
+
+
+def test_learned_build_falls_back_outside_the_trained_range(stream, trained_2d_n32):
+    from paper_1607_02560_gb300 import Context
+    mlp, _ = trained_2d_n32
+    v = make_workload("helm2d_n32") * 20.0  # h^2 v far below the training range
+    ctx = Context(2, 32, stream=stream)
+    ctx.set_mlp(mlp)
+    ctx.set_potential(v)
+    ctx.build_stencils(mode="learned")
+    assert ctx.mode_used() == "fp64"
+    q = ctx.get_rows("Q").copy()
+    ctx.build_stencils(mode="fp64")
+    assert np.array_equal(ctx.get_rows("Q"), q)
+
+
+def test_learned_gain_over_the_eigen_path(stream):
+    """What the network gains: stencils per second at 2D n=256 against the FP64 eigen build."""
+    import torch
+    from paper_1607_02560_gb300 import Context
+    from paper_1607_02560_gb300.learned import train_surrogate
+    n = 256
+    pots = [helmholtz_random_bumps(n, 2 * np.pi * 64, 16, s) for s in range(100, 108)]
+    mlp, _ = train_surrogate(2, pots, samples_per_potential=16384, steps=600, batch=4096,
+                             stream=stream)
+    v = make_workload("helm2d_n256")
+    ctx = Context(2, n, stream=stream)
+    ctx.set_mlp(mlp)
+    ctx.set_potential(v)
+
+    def timed(mode):
+        for _ in range(3):
+            ctx.build_stencils(mode=mode)
+        ctx.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(10):
+            ctx.build_stencils(mode=mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 10
+
+    t64 = timed("fp64")
+    tl = timed("learned")
+    assert ctx.mode_used() == "learned"
+    print(f"n=256: fp64 {t64:.3f} ms, learned {tl:.3f} ms, gain {t64 / tl:.1f}x")
+    assert tl < t64
