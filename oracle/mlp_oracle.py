@@ -5,7 +5,7 @@ imports it. The paper has no learned component: this network is a surrogate trai
 paper's own stencils (Sec. 4.1, 4.2), so its oracle is the textbook definition of a
 multilayer perceptron, written out in numpy:
 
-    z_l = a_{l-1} W_l^T + b_l,   a_l = silu(z_l) = z_l * sigmoid(z_l)   (hidden layers),
+    z_l = a_{l-1} W_l^T + b_l,   a_l = hswish(z_l) = z_l * clamp(z_l + 3, 0, 6) / 6   (hidden),
     y   = a_{L-1} W_L^T + b_L,   loss = mean over the batch and the outputs of (y - t)^2,
 
 with the gradients of that loss by the chain rule. Weights enter as float64 copies of the
@@ -13,24 +13,28 @@ values the GPU uses (bf16 weights, fp32 biases); the comparison tolerance reflec
 activations on the GPU.
 
 Input of the network for a point j: the (2r+1)^d patch of h^2 v around j (periodic), in
-lexicographic offset order (last axis fastest), normalised by (x - mean) / std of the training
-set. Output: alpha (|mu| values) and c / c_scale (|mu| values), normalised per output.
+lexicographic offset order (last axis fastest), then h^2 s_j with s_j the point's snapped shift;
+normalised by (x - mean) / std of the training set. Output: alpha (|mu| values) and c (|mu|
+values), normalised per output.
 """
 
 from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["silu", "silu_grad", "mlp_forward", "mlp_backward", "patches", "finite_difference"]
+__all__ = ["hswish", "hswish_grad", "mlp_forward", "mlp_backward", "patches",
+           "finite_difference"]
 
 
-def silu(z):
-    return z / (1.0 + np.exp(-z))
+def hswish(z):
+    """Hard-swish activation z * clamp(z + 3, 0, 6) / 6."""
+    return z * np.clip(z + 3.0, 0.0, 6.0) / 6.0
 
 
-def silu_grad(z):
-    s = 1.0 / (1.0 + np.exp(-z))
-    return s * (1.0 + z * (1.0 - s))
+def hswish_grad(z):
+    """Its derivative: 0 below -3, (2z + 3) / 6 on [-3, 3], 1 above 3."""
+    z = np.asarray(z, dtype=np.float64)
+    return np.where(z < -3.0, 0.0, np.where(z > 3.0, 1.0, (2.0 * z + 3.0) / 6.0))
 
 
 def mlp_forward(x: np.ndarray, weights: list, biases: list):
@@ -41,7 +45,7 @@ def mlp_forward(x: np.ndarray, weights: list, biases: list):
     for li, (W, b) in enumerate(zip(weights, biases)):
         z = a @ np.asarray(W, np.float64).T + np.asarray(b, np.float64)
         zs.append(z)
-        a = silu(z) if li < L - 1 else z
+        a = hswish(z) if li < L - 1 else z
         acts.append(a)
     return a, (zs, acts)
 
@@ -55,7 +59,7 @@ def mlp_backward(x, t, weights, biases):
     L = len(weights)
     dWs, dbs = [None] * L, [None] * L
     for li in range(L - 1, -1, -1):
-        dz = g if li == L - 1 else g * silu_grad(zs[li])
+        dz = g if li == L - 1 else g * hswish_grad(zs[li])
         dWs[li] = dz.T @ acts[li]
         dbs[li] = dz.sum(axis=0)
         g = dz @ np.asarray(weights[li], np.float64)

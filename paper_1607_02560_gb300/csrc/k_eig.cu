@@ -76,6 +76,129 @@ __device__ int jacobi_small(double a[4][4], double v[4][4], int dim) {
 
 // Per-block copies of the class table and the symmetry-adapted vectors: the warp kernel
 // indexes them with lane-dependent indices, which constant memory would serialise.
+
+// 2^-e for the exponent of |x| (exact scaling without FP64 arithmetic on the exponent).
+__device__ __forceinline__ double pow2_inv_exp(double x) {
+  const long long bits = __double_as_longlong(x) & 0x7ff0000000000000LL;
+  if (bits == 0 || bits == 0x7ff0000000000000LL) return 1.0;
+  return __longlong_as_double(0x7fe0000000000000LL - bits);  // 2^(1023 - e) * 2^... = 2^-e
+}
+
+// LDL^T factorisation (no pivoting) of a symmetric positive definite dim x dim matrix; returns
+// false if a pivot is not positive. L unit lower triangular, id = 1 / D.
+__device__ bool ldlt(const double s[4][4], int dim, double L[4][4], double id[4]) {
+  double d[4];
+  for (int j = 0; j < dim; ++j) {
+    double dj = s[j][j];
+    for (int k = 0; k < j; ++k) dj -= L[j][k] * L[j][k] * d[k];
+    if (!(dj > 0.0)) return false;
+    d[j] = dj;
+    id[j] = 1.0 / dj;
+    for (int i = j + 1; i < dim; ++i) {
+      double a = s[i][j];
+      for (int k = 0; k < j; ++k) a -= L[i][k] * L[j][k] * d[k];
+      L[i][j] = a * id[j];
+    }
+  }
+  return true;
+}
+
+// x <- (L D L^T)^-1 x, renormalised by a power of two.
+__device__ __forceinline__ void ldlt_solve(const double L[4][4], const double id[4], int dim,
+                                           double x[4]) {
+  for (int i = 0; i < dim; ++i)
+    for (int k = 0; k < i; ++k) x[i] -= L[i][k] * x[k];
+  for (int i = 0; i < dim; ++i) x[i] *= id[i];
+  for (int i = dim - 1; i >= 0; --i)
+    for (int k = i + 1; k < dim; ++k) x[i] -= L[k][i] * x[k];
+  double mx = 0.0;
+  for (int i = 0; i < dim; ++i) mx = fmax(mx, fabs(x[i]));
+  const double p2 = pow2_inv_exp(mx);
+  for (int i = 0; i < dim; ++i) x[i] *= p2;
+}
+
+// Smallest eigenpair of a small symmetric positive semidefinite block (dim <= 4) by inverse
+// iteration with one LDL^T factorisation, checked by its residual; cyclic Jacobi when the
+// factorisation fails or the iteration has not converged. *lam2 receives the block's next
+// eigenvalue (inverse iteration on the block deflated by the first pair; used for the
+// degeneracy flag only). Far fewer FP64 instructions than Jacobi's divide/square-root chains.
+__device__ int block_min_eig(const double b[4][4], int dim, double y[4], double* lam_min,
+                             double* lam2) {
+  y[0] = y[1] = y[2] = y[3] = 0.0;
+  if (dim == 1) {
+    y[0] = 1.0;
+    *lam_min = b[0][0];
+    *lam2 = DBL_MAX;
+    return 1;
+  }
+  double sc = 0.0;
+  for (int i = 0; i < dim; ++i)
+    for (int j = 0; j < dim; ++j) sc = fmax(sc, fabs(b[i][j]));
+  const double isc = sc > 0 ? 1.0 / sc : 0.0;
+  double s[4][4], L[4][4], id[4];
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      s[i][j] = (i < dim && j < dim) ? b[i][j] * isc : 0.0;
+      L[i][j] = 0.0;
+    }
+  bool ok = ldlt(s, dim, L, id);
+  double x[4] = {1.0, 0.5, 0.25, 0.125};
+  double ls = 0.0;
+  if (ok) {
+    for (int it = 0; it < 40; ++it) ldlt_solve(L, id, dim, x);
+    double nrm = 0.0;
+    for (int i = 0; i < dim; ++i) nrm = fma(x[i], x[i], nrm);
+    const double inv = rsqrt(nrm);
+    double r[4] = {0, 0, 0, 0}, res = 0.0;
+    for (int i = 0; i < dim; ++i) x[i] *= inv;
+    for (int i = 0; i < dim; ++i) {
+      for (int j = 0; j < dim; ++j) r[i] = fma(s[i][j], x[j], r[i]);
+      ls = fma(x[i], r[i], ls);
+    }
+    for (int i = 0; i < dim; ++i) res = fmax(res, fabs(r[i] - ls * x[i]));
+    ok = res <= 64 * 2.2e-16 && isfinite(ls);
+  }
+  if (!ok) {
+    double a[4][4], vv[4][4];
+    for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) a[i][j] = s[i][j];
+    const int conv = jacobi_small(a, vv, dim);
+    int kk = 0;
+    for (int i = 1; i < dim; ++i)
+      if (a[i][i] < a[kk][kk]) kk = i;
+    double second = DBL_MAX;
+    for (int i = 0; i < dim; ++i)
+      if (i != kk) second = fmin(second, a[i][i]);
+    for (int i = 0; i < dim; ++i) y[i] = vv[i][kk];
+    *lam_min = a[kk][kk] * sc;
+    *lam2 = second * sc;
+    return conv;
+  }
+  for (int i = 0; i < dim; ++i) y[i] = x[i];
+  *lam_min = ls * sc;
+  // second eigenvalue: move the found one above the others, iterate again
+  double tr = 0.0;
+  for (int i = 0; i < dim; ++i) tr += s[i][i];
+  const double shift = fabs(tr) + 1.0;
+  for (int i = 0; i < dim; ++i)
+    for (int j = 0; j < dim; ++j) s[i][j] = fma(shift * y[i], y[j], s[i][j]);
+  double z[4] = {0.125, 0.25, 0.5, 1.0};
+  if (ldlt(s, dim, L, id)) {
+    for (int it = 0; it < 12; ++it) ldlt_solve(L, id, dim, z);
+    double nrm = 0.0, q = 0.0;
+    for (int i = 0; i < dim; ++i) nrm = fma(z[i], z[i], nrm);
+    for (int i = 0; i < dim; ++i) {
+      double r = 0.0;
+      for (int j = 0; j < dim; ++j) r = fma(s[i][j], z[j], r);
+      q = fma(z[i], r, q);
+    }
+    *lam2 = (q / nrm) * sc;
+  } else {
+    *lam2 = *lam_min;  // degenerate
+  }
+  return 1;
+}
+
 template <int MU>
 struct __align__(16) BlockTables {
   double u[kMaxSymVec][MU];
@@ -309,21 +432,38 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
       __syncwarp();
       if (lane < c_sym.nblk) {
         const int dim = c_sym.dim[lane];
-        double a[4][4], v[4][4];
+        double a[4][4], y[4], lmin, l2;
         for (int r = 0; r < 4; ++r)
           for (int q = 0; q < 4; ++q) a[r][q] = (r < dim && q < dim) ? sm.B[lane][r * 4 + q] : 0.0;
-        sm.conv[lane] = jacobi_small(a, v, dim);
-        // sort eigenvalues ascending, keep the eigenvector of the smallest
-        int order[4] = {0, 1, 2, 3};
-        for (int r = 0; r < dim; ++r)
-          for (int q = r + 1; q < dim; ++q)
-            if (a[order[q]][order[q]] < a[order[r]][order[r]]) {
-              int tmp = order[r];
-              order[r] = order[q];
-              order[q] = tmp;
-            }
-        for (int r = 0; r < 4; ++r) sm.lam[lane][r] = r < dim ? a[order[r]][order[r]] : DBL_MAX;
-        for (int r = 0; r < 4; ++r) sm.y[lane][r] = r < dim ? v[r][order[0]] : 0.0;
+        if (dim == 2) {
+          // closed form for 2 x 2 blocks
+          const double m = 0.5 * (a[0][0] + a[1][1]), h = 0.5 * (a[0][0] - a[1][1]);
+          const double rr = sqrt(fma(h, h, a[0][1] * a[0][1]));
+          const double hi = m + rr;
+          lmin = hi != 0.0 ? (a[0][0] * a[1][1] - a[0][1] * a[0][1]) / hi : m - rr;
+          l2 = hi;
+          double p = a[0][1], q = lmin - a[0][0];
+          if (fabs(a[0][0] - lmin) < fabs(a[1][1] - lmin)) {
+            p = lmin - a[1][1];
+            q = a[0][1];
+          }
+          double nr = sqrt(p * p + q * q);
+          if (nr == 0) { p = 1; q = 0; nr = 1; }
+          y[0] = p / nr;
+          y[1] = q / nr;
+          y[2] = y[3] = 0.0;
+          sm.conv[lane] = 1;
+        } else {
+          sm.conv[lane] = block_min_eig(a, dim, y, &lmin, &l2);
+        }
+        sm.lam[lane][0] = lmin;
+        sm.lam[lane][1] = dim > 1 ? l2 : DBL_MAX;
+        sm.lam[lane][2] = DBL_MAX;
+        sm.lam[lane][3] = DBL_MAX;
+        double tr = 0.0;
+        for (int r = 0; r < dim; ++r) tr += a[r][r];
+        sm.work[lane] = tr;  // bound of the block's largest eigenvalue (PSD blocks)
+        for (int r = 0; r < 4; ++r) sm.y[lane][r] = y[r];
       }
       __syncwarp();
       if (lane == 0) {
@@ -332,9 +472,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
           if (sm.lam[b][0] < sm.lam[bstar][0]) bstar = b;
         lam1 = sm.lam[bstar][0];
         lam2 = DBL_MAX;
+        for (int b = 0; b < c_sym.nblk; ++b) lmax = fmax(lmax, fabs(sm.work[b]));
         for (int b = 0; b < c_sym.nblk; ++b) {
-          for (int r = 0; r < c_sym.dim[b]; ++r) {
-            lmax = fmax(lmax, fabs(sm.lam[b][r]));
+          for (int r = 0; r < c_sym.dim[b] && r < 2; ++r) {
             if (b == bstar && r == 0) {
               if (c_sym.copies[b] > 1) lam2 = fmin(lam2, sm.lam[b][r]);
               continue;

@@ -7,15 +7,15 @@
 //        (h^2 s_j - mu_x) / sigma_x with s_j = snap(v_j), zero-padded to K0. The stencil of the
 //        method depends on v_j only through the snapped shift s_j (a step function of v_j), so
 //        s_j is given to the network directly; the patch lets it use the neighbourhood too.
-//   z1 = x W1^T + b1, h1 = silu(z1);  z2, h2;  z3, h3 (hidden width 256)
+//   z1 = x W1^T + b1, h1 = a(z1);  z2, h2;  z3, h3 (hidden width 256), a = hard-swish
 //   y  = h3 W4^T + b4;  (alpha, c) = y * sigma_y + mu_y;  alpha /= |alpha|, c scaled alike
 //   rows: Q = alpha, C = c, P = alpha + c .* (v[mu_j] - s_j), s_j = snap(v_j)   (Sec. 4.1)
 //
 // Tensor cores: every layer is a BF16 x BF16 -> FP32 tcgen05 MMA with the accumulator in
 // tensor memory (M = 128 rows per tile, N = 256). A single elected thread issues the MMAs and
-// the bulk copies of the weight chunks (double-buffered, 32 KiB each); the epilogue (bias,
-// SiLU, bf16 pack into the canonical shared-memory layout of the next layer's A operand) runs
-// on all four warps from tcgen05.ld. Training uses the same fused forward (saving z and h),
+// the bulk copies of the weight chunks (double-buffered); the epilogue (bias, activation, bf16
+// pack into the canonical shared-memory layout of the next layer's A operand) runs on eight
+// warps from tcgen05.ld. Training uses the same fused forward (saving z and h),
 // a generic tcgen05 TN GEMM for the backward products, and Adam.
 #include <math.h>
 #include <stdarg.h>
@@ -34,9 +34,10 @@ namespace {
 
 constexpr int kH = 256;         // hidden width
 constexpr int kTile = 128;      // rows per tile (MMA M)
-constexpr int kChunkK = 64;     // K width of a streamed weight chunk
+constexpr int kChunkK = 64;     // K width of a GEMM staging chunk (training)
+constexpr int kChunkBytes = 16384;  // bytes of a streamed weight chunk (fused kernel)
 constexpr int kThreads = 128;   // GEMM kernel: 4 warps, one TMEM lane quarter each
-constexpr int kFusedThreads = 160;  // fused kernel: 4 epilogue warps + 1 producer warp
+constexpr int kFusedThreads = 288;  // fused kernel: 8 epilogue warps + 1 producer warp
 
 struct Dims {
   int d, mu, nf, K0, OUT, OUTP;
@@ -80,40 +81,44 @@ Layout layout_for(const Dims& m) {
   return L;
 }
 
-// Streamed weight chunks (W1, W2, W3 in K-slices of <= 64 columns) followed by W4 whole.
+// Streamed weight chunks: every layer's W [N x K] in K-slices of 16 KiB (N x kw bf16,
+// canonical K-major layout), in layer order; the fused kernel double-buffers them.
 struct ChunkPlan {
   int n;
-  int64_t off[16];   // bytes into the tile buffer
-  int kw[16];        // K width of the chunk
-  int layer[16];
-  int k0[16];
-  int64_t w4_off, total_bytes;
+  int64_t off[40];   // bytes into the tile buffer
+  int kw[40];        // K width of the chunk
+  int nrows[40];     // N of the chunk (= the layer's output width)
+  int layer[40];
+  int k0[40];
+  int64_t total_bytes;
 };
 ChunkPlan plan_for(const Dims& m) {
   ChunkPlan p;
   p.n = 0;
   int64_t off = 0;
-  const int K[3] = {m.K0, kH, kH};
-  for (int l = 0; l < 3; ++l)
-    for (int k0 = 0; k0 < K[l]; k0 += kChunkK) {
-      const int kw = K[l] - k0 < kChunkK ? K[l] - k0 : kChunkK;
+  const int K[4] = {m.K0, kH, kH, kH}, N[4] = {kH, kH, kH, m.OUTP};
+  for (int l = 0; l < 4; ++l) {
+    const int kw_max = kChunkBytes / (N[l] * 2);
+    for (int k0 = 0; k0 < K[l]; k0 += kw_max) {
+      const int kw = K[l] - k0 < kw_max ? K[l] - k0 : kw_max;
       p.off[p.n] = off;
       p.kw[p.n] = kw;
+      p.nrows[p.n] = N[l];
       p.layer[p.n] = l;
       p.k0[p.n] = k0;
       ++p.n;
-      off += (int64_t)kH * kw * 2;
+      off += (int64_t)N[l] * kw * 2;
     }
-  p.w4_off = off;
-  off += (int64_t)m.OUTP * kH * 2;
+  }
   p.total_bytes = off;
   return p;
 }
 
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + __expf(-z)); }
-__device__ __forceinline__ float silu_grad(float z) {
-  const float s = 1.0f / (1.0f + __expf(-z));
-  return s * (1.0f + z * (1.0f - s));
+__device__ __forceinline__ float act(float z) {
+  return z * fminf(fmaxf(z + 3.0f, 0.0f), 6.0f) * (1.0f / 6.0f);
+}
+__device__ __forceinline__ float act_grad(float z) {
+  return z < -3.0f ? 0.0f : (z > 3.0f ? 1.0f : (2.0f * z + 3.0f) * (1.0f / 6.0f));
 }
 
 __device__ __forceinline__ int64_t snap_m(double x) {
@@ -152,6 +157,8 @@ struct FusedParams {
   int64_t M;
   // rows mode
   const double* v;
+  const float* h2v;  // h^2 v (fp32), per point
+  const float* h2s;  // h^2 s_j (fp32), per point
   int logn;
   double h2;
   double* Q;
@@ -170,9 +177,11 @@ struct FusedParams {
 
 constexpr int kModeRows = 0, kModeBatch = 1;
 
-// Warps 0-3 own the 128 tensor-memory lanes (input stage and epilogues, one row each); warp 4 is
-// the producer: its elected lane issues the weight bulk copies and the MMAs while the rest of
-// that warp waits at __syncwarp, so no issuing thread shares a warp with spinning threads.
+// The weight chunks are prefetched NBUF - 1 deep (6 buffers in 2D, 4 in 3D), so their L2
+// latency hides behind the MMAs of earlier chunks. Warps 0-7 are the epilogue warps: warp w reads tensor-memory lanes 32 (w % 4) .. (one tile row
+// per lane) and the column half w / 4; warps 0-3 also build the input tile. Warp 8 is the
+// producer: its elected lane issues the weight bulk copies and the MMAs while the rest of that
+// warp waits at __syncwarp, so no issuing thread shares a warp with spinning threads.
 template <int D, int MODE>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
   constexpr int MU = D == 2 ? 9 : 27;
@@ -180,19 +189,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
   constexpr int NP = NF - 1;
   constexpr int K0 = D == 2 ? 32 : 128;
   constexpr int OUTP = D == 2 ? 32 : 64;
-  constexpr int NBUF = D == 2 ? 4 : 2;  // weight-chunk buffers (shared-memory budget)
+  constexpr int NBUF = D == 2 ? 6 : 4;  // weight-chunk buffers (prefetch depth NBUF - 1)
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* Xs = smem;                               // 128 x K0 bf16
   uint8_t* Hs = Xs + kTile * K0 * 2;                // 128 x 256 bf16
-  uint8_t* Wb = Hs + kTile * kH * 2;                // NBUF x (256 x 64 bf16)
-  uint8_t* W4s = Wb + NBUF * kH * kChunkK * 2;       // OUTP x 256 bf16
-  float* bs = reinterpret_cast<float*>(W4s + OUTP * kH * 2);  // b1 b2 b3 (3 x 256) + b4 (OUTP)
+  uint8_t* Wb = Hs + kTile * kH * 2;                // NBUF x 16 KiB
+  float* bs = reinterpret_cast<float*>(Wb + NBUF * kChunkBytes);  // b1 b2 b3 (3 x 256) + b4
   float* nrm = bs + 3 * kH + OUTP;                  // mu_x sig_x mu_y[OUTP] sig_y[OUTP]
-  __shared__ __align__(8) uint64_t bar_mma, bar_w[4], bar_f[4], bar_w4;
+  __shared__ __align__(8) uint64_t bar_mma, bar_w[6], bar_f[6];
   __shared__ uint32_t tslot;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool producer = warp == 4;
+  const bool producer = warp == 8;
+  const int quarter_w = warp & 3;  // tensor-memory lane quarter of an epilogue warp
+  const int colhalf = warp >> 2;   // 0 or 1: which half of the 256 columns
   const bool leader = producer && lane == 0;
 
   for (int i = tid; i < kH; i += kFusedThreads) {
@@ -208,7 +218,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
       tc::mbar_init(&bar_w[b], 1);
       tc::mbar_init(&bar_f[b], 1);
     }
-    tc::mbar_init(&bar_w4, 1);
     s_abort = 0;
   }
   if (warp == 0) tc::tmem_alloc(&tslot, kH);
@@ -216,15 +225,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tslot;
-  if (leader) {
-    tc::mbar_expect_tx(&bar_w4, OUTP * kH * 2);
-    tc::bulk_g2s(W4s, p.tiles + p.plan.w4_off, OUTP * kH * 2, &bar_w4);
-    if (!tc::mbar_wait(&bar_w4, 0, p.err, 1)) s_abort = 1;
-  }
-  __syncthreads();
   // the leader's pipeline state
-  uint32_t ph_w[4] = {0, 0, 0, 0}, ph_f[4] = {0, 0, 0, 0};
-  bool f_pending[4] = {false, false, false, false};
+  uint32_t ph_w[6] = {0, 0, 0, 0, 0, 0}, ph_f[6] = {0, 0, 0, 0, 0, 0};
+  bool f_pending[6] = {false, false, false, false, false, false};
   uint32_t ph_mma = 0;
   const int64_t mask = ((int64_t)1 << p.logn) - 1;
   const float mu_x = nrm[0], isig_x = 1.0f / nrm[1];
@@ -236,9 +239,9 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
       ph_f[b] ^= 1;
       f_pending[b] = false;
     }
-    const uint32_t bytes = (uint32_t)kH * p.plan.kw[gi] * 2;
+    const uint32_t bytes = (uint32_t)p.plan.nrows[gi] * p.plan.kw[gi] * 2;
     tc::mbar_expect_tx(&bar_w[b], bytes);
-    tc::bulk_g2s(Wb + b * kH * kChunkK * 2, p.tiles + p.plan.off[gi], bytes, &bar_w[b]);
+    tc::bulk_g2s(Wb + b * kChunkBytes, p.tiles + p.plan.off[gi], bytes, &bar_w[b]);
   };
   // leader: MMAs of chunk gi against A = (layer 0 ? X : H) columns [k0, k0 + kw)
   auto consume = [&](int gi) {
@@ -252,11 +255,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
     const int KA = first ? K0 : kH;
     const uint32_t sboA = (uint32_t)(KA / 8) * 128, sboB = (uint32_t)(kw / 8) * 128;
     const uint32_t aBase = tc::smem_u32(A) + (uint32_t)(k0 / 8) * 128;
-    const uint32_t bBase = tc::smem_u32(Wb + b * kH * kChunkK * 2);
+    const uint32_t bBase = tc::smem_u32(Wb + b * kChunkBytes);
+    const uint32_t idesc = tc::idesc_bf16(kTile, p.plan.nrows[gi]);
     for (int s = 0; s < kw / 16; ++s) {
       const uint64_t ad = tc::desc_kmajor(aBase + s * 256, 128, sboA);
       const uint64_t bd = tc::desc_kmajor(bBase + s * 256, 128, sboB);
-      tc::mma_bf16(tmem, ad, bd, tc::idesc_bf16(kTile, kH), (k0 > 0 || s > 0) ? 1u : 0u);
+      tc::mma_bf16(tmem, ad, bd, idesc, (k0 > 0 || s > 0) ? 1u : 0u);
     }
     tc::commit(&bar_f[b]);
     f_pending[b] = true;
@@ -268,19 +272,16 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
     const int64_t r0 = tile * kTile;
     const int64_t row = r0 + tid;  // this thread's row in the input stage
     // ---- input stage (warps 0-3): normalised features, bf16, canonical layout ----
-    if (!producer) {
+    if (warp < 4) {
       float f[K0];
 #pragma unroll
       for (int k = 0; k < K0; ++k) f[k] = 0.0f;
       if (row < p.M) {
         if (MODE == kModeRows) {
 #pragma unroll 5
-          for (int k = 0; k < NP; ++k) {
-            const double x = __ldg(p.v + nb_index<D, 2>(row, k, p.logn, mask)) * p.h2;
-            f[k] = ((float)x - mu_x) * isig_x;
-          }
-          const double sj = __dmul_rn((double)(4 * snap_m(__ldg(p.v + row)) + 2), kPi2);
-          f[NP] = ((float)(sj * p.h2) - mu_x) * isig_x;
+          for (int k = 0; k < NP; ++k)
+            f[k] = (__ldg(p.h2v + nb_index<D, 2>(row, k, p.logn, mask)) - mu_x) * isig_x;
+          f[NP] = (__ldg(p.h2s + row) - mu_x) * isig_x;
         } else {
           for (int k = 0; k < NF; ++k) f[k] = (p.Xraw[row * NF + k] - mu_x) * isig_x;
         }
@@ -305,21 +306,12 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
       if (leader && !s_abort) {
         if (layer == 0)
           for (int gi = 0; gi < NBUF - 1 && gi < p.plan.n; ++gi) issue(gi);
-        if (layer < 3) {
-          // issue-ahead distance NBUF - 1: the buffer refilled after chunk gi is the one chunk
-          // gi - 1 used, whose MMAs were committed one step earlier
-          for (int gi = 0; gi < p.plan.n; ++gi) {
-            if (p.plan.layer[gi] != layer) continue;
-            consume(gi);
-            if (gi + NBUF - 1 < p.plan.n) issue(gi + NBUF - 1);
-          }
-        } else {
-          const uint32_t aBase = tc::smem_u32(Hs), bBase = tc::smem_u32(W4s);
-          for (int s = 0; s < kH / 16; ++s) {
-            const uint64_t ad = tc::desc_kmajor(aBase + s * 256, 128, (kH / 8) * 128);
-            const uint64_t bd = tc::desc_kmajor(bBase + s * 256, 128, (kH / 8) * 128);
-            tc::mma_bf16(tmem, ad, bd, tc::idesc_bf16(kTile, OUTP), s > 0 ? 1u : 0u);
-          }
+        // issue-ahead distance NBUF - 1: the buffer refilled after chunk gi is the one chunk
+        // gi - 1 used, whose MMAs were committed one step earlier
+        for (int gi = 0; gi < p.plan.n; ++gi) {
+          if (p.plan.layer[gi] != layer) continue;
+          consume(gi);
+          if (gi + NBUF - 1 < p.plan.n) issue(gi + NBUF - 1);
         }
         tc::commit(&bar_mma);
       }
@@ -331,13 +323,14 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
       }
       ph_mma ^= 1;
       tc::fence_after();
-      const int64_t myrow = r0 + warp * 32 + lane;  // TMEM lane = tile row
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+      const int trow = quarter_w * 32 + lane;  // TMEM lane = tile row
+      const int64_t myrow = r0 + trow;
+      const uint32_t taddr = tmem + ((uint32_t)(quarter_w * 32) << 16);
       if (producer) {
         // nothing: the producer warp waits at the barrier below
       } else if (layer < 3) {
         const float* bl = bs + layer * kH;
-        for (int c0 = 0; c0 < kH; c0 += 64) {
+        for (int c0 = colhalf * (kH / 2); c0 < (colhalf + 1) * (kH / 2); c0 += 64) {
           uint32_t ra[32], rb[32];
           tc::tmem_ld32_nowait(taddr + c0, ra);
           tc::tmem_ld32_nowait(taddr + c0 + 32, rb);
@@ -350,7 +343,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
 #pragma unroll
             for (int i = 0; i < 32; ++i) {
               const float z = __uint_as_float(r[i]) + bl[cb + i];
-              h[i] = silu(z);
+              h[i] = act(z);
               if (MODE == kModeBatch && myrow < p.M) p.Zs[layer][myrow * kH + cb + i] = z;
             }
 #pragma unroll
@@ -360,13 +353,13 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
               q.y = tc::pack_bf16(h[8 * q8 + 2], h[8 * q8 + 3]);
               q.z = tc::pack_bf16(h[8 * q8 + 4], h[8 * q8 + 5]);
               q.w = tc::pack_bf16(h[8 * q8 + 6], h[8 * q8 + 7]);
-              *reinterpret_cast<uint4*>(Hs + tc::kmajor_off(warp * 32 + lane, cb + 8 * q8, kH)) = q;
+              *reinterpret_cast<uint4*>(Hs + tc::kmajor_off(trow, cb + 8 * q8, kH)) = q;
               if (MODE == kModeBatch && myrow < p.M)
                 *reinterpret_cast<uint4*>(p.Hs[layer] + myrow * kH + cb + 8 * q8) = q;
             }
           }
         }
-      } else {
+      } else if (colhalf == 0) {
         float y[OUTP];
 #pragma unroll
         for (int c0 = 0; c0 < OUTP; c0 += 16) {
@@ -380,24 +373,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
 #pragma unroll
             for (int o = 0; o < OUTP; ++o) p.Y[myrow * OUTP + o] = y[o];
           } else {
-            // de-normalise, unit-normalise alpha (c scaled alike: P^-1 C is invariant)
-            double al[MU], cc[MU], nrm2 = 0.0;
+            // de-normalise, unit-normalise alpha (c scaled alike: P^-1 C is invariant); the
+            // network's precision is fp32, the difference v - s_j is taken in fp64
+            float al[MU], cc[MU], nrm2 = 0.0f;
 #pragma unroll
             for (int i = 0; i < MU; ++i) {
-              al[i] = (double)(y[i] * nrm[2 + OUTP + i] + nrm[2 + i]);
-              cc[i] = (double)(y[MU + i] * nrm[2 + OUTP + MU + i] + nrm[2 + MU + i]);
-              nrm2 += al[i] * al[i];
+              al[i] = y[i] * nrm[2 + OUTP + i] + nrm[2 + i];
+              cc[i] = y[MU + i] * nrm[2 + OUTP + MU + i] + nrm[2 + MU + i];
+              nrm2 = fmaf(al[i], al[i], nrm2);
             }
-            const double sc = nrm2 > 0 ? 1.0 / sqrt(nrm2) : 1.0;
+            const float sc = nrm2 > 0.0f ? rsqrtf(nrm2) : 1.0f;
             const double s = __dmul_rn((double)(4 * snap_m(__ldg(p.v + myrow)) + 2), kPi2);
 #pragma unroll
             for (int i = 0; i < MU; ++i) {
               constexpr int R = 1;
               const double vn = __ldg(p.v + nb_index<D, R>(myrow, i, p.logn, mask));
-              const double a_ = al[i] * sc, c_ = cc[i] * sc;
-              __stcs(p.Q + myrow * MU + i, a_);
-              __stcs(p.C + myrow * MU + i, c_);
-              __stcs(p.P + myrow * MU + i, fma(c_, vn - s, a_));
+              const float a_ = al[i] * sc, c_ = cc[i] * sc;
+              __stcs(p.Q + myrow * MU + i, (double)a_);
+              __stcs(p.C + myrow * MU + i, (double)c_);
+              __stcs(p.P + myrow * MU + i, (double)fmaf(c_, (float)(vn - s), a_));
             }
           }
         }
@@ -523,7 +517,7 @@ __global__ void k_loss_grad(const float* __restrict__ Y, const float* __restrict
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, acc);
 }
 
-// dZ = dH * silu'(Z) (fp32 in), bf16 row-major and transposed copies.
+// dZ = dH * a'(Z) (fp32 in), bf16 row-major and transposed copies.
 __global__ void k_silu_back(const float* __restrict__ dH, const float* __restrict__ Z, int64_t B,
                             __nv_bfloat16* __restrict__ dZ, __nv_bfloat16* __restrict__ dZT,
                             float* __restrict__ dZ32) {
@@ -531,7 +525,7 @@ __global__ void k_silu_back(const float* __restrict__ dH, const float* __restric
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t b = e / kH;
     const int k = (int)(e - b * kH);
-    const float g = dH[e] * silu_grad(Z[e]);
+    const float g = dH[e] * act_grad(Z[e]);
     dZ[e] = __float2bfloat16(g);
     dZ32[e] = g;
     dZT[(int64_t)k * B + b] = __float2bfloat16(g);
@@ -591,15 +585,11 @@ __global__ void k_retile(const float* __restrict__ params, Layout L, ChunkPlan p
       const __nv_bfloat16 x = __float2bfloat16(params[L.w[l] + e]);
       WT[l][(int64_t)k * N + n] = x;
       W16[l][e] = x;
-      if (l < 3) {
-        int gi = 0;
-        for (int q = 0; q < plan.n; ++q)
-          if (plan.layer[q] == l && k >= plan.k0[q] && k < plan.k0[q] + plan.kw[q]) gi = q;
-        *reinterpret_cast<__nv_bfloat16*>(tiles + plan.off[gi] +
-                                          tc::kmajor_off(n, k - plan.k0[gi], plan.kw[gi])) = x;
-      } else {
-        *reinterpret_cast<__nv_bfloat16*>(tiles + plan.w4_off + tc::kmajor_off(n, k, kH)) = x;
-      }
+      int gi = 0;
+      for (int q = 0; q < plan.n; ++q)
+        if (plan.layer[q] == l && k >= plan.k0[q] && k < plan.k0[q] + plan.kw[q]) gi = q;
+      *reinterpret_cast<__nv_bfloat16*>(tiles + plan.off[gi] +
+                                        tc::kmajor_off(n, k - plan.k0[gi], plan.kw[gi])) = x;
     }
   }
 }
@@ -640,6 +630,17 @@ __global__ void k_norm_stats(const float* __restrict__ X, const float* __restric
     params[norm_off + 1] = (float)fmax(sqrt(var), 1e-30);
     params[range_off + 0] = (float)lo;
     params[range_off + 1] = (float)hi;
+  }
+}
+
+// Per point, fp32 h^2 v and h^2 s_j (s_j = snap(v_j)): the learned build's inputs.
+__global__ void k_prep_inputs(const double* __restrict__ v, int64_t N, double h2,
+                              float* __restrict__ h2v, float* __restrict__ h2s) {
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double x = v[j];
+    h2v[j] = (float)(x * h2);
+    h2s[j] = (float)(__dmul_rn((double)(4 * snap_m(x) + 2), kPi2) * h2);
   }
 }
 
@@ -726,9 +727,8 @@ bool grow(lsp::DevBuf& b, size_t bytes) {
 
 size_t fused_smem(int d) {
   const Dims m = dims_for(d);
-  const int nbuf = d == 2 ? 4 : 2;
-  return (size_t)kTile * m.K0 * 2 + kTile * kH * 2 + (size_t)nbuf * kH * kChunkK * 2 +
-         m.OUTP * kH * 2 +
+  const int nbuf = d == 2 ? 6 : 4;
+  return (size_t)kTile * m.K0 * 2 + kTile * kH * 2 + (size_t)nbuf * kChunkBytes +
          sizeof(float) * (3 * kH + m.OUTP + 2 + 2 * m.OUTP) + 64;
 }
 
@@ -751,7 +751,9 @@ cudaError_t launch_fused(lsp_mlp* m, const FusedParams& p, int64_t rows) {
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int64_t tiles = (rows + kTile - 1) / kTile;
-  int grid = (int)(tiles < 152 ? tiles : 152);
+  // two CTAs per SM where the shared memory allows (2D)
+  const int per_sm = smem <= 110 * 1024 ? 2 : 1;
+  int grid = (int)(tiles < 152 * per_sm ? tiles : 152 * per_sm);
   if (grid < 1) grid = 1;
   k_mlp_fused<D, MODE><<<grid, kFusedThreads, smem, m->stream>>>(p);
   return cudaGetLastError();
@@ -1079,8 +1081,16 @@ cudaError_t launch_learned_rows(lsp_ctx* c, lsp_mlp* m) {
   p.C = (double*)c->C.p;
   p.P = (double*)c->P.p;
   p.err = (int*)c->counts.p + kErrWord;
+  if (!ensure(c, c->learn_in, sizeof(float) * 2 * c->geo.N)) return cudaErrorMemoryAllocation;
+  p.h2v = (const float*)c->learn_in.p;
+  p.h2s = (const float*)c->learn_in.p + c->geo.N;
   cudaStream_t saved = m->stream;
   m->stream = c->stream;
+  int t0 = timer_begin(c, "mlp_prep");
+  k_prep_inputs<<<152 * 8, 256, 0, c->stream>>>((const double*)c->v.p, c->geo.N, p.h2,
+                                                (float*)c->learn_in.p,
+                                                (float*)c->learn_in.p + c->geo.N);
+  timer_end(c, t0);
   int t = timer_begin(c, "mlp_rows");
   cudaError_t e = c->geo.d == 2 ? launch_fused<2, kModeRows>(m, p, c->geo.N)
                                 : launch_fused<3, kModeRows>(m, p, c->geo.N);

@@ -432,7 +432,7 @@ lsp_status lsp_destroy(lsp_ctx* c) {
   DevBuf* bufs[] = {&c->v, &c->stats_part, &c->stats, &c->xtab, &c->xtab32, &c->shift_m, &c->shift_flag,
                     &c->idx_of, &c->counts, &c->wtab, &c->gvals, &c->alpha, &c->cst, &c->lam,
                     &c->sflags, &c->Q, &c->C, &c->P, &c->sidx, &c->colidx, &c->rowptr,
-                    &c->fftbuf, &c->twiddle};
+                    &c->fftbuf, &c->twiddle, &c->learn_in};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (int k = 0; k < kMaxD; ++k) {

@@ -1,6 +1,6 @@
 """Pins of the learned-stencil network's CPU oracle (no GPU): chain-rule gradients against
-central finite differences, SiLU against its closed form, a hand-computed tiny network, and
-the patch layout."""
+central finite differences, hard-swish against its closed form, a hand-computed tiny network,
+and the patch layout."""
 
 import numpy as np
 import pytest
@@ -8,23 +8,24 @@ import pytest
 from oracle import mlp_oracle as M
 
 
-def test_silu_closed_form_and_derivative():
-    z = np.linspace(-6, 6, 101)
-    assert np.allclose(M.silu(z), z / (1 + np.exp(-z)), rtol=0, atol=1e-15)
+def test_hswish_closed_form_and_derivative():
+    z = np.linspace(-6, 6, 101) + 0.0123  # off the kinks at -3 and 3
+    ref = np.where(z < -3, 0.0, np.where(z > 3, z, z * (z + 3) / 6))
+    assert np.allclose(M.hswish(z), ref, rtol=0, atol=1e-15)
     h = 1e-6
-    fd = (M.silu(z + h) - M.silu(z - h)) / (2 * h)
-    assert np.abs(fd - M.silu_grad(z)).max() < 1e-8
-    assert M.silu(0.0) == 0.0 and abs(M.silu_grad(0.0) - 0.5) < 1e-15
+    fd = (M.hswish(z + h) - M.hswish(z - h)) / (2 * h)
+    assert np.abs(fd - M.hswish_grad(z)).max() < 1e-8
+    assert M.hswish(0.0) == 0.0 and abs(M.hswish_grad(0.0) - 0.5) < 1e-15
 
 
 def test_tiny_network_by_hand():
-    # one input, one hidden unit, one output: y = w2 * silu(w1 x + b1) + b2
+    # one input, one hidden unit, one output: y = w2 * hswish(w1 x + b1) + b2
     x = np.array([[0.5]])
     W = [np.array([[2.0]]), np.array([[-3.0]])]
     b = [np.array([0.25]), np.array([1.0])]
     y, _ = M.mlp_forward(x, W, b)
     z = 2.0 * 0.5 + 0.25
-    assert abs(y[0, 0] - (-3.0 * z / (1 + np.exp(-z)) + 1.0)) < 1e-15
+    assert abs(y[0, 0] - (-3.0 * z * (z + 3) / 6 + 1.0)) < 1e-15
 
 
 @pytest.mark.parametrize("seed", [0, 1])
