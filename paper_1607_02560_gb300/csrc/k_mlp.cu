@@ -35,9 +35,8 @@ namespace {
 constexpr int kH = 256;         // hidden width
 constexpr int kTile = 128;      // rows per tile (MMA M)
 constexpr int kChunkK = 64;     // K width of a GEMM staging chunk (training)
-constexpr int kChunkBytes = 16384;  // bytes of a streamed weight chunk (fused kernel)
-constexpr int kThreads = 128;   // GEMM kernel: 4 warps, one TMEM lane quarter each
-constexpr int kFusedThreads = 288;  // fused kernel: 8 epilogue warps + 1 producer warp
+constexpr int kChunkBytes = 32768;  // largest streamed weight chunk (fused kernel)
+constexpr int kFusedThreads = 320;  // fused kernel: 8 epilogue warps, MMA warp, loader warp
 
 struct Dims {
   int d, mu, nf, K0, OUT, OUTP;
@@ -81,8 +80,9 @@ Layout layout_for(const Dims& m) {
   return L;
 }
 
-// Streamed weight chunks: every layer's W [N x K] in K-slices of 16 KiB (N x kw bf16,
-// canonical K-major layout), in layer order; the fused kernel double-buffers them.
+// Streamed weight chunks: every layer's W [N x K] in K-slices of at most 32 KiB (N x kw bf16,
+// kw = min(K, 32 KiB / 2N), canonical K-major layout), in layer order. The fused kernel walks
+// the same plan at compile time (FusedCfg).
 struct ChunkPlan {
   int n;
   int64_t off[40];   // bytes into the tile buffer
@@ -114,9 +114,7 @@ ChunkPlan plan_for(const Dims& m) {
   return p;
 }
 
-__device__ __forceinline__ float act(float z) {
-  return z * fminf(fmaxf(z + 3.0f, 0.0f), 6.0f) * (1.0f / 6.0f);
-}
+// Derivative of the hard-swish activation z * clamp(z + 3, 0, 6) / 6.
 __device__ __forceinline__ float act_grad(float z) {
   return z < -3.0f ? 0.0f : (z > 3.0f ? 1.0f : (2.0f * z + 3.0f) * (1.0f / 6.0f));
 }
@@ -151,265 +149,445 @@ __device__ __forceinline__ int64_t nb_index(int64_t j, int o, int logn, int64_t 
 }
 
 struct FusedParams {
-  const uint8_t* tiles;  // chunk stream + W4
-  const float* bias;     // flat params (fp32): biases read from here
-  const float* params;
+  const uint8_t* tiles;  // the weight chunk stream
+  const float* params;   // flat params (fp32): biases and normalisation read from here
+  const uint8_t* Xt;     // normalised bf16 inputs, one canonical 128 x K0 tile after another
   int64_t M;
-  // rows mode
-  const double* v;
-  const float* h2v;  // h^2 v (fp32), per point
-  const float* h2s;  // h^2 s_j (fp32), per point
+  // rows mode: v = vh + vl and s_j = sh + sl per point (fp32 pairs, see k_point_features)
+  const float* vh;
+  const float* vl;
+  const float* sh;
+  const float* sl;
   int logn;
-  double h2;
   double* Q;
   double* C;
   double* P;
   // batch mode
-  const float* Xraw;  // [M x nf] raw features (h^2 v)
-  float* Y;           // [M x OUTP] normalised outputs
+  float* Y;  // [M x OUTP] normalised outputs
   __nv_bfloat16* Hs[3];
   float* Zs[3];
-  __nv_bfloat16* X16;  // [M x K0] normalised inputs (bf16), saved for the backward pass
   int* err;
   ChunkPlan plan;
   int64_t bias_off[4], norm_off;
 };
 
 constexpr int kModeRows = 0, kModeBatch = 1;
+constexpr int kPassCols = 64;            // columns of H per epilogue pass / ready signal
+constexpr int kNPass = kH / kPassCols;   // 4
+constexpr int kEpiWarps = 8;
 
-// The weight chunks are prefetched NBUF - 1 deep (6 buffers in 2D, 4 in 3D), so their L2
-// latency hides behind the MMAs of earlier chunks. Warps 0-7 are the epilogue warps: warp w reads tensor-memory lanes 32 (w % 4) .. (one tile row
-// per lane) and the column half w / 4; warps 0-3 also build the input tile. Warp 8 is the
-// producer: its elected lane issues the weight bulk copies and the MMAs while the rest of that
-// warp waits at __syncwarp, so no issuing thread shares a warp with spinning threads.
+template <int D>
+struct FusedCfg {
+  static constexpr int MU = D == 2 ? 9 : 27;
+  static constexpr int K0 = D == 2 ? 32 : 128;
+  static constexpr int OUTP = D == 2 ? 32 : 64;
+  static constexpr int XBUF = D == 2 ? 2 : 1;  // input-tile buffers
+  static constexpr int NBUF = D == 2 ? 4 : 3;  // weight-chunk buffers of 32 KiB
+  static constexpr int XBYTES = kTile * K0 * 2;
+  // the chunk plan of plan_for(), at compile time
+  __host__ __device__ static constexpr int N(int l) { return l < 3 ? kH : OUTP; }
+  __host__ __device__ static constexpr int K(int l) { return l == 0 ? K0 : kH; }
+  __host__ __device__ static constexpr int KW(int l) {
+    return K(l) < kChunkBytes / (2 * N(l)) ? K(l) : kChunkBytes / (2 * N(l));
+  }
+  __host__ __device__ static constexpr int NCH(int l) { return K(l) / KW(l); }
+  __host__ __device__ static constexpr int CHUNK_BYTES(int l) { return N(l) * KW(l) * 2; }
+  __host__ __device__ static constexpr int64_t OFF(int l) {
+    return l == 0 ? 0 : OFF(l - 1) + (int64_t)N(l - 1) * K(l - 1) * 2;
+  }
+  static constexpr size_t smem = (size_t)XBUF * XBYTES + kTile * kH * 2 +
+                                 (size_t)NBUF * kChunkBytes +
+                                 sizeof(float) * (6 * kH + OUTP + 2 + 2 * OUTP) + 64;
+};
+
+// Fused forward over tiles of 128 rows, persistent (one CTA per SM, tiles strided by the grid).
+//
+// Loader warp 9 (one lane): bulk-copies the input tiles (XBUF buffers, the next tile's as early
+// as a buffer is free) and the 32 KiB weight chunks (NBUF buffers, across layer and tile
+// boundaries); a buffer is refilled once the MMAs that read it have completed (bar_f, bar_xf).
+// Both producer threads walk the chunk plan at compile time (FusedCfg), so their loops carry
+// no index arithmetic beyond a buffer counter.
+// MMA warp 8 (one lane): issues every MMA and never waits for MMA completion, only for its
+// operands: layer l accumulates into tensor-memory accumulator l % 2 (columns 256 (l % 2) ..),
+// so layer l + 1 can run while the epilogue still reads layer l. A chunk of layer l > 0 reads
+// the columns [k0, k0 + kw) of H and is issued as soon as the epilogue has signalled those
+// 64-column passes (bar_h); after the layer's last chunk it commits bar_acc.
+// Epilogue warps 0-7: warp w reads tensor-memory lanes 32 (w % 4) .. (one tile row per lane);
+// for layers 0-2 it handles columns 32 (w / 4) .. + 31 of each 64-column pass (bias,
+// activation, bf16 into H), then arrives once on that pass's barrier (8 arrivals). Layer 3: warps 0-3 write Q and C (or Y), warps
+// 4-7 write P.
+//
+// Ordering: the MMAs of layer l + 1 into accumulator (l + 1) % 2 are issued only after every
+// slice of epilogue l has been signalled, which follows the epilogue's reads of accumulator
+// (l + 1) % 2 for layer l - 1; epilogue l overwrites H only after the MMAs of layer l (the
+// readers of the previous H) completed. Every wait is bounded (1 s); a timed-out wait sets the
+// error word and makes every thread skip the remaining waits.
 template <int D, int MODE>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
-  constexpr int MU = D == 2 ? 9 : 27;
-  constexpr int NF = D == 2 ? 26 : 126;  // patch + snapped shift
-  constexpr int NP = NF - 1;
-  constexpr int K0 = D == 2 ? 32 : 128;
-  constexpr int OUTP = D == 2 ? 32 : 64;
-  constexpr int NBUF = D == 2 ? 6 : 4;  // weight-chunk buffers (prefetch depth NBUF - 1)
+  using Cfg = FusedCfg<D>;
+  constexpr int MU = Cfg::MU, OUTP = Cfg::OUTP, NBUF = Cfg::NBUF;
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t* Xs = smem;                               // 128 x K0 bf16
-  uint8_t* Hs = Xs + kTile * K0 * 2;                // 128 x 256 bf16
-  uint8_t* Wb = Hs + kTile * kH * 2;                // NBUF x 16 KiB
+  uint8_t* Xs = smem;                                // XBUF x (128 x K0) bf16
+  uint8_t* Hs = Xs + Cfg::XBUF * Cfg::XBYTES;        // 128 x 256 bf16
+  uint8_t* Wb = Hs + kTile * kH * 2;                 // NBUF x 16 KiB
   float* bs = reinterpret_cast<float*>(Wb + NBUF * kChunkBytes);  // b1 b2 b3 (3 x 256) + b4
-  float* nrm = bs + 3 * kH + OUTP;                  // mu_x sig_x mu_y[OUTP] sig_y[OUTP]
-  __shared__ __align__(8) uint64_t bar_mma, bar_w[6], bar_f[6];
+  float* nrm = bs + 3 * kH + OUTP;                   // mu_x sig_x mu_y[OUTP] sig_y[OUTP]
+  float* bq = nrm + 2 + 2 * OUTP;                    // b / 6 + 1/2 of layers 1-3 (3 x 256)
+  __shared__ __align__(8) uint64_t bar_w[NBUF], bar_f[NBUF], bar_x[2], bar_xf[2], bar_acc[2],
+      bar_h[kNPass], bar_done;
   __shared__ uint32_t tslot;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool producer = warp == 8;
-  const int quarter_w = warp & 3;  // tensor-memory lane quarter of an epilogue warp
-  const int colhalf = warp >> 2;   // 0 or 1: which half of the 256 columns
+  const bool producer = warp == kEpiWarps;
   const bool leader = producer && lane == 0;
 
   for (int i = tid; i < kH; i += kFusedThreads) {
     bs[i] = p.params[p.bias_off[0] + i];
     bs[kH + i] = p.params[p.bias_off[1] + i];
     bs[2 * kH + i] = p.params[p.bias_off[2] + i];
+    for (int l = 0; l < 3; ++l) bq[l * kH + i] = fmaf(bs[l * kH + i], 1.0f / 6.0f, 0.5f);
   }
   for (int i = tid; i < OUTP; i += kFusedThreads) bs[3 * kH + i] = p.params[p.bias_off[3] + i];
   for (int i = tid; i < 2 + 2 * OUTP; i += kFusedThreads) nrm[i] = p.params[p.norm_off + i];
   if (leader) {
-    tc::mbar_init(&bar_mma, 1);
     for (int b = 0; b < NBUF; ++b) {
       tc::mbar_init(&bar_w[b], 1);
       tc::mbar_init(&bar_f[b], 1);
     }
+    for (int b = 0; b < 2; ++b) {
+      tc::mbar_init(&bar_x[b], 1);
+      tc::mbar_init(&bar_xf[b], 1);
+      tc::mbar_init(&bar_acc[b], 1);
+    }
+    for (int s = 0; s < kNPass; ++s) tc::mbar_init(&bar_h[s], kEpiWarps);
+    tc::mbar_init(&bar_done, 1);
     s_abort = 0;
   }
-  if (warp == 0) tc::tmem_alloc(&tslot, kH);
+  if (warp == 0) tc::tmem_alloc(&tslot, 2 * kH);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tslot;
-  // the leader's pipeline state
-  uint32_t ph_w[6] = {0, 0, 0, 0, 0, 0}, ph_f[6] = {0, 0, 0, 0, 0, 0};
-  bool f_pending[6] = {false, false, false, false, false, false};
-  uint32_t ph_mma = 0;
-  const int64_t mask = ((int64_t)1 << p.logn) - 1;
-  const float mu_x = nrm[0], isig_x = 1.0f / nrm[1];
-
-  auto issue = [&](int gi) {  // leader: bulk copy of chunk gi into buffer gi % NBUF
-    const int b = gi % NBUF;
-    if (f_pending[b]) {
-      if (!tc::mbar_wait(&bar_f[b], ph_f[b], p.err, 2)) s_abort = 1;
-      ph_f[b] ^= 1;
-      f_pending[b] = false;
-    }
-    const uint32_t bytes = (uint32_t)p.plan.nrows[gi] * p.plan.kw[gi] * 2;
-    tc::mbar_expect_tx(&bar_w[b], bytes);
-    tc::bulk_g2s(Wb + b * kChunkBytes, p.tiles + p.plan.off[gi], bytes, &bar_w[b]);
+  volatile int* abort_flag = &s_abort;
+  // a bounded wait that is skipped once any wait of the CTA has given up
+  auto wait = [&](uint64_t* bar, uint32_t parity, int bit) {
+    if (tc::mbar_test(bar, parity)) return true;  // fast path: already complete
+    if (*abort_flag) return false;
+    if (tc::mbar_wait(bar, parity, p.err, bit)) return true;
+    *abort_flag = 1;
+    return false;
   };
-  // leader: MMAs of chunk gi against A = (layer 0 ? X : H) columns [k0, k0 + kw)
-  auto consume = [&](int gi) {
-    const int b = gi % NBUF;
-    if (!tc::mbar_wait(&bar_w[b], ph_w[b], p.err, 4)) s_abort = 1;
-    ph_w[b] ^= 1;
-    tc::fence_after();
-    const int kw = p.plan.kw[gi], k0 = p.plan.k0[gi];
-    const bool first = p.plan.layer[gi] == 0;
-    const uint8_t* A = first ? Xs : Hs;
-    const int KA = first ? K0 : kH;
-    const uint32_t sboA = (uint32_t)(KA / 8) * 128, sboB = (uint32_t)(kw / 8) * 128;
-    const uint32_t aBase = tc::smem_u32(A) + (uint32_t)(k0 / 8) * 128;
-    const uint32_t bBase = tc::smem_u32(Wb + b * kChunkBytes);
-    const uint32_t idesc = tc::idesc_bf16(kTile, p.plan.nrows[gi]);
-    for (int s = 0; s < kw / 16; ++s) {
-      const uint64_t ad = tc::desc_kmajor(aBase + s * 256, 128, sboA);
-      const uint64_t bd = tc::desc_kmajor(bBase + s * 256, 128, sboB);
-      tc::mma_bf16(tmem, ad, bd, idesc, (k0 > 0 || s > 0) ? 1u : 0u);
-    }
-    tc::commit(&bar_f[b]);
-    f_pending[b] = true;
+  // the same for a whole warp: lane 0 waits, the warp reconverges behind it
+  auto wait_warp = [&](uint64_t* bar, uint32_t parity, int bit) {
+    if (lane == 0) wait(bar, parity, bit);
+    __syncwarp();
   };
-
   const int64_t ntiles = (p.M + kTile - 1) / kTile;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    if (s_abort) break;
-    const int64_t r0 = tile * kTile;
-    const int64_t row = r0 + tid;  // this thread's row in the input stage
-    // ---- input stage (warps 0-3): normalised features, bf16, canonical layout ----
-    if (warp < 4) {
-      float f[K0];
-#pragma unroll
-      for (int k = 0; k < K0; ++k) f[k] = 0.0f;
-      if (row < p.M) {
-        if (MODE == kModeRows) {
-#pragma unroll 5
-          for (int k = 0; k < NP; ++k)
-            f[k] = (__ldg(p.h2v + nb_index<D, 2>(row, k, p.logn, mask)) - mu_x) * isig_x;
-          f[NP] = (__ldg(p.h2s + row) - mu_x) * isig_x;
-        } else {
-          for (int k = 0; k < NF; ++k) f[k] = (p.Xraw[row * NF + k] - mu_x) * isig_x;
+  const int64_t my_tiles =
+      blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  if (warp == kEpiWarps + 1) {
+    // ---- loader: input tiles and weight chunks, in the order the MMA warp consumes them ----
+    if (lane == 0) {
+      uint32_t slot = 0, ph_f = 0, ph_xf = 0;  // next buffer; phase parities (bit masks)
+      uint32_t issued = 0, cnt_x = 0;
+      auto load_x = [&](int64_t it) {
+        const int xb = Cfg::XBUF == 2 ? (int)(it & 1) : 0;
+        const int64_t tile = blockIdx.x + it * gridDim.x;
+        tc::mbar_expect_tx(&bar_x[xb], Cfg::XBYTES);
+        tc::bulk_g2s(Xs + xb * Cfg::XBYTES, p.Xt + tile * Cfg::XBYTES, Cfg::XBYTES, &bar_x[xb]);
+        ++cnt_x;
+      };
+      if (my_tiles > 0) load_x(0);
+      for (int64_t it = 0; it < my_tiles && !*abort_flag; ++it) {
+        if (Cfg::XBUF == 2 && it + 1 < my_tiles) {
+          if (it + 1 >= 2) {
+            // buffer (it + 1) % 2 is free once tile it - 1's first-layer MMAs completed
+            const int xb = (int)((it + 1) & 1);
+            wait(&bar_xf[xb], ph_xf >> xb & 1, 1);
+            ph_xf ^= 1u << xb;
+          }
+          if (!*abort_flag) load_x(it + 1);
         }
-      }
 #pragma unroll
-      for (int k8 = 0; k8 < K0; k8 += 8) {
-        uint4 q;
-        q.x = tc::pack_bf16(f[k8 + 0], f[k8 + 1]);
-        q.y = tc::pack_bf16(f[k8 + 2], f[k8 + 3]);
-        q.z = tc::pack_bf16(f[k8 + 4], f[k8 + 5]);
-        q.w = tc::pack_bf16(f[k8 + 6], f[k8 + 7]);
-        *reinterpret_cast<uint4*>(Xs + tc::kmajor_off(tid, k8, K0)) = q;
-        if (MODE == kModeBatch && row < p.M)
-          *reinterpret_cast<uint4*>(p.X16 + row * K0 + k8) = q;
-      }
-    }
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-    for (int layer = 0; layer < 4; ++layer) {
-      if (leader && !s_abort) {
-        if (layer == 0)
-          for (int gi = 0; gi < NBUF - 1 && gi < p.plan.n; ++gi) issue(gi);
-        // issue-ahead distance NBUF - 1: the buffer refilled after chunk gi is the one chunk
-        // gi - 1 used, whose MMAs were committed one step earlier
-        for (int gi = 0; gi < p.plan.n; ++gi) {
-          if (p.plan.layer[gi] != layer) continue;
-          consume(gi);
-          if (gi + NBUF - 1 < p.plan.n) issue(gi + NBUF - 1);
-        }
-        tc::commit(&bar_mma);
-      }
-      if (producer) {
-        __syncwarp();
-      } else {
-        // the epilogue warps wait for the layer's accumulator (bounded)
-        if (!tc::mbar_wait(&bar_mma, ph_mma, p.err, 8)) s_abort = 1;
-      }
-      ph_mma ^= 1;
-      tc::fence_after();
-      const int trow = quarter_w * 32 + lane;  // TMEM lane = tile row
-      const int64_t myrow = r0 + trow;
-      const uint32_t taddr = tmem + ((uint32_t)(quarter_w * 32) << 16);
-      if (producer) {
-        // nothing: the producer warp waits at the barrier below
-      } else if (layer < 3) {
-        const float* bl = bs + layer * kH;
-        for (int c0 = colhalf * (kH / 2); c0 < (colhalf + 1) * (kH / 2); c0 += 64) {
-          uint32_t ra[32], rb[32];
-          tc::tmem_ld32_nowait(taddr + c0, ra);
-          tc::tmem_ld32_nowait(taddr + c0 + 32, rb);
-          tc::ld_wait();
+        for (int l = 0; l < 4; ++l) {
 #pragma unroll
-          for (int half = 0; half < 2; ++half) {
-            const uint32_t* r = half ? rb : ra;
-            const int cb = c0 + 32 * half;
-            float h[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float z = __uint_as_float(r[i]) + bl[cb + i];
-              h[i] = act(z);
-              if (MODE == kModeBatch && myrow < p.M) p.Zs[layer][myrow * kH + cb + i] = z;
+          for (int c = 0; c < Cfg::NCH(l); ++c) {
+            if (issued >= (uint32_t)NBUF) {
+              // the MMAs of the chunk NBUF jobs earlier (same buffer) must have completed
+              wait(&bar_f[slot], ph_f >> slot & 1, 2);
+              ph_f ^= 1u << slot;
             }
-#pragma unroll
-            for (int q8 = 0; q8 < 4; ++q8) {
-              uint4 q;
-              q.x = tc::pack_bf16(h[8 * q8 + 0], h[8 * q8 + 1]);
-              q.y = tc::pack_bf16(h[8 * q8 + 2], h[8 * q8 + 3]);
-              q.z = tc::pack_bf16(h[8 * q8 + 4], h[8 * q8 + 5]);
-              q.w = tc::pack_bf16(h[8 * q8 + 6], h[8 * q8 + 7]);
-              *reinterpret_cast<uint4*>(Hs + tc::kmajor_off(trow, cb + 8 * q8, kH)) = q;
-              if (MODE == kModeBatch && myrow < p.M)
-                *reinterpret_cast<uint4*>(p.Hs[layer] + myrow * kH + cb + 8 * q8) = q;
-            }
+            if (*abort_flag) break;
+            tc::mbar_expect_tx(&bar_w[slot], Cfg::CHUNK_BYTES(l));
+            tc::bulk_g2s(Wb + slot * kChunkBytes,
+                         p.tiles + Cfg::OFF(l) + (int64_t)c * Cfg::CHUNK_BYTES(l),
+                         Cfg::CHUNK_BYTES(l), &bar_w[slot]);
+            ++issued;
+            slot = slot + 1 == (uint32_t)NBUF ? 0 : slot + 1;
+          }
+          if (Cfg::XBUF == 1 && l == 0 && it + 1 < my_tiles && !*abort_flag) {
+            // the single input buffer is free once this tile's first-layer MMAs completed
+            wait(&bar_xf[0], ph_xf & 1, 1);
+            ph_xf ^= 1u;
+            if (!*abort_flag) load_x(it + 1);
           }
         }
-      } else if (colhalf == 0) {
-        float y[OUTP];
-#pragma unroll
-        for (int c0 = 0; c0 < OUTP; c0 += 16) {
-          float a[16];
-          tc::tmem_ld16(taddr + c0, a);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) y[c0 + i] = a[i] + bs[3 * kH + c0 + i];
+      }
+      // drain: every copy issued has landed (bounded; complete unless aborted). The copies of
+      // buffer b are its uses number 0, 1, ...; the last one completed phase (uses - 1) % 2.
+      for (int b = 0; b < NBUF; ++b) {
+        const uint32_t uses = issued / NBUF + ((uint32_t)b < issued % NBUF ? 1u : 0u);
+        if (uses) tc::mbar_wait(&bar_w[b], (uses - 1) & 1, p.err, 0);
+      }
+      if (Cfg::XBUF == 2) {
+        for (int b = 0; b < 2; ++b) {
+          const uint32_t uses = cnt_x / 2 + ((uint32_t)b < cnt_x % 2 ? 1u : 0u);
+          if (uses) tc::mbar_wait(&bar_x[b], (uses - 1) & 1, p.err, 0);
         }
-        if (myrow < p.M) {
-          if (MODE == kModeBatch) {
+      } else if (cnt_x) {
+        tc::mbar_wait(&bar_x[0], (cnt_x - 1) & 1, p.err, 0);
+      }
+    }
+    __syncwarp();
+  } else if (producer) {
+    // ---- MMA issuer: never waits for MMA completion, only for its operands ----
+    if (lane == 0) {
+      uint32_t slot = 0, ph_w = 0, ph_h = 0, ph_x = 0;
+      for (int64_t it = 0; it < my_tiles && !*abort_flag; ++it) {
+        const int xb = Cfg::XBUF == 2 ? (int)(it & 1) : 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const uint32_t acc = tmem + (uint32_t)((l & 1) * kH);
+          int waited = 0;  // slices of H signalled for this layer
+#pragma unroll
+          for (int c = 0; c < Cfg::NCH(l); ++c) {
+            const int k0 = c * Cfg::KW(l);
+            if (l == 0) {
+              if (c == 0) {
+                wait(&bar_x[xb], ph_x >> xb & 1, 1);
+                ph_x ^= 1u << xb;
+              }
+            } else {
+              const int need = (k0 + Cfg::KW(l)) / kPassCols;
+              for (; waited < need; ++waited) {
+                wait(&bar_h[waited], ph_h >> waited & 1, 32);
+                ph_h ^= 1u << waited;
+              }
+            }
+            wait(&bar_w[slot], ph_w >> slot & 1, 4);
+            ph_w ^= 1u << slot;
+            if (*abort_flag) break;
+            tc::fence_after();
+            const uint32_t aBase = l == 0 ? tc::smem_u32(Xs + xb * Cfg::XBYTES) + (k0 / 8) * 128
+                                          : tc::smem_u32(Hs) + (k0 / 8) * 128;
+            const uint32_t sboA = (uint32_t)((l == 0 ? Cfg::K0 : kH) / 8) * 128;
+            const uint32_t sboB = (uint32_t)(Cfg::KW(l) / 8) * 128;
+            const uint32_t bBase = tc::smem_u32(Wb + slot * kChunkBytes);
+            constexpr uint32_t idesc_h = tc::idesc_bf16(kTile, kH);
+            const uint32_t idesc = l < 3 ? idesc_h : tc::idesc_bf16(kTile, Cfg::OUTP);
+            // the start-address field (address / 16, 14 bits) of a descriptor advances by
+            // 256 / 16 per K step of 16; shared addresses stay below 2^18, so no carry
+            const uint64_t ad0 = tc::desc_kmajor(aBase, 128, sboA);
+            const uint64_t bd0 = tc::desc_kmajor(bBase, 128, sboB);
+#pragma unroll
+            for (int s = 0; s < Cfg::KW(l) / 16; ++s)
+              tc::mma_bf16(acc, ad0 + (uint64_t)(16 * s), bd0 + (uint64_t)(16 * s), idesc,
+                           (c == 0 && s == 0) ? 0u : 1u);
+            tc::commit(&bar_f[slot]);
+            slot = slot + 1 == (uint32_t)NBUF ? 0 : slot + 1;
+          }
+          if (*abort_flag) break;
+          tc::commit(&bar_acc[l & 1]);
+          if (l == 0) tc::commit(&bar_xf[xb]);
+        }
+      }
+      // every MMA of this thread has completed before the tensor memory is released
+      tc::commit(&bar_done);
+      tc::mbar_wait(&bar_done, 0, p.err, 0);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue warps ----
+    const int quarter = warp & 3, grp = warp >> 2;
+    const int trow = quarter * 32 + lane;  // tensor-memory lane = tile row
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    uint32_t ph_acc[2] = {0, 0};
+    const int64_t mask = ((int64_t)1 << p.logn) - 1;
+    for (int64_t it = 0; it < my_tiles; ++it) {
+      if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;  // warp-uniform
+      const int64_t r0 = (blockIdx.x + it * gridDim.x) * kTile;
+      const int64_t myrow = r0 + trow;
+      for (int layer = 0; layer < 3; ++layer) {
+        const int a = layer & 1;
+        wait_warp(&bar_acc[a], ph_acc[a], 8);
+        ph_acc[a] ^= 1;
+        tc::fence_after();
+        const uint32_t taddr = tmem + lane_off + (uint32_t)(a * kH);
+        const float* bl = bs + layer * kH;
+        const float* ql = bq + layer * kH;
+        uint32_t r[2][32];
+        tc::tmem_ld32_nowait(taddr + grp * 32, r[0]);
+#pragma unroll
+        for (int pass = 0; pass < kNPass; ++pass) {
+          const int cb = pass * kPassCols + grp * 32;  // this warp's 32 columns of the pass
+          tc::ld_wait(r[pass & 1]);
+          if (pass + 1 < kNPass)
+            tc::tmem_ld32_nowait(taddr + cb + kPassCols, r[(pass + 1) & 1]);
+          const uint32_t* rr = r[pass & 1];
+          float h[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            // hard-swish of z = acc + b: z * clamp(z / 6 + 1/2, 0, 1), the clamp argument
+            // formed directly from the accumulator as acc / 6 + (b / 6 + 1/2)
+            const float acc = __uint_as_float(rr[i]);
+            const float z = acc + bl[cb + i];
+            h[i] = z * __saturatef(fmaf(acc, 1.0f / 6.0f, ql[cb + i]));
+            if (MODE == kModeBatch && myrow < p.M) p.Zs[layer][myrow * kH + cb + i] = z;
+          }
+#pragma unroll
+          for (int q8 = 0; q8 < 4; ++q8) {
+            uint4 q;
+            q.x = tc::pack_bf16(h[8 * q8 + 0], h[8 * q8 + 1]);
+            q.y = tc::pack_bf16(h[8 * q8 + 2], h[8 * q8 + 3]);
+            q.z = tc::pack_bf16(h[8 * q8 + 4], h[8 * q8 + 5]);
+            q.w = tc::pack_bf16(h[8 * q8 + 6], h[8 * q8 + 7]);
+            *reinterpret_cast<uint4*>(Hs + tc::kmajor_off(trow, cb + 8 * q8, kH)) = q;
+            if (MODE == kModeBatch && myrow < p.M)
+              *reinterpret_cast<uint4*>(p.Hs[layer] + myrow * kH + cb + 8 * q8) = q;
+          }
+          // this warp's part of the pass is written: make it visible to the tensor cores
+          tc::fence_async_smem();
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&bar_h[pass]);
+        }
+      }
+      // ---- layer 3: the outputs (accumulator 1) ----
+      wait_warp(&bar_acc[1], ph_acc[1], 8);
+      ph_acc[1] ^= 1;
+      tc::fence_after();
+      if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;
+      float y[OUTP];
+      {
+        const uint32_t taddr = tmem + lane_off + (uint32_t)kH;
+        uint32_t r[32];
+#pragma unroll
+        for (int c0 = 0; c0 < OUTP; c0 += 32) {
+          tc::tmem_ld32_nowait(taddr + c0, r);
+          tc::ld_wait(r);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) y[c0 + i] = __uint_as_float(r[i]) + bs[3 * kH + c0 + i];
+        }
+      }
+      tc::fence_before();
+      if (myrow < p.M) {
+        if (MODE == kModeBatch) {
+          if (grp == 0) {
 #pragma unroll
             for (int o = 0; o < OUTP; ++o) p.Y[myrow * OUTP + o] = y[o];
-          } else {
-            // de-normalise, unit-normalise alpha (c scaled alike: P^-1 C is invariant); the
-            // network's precision is fp32, the difference v - s_j is taken in fp64
-            float al[MU], cc[MU], nrm2 = 0.0f;
+          }
+        } else {
+          // de-normalise, unit-normalise alpha (c scaled alike: P^-1 C is invariant); the
+          // network's precision is fp32, the difference v - s_j is taken in fp64
+          float al[MU], cc[MU], nrm2 = 0.0f;
+#pragma unroll
+          for (int i = 0; i < MU; ++i) {
+            al[i] = y[i] * nrm[2 + OUTP + i] + nrm[2 + i];
+            cc[i] = y[MU + i] * nrm[2 + OUTP + MU + i] + nrm[2 + MU + i];
+            nrm2 = fmaf(al[i], al[i], nrm2);
+          }
+          const float sc = nrm2 > 0.0f ? rsqrtf(nrm2) : 1.0f;
+          if (grp == 0) {
 #pragma unroll
             for (int i = 0; i < MU; ++i) {
-              al[i] = y[i] * nrm[2 + OUTP + i] + nrm[2 + i];
-              cc[i] = y[MU + i] * nrm[2 + OUTP + MU + i] + nrm[2 + MU + i];
-              nrm2 = fmaf(al[i], al[i], nrm2);
+              __stcs(p.Q + myrow * MU + i, (double)(al[i] * sc));
+              __stcs(p.C + myrow * MU + i, (double)(cc[i] * sc));
             }
-            const float sc = nrm2 > 0.0f ? rsqrtf(nrm2) : 1.0f;
-            const double s = __dmul_rn((double)(4 * snap_m(__ldg(p.v + myrow)) + 2), kPi2);
+          } else {
+            // v[mu_j] - s_j from the fp32 pairs: the difference of the high parts is exact
+            // when v and s_j are within a factor of two of each other (the usual case)
+            const float sh = __ldg(p.sh + myrow), sl = __ldg(p.sl + myrow);
 #pragma unroll
             for (int i = 0; i < MU; ++i) {
-              constexpr int R = 1;
-              const double vn = __ldg(p.v + nb_index<D, R>(myrow, i, p.logn, mask));
-              const float a_ = al[i] * sc, c_ = cc[i] * sc;
-              __stcs(p.Q + myrow * MU + i, (double)a_);
-              __stcs(p.C + myrow * MU + i, (double)c_);
-              __stcs(p.P + myrow * MU + i, (double)fmaf(c_, (float)(vn - s), a_));
+              const int64_t nb = nb_index<D, 1>(myrow, i, p.logn, mask);
+              const float dv = (__ldg(p.vh + nb) - sh) + (__ldg(p.vl + nb) - sl);
+              __stcs(p.P + myrow * MU + i, (double)fmaf(cc[i] * sc, dv, al[i] * sc));
             }
           }
         }
       }
-      tc::fence_async_smem();
-      tc::fence_before();
-      __syncthreads();
-      tc::fence_after();
     }
-  }
-  // drain: the last chunks' completion barriers (already complete unless aborted)
-  if (leader && !s_abort) {
-    for (int b = 0; b < NBUF; ++b)
-      if (f_pending[b]) tc::mbar_wait(&bar_f[b], ph_f[b], p.err, 2);
   }
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, kH);
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * kH);
+}
+
+// Per point j of a learned build: the normalised features of h^2 v_j and of h^2 s_j (bf16,
+// s_j = snap(v_j)), and fp32 pairs v_j = vh + vl, s_j = sh + sl for the P epilogue. Since
+// h^2 = 1/n^2 is a power of two, (float)(v h^2) = (float)v * h^2 exactly.
+__global__ void k_point_features(const double* __restrict__ v, int64_t N, float h2f,
+                                 const float* __restrict__ params, int64_t norm_off,
+                                 __nv_bfloat16* __restrict__ xb, __nv_bfloat16* __restrict__ sb,
+                                 float* __restrict__ vh, float* __restrict__ vl,
+                                 float* __restrict__ sh, float* __restrict__ sl) {
+  const float mu_x = params[norm_off], isig_x = 1.0f / params[norm_off + 1];
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double x = v[j];
+    const float xf = (float)x;
+    const double s = __dmul_rn((double)(4 * snap_m(x) + 2), kPi2);
+    const float sf = (float)s;
+    xb[j] = __float2bfloat16((xf * h2f - mu_x) * isig_x);
+    sb[j] = __float2bfloat16(((float)(s * (double)h2f) - mu_x) * isig_x);
+    vh[j] = xf;
+    vl[j] = (float)(x - (double)xf);
+    sh[j] = sf;
+    sl[j] = (float)(s - (double)sf);
+  }
+}
+
+// Normalised bf16 network inputs, written in the canonical K-major tile layout of the fused
+// kernel: 16 bytes (8 features of one row) per thread, consecutive threads writing
+// consecutive 16-byte units. Rows beyond M (the last tile's tail) are zero.
+//   rows mode: features of point j = xb over its 5^d patch (lexicographic offsets), then sb[j]
+//   batch mode: the raw features Xraw[j][0..NF), normalised here, also stored row-major (X16)
+//   for the backward pass
+template <int D, int MODE>
+__global__ void k_inputs(const __nv_bfloat16* __restrict__ xb,
+                         const __nv_bfloat16* __restrict__ sb, int logn,
+                         const float* __restrict__ Xraw, const float* __restrict__ params,
+                         int64_t norm_off, int64_t M, uint8_t* __restrict__ Xt,
+                         __nv_bfloat16* __restrict__ X16) {
+  constexpr int NF = D == 2 ? 26 : 126, NP = NF - 1;
+  constexpr int K0 = D == 2 ? 32 : 128, KG = K0 / 8;
+  const float mu_x = params[norm_off], isig_x = 1.0f / params[norm_off + 1];
+  const int64_t mask = ((int64_t)1 << logn) - 1;
+  const int64_t units = (M + kTile - 1) / kTile * kTile * KG;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < units;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    // e = ((tile * 16 + row / 8) * KG + kg) * 8 + row % 8
+    const int64_t qv = e >> 3;
+    const int kg = (int)(qv % KG);
+    const int64_t row = (qv / KG) * 8 + (e & 7);
+    __nv_bfloat16 f[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = kg * 8 + i;
+      __nv_bfloat16 x = __float2bfloat16(0.0f);
+      if (row < M && k < NF) {
+        if (MODE == kModeRows)
+          x = k < NP ? xb[nb_index<D, 2>(row, k, logn, mask)] : sb[row];
+        else
+          x = __float2bfloat16((Xraw[row * NF + k] - mu_x) * isig_x);
+      }
+      f[i] = x;
+    }
+    const uint4 q = *reinterpret_cast<const uint4*>(f);
+    reinterpret_cast<uint4*>(Xt)[e] = q;
+    if (MODE == kModeBatch && row < M) reinterpret_cast<uint4*>(X16 + row * K0)[kg] = q;
+  }
 }
 
 // ---- generic C[M x N] (fp32) = A[M x K] B[N x K]^T, bf16 row-major operands ---------------
@@ -633,17 +811,6 @@ __global__ void k_norm_stats(const float* __restrict__ X, const float* __restric
   }
 }
 
-// Per point, fp32 h^2 v and h^2 s_j (s_j = snap(v_j)): the learned build's inputs.
-__global__ void k_prep_inputs(const double* __restrict__ v, int64_t N, double h2,
-                              float* __restrict__ h2v, float* __restrict__ h2s) {
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const double x = v[j];
-    h2v[j] = (float)(x * h2);
-    h2s[j] = (float)(__dmul_rn((double)(4 * snap_m(x) + 2), kPi2) * h2);
-  }
-}
-
 // Training pairs from a context's last eigen-path build: raw patch features of random points
 // and their (alpha, c) targets. The random point of sample i is a hash of (seed, i).
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
@@ -689,7 +856,7 @@ struct lsp_mlp {
   lsp::DevBuf params, grads, adam_m, adam_v, tiles, WT[4], W16[4], errflag, loss;
   // training workspace
   int64_t cap = 0;
-  lsp::DevBuf X16, XT, Zs[3], Hs[3], HT[3], Y, dY16, dYT, dY32, G, dZ16, dZT, dZ32;
+  lsp::DevBuf X16, XT, Xt, Zs[3], Hs[3], HT[3], Y, dY16, dYT, dY32, G, dZ16, dZT, dZ32;
   int64_t step = 0;
 };
 
@@ -725,13 +892,6 @@ bool grow(lsp::DevBuf& b, size_t bytes) {
   return true;
 }
 
-size_t fused_smem(int d) {
-  const Dims m = dims_for(d);
-  const int nbuf = d == 2 ? 6 : 4;
-  return (size_t)kTile * m.K0 * 2 + kTile * kH * 2 + (size_t)nbuf * kChunkBytes +
-         sizeof(float) * (3 * kH + m.OUTP + 2 + 2 * m.OUTP) + 64;
-}
-
 FusedParams fused_params(lsp_mlp* m) {
   FusedParams p;
   memset(&p, 0, sizeof p);
@@ -744,16 +904,28 @@ FusedParams fused_params(lsp_mlp* m) {
   return p;
 }
 
+// Bytes of the canonical input tiles for `rows` rows (whole tiles).
+size_t input_tile_bytes(int d, int64_t rows) {
+  return (size_t)((rows + kTile - 1) / kTile) * kTile * dims_for(d).K0 * 2;
+}
+
+template <int D, int MODE>
+cudaError_t launch_inputs(cudaStream_t st, const FusedParams& p, const __nv_bfloat16* xb,
+                          const __nv_bfloat16* sb, const float* Xraw, __nv_bfloat16* X16) {
+  k_inputs<D, MODE><<<152 * 8, 256, 0, st>>>(xb, sb, p.logn, Xraw, p.params, p.norm_off, p.M,
+                                             (uint8_t*)p.Xt, X16);
+  return cudaGetLastError();
+}
+
 template <int D, int MODE>
 cudaError_t launch_fused(lsp_mlp* m, const FusedParams& p, int64_t rows) {
-  const size_t smem = fused_smem(D);
+  const size_t smem = FusedCfg<D>::smem;
   cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<D, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int64_t tiles = (rows + kTile - 1) / kTile;
-  // two CTAs per SM where the shared memory allows (2D)
-  const int per_sm = smem <= 110 * 1024 ? 2 : 1;
-  int grid = (int)(tiles < 152 * per_sm ? tiles : 152 * per_sm);
+  const int64_t tiles = (rows + kTile - 1) / kTile;
+  // persistent: one CTA per SM (its tensor memory takes all 512 columns)
+  int grid = (int)(tiles < 152 ? tiles : 152);
   if (grid < 1) grid = 1;
   k_mlp_fused<D, MODE><<<grid, kFusedThreads, smem, m->stream>>>(p);
   return cudaGetLastError();
@@ -781,6 +953,7 @@ lsp_status ensure_workspace(lsp_mlp* m, int64_t B) {
   if (m->cap >= B) return LSP_OK;
   const Dims& d = m->dm;
   bool ok = grow(m->X16, sizeof(__nv_bfloat16) * B * d.K0) &&
+            grow(m->Xt, input_tile_bytes(d.d, B)) &&
             grow(m->XT, sizeof(__nv_bfloat16) * B * d.K0) && grow(m->Y, sizeof(float) * B * d.OUTP) &&
             grow(m->dY16, sizeof(__nv_bfloat16) * B * d.OUTP) &&
             grow(m->dYT, sizeof(__nv_bfloat16) * B * 128) &&
@@ -806,6 +979,26 @@ cudaError_t gemm(lsp_mlp* m, const void* A, const void* B, float* C, int M, int 
   k_gemm_tn<<<grid, 128, smem, m->stream>>>((const __nv_bfloat16*)A, (const __nv_bfloat16*)B, C, M,
                                             N, K, (int*)m->errflag.p);
   return cudaGetLastError();
+}
+
+// Training-mode forward: normalised bf16 inputs (canonical tiles and row-major), then the fused
+// network, saving z and h of every hidden layer.
+cudaError_t batch_forward(lsp_mlp* m, const float* X_dev, int64_t batch, float* Y_dev) {
+  FusedParams p = fused_params(m);
+  p.M = batch;
+  p.Xt = (const uint8_t*)m->Xt.p;
+  p.Y = Y_dev;
+  for (int l = 0; l < 3; ++l) {
+    p.Zs[l] = (float*)m->Zs[l].p;
+    p.Hs[l] = (__nv_bfloat16*)m->Hs[l].p;
+  }
+  __nv_bfloat16* X16 = (__nv_bfloat16*)m->X16.p;
+  cudaError_t e =
+      m->dm.d == 2 ? launch_inputs<2, kModeBatch>(m->stream, p, nullptr, nullptr, X_dev, X16)
+                   : launch_inputs<3, kModeBatch>(m->stream, p, nullptr, nullptr, X_dev, X16);
+  if (e != cudaSuccess) return e;
+  return m->dm.d == 2 ? launch_fused<2, kModeBatch>(m, p, batch)
+                      : launch_fused<3, kModeBatch>(m, p, batch);
 }
 
 }  // namespace
@@ -879,7 +1072,7 @@ lsp_status lsp_mlp_destroy(lsp_mlp* m) {
   if (!m) return LSP_OK;
   cudaStreamSynchronize(m->stream);
   lsp::DevBuf* bufs[] = {&m->params, &m->grads, &m->adam_m, &m->adam_v, &m->tiles, &m->errflag,
-                         &m->loss, &m->X16, &m->XT, &m->Y, &m->dY16, &m->dYT, &m->dY32, &m->G,
+                         &m->loss, &m->X16, &m->XT, &m->Xt, &m->Y, &m->dY16, &m->dYT, &m->dY32, &m->G,
                          &m->dZ16, &m->dZT, &m->dZ32};
   for (auto* b : bufs)
     if (b->p) cudaFree(b->p);
@@ -938,20 +1131,7 @@ lsp_status lsp_mlp_forward(lsp_mlp* m, const float* X_dev, int64_t batch, float*
   const int64_t B = (batch + 127) / 128 * 128;
   lsp_status st = ensure_workspace(m, B);
   if (st != LSP_OK) return st;
-  FusedParams p = fused_params(m);
-  p.M = batch;
-  p.Xraw = X_dev;
-  p.Y = Y_dev;
-  p.X16 = (__nv_bfloat16*)m->X16.p;
-  for (int l = 0; l < 3; ++l) {
-    p.Zs[l] = (float*)m->Zs[l].p;
-    p.Hs[l] = (__nv_bfloat16*)m->Hs[l].p;
-  }
-  {
-    const cudaError_t e = m->dm.d == 2 ? launch_fused<2, kModeBatch>(m, p, batch)
-                                       : launch_fused<3, kModeBatch>(m, p, batch);
-    MCUDA(m, e);
-  }
+  MCUDA(m, batch_forward(m, X_dev, batch, Y_dev));
   return check_err(m);
 }
 
@@ -964,20 +1144,7 @@ lsp_status lsp_mlp_train_step(lsp_mlp* m, const float* X_dev, const float* T_dev
   lsp_status st = ensure_workspace(m, batch);
   if (st != LSP_OK) return st;
   // forward (saves z, h, and the normalised bf16 inputs)
-  FusedParams p = fused_params(m);
-  p.M = batch;
-  p.Xraw = X_dev;
-  p.Y = (float*)m->Y.p;
-  p.X16 = (__nv_bfloat16*)m->X16.p;
-  for (int l = 0; l < 3; ++l) {
-    p.Zs[l] = (float*)m->Zs[l].p;
-    p.Hs[l] = (__nv_bfloat16*)m->Hs[l].p;
-  }
-  {
-    const cudaError_t e = d.d == 2 ? launch_fused<2, kModeBatch>(m, p, batch)
-                                   : launch_fused<3, kModeBatch>(m, p, batch);
-    MCUDA(m, e);
-  }
+  MCUDA(m, batch_forward(m, X_dev, batch, (float*)m->Y.p));
   // loss and dY
   MCUDA(m, cudaMemsetAsync(m->loss.p, 0, sizeof(double), m->stream));
   MCUDA(m, cudaMemsetAsync(m->dYT.p, 0, sizeof(__nv_bfloat16) * 128 * batch, m->stream));
@@ -1071,30 +1238,49 @@ cudaError_t launch_learned_rows(lsp_ctx* c, lsp_mlp* m) {
   cudaError_t se = cudaStreamSynchronize(m->stream);
   if (se != cudaSuccess) return se;
   FusedParams p = fused_params(m);
-  p.M = c->geo.N;
-  p.v = (const double*)c->v.p;
+  const int64_t N = c->geo.N;
+  p.M = N;
   int logn = 0;
   while ((1 << logn) < c->geo.n) ++logn;
   p.logn = logn;
-  p.h2 = 1.0 / ((double)c->geo.n * c->geo.n);
   p.Q = (double*)c->Q.p;
   p.C = (double*)c->C.p;
   p.P = (double*)c->P.p;
   p.err = (int*)c->counts.p + kErrWord;
-  if (!ensure(c, c->learn_in, sizeof(float) * 2 * c->geo.N)) return cudaErrorMemoryAllocation;
-  p.h2v = (const float*)c->learn_in.p;
-  p.h2s = (const float*)c->learn_in.p + c->geo.N;
+  // learn_in: the input tiles, then per point xb, sb (bf16) and vh, vl, sh, sl (fp32)
+  const size_t xt_bytes = input_tile_bytes(c->geo.d, N);
+  const size_t pts = ((size_t)N * 2 + 255) / 256 * 256, ptf = ((size_t)N * 4 + 255) / 256 * 256;
+  if (!ensure(c, c->learn_in, xt_bytes + 2 * pts + 4 * ptf)) return cudaErrorMemoryAllocation;
+  uint8_t* base = (uint8_t*)c->learn_in.p;
+  p.Xt = base;
+  __nv_bfloat16* xb = (__nv_bfloat16*)(base + xt_bytes);
+  __nv_bfloat16* sb = (__nv_bfloat16*)(base + xt_bytes + pts);
+  float* f32 = (float*)(base + xt_bytes + 2 * pts);
+  float* vh = f32;
+  float* vl = (float*)((uint8_t*)f32 + ptf);
+  float* sh = (float*)((uint8_t*)f32 + 2 * ptf);
+  float* sl = (float*)((uint8_t*)f32 + 3 * ptf);
+  p.vh = vh;
+  p.vl = vl;
+  p.sh = sh;
+  p.sl = sl;
+  const float h2f = (float)(1.0 / ((double)c->geo.n * c->geo.n));
   cudaStream_t saved = m->stream;
   m->stream = c->stream;
-  int t0 = timer_begin(c, "mlp_prep");
-  k_prep_inputs<<<152 * 8, 256, 0, c->stream>>>((const double*)c->v.p, c->geo.N, p.h2,
-                                                (float*)c->learn_in.p,
-                                                (float*)c->learn_in.p + c->geo.N);
+  int t0 = timer_begin(c, "mlp_inputs");
+  k_point_features<<<152 * 8, 256, 0, c->stream>>>((const double*)c->v.p, N, h2f, p.params,
+                                                   p.norm_off, xb, sb, vh, vl, sh, sl);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = c->geo.d == 2 ? launch_inputs<2, kModeRows>(c->stream, p, xb, sb, nullptr, nullptr)
+                      : launch_inputs<3, kModeRows>(c->stream, p, xb, sb, nullptr, nullptr);
   timer_end(c, t0);
-  int t = timer_begin(c, "mlp_rows");
-  cudaError_t e = c->geo.d == 2 ? launch_fused<2, kModeRows>(m, p, c->geo.N)
-                                : launch_fused<3, kModeRows>(m, p, c->geo.N);
-  timer_end(c, t);
+  if (e == cudaSuccess) {
+    int t = timer_begin(c, "mlp_rows");
+    e = c->geo.d == 2 ? launch_fused<2, kModeRows>(m, p, c->geo.N)
+                      : launch_fused<3, kModeRows>(m, p, c->geo.N);
+    timer_end(c, t);
+  }
   m->stream = saved;
   return e;
 }

@@ -119,7 +119,7 @@ struct lsp_ctx {
 
   // learned surrogate (LSP_LEARNED builds)
   lsp_mlp* mlp = nullptr;
-  lsp::DevBuf learn_in;  // fp32 h^2 v and h^2 s_j per point (learned builds)
+  lsp::DevBuf learn_in;  // the network inputs (bf16, canonical tiles) of a learned build
   bool built_learned = false;
   int mode_used = -1;
 

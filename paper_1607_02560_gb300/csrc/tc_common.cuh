@@ -68,24 +68,34 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Wait until the phase with the given parity has completed. Non-blocking polls with a short
-// back-off; after kWaitLimitNs of wall time the wait gives up, records bit `errbit` in *err
-// and returns false.
+// Wait until the phase with the given parity has completed: one non-blocking test, then
+// try_wait with a suspend-time hint (the thread sleeps in hardware until the phase completes or
+// about 2 us pass), so that waiting threads do not flood the shared-memory pipe with polls.
+// After kWaitLimitNs of wall time the wait gives up, records bit `errbit` in *err and returns
+// false.
+__device__ __forceinline__ bool mbar_test(uint64_t* mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred P1;\nmbarrier.test_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+      "selp.b32 %0, 1, 0, P1;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int* err, int errbit) {
+  if (mbar_test(mbar, parity)) return true;
   const uint64_t t0 = global_ns();
-  for (int it = 0;; ++it) {
+  for (;;) {
     uint32_t done;
     asm volatile(
-        "{\n.reg .pred P1;\nmbarrier.test_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+        "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2, %3;\n"
         "selp.b32 %0, 1, 0, P1;\n}\n"
         : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(parity)
+        : "r"(smem_u32(mbar)), "r"(parity), "r"(2000u)
         : "memory");
     if (done) return true;
-    if ((it & 255) == 255) {
-      if (global_ns() - t0 > kWaitLimitNs) break;
-      __nanosleep(64);
-    }
+    if (global_ns() - t0 > kWaitLimitNs) break;
   }
   atomicOr(err, errbit);
   return false;
@@ -96,6 +106,11 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(mbar)),
                "r"(bytes)
                : "memory");
+}
+
+// One plain arrival (release semantics at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
 }
 
 // 1D bulk copy global -> shared, completing `bytes` on the mbarrier. Both addresses 16-byte
@@ -160,6 +175,14 @@ __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t (&r)[3
 }
 __device__ __forceinline__ void ld_wait() {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+// The same wait, tied to the destination registers of an earlier tmem_ld32_nowait, so that no
+// use of them can be scheduled before it.
+__device__ __forceinline__ void ld_wait(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]),"+r"(r[1]),"+r"(r[2]),"+r"(r[3]),"+r"(r[4]),"+r"(r[5]),"+r"(r[6]),"+r"(r[7]),"+r"(r[8]),"+r"(r[9]),"+r"(r[10]),"+r"(r[11]),"+r"(r[12]),"+r"(r[13]),"+r"(r[14]),"+r"(r[15]),"+r"(r[16]),"+r"(r[17]),"+r"(r[18]),"+r"(r[19]),"+r"(r[20]),"+r"(r[21]),"+r"(r[22]),"+r"(r[23]),"+r"(r[24]),"+r"(r[25]),"+r"(r[26]),"+r"(r[27]),"+r"(r[28]),"+r"(r[29]),"+r"(r[30]),"+r"(r[31])
+               :
+               : "memory");
 }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
