@@ -86,7 +86,8 @@ __device__ __forceinline__ double pow2_inv_exp(double x) {
 
 // LDL^T factorisation (no pivoting) of a symmetric positive definite dim x dim matrix; returns
 // false if a pivot is not positive. L unit lower triangular, id = 1 / D.
-__device__ bool ldlt(const double s[4][4], int dim, double L[4][4], double id[4]) {
+__device__ __forceinline__ bool ldlt(const double s[4][4], int dim, double L[4][4],
+                                     double id[4]) {
   double d[4];
   for (int j = 0; j < dim; ++j) {
     double dj = s[j][j];
@@ -514,6 +515,336 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
   }
 }
 
+// ---- 3D, one warp per shift, blocks formed from the class values --------------------------
+// The blocks of A in 3D are A1g (4 x 4), T1u (3 x 3), Eg and T2g (2 x 2), T2u and A2u (1 x 1),
+// each on the vectors U_b of one partner of an irreducible representation. G = G_s[mu, mu]
+// commutes with the symmetry group, so it maps span(U_b) into itself: G U_b = U_b G_b with
+// G_b = U_b^T G U_b, and the block of A = A1 - G G^T is B_b = U_b^T A1 U_b - G_b G_b. Both
+// U_b^T A1 U_b and G_b are linear in the class values, X_b[i][j] = sum_k coef[e][k] x[k] with
+// coef[e][k] = sum of u_i[a] u_j[c] over the pairs (a, c) of class k (e = (b, i, j), i <= j):
+// 20 terms per entry instead of forming the 27 x 27 matrix A and projecting it.
+//
+// The 4 x 4 and 3 x 3 blocks are solved side by side on the two 16-lane halves of the warp
+// (lane (r, c) of a half holds entry (r, c)): M = (B + delta I)^-1 from an LDL^T factorisation
+// (delta = 1e-13 tr B keeps the factorisation positive definite without moving eigenvectors),
+// then seven squarings M <- M^2, scaled by a power of two, so M^128 is dominated by the
+// eigenvector of the smallest eigenvalue (inverse iteration with exponent 128). Its Rayleigh
+// quotient and residual are taken with B; a block whose residual fails the check is solved
+// again by block_min_eig. The next eigenvalue of the block (for the degeneracy flag) comes from
+// three squarings of M deflated by the found pair. The 2 x 2 blocks use the closed form.
+__constant__ double c_coef3[24][kMaxCls];
+
+struct Eig3Warp {
+  double g[2 * kMaxCls];
+  double Gb[6][16];
+  double B[6][16];
+  double M[2][16];
+  double v[6][4];    // eigenvector (block coordinates) of each block's smallest eigenvalue
+  double lam[6][2];  // each block's smallest and next eigenvalue
+  double tr[6];      // each block's trace (bound of its largest eigenvalue)
+  int conv[2];
+};
+
+// 2^-2e for the exponent e of x: squares of entries scaled by the square of the trace's scale.
+__device__ __forceinline__ double pow2_inv_exp_sq(double x) {
+  const double p = pow2_inv_exp(x);
+  return p * p;
+}
+
+// Scaled squaring of the symmetric 4 x 4 matrix M of a 16-lane half; lane (r, c) gets the new
+// entry (r, c). Reads before the caller's __syncwarp, writes after it.
+__device__ __forceinline__ double sq_entry(const double* M, int r, int c) {
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) s = fma(M[r * 4 + k], M[k * 4 + c], s);
+  return s * pow2_inv_exp_sq(M[0] + M[5] + M[10] + M[15]);
+}
+
+// Dominant column of the matrix of a half after the squarings, normalised.
+__device__ __forceinline__ void dominant_column(const double* M, double v[4]) {
+  int jm = 0;
+#pragma unroll
+  for (int j = 1; j < 4; ++j)
+    if (M[j * 5] > M[jm * 5]) jm = j;
+  double n2 = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = M[k * 4 + jm];
+    n2 = fma(v[k], v[k], n2);
+  }
+  const double inv = n2 > 0.0 ? rsqrt(n2) : 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] *= inv;
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_eig3d(const double* __restrict__ gvals,
+                                                      int64_t cap,
+                                                      const int32_t* __restrict__ count,
+                                                      double* __restrict__ alpha_out,
+                                                      double* __restrict__ c_out,
+                                                      double* __restrict__ lam_out,
+                                                      int32_t* __restrict__ flags_out) {
+  constexpr int MU = 27, NCLS = 10, NENT = 24, CENTRE = 13;
+  __shared__ double s_coef[NENT][NCLS];
+  __shared__ double s_u[kMaxSymVec][MU];
+  __shared__ int8_t s_ent[NENT][3];
+  __shared__ Eig3Warp sw[WARPS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < NENT * NCLS; e += WARPS * 32)
+    s_coef[e / NCLS][e % NCLS] = c_coef3[e / NCLS][e % NCLS];
+  for (int e = threadIdx.x; e < kMaxSymVec * MU; e += WARPS * 32)
+    s_u[e / MU][e % MU] = c_sym.u[e / MU][e % MU];
+  for (int e = threadIdx.x; e < NENT * 3; e += WARPS * 32) s_ent[e / 3][e % 3] = c_ent[e / 3][e % 3];
+  __syncthreads();
+  Eig3Warp& sm = sw[w];
+  const int64_t cnt = *count;
+  const int h = lane >> 4, q = lane & 15, r = q >> 2, cc = q & 3;  // half h solves block h
+  for (int64_t i = (int64_t)blockIdx.x * WARPS + w; i < cnt; i += (int64_t)gridDim.x * WARPS) {
+    if (lane < 2 * NCLS) sm.g[lane] = gvals[(int64_t)lane * cap + i];
+    for (int e = lane; e < 6 * 16; e += 32) {
+      (&sm.Gb[0][0])[e] = 0.0;
+      (&sm.B[0][0])[e] = 0.0;
+    }
+    __syncwarp();
+    // ---- a4: G_b and U_b^T A1 U_b entries, then B_b = U_b^T A1 U_b - G_b G_b ----
+    int eb = 0, ei = 0, ej = 0;
+    double a1 = 0.0;
+    if (lane < NENT) {
+      eb = s_ent[lane][0];
+      ei = s_ent[lane][1];
+      ej = s_ent[lane][2];
+      double gg = 0.0;
+#pragma unroll
+      for (int k = 0; k < NCLS; ++k) {
+        gg = fma(s_coef[lane][k], sm.g[2 * k], gg);
+        a1 = fma(s_coef[lane][k], sm.g[2 * k + 1], a1);
+      }
+      sm.Gb[eb][ei * 4 + ej] = gg;
+      sm.Gb[eb][ej * 4 + ei] = gg;
+    }
+    __syncwarp();
+    if (lane < NENT) {
+      double s = a1;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) s = fma(-sm.Gb[eb][ei * 4 + k], sm.Gb[eb][k * 4 + ej], s);
+      sm.B[eb][ei * 4 + ej] = s;
+      sm.B[eb][ej * 4 + ei] = s;
+    }
+    __syncwarp();
+    // ---- a5 for blocks 0 and 1 (one per half) ----
+    double b[4][4], scale = 0.0, tr = 0.0;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        b[x][y] = sm.B[h][x * 4 + y];
+        scale = fmax(scale, fabs(b[x][y]));
+      }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) tr += b[x][x];
+    if (h == 1) b[3][3] = 4.0 * scale + 1.0;  // decoupled pad above every eigenvalue of the 3 x 3
+    double s4[4][4], L[4][4], id[4];
+    const double delta = 1e-13 * fabs(tr);
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) {
+        s4[x][y] = b[x][y] + (x == y ? delta : 0.0);
+        L[x][y] = 0.0;
+      }
+    const bool fact = ldlt(s4, 4, L, id);
+    // entry (r, cc) of M0 = (B + delta I)^-1: column cc by forward and back substitution
+    double xv[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xv[k] = k == cc ? 1.0 : 0.0;
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int k = 0; k < x; ++k) xv[x] = fma(-L[x][k], xv[k], xv[x]);
+#pragma unroll
+    for (int x = 0; x < 4; ++x) xv[x] *= id[x];
+#pragma unroll
+    for (int x = 3; x >= 0; --x)
+#pragma unroll
+      for (int k = x + 1; k < 4; ++k) xv[x] = fma(-L[k][x], xv[k], xv[x]);
+    double m0 = xv[0];
+#pragma unroll
+    for (int k = 1; k < 4; ++k)
+      if (r == k) m0 = xv[k];
+    if (!fact) m0 = r == cc ? 1.0 : 0.0;
+    sm.M[h][q] = m0;
+    __syncwarp();
+#pragma unroll 1
+    for (int k = 0; k < 7; ++k) {
+      const double nv = sq_entry(sm.M[h], r, cc);
+      __syncwarp();
+      sm.M[h][q] = nv;
+      __syncwarp();
+    }
+    double v1[4];
+    dominant_column(sm.M[h], v1);
+    if (h == 1) v1[3] = 0.0;
+    double lam = 0.0, res = 0.0, bv[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      bv[x] = 0.0;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) bv[x] = fma(b[x][y], v1[y], bv[x]);
+      lam = fma(v1[x], bv[x], lam);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x) res = fmax(res, fabs(fma(-lam, v1[x], bv[x])));
+    const int conv = fact && isfinite(lam) && res <= 64.0 * DBL_EPSILON * scale;
+    // next eigenvalue of the block: M0 deflated by (v1, mu1), three squarings, Rayleigh quotient
+    double part = v1[r] * m0 * v1[cc];
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    __syncwarp();
+    sm.M[h][q] = fma(-part * v1[r], v1[cc], m0);
+    __syncwarp();
+#pragma unroll 1
+    for (int k = 0; k < 3; ++k) {
+      const double nv = sq_entry(sm.M[h], r, cc);
+      __syncwarp();
+      sm.M[h][q] = nv;
+      __syncwarp();
+    }
+    double v2[4];
+    dominant_column(sm.M[h], v2);
+    double lam2b = 0.0;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      double t = 0.0;
+#pragma unroll
+      for (int y = 0; y < 4; ++y) t = fma(b[x][y], v2[y], t);
+      lam2b = fma(v2[x], t, lam2b);
+    }
+    if (!(v2[0] != 0.0 || v2[1] != 0.0 || v2[2] != 0.0 || v2[3] != 0.0)) lam2b = lam;
+    if (q == 0) {
+      sm.lam[h][0] = lam;
+      sm.lam[h][1] = lam2b;
+      sm.tr[h] = tr;
+      sm.conv[h] = conv;
+#pragma unroll
+      for (int x = 0; x < 4; ++x) sm.v[h][x] = v1[x];
+    }
+    // ---- the 2 x 2 (Eg, T2g) and 1 x 1 (T2u, A2u) blocks ----
+    if (lane < 4) {
+      const int bb = 2 + lane;
+      const double a00 = sm.B[bb][0], a01 = sm.B[bb][1], a11 = sm.B[bb][5];
+      double lo, hi, y0 = 1.0, y1 = 0.0;
+      if (bb < 4) {
+        const double mm = 0.5 * (a00 + a11), hh = 0.5 * (a00 - a11);
+        const double rr = sqrt(fma(hh, hh, a01 * a01));
+        hi = mm + rr;
+        lo = hi != 0.0 ? (a00 * a11 - a01 * a01) / hi : mm - rr;
+        double pp = a01, qq = lo - a00;
+        if (fabs(a00 - lo) < fabs(a11 - lo)) {
+          pp = lo - a11;
+          qq = a01;
+        }
+        double nr = sqrt(pp * pp + qq * qq);
+        if (nr == 0.0) {
+          pp = 1.0;
+          qq = 0.0;
+          nr = 1.0;
+        }
+        y0 = pp / nr;
+        y1 = qq / nr;
+        sm.tr[bb] = a00 + a11;
+      } else {
+        lo = a00;
+        hi = DBL_MAX;
+        sm.tr[bb] = a00;
+      }
+      sm.lam[bb][0] = lo;
+      sm.lam[bb][1] = hi;
+      sm.v[bb][0] = y0;
+      sm.v[bb][1] = y1;
+      sm.v[bb][2] = 0.0;
+      sm.v[bb][3] = 0.0;
+    }
+    __syncwarp();
+    // ---- fallback for a 4 x 4 or 3 x 3 block whose residual check failed ----
+    if (lane < 2 && !sm.conv[lane]) {
+      const int dim = lane == 0 ? 4 : 3;
+      double a[4][4], y[4], lmin, l2;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int z = 0; z < 4; ++z) a[x][z] = sm.B[lane][x * 4 + z];
+      sm.conv[lane] = block_min_eig(a, dim, y, &lmin, &l2) ? 2 : 0;
+      sm.lam[lane][0] = lmin;
+      sm.lam[lane][1] = l2;
+#pragma unroll
+      for (int x = 0; x < 4; ++x) sm.v[lane][x] = y[x];
+    }
+    __syncwarp();
+    // ---- selection (every lane, uniform) ----
+    int bstar = 0;
+#pragma unroll
+    for (int bb = 1; bb < 6; ++bb)
+      if (sm.lam[bb][0] < sm.lam[bstar][0]) bstar = bb;
+    const double lam1 = sm.lam[bstar][0];
+    double lam2 = DBL_MAX, lmax = 0.0;
+#pragma unroll
+    for (int bb = 0; bb < 6; ++bb) {
+      lmax = fmax(lmax, fabs(sm.tr[bb]));
+      if (bb == bstar) {
+        lam2 = fmin(lam2, sm.lam[bb][1]);
+        if (c_sym.copies[bb] > 1) lam2 = fmin(lam2, sm.lam[bb][0]);
+      } else {
+        lam2 = fmin(lam2, sm.lam[bb][0]);
+      }
+    }
+    int flags = 0;
+    if (!sm.conv[0] || !sm.conv[1]) flags |= LSP_FLAG_NOT_CONVERGED;
+    if (bstar != 0) flags |= LSP_FLAG_NONSYMMETRIC;
+    if (lam2 - lam1 < 1e-8 * lmax) flags |= LSP_FLAG_DEGENERATE;
+    // ---- alpha = U_b y and (a6) c = G alpha = U_b (G_b y) ----
+    const int first = c_sym.first[bstar];
+    double y[4], gy[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) y[x] = sm.v[bstar][x];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+      gy[x] = 0.0;
+#pragma unroll
+      for (int z = 0; z < 4; ++z) gy[x] = fma(sm.Gb[bstar][x * 4 + z], y[z], gy[x]);
+    }
+    double av = 0.0, cv = 0.0;
+    if (lane < MU) {
+      const int dimb = c_sym.dim[bstar];
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+        if (x < dimb) {
+          av = fma(y[x], s_u[first + x][lane], av);
+          cv = fma(gy[x], s_u[first + x][lane], cv);
+        }
+    }
+    // sign: alpha[centre] > 0, else the first entry above 1e-12 in magnitude
+    const double acen = __shfl_sync(0xffffffffu, av, CENTRE);
+    const unsigned big = __ballot_sync(0xffffffffu, lane < MU && fabs(av) > 1e-12);
+    const double afirst = __shfl_sync(0xffffffffu, av, big ? __ffs(big) - 1 : 0);
+    const double ref = fabs(acen) > 1e-12 ? acen : (big ? afirst : 0.0);
+    if (ref < 0.0) {
+      av = -av;
+      cv = -cv;
+    }
+    if (lane < MU) {
+      alpha_out[i * MU + lane] = av;
+      c_out[i * MU + lane] = cv;
+    }
+    if (lane == 0) {
+      lam_out[2 * i + 0] = lam1;
+      lam_out[2 * i + 1] = lam2;
+      flags_out[i] = flags;
+    }
+    __syncwarp();
+  }
+}
+
 // ---- 2D, one thread per shift ------------------------------------------------------------
 // In 2D the symmetry-adapted vectors are u_0..u_2 (fully symmetric: centre, edges, corners),
 // u_3 (edges, x^2 - y^2), u_4 (corners, xy) and u_5, u_6 (x-odd on edges and corners). With
@@ -798,7 +1129,21 @@ cudaError_t upload_sym(lsp_ctx* c) {
   e = cudaMemcpyToSymbol(c_ent, ent, sizeof(ent));
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(c_nent, &n, sizeof(int));
-  if (e != cudaSuccess || c->geo.d != 2) return e;
+  if (e != cudaSuccess) return e;
+  if (c->geo.d == 3) {
+    // coef[e][k] = sum of u_i[a] u_j[b] over the pairs (a, b) of class k, e = (block, i, j)
+    static double coef[24][kMaxCls];
+    memset(coef, 0, sizeof coef);
+    if (n != 24) return cudaErrorInvalidValue;
+    for (int q = 0; q < n; ++q) {
+      const int b = ent[q][0], i = ent[q][1], j = ent[q][2];
+      const double* ui = c->sym.u[c->sym.first[b] + i];
+      const double* uj = c->sym.u[c->sym.first[b] + j];
+      for (int a = 0; a < c->geo.mu; ++a)
+        for (int bb = 0; bb < c->geo.mu; ++bb) coef[q][c->geo.cls_of[a][bb]] += ui[a] * uj[bb];
+    }
+    return cudaMemcpyToSymbol(c_coef3, coef, sizeof coef);
+  }
   // W_i[k] = sum_a G[k, a] u_i[a] = sum_a g[cls(k, a)] u_i[a];  u_i^T A1 u_j = sum g2[cls(a,b)] u_i[a] u_j[b]
   static double W2[7][9][6], B2[7][7][6];
   memset(W2, 0, sizeof W2);
@@ -843,6 +1188,15 @@ cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int method
       k_eig2d<double><<<(int)b, 128, 0, c->stream>>>((const double*)c->gvals.p, cap, count,
                                                      (double*)c->alpha.p, (double*)c->cst.p,
                                                      (double*)c->lam.p, (int32_t*)c->sflags.p);
+    e = cudaGetLastError();
+  } else if (c->geo.d == 3 && method == LSP_EIG_SYMMETRIC && refine == 0) {
+    constexpr int kW = 4;
+    int64_t b = (cap + kW - 1) / kW;
+    if (b > 152 * 8) b = 152 * 8;
+    if (b < 1) b = 1;
+    k_eig3d<kW><<<(int)b, kW * 32, 0, c->stream>>>((const double*)c->gvals.p, cap, count,
+                                                   (double*)c->alpha.p, (double*)c->cst.p,
+                                                   (double*)c->lam.p, (int32_t*)c->sflags.p);
     e = cudaGetLastError();
   } else {
     e = c->geo.d == 2 ? launch_eig_t<9, 6, 8>(c, count, cap, method, refine)

@@ -548,22 +548,52 @@ __global__ void k_point_features(const double* __restrict__ v, int64_t N, float 
   }
 }
 
-// Normalised bf16 network inputs, written in the canonical K-major tile layout of the fused
-// kernel: 16 bytes (8 features of one row) per thread, consecutive threads writing
-// consecutive 16-byte units. Rows beyond M (the last tile's tail) are zero.
-//   rows mode: features of point j = xb over its 5^d patch (lexicographic offsets), then sb[j]
-//   batch mode: the raw features Xraw[j][0..NF), normalised here, also stored row-major (X16)
-//   for the backward pass
-template <int D, int MODE>
-__global__ void k_inputs(const __nv_bfloat16* __restrict__ xb,
-                         const __nv_bfloat16* __restrict__ sb, int logn,
-                         const float* __restrict__ Xraw, const float* __restrict__ params,
-                         int64_t norm_off, int64_t M, uint8_t* __restrict__ Xt,
-                         __nv_bfloat16* __restrict__ X16) {
+// Learned-build inputs in the canonical K-major tile layout of the fused kernel, one thread per
+// row (grid point j): the features xb over the 5^d patch of j (lexicographic offsets), then
+// sb[j], zero-padded to K0. Consecutive threads are consecutive points along the last axis,
+// so every patch offset is one coalesced load per warp. Rows beyond M (the last tile's tail)
+// are zero.
+template <int D>
+__global__ void k_inputs_rows(const __nv_bfloat16* __restrict__ xb,
+                              const __nv_bfloat16* __restrict__ sb, int logn, int64_t M,
+                              uint8_t* __restrict__ Xt) {
   constexpr int NF = D == 2 ? 26 : 126, NP = NF - 1;
+  constexpr int K0 = D == 2 ? 32 : 128;
+  const int64_t mask = ((int64_t)1 << logn) - 1;
+  const int64_t rows = (M + kTile - 1) / kTile * kTile;
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    const bool live = row < M;
+    uint8_t* tile = Xt + (row / kTile) * (int64_t)(kTile * K0 * 2);
+    const int r = (int)(row % kTile);
+#pragma unroll
+    for (int k8 = 0; k8 < K0; k8 += 8) {
+      __nv_bfloat16 f[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = k8 + i;
+        __nv_bfloat16 x = __float2bfloat16(0.0f);
+        if (live && k < NP) x = xb[nb_index<D, 2>(row, k, logn, mask)];
+        if (live && k == NP) x = sb[row];
+        f[i] = x;
+      }
+      *reinterpret_cast<uint4*>(tile + tc::kmajor_off(r, k8, K0)) =
+          *reinterpret_cast<const uint4*>(f);
+    }
+  }
+}
+
+// Training-batch inputs: the raw features Xraw[j][0..NF) normalised, bf16, written in the
+// canonical K-major tile layout of the fused kernel (16 bytes = 8 features of one row per
+// thread, consecutive threads writing consecutive 16-byte units) and row-major (X16) for the
+// backward pass. Rows beyond M (the last tile's tail) are zero.
+template <int D>
+__global__ void k_inputs_batch(const float* __restrict__ Xraw, const float* __restrict__ params,
+                               int64_t norm_off, int64_t M, uint8_t* __restrict__ Xt,
+                               __nv_bfloat16* __restrict__ X16) {
+  constexpr int NF = D == 2 ? 26 : 126;
   constexpr int K0 = D == 2 ? 32 : 128, KG = K0 / 8;
   const float mu_x = params[norm_off], isig_x = 1.0f / params[norm_off + 1];
-  const int64_t mask = ((int64_t)1 << logn) - 1;
   const int64_t units = (M + kTile - 1) / kTile * kTile * KG;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < units;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -575,18 +605,11 @@ __global__ void k_inputs(const __nv_bfloat16* __restrict__ xb,
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int k = kg * 8 + i;
-      __nv_bfloat16 x = __float2bfloat16(0.0f);
-      if (row < M && k < NF) {
-        if (MODE == kModeRows)
-          x = k < NP ? xb[nb_index<D, 2>(row, k, logn, mask)] : sb[row];
-        else
-          x = __float2bfloat16((Xraw[row * NF + k] - mu_x) * isig_x);
-      }
-      f[i] = x;
+      f[i] = __float2bfloat16(row < M && k < NF ? (Xraw[row * NF + k] - mu_x) * isig_x : 0.0f);
     }
     const uint4 q = *reinterpret_cast<const uint4*>(f);
     reinterpret_cast<uint4*>(Xt)[e] = q;
-    if (MODE == kModeBatch && row < M) reinterpret_cast<uint4*>(X16 + row * K0)[kg] = q;
+    if (row < M) reinterpret_cast<uint4*>(X16 + row * K0)[kg] = q;
   }
 }
 
@@ -910,14 +933,6 @@ size_t input_tile_bytes(int d, int64_t rows) {
 }
 
 template <int D, int MODE>
-cudaError_t launch_inputs(cudaStream_t st, const FusedParams& p, const __nv_bfloat16* xb,
-                          const __nv_bfloat16* sb, const float* Xraw, __nv_bfloat16* X16) {
-  k_inputs<D, MODE><<<152 * 8, 256, 0, st>>>(xb, sb, p.logn, Xraw, p.params, p.norm_off, p.M,
-                                             (uint8_t*)p.Xt, X16);
-  return cudaGetLastError();
-}
-
-template <int D, int MODE>
 cudaError_t launch_fused(lsp_mlp* m, const FusedParams& p, int64_t rows) {
   const size_t smem = FusedCfg<D>::smem;
   cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<D, MODE>,
@@ -993,9 +1008,13 @@ cudaError_t batch_forward(lsp_mlp* m, const float* X_dev, int64_t batch, float* 
     p.Hs[l] = (__nv_bfloat16*)m->Hs[l].p;
   }
   __nv_bfloat16* X16 = (__nv_bfloat16*)m->X16.p;
-  cudaError_t e =
-      m->dm.d == 2 ? launch_inputs<2, kModeBatch>(m->stream, p, nullptr, nullptr, X_dev, X16)
-                   : launch_inputs<3, kModeBatch>(m->stream, p, nullptr, nullptr, X_dev, X16);
+  if (m->dm.d == 2)
+    k_inputs_batch<2><<<152 * 8, 256, 0, m->stream>>>(X_dev, p.params, p.norm_off, batch,
+                                                      (uint8_t*)p.Xt, X16);
+  else
+    k_inputs_batch<3><<<152 * 8, 256, 0, m->stream>>>(X_dev, p.params, p.norm_off, batch,
+                                                      (uint8_t*)p.Xt, X16);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return m->dm.d == 2 ? launch_fused<2, kModeBatch>(m, p, batch)
                       : launch_fused<3, kModeBatch>(m, p, batch);
@@ -1267,14 +1286,20 @@ cudaError_t launch_learned_rows(lsp_ctx* c, lsp_mlp* m) {
   const float h2f = (float)(1.0 / ((double)c->geo.n * c->geo.n));
   cudaStream_t saved = m->stream;
   m->stream = c->stream;
-  int t0 = timer_begin(c, "mlp_inputs");
+  int t0 = timer_begin(c, "mlp_features");
   k_point_features<<<152 * 8, 256, 0, c->stream>>>((const double*)c->v.p, N, h2f, p.params,
                                                    p.norm_off, xb, sb, vh, vl, sh, sl);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess)
-    e = c->geo.d == 2 ? launch_inputs<2, kModeRows>(c->stream, p, xb, sb, nullptr, nullptr)
-                      : launch_inputs<3, kModeRows>(c->stream, p, xb, sb, nullptr, nullptr);
   timer_end(c, t0);
+  int t1 = timer_begin(c, "mlp_inputs");
+  if (e == cudaSuccess) {
+    if (c->geo.d == 2)
+      k_inputs_rows<2><<<152 * 8, 256, 0, c->stream>>>(xb, sb, logn, N, base);
+    else
+      k_inputs_rows<3><<<152 * 8, 256, 0, c->stream>>>(xb, sb, logn, N, base);
+    e = cudaGetLastError();
+  }
+  timer_end(c, t1);
   if (e == cudaSuccess) {
     int t = timer_begin(c, "mlp_rows");
     e = c->geo.d == 2 ? launch_fused<2, kModeRows>(m, p, c->geo.N)
