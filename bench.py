@@ -166,6 +166,13 @@ def kernel_work(name: str, n: int, d: int, N: int, mu: int, sizes: list[int]):
         return N * (8 + 3 * mu * 8), "byte"
     if name == "stats":
         return N * 8, "byte"
+    if name == "mlp_rows":
+        # the network's dense contractions: (5^d + 1) -> 256 -> 256 -> 256 -> 2|mu|
+        nf = 5 ** d + 1
+        return N * 2 * (nf * 256 + 2 * 256 * 256 + 256 * 2 * mu), "tensor_flop"
+    if name == "mlp_inputs":
+        # read the bf16 feature of every point, write the bf16 input tiles (K0 = 32 / 128)
+        return N * (2 + (32 if d == 2 else 128) * 2), "byte"
     return None
 
 
@@ -206,6 +213,12 @@ def run_ours(args):
     v_dev = torch.from_numpy(v_host).to("cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
+    mlp = None
+    train_info = None
+    if args.mode == "learned":
+        mlp, train_info = train_for(torch, args.workload, args.learned_steps, stream)
+        ctx.set_mlp(mlp)
+
     def step():
         ctx.set_potential(v_dev)
         ctx.build_stencils(policy=args.policy, mode=args.mode, use_graph=True)
@@ -214,9 +227,12 @@ def run_ours(args):
         for _ in range(args.warmup):
             step()
         ctx.synchronize()
-        tab = ctx.get_shift_table(with_sidx=False)
-        ns = len(tab["s"])
-        m_list = np.round((tab["s"] / (np.pi ** 2) - 2) / 4).astype(np.int64)
+        if ctx.mode_used() == "learned":  # no shift table: the network replaces a2-a6
+            ns, m_list = None, None
+        else:
+            tab = ctx.get_shift_table(with_sidx=False)
+            ns = len(tab["s"])
+            m_list = np.round((tab["s"] / (np.pi ** 2) - 2) / 4).astype(np.int64)
 
         # ---- timed region: K steps, graph replay, L2 flushed before each ----
         if ws > 1:
@@ -276,7 +292,7 @@ def run_ours(args):
 
     value = job_throughput(N, args.steps, ws, total_ms)
     peaks, peak_src = load_peaks()
-    sizes = lattice_domain_sizes(m_list, n, d)
+    sizes = lattice_domain_sizes(m_list, n, d) if m_list is not None else []
     launches = int(sum(c for _, c in ktimes.values()))
     kern = {}
     for name, (ms, cnt) in ktimes.items():
@@ -284,12 +300,19 @@ def run_ours(args):
         kern[name] = {"ms_per_launch": ms / max(cnt, 1), "launches": cnt}
         if w:
             per = w[0] / (ms / max(cnt, 1) * 1e-3)
-            kern[name]["achieved"] = per / (1e12 if w[1] == "flop" else 1e9)
-            kern[name]["unit"] = "TFLOP/s" if w[1] == "flop" else "GB/s"
+            flops = w[1] in ("flop", "tensor_flop")
+            kern[name]["achieved"] = per / (1e12 if flops else 1e9)
+            kern[name]["unit"] = "TFLOP/s" if flops else "GB/s"
     dom = max(ktimes.items(), key=lambda kv: kv[1][0])[0]
     fp64_peak = measure_fp64_peak(torch)
     w = kernel_work(dom, n, d, N, mu, sizes)
-    if w and w[1] == "flop":
+    if w and w[1] == "tensor_flop":
+        roof = {"bound": "tensor", "kernel": dom, "achieved": kern[dom]["achieved"],
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": kern[dom]["achieved"] / peaks["bf16_tflops"], "traffic": None,
+                "peak_source": f"MEASURED_PEAKS.json bf16_tflops, burst ({peak_src})",
+                "work_per_launch": w[0]}
+    elif w and w[1] == "flop":
         roof = {"bound": "alu", "kernel": dom, "achieved": kern[dom]["achieved"],
                 "peak": fp64_peak, "unit": "TFLOP/s",
                 "frac": kern[dom]["achieved"] / fp64_peak, "traffic": None,
@@ -309,11 +332,11 @@ def run_ours(args):
         "metric": "local stencils/sec (Q, C, P rows of every grid point, steps a1-a7)",
         "value": value, "unit": "stencils/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.mode == "fp64" else "f32+f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "learned": "bf16+f32"}[args.mode],
         "data": "synthetic",
         "config": {"workload": args.workload, "text": WORKLOAD_TEXT.get(args.workload, ""),
                    "policy": args.policy, "mode": args.mode, "d": d, "n": n, "points": N,
-                   "shifts": ns, "lattice_domains": sizes,
+                   "shifts": ns, "lattice_domains": sizes, "mode_used": ctx.mode_used(),
                    "l2": "flushed before every timed step (256 MiB write), outside the step events",
                    "parallelism": f"replicas x{ws} (independent potentials)"},
         "roofline": roof,
@@ -328,6 +351,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(N * 8), "d2h_bytes_per_step": int(3 * N * mu * 8),
                 "ms_per_step": float(np.median(e2e_ms))},
     }
+    if train_info is not None:
+        out["config"]["training"] = train_info
     if not args.no_variants:
         out["variants"] = variants(args, torch)
     if ws == 1 and not args.no_cpu_baseline:
@@ -372,7 +397,12 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
         if used == "learned":
             q_learned = ctx.get_rows("Q").copy()
             ctx.build_stencils(policy=policy, mode="fp64")
-            extra["max_abs_dalpha_vs_fp64"] = float(np.abs(q_learned - ctx.get_rows("Q")).max())
+            err = np.abs(q_learned - ctx.get_rows("Q")).max(axis=1)  # per point
+            extra["max_abs_dalpha_vs_fp64"] = float(err.max())
+            extra["dalpha_vs_fp64_per_point"] = {
+                "p50": float(np.percentile(err, 50)), "p99": float(np.percentile(err, 99)),
+                "p99.9": float(np.percentile(err, 99.9)), "max": float(err.max()),
+                "frac_above_1e-2": float(np.mean(err > 1e-2))}
             ctx.build_stencils(policy=policy, mode=mode, use_graph=True)
         ctx.kernel_timing(True)
         for _ in range(5):
@@ -390,24 +420,30 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
     return out
 
 
-def learned_variant(torch, workload: str, steps: int = 3000):
-    """Train the surrogate on 16 other seeds of the workload, then time the learned build."""
+def train_for(torch, workload: str, steps: int, stream):
+    """Train the surrogate on 16 other seeds (100-115) of the workload."""
     from lsp_inputs import make_workload
     from paper_1607_02560_gb300.learned import train_surrogate
 
-    stream = torch.cuda.Stream()
     pots = [make_workload(workload, seed=s) for s in range(100, 116)]
     t0 = time.time()
     with torch.cuda.stream(stream):
         mlp, losses = train_surrogate(pots[0].ndim, pots, samples_per_potential=65536,
                                       steps=steps, batch=4096, lr=2e-3, stream=stream)
     torch.cuda.synchronize()
-    t_train = time.time() - t0
+    info = {"potentials": len(pots), "seeds": "100-115", "pairs": 16 * 65536, "steps": steps,
+            "batch": 4096, "seconds": round(time.time() - t0, 2),
+            "final_loss": float(np.mean(losses[-50:]))}
+    return mlp, info
+
+
+def learned_variant(torch, workload: str, steps: int = 3000):
+    """Train the surrogate on 16 other seeds of the workload, then time the learned build."""
+    stream = torch.cuda.Stream()
+    mlp, info = train_for(torch, workload, steps, stream)
     out = time_config(torch, workload, "local", "learned", steps=20, warmup=3, mlp=mlp,
                       stream=stream)
-    out["training"] = {"potentials": len(pots), "pairs": 16 * 65536, "steps": steps,
-                       "batch": 4096, "seconds": round(t_train, 2),
-                       "final_loss": float(np.mean(losses[-50:]))}
+    out["training"] = info
     mlp.close()
     return out
 
@@ -428,7 +464,7 @@ def variants(args, torch):
     if not args.no_learned:
         for wl in ("helm2d_n1024", "schr3d_n64"):
             try:
-                out.append(learned_variant(torch, wl))
+                out.append(learned_variant(torch, wl, args.learned_steps))
             except Exception as exc:
                 out.append({"workload": wl, "mode": "learned", "error": str(exc)[:300]})
     return out
@@ -499,7 +535,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="helm2d_n1024")
     ap.add_argument("--policy", default="local", choices=["local", "paper", "mean"])
-    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed", "learned"])
+    ap.add_argument("--learned-steps", type=int, default=3000,
+                    help="training steps of the surrogate (learned mode and variants)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip training the surrogate")
     ap.add_argument("--n", type=int, default=None, help="rescale the workload's grid (small cases)")
