@@ -41,7 +41,7 @@ __all__ = [
     "neighbourhood_offsets", "kernel_vectors", "gram_matrix", "near_null",
     "stencil_for_shift", "build_stencils", "rows_to_csr", "sparse_matrices",
     "gmres_solve", "dense_green_matrix", "brute_force_stencil", "sign_fix",
-    "local_shift_indices", "gather_offsets",
+    "local_shift_indices", "gather_offsets", "t_choice", "build_stencils_multi",
 ]
 
 PI2 = math.pi * math.pi  # pi^2 as one correctly rounded product of the float64 pi
@@ -277,6 +277,73 @@ def build_stencils(v: np.ndarray, policy: str = "local", nshifts: int | None = N
     P = Q + C * (vnb - S[idx][:, None])
     return dict(m=m_arr, S=S, s_idx=s_idx, alpha=alpha, c=cst, lam1=lam1, degenerate=degen,
                 Q=Q, C=C, P=P, offsets=offs)
+
+
+# --------------------------------------------------------------------------------------------
+# Sec. 4.2: per-point neighbourhood size t_j from the nested-dissection geometry
+# --------------------------------------------------------------------------------------------
+
+def t_choice(n: int, d: int, leaf: int = 8, t_max: int = 2) -> np.ndarray:
+    """t_j for every point (Sec. 4.2 and its figure of t choices), shape (n,)*d.
+
+    Nested dissection with leaf boxes of width `leaf` puts separators on the grid lines
+    x_a = 0 (mod leaf). Two points of different boxes must not interact, so t_j is the largest
+    t with mu_j^t inside the closed box of j along every axis: along an axis where j is not on
+    a separator (r = x_a mod leaf > 0) that is min(r, leaf - r); along an axis where it is, the
+    neighbourhood may reach the next separator line, i.e. leaf. t_j is the minimum over the
+    axes, capped by t_max (the largest t for which stencils are built). With leaf = 4 and
+    t_max = 4 this reproduces the paper's 16 x 16 example point by point.
+    """
+    x = np.indices((n,) * d)
+    r = x % leaf
+    f = np.where(r == 0, leaf, np.minimum(r, leaf - r))
+    return np.minimum(f.min(axis=0), t_max).astype(np.int64)
+
+
+def build_stencils_multi(v: np.ndarray, policy: str = "paper", nshifts: int | None = None,
+                         m_list=None, leaf: int = 8, t_max: int = 2, t_of=None):
+    """Rows with per-point neighbourhoods mu_j^{t_j} (Sec. 4.2):
+
+    Q[j, mu_j^{t_j}] = (alpha_{s_j}^{t_j})^T, C[j, .] = Q[j, .] G_{s_j}[mu_j^{t_j}, mu_j^{t_j}],
+    P[j, .] = Q[j, .] + C[j, .] diag(v[mu_j^{t_j}] - s_j),
+
+    with t_j from t_choice (or the array t_of) and s_j from the shift policy as in
+    build_stencils. A stencil (alpha_s^t, c_s^t) is computed for every (shift, t) pair that
+    some point uses. Returns scipy CSR matrices Q, C, P (columns of each row in the
+    lexicographic offset order of mu^{t_j}) and the per-(shift, t) tables.
+    """
+    n, d = v.shape[0], v.ndim
+    base = build_stencils(v, policy, nshifts=nshifts, m_list=m_list, shift_subset=[])
+    S, s_idx = base["S"], base["s_idx"].reshape(-1)
+    tj = (t_choice(n, d, leaf, t_max) if t_of is None else np.asarray(t_of)).reshape(-1)
+    N = n ** d
+    tables = {}
+    for t in sorted(set(int(x) for x in tj)):
+        used = sorted(set(int(i) for i in s_idx[tj == t]))
+        for i in used:
+            st = stencil_for_shift(n, d, float(S[i]), t)
+            tables[(i, t)] = st
+    coords = np.stack(np.unravel_index(np.arange(N), (n,) * d), axis=-1)
+    rows = {k: [] for k in "QCP"}
+    cols, ptr = [], [0]
+    flat_v = v.reshape(-1)
+    for j in range(N):
+        t = int(tj[j])
+        st = tables[(int(s_idx[j]), t)]
+        offs = neighbourhood_offsets(d, t)
+        cj = np.ravel_multi_index(tuple(((coords[j] + offs) % n).T), (n,) * d)
+        q, c = st["alpha"], st["c"]
+        rows["Q"].append(q)
+        rows["C"].append(c)
+        rows["P"].append(q + c * (flat_v[cj] - S[s_idx[j]]))
+        cols.append(cj)
+        ptr.append(ptr[-1] + len(offs))
+    colidx = np.concatenate(cols)
+    indptr = np.asarray(ptr, dtype=np.int64)
+    mats = {k: scipy.sparse.csr_matrix((np.concatenate(rows[k]), colidx, indptr), shape=(N, N))
+            for k in "QCP"}
+    return dict(S=S, s_idx=base["s_idx"], t=tj.reshape(v.shape), tables=tables,
+                Q=mats["Q"], C=mats["C"], P=mats["P"])
 
 
 def rows_to_csr(rows: np.ndarray, n: int, d: int, t: int = 1) -> scipy.sparse.csr_matrix:

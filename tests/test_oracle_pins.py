@@ -103,14 +103,15 @@ def test_kernel_vector_matches_direct_sum(n, d, m):
 
 # ---- Sec. 3 / 4.2: Eq. A against the dense Green's matrix and its SVD --------------------
 
-@pytest.mark.parametrize("n,d,m", [(8, 2, -8), (10, 2, -12), (12, 2, -18), (8, 2, 3),
-                                   (6, 3, -5), (8, 3, -9)])
-def test_gram_identity_and_svd_match_dense(n, d, m):
+@pytest.mark.parametrize("n,d,m,t", [(8, 2, -8, 1), (10, 2, -12, 1), (12, 2, -18, 1),
+                                     (8, 2, 3, 1), (6, 3, -5, 1), (8, 3, -9, 1),
+                                     (10, 2, -12, 2), (12, 2, -18, 2), (12, 2, 3, 2)])
+def test_gram_identity_and_svd_match_dense(n, d, m, t):
     s = float(O.shift_value(m))
-    st = O.stencil_for_shift(n, d, s)
-    offs = O.neighbourhood_offsets(d)
+    st = O.stencil_for_shift(n, d, s, t)
+    offs = O.neighbourhood_offsets(d, t)
     for j in [(0,) * d, tuple(range(1, d + 1)), (n - 1,) * d]:
-        alpha, sig, mu, G = O.brute_force_stencil(n, d, s, j)
+        alpha, sig, mu, G = O.brute_force_stencil(n, d, s, j, t)
         comp = sorted(set(range(n ** d)) - set(mu))
         B = G[np.ix_(mu, comp)]
         A_dense = B @ B.T
@@ -122,7 +123,7 @@ def test_gram_identity_and_svd_match_dense(n, d, m):
         # C[j, mu] = Q[j, mu] G[mu, mu]
         c_dense = alpha @ G[np.ix_(mu, mu)]
         assert np.abs(c_dense - st["c"]).max() <= 1e-9 * np.abs(c_dense).max()
-    assert len(offs) == 3 ** d
+    assert len(offs) == (2 * t + 1) ** d
 
 
 def test_gram_is_positive_semidefinite():
@@ -248,6 +249,71 @@ def test_unpreconditioned_gmres_stalls():
     assert info != 0 and res > 1e-3
 
 
+# ---- Sec. 4.2: per-point neighbourhood size t_j from the nested-dissection geometry -------
+
+def test_t_choice_reproduces_the_paper_figure():
+    with open(os.path.join(GOLDEN, "tchoice_fig_16x16.json")) as fh:
+        fig = json.load(fh)
+    T = O.t_choice(16, 2, leaf=fig["leaf"], t_max=fig["t_max_drawn"])
+    assert np.array_equal(T, np.array(fig["grid"]))
+
+
+@pytest.mark.parametrize("n,d,leaf", [(32, 2, 8), (16, 2, 4), (16, 3, 8)])
+def test_t_choice_keeps_boxes_apart_and_is_maximal(n, d, leaf):
+    # the sparsity requirement of nested dissection, stated independently of the rule: an
+    # interaction between j and i may not cross an edge, i.e. along no axis may a separator
+    # line (a multiple of leaf; the periodic seam is one) lie strictly between j_a and i_a.
+    # t_j (uncapped) must satisfy it for all of mu_j^{t_j}, and t_j + 1 must not.
+    T = O.t_choice(n, d, leaf=leaf, t_max=10 * leaf)
+
+    def crosses(j, t):
+        for a in range(d):
+            for i_a in (j[a] - t, j[a] + t):  # the extreme offsets decide along each axis
+                lo, hi = min(j[a], i_a), max(j[a], i_a)
+                if any(m % leaf == 0 for m in range(lo + 1, hi)):
+                    return True
+        return False
+
+    for j in np.ndindex(*(n,) * d):
+        t = int(T[j])
+        assert 1 <= t <= leaf
+        assert not crosses(j, t) and crosses(j, t + 1), (j, t)
+
+
+def test_multi_t_rows_reduce_to_the_uniform_build():
+    v = make_workload("helm2d_n32")
+    for pol in ("paper", "local"):
+        ref = O.build_stencils(v, pol)
+        for t in (1, 2):
+            multi = O.build_stencils_multi(v, pol, t_of=t * np.ones(v.shape, dtype=np.int64))
+            if t == 1:
+                Q, C, P = O.sparse_matrices(ref, 32, 2)
+            else:
+                ref2 = O.build_stencils(v, pol, t=2)
+                Q, C, P = O.sparse_matrices(ref2, 32, 2, t=2)
+            for a, b in ((Q, multi["Q"]), (C, multi["C"]), (P, multi["P"])):
+                assert (a != b).nnz == 0
+    # mixed t: every row has (2 t_j + 1)^d entries at its own neighbourhood
+    st = O.build_stencils_multi(v, "paper")
+    lens = np.diff(st["Q"].indptr)
+    assert np.array_equal(lens, (2 * st["t"].reshape(-1) + 1) ** 2)
+
+
+def test_multi_t_gmres_counts_match_golden():
+    with open(os.path.join(GOLDEN, "gmres_multi_t_helm2d_n32.json")) as fh:
+        gold = json.load(fh)["iterations"]
+    v = make_workload("helm2d_n32")
+    f = gaussian_source(32, 2, 2.0)
+    for key, want in gold.items():
+        pol, label = key.split("/")
+        kw = {} if label == "nd8" else {"t_of": 2 * np.ones(v.shape, dtype=np.int64)}
+        st = O.build_stencils_multi(v, pol, **kw)
+        _, it, res, info = O.gmres_solve(v, f, st["P"], st["C"])
+        assert info == 0 and it == want and res < 1e-4, (key, it, want)
+        # within the paper's range for this method (Sec. 5 tables: 5-12)
+        assert 2 <= it <= 12
+
+
 # ---- planted mistakes: each must be caught by one of the pins above ---------------------
 
 def _dense_A(n, d, s):
@@ -293,3 +359,20 @@ def test_pins_catch_planted_mistakes(monkeypatch, mutation):
     caught = (np.abs(st["A"] - A_ref).max() > 1e-12 * np.abs(A_ref).max()
               or np.abs(st["alpha"] - alpha_ref).max() > 1e-9)
     assert caught
+
+
+@pytest.mark.parametrize("mutation", ["separators_like_boxes", "leaf_off_by_one"])
+def test_t_choice_pins_catch_planted_mistakes(mutation):
+    # plausible slips in the t_j rule, each caught by the paper's figure
+    with open(os.path.join(GOLDEN, "tchoice_fig_16x16.json")) as fh:
+        fig = json.load(fh)
+    x = np.indices((16, 16))
+    leaf = fig["leaf"]
+    if mutation == "separators_like_boxes":
+        r = x % leaf
+        T = np.minimum(np.where(r == 0, 0, np.minimum(r, leaf - r)).min(axis=0), 4)
+    else:
+        r = x % (leaf + 1)
+        T = np.minimum(np.where(r == 0, leaf + 1, np.minimum(r, leaf + 1 - r)).min(axis=0), 4)
+    assert not np.array_equal(T, np.array(fig["grid"]))
+    assert np.array_equal(O.t_choice(16, 2, leaf=leaf, t_max=4), np.array(fig["grid"]))
