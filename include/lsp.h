@@ -65,7 +65,8 @@ typedef enum {
 #define LSP_FLAG_NOT_CONVERGED 4 /* Jacobi hit its sweep limit                                 */
 
 typedef struct {
-  int t;               /* neighbourhood radius; this build supports t = 1 (|mu| = 3^d)         */
+  int t;               /* neighbourhood radius t of mu_j^t (Sec. 4.2): 1 (|mu| = 3^d), or 2    */
+                       /* in 2D (|mu| = 25; rows are 25 wide, see nd_leaf)                    */
   int policy;          /* lsp_shift_policy                                                     */
   int nshifts;         /* PAPER: |S| before de-duplication; 0 selects n/16 (2D) or n/4 (3D)   */
   const double* shifts;/* LIST: nshifts shift values in host memory, each (4m+2) pi^2          */
@@ -73,9 +74,17 @@ typedef struct {
   int refine_steps;    /* inverse-iteration steps applied to each near-null vector (0 or 1)   */
   int eig_method;      /* lsp_eig_method                                                       */
   int use_graph;       /* 1: record the launch sequence once per configuration, replay it     */
+  int nd_leaf;         /* t = 2 only. 0: every point uses mu_j^2. b > 0 (even, dividing n):   */
+                       /* point j uses t_j = min(2, T_b(j)), the largest t whose neighbourhood */
+                       /* crosses no separator line x_a = 0 (mod b) of a nested dissection    */
+                       /* with leaf boxes of width b (Sec. 4.2, figure of t choices: along an */
+                       /* axis with r = x_a mod b > 0 the bound is min(r, b - r), on a        */
+                       /* separator it is b). Rows stay 25 wide: a t_j = 1 row fills its inner */
+                       /* 3 x 3 columns and holds zeros elsewhere; the CSR export omits them. */
 } lsp_stencil_opts;
 
-/* Fill *opts with the defaults: t=1, LOCAL policy, FP64, symmetric eigen-solve, no graph. */
+/* Fill *opts with the defaults: t=1, LOCAL policy, FP64, symmetric eigen-solve, no graph,
+ * nd_leaf = 0. */
 void lsp_default_opts(lsp_stencil_opts* opts);
 
 /*
@@ -110,8 +119,11 @@ lsp_status lsp_set_potential(lsp_ctx* ctx, const double* v, int v_on_device);
  * Asynchronous on the context stream (except LIST/PAPER/MEAN, which upload a small shift list
  * from pinned host memory). Results stay on the device until read with lsp_get_rows(),
  * lsp_export_sparse_rows() or lsp_get_shift_table(). opts = NULL uses lsp_default_opts().
+ * With t = 2 (2D) the same steps run on mu^2 (25 offsets; g_s at offsets up to 4) and, when
+ * nd_leaf > 0, also on mu^1 for the points with t_j = 1 (Sec. 4.2).
  * Errors: LSP_ERR_STATE without a potential; LSP_ERR_ARG for bad options or an off-lattice
- * LIST shift; LSP_ERR_RESONANT_SHIFT for a LIST shift equal to -4 pi^2 |k|^2 for a k in K.
+ * LIST shift; LSP_ERR_RESONANT_SHIFT for a LIST shift equal to -4 pi^2 |k|^2 for a k in K;
+ * LSP_ERR_UNSUPPORTED for t = 2 in 3D or with the LEARNED mode.
  */
 lsp_status lsp_build_stencils(lsp_ctx* ctx, const lsp_stencil_opts* opts);
 
@@ -124,15 +136,17 @@ lsp_status lsp_apply_operator(lsp_ctx* ctx, const double* u_dev, double* y_dev);
 
 /*
  * Copy the dense row block of Q, C or P (which = 'Q', 'C', 'P'): n^d x |mu| float64,
- * row j at rows[j * |mu| ...], in mu_0 offset order. on_device = 1: rows is a device pointer
+ * row j at rows[j * |mu| ...], in mu_0 offset order (|mu| = (2t+1)^d of the last build, as
+ * lsp_get_sizes reports it). on_device = 1: rows is a device pointer
  * (asynchronous copy); 0: host pointer (the call waits for the copy).
  */
 lsp_status lsp_get_rows(lsp_ctx* ctx, char which, double* rows, int on_device);
 
 /*
  * Export Q, C or P as CSR in host memory: rowptr[n^d + 1] (int64), colidx[nnz] (int32),
- * vals[nnz] (float64), nnz = n^d |mu|. Column indices of a row follow the mu_0 offset order,
- * so they are not sorted where the neighbourhood wraps around the periodic boundary.
+ * vals[nnz] (float64), nnz = n^d |mu| (t = 2 builds with nd_leaf > 0: the sum over points
+ * of (2 t_j + 1)^2). Column indices of a row follow the mu_j^{t_j} offset order, so they are
+ * not sorted where the neighbourhood wraps around the periodic boundary.
  * With rowptr, colidx and vals all NULL only *nnz_out is written (size query). Waits for the
  * copies before returning.
  */
@@ -140,8 +154,9 @@ lsp_status lsp_export_sparse_rows(lsp_ctx* ctx, char which, int64_t* rowptr, int
                                   double* vals, int64_t* nnz_out);
 
 /*
- * Read the per-shift table of the last build into host memory (Sec. 4.1: "only needs to be
- * computed once for different locations sharing the same shift"). *nshifts_out receives |S|.
+ * Read the per-shift table of the last build into host memory (Sec. 4.1: one stencil per
+ * shift, shared by every point that uses that shift). *nshifts_out receives |S|. For a t = 2
+ * build the table holds the t = 2 stencils (|mu| = 25).
  * Any output pointer may be NULL. s[|S|] shift values (increasing), alpha[|S| x |mu|],
  * c[|S| x |mu|], lam[|S| x 2] = (lambda_1, lambda_2) of A, flags[|S|] (LSP_FLAG_* bits),
  * s_idx[n^d] = index into s of each point's shift s_j. Waits before returning.

@@ -31,9 +31,10 @@ __constant__ int c_nent;
 // Rotations follow the standard choice tan(phi) = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
 // theta = (a_qq - a_pp) / (2 a_pq); off-diagonal entries at or below 1e-17 sqrt|a_pp a_qq| are
 // treated as converged (relative criterion, accurate for positive semidefinite matrices).
-__device__ int jacobi_small(double a[4][4], double v[4][4], int dim) {
-  for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) v[i][j] = (i == j) ? 1.0 : 0.0;
+template <int NM>
+__device__ int jacobi_nm(double (&a)[NM][NM], double (&v)[NM][NM], int dim) {
+  for (int i = 0; i < NM; ++i)
+    for (int j = 0; j < NM; ++j) v[i][j] = (i == j) ? 1.0 : 0.0;
   for (int sweep = 0; sweep < 40; ++sweep) {
     bool rotated = false;
     for (int p = 0; p < dim - 1; ++p) {
@@ -72,6 +73,10 @@ __device__ int jacobi_small(double a[4][4], double v[4][4], int dim) {
     if (!rotated) return 1;
   }
   return 0;
+}
+__device__ int jacobi_small(double a[4][4], double v[4][4], int dim) {
+  return jacobi_nm<4>(*reinterpret_cast<double(*)[4][4]>(a), *reinterpret_cast<double(*)[4][4]>(v),
+                      dim);
 }
 
 // Per-block copies of the class table and the symmetry-adapted vectors: the warp kernel
@@ -845,6 +850,431 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig3d(const double* __restrict__
   }
 }
 
+// ---- 2D, t = 2: one warp per shift, blocks of mu_0^2 formed from the class values ----------
+// mu_0^2 is the 5 x 5 neighbourhood; its symmetry blocks (host-built basis, see build_sym_t2)
+// are A1 (6 x 6), E (6 x 6, two partners), B1 (3 x 3), B2 (3 x 3) and A2 (1 x 1). As in 3D,
+// G maps every block's span into itself, so B_b = U_b^T A1 U_b - G_b G_b with both terms linear
+// in the 15 class values through one coefficient table (55 entries). The 6 x 6 blocks are
+// solved one after the other on the whole warp as 8 x 8 matrices (two entries per lane, the
+// padding decoupled on the diagonal above the block's spectrum): LDL^T of B + delta I column by
+// column, the inverse by lanes 0-7 (one column each), seven scaled squarings, Rayleigh quotient
+// and residual; the next eigenvalue from three squarings of the deflated inverse. The 3 x 3
+// blocks run side by side on the two half-warps (4 x 4 padded, as in 3D); A2 is 1 x 1.
+constexpr int kT2Ent = 55;
+__constant__ double c_coef2[kT2Ent][kMaxCls];
+__constant__ int8_t c_ent2[kT2Ent][3];
+__constant__ SymBasis c_sym2;
+
+struct EigT2Warp {
+  double g[2 * 15];
+  double Gb[5][64];   // 8 x 8 padded blocks (row stride 8)
+  double B[5][64];
+  double L[64], dd[8], dinv[8];
+  double M[64], M0[64];
+  double M4[2][16];   // the two half-warps' 4 x 4 matrices
+  double v[5][8];     // eigenvector (block coordinates) of each block's smallest eigenvalue
+  double lam[5][2];
+  double tr[5];
+  int conv[5];
+};
+
+// Smallest eigenpair (and next eigenvalue) of the block b (dim <= 6) held in sm.B[b], on the
+// whole warp. Writes sm.v[b], sm.lam[b], sm.tr[b], sm.conv[b].
+__device__ void warp_block_eig8(EigT2Warp& sm, int b, int dim, int lane) {
+  const double* Bb = sm.B[b];
+  const int r0 = lane >> 3, r1 = r0 + 4, cc = lane & 7;
+  // scale and trace of the block
+  double sc = fmax(fabs(Bb[r0 * 8 + cc]), fabs(Bb[r1 * 8 + cc]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sc = fmax(sc, __shfl_xor_sync(0xffffffffu, sc, o));
+  double tr = 0.0;
+  for (int k = 0; k < dim; ++k) tr += Bb[k * 9];
+  const double pad = 4.0 * sc * dim + 1.0;  // above every eigenvalue of the block
+  const double delta = 1e-13 * fabs(tr);
+  // S = B + delta I with the padding, into M (lane-parallel)
+  auto S_at = [&](int r, int c) {
+    const double x = (r < dim && c < dim) ? Bb[r * 8 + c] : (r == c ? pad : 0.0);
+    return r == c ? x + delta : x;
+  };
+  sm.M[r0 * 8 + cc] = S_at(r0, cc);
+  sm.M[r1 * 8 + cc] = S_at(r1, cc);
+  __syncwarp();
+  // LDL^T, one column at a time; lane i (j < i < 8) forms L[i][j]
+  bool fact = true;
+  for (int j = 0; j < 8; ++j) {
+    double dj = sm.M[j * 9];
+    for (int k = 0; k < j; ++k) dj -= sm.L[j * 8 + k] * sm.L[j * 8 + k] * sm.dd[k];
+    if (!(dj > 0.0)) fact = false;
+    const double idj = 1.0 / dj;
+    if (lane > j && lane < 8) {
+      double a = sm.M[lane * 8 + j];
+      for (int k = 0; k < j; ++k) a -= sm.L[lane * 8 + k] * sm.L[j * 8 + k] * sm.dd[k];
+      sm.L[lane * 8 + j] = a * idj;
+    }
+    if (lane == 0) {
+      sm.dd[j] = dj;
+      sm.dinv[j] = idj;
+    }
+    __syncwarp();
+  }
+  // M0 = (L D L^T)^-1: lane c < 8 forms column c
+  if (lane < 8) {
+    double x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = k == lane ? 1.0 : 0.0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int k = 0; k < i; ++k) x[i] = fma(-sm.L[i * 8 + k], x[k], x[i]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] *= sm.dinv[i];
+#pragma unroll
+    for (int i = 7; i >= 0; --i)
+#pragma unroll
+      for (int k = i + 1; k < 8; ++k) x[i] = fma(-sm.L[k * 8 + i], x[k], x[i]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) sm.M0[i * 8 + lane] = fact ? x[i] : (i == lane ? 1.0 : 0.0);
+  }
+  __syncwarp();
+  const double m00 = sm.M0[r0 * 8 + cc], m01 = sm.M0[r1 * 8 + cc];
+  sm.M[r0 * 8 + cc] = m00;
+  sm.M[r1 * 8 + cc] = m01;
+  __syncwarp();
+  auto square = [&](int rounds) {
+    for (int k = 0; k < rounds; ++k) {
+      double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        s0 = fma(sm.M[r0 * 8 + q], sm.M[q * 8 + cc], s0);
+        s1 = fma(sm.M[r1 * 8 + q], sm.M[q * 8 + cc], s1);
+      }
+      double t8 = 0.0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t8 += sm.M[q * 9];
+      const double p2 = pow2_inv_exp_sq(t8);
+      __syncwarp();
+      sm.M[r0 * 8 + cc] = s0 * p2;
+      sm.M[r1 * 8 + cc] = s1 * p2;
+      __syncwarp();
+    }
+  };
+  auto dominant = [&](double (&vv)[8]) {
+    int jm = 0;
+    for (int q = 1; q < 8; ++q)
+      if (sm.M[q * 9] > sm.M[jm * 9]) jm = q;
+    double n2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      vv[q] = q < dim ? sm.M[q * 8 + jm] : 0.0;
+      n2 = fma(vv[q], vv[q], n2);
+    }
+    const double inv = n2 > 0.0 ? rsqrt(n2) : 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) vv[q] *= inv;
+  };
+  // Rayleigh quotient v^T B v and residual max |B v - lambda v| (lanes 0-7 form one row each)
+  auto rayleigh = [&](const double (&vv)[8], double* res) {
+    double row = 0.0;
+    if (lane < dim)
+      for (int q = 0; q < dim; ++q) row = fma(Bb[lane * 8 + q], vv[q], row);
+    double bv[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) bv[q] = __shfl_sync(0xffffffffu, row, q);
+    double lam = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) lam = fma(vv[q], bv[q], lam);
+    double rr = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (q < dim) rr = fmax(rr, fabs(fma(-lam, vv[q], bv[q])));
+    *res = rr;
+    return lam;
+  };
+  square(7);
+  double v1[8], res1;
+  dominant(v1);
+  const double lam1 = rayleigh(v1, &res1);
+  const int conv = fact && isfinite(lam1) && res1 <= 64.0 * DBL_EPSILON * sc;
+  // next eigenvalue: M0 deflated by (v1, mu1), three squarings
+  double part = v1[r0] * m00 * v1[cc] + v1[r1] * m01 * v1[cc];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  __syncwarp();
+  sm.M[r0 * 8 + cc] = fma(-part * v1[r0], v1[cc], m00);
+  sm.M[r1 * 8 + cc] = fma(-part * v1[r1], v1[cc], m01);
+  __syncwarp();
+  square(3);
+  double v2[8], res2;
+  dominant(v2);
+  double lam2 = dim > 1 ? rayleigh(v2, &res2) : DBL_MAX;
+  if (dim > 1 && !(v2[0] != 0.0 || v2[1] != 0.0 || v2[2] != 0.0 || v2[3] != 0.0 ||
+                   v2[4] != 0.0 || v2[5] != 0.0))
+    lam2 = lam1;
+  if (lane == 0) {
+    sm.lam[b][0] = lam1;
+    sm.lam[b][1] = lam2;
+    sm.tr[b] = tr;
+    sm.conv[b] = conv;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) sm.v[b][q] = v1[q];
+  }
+  __syncwarp();
+}
+
+template <int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) k_eig2d_t2(const double* __restrict__ gvals,
+                                                         int64_t cap,
+                                                         const int32_t* __restrict__ count,
+                                                         double* __restrict__ alpha_out,
+                                                         double* __restrict__ c_out,
+                                                         double* __restrict__ lam_out,
+                                                         int32_t* __restrict__ flags_out) {
+  constexpr int MU = 25, NCLS = 15, CENTRE = 12;
+  __shared__ double s_coef[kT2Ent][NCLS];
+  __shared__ double s_u[kMaxSymVec][MU];
+  __shared__ int8_t s_ent[kT2Ent][3];
+  __shared__ EigT2Warp sw[WARPS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < kT2Ent * NCLS; e += WARPS * 32)
+    s_coef[e / NCLS][e % NCLS] = c_coef2[e / NCLS][e % NCLS];
+  for (int e = threadIdx.x; e < kMaxSymVec * MU; e += WARPS * 32)
+    s_u[e / MU][e % MU] = c_sym2.u[e / MU][e % MU];
+  for (int e = threadIdx.x; e < kT2Ent * 3; e += WARPS * 32) s_ent[e / 3][e % 3] = c_ent2[e / 3][e % 3];
+  __syncthreads();
+  EigT2Warp& sm = sw[w];
+  const int64_t cnt = *count;
+  const int h = lane >> 4, q = lane & 15, r = q >> 2, cc = q & 3;
+  for (int64_t i = (int64_t)blockIdx.x * WARPS + w; i < cnt; i += (int64_t)gridDim.x * WARPS) {
+    if (lane < 2 * NCLS) sm.g[lane] = gvals[(int64_t)lane * cap + i];
+    for (int e = lane; e < 5 * 64; e += 32) {
+      (&sm.Gb[0][0])[e] = 0.0;
+      (&sm.B[0][0])[e] = 0.0;
+    }
+    __syncwarp();
+    // ---- a4: G_b and U_b^T A1 U_b, then B_b = U_b^T A1 U_b - G_b G_b (entries e, e + 32) ----
+    double a1v[2] = {0.0, 0.0};
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+      const int e = lane + 32 * pass;
+      if (e < kT2Ent) {
+        const int eb = s_ent[e][0], ei = s_ent[e][1], ej = s_ent[e][2];
+        double gg = 0.0, aa = 0.0;
+#pragma unroll
+        for (int k = 0; k < NCLS; ++k) {
+          gg = fma(s_coef[e][k], sm.g[2 * k], gg);
+          aa = fma(s_coef[e][k], sm.g[2 * k + 1], aa);
+        }
+        sm.Gb[eb][ei * 8 + ej] = gg;
+        sm.Gb[eb][ej * 8 + ei] = gg;
+        a1v[pass] = aa;
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+      const int e = lane + 32 * pass;
+      if (e < kT2Ent) {
+        const int eb = s_ent[e][0], ei = s_ent[e][1], ej = s_ent[e][2];
+        double sv = a1v[pass];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) sv = fma(-sm.Gb[eb][ei * 8 + k], sm.Gb[eb][k * 8 + ej], sv);
+        sm.B[eb][ei * 8 + ej] = sv;
+        sm.B[eb][ej * 8 + ei] = sv;
+      }
+    }
+    __syncwarp();
+    // ---- a5: the two 6 x 6 blocks (A1, E) on the whole warp ----
+    warp_block_eig8(sm, 0, 6, lane);
+    warp_block_eig8(sm, 1, 6, lane);
+    // ---- the 3 x 3 blocks (B1, B2) on the two half-warps, padded to 4 x 4 ----
+    {
+      const int bb = 2 + h;
+      double b4[4][4], scale = 0.0, tr = 0.0;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          b4[x][y] = (x < 3 && y < 3) ? sm.B[bb][x * 8 + y] : 0.0;
+          scale = fmax(scale, fabs(b4[x][y]));
+        }
+#pragma unroll
+      for (int x = 0; x < 3; ++x) tr += b4[x][x];
+      b4[3][3] = 4.0 * scale * 3 + 1.0;
+      double s4[4][4], L4[4][4], id4[4];
+      const double delta = 1e-13 * fabs(tr);
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          s4[x][y] = b4[x][y] + (x == y ? delta : 0.0);
+          L4[x][y] = 0.0;
+        }
+      const bool fact = ldlt(s4, 4, L4, id4);
+      double xv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) xv[k] = k == cc ? 1.0 : 0.0;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int k = 0; k < x; ++k) xv[x] = fma(-L4[x][k], xv[k], xv[x]);
+#pragma unroll
+      for (int x = 0; x < 4; ++x) xv[x] *= id4[x];
+#pragma unroll
+      for (int x = 3; x >= 0; --x)
+#pragma unroll
+        for (int k = x + 1; k < 4; ++k) xv[x] = fma(-L4[k][x], xv[k], xv[x]);
+      double m0 = xv[0];
+#pragma unroll
+      for (int k = 1; k < 4; ++k)
+        if (r == k) m0 = xv[k];
+      if (!fact) m0 = r == cc ? 1.0 : 0.0;
+      sm.M4[h][q] = m0;
+      __syncwarp();
+#pragma unroll 1
+      for (int k = 0; k < 7; ++k) {
+        const double nv = sq_entry(sm.M4[h], r, cc);
+        __syncwarp();
+        sm.M4[h][q] = nv;
+        __syncwarp();
+      }
+      double v1[4];
+      dominant_column(sm.M4[h], v1);
+      v1[3] = 0.0;
+      double lam = 0.0, res = 0.0, bv[4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        bv[x] = 0.0;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) bv[x] = fma(b4[x][y], v1[y], bv[x]);
+        lam = fma(v1[x], bv[x], lam);
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x) res = fmax(res, fabs(fma(-lam, v1[x], bv[x])));
+      const int conv = fact && isfinite(lam) && res <= 64.0 * DBL_EPSILON * scale;
+      double part = v1[r] * m0 * v1[cc];
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      __syncwarp();
+      sm.M4[h][q] = fma(-part * v1[r], v1[cc], m0);
+      __syncwarp();
+#pragma unroll 1
+      for (int k = 0; k < 3; ++k) {
+        const double nv = sq_entry(sm.M4[h], r, cc);
+        __syncwarp();
+        sm.M4[h][q] = nv;
+        __syncwarp();
+      }
+      double v2[4];
+      dominant_column(sm.M4[h], v2);
+      double lam2b = 0.0;
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        double t = 0.0;
+#pragma unroll
+        for (int y = 0; y < 4; ++y) t = fma(b4[x][y], v2[y], t);
+        lam2b = fma(v2[x], t, lam2b);
+      }
+      if (!(v2[0] != 0.0 || v2[1] != 0.0 || v2[2] != 0.0)) lam2b = lam;
+      if (q == 0) {
+        sm.lam[bb][0] = lam;
+        sm.lam[bb][1] = lam2b;
+        sm.tr[bb] = tr;
+        sm.conv[bb] = conv;
+#pragma unroll
+        for (int x = 0; x < 8; ++x) sm.v[bb][x] = x < 4 ? v1[x] : 0.0;
+      }
+    }
+    // ---- A2 (1 x 1) ----
+    if (lane == 0) {
+      sm.lam[4][0] = sm.B[4][0];
+      sm.lam[4][1] = DBL_MAX;
+      sm.tr[4] = sm.B[4][0];
+      sm.conv[4] = 1;
+#pragma unroll
+      for (int x = 0; x < 8; ++x) sm.v[4][x] = x == 0 ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    // ---- fallback: cyclic Jacobi for a block whose residual check failed (one lane each) ----
+    if (lane < 4 && !sm.conv[lane]) {
+      const int dim = lane < 2 ? 6 : 3;
+      double a[8][8], vv[8][8];
+      for (int x = 0; x < 8; ++x)
+        for (int y = 0; y < 8; ++y) a[x][y] = (x < dim && y < dim) ? sm.B[lane][x * 8 + y] : 0.0;
+      const int ok = jacobi_nm<8>(a, vv, dim);
+      int kk = 0;
+      for (int x = 1; x < dim; ++x)
+        if (a[x][x] < a[kk][kk]) kk = x;
+      double second = DBL_MAX;
+      for (int x = 0; x < dim; ++x)
+        if (x != kk) second = fmin(second, a[x][x]);
+      sm.lam[lane][0] = a[kk][kk];
+      sm.lam[lane][1] = second;
+      for (int x = 0; x < 8; ++x) sm.v[lane][x] = x < dim ? vv[x][kk] : 0.0;
+      sm.conv[lane] = ok ? 2 : 0;
+    }
+    __syncwarp();
+    // ---- selection (uniform) ----
+    int bstar = 0;
+#pragma unroll
+    for (int bb = 1; bb < 5; ++bb)
+      if (sm.lam[bb][0] < sm.lam[bstar][0]) bstar = bb;
+    const double lam1 = sm.lam[bstar][0];
+    double lam2 = DBL_MAX, lmax = 0.0;
+    int flags = 0;
+#pragma unroll
+    for (int bb = 0; bb < 5; ++bb) {
+      lmax = fmax(lmax, fabs(sm.tr[bb]));
+      if (!sm.conv[bb]) flags |= LSP_FLAG_NOT_CONVERGED;
+      if (bb == bstar) {
+        lam2 = fmin(lam2, sm.lam[bb][1]);
+        if (c_sym2.copies[bb] > 1) lam2 = fmin(lam2, sm.lam[bb][0]);
+      } else {
+        lam2 = fmin(lam2, sm.lam[bb][0]);
+      }
+    }
+    if (bstar != 0) flags |= LSP_FLAG_NONSYMMETRIC;
+    if (lam2 - lam1 < 1e-8 * lmax) flags |= LSP_FLAG_DEGENERATE;
+    // ---- alpha = U_b y and (a6) c = G alpha = U_b (G_b y) ----
+    const int first = c_sym2.first[bstar], dimb = c_sym2.dim[bstar];
+    double y[8], gy[8];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) y[x] = sm.v[bstar][x];
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      gy[x] = 0.0;
+#pragma unroll
+      for (int z = 0; z < 8; ++z) gy[x] = fma(sm.Gb[bstar][x * 8 + z], y[z], gy[x]);
+    }
+    double av = 0.0, cv = 0.0;
+    if (lane < MU) {
+#pragma unroll
+      for (int x = 0; x < 8; ++x)
+        if (x < dimb) {
+          av = fma(y[x], s_u[first + x][lane], av);
+          cv = fma(gy[x], s_u[first + x][lane], cv);
+        }
+    }
+    const double acen = __shfl_sync(0xffffffffu, av, CENTRE);
+    const unsigned big = __ballot_sync(0xffffffffu, lane < MU && fabs(av) > 1e-12);
+    const double afirst = __shfl_sync(0xffffffffu, av, big ? __ffs(big) - 1 : 0);
+    const double ref = fabs(acen) > 1e-12 ? acen : (big ? afirst : 0.0);
+    if (ref < 0.0) {
+      av = -av;
+      cv = -cv;
+    }
+    if (lane < MU) {
+      alpha_out[i * MU + lane] = av;
+      c_out[i * MU + lane] = cv;
+    }
+    if (lane == 0) {
+      lam_out[2 * i + 0] = lam1;
+      lam_out[2 * i + 1] = lam2;
+      flags_out[i] = flags;
+    }
+    __syncwarp();
+  }
+}
+
 // ---- 2D, one thread per shift ------------------------------------------------------------
 // In 2D the symmetry-adapted vectors are u_0..u_2 (fully symmetric: centre, edges, corners),
 // u_3 (edges, x^2 - y^2), u_4 (corners, xy) and u_5, u_6 (x-odd on edges and corners). With
@@ -1165,11 +1595,53 @@ cudaError_t upload_sym(lsp_ctx* c) {
       for (int q = 0; q < 6; ++q) B2f[i][j][q] = (float)B2[i][j][q];
   e = cudaMemcpyToSymbol(c_W2, W2, sizeof W2);
   if (e != cudaSuccess) return e;
+  {
+    // t = 2 (2D): block entries (b, i <= j) of mu_0^2 and their class coefficients
+    const SymBasis& s2 = c->sym2;
+    const Geometry& g2 = c->geo2;
+    static double coef2[kT2Ent][kMaxCls];
+    int8_t ent2[kT2Ent][3];
+    memset(coef2, 0, sizeof coef2);
+    int q = 0;
+    for (int b = 0; b < s2.nblk; ++b)
+      for (int i = 0; i < s2.dim[b]; ++i)
+        for (int j = i; j < s2.dim[b]; ++j) {
+          if (q >= kT2Ent) return cudaErrorInvalidValue;
+          ent2[q][0] = (int8_t)b;
+          ent2[q][1] = (int8_t)i;
+          ent2[q][2] = (int8_t)j;
+          const double* ui = s2.u[s2.first[b] + i];
+          const double* uj = s2.u[s2.first[b] + j];
+          for (int a = 0; a < g2.mu; ++a)
+            for (int bb = 0; bb < g2.mu; ++bb) coef2[q][g2.cls_of[a][bb]] += ui[a] * uj[bb];
+          ++q;
+        }
+    if (q != kT2Ent) return cudaErrorInvalidValue;
+    e = cudaMemcpyToSymbol(c_coef2, coef2, sizeof coef2);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyToSymbol(c_ent2, ent2, sizeof ent2);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyToSymbol(c_sym2, &s2, sizeof(SymBasis));
+    if (e != cudaSuccess) return e;
+  }
   e = cudaMemcpyToSymbol(c_W2f, W2f, sizeof W2f);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(c_B2f, B2f, sizeof B2f);
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_B2, B2, sizeof B2);
+}
+
+cudaError_t launch_eig_t2(lsp_ctx* c, const int32_t* count, int64_t cap) {
+  int t = timer_begin(c, "eig_t2");
+  constexpr int kW = 2;
+  int64_t b = (cap + kW - 1) / kW;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  k_eig2d_t2<kW><<<(int)b, kW * 32, 0, c->stream>>>(
+      (const double*)c->gvals.p, cap, count, (double*)c->alpha2.p, (double*)c->cst2.p,
+      (double*)c->lam2.p, (int32_t*)c->sflags2.p);
+  timer_end(c, t);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int method, int refine,

@@ -125,6 +125,105 @@ __global__ void __launch_bounds__(kThreads) k_colidx(int64_t N, int logn, int32_
     rowptr[j] = j * MU;
 }
 
+// ---- t = 2 rows (2D): 25 columns per point in the lexicographic 5 x 5 offset order ---------
+// t_j at point j = (x0, x1): 2 without a leaf; else min(2, min_a f(x_a mod leaf)) with
+// f(0) = leaf, f(r) = min(r, leaf - r): the largest t whose neighbourhood crosses no separator
+// line of a nested dissection with leaf boxes of width `leaf` (Sec. 4.2).
+__device__ __forceinline__ int t_of_point(int64_t x0, int64_t x1, int leaf) {
+  if (leaf <= 0) return 2;
+  int t = 2;
+  const int r0 = (int)(x0 % leaf), r1 = (int)(x1 % leaf);
+  t = min(t, r0 == 0 ? leaf : min(r0, leaf - r0));
+  t = min(t, r1 == 0 ? leaf : min(r1, leaf - r1));
+  return t;
+}
+
+// A t_j = 2 point writes alpha2/c2 of its shift in all 25 columns; a t_j = 1 point writes
+// alpha/c of the 3 x 3 stencil in the inner columns (|o_a| <= 1) and zeros in the outer ring.
+template <bool LOCAL>
+__global__ void __launch_bounds__(kThreads) k_rows_t2(
+    const double* __restrict__ v, int64_t N, int logn, int leaf,
+    const int32_t* __restrict__ idx_of, int64_t mlo, int64_t R, int32_t* __restrict__ err,
+    const int32_t* __restrict__ shift_m, const int32_t* __restrict__ count,
+    const double* __restrict__ alpha1, const double* __restrict__ c1,
+    const double* __restrict__ alpha2, const double* __restrict__ c2, double* __restrict__ Q,
+    double* __restrict__ C, double* __restrict__ P) {
+  constexpr int MU = 25;
+  __shared__ int s_idx[kThreads];
+  __shared__ int s_t[kThreads];
+  __shared__ double s_val[kThreads];
+  const int64_t mask = ((int64_t)1 << logn) - 1;
+  const int ns = *count;
+  for (int64_t j0 = (int64_t)blockIdx.x * kThreads; j0 < N; j0 += (int64_t)gridDim.x * kThreads) {
+    const int npts = (int)min((int64_t)kThreads, N - j0);
+    const int t = threadIdx.x;
+    if (t < npts) {
+      const int64_t j = j0 + t;
+      const double x = __ldg(v + j);
+      int idx;
+      if (LOCAL) {
+        const int64_t r = snap_m(x) - mlo;
+        idx = (r >= 0 && r < R) ? __ldg(idx_of + r) : -1;
+        if (idx < 0) {
+          atomicOr(err, 2);
+          idx = 0;
+        }
+      } else {
+        idx = nearest_shift(shift_m, ns, x);
+      }
+      s_idx[t] = idx;
+      s_t[t] = t_of_point(j >> logn, j & mask, leaf);
+      s_val[t] = shift_of(__ldg(shift_m + idx));
+    }
+    __syncthreads();
+    const int64_t obase = j0 * MU;
+    for (int e = t; e < npts * MU; e += kThreads) {
+      const int p = e / MU, o = e - p * MU;
+      const int o0 = o / 5 - 2, o1 = o % 5 - 2;
+      const int idx = s_idx[p];
+      double a = 0.0, cc = 0.0;
+      if (s_t[p] == 2) {
+        a = __ldg(alpha2 + (int64_t)idx * MU + o);
+        cc = __ldg(c2 + (int64_t)idx * MU + o);
+      } else if (o0 >= -1 && o0 <= 1 && o1 >= -1 && o1 <= 1) {
+        const int b = (o0 + 1) * 3 + (o1 + 1);
+        a = __ldg(alpha1 + (int64_t)idx * 9 + b);
+        cc = __ldg(c1 + (int64_t)idx * 9 + b);
+      }
+      const int64_t jj = j0 + p;
+      const int64_t nb = (((jj >> logn) + o0) & mask) << logn | (((jj & mask) + o1) & mask);
+      const double vn = __ldg(v + nb);
+      __stcs(Q + obase + e, a);
+      __stcs(C + obase + e, cc);
+      __stcs(P + obase + e, fma(cc, vn - s_val[p], a));
+    }
+    __syncthreads();
+  }
+}
+
+// CSR export of a t = 2 build: row j keeps the (2 t_j + 1)^2 columns of mu_j^{t_j}, in the
+// lexicographic order of its own offsets (the inner 3 x 3 of the 25-wide row when t_j = 1).
+// rowptr holds the prefix sums of the row lengths.
+__global__ void __launch_bounds__(kThreads) k_export_t2(const double* __restrict__ rows,
+                                                        int64_t N, int logn, int leaf,
+                                                        const int64_t* __restrict__ rowptr,
+                                                        int32_t* __restrict__ col,
+                                                        double* __restrict__ val) {
+  const int64_t mask = ((int64_t)1 << logn) - 1;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < N * 25;
+       e += (int64_t)gridDim.x * kThreads) {
+    const int64_t j = e / 25;
+    const int o = (int)(e - j * 25);
+    const int o0 = o / 5 - 2, o1 = o % 5 - 2;
+    const int tj = t_of_point(j >> logn, j & mask, leaf);
+    if (tj == 1 && (o0 < -1 || o0 > 1 || o1 < -1 || o1 > 1)) continue;
+    const int k = tj == 2 ? o : (o0 + 1) * 3 + (o1 + 1);
+    const int64_t pos = rowptr[j] + k;
+    col[pos] = (int32_t)((((j >> logn) + o0) & mask) << logn | (((j & mask) + o1) & mask));
+    val[pos] = rows[e];
+  }
+}
+
 int log2i(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;
@@ -171,6 +270,37 @@ cudaError_t launch_sidx(lsp_ctx* c, int policy, const int32_t* count) {
   int t = timer_begin(c, "sidx");
   dispatch_rows<false, true>(c, policy, count);
   timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_t2(lsp_ctx* c, int policy, const int32_t* count, int leaf) {
+  const int64_t N = c->geo.N;
+  int64_t b = (N + kThreads - 1) / kThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  int t = timer_begin(c, "rows");
+  auto args = [&](auto kern) {
+    kern<<<(int)b, kThreads, 0, c->stream>>>(
+        (const double*)c->v.p, N, log2i(c->geo.n), leaf, (const int32_t*)c->idx_of.p,
+        c->mrange.lo, c->mrange.size(), (int32_t*)c->counts.p + kErrWord,
+        (const int32_t*)c->shift_m.p, count, (const double*)c->alpha.p, (const double*)c->cst.p,
+        (const double*)c->alpha2.p, (const double*)c->cst2.p, (double*)c->Q.p, (double*)c->C.p,
+        (double*)c->P.p);
+  };
+  if (policy == LSP_SHIFT_LOCAL)
+    args(k_rows_t2<true>);
+  else
+    args(k_rows_t2<false>);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_t2(lsp_ctx* c, const double* rows, int leaf, const int64_t* rowptr,
+                             int32_t* colidx, double* vals) {
+  const int64_t work = c->geo.N * 25;
+  int64_t b = (work + kThreads - 1) / kThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  k_export_t2<<<(int)b, kThreads, 0, c->stream>>>(rows, c->geo.N, log2i(c->geo.n), leaf, rowptr,
+                                                  colidx, vals);
   return cudaGetLastError();
 }
 

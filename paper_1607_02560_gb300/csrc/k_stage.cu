@@ -22,20 +22,23 @@ namespace {
 
 constexpr int kThreads = 256;
 
-// Output class c of stage k: (first index a, class of the remaining tuple in stage k-1).
-// Stage 2 pairs (a<=b): 00 01 02 11 12 22. Stage 3 triples (a<=b<=c): 000 001 002 011 012 022
-// 111 112 122 222, remaining pair indexed as in stage 2. Compile-time tables, so the register
-// arrays below are indexed by constants after unrolling.
-template <int K>
+// Output class c of stage k: (first index a, class of the remaining tuple in stage k-1), for
+// A cosine rows X_0..X_{A-1} (A = 2t + 1: offsets up to 2t are needed for mu^t). Stage 1 has A
+// classes (a). Stage 2 pairs (a <= b): for A = 3 in the order 00 01 02 11 12 22; for A = 5
+// the same six first, then the pairs with b = 3 (03 13 23 33) and b = 4 (04 14 24 34 44), so
+// the classes of t = 1 keep their indices in a t = 2 table. Stage 3 triples (a <= b <= c, A = 3):
+// 000 001 002 011 012 022 111 112 122 222, remaining pair indexed as in stage 2. Compile-time
+// tables, so the register arrays below are indexed by constants after unrolling.
+template <int K, int A>
 struct StageMap;
-template <>
-struct StageMap<1> {
-  static constexpr int NCP = 1, NCO = 3;
+template <int A>
+struct StageMap<1, A> {
+  static constexpr int NCP = 1, NCO = A;
   __host__ __device__ static constexpr int a(int c) { return c; }
   __host__ __device__ static constexpr int r(int) { return 0; }
 };
 template <>
-struct StageMap<2> {
+struct StageMap<2, 3> {
   static constexpr int NCP = 3, NCO = 6;
   __host__ __device__ static constexpr int a(int c) {
     return c < 3 ? 0 : (c < 5 ? 1 : 2);
@@ -45,7 +48,17 @@ struct StageMap<2> {
   }
 };
 template <>
-struct StageMap<3> {
+struct StageMap<2, 5> {
+  static constexpr int NCP = 5, NCO = 15;
+  __host__ __device__ static constexpr int a(int c) {
+    return c < 6 ? StageMap<2, 3>::a(c) : (c < 10 ? c - 6 : c - 10);
+  }
+  __host__ __device__ static constexpr int r(int c) {
+    return c < 6 ? StageMap<2, 3>::r(c) : (c < 10 ? 3 : 4);
+  }
+};
+template <>
+struct StageMap<3, 3> {
   static constexpr int NCP = 6, NCO = 10;
   __host__ __device__ static constexpr int a(int c) {
     return c < 6 ? 0 : (c < 9 ? 1 : 2);
@@ -75,12 +88,12 @@ struct Vec2<float> { using type = float2; };
 // identity exactly). In FP64 the table interleaves (w, w^2) and is read with one 16-byte load
 // (the FP64 pipe is the bound); in FP32 it holds w alone and the square is formed in registers
 // (the L2 bandwidth is the bound).
-template <int K, typename R>
+template <int K, int A, typename R>
 __device__ __forceinline__ void stage_accumulate(const R* __restrict__ xs, int P, int64_t l,
                                                  const R* __restrict__ Tprev, int64_t lo_prev,
                                                  int64_t stride_prev, int first, int step,
-                                                 R (&acc)[StageMap<K>::NCO][2]) {
-  using M = StageMap<K>;
+                                                 R (&acc)[StageMap<K, A>::NCO][2]) {
+  using M = StageMap<K, A>;
   using R2 = typename Vec2<R>::type;
   const int half = P - 1;  // n/2
   if (K == 1) {
@@ -103,13 +116,12 @@ __device__ __forceinline__ void stage_accumulate(const R* __restrict__ xs, int P
       }
       const R s1 = wa.x + wb.x, d1 = wa.x - wb.x;
       const R s2 = wa.y + wb.y, d2 = wa.y - wb.y;
-      const R x0 = xs[p], x1 = xs[P + p], x2 = xs[2 * P + p];
-      acc[0][0] = fma(x0, s1, acc[0][0]);
-      acc[1][0] = fma(x1, d1, acc[1][0]);
-      acc[2][0] = fma(x2, s1, acc[2][0]);
-      acc[0][1] = fma(x0, s2, acc[0][1]);
-      acc[1][1] = fma(x1, d2, acc[1][1]);
-      acc[2][1] = fma(x2, s2, acc[2][1]);
+#pragma unroll
+      for (int a = 0; a < A; ++a) {  // even a: X_a(q) = X_a(p); odd a: X_a(q) = -X_a(p)
+        const R xa = xs[a * P + p];
+        acc[a][0] = fma(xa, (a & 1) ? d1 : s1, acc[a][0]);
+        acc[a][1] = fma(xa, (a & 1) ? d2 : s2, acc[a][1]);
+      }
     }
     if (first == 0) {
       R2 wm;
@@ -120,7 +132,7 @@ __device__ __forceinline__ void stage_accumulate(const R* __restrict__ xs, int P
         wm.y = wm.x * wm.x;
       }
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
+      for (int c = 0; c < A; ++c) {
         acc[c][0] = fma(xs[c * P + quarter], wm.x, acc[c][0]);
         acc[c][1] = fma(xs[c * P + quarter], wm.y, acc[c][1]);
       }
@@ -135,7 +147,9 @@ __device__ __forceinline__ void stage_accumulate(const R* __restrict__ xs, int P
         in[c][0] = __ldg(base + (2 * c + 0) * stride_prev + off);
         in[c][1] = __ldg(base + (2 * c + 1) * stride_prev + off);
       }
-      const R x[3] = {xs[p], xs[P + p], xs[2 * P + p]};
+      R x[A];
+#pragma unroll
+      for (int a = 0; a < A; ++a) x[a] = xs[a * P + p];
 #pragma unroll
       for (int c = 0; c < M::NCO; ++c) {
         acc[c][0] = fma(x[M::a(c)], in[M::r(c)][0], acc[c][0]);
@@ -149,7 +163,7 @@ __device__ __forceinline__ void stage_accumulate(const R* __restrict__ xs, int P
 // splitting the frequencies and a shuffle reduction at the end (SPLIT = true, used when the
 // domain is too small to fill the GPU, e.g. a few dozen shifts). Output: Tout[(c * 2 + f) *
 // stride_out + pos], pos = index in the list (by_index) or l - lo_out.
-template <int K, typename R, typename OUT, bool SPLIT>
+template <int K, int A, typename R, typename OUT, bool SPLIT>
 __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ list,
                                                     const int32_t* __restrict__ count_ptr, int P,
                                                     const R* __restrict__ X,
@@ -158,10 +172,10 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
                                                     OUT* __restrict__ Tout, int64_t lo_out,
                                                     int64_t stride_out, int by_index,
                                                     double scale) {
-  using M = StageMap<K>;
+  using M = StageMap<K, A>;
   extern __shared__ __align__(16) unsigned char xs_raw[];
-  R* xs = reinterpret_cast<R*>(xs_raw);  // [3][P]
-  for (int i = threadIdx.x; i < 3 * P; i += kThreads) xs[i] = X[i];
+  R* xs = reinterpret_cast<R*>(xs_raw);  // [A][P]
+  for (int i = threadIdx.x; i < A * P; i += kThreads) xs[i] = X[i];
   __syncthreads();
   // list == nullptr: the domain is the whole range [lo_out, lo_out + stride_out)
   const int64_t cnt = list ? (int64_t)*count_ptr : stride_out;
@@ -174,7 +188,7 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
     R acc[M::NCO][2];
 #pragma unroll
     for (int c = 0; c < M::NCO; ++c) acc[c][0] = acc[c][1] = R(0);
-    stage_accumulate<K, R>(xs, P, l, Tprev, lo_prev, stride_prev, SPLIT ? lane : 0,
+    stage_accumulate<K, A, R>(xs, P, l, Tprev, lo_prev, stride_prev, SPLIT ? lane : 0,
                            SPLIT ? 32 : 1, acc);
     if (SPLIT) {
 #pragma unroll
@@ -194,14 +208,14 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
   }
 }
 
-template <int K, typename R, typename OUT, bool SPLIT>
+template <int K, int A, typename R, typename OUT, bool SPLIT>
 cudaError_t launch_kk(lsp_ctx* c, const int32_t* list, const int32_t* count, int64_t cap,
                       const R* X, const R* Tprev, int64_t lo_prev, int64_t stride_prev, OUT* Tout,
                       int64_t lo_out, int64_t stride_out, bool by_index, double scale) {
   const int P = c->geo.P;
-  const size_t smem = sizeof(R) * 3 * P;
+  const size_t smem = sizeof(R) * A * P;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_stage<K, R, OUT, SPLIT>,
+    cudaError_t e = cudaFuncSetAttribute(k_stage<K, A, R, OUT, SPLIT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -209,7 +223,7 @@ cudaError_t launch_kk(lsp_ctx* c, const int32_t* list, const int32_t* count, int
   int64_t b = (cap + per_block - 1) / per_block;
   if (b < 1) b = 1;
   if (b > 152 * 16) b = 152 * 16;
-  k_stage<K, R, OUT, SPLIT><<<(int)b, kThreads, smem, c->stream>>>(
+  k_stage<K, A, R, OUT, SPLIT><<<(int)b, kThreads, smem, c->stream>>>(
       list, count, P, X, Tprev, lo_prev, stride_prev, Tout, lo_out, stride_out, by_index ? 1 : 0,
       scale);
   return cudaGetLastError();
@@ -218,55 +232,62 @@ cudaError_t launch_kk(lsp_ctx* c, const int32_t* list, const int32_t* count, int
 // Domains below about two threads per SM-lane slot are spread over warps instead.
 constexpr int64_t kSplitBelow = 152 * 256;
 
-template <int K, typename R, typename OUT>
+template <int K, int A, typename R, typename OUT>
 cudaError_t launch_k(lsp_ctx* c, const int32_t* list, const int32_t* count, int64_t cap,
                      const R* X, const R* Tprev, int64_t lo_prev, int64_t stride_prev, OUT* Tout,
                      int64_t lo_out, int64_t stride_out, bool by_index, double scale) {
   if (cap < kSplitBelow)
-    return launch_kk<K, R, OUT, true>(c, list, count, cap, X, Tprev, lo_prev, stride_prev, Tout,
-                                      lo_out, stride_out, by_index, scale);
-  return launch_kk<K, R, OUT, false>(c, list, count, cap, X, Tprev, lo_prev, stride_prev, Tout,
-                                     lo_out, stride_out, by_index, scale);
+    return launch_kk<K, A, R, OUT, true>(c, list, count, cap, X, Tprev, lo_prev, stride_prev,
+                                         Tout, lo_out, stride_out, by_index, scale);
+  return launch_kk<K, A, R, OUT, false>(c, list, count, cap, X, Tprev, lo_prev, stride_prev, Tout,
+                                        lo_out, stride_out, by_index, scale);
 }
 
 template <typename R>
-cudaError_t launch_typed(lsp_ctx* c, int d, int k, const int32_t* list, const int32_t* count,
-                         int64_t cap, const void* Tprev, int64_t lo_prev, int64_t stride_prev,
-                         void* Tout, int64_t lo_out, int64_t stride_out, bool by_index,
-                         double scale, const R* X) {
+cudaError_t launch_typed(lsp_ctx* c, int d, int k, int t, const int32_t* list,
+                         const int32_t* count, int64_t cap, const void* Tprev, int64_t lo_prev,
+                         int64_t stride_prev, void* Tout, int64_t lo_out, int64_t stride_out,
+                         bool by_index, double scale, const R* X) {
   const R* prev = (const R*)Tprev;
+  if (t == 2) {  // 2D only (validated by the caller): five cosine rows
+    if (k == 1)
+      return launch_k<1, 5, R, R>(c, list, count, cap, X, prev, lo_prev, stride_prev, (R*)Tout,
+                                  lo_out, stride_out, by_index, scale);
+    return launch_k<2, 5, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev,
+                                     (double*)Tout, lo_out, stride_out, by_index, scale);
+  }
   if (k == d) {  // last stage: double g values for the eigen step
     double* out = (double*)Tout;
     if (k == 2)
-      return launch_k<2, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev, out,
-                                    lo_out, stride_out, by_index, scale);
-    return launch_k<3, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev, out, lo_out,
-                                  stride_out, by_index, scale);
+      return launch_k<2, 3, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev, out,
+                                       lo_out, stride_out, by_index, scale);
+    return launch_k<3, 3, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev, out,
+                                     lo_out, stride_out, by_index, scale);
   }
   R* out = (R*)Tout;
   if (k == 1)
-    return launch_k<1, R, R>(c, list, count, cap, X, prev, lo_prev, stride_prev, out, lo_out,
-                             stride_out, by_index, scale);
-  return launch_k<2, R, R>(c, list, count, cap, X, prev, lo_prev, stride_prev, out, lo_out,
-                           stride_out, by_index, scale);
+    return launch_k<1, 3, R, R>(c, list, count, cap, X, prev, lo_prev, stride_prev, out, lo_out,
+                                stride_out, by_index, scale);
+  return launch_k<2, 3, R, R>(c, list, count, cap, X, prev, lo_prev, stride_prev, out, lo_out,
+                              stride_out, by_index, scale);
 }
 
 }  // namespace
 
-cudaError_t launch_stage(lsp_ctx* c, int d, int k, const int32_t* list, const int32_t* count,
-                         int64_t cap, const void* Tprev, int64_t lo_prev, int64_t stride_prev,
-                         void* Tout, int64_t lo_out, int64_t stride_out, bool by_index,
-                         bool fp32) {
+cudaError_t launch_stage(lsp_ctx* c, int d, int k, int t, const int32_t* list,
+                         const int32_t* count, int64_t cap, const void* Tprev, int64_t lo_prev,
+                         int64_t stride_prev, void* Tout, int64_t lo_out, int64_t stride_out,
+                         bool by_index, bool fp32) {
   // The final stage carries the 1/N of the inverse transform (N a power of two: exact).
   const double scale = (k == d) ? 1.0 / (double)c->geo.N : 1.0;
   static const char* names[4] = {"", "stage1", "stage2", "stage3"};
-  int t = timer_begin(c, names[k]);
+  int tm = timer_begin(c, names[k]);
   cudaError_t e =
-      fp32 ? launch_typed<float>(c, d, k, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
+      fp32 ? launch_typed<float>(c, d, k, t, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
                                  lo_out, stride_out, by_index, scale, (const float*)c->xtab32.p)
-           : launch_typed<double>(c, d, k, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
+           : launch_typed<double>(c, d, k, t, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
                                   lo_out, stride_out, by_index, scale, (const double*)c->xtab.p);
-  timer_end(c, t);
+  timer_end(c, tm);
   return e;
 }
 

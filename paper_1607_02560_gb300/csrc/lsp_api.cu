@@ -73,9 +73,12 @@ bool is_norm(int64_t r, int d, int half) {
 
 // ---- geometry and symmetry basis ------------------------------------------------------
 
-int pair_index(int a, int b) {  // a <= b in {0,1,2}
+// Class of a sorted pair a <= b of |offset| components: the six pairs over {0,1,2} in the order
+// 00 01 02 11 12 22, then (t = 2) the pairs with b = 3 (03 13 23 33) and b = 4 (04 .. 44), so
+// the classes of t = 1 keep their indices in a t = 2 table (the stage kernels use this order).
+int pair_index(int a, int b) {
   static const int t[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
-  return t[a][b];
+  return b <= 2 ? t[a][b] : b * (b + 1) / 2 + a;
 }
 int triple_index(int a, int b, int c) {  // a <= b <= c
   int idx = 0;
@@ -88,12 +91,15 @@ int triple_index(int a, int b, int c) {  // a <= b <= c
   return -1;
 }
 
-void build_geometry(Geometry& g, int d, int n) {
+// mu_0^t = [-t, t]^d (t = 1 in 2D and 3D, t = 2 in 2D), lexicographic, last axis fastest.
+void build_geometry(Geometry& g, int d, int n, int t = 1) {
   memset(&g, 0, sizeof g);
   g.d = d;
   g.n = n;
-  g.mu = d == 2 ? 9 : 27;
-  g.ncls = d == 2 ? 6 : 10;
+  g.t = t;
+  const int w = 2 * t + 1;
+  g.mu = d == 2 ? w * w : w * w * w;
+  g.ncls = d == 2 ? w * (w + 1) / 2 : 10;
   g.centre = g.mu / 2;
   g.N = 1;
   for (int i = 0; i < d; ++i) g.N *= n;
@@ -101,8 +107,8 @@ void build_geometry(Geometry& g, int d, int n) {
   for (int a = 0; a < g.mu; ++a) {
     int rem = a;
     for (int i = d - 1; i >= 0; --i) {
-      g.off[a][i] = rem % 3 - 1;
-      rem /= 3;
+      g.off[a][i] = rem % w - t;
+      rem /= w;
     }
   }
   for (int a = 0; a < g.mu; ++a)
@@ -177,6 +183,73 @@ bool build_sym(SymBasis& s, const Geometry& g) {
       double dot = 0.0;
       for (int a = 0; a < g.mu; ++a) dot += s.u[i][a] * s.u[j][a];
       if (fabs(dot - (i == j ? 1.0 : 0.0)) > 1e-14) return false;
+    }
+  return true;
+}
+
+// Symmetry-adapted basis of mu_0^2 in 2D (25 points, orbits of the signed permutations of the
+// axes: |o| = (0,0), (0,1), (1,1), (0,2), (1,2), (2,2) of sizes 1, 4, 4, 4, 8, 4). Blocks:
+// A1 (the constant on each orbit, 6), A2 (xy(x^2 - y^2) on (1,2)), B1 (x^2 - y^2 on (0,1),
+// (0,2), (1,2)), B2 (xy on (1,1), (2,2), (1,2)) and E (partner x: x on (0,1), (1,1), (0,2),
+// (2,2), (1,2), and x y^2 on (1,2); 2 copies). Vectors of a block are orthonormalised in
+// order (Gram-Schmidt: x and x y^2 share the 8-point orbit).
+bool build_sym_t2(SymBasis& s, const Geometry& g) {
+  memset(&s, 0, sizeof s);
+  if (g.d != 2 || g.t != 2) return false;
+  enum { kOne, kX, kX2mY2, kXY, kXYx2mY2, kXY2 };
+  struct Vec { int o0, o1, kind; };
+  struct Blk { int copies; int nv; Vec v[6]; };
+  const Blk blks[5] = {
+      {1, 6, {{0, 0, kOne}, {0, 1, kOne}, {1, 1, kOne}, {0, 2, kOne}, {1, 2, kOne}, {2, 2, kOne}}},
+      {2, 6, {{0, 1, kX}, {1, 1, kX}, {0, 2, kX}, {2, 2, kX}, {1, 2, kX}, {1, 2, kXY2}}},
+      {1, 3, {{0, 1, kX2mY2}, {0, 2, kX2mY2}, {1, 2, kX2mY2}}},
+      {1, 3, {{1, 1, kXY}, {2, 2, kXY}, {1, 2, kXY}}},
+      {1, 1, {{1, 2, kXYx2mY2}}}};
+  s.nblk = 5;
+  int total = 0;
+  for (int b = 0; b < s.nblk; ++b) {
+    s.dim[b] = blks[b].nv;
+    s.copies[b] = blks[b].copies;
+    s.first[b] = s.nvec;
+    total += blks[b].nv * blks[b].copies;
+    for (int i = 0; i < blks[b].nv; ++i) {
+      double* u = s.u[s.nvec];
+      for (int a = 0; a < g.mu; ++a) {
+        const int x = g.off[a][0], y = g.off[a][1];
+        int o[2] = {abs(x), abs(y)};
+        if (o[0] > o[1]) std::swap(o[0], o[1]);
+        double val = 0.0;
+        if (o[0] == blks[b].v[i].o0 && o[1] == blks[b].v[i].o1) {
+          switch (blks[b].v[i].kind) {
+            case kOne: val = 1.0; break;
+            case kX: val = x; break;
+            case kX2mY2: val = x * x - y * y; break;
+            case kXY: val = x * y; break;
+            case kXYx2mY2: val = x * y * (x * x - y * y); break;
+            default: val = x * y * y; break;
+          }
+        }
+        u[a] = val;
+      }
+      for (int k = s.first[b]; k < s.nvec; ++k) {  // Gram-Schmidt within the block
+        double dot = 0.0;
+        for (int a = 0; a < g.mu; ++a) dot += s.u[k][a] * u[a];
+        for (int a = 0; a < g.mu; ++a) u[a] -= dot * s.u[k][a];
+      }
+      double nrm = 0.0;
+      for (int a = 0; a < g.mu; ++a) nrm += u[a] * u[a];
+      if (nrm < 1e-12) return false;
+      nrm = sqrt(nrm);
+      for (int a = 0; a < g.mu; ++a) u[a] /= nrm;
+      ++s.nvec;
+    }
+  }
+  if (total != g.mu) return false;
+  for (int i = 0; i < s.nvec; ++i)
+    for (int j = 0; j < s.nvec; ++j) {
+      double dot = 0.0;
+      for (int a = 0; a < g.mu; ++a) dot += s.u[i][a] * s.u[j][a];
+      if (fabs(dot - (i == j ? 1.0 : 0.0)) > 1e-13) return false;
     }
   return true;
 }
@@ -306,17 +379,24 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
     const int64_t lo_prev = c->erange[k - 1].lo, stride_prev = c->erange[k - 1].size();
     if (k < d) {
       const bool dense = c->edense[k];
-      CUDA_OK(c, launch_stage(c, d, k, dense ? nullptr : (const int32_t*)c->elist[k].p,
+      CUDA_OK(c, launch_stage(c, d, k, o.t, dense ? nullptr : (const int32_t*)c->elist[k].p,
                               dense ? nullptr : counts + (d - k), c->erange[k].size(), prev,
                               lo_prev, stride_prev, c->T[k].p, c->erange[k].lo,
                               c->erange[k].size(), false, fp32));
     } else {
-      CUDA_OK(c, launch_stage(c, d, k, (const int32_t*)c->shift_m.p, counts + 0, cap_s, prev,
-                              lo_prev, stride_prev, c->gvals.p, 0, cap_s, true, fp32));
+      CUDA_OK(c, launch_stage(c, d, k, o.t, (const int32_t*)c->shift_m.p, counts + 0, cap_s,
+                              prev, lo_prev, stride_prev, c->gvals.p, 0, cap_s, true, fp32));
     }
   }
-  CUDA_OK(c, launch_eig(c, counts + 0, cap_s, o.eig_method, o.refine_steps, fp32));
-  CUDA_OK(c, launch_rows(c, o.policy, counts + 0));
+  // t = 1 stencils read the first classes of a t = 2 table (same row stride cap_s)
+  if (o.t == 1 || o.nd_leaf > 0)
+    CUDA_OK(c, launch_eig(c, counts + 0, cap_s, o.eig_method, o.refine_steps, fp32));
+  if (o.t == 2) {
+    CUDA_OK(c, launch_eig_t2(c, counts + 0, cap_s));
+    CUDA_OK(c, launch_rows_t2(c, o.policy, counts + 0, o.nd_leaf));
+  } else {
+    CUDA_OK(c, launch_rows(c, o.policy, counts + 0));
+  }
   return LSP_OK;
 }
 
@@ -346,6 +426,13 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
     delete c;
     return LSP_ERR_STATE;
   }
+  if (d == 2) {  // t = 2 neighbourhoods (2D)
+    build_geometry(c->geo2, d, n, 2);
+    if (!build_sym_t2(c->sym2, c->geo2)) {
+      delete c;
+      return LSP_ERR_STATE;
+    }
+  }
   lsp_status st = LSP_OK;
   do {
     if (cudaGetDevice(&c->device) != cudaSuccess) {
@@ -360,11 +447,11 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
       st = LSP_ERR_CUDA;
       break;
     }
-    // X_a(p) = w_p cos(2 pi a p / n), w_p = 1 at p = 0 and p = n/2, else 2. The cosine of
+    // X_a(p) = w_p cos(2 pi a p / n), a = 0..4, w_p = 1 at p = 0 and p = n/2, else 2. The cosine of
     // 2 pi r / n is taken from the first octant by exact symmetries, so the table satisfies
     // cos(pi a - t) = (-1)^a cos(t) (used by the mirror pairing of stage 1) bit for bit.
     const int P = c->geo.P;
-    std::vector<double> X(3 * P);
+    std::vector<double> X(5 * P);
     const long double two_pi = 6.283185307179586476925286766559005768L;
     auto cos_r = [&](int r) -> long double {  // cos(2 pi r / n), r in [0, n)
       r %= n;
@@ -385,7 +472,7 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
         val = cosl(two_pi * (long double)r / (long double)n);
       return sign * val;
     };
-    for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 5; ++a)
       for (int p = 0; p < P; ++p) {
         const long double wgt = (p == 0 || p == n / 2) ? 1.0L : 2.0L;
         X[a * P + p] = (double)(wgt * cos_r(a * p));
@@ -432,7 +519,8 @@ lsp_status lsp_destroy(lsp_ctx* c) {
   DevBuf* bufs[] = {&c->v, &c->stats_part, &c->stats, &c->xtab, &c->xtab32, &c->shift_m, &c->shift_flag,
                     &c->idx_of, &c->counts, &c->wtab, &c->gvals, &c->alpha, &c->cst, &c->lam,
                     &c->sflags, &c->Q, &c->C, &c->P, &c->sidx, &c->colidx, &c->rowptr,
-                    &c->fftbuf, &c->twiddle, &c->learn_in};
+                    &c->fftbuf, &c->twiddle, &c->learn_in, &c->alpha2, &c->cst2, &c->lam2,
+                    &c->sflags2, &c->expvals};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   for (int k = 0; k < kMaxD; ++k) {
@@ -489,7 +577,13 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   else
     lsp_default_opts(&o);
   if (!c->have_v) return fail(c, LSP_ERR_STATE, "build_stencils before set_potential");
-  if (o.t != 1) return fail(c, LSP_ERR_UNSUPPORTED, "only t = 1 neighbourhoods are built");
+  if (o.t != 1 && o.t != 2) return fail(c, LSP_ERR_ARG, "t must be 1 or 2");
+  if (o.t == 2 && c->geo.d != 2)
+    return fail(c, LSP_ERR_UNSUPPORTED, "t = 2 neighbourhoods are built in 2D only");
+  if (o.nd_leaf < 0 || (o.nd_leaf > 0 && (o.nd_leaf < 2 || c->geo.n % o.nd_leaf != 0)))
+    return fail(c, LSP_ERR_ARG, "nd_leaf must be 0 or an even divisor >= 2 of n");
+  if (o.t == 2 && o.mode == LSP_LEARNED)
+    return fail(c, LSP_ERR_UNSUPPORTED, "learned builds use t = 1 neighbourhoods");
   if (o.mode != LSP_FP64 && o.mode != LSP_MIXED && o.mode != LSP_LEARNED)
     return fail(c, LSP_ERR_ARG, "bad mode %d", o.mode);
   if (o.mode == LSP_LEARNED) {
@@ -513,6 +607,8 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
       c->built = true;
       c->built_learned = true;
       c->mode_used = LSP_LEARNED;
+      c->t_built = 1;
+      c->leaf_built = 0;
       return LSP_OK;
     }
     o.mode = LSP_FP64;  // fallback
@@ -524,7 +620,9 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     return fail(c, LSP_ERR_ARG, "refine_steps must be in [0, 4]");
   const int d = c->geo.d, n = c->geo.n;
   const int64_t N = c->geo.N;
-  const int mu = c->geo.mu;
+  const Geometry& G = o.t == 2 ? c->geo2 : c->geo;
+  const int mu = G.mu;
+  const bool need_t1 = o.t == 1 || o.nd_leaf > 0;  // some point uses the 3 x 3 stencil
   c->built = false;
 
   // ---- a2: the shift set ----
@@ -597,11 +695,15 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   const int64_t R = c->mrange.size();
   bool ok = ensure(c, c->shift_m, sizeof(int32_t) * cap_s) &&
             ensure(c, c->counts, sizeof(int32_t) * (16 + 2 + c->erange[0].size() / 4096 + 16)) &&
-            ensure(c, c->gvals, sizeof(double) * 2 * c->geo.ncls * cap_s) &&
-            ensure(c, c->alpha, sizeof(double) * mu * cap_s) &&
-            ensure(c, c->cst, sizeof(double) * mu * cap_s) &&
-            ensure(c, c->lam, sizeof(double) * 2 * cap_s) &&
-            ensure(c, c->sflags, sizeof(int32_t) * cap_s) &&
+            ensure(c, c->gvals, sizeof(double) * 2 * G.ncls * cap_s) &&
+            (!need_t1 || (ensure(c, c->alpha, sizeof(double) * c->geo.mu * cap_s) &&
+                          ensure(c, c->cst, sizeof(double) * c->geo.mu * cap_s) &&
+                          ensure(c, c->lam, sizeof(double) * 2 * cap_s) &&
+                          ensure(c, c->sflags, sizeof(int32_t) * cap_s))) &&
+            (o.t != 2 || (ensure(c, c->alpha2, sizeof(double) * mu * cap_s) &&
+                          ensure(c, c->cst2, sizeof(double) * mu * cap_s) &&
+                          ensure(c, c->lam2, sizeof(double) * 2 * cap_s) &&
+                          ensure(c, c->sflags2, sizeof(int32_t) * cap_s))) &&
             ensure_tracked(c, c->wtab, sizeof(double) * 2 * c->erange[0].size(), &c->wtab_size) &&
             ensure(c, c->Q, sizeof(double) * mu * N) && ensure(c, c->C, sizeof(double) * mu * N) &&
             ensure(c, c->P, sizeof(double) * mu * N);
@@ -610,7 +712,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   for (int k = 1; ok && k < d; ++k) {
     const int64_t sz = c->erange[k].size();
     ok = ensure(c, c->eflag[k], round_up(sz, 4096)) && ensure(c, c->elist[k], sizeof(int32_t) * sz) &&
-         ensure(c, c->T[k], sizeof(double) * 2 * ncls_stage(k) * sz);
+         ensure(c, c->T[k], sizeof(double) * 2 * (o.t == 2 ? 5 : ncls_stage(k)) * sz);
   }
   if (!ok) return LSP_ERR_OOM;
   if (o.policy != LSP_SHIFT_LOCAL) {
@@ -649,7 +751,8 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy &&
                           c->stream != cudaStreamPerThread;
   if (o.use_graph && !c->timing && capturable) {
-    std::vector<int64_t> key = {o.policy, o.mode, o.eig_method, o.refine_steps, cap_s, c->mrange.lo,
+    std::vector<int64_t> key = {o.policy, o.mode, o.eig_method, o.refine_steps, o.t, o.nd_leaf,
+                                cap_s, c->mrange.lo,
                                 c->mrange.hi, (int64_t)(intptr_t)c->v.p,
                                 (int64_t)(intptr_t)c->Q.p};
     for (int k = 0; k <= d; ++k) key.push_back(c->erange[k].lo);
@@ -678,6 +781,8 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     c->built = true;
     c->built_learned = false;
     c->mode_used = o.mode;
+    c->t_built = o.t;
+    c->leaf_built = o.t == 2 ? o.nd_leaf : 0;
   }
   return st;
 }
@@ -690,6 +795,23 @@ lsp_status lsp_apply_operator(lsp_ctx* c, const double* u, double* y) {
   if (!ensure(c, c->fftbuf, sizeof(double) * 2 * c->geo.N)) return LSP_ERR_OOM;
   CUDA_OK(c, launch_apply(c, u, y));
   return LSP_OK;
+}
+
+// Row width of the last build: (2t+1)^d.
+static int built_mu(const lsp_ctx* c) { return c->t_built == 2 ? c->geo2.mu : c->geo.mu; }
+
+// t_j of a t = 2 build at point j (2D): 2 everywhere without a leaf, else the largest t <= 2
+// whose neighbourhood crosses no separator line x_a = 0 (mod leaf) (Sec. 4.2).
+static int t_of_point(int64_t j, int n, int leaf) {
+  if (leaf <= 0) return 2;
+  int t = 2;
+  const int64_t x[2] = {j / n, j % n};
+  for (int a = 0; a < 2; ++a) {
+    const int r = (int)(x[a] % leaf);
+    const int f = r == 0 ? leaf : std::min(r, leaf - r);
+    t = std::min(t, f);
+  }
+  return t;
 }
 
 static lsp_status rows_of(lsp_ctx* c, char which, const double** out) {
@@ -708,7 +830,7 @@ lsp_status lsp_get_rows(lsp_ctx* c, char which, double* rows, int on_device) {
   const double* src;
   lsp_status st = rows_of(c, which, &src);
   if (st != LSP_OK) return st;
-  const size_t bytes = sizeof(double) * c->geo.mu * c->geo.N;
+  const size_t bytes = sizeof(double) * built_mu(c) * c->geo.N;
   CUDA_OK(c, cudaMemcpyAsync(rows, src, bytes,
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              c->stream));
@@ -720,6 +842,39 @@ lsp_status lsp_export_sparse_rows(lsp_ctx* c, char which, int64_t* rowptr, int32
                                   double* vals, int64_t* nnz_out) {
   if (!c) return LSP_ERR_ARG;
   cudaGetLastError();
+  const int64_t N = c->geo.N;
+  if (c->built && c->t_built == 2) {
+    // rows of (2 t_j + 1)^2 entries: the structural zeros of t_j = 1 rows are left out
+    std::vector<int64_t> ptr(N + 1);
+    ptr[0] = 0;
+    for (int64_t j = 0; j < N; ++j) {
+      const int w = 2 * t_of_point(j, c->geo.n, c->leaf_built) + 1;
+      ptr[j + 1] = ptr[j] + w * w;
+    }
+    const int64_t nnz = ptr[N];
+    if (nnz_out) *nnz_out = nnz;
+    if (!rowptr && !colidx && !vals) return LSP_OK;
+    if (!rowptr || !colidx || !vals)
+      return fail(c, LSP_ERR_ARG, "rowptr, colidx and vals must all be given");
+    const double* src;
+    lsp_status st = rows_of(c, which, &src);
+    if (st != LSP_OK) return st;
+    if (!ensure(c, c->colidx, sizeof(int32_t) * nnz) ||
+        !ensure(c, c->rowptr, sizeof(int64_t) * (N + 1)) ||
+        !ensure(c, c->expvals, sizeof(double) * nnz))
+      return LSP_ERR_OOM;
+    CUDA_OK(c, cudaMemcpyAsync(c->rowptr.p, ptr.data(), sizeof(int64_t) * (N + 1),
+                               cudaMemcpyHostToDevice, c->stream));
+    CUDA_OK(c, launch_export_t2(c, src, c->leaf_built, (const int64_t*)c->rowptr.p,
+                                (int32_t*)c->colidx.p, (double*)c->expvals.p));
+    CUDA_OK(c, cudaMemcpyAsync(colidx, c->colidx.p, sizeof(int32_t) * nnz,
+                               cudaMemcpyDeviceToHost, c->stream));
+    CUDA_OK(c, cudaMemcpyAsync(vals, c->expvals.p, sizeof(double) * nnz, cudaMemcpyDeviceToHost,
+                               c->stream));
+    CUDA_OK(c, cudaStreamSynchronize(c->stream));
+    memcpy(rowptr, ptr.data(), sizeof(int64_t) * (N + 1));
+    return LSP_OK;
+  }
   const int64_t nnz = c->geo.N * c->geo.mu;
   if (nnz_out) *nnz_out = nnz;
   if (!rowptr && !colidx && !vals) return LSP_OK;
@@ -756,18 +911,25 @@ lsp_status lsp_get_shift_table(lsp_ctx* c, int64_t* nshifts_out, double* s, doub
     return fail(c, LSP_ERR_STATE, "device lattice snap disagreed with the host (bits %d)",
                 head[kErrWord]);
   if (nshifts_out) *nshifts_out = ns;
-  const int mu = c->geo.mu;
+  const bool t2 = c->t_built == 2;  // the t = 2 stencils of a t = 2 build
+  const int mu = built_mu(c);
   if (s) {
     std::vector<int32_t> m(ns);
     CUDA_OK(c, cudaMemcpy(m.data(), c->shift_m.p, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost));
     for (int i = 0; i < ns; ++i) s[i] = shift_host(m[i]);
   }
   if (alpha)
-    CUDA_OK(c, cudaMemcpy(alpha, c->alpha.p, sizeof(double) * mu * ns, cudaMemcpyDeviceToHost));
-  if (cst) CUDA_OK(c, cudaMemcpy(cst, c->cst.p, sizeof(double) * mu * ns, cudaMemcpyDeviceToHost));
-  if (lam) CUDA_OK(c, cudaMemcpy(lam, c->lam.p, sizeof(double) * 2 * ns, cudaMemcpyDeviceToHost));
+    CUDA_OK(c, cudaMemcpy(alpha, (t2 ? c->alpha2 : c->alpha).p, sizeof(double) * mu * ns,
+                          cudaMemcpyDeviceToHost));
+  if (cst)
+    CUDA_OK(c, cudaMemcpy(cst, (t2 ? c->cst2 : c->cst).p, sizeof(double) * mu * ns,
+                          cudaMemcpyDeviceToHost));
+  if (lam)
+    CUDA_OK(c, cudaMemcpy(lam, (t2 ? c->lam2 : c->lam).p, sizeof(double) * 2 * ns,
+                          cudaMemcpyDeviceToHost));
   if (flags)
-    CUDA_OK(c, cudaMemcpy(flags, c->sflags.p, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost));
+    CUDA_OK(c, cudaMemcpy(flags, (t2 ? c->sflags2 : c->sflags).p, sizeof(int32_t) * ns,
+                          cudaMemcpyDeviceToHost));
   if (s_idx) {
     if (!ensure(c, c->sidx, sizeof(int32_t) * c->geo.N)) return LSP_ERR_OOM;
     CUDA_OK(c, launch_sidx(c, c->last_policy, (const int32_t*)c->counts.p));
@@ -781,7 +943,7 @@ lsp_status lsp_get_shift_table(lsp_ctx* c, int64_t* nshifts_out, double* s, doub
 lsp_status lsp_get_sizes(const lsp_ctx* c, int64_t* npoints, int* mu) {
   if (!c) return LSP_ERR_ARG;
   if (npoints) *npoints = c->geo.N;
-  if (mu) *mu = c->geo.mu;
+  if (mu) *mu = built_mu(c);
   return LSP_OK;
 }
 

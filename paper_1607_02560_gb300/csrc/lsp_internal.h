@@ -20,15 +20,15 @@ constexpr double kPi2 = kPi * kPi;
 constexpr double kQuarterInvPi2 = 0.25 / kPi2;  // for the fast path of the lattice snap
 
 constexpr int kMaxD = 3;
-constexpr int kMaxMu = 27;      // (2t+1)^d for t = 1, d = 3
-constexpr int kMaxCls = 10;     // sorted |offset| tuples over {0,1,2}^d, d = 3
-constexpr int kMaxSymVec = 13;  // symmetry-adapted basis vectors (3D)
+constexpr int kMaxMu = 27;      // (2t+1)^d: 27 for t = 1, d = 3; 25 for t = 2, d = 2
+constexpr int kMaxCls = 15;     // sorted |offset| tuples: 10 over {0,1,2}^3, 15 over {0..4}^2
+constexpr int kMaxSymVec = 19;  // symmetry-adapted basis vectors (19 for t = 2, d = 2)
 constexpr int kMaxSymBlk = 6;
 // counts[] layout: [0] |S|, [1], [2] sizes of the compacted stage domains, [kErrWord] device
 // error bits, [16...] compaction tile scratch.
 constexpr int kErrWord = 15;
 
-// Symmetry-adapted basis of R^{|mu|} for the hyperoctahedral group acting on mu_0 (t = 1):
+// Symmetry-adapted basis of R^{|mu|} for the hyperoctahedral group acting on mu_0^t:
 // one row of every irreducible representation that occurs. Block b has `dim` basis vectors
 // (its multiplicity in mu_0) and stands for `copies` identical blocks (the irrep dimension).
 struct SymBasis {
@@ -40,9 +40,9 @@ struct SymBasis {
   double u[kMaxSymVec][kMaxMu];   // orthonormal vectors, dense over mu_0
 };
 
-// Offset tables for t = 1.
+// Offset tables of mu_0^t.
 struct Geometry {
-  int d, n, mu, ncls, centre;
+  int d, n, t, mu, ncls, centre;
   int64_t N;
   int P;                           // n/2 + 1 frequencies per axis in [0, n/2]
   int off[kMaxMu][kMaxD];          // mu_0 offsets, lexicographic
@@ -81,8 +81,17 @@ struct lsp_ctx {
   lsp::DevBuf v, stats_part, stats;
   double* h_stats = nullptr;  // pinned
 
-  // cos table X_a(p) = w_p cos(2 pi a p / n), a = 0..2, p = 0..n/2 (FP64 and FP32 copies)
+  // cos table X_a(p) = w_p cos(2 pi a p / n), a = 0..4, p = 0..n/2 (FP64 and FP32 copies;
+  // t = 1 reads rows 0..2)
   lsp::DevBuf xtab, xtab32;
+
+  // t = 2 neighbourhoods (2D): offsets, classes and symmetry basis of mu_0^2, and the build's
+  // choice: rows of a t = 2 build are (2t+1)^d = 25 wide; with nd_leaf > 0 a point uses
+  // t_j = min(2, largest t whose neighbourhood crosses no separator x_a = 0 mod nd_leaf) and
+  // its inner 3 x 3 columns when t_j = 1
+  lsp::Geometry geo2;
+  lsp::SymBasis sym2;
+  int t_built = 1, leaf_built = 0;
 
   // shift list (a2)
   bool built = false;
@@ -101,11 +110,11 @@ struct lsp_ctx {
   int wtab_fp32 = -1;
   int64_t alloc_gen = 0;  // bumped whenever a device buffer is (re)allocated
 
-  // per-shift results (a3-a6)
-  lsp::DevBuf gvals, alpha, cst, lam, sflags;
+  // per-shift results (a3-a6); *2: the t = 2 stencils
+  lsp::DevBuf gvals, alpha, cst, lam, sflags, alpha2, cst2, lam2, sflags2;
 
   // rows (a7) and export
-  lsp::DevBuf Q, C, P, sidx, colidx, rowptr;
+  lsp::DevBuf Q, C, P, sidx, colidx, rowptr, expvals;
 
   // FFT (apply_operator)
   lsp::DevBuf fftbuf, twiddle;
@@ -144,10 +153,14 @@ cudaError_t launch_compact(lsp_ctx* c, const uint8_t* flags, int64_t lo, int64_t
 cudaError_t launch_mark_stage(lsp_ctx* c, const int32_t* list, const int32_t* count,
                               int64_t cap, int64_t lo_prev, uint8_t* flag_prev);
 cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, void* w, bool fp32);
-cudaError_t launch_stage(lsp_ctx* c, int d, int k, const int32_t* list, const int32_t* count,
-                         int64_t cap, const void* Tprev, int64_t lo_prev, int64_t stride_prev,
-                         void* Tout, int64_t lo_out, int64_t stride_out, bool by_index,
-                         bool fp32);
+cudaError_t launch_stage(lsp_ctx* c, int d, int k, int t, const int32_t* list,
+                         const int32_t* count, int64_t cap, const void* Tprev, int64_t lo_prev,
+                         int64_t stride_prev, void* Tout, int64_t lo_out, int64_t stride_out,
+                         bool by_index, bool fp32);
+cudaError_t launch_eig_t2(lsp_ctx* c, const int32_t* count, int64_t cap);
+cudaError_t launch_rows_t2(lsp_ctx* c, int policy, const int32_t* count, int leaf);
+cudaError_t launch_export_t2(lsp_ctx* c, const double* rows, int leaf, const int64_t* rowptr,
+                             int32_t* colidx, double* vals);
 cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int eig_method,
                        int refine_steps, bool fp32_gram);
 cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count);

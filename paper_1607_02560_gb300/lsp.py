@@ -38,7 +38,7 @@ class StencilOpts(ctypes.Structure):
     _fields_ = [("t", ctypes.c_int), ("policy", ctypes.c_int), ("nshifts", ctypes.c_int),
                 ("shifts", ctypes.POINTER(ctypes.c_double)), ("mode", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("eig_method", ctypes.c_int),
-                ("use_graph", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("nd_leaf", ctypes.c_int)]
 
 
 _lib = None
@@ -165,8 +165,15 @@ class Context:
         N = ctypes.c_int64()
         mu = ctypes.c_int()
         lib().lsp_get_sizes(self.h, ctypes.byref(N), ctypes.byref(mu))
-        self.N, self.mu = N.value, mu.value
+        self.N = N.value
         self._keep = None
+
+    @property
+    def mu(self) -> int:
+        """Row width (2t+1)^d of the last build (3^d before any build)."""
+        N, mu = ctypes.c_int64(), ctypes.c_int()
+        self._check(lib().lsp_get_sizes(self.h, ctypes.byref(N), ctypes.byref(mu)), "get_sizes")
+        return mu.value
 
     def _check(self, st: int, what: str):
         if st != LSP_OK:
@@ -194,10 +201,13 @@ class Context:
         self._check(lib().lsp_set_potential(self.h, _ptr(v), _on_device(v)), "set_potential")
 
     def build_stencils(self, policy="local", nshifts=0, shifts=None, mode="fp64",
-                       refine_steps=0, eig_method="symmetric", use_graph=False, t=1):
-        """Steps a2-a7 (asynchronous on the context stream)."""
+                       refine_steps=0, eig_method="symmetric", use_graph=False, t=1,
+                       nd_leaf=0):
+        """Steps a2-a7 (asynchronous on the context stream). t = 2 (2D) builds 25-wide rows;
+        nd_leaf > 0 gives each point t_j from a nested dissection with that leaf width."""
         o = StencilOpts()
         o.t = t
+        o.nd_leaf = int(nd_leaf)
         o.policy = POLICY[policy] if isinstance(policy, str) else int(policy)
         o.mode = MODE[mode] if isinstance(mode, str) else int(mode)
         o.refine_steps = refine_steps
