@@ -364,7 +364,7 @@ def run_ours(args):
 
 
 def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup: int,
-                mlp=None, stream=None):
+                mlp=None, stream=None, t: int = 1, nd_leaf: int = 0):
     """stencils/s of one configuration (same step, L2 flush and events as the main line)."""
     from lsp_inputs import make_workload
     from paper_1607_02560_gb300 import Context
@@ -379,7 +379,7 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             ctx.set_potential(v_dev)
-            ctx.build_stencils(policy=policy, mode=mode, use_graph=True)
+            ctx.build_stencils(policy=policy, mode=mode, use_graph=True, t=t, nd_leaf=nd_leaf)
         ctx.synchronize()
         tot = 0.0
         for _ in range(steps):
@@ -387,7 +387,7 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             ctx.set_potential(v_dev)
-            ctx.build_stencils(policy=policy, mode=mode, use_graph=True)
+            ctx.build_stencils(policy=policy, mode=mode, use_graph=True, t=t, nd_leaf=nd_leaf)
             e1.record(stream)
             torch.cuda.synchronize()
             tot += e0.elapsed_time(e1)
@@ -403,17 +403,18 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
                 "p50": float(np.percentile(err, 50)), "p99": float(np.percentile(err, 99)),
                 "p99.9": float(np.percentile(err, 99.9)), "max": float(err.max()),
                 "frac_above_1e-2": float(np.mean(err > 1e-2))}
-            ctx.build_stencils(policy=policy, mode=mode, use_graph=True)
+            ctx.build_stencils(policy=policy, mode=mode, use_graph=True, t=t, nd_leaf=nd_leaf)
         ctx.kernel_timing(True)
         for _ in range(5):
             flush.zero_()
             ctx.set_potential(v_dev)
-            ctx.build_stencils(policy=policy, mode=mode, use_graph=True)
+            ctx.build_stencils(policy=policy, mode=mode, use_graph=True, t=t, nd_leaf=nd_leaf)
         ctx.synchronize()
         kt = {k: round(ms / max(cnt, 1), 4) for k, (ms, cnt) in ctx.kernel_times().items()}
         ctx.kernel_timing(False)
     ctx.close()
-    out = {"workload": workload, "policy": policy, "mode": mode, "mode_used": used,
+    out = {"workload": workload, "policy": policy, "mode": mode, "mode_used": used, "t": t,
+           "nd_leaf": nd_leaf,
            "value": v.size * steps / (tot * 1e-3), "unit": "stencils/s",
            "ms_per_step": tot / steps, "shifts": ns, "kernel_ms_per_launch": kt}
     out.update(extra)
@@ -461,6 +462,13 @@ def variants(args, torch):
             out.append(time_config(torch, wl, pol, mode, steps=20, warmup=3))
         except Exception as exc:  # a variant must not hide the main line
             out.append({"workload": wl, "policy": pol, "mode": mode, "error": str(exc)[:200]})
+    # multi-t (Sec. 4.2): t_j from a nested dissection with leaf boxes of width 8, t_max = 2
+    for pol in ("paper", "local"):
+        wl = "helm2d_n1024" if pol == "paper" else "helm2d_n256"
+        try:
+            out.append(time_config(torch, wl, pol, "fp64", steps=20, warmup=3, t=2, nd_leaf=8))
+        except Exception as exc:
+            out.append({"workload": wl, "policy": pol, "t": 2, "error": str(exc)[:200]})
     if not args.no_learned:
         for wl in ("helm2d_n1024", "schr3d_n64"):
             try:
