@@ -68,7 +68,7 @@ typedef struct {
   int t;               /* neighbourhood radius t of mu_j^t (Sec. 4.2): 1 (|mu| = 3^d), or 2    */
                        /* in 2D (|mu| = 25; rows are 25 wide, see nd_leaf)                    */
   int policy;          /* lsp_shift_policy                                                     */
-  int nshifts;         /* PAPER: |S| before de-duplication; 0 selects n/16 (2D) or n/4 (3D)   */
+  int nshifts;         /* PAPER: |S| before de-duplication; 0 selects n/16 (2D), n/4 (1D, 3D) */
   const double* shifts;/* LIST: nshifts shift values in host memory, each (4m+2) pi^2          */
   int mode;            /* lsp_mode: FP64, MIXED (FP32 contractions/Gram, FP64 solve), LEARNED  */
   int refine_steps;    /* inverse-iteration steps applied to each near-null vector (0 or 1)   */
@@ -88,9 +88,9 @@ typedef struct {
 void lsp_default_opts(lsp_stencil_opts* opts);
 
 /*
- * Create a context for the d-dimensional n^d grid (Sec. 2). d in {2, 3}; n a power of two,
- * 8 <= n <= 4096 (2D) or 8 <= n <= 256 (3D), so that the offsets of mu_0 - mu_0 stay distinct
- * mod n. cuda_stream is a cudaStream_t (NULL = the legacy default stream) that every device
+ * Create a context for the d-dimensional n^d grid (Sec. 2). d in {1, 2, 3}; n a power of two,
+ * 8 <= n <= 4096 (1D, 2D) or 8 <= n <= 256 (3D), so that the offsets of mu_0 - mu_0 stay
+ * distinct mod n. The 1D form (|mu| = 3) serves the one-dimensional example of Sec. 4.1. cuda_stream is a cudaStream_t (NULL = the legacy default stream) that every device
  * operation of the context is issued on. The current CUDA device at this call is the one used.
  * On success *out receives the context; release it with lsp_destroy().
  */

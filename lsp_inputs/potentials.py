@@ -109,6 +109,8 @@ WORKLOADS = {
     "helm2d_n1024": dict(d=2, n=1024, kind="bumps", omega=2 * math.pi * 256, nb=64, seed=3),
     # 3D Schroedinger-type, 8 random wells, max|v| h^2 = 0.6, n = 64.
     "schr3d_n64": dict(d=3, n=64, kind="wells", nb=8, seed=4),
+    # 1D Helmholtz, one centred bump, 4 points per wavelength (omega = 2 pi 64, n = 256).
+    "helm1d_n256": dict(d=1, n=256, kind="bump", omega=2 * math.pi * 64, seed=5),
 }
 
 

@@ -1574,6 +1574,7 @@ cudaError_t upload_sym(lsp_ctx* c) {
     }
     return cudaMemcpyToSymbol(c_coef3, coef, sizeof coef);
   }
+  if (c->geo.d != 2) return cudaSuccess;  // the tables below are for the 2D kernels
   // W_i[k] = sum_a G[k, a] u_i[a] = sum_a g[cls(k, a)] u_i[a];  u_i^T A1 u_j = sum g2[cls(a,b)] u_i[a] u_j[b]
   static double W2[7][9][6], B2[7][7][6];
   memset(W2, 0, sizeof W2);
@@ -1671,8 +1672,9 @@ cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int method
                                                    (double*)c->lam.p, (int32_t*)c->sflags.p);
     e = cudaGetLastError();
   } else {
-    e = c->geo.d == 2 ? launch_eig_t<9, 6, 8>(c, count, cap, method, refine)
-                      : launch_eig_t<27, 10, 2>(c, count, cap, method, refine);
+    e = c->geo.d == 1   ? launch_eig_t<3, 3, 8>(c, count, cap, method, refine)
+        : c->geo.d == 2 ? launch_eig_t<9, 6, 8>(c, count, cap, method, refine)
+                        : launch_eig_t<27, 10, 2>(c, count, cap, method, refine);
   }
   timer_end(c, t);
   return e;

@@ -3,6 +3,7 @@
 // A d-dimensional complex FP64 FFT done one axis at a time: every block transforms whole
 // lines of the chosen axis in shared memory (iterative radix-2, bit-reversed load, twiddles
 // from a table computed on the host in extended precision). Passes:
+//   1D: [fwd from real u, * 4 pi^2 k^2, inv, y = Re/n + v u] in one pass
 //   2D: [fwd axis0 from real u] -> [fwd axis1, * 4 pi^2 |k|^2, inv axis1] -> [inv axis0, y = Re/N + v u]
 //   3D: [fwd 0] -> [fwd 1] -> [fwd 2, * symbol, inv 2] -> [inv 1] -> [inv 0, output]
 // The unitary factors n^{-d/2} of F and F^-1 combine into the single 1/N of the output pass.
@@ -11,7 +12,8 @@
 namespace lsp {
 namespace {
 
-enum Mode { kPlain = 0, kLoadReal = 1, kSymbol = 2, kOutput = 3 };
+// kAll (d = 1): load the real input, transform, apply the symbol, transform back and output.
+enum Mode { kPlain = 0, kLoadReal = 1, kSymbol = 2, kOutput = 3, kAll = 4 };
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -48,11 +50,11 @@ __global__ void k_fft_axis(double2* __restrict__ Z, const double* __restrict__ u
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int r = __brev(i) >> (32 - logn);
       const int64_t g = base + (int64_t)i * S;
-      line[r] = (mode == kLoadReal) ? make_double2(u[g], 0.0) : Z[g];
+      line[r] = (mode == kLoadReal || mode == kAll) ? make_double2(u[g], 0.0) : Z[g];
     }
     __syncthreads();
     fft_line(line, n, logn, tw, !fwd_first);
-    if (mode == kSymbol) {
+    if (mode == kSymbol || mode == kAll) {
       // multiply by 4 pi^2 |k|^2 (k in FFT order), then transform back along this axis
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         int64_t g = base + (int64_t)i * S;
@@ -82,7 +84,7 @@ __global__ void k_fft_axis(double2* __restrict__ Z, const double* __restrict__ u
     }
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const int64_t g = base + (int64_t)i * S;
-      if (mode == kOutput) {
+      if (mode == kOutput || mode == kAll) {
         const double inv_n = 1.0 / (double)nlines / (double)n;  // 1/N (exact, power of two)
         y[g] = fma(v[g], u[g], line[i].x * inv_n);
       } else {
@@ -112,6 +114,12 @@ cudaError_t launch_apply(lsp_ctx* c, const double* u, double* y) {
   const double2* tw = (const double2*)c->twiddle.p;
   const double* v = (const double*)c->v.p;
   int t = timer_begin(c, "apply_fft");
+  if (d == 1) {  // one pass: forward, symbol, inverse, output
+    k_fft_axis<<<(int)blocks, threads, smem, c->stream>>>(Z, u, v, y, 1, n, logn, 0, nlines, tw,
+                                                          kAll, 1);
+    timer_end(c, t);
+    return cudaGetLastError();
+  }
   // forward passes on axes 0..d-2
   for (int axis = 0; axis < d - 1; ++axis)
     k_fft_axis<<<(int)blocks, threads, smem, c->stream>>>(Z, u, v, y, d, n, logn, axis, nlines, tw,

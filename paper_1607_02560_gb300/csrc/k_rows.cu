@@ -48,7 +48,9 @@ __device__ __forceinline__ int nearest_shift(const int32_t* __restrict__ m, int 
 
 template <int D>
 __device__ __forceinline__ int64_t neighbour(int64_t j, int o, int logn, int64_t mask) {
-  if (D == 2) {
+  if (D == 1) {
+    return (j + o - 1) & mask;
+  } else if (D == 2) {
     const int64_t x1 = j & mask, x0 = j >> logn;
     const int64_t y0 = (x0 + (o / 3) - 1) & mask, y1 = (x1 + (o % 3) - 1) & mask;
     return (y0 << logn) | y1;
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(kThreads) k_rows(
     const int32_t* __restrict__ count,
     const double* __restrict__ alpha, const double* __restrict__ cst, double* __restrict__ Q,
     double* __restrict__ C, double* __restrict__ P, int32_t* __restrict__ sidx_out) {
-  constexpr int MU = D == 2 ? 9 : 27;
+  constexpr int MU = D == 1 ? 3 : (D == 2 ? 9 : 27);
   __shared__ int s_idx[kThreads];
   __shared__ double s_val[kThreads];
   const int64_t mask = ((int64_t)1 << logn) - 1;
@@ -112,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) k_rows(
 template <int D>
 __global__ void __launch_bounds__(kThreads) k_colidx(int64_t N, int logn, int32_t* __restrict__ col,
                                                      int64_t* __restrict__ rowptr) {
-  constexpr int MU = D == 2 ? 9 : 27;
+  constexpr int MU = D == 1 ? 3 : (D == 2 ? 9 : 27);
   const int64_t mask = ((int64_t)1 << logn) - 1;
   for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < N * MU;
        e += (int64_t)gridDim.x * kThreads) {
@@ -244,7 +246,12 @@ void launch_rows_t(lsp_ctx* c, const int32_t* count) {
 template <bool ROWS, bool SIDX>
 void dispatch_rows(lsp_ctx* c, int policy, const int32_t* count) {
   const bool local = policy == LSP_SHIFT_LOCAL;
-  if (c->geo.d == 2) {
+  if (c->geo.d == 1) {
+    if (local)
+      launch_rows_t<1, true, ROWS, SIDX>(c, count);
+    else
+      launch_rows_t<1, false, ROWS, SIDX>(c, count);
+  } else if (c->geo.d == 2) {
     if (local)
       launch_rows_t<2, true, ROWS, SIDX>(c, count);
     else
@@ -309,7 +316,10 @@ cudaError_t launch_colidx(lsp_ctx* c) {
   int64_t b = (work + kThreads - 1) / kThreads;
   if (b > 152 * 16) b = 152 * 16;
   int t = timer_begin(c, "colidx");
-  if (c->geo.d == 2)
+  if (c->geo.d == 1)
+    k_colidx<1><<<(int)b, kThreads, 0, c->stream>>>(c->geo.N, log2i(c->geo.n),
+                                                     (int32_t*)c->colidx.p, (int64_t*)c->rowptr.p);
+  else if (c->geo.d == 2)
     k_colidx<2><<<(int)b, kThreads, 0, c->stream>>>(c->geo.N, log2i(c->geo.n),
                                                      (int32_t*)c->colidx.p, (int64_t*)c->rowptr.p);
   else

@@ -258,6 +258,9 @@ cudaError_t launch_typed(lsp_ctx* c, int d, int k, int t, const int32_t* list,
   }
   if (k == d) {  // last stage: double g values for the eigen step
     double* out = (double*)Tout;
+    if (k == 1)  // 1D: the single stage
+      return launch_k<1, 3, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev, out,
+                                       lo_out, stride_out, by_index, scale);
     if (k == 2)
       return launch_k<2, 3, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev, out,
                                        lo_out, stride_out, by_index, scale);

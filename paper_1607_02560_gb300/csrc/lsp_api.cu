@@ -98,8 +98,8 @@ void build_geometry(Geometry& g, int d, int n, int t = 1) {
   g.n = n;
   g.t = t;
   const int w = 2 * t + 1;
-  g.mu = d == 2 ? w * w : w * w * w;
-  g.ncls = d == 2 ? w * (w + 1) / 2 : 10;
+  g.mu = d == 1 ? w : (d == 2 ? w * w : w * w * w);
+  g.ncls = d == 1 ? 2 * t + 1 : (d == 2 ? w * (w + 1) / 2 : 10);
   g.centre = g.mu / 2;
   g.N = 1;
   for (int i = 0; i < d; ++i) g.N *= n;
@@ -116,7 +116,9 @@ void build_geometry(Geometry& g, int d, int n, int t = 1) {
       int v[3] = {0, 0, 0};
       for (int i = 0; i < d; ++i) v[i] = abs(g.off[a][i] - g.off[b][i]);
       std::sort(v, v + d);
-      g.cls_of[a][b] = (uint8_t)(d == 2 ? pair_index(v[0], v[1]) : triple_index(v[0], v[1], v[2]));
+      g.cls_of[a][b] = (uint8_t)(d == 1 ? v[0]
+                                        : d == 2 ? pair_index(v[0], v[1])
+                                                 : triple_index(v[0], v[1], v[2]));
     }
 }
 
@@ -140,7 +142,9 @@ bool build_sym(SymBasis& s, const Geometry& g) {
   memset(&s, 0, sizeof s);
   struct Blk { int copies; int nv; int orbit[4]; int kind[4]; };
   std::vector<Blk> blks;
-  if (g.d == 2) {
+  if (g.d == 1) {  // the reflection o -> -o: even (centre, the pair) and odd (the pair)
+    blks = {{1, 2, {0, 1}, {kOne, kOne}}, {1, 1, {1}, {kX}}};
+  } else if (g.d == 2) {
     blks = {{1, 3, {0, 1, 2}, {kOne, kOne, kOne}},
             {1, 1, {1}, {kX2mY2}},
             {1, 1, {2}, {kXY}},
@@ -416,8 +420,8 @@ void lsp_default_opts(lsp_stencil_opts* o) {
 lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
   if (!out) return LSP_ERR_ARG;
   *out = nullptr;
-  if (d != 2 && d != 3) return LSP_ERR_ARG;
-  if (n < 8 || (n & (n - 1)) != 0 || n > (d == 2 ? 4096 : 256)) return LSP_ERR_ARG;
+  if (d < 1 || d > 3) return LSP_ERR_ARG;
+  if (n < 8 || (n & (n - 1)) != 0 || n > (d == 3 ? 256 : 4096)) return LSP_ERR_ARG;
   lsp_ctx* c = new (std::nothrow) lsp_ctx();
   if (!c) return LSP_ERR_OOM;
   c->stream = (cudaStream_t)cuda_stream;
@@ -634,6 +638,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     cap_s = c->mrange.size();
   } else {
     if (o.policy == LSP_SHIFT_PAPER) {
+      // |S| of the Sec. 5 tables: n/16 in 2D, n/4 in 3D; 1D (no experiment) as 3D
       int K = o.nshifts > 0 ? o.nshifts : std::max(2, d == 2 ? n / 16 : n / 4);
       if (K == 1) {
         ms.push_back(snap_host(c->vmin));

@@ -28,10 +28,11 @@ def test_every_declared_symbol_is_exported(L):
 
 def test_default_opts(L):
     o = lsp.default_opts()
-    assert (o.t, o.policy, o.mode, o.eig_method, o.use_graph) == (1, 1, 0, 0, 0)
+    assert (o.t, o.policy, o.mode, o.eig_method, o.use_graph, o.nd_leaf) == (1, 1, 0, 0, 0, 0)
 
 
-@pytest.mark.parametrize("d,n", [(1, 16), (4, 16), (2, 12), (2, 4), (2, 8192), (3, 512)])
+@pytest.mark.parametrize("d,n", [(0, 16), (4, 16), (2, 12), (2, 4), (2, 8192), (3, 512),
+                                 (1, 4), (1, 8192)])
 def test_create_rejects_bad_sizes_before_touching_the_device(L, d, n):
     h = ctypes.c_void_p()
     st = L.lsp_create(d, n, None, ctypes.byref(h))
