@@ -37,7 +37,7 @@ import scipy.sparse.linalg
 
 __all__ = [
     "PI2", "freq_axis", "symbol", "apply_operator", "round_half_away", "snap_index",
-    "shift_value", "paper_shift_list", "default_nshifts", "assign_shifts",
+    "shift_value", "paper_shift_list", "default_nshifts", "assign_shifts", "solve_p",
     "neighbourhood_offsets", "kernel_vectors", "gram_matrix", "near_null",
     "stencil_for_shift", "build_stencils", "rows_to_csr", "sparse_matrices",
     "gmres_solve", "dense_green_matrix", "brute_force_stencil", "sign_fix",
@@ -403,6 +403,16 @@ def gmres_solve(v: np.ndarray, f: np.ndarray, P=None, C=None, restart: int = 40,
                                         maxiter=maxiter, callback=cb, callback_type="pr_norm")
     res = np.linalg.norm(A(u) - f.reshape(-1)) / np.linalg.norm(f)
     return u.reshape(shape), count[0], float(res), int(info)
+
+
+def solve_p(P: scipy.sparse.spmatrix, y: np.ndarray) -> np.ndarray:
+    """x = P^-1 y: the sparse solve behind the preconditioner P^-1 C (Sec. 3, Eq. QC; Sec. 4.1).
+
+    The paper factors P by nested dissection (Fig. nd, Table cost); every exact factorisation
+    gives the same x up to rounding, so this is the definition with a sparse LU as its step.
+    """
+    lu = scipy.sparse.linalg.splu(scipy.sparse.csc_matrix(P))
+    return lu.solve(np.asarray(y, dtype=np.float64))
 
 
 # --------------------------------------------------------------------------------------------

@@ -243,6 +243,29 @@ def test_gmres_iteration_counts_match_golden():
         assert res < 1e-4
 
 
+@pytest.mark.parametrize("case", ["t1_n8", "t1_n16_paper", "multi_t_n16"])
+def test_solve_p_is_the_exact_inverse(case):
+    """x = P^-1 y (Eq. QC): the sparse LU agrees with a dense solve and leaves a residual at
+    the rounding level, for t = 1 rows and for the multi-t rows of a leaf-8 dissection."""
+    if case == "t1_n8":
+        v = make_workload("helm2d_n32", n=8)
+        P = O.sparse_matrices(O.build_stencils(v, "local"), 8, 2)[2]
+    elif case == "t1_n16_paper":
+        v = make_workload("helm2d_n32", n=16)
+        P = O.sparse_matrices(O.build_stencils(v, "paper"), 16, 2)[2]
+    else:
+        v = make_workload("helm2d_n32", n=16)
+        P = O.build_stencils_multi(v, "paper", leaf=8, t_max=2)["P"]
+    N = v.size
+    y = np.random.default_rng(11).standard_normal(N)
+    x = O.solve_p(P, y)
+    Pd = P.toarray()
+    xd = np.linalg.solve(Pd, y)
+    cond = np.linalg.cond(Pd)
+    assert np.abs(x - xd).max() <= 1e-13 * cond * np.abs(xd).max()
+    assert np.linalg.norm(Pd @ x - y) <= 1e-12 * np.linalg.norm(Pd, 2) * np.linalg.norm(x)
+
+
 def test_unpreconditioned_gmres_stalls():
     v = make_workload("helm2d_n32")
     _, it, res, info = O.gmres_solve(v, gaussian_source(32, 2), maxiter=3)
