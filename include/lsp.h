@@ -257,6 +257,92 @@ lsp_status lsp_get_mode_used(const lsp_ctx* ctx, int* mode);
 lsp_status lsp_apply_operator_noalloc(int d, int n, const double* v_dev, const double* u_dev,
                                       double* y_dev, void* cuda_stream);
 
+/* ---- Applying the preconditioner (Sec. 3, Eq. QC and Eq. PC; Fig. nd; Table cost; Sec. 5) ----
+ *
+ * P = Q + C diag(v - s) has the sparsity of Q, so P^-1 is applied through a nested-dissection
+ * factorisation, and (L + diag v) u = f is solved by GMRES left-preconditioned with P^-1 C.
+ * 2D grids only (n a power of two, 4 <= n <= 1024); rows of a t = 1 build, or of a t = 2 build
+ * with nd_leaf = b (the t_j rule keeps every row inside the separators of that dissection).
+ *
+ * Elimination tree: the cross {x_0 = 0} U {x_1 = 0} last; before it, the boxes of the remaining
+ * open square, each split through its middle grid line (longer side first) down to leaf boxes
+ * of at most (b - 1) x (b - 1) points. Every separator is a line x_a = 0 (mod b). Each front
+ * (eliminated set E, ring R of ancestors' points) is inverted on E in place with row pivoting
+ * inside E; the figure of Sec. 3 groups the separators into edges and vertices instead, with the
+ * same leaf boxes and the same separator lines. */
+typedef struct {
+  int leaf;   /* b: power of two in [4, n]. 0: the nd_leaf of a t = 2 build, else 8 (Sec. 5) */
+} lsp_nd_opts;
+
+typedef struct {
+  int levels;           /* depth of the elimination tree + 1                                  */
+  int leaf;             /* b                                                                  */
+  int max_front;        /* largest front |E| + |R|                                            */
+  int factored;         /* 1 when a factorisation of the current stencils is held             */
+  int64_t fronts;       /* number of fronts                                                   */
+  int64_t front_bytes;  /* device bytes of the fronts (sum of (|E| + |R|)^2 * 8)              */
+  int64_t solve_bytes;  /* front bytes one solve reads (sum of (|E| + |R|) |E| + |E| |R|, x 8) */
+  double flops;         /* FP64 flops of the factorisation as run: 2 |E| (|E| + |R|)^2 a front  */
+  double flops_lu;      /* the multifrontal LU count 2/3 |E|^3 + 2 |E|^2 |R| + 2 |E| |R|^2    */
+} lsp_nd_info;
+
+/* Zero-initialised options (leaf 0). */
+void lsp_default_nd_opts(lsp_nd_opts* opts);
+
+/* Factorise the P rows of the last build (stream-ordered on the context stream; returns after
+ * the stream has finished, so the call's duration is the setup time T_NDsetup of Sec. 5). The
+ * symbolic plan of the dissection is made on the host once per (n, b, row pattern) and kept.
+ * Errors: LSP_ERR_STATE before a build; LSP_ERR_UNSUPPORTED for 1D/3D grids, n > 1024 or rows
+ * that cross the separators (t = 2 without nd_leaf); LSP_ERR_ARG for a bad b or b != nd_leaf;
+ * LSP_ERR_DEGENERATE when a pivot vanishes (P singular). A later build invalidates the factor. */
+lsp_status lsp_nd_factor(lsp_ctx* ctx, const lsp_nd_opts* opts);
+
+/* Host only (no context, no device): plan the dissection of an n x n grid with leaf b for the
+ * rows of a t = 1 build (t = 1) or of a t = 2 build with nd_leaf (t = 2) and report its sizes;
+ * the first `cap` depths (0 = the cross) also give their front count and |E|, |R| in count[],
+ * s[], r[] (any may be NULL). LSP_ERR_UNSUPPORTED with the reason in err (errcap bytes) when the
+ * rows or sizes do not fit; LSP_ERR_ARG for t outside {1, 2} or a NULL info. */
+lsp_status lsp_nd_plan_info(int n, int leaf, int t, int nd_leaf, lsp_nd_info* info, int cap,
+                            int* count, int* s, int* r, char* err, int errcap);
+
+/* Sizes and flop counts of the planned dissection. LSP_ERR_STATE if none was planned. */
+lsp_status lsp_nd_get_info(lsp_ctx* ctx, lsp_nd_info* info);
+
+/* x = P^-1 y for device vectors of n^d float64 (x may equal y); stream-ordered, deterministic.
+ * LSP_ERR_STATE unless lsp_nd_factor ran on the current stencils. */
+lsp_status lsp_nd_solve(lsp_ctx* ctx, const double* y_dev, double* x_dev);
+
+/* y = M u for M = Q, C or P of the last build (row j: sum over its neighbourhood columns,
+ * periodic wrap), device vectors of n^d float64 that must not alias; stream-ordered. */
+lsp_status lsp_apply_rows(lsp_ctx* ctx, char which, const double* u_dev, double* y_dev);
+
+typedef struct {
+  double rtol;     /* stop when |P^-1 C (f - A u)| <= rtol |P^-1 C f| (Sec. 5: 1e-6)              */
+  int restart;     /* Krylov dimension per cycle, 1..60 (Sec. 5: 40)                             */
+  int max_cycles;  /* restart cycles before giving up                                           */
+  int precond;     /* 1: left preconditioner P^-1 C (needs lsp_nd_factor); 0: none              */
+} lsp_gmres_opts;
+
+typedef struct {
+  int iterations;        /* inner (Arnoldi) iterations: N_iter of the tables of Sec. 5           */
+  int converged;         /* 1 when the preconditioned residual met rtol                          */
+  double resid_precond;  /* |P^-1 C (f - A u)| / |P^-1 C f| at exit (A = L + diag v)             */
+  double resid_true;     /* |f - A u| / |f|                                                      */
+} lsp_gmres_result;
+
+/* rtol 1e-6, restart 40, max_cycles 50, precond 1. */
+void lsp_default_gmres_opts(lsp_gmres_opts* opts);
+
+/* Solve (L + diag v) u = f by restarted GMRES with x0 = 0, modified Gram-Schmidt Arnoldi and
+ * Givens rotations; the inner loop stops when the least-squares residual reaches rtol |b|
+ * (b = P^-1 C f), a cycle ends with the explicit residual of the preconditioned system, and the
+ * next cycle restarts from it. f and u are n^d float64, both in device memory (on_device = 1)
+ * or both in host memory (0); the call returns after the stream has finished. Every vector
+ * operation runs on the device; the host reads one residual estimate per inner iteration.
+ * Errors: LSP_ERR_STATE before set_potential or, with precond, without a current factor. */
+lsp_status lsp_gmres(lsp_ctx* ctx, const lsp_gmres_opts* opts, const double* f, double* u,
+                     int on_device, lsp_gmres_result* result);
+
 /* Message of the last failed call on this context ("" if none). Never NULL. */
 const char* lsp_last_error(const lsp_ctx* ctx);
 

@@ -1,0 +1,665 @@
+// Numeric phases of the nested dissection of P (Sec. 3, Eq. QC; Fig. nd; Table cost), see
+// nd.h for the tree and the front layout:
+//  - assembly: a front = its children's Schur complements (extend-add through the ring maps)
+//    plus P's entries listed for it;
+//  - partial inversion of each front on its eliminated set E with row pivoting inside E
+//    (Gauss-Jordan sweep): in shared memory for small fronts, else in blocked steps of
+//    kNdPanel pivots (panel choice, row block, rank-kNdPanel update of the whole front);
+//  - the solve: one matrix-vector product per front going up the tree, one coming down.
+// Every reduction runs in a fixed order, so a factorisation and a solve are deterministic.
+#include <math.h>
+
+#include "nd.h"
+
+namespace lsp {
+namespace {
+
+constexpr int NP = kNdPanel;
+
+__global__ void k_nd_extend(double* __restrict__ F, const double* __restrict__ Fc,
+                            const int32_t* __restrict__ inv, int count, int f, int nchild,
+                            int fc, int sc) {
+  const int64_t ff = (int64_t)f * f, total = (int64_t)count * ff;
+  const int64_t fcc = (int64_t)fc * fc;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = idx / ff;
+    const int rem = (int)(idx - p * ff);
+    const int i = rem / f, j = rem - i * f;
+    const int32_t* iv = inv + p * f * 2;
+    double acc = 0.0;
+    for (int c = 0; c < nchild; ++c) {
+      const int ai = iv[i * 2 + c], aj = iv[j * 2 + c];
+      if (ai >= 0 && aj >= 0) {
+        const int64_t child = nchild == 1 ? p : 2 * p + c;
+        acc += Fc[child * fcc + (int64_t)(sc + ai) * fc + sc + aj];
+      }
+    }
+    F[idx] = acc;
+  }
+}
+
+__global__ void k_nd_scatter(double* __restrict__ F, const double* __restrict__ rows,
+                             const int32_t* __restrict__ dst, const int32_t* __restrict__ src,
+                             int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    F[dst[e]] += rows[src[e]];
+}
+
+// argmax of |value| over a warp with ties to the smaller index
+__device__ __forceinline__ void warp_argmax(double& best, int& bi) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+}
+
+// Partial inversion of one front (f <= kNdSmallFront) in shared memory, one pivot at a time.
+// Pivot k: the row of largest |F[i][k]| among the rows k..s-1 still unpivoted; then
+//   F[k][k] <- 1/F[k][k], F[k][j] <- F[k][j]/F[k][k], F[i][k] <- -F[i][k]/F[k][k],
+//   F[i][j] <- F[i][j] - F[i][k] F[k][j]/F[k][k]   (i, j != k).
+__global__ void __launch_bounds__(256) k_nd_sweep_small(double* __restrict__ fronts, int f, int s,
+                                                        int32_t* __restrict__ perm,
+                                                        int32_t* __restrict__ err) {
+  extern __shared__ double sm[];
+  double* F = sm;
+  double* colk = F + f * f;
+  double* rowk = colk + f;
+  __shared__ int sperm[kNdSmallFront];
+  __shared__ int piv, bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  double* G = fronts + (int64_t)blockIdx.x * f * f;
+  for (int e = tid; e < f * f; e += nt) F[e] = G[e];
+  for (int e = tid; e < s; e += nt) sperm[e] = e;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < s; ++k) {
+    if (warp == 0) {
+      double best = -1.0;
+      int bi = s;
+      for (int i = k + lane; i < s; i += 32) {
+        const double a = fabs(F[i * f + k]);
+        if (a > best) {
+          best = a;
+          bi = i;
+        }
+      }
+      warp_argmax(best, bi);
+      if (lane == 0) {
+        if (!(best > 0.0) || !isfinite(best)) {
+          bad = 1;
+          atomicOr(err, 1);
+        }
+        piv = bi < s ? bi : k;
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const int p = piv;
+    if (p != k) {
+      for (int j = tid; j < f; j += nt) {
+        const double a = F[k * f + j];
+        F[k * f + j] = F[p * f + j];
+        F[p * f + j] = a;
+      }
+      if (tid == 0) {
+        const int t = sperm[k];
+        sperm[k] = sperm[p];
+        sperm[p] = t;
+      }
+      __syncthreads();
+    }
+    const double dinv = 1.0 / F[k * f + k];
+    for (int j = tid; j < f; j += nt) {
+      rowk[j] = F[k * f + j] * dinv;
+      colk[j] = F[j * f + k];
+    }
+    __syncthreads();
+    for (int i = warp; i < f; i += nt / 32) {
+      double* Fi = F + i * f;
+      if (i == k) {
+        for (int j = lane; j < f; j += 32) Fi[j] = j == k ? dinv : rowk[j];
+      } else {
+        const double ci = colk[i];
+        for (int j = lane; j < f; j += 32) Fi[j] = j == k ? -ci * dinv : fma(-ci, rowk[j], Fi[j]);
+      }
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < f * f; e += nt) G[e] = F[e];
+  for (int e = tid; e < s; e += nt) perm[(int64_t)blockIdx.x * s + e] = sperm[e];
+}
+
+// ---- blocked partial inversion: one step eliminates the pivot columns K = [k, k + nb) ----
+// swaps layout per front: [0] = number of entries q, then dst[q] at 1 + q, src[q] at
+// 1 + 2 NP + q: after the step, position dst holds the row that was at position src.
+constexpr int kSwapInts = 1 + 4 * NP;
+
+// Part 1, one CTA per front: choose nb pivot rows among positions k..s-1 by partial pivoting
+// on the panel F[k.., K]; record the row exchanges, update perm, write the permuted column
+// block cbuf[x][c] = F[src(x)][k + c] for every row x, and the inverse of the pivot block.
+__global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fronts, int f, int s,
+                                                  int k, int nb, int32_t* __restrict__ perm,
+                                                  double* __restrict__ cbuf,
+                                                  double* __restrict__ pinv,
+                                                  int32_t* __restrict__ swaps,
+                                                  int32_t* __restrict__ err) {
+  extern __shared__ double sm[];
+  const int m = s - k;
+  double* pan = sm;                                   // m x NP
+  uint8_t* used = (uint8_t*)(pan + (size_t)m * NP);   // m
+  __shared__ int sel[NP];
+  __shared__ double wbest[8];
+  __shared__ int wbi[8];
+  __shared__ int bad, nq;
+  __shared__ int dstp[2 * NP], srcp[2 * NP];
+  __shared__ double aug[NP][2 * NP];
+  __shared__ int gpiv;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  const int64_t fid = blockIdx.x;
+  const double* F = fronts + fid * f * f;
+  for (int i = tid; i < m; i += nt) {
+    for (int c = 0; c < NP; ++c) pan[i * NP + c] = c < nb ? F[(int64_t)(k + i) * f + k + c] : 0.0;
+    used[i] = 0;
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    double best = -1.0;
+    int bi = m;
+    for (int i = tid; i < m; i += nt) {
+      if (used[i]) continue;
+      const double a = fabs(pan[i * NP + j]);
+      if (a > best) {
+        best = a;
+        bi = i;
+      }
+    }
+    warp_argmax(best, bi);
+    if (lane == 0) {
+      wbest[warp] = best;
+      wbi[warp] = bi;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double b = wbest[0];
+      int ix = wbi[0];
+      for (int w = 1; w < nt / 32; ++w)
+        if (wbest[w] > b || (wbest[w] == b && wbi[w] < ix)) {
+          b = wbest[w];
+          ix = wbi[w];
+        }
+      if (!(b > 0.0) || !isfinite(b) || ix >= m) {
+        bad = 1;
+        atomicOr(err, 2);
+        ix = 0;
+      }
+      sel[j] = ix;
+      used[ix] = 1;
+    }
+    __syncthreads();
+    if (bad) {  // leave a step that the next kernels read safely (no exchanges)
+      if (tid == 0) swaps[fid * kSwapInts] = 0;
+      return;
+    }
+    const int pr = sel[j];
+    const double pv = pan[pr * NP + j];
+    for (int i = tid; i < m; i += nt) {
+      if (used[i]) continue;
+      const double l = pan[i * NP + j] / pv;
+      for (int c = j + 1; c < nb; ++c) pan[i * NP + c] = fma(-l, pan[pr * NP + c], pan[i * NP + c]);
+    }
+    __syncthreads();
+  }
+  // row exchanges, applied in order: position k + j takes the row chosen j-th
+  if (tid == 0) {
+    int q = 0;
+    for (int j = 0; j < nb; ++j) {
+      const int want = k + sel[j], target = k + j;
+      int qw = -1, qt = -1;
+      for (int a = 0; a < q; ++a) {
+        if (srcp[a] == want) qw = a;
+        if (dstp[a] == target) qt = a;
+      }
+      if (qw < 0) {  // still at its own position
+        for (int a = 0; a < q; ++a)
+          if (dstp[a] == want) qw = a;
+        if (qw < 0) {
+          dstp[q] = want;
+          srcp[q] = want;
+          qw = q++;
+        }
+      }
+      if (qt < 0) {
+        dstp[q] = target;
+        srcp[q] = target;
+        qt = q++;
+      }
+      const int t = srcp[qt];
+      srcp[qt] = srcp[qw];
+      srcp[qw] = t;
+    }
+    nq = q;
+    int32_t* sw = swaps + fid * kSwapInts;
+    sw[0] = q;
+    int32_t* pf = perm + fid * s;
+    int old[2 * NP];
+    for (int a = 0; a < q; ++a) old[a] = pf[srcp[a]];
+    for (int a = 0; a < q; ++a) {
+      pf[dstp[a]] = old[a];
+      sw[1 + a] = dstp[a];
+      sw[1 + 2 * NP + a] = srcp[a];
+    }
+  }
+  __syncthreads();
+  const int q = nq;
+  // the permuted column block
+  double* cb = cbuf + fid * (int64_t)f * NP;
+  for (int x = tid; x < f; x += nt) {
+    int src = x;
+    for (int a = 0; a < q; ++a)
+      if (dstp[a] == x) src = srcp[a];
+    for (int c = 0; c < NP; ++c) cb[(int64_t)x * NP + c] = c < nb ? F[(int64_t)src * f + k + c] : 0.0;
+  }
+  // inverse of the pivot block by Gauss-Jordan with partial pivoting: [A | I] -> [I | A^-1]
+  if (tid < NP * 2 * NP) {
+    const int r = tid / (2 * NP), c = tid % (2 * NP);
+    double v = 0.0;
+    if (r < nb) {
+      if (c < NP) {
+        int src = k + r;
+        for (int a = 0; a < q; ++a)
+          if (dstp[a] == k + r) src = srcp[a];
+        v = c < nb ? F[(int64_t)src * f + k + c] : 0.0;
+      } else {
+        v = (c - NP) == r ? 1.0 : 0.0;
+      }
+    }
+    aug[r][c] = v;
+  }
+  __syncthreads();
+  for (int j = 0; j < nb; ++j) {
+    if (tid == 0) {
+      int p = j;
+      double b = fabs(aug[j][j]);
+      for (int r = j + 1; r < nb; ++r)
+        if (fabs(aug[r][j]) > b) {
+          b = fabs(aug[r][j]);
+          p = r;
+        }
+      gpiv = p;
+      if (!(b > 0.0)) atomicOr(err, 4);
+    }
+    __syncthreads();
+    const int p = gpiv;
+    if (p != j && tid < 2 * NP) {
+      const double t = aug[j][tid];
+      aug[j][tid] = aug[p][tid];
+      aug[p][tid] = t;
+    }
+    __syncthreads();
+    const double d = 1.0 / aug[j][j];
+    double lr = 0.0, pjc = 0.0;
+    const int r = tid / (2 * NP), c = tid % (2 * NP);
+    if (tid < NP * 2 * NP) {
+      lr = aug[r][j];
+      pjc = aug[j][c] * d;
+    }
+    __syncthreads();
+    if (tid < NP * 2 * NP && r < nb) aug[r][c] = r == j ? pjc : fma(-lr, pjc, aug[r][c]);
+    __syncthreads();
+  }
+  if (tid < NP * NP) {
+    const int r = tid / NP, c = tid % NP;
+    pinv[fid * NP * NP + tid] = (r < nb && c < nb) ? aug[r][NP + c] : 0.0;
+  }
+}
+
+// Part 2: rows K become A_KK^-1 F[K, j] for the columns j outside K (after applying the row
+// exchanges to those columns), and the column block becomes [A_KK^-1 on K; -cbuf A_KK^-1 off K].
+__global__ void __launch_bounds__(256) k_nd_rowblock(double* __restrict__ fronts, int f, int k,
+                                                     int nb, int tiles_w,
+                                                     const double* __restrict__ cbuf,
+                                                     const double* __restrict__ pinv,
+                                                     const int32_t* __restrict__ swaps) {
+  __shared__ double pi[NP][NP];
+  __shared__ int dstp[2 * NP], srcp[2 * NP], kq[NP];
+  __shared__ int nq;
+  const int tid = threadIdx.x;
+  const int64_t fid = blockIdx.y;
+  double* F = fronts + fid * f * f;
+  const int32_t* sw = swaps + fid * kSwapInts;
+  if (tid < NP * NP) pi[tid / NP][tid % NP] = pinv[fid * NP * NP + tid];
+  if (tid == 0) {
+    int q0 = sw[0];
+    q0 = q0 < 0 || q0 > 2 * NP ? 0 : q0;
+    for (int a = 0; a < q0; ++a) {
+      const int dp = sw[1 + a], sp = sw[1 + 2 * NP + a];
+      if (dp < 0 || dp >= f || sp < 0 || sp >= f) q0 = 0;
+    }
+    nq = q0;
+  }
+  __syncthreads();
+  const int q = nq;
+  if (tid < q) {
+    dstp[tid] = sw[1 + tid];
+    srcp[tid] = sw[1 + 2 * NP + tid];
+  }
+  __syncthreads();
+  if (tid < nb) {
+    int a0 = -1;
+    for (int a = 0; a < q; ++a)
+      if (dstp[a] == k + tid) a0 = a;
+    kq[tid] = a0;
+  }
+  __syncthreads();
+  if ((int)blockIdx.x < tiles_w) {
+    const int j = blockIdx.x * blockDim.x + tid;
+    if (j >= f || (j >= k && j < k + nb)) return;
+    double val[2 * NP];
+    for (int a = 0; a < 2 * NP; ++a)
+      if (a < q) val[a] = F[(int64_t)srcp[a] * f + j];
+    double rv[NP];
+    for (int c = 0; c < NP; ++c) {
+      double v = 0.0;
+      if (c < nb) {
+        v = F[(int64_t)(k + c) * f + j];
+        for (int a = 0; a < 2 * NP; ++a)
+          if (a == kq[c]) v = val[a];
+      }
+      rv[c] = v;
+    }
+    for (int c = 0; c < nb; ++c) {
+      double w = 0.0;
+      for (int mm = 0; mm < NP; ++mm) w = fma(pi[c][mm], rv[mm], w);
+      F[(int64_t)(k + c) * f + j] = w;
+    }
+    for (int a = 0; a < 2 * NP; ++a)
+      if (a < q && (dstp[a] < k || dstp[a] >= k + nb)) F[(int64_t)dstp[a] * f + j] = val[a];
+  } else {
+    const int x = (blockIdx.x - tiles_w) * blockDim.x + tid;
+    if (x >= f) return;
+    if (x >= k && x < k + nb) {
+      for (int c = 0; c < nb; ++c) F[(int64_t)x * f + k + c] = pi[x - k][c];
+    } else {
+      const double* cx = cbuf + fid * (int64_t)f * NP + (int64_t)x * NP;
+      double cr[NP];
+      for (int mm = 0; mm < NP; ++mm) cr[mm] = cx[mm];
+      for (int c = 0; c < nb; ++c) {
+        double acc = 0.0;
+        for (int mm = 0; mm < NP; ++mm) acc = fma(cr[mm], pi[mm][c], acc);
+        F[(int64_t)x * f + k + c] = -acc;
+      }
+    }
+  }
+}
+
+// Part 3: F[i][j] -= cbuf[i][:] . F[K][j] for every i, j outside K (64 x 64 tiles).
+constexpr int kUT = 64;
+__global__ void __launch_bounds__(256) k_nd_update(double* __restrict__ fronts, int f, int k,
+                                                   int nb, int tiles_j,
+                                                   const double* __restrict__ cbuf) {
+  __shared__ double cs[kUT][NP + 1];
+  __shared__ double ws[NP][kUT];
+  const int tid = threadIdx.x;
+  const int64_t fid = blockIdx.y;
+  double* F = fronts + fid * f * f;
+  const int ti = blockIdx.x / tiles_j, tj = blockIdx.x % tiles_j;
+  const int i0 = ti * kUT, j0 = tj * kUT;
+  const double* cb = cbuf + fid * (int64_t)f * NP;
+  for (int e = tid; e < kUT * NP; e += blockDim.x) {
+    const int r = e / NP, c = e % NP;
+    cs[r][c] = (i0 + r < f) ? cb[(int64_t)(i0 + r) * NP + c] : 0.0;
+    const int c2 = e / kUT, col = e % kUT;
+    ws[c2][col] = (c2 < nb && j0 + col < f) ? F[(int64_t)(k + c2) * f + j0 + col] : 0.0;
+  }
+  __syncthreads();
+  const int ty = tid / 16, tx = tid % 16;
+  double acc[4][4];
+  bool rok[4], cok[4];
+  for (int a = 0; a < 4; ++a) {
+    const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * a;
+    rok[a] = i < f && (i < k || i >= k + nb);
+    cok[a] = j < f && (j < k || j >= k + nb);
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      acc[a][b] = (rok[a] && cok[b]) ? F[(int64_t)(i0 + ty + 16 * a) * f + j0 + tx + 16 * b] : 0.0;
+#pragma unroll
+  for (int c = 0; c < NP; ++c) {
+    double cr[4], wr[4];
+    for (int a = 0; a < 4; ++a) cr[a] = cs[ty + 16 * a][c];
+    for (int b = 0; b < 4; ++b) wr[b] = ws[c][tx + 16 * b];
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b) acc[a][b] = fma(-cr[a], wr[b], acc[a][b]);
+  }
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      if (rok[a] && cok[b]) F[(int64_t)(i0 + ty + 16 * a) * f + j0 + tx + 16 * b] = acc[a][b];
+}
+
+// ---- solve ----
+// Going up: w = [y_E; 0] + children's u (through the ring maps), w'_E = w_E[perm];
+// z = A^-1 w_E = F[E, E] w'_E; u = w_R + F[R, E] w'_E. 64 rows of one front per CTA.
+__global__ void __launch_bounds__(256) k_nd_fwd(const double* __restrict__ F, int f, int s, int r,
+                                                const int32_t* __restrict__ E,
+                                                const int32_t* __restrict__ perm,
+                                                const int32_t* __restrict__ inv, int nchild,
+                                                const double* __restrict__ uc, int rc,
+                                                const double* __restrict__ y,
+                                                double* __restrict__ z, double* __restrict__ u) {
+  extern __shared__ double wE[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t p = blockIdx.y;
+  const double* Fp = F + p * f * f;
+  const int32_t* iv = nchild ? inv + p * f * 2 : nullptr;
+  auto wsum = [&](int i) -> double {
+    double v = i < s ? y[E[p * s + i]] : 0.0;
+    for (int c = 0; c < nchild; ++c) {
+      const int a = iv[i * 2 + c];
+      if (a >= 0) v += uc[(nchild == 1 ? p : 2 * p + c) * rc + a];
+    }
+    return v;
+  };
+  for (int m = tid; m < s; m += blockDim.x) wE[m] = wsum(perm[p * s + m]);
+  __syncthreads();
+  const int row0 = blockIdx.x * 64;
+  for (int rr = warp; rr < 64; rr += blockDim.x / 32) {
+    const int i = row0 + rr;
+    if (i >= f) break;
+    const double* Fi = Fp + (int64_t)i * f;
+    double acc = 0.0;
+    for (int m = lane; m < s; m += 32) acc = fma(Fi[m], wE[m], acc);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) {
+      if (i < s)
+        z[p * s + i] = acc;
+      else
+        u[p * r + (i - s)] = wsum(i) + acc;
+    }
+  }
+}
+
+// Coming down: x_E = z - F[E, R] x_R, x_R read from the ancestors' results.
+__global__ void __launch_bounds__(256) k_nd_bwd(const double* __restrict__ F, int f, int s, int r,
+                                                const int32_t* __restrict__ E,
+                                                const int32_t* __restrict__ R,
+                                                const double* __restrict__ z,
+                                                double* __restrict__ x) {
+  extern __shared__ double xR[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t p = blockIdx.y;
+  const double* Fp = F + p * f * f;
+  for (int m = tid; m < r; m += blockDim.x) xR[m] = x[R[p * r + m]];
+  __syncthreads();
+  const int row0 = blockIdx.x * 64;
+  for (int rr = warp; rr < 64; rr += blockDim.x / 32) {
+    const int i = row0 + rr;
+    if (i >= s) break;
+    const double* Fi = Fp + (int64_t)i * f + s;
+    double acc = 0.0;
+    for (int m = lane; m < r; m += 32) acc = fma(Fi[m], xR[m], acc);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) x[E[p * s + i]] = z[p * s + i] - acc;
+  }
+}
+
+// y_j = sum_a rows[j][a] u[(j + o_a) mod n], o_a in [-t, t]^d lexicographic (last fastest).
+__global__ void k_apply_rows(const double* __restrict__ rows, int mu, int d, int n, int t,
+                             const double* __restrict__ u, double* __restrict__ y, int64_t N) {
+  const int w = 2 * t + 1;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    int x[3] = {0, 0, 0};
+    int64_t rem = j;
+    for (int a = d - 1; a >= 0; --a) {
+      x[a] = (int)(rem % n);
+      rem /= n;
+    }
+    const double* rj = rows + j * mu;
+    double acc = 0.0;
+    for (int a = 0; a < mu; ++a) {
+      int o = a;
+      int64_t col = 0;
+      int64_t stride = 1;
+      for (int b = d - 1; b >= 0; --b) {
+        const int ob = o % w - t;
+        o /= w;
+        col += (int64_t)((x[b] + ob + n) % n) * stride;
+        stride *= n;
+      }
+      acc = fma(rj[a], u[col], acc);
+    }
+    y[j] = acc;
+  }
+}
+
+__global__ void k_nd_iota(int32_t* __restrict__ perm, int count, int s) {
+  const int64_t total = (int64_t)count * s;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    perm[e] = (int32_t)(e % s);
+}
+
+int grid_for(int64_t n, int threads) {
+  const int64_t b = (n + threads - 1) / threads;
+  return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+}  // namespace
+
+cudaError_t launch_nd_assemble(lsp_ctx* c, int depth, const double* rows) {
+  NdState& S = *c->nd;
+  const NdLevel& lv = S.plan.lv[depth];
+  double* F = (double*)S.fronts.p + lv.front_off;
+  const int64_t total = (int64_t)lv.count * lv.f * lv.f;
+  int t = timer_begin(c, "nd_assemble");
+  if (lv.nchild == 0) {
+    cudaError_t e = cudaMemsetAsync(F, 0, sizeof(double) * total, c->stream);
+    if (e != cudaSuccess) return e;
+  } else {
+    const NdLevel& cl = S.plan.lv[depth + 1];
+    k_nd_extend<<<grid_for(total, 256), 256, 0, c->stream>>>(
+        F, (const double*)S.fronts.p + cl.front_off, (const int32_t*)S.inv.p + lv.inv_off,
+        lv.count, lv.f, lv.nchild, cl.f, cl.s);
+  }
+  if (lv.asm_n > 0)
+    k_nd_scatter<<<grid_for(lv.asm_n, 256), 256, 0, c->stream>>>(
+        F, rows, (const int32_t*)S.asm_dst.p + lv.asm_off, (const int32_t*)S.asm_src.p + lv.asm_off,
+        lv.asm_n);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nd_sweep(lsp_ctx* c, int depth) {
+  NdState& S = *c->nd;
+  const NdLevel& lv = S.plan.lv[depth];
+  double* F = (double*)S.fronts.p + lv.front_off;
+  int32_t* perm = (int32_t*)S.perm.p + lv.perm_off;
+  int32_t* err = (int32_t*)S.err.p;
+  if (lv.s == 0) return cudaSuccess;
+  int t = timer_begin(c, "nd_sweep");
+  if (lv.f <= kNdSmallFront) {
+    const size_t smem = sizeof(double) * ((size_t)lv.f * lv.f + 2 * lv.f);
+    cudaError_t e = cudaFuncSetAttribute(k_nd_sweep_small,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_nd_sweep_small<<<lv.count, 256, smem, c->stream>>>(F, lv.f, lv.s, perm, err);
+    timer_end(c, t);
+    return cudaGetLastError();
+  }
+  // blocked steps; perm starts as the identity
+  k_nd_iota<<<grid_for((int64_t)lv.count * lv.s, 256), 256, 0, c->stream>>>(perm, lv.count, lv.s);
+  const size_t psmem = sizeof(double) * (size_t)lv.s * NP + (size_t)lv.s + 16;
+  cudaError_t e =
+      cudaFuncSetAttribute(k_nd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+  if (e != cudaSuccess) return e;
+  const int tiles_w = (lv.f + 255) / 256;
+  const int tiles_c = (lv.f + 255) / 256;
+  const int tiles_u = (lv.f + kUT - 1) / kUT;
+  for (int k = 0; k < lv.s; k += NP) {
+    const int nb = lv.s - k < NP ? lv.s - k : NP;
+    k_nd_panel<<<lv.count, 256, psmem, c->stream>>>(F, lv.f, lv.s, k, nb, perm,
+                                                    (double*)S.cbuf.p, (double*)S.pinv.p,
+                                                    (int32_t*)S.swaps.p, err);
+    k_nd_rowblock<<<dim3(tiles_w + tiles_c, lv.count), 256, 0, c->stream>>>(
+        F, lv.f, k, nb, tiles_w, (const double*)S.cbuf.p, (const double*)S.pinv.p,
+        (const int32_t*)S.swaps.p);
+    k_nd_update<<<dim3(tiles_u * tiles_u, lv.count), 256, 0, c->stream>>>(
+        F, lv.f, k, nb, tiles_u, (const double*)S.cbuf.p);
+  }
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nd_solve(lsp_ctx* c, const double* y, double* x) {
+  NdState& S = *c->nd;
+  const NdPlan& P = S.plan;
+  const int L = (int)P.lv.size();
+  const double* Fb = (const double*)S.fronts.p;
+  double* z = (double*)S.z.p;
+  double* u = (double*)S.u.p;
+  const int32_t* E = (const int32_t*)S.E.p;
+  const int32_t* R = (const int32_t*)S.R.p;
+  int t = timer_begin(c, "nd_solve");
+  for (int d = L - 1; d >= 0; --d) {
+    const NdLevel& lv = P.lv[d];
+    const NdLevel* cl = lv.nchild ? &P.lv[d + 1] : nullptr;
+    dim3 grid((lv.f + 63) / 64, lv.count);
+    k_nd_fwd<<<grid, 256, sizeof(double) * (lv.s > 0 ? lv.s : 1), c->stream>>>(
+        Fb + lv.front_off, lv.f, lv.s, lv.r, E + lv.E_off, (const int32_t*)S.perm.p + lv.perm_off,
+        lv.nchild ? (const int32_t*)S.inv.p + lv.inv_off : nullptr, lv.nchild,
+        cl ? u + cl->u_off : nullptr, cl ? cl->r : 0, y, z + lv.z_off, u + lv.u_off);
+  }
+  for (int d = 0; d < L; ++d) {
+    const NdLevel& lv = P.lv[d];
+    dim3 grid((lv.s + 63) / 64, lv.count);
+    k_nd_bwd<<<grid, 256, sizeof(double) * (lv.r > 0 ? lv.r : 1), c->stream>>>(
+        Fb + lv.front_off, lv.f, lv.s, lv.r, E + lv.E_off, R + lv.R_off, z + lv.z_off, x);
+  }
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t nd_prepare_kernels(int max_smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_nd_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       max_smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_nd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
+}
+
+cudaError_t launch_apply_rows(lsp_ctx* c, const double* rows, int mu, int t, const double* u,
+                              double* y) {
+  const int64_t N = c->geo.N;
+  int tm = timer_begin(c, "apply_rows");
+  k_apply_rows<<<grid_for(N, 256), 256, 0, c->stream>>>(rows, mu, c->geo.d, c->geo.n, t, u, y, N);
+  timer_end(c, tm);
+  return cudaGetLastError();
+}
+
+}  // namespace lsp

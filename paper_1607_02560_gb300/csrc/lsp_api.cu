@@ -536,6 +536,7 @@ lsp_status lsp_destroy(lsp_ctx* c) {
   if (c->h_list) cudaFreeHost(c->h_list);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   if (c->graph) cudaGraphExecDestroy(c->graph);
+  nd_free(c->nd);
   delete c;
   return LSP_OK;
 }
@@ -610,6 +611,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
       CUDA_OK(c, launch_learned_rows(c, c->mlp));
       c->built = true;
       c->built_learned = true;
+      ++c->build_gen;
       c->mode_used = LSP_LEARNED;
       c->t_built = 1;
       c->leaf_built = 0;
@@ -784,6 +786,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   }
   if (st == LSP_OK) {
     c->built = true;
+    ++c->build_gen;
     c->built_learned = false;
     c->mode_used = o.mode;
     c->t_built = o.t;

@@ -10,6 +10,9 @@
 #include "../../include/lsp.h"
 
 struct lsp_mlp;
+namespace lsp {
+struct NdState;
+}
 
 namespace lsp {
 
@@ -132,6 +135,11 @@ struct lsp_ctx {
   bool built_learned = false;
   int mode_used = -1;
 
+  // nested dissection of P and the GMRES workspace (lsp_nd_factor, lsp_gmres); build_gen
+  // counts successful builds so that a factorisation of older rows is never used
+  lsp::NdState* nd = nullptr;
+  int64_t build_gen = 0;
+
   // graph cache
   cudaGraphExec_t graph = nullptr;
   std::vector<int64_t> graph_key;
@@ -167,6 +175,7 @@ cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count);
 cudaError_t launch_sidx(lsp_ctx* c, int policy, const int32_t* count);
 cudaError_t launch_colidx(lsp_ctx* c);
 cudaError_t launch_apply(lsp_ctx* c, const double* u, double* y);
+void nd_free(NdState* s);
 cudaError_t upload_sym(lsp_ctx* c);
 cudaError_t launch_learned_rows(lsp_ctx* c, lsp_mlp* m);
 bool mlp_input_range(lsp_mlp* m, float* lo, float* hi);

@@ -41,6 +41,30 @@ class StencilOpts(ctypes.Structure):
                 ("use_graph", ctypes.c_int), ("nd_leaf", ctypes.c_int)]
 
 
+class NdOpts(ctypes.Structure):
+    _fields_ = [("leaf", ctypes.c_int)]
+
+
+class NdInfo(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("leaf", ctypes.c_int), ("max_front", ctypes.c_int),
+                ("factored", ctypes.c_int), ("fronts", ctypes.c_int64),
+                ("front_bytes", ctypes.c_int64), ("solve_bytes", ctypes.c_int64),
+                ("flops", ctypes.c_double), ("flops_lu", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class GmresOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("precond", ctypes.c_int)]
+
+
+class GmresResult(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("resid_precond", ctypes.c_double), ("resid_true", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -92,6 +116,17 @@ def lib() -> ctypes.CDLL:
         "lsp_mlp_last_error": (ctypes.c_char_p, [vp]),
         "lsp_set_mlp": (ctypes.c_int, [vp, vp]),
         "lsp_get_mode_used": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
+        "lsp_default_nd_opts": (None, [ctypes.POINTER(NdOpts)]),
+        "lsp_nd_factor": (ctypes.c_int, [vp, ctypes.POINTER(NdOpts)]),
+        "lsp_nd_get_info": (ctypes.c_int, [vp, ctypes.POINTER(NdInfo)]),
+        "lsp_nd_plan_info": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, ctypes.POINTER(NdInfo), ctypes.c_int,
+                                             vp, vp, vp, ctypes.c_char_p, ctypes.c_int]),
+        "lsp_nd_solve": (ctypes.c_int, [vp, vp, vp]),
+        "lsp_apply_rows": (ctypes.c_int, [vp, ctypes.c_char, vp, vp]),
+        "lsp_default_gmres_opts": (None, [ctypes.POINTER(GmresOpts)]),
+        "lsp_gmres": (ctypes.c_int, [vp, ctypes.POINTER(GmresOpts), vp, vp, ctypes.c_int,
+                                      ctypes.POINTER(GmresResult)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -137,6 +172,25 @@ def apply_operator_noalloc(d: int, n: int, v, u, y, stream=None) -> None:
                                           ctypes.c_void_p(stream.cuda_stream))
     if st != LSP_OK:
         raise LspError(st, f"lsp_apply_operator_noalloc(d={d}, n={n}) failed")
+
+
+def nd_plan_info(n: int, leaf: int = 8, t: int = 1, nd_leaf: int = 0) -> dict:
+    """Host-only plan of the nested dissection (lsp_nd_plan_info): sizes, flop counts and the
+    (count, |E|, |R|) of every depth, depth 0 being the cross."""
+    info = NdInfo()
+    cap = 64
+    cnt = np.zeros(cap, dtype=np.int32)
+    s = np.zeros(cap, dtype=np.int32)
+    r = np.zeros(cap, dtype=np.int32)
+    err = ctypes.create_string_buffer(256)
+    st = lib().lsp_nd_plan_info(n, leaf, t, nd_leaf, ctypes.byref(info), cap, _ptr(cnt),
+                                _ptr(s), _ptr(r), err, 256)
+    if st != LSP_OK:
+        raise LspError(st, err.value.decode())
+    out = info.as_dict()
+    L = info.levels
+    out["depths"] = [(int(cnt[d]), int(s[d]), int(r[d])) for d in range(min(L, cap))]
+    return out
 
 
 def default_opts() -> StencilOpts:
@@ -268,6 +322,53 @@ class Context:
 
     def synchronize(self):
         self._check(lib().lsp_synchronize(self.h), "synchronize")
+
+    # ---- applying the preconditioner: nested dissection of P, GMRES ----
+    def nd_factor(self, leaf: int = 0):
+        """Factorise the current P rows by nested dissection (returns when done)."""
+        o = NdOpts()
+        o.leaf = int(leaf)
+        self._check(lib().lsp_nd_factor(self.h, ctypes.byref(o)), "nd_factor")
+
+    def nd_info(self) -> dict:
+        info = NdInfo()
+        self._check(lib().lsp_nd_get_info(self.h, ctypes.byref(info)), "nd_get_info")
+        return info.as_dict()
+
+    def nd_solve(self, y, x):
+        """x = P^-1 y for torch CUDA tensors (n^d float64; x may be y). Stream-ordered."""
+        if not (_on_device(y) and _on_device(x)):
+            raise ValueError("nd_solve takes device tensors")
+        self._check(lib().lsp_nd_solve(self.h, _ptr(y), _ptr(x)), "nd_solve")
+
+    def apply_rows(self, which: str, u, y):
+        """y = M u for M = Q, C or P of the last build (torch CUDA tensors). Stream-ordered."""
+        if not (_on_device(u) and _on_device(y)):
+            raise ValueError("apply_rows takes device tensors")
+        self._check(lib().lsp_apply_rows(self.h, which.encode(), _ptr(u), _ptr(y)), "apply_rows")
+
+    def gmres(self, f, u=None, rtol: float = 1e-6, restart: int = 40, max_cycles: int = 50,
+              precond: bool = True):
+        """Solve (L + diag v) u = f by GMRES preconditioned with P^-1 C (Sec. 5 settings by
+        default). f and u: both numpy arrays or both torch CUDA tensors of n^d float64.
+        Returns (u, result dict with iterations, converged, resid_precond, resid_true)."""
+        if u is None:
+            if _on_device(f):
+                import torch
+                u = torch.empty_like(f)
+            else:
+                u = np.empty_like(np.ascontiguousarray(f, dtype=np.float64))
+        if _on_device(f) != _on_device(u):
+            raise ValueError("f and u must both be on the device or both on the host")
+        if not _on_device(f):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+        o = GmresOpts()
+        lib().lsp_default_gmres_opts(ctypes.byref(o))
+        o.rtol, o.restart, o.max_cycles, o.precond = rtol, restart, max_cycles, int(bool(precond))
+        res = GmresResult()
+        self._check(lib().lsp_gmres(self.h, ctypes.byref(o), _ptr(f), _ptr(u), _on_device(f),
+                                    ctypes.byref(res)), "gmres")
+        return u, {name: getattr(res, name) for name, _ in res._fields_}
 
     def set_mlp(self, mlp):
         """Attach a trained Mlp for mode="learned" builds (None detaches)."""

@@ -1,0 +1,268 @@
+"""Applying the preconditioner on the GPU (Sec. 3, Eq. QC and Eq. PC; Fig. nd; Sec. 5) against
+the CPU oracle:
+
+* lsp_apply_rows: Q u, C u, P u equal the oracle's sparse products of the exported rows;
+* lsp_nd_solve: x = P^-1 y from the nested-dissection factor equals the oracle's sparse-LU
+  solve of the same P within the forward-error bound of the problem's condition number, with a
+  backward error at the rounding level, for t = 1 rows, multi-t rows and the full-size grid;
+* lsp_gmres: the GMRES(40) iteration counts equal the oracle's (stored golden counts at
+  n = 32, counts computed here at n = 256) and the solutions agree;
+* the unsupported and out-of-order calls fail cleanly; solves are deterministic.
+"""
+
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse
+import scipy.sparse.linalg
+
+import oracle as O
+from lsp_inputs import gaussian_source, make_workload
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+U = 2.0 ** -53
+_STREAM = []
+
+
+def ctx_for(v):
+    import torch
+    from paper_1607_02560_gb300 import Context, build
+    build.build()
+    if not _STREAM:
+        _STREAM.append(torch.cuda.Stream())
+    return Context(v.ndim, v.shape[0], stream=_STREAM[0])
+
+
+def csr(ctx, which, N):
+    rowptr, colidx, vals = ctx.export_sparse_rows(which)
+    return scipy.sparse.csr_matrix((vals, colidx, rowptr), shape=(N, N))
+
+
+def dev(a):
+    """A device copy of a, complete before the library's stream reads it."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    torch.cuda.synchronize()
+    return t
+
+
+def gpu_solve(ctx, y):
+    import torch
+    yd = dev(y)
+    xd = torch.empty_like(yd)
+    ctx.nd_solve(yd, xd)
+    ctx.synchronize()
+    return xd.cpu().numpy()
+
+
+def kappa_1(P):
+    """1-norm condition number estimate ||P||_1 ||P^-1||_1 (Hager/Higham estimator)."""
+    lu = scipy.sparse.linalg.splu(P.tocsc())
+    N = P.shape[0]
+    inv = scipy.sparse.linalg.LinearOperator(
+        (N, N), matvec=lu.solve, rmatvec=lambda x: lu.solve(x, trans="T"), dtype=np.float64)
+    return scipy.sparse.linalg.onenormest(P) * scipy.sparse.linalg.onenormest(inv)
+
+
+def check_solve(P, y, x):
+    ref = O.solve_p(P, y)
+    kap = kappa_1(P)
+    fwd = np.abs(x - ref).max() / np.abs(ref).max()
+    back = np.abs(P @ x - y).max() / (abs(P).max(axis=1).toarray().max() * 9 * np.abs(x).max()
+                                       + np.abs(y).max())
+    assert fwd <= 256 * U * kap, (fwd, kap)
+    assert back <= 1e-12, back
+    return fwd, back, kap
+
+
+@pytest.mark.parametrize("n,leaf,policy", [(16, 8, "local"), (32, 8, "paper"), (32, 4, "local"),
+                                           (64, 8, "local"), (64, 16, "paper"), (128, 8, "mean")])
+def test_nd_solve_matches_oracle(n, leaf, policy):
+    v = make_workload("helm2d_n32", n=n)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy=policy)
+    ctx.nd_factor(leaf=leaf)
+    info = ctx.nd_info()
+    assert info["factored"] == 1 and info["leaf"] == leaf
+    y = np.random.default_rng(n + leaf).standard_normal(n * n)
+    x = gpu_solve(ctx, y)
+    fwd, back, kap = check_solve(csr(ctx, "P", n * n), y, x)
+    print(f"n={n} b={leaf} {policy}: forward {fwd:.2e} (kappa_1 {kap:.2e}), backward {back:.2e}")
+
+
+@pytest.mark.parametrize("n,policy", [(32, "paper"), (64, "local")])
+def test_nd_solve_multi_t_rows(n, policy):
+    """Rows of 9 or 25 entries by the leaf-8 t_j rule (Sec. 4.2) stay inside the separators."""
+    v = make_workload("helm2d_n32", n=n)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy=policy, t=2, nd_leaf=8)
+    ctx.nd_factor()
+    assert ctx.nd_info()["leaf"] == 8
+    y = np.random.default_rng(7).standard_normal(n * n)
+    check_solve(csr(ctx, "P", n * n), y, gpu_solve(ctx, y))
+
+
+@pytest.mark.parametrize("t,leaf", [(1, 0), (2, 8)])
+def test_apply_rows_matches_sparse_products(t, leaf):
+    import torch
+    n = 32
+    v = make_workload("helm2d_n32", n=n)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="paper", t=t, nd_leaf=leaf)
+    u = np.random.default_rng(3).standard_normal(n * n)
+    ud = dev(u)
+    yd = torch.empty_like(ud)
+    for which in "QCP":
+        ctx.apply_rows(which, ud, yd)
+        ctx.synchronize()
+        M = csr(ctx, which, n * n)
+        ref = M @ u
+        scale = (abs(M) @ np.abs(u)).max()
+        assert np.abs(yd.cpu().numpy() - ref).max() <= 32 * U * scale, which
+
+
+def test_full_size_n1024_solve_backward_error_and_determinism():
+    """The 2D n = 1024 workload (1,048,576 points, local shifts): the whole residual P x - y
+    computed by the oracle's sparse product, and two solves and two factorisations agree bit for
+    bit."""
+    n = 1024
+    v = make_workload("helm2d_n1024")
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="local")
+    ctx.nd_factor()
+    y = np.random.default_rng(1).standard_normal(n * n)
+    x1 = gpu_solve(ctx, y)
+    P = csr(ctx, "P", n * n)
+    back = np.abs(P @ x1 - y).max() / (abs(P).max(axis=1).toarray().max() * 9 * np.abs(x1).max()
+                                       + np.abs(y).max())
+    print(f"n=1024 backward error {back:.2e}")
+    assert back <= 1e-12
+    x2 = gpu_solve(ctx, y)
+    assert np.array_equal(x1, x2)
+    ctx.nd_factor()
+    assert np.array_equal(gpu_solve(ctx, y), x1)
+    # sampled rows, one by one from the exported rows
+    rng = np.random.default_rng(2)
+    for j in rng.choice(n * n, size=200, replace=False):
+        lo, hi = P.indptr[j], P.indptr[j + 1]
+        row = float(np.dot(P.data[lo:hi], x1[P.indices[lo:hi]]))
+        assert abs(row - y[j]) <= 1e-10 * (np.abs(P.data[lo:hi]).sum() * np.abs(x1).max())
+
+
+def test_gmres_counts_match_golden():
+    with open(os.path.join(GOLDEN, "gmres_helm2d_n32.json")) as fh:
+        gold = json.load(fh)["iterations"]
+    v = make_workload("helm2d_n32")
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    for key, want in gold.items():
+        pol, sig = key.split("/")
+        f = gaussian_source(32, 2, float(sig))
+        ctx.build_stencils(policy=pol)
+        ctx.nd_factor()
+        u, res = ctx.gmres(f.reshape(-1))
+        assert res["converged"] == 1 and res["iterations"] == want, (key, res, want)
+        assert res["resid_true"] < 1e-4
+        u_ref, it, _, info = O.gmres_solve(v, f, csr(ctx, "P", 1024), csr(ctx, "C", 1024))
+        assert info == 0 and it == want
+        assert np.abs(u - u_ref.reshape(-1)).max() <= 1e-8 * np.abs(u_ref).max(), key
+
+
+def test_gmres_multi_t_counts_match_golden():
+    with open(os.path.join(GOLDEN, "gmres_multi_t_helm2d_n32.json")) as fh:
+        gold = json.load(fh)["iterations"]
+    v = make_workload("helm2d_n32")
+    f = gaussian_source(32, 2, 2.0)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    done = 0
+    for key, want in gold.items():
+        pol, label = key.split("/")
+        if label != "nd8":
+            continue  # t = 2 at every point crosses the separators (not factorable by ND)
+        ctx.build_stencils(policy=pol, t=2, nd_leaf=8)
+        ctx.nd_factor()
+        _, res = ctx.gmres(f.reshape(-1))
+        assert res["converged"] == 1 and res["iterations"] == want, (key, res, want)
+        done += 1
+    assert done >= 2
+
+
+@pytest.mark.parametrize("policy", ["local", "paper"])
+def test_gmres_n256_matches_oracle(policy):
+    import torch
+    n = 256
+    v = make_workload("helm2d_n256")
+    f = gaussian_source(n, 2, 2.0)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy=policy)
+    ctx.nd_factor()
+    fd = dev(f.reshape(-1))
+    ud, res = ctx.gmres(fd)
+    u = ud.cpu().numpy()
+    N = n * n
+    u_ref, it, res_ref, info = O.gmres_solve(v, f, csr(ctx, "P", N), csr(ctx, "C", N), maxiter=5)
+    print(f"n=256 {policy}: GPU {res}, oracle {it} iterations (true residual {res_ref:.2e})")
+    assert info == 0 and res["converged"] == 1
+    assert res["iterations"] == it
+    assert np.abs(u - u_ref.reshape(-1)).max() <= 1e-7 * np.abs(u_ref).max()
+    # the host-buffer call gives the same result
+    u_h, res_h = ctx.gmres(f.reshape(-1))
+    assert res_h["iterations"] == res["iterations"] and np.array_equal(u_h, u)
+    del torch
+
+
+def test_unpreconditioned_gmres_stalls():
+    v = make_workload("helm2d_n32")
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    _, res = ctx.gmres(gaussian_source(32, 2).reshape(-1), precond=False, max_cycles=3)
+    assert res["converged"] == 0 and res["iterations"] == 120
+    _, it, _, info = O.gmres_solve(v, gaussian_source(32, 2), maxiter=3)
+    assert info != 0 and it == 120
+
+
+def test_calls_out_of_order_and_unsupported_fail_cleanly():
+    import torch
+    from paper_1607_02560_gb300 import LspError
+    v = make_workload("helm2d_n32")
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    y = torch.zeros(1024, dtype=torch.float64, device="cuda")
+    with pytest.raises(LspError, match="STATE"):
+        ctx.nd_factor()
+    ctx.build_stencils(policy="paper")
+    with pytest.raises(LspError, match="STATE"):
+        ctx.nd_solve(y, y)
+    with pytest.raises(LspError, match="STATE"):
+        ctx.gmres(np.ones(1024))
+    for leaf in (3, 6, 64):
+        with pytest.raises(LspError, match="ARG"):
+            ctx.nd_factor(leaf=leaf)
+    ctx.nd_factor()
+    ctx.nd_solve(y, y)
+    ctx.build_stencils(policy="local")  # a new build invalidates the factor
+    with pytest.raises(LspError, match="STATE"):
+        ctx.nd_solve(y, y)
+    ctx.build_stencils(policy="paper", t=2)  # t = 2 at every point
+    with pytest.raises(LspError, match="UNSUPPORTED"):
+        ctx.nd_factor()
+    ctx.build_stencils(policy="paper", t=2, nd_leaf=8)
+    with pytest.raises(LspError, match="ARG"):
+        ctx.nd_factor(leaf=4)
+    ctx.nd_factor()
+    v3 = make_workload("schr3d_n64", n=16)
+    ctx3 = ctx_for(v3)
+    ctx3.set_potential(v3)
+    ctx3.build_stencils()
+    with pytest.raises(LspError, match="UNSUPPORTED"):
+        ctx3.nd_factor()

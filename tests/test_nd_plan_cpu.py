@@ -1,0 +1,75 @@
+"""Host logic of the nested dissection of P (Sec. 3, Fig. nd; Table cost), no GPU needed.
+
+The planner runs in liblsp.so (lsp_nd_plan_info) and refuses any row pattern whose entries it
+cannot assemble exactly once; these tests compare its tree with sizes derived by hand from the
+geometry, its flop counts with the formulas of the header, and its refusals.
+"""
+
+import pytest
+
+from paper_1607_02560_gb300 import build as B
+from paper_1607_02560_gb300 import lsp
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    B.build()
+    lsp.lib()
+
+
+def ring(h, w, n):
+    """Points around an h x w box of the n-periodic grid (no wrap-around when h, w < n - 1)."""
+    return 2 * (h + w) + 4
+
+
+def test_n16_leaf8_by_hand():
+    # cross: row 0 + column 0 = 31 points; root box 15 x 15 split by its middle column: 15 points,
+    # ring = the whole cross (31); halves 15 x 7 split by their middle row: 7 points, ring = 9 + 15
+    # + 15 (top and bottom rows coincide: row 16 = row 0); leaves 7 x 7 with a 32-point ring
+    info = lsp.nd_plan_info(16, 8)
+    assert info["depths"] == [(1, 31, 0), (1, 15, 31), (2, 7, 39), (4, 49, ring(7, 7, 16))]
+    assert info["fronts"] == 8 and info["levels"] == 4 and info["max_front"] == 81
+
+
+def test_n16_leaf4_goes_two_levels_deeper():
+    info = lsp.nd_plan_info(16, 4)
+    assert info["depths"] == [(1, 31, 0), (1, 15, 31), (2, 7, 39), (4, 7, ring(7, 7, 16)),
+                              (8, 3, ring(7, 3, 16)), (16, 9, ring(3, 3, 16))]
+
+
+@pytest.mark.parametrize("n,leaf,t", [(16, 8, 1), (64, 8, 1), (64, 4, 1), (32, 8, 2), (256, 8, 1)])
+def test_every_point_is_eliminated_once_and_flops_follow_the_formulas(n, leaf, t):
+    info = lsp.nd_plan_info(n, leaf, t, leaf if t == 2 else 0)
+    depths = info["depths"]
+    assert sum(c * s for c, s, _ in depths) == n * n
+    sweep = sum(c * 2.0 * s * (s + r) ** 2 for c, s, r in depths)
+    lu = sum(c * (2.0 / 3.0 * s ** 3 + 2.0 * s * s * r + 2.0 * s * r * r) for c, s, r in depths)
+    assert info["flops"] == pytest.approx(sweep, rel=1e-12)
+    assert info["flops_lu"] == pytest.approx(lu, rel=1e-12)
+    assert info["front_bytes"] == 8 * sum(c * (s + r) ** 2 for c, s, r in depths)
+    assert info["solve_bytes"] == 8 * sum(c * ((s + r) * s + s * r) for c, s, r in depths)
+    # front counts double with every depth below the root box
+    assert [c for c, _, _ in depths] == [1] + [2 ** k for k in range(len(depths) - 1)]
+    # the separators are the lines x_a = 0 (mod b): leaves hold (b - 1)^2 points
+    assert depths[-1][1] == (leaf - 1) ** 2
+
+
+def test_cost_grows_like_n_cubed():
+    """Table cost, 2D: T_NDsetup = O(N^{3/2} + b^4 N) = O(n^3) at fixed b."""
+    f256 = lsp.nd_plan_info(256)["flops_lu"]
+    f512 = lsp.nd_plan_info(512)["flops_lu"]
+    f1024 = lsp.nd_plan_info(1024)["flops_lu"]
+    assert 6.0 < f512 / f256 < 9.0 and 6.0 < f1024 / f512 < 9.0
+
+
+@pytest.mark.parametrize("args,msg", [
+    ((16, 8, 2, 0), "cross the separators"),      # t = 2 everywhere
+    ((16, 8, 2, 4), "must equal the nd_leaf"),    # t_j rule of another leaf width
+    ((12, 4, 1, 0), "power of two"),
+    ((16, 6, 1, 0), "leaf width"),
+    ((16, 32, 1, 0), "leaf width"),
+    ((2048, 8, 1, 0), "n <= 1024"),
+])
+def test_plans_that_do_not_fit_are_refused(args, msg):
+    with pytest.raises(lsp.LspError, match=msg):
+        lsp.nd_plan_info(*args)
