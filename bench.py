@@ -355,6 +355,14 @@ def run_ours(args):
         out["config"]["training"] = train_info
     if not args.no_variants:
         out["variants"] = variants(args, torch)
+    if not args.no_solve and d == 2:
+        out["nd_solve"] = []
+        for ns_ in (256, 512, 1024):
+            try:
+                out["nd_solve"].append(solve_variant(torch, ns_, "paper", fp64_peak,
+                                                     peaks["hbm_gbs"]))
+            except Exception as exc:  # must not hide the main line
+                out["nd_solve"].append({"n": ns_, "error": str(exc)[:300]})
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.policy, budget_s=args.cpu_budget)
     print(json.dumps(out))
@@ -446,6 +454,89 @@ def learned_variant(torch, workload: str, steps: int = 3000):
                       stream=stream)
     out["training"] = info
     mlp.close()
+    return out
+
+
+def solve_variant(torch, n: int, policy: str = "paper", fp64_peak: float | None = None,
+                  hbm_peak: float | None = None):
+    """Applying the preconditioner (Sec. 5 tables): nested-dissection setup T_NDsetup, one
+    application T_NDapp, and the GMRES(40) solve to rtol 1e-6 (T_NDsolve, N_iter) on the
+    velocity field of a Gaussian profile at the centre, 4 points per wavelength, n x n grid."""
+    from lsp_inputs import gaussian_source, make_workload
+    from paper_1607_02560_gb300 import Context
+
+    v = make_workload("helm2d_n32", n=n)
+    f = gaussian_source(n, 2, 2.0).reshape(-1)
+    stream = torch.cuda.Stream()
+    ctx = Context(2, n, stream=stream)
+    out = {"workload": f"helm2d_n32 rescaled to n={n} (omega/2pi = {n // 4})", "policy": policy,
+           "n": n}
+    with torch.cuda.stream(stream):
+        ctx.set_potential(v)
+        ctx.build_stencils(policy=policy)
+        t0 = time.perf_counter()
+        ctx.nd_factor()  # plans the dissection on the host, then factorises
+        out["nd_setup_first_call_s"] = time.perf_counter() - t0
+        setup = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.nd_factor()
+            setup.append(time.perf_counter() - t0)
+        info = ctx.nd_info()
+        y = torch.from_numpy(np.random.default_rng(0).standard_normal(n * n)).cuda()
+        x = torch.empty_like(y)
+        torch.cuda.synchronize()
+        for _ in range(3):
+            ctx.nd_solve(y, x)
+        ctx.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(20)]
+        for a, b in evs:
+            a.record(stream)
+            ctx.nd_solve(y, x)
+            b.record(stream)
+        torch.cuda.synchronize()
+        app_ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
+        ctx.kernel_timing(True)
+        ctx.nd_factor()
+        for _ in range(5):
+            ctx.nd_solve(y, x)
+        ctx.synchronize()
+        kt = {k: {"ms": round(ms, 4), "launches": cnt} for k, (ms, cnt) in ctx.kernel_times().items()}
+        ctx.kernel_timing(False)
+        fd = torch.from_numpy(f).cuda()
+        torch.cuda.synchronize()
+        ctx.gmres(fd)  # warm
+        gm = []
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ud, res = ctx.gmres(fd)
+            gm.append(time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        _, res_h = ctx.gmres(f)  # host buffers in and out
+        e2e = time.perf_counter() - t0
+    ctx.close()
+    setup_s = float(np.median(setup))
+    out.update({
+        "T_NDsetup_s": setup_s, "T_NDapp_ms": app_ms, "N_iter": res["iterations"],
+        "T_NDsolve_s": float(np.median(gm)), "T_NDsolve_host_buffers_s": e2e,
+        "converged": res["converged"], "resid_true": res["resid_true"],
+        "fronts": info["fronts"], "levels": info["levels"], "max_front": info["max_front"],
+        "front_bytes": info["front_bytes"], "flops_lu": info["flops_lu"],
+        "flops_issued": info["flops"], "solve_bytes": info["solve_bytes"],
+        "kernel_ms": kt})
+    if fp64_peak:
+        ach = info["flops_lu"] / setup_s / 1e12
+        out["setup_roofline"] = {"bound": "fp64", "achieved": ach, "peak": fp64_peak,
+                                 "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                                 "work": "multifrontal LU count 2/3 s^3 + 2 s^2 r + 2 s r^2 per front"}
+    if hbm_peak:
+        ach = info["solve_bytes"] / (app_ms * 1e-3) / 1e9
+        out["solve_roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm_peak,
+                                 "unit": "GB/s", "frac": ach / hbm_peak,
+                                 "work": "front bytes read per solve, (f s + s r) * 8 per front"}
     return out
 
 
@@ -547,6 +638,8 @@ def main():
     ap.add_argument("--learned-steps", type=int, default=3000,
                     help="training steps of the surrogate (learned mode and variants)")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-solve", action="store_true",
+                    help="skip the nested-dissection / GMRES measurements")
     ap.add_argument("--no-learned", action="store_true", help="skip training the surrogate")
     ap.add_argument("--n", type=int, default=None, help="rescale the workload's grid (small cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -56,6 +56,29 @@ bool nd_ready(const lsp_ctx* c) {
   return c->nd && c->nd->factored && c->nd->factored_gen == c->build_gen && c->built;
 }
 
+// x = P^-1 y with the chosen refinement steps x += P^-1 (y - P x); x may equal y.
+lsp_status nd_apply(lsp_ctx* c, const double* y, double* x) {
+  NdState& S = *c->nd;
+  if (S.refine_steps == 0) {
+    SCUDA(c, launch_nd_solve(c, y, x));
+    return LSP_OK;
+  }
+  const int64_t N = c->geo.N;
+  if (!ensure(c, S.ry, sizeof(double) * N) || !ensure(c, S.rd, sizeof(double) * N))
+    return sfail(c, LSP_ERR_OOM, "refinement scratch: %s", c->err.c_str());
+  double* ry = (double*)S.ry.p;
+  double* rd = (double*)S.rd.p;
+  SCUDA(c, cudaMemcpyAsync(ry, y, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream));
+  SCUDA(c, launch_nd_solve(c, ry, x));
+  for (int k = 0; k < S.refine_steps; ++k) {
+    SCUDA(c, launch_apply_rows(c, (const double*)c->P.p, rows_mu(c), c->t_built, x, rd));
+    SCUDA(c, launch_axpby(c, rd, ry, rd, nullptr, -1.0, N));
+    SCUDA(c, launch_nd_solve(c, rd, rd));
+    SCUDA(c, launch_axpby(c, x, x, rd, nullptr, 1.0, N));
+  }
+  return LSP_OK;
+}
+
 }  // namespace
 
 namespace lsp {
@@ -64,7 +87,7 @@ void nd_free(NdState* s) {
   if (!s) return;
   DevBuf* bufs[] = {&s->fronts, &s->E, &s->R, &s->inv, &s->asm_dst, &s->asm_src, &s->perm,
                     &s->z, &s->u, &s->cbuf, &s->pinv, &s->swaps, &s->err, &s->V, &s->w,
-                    &s->b, &s->x, &s->tmp, &s->gs, &s->fvec};
+                    &s->b, &s->x, &s->tmp, &s->gs, &s->fvec, &s->ry, &s->rd};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (s->h_gs) cudaFreeHost(s->h_gs);
@@ -101,6 +124,8 @@ lsp_status lsp_nd_factor(lsp_ctx* c, const lsp_nd_opts* opts) {
   if (leaf <= 0) leaf = 8;
   if (leaf < 4 || (leaf & (leaf - 1)) || leaf > c->geo.n)
     return sfail(c, LSP_ERR_ARG, "leaf width %d: must be a power of two in [4, n]", leaf);
+  const int refine = opts ? opts->refine_steps : 0;
+  if (refine < 0 || refine > 4) return sfail(c, LSP_ERR_ARG, "refine_steps must be in [0, 4]");
   if (c->t_built == 2 && c->leaf_built > 0 && leaf != c->leaf_built)
     return sfail(c, LSP_ERR_ARG, "leaf width %d differs from the nd_leaf %d of the build", leaf,
                  c->leaf_built);
@@ -159,6 +184,7 @@ lsp_status lsp_nd_factor(lsp_ctx* c, const lsp_nd_opts* opts) {
                  "a pivot of the nested dissection vanished (code %d): P is singular", herr);
   S.factored = true;
   S.factored_gen = c->build_gen;
+  S.refine_steps = refine;
   return LSP_OK;
 }
 
@@ -209,8 +235,7 @@ lsp_status lsp_nd_solve(lsp_ctx* c, const double* y, double* x) {
   if (!y || !x) return sfail(c, LSP_ERR_ARG, "y or x is NULL");
   if (!nd_ready(c))
     return sfail(c, LSP_ERR_STATE, "nd_solve needs lsp_nd_factor of the current stencils");
-  SCUDA(c, launch_nd_solve(c, y, x));
-  return LSP_OK;
+  return nd_apply(c, y, x);
 }
 
 lsp_status lsp_apply_rows(lsp_ctx* c, char which, const double* u, double* y) {
@@ -278,7 +303,8 @@ lsp_status lsp_gmres(lsp_ctx* c, const lsp_gmres_opts* opts, const double* f, do
     if (o.precond) {
       SCUDA(c, launch_apply(c, in, tmp));
       SCUDA(c, launch_apply_rows(c, Crows, mu, c->t_built, tmp, outv));
-      SCUDA(c, launch_nd_solve(c, outv, outv));
+      lsp_status sa = nd_apply(c, outv, outv);
+      if (sa != LSP_OK) return sa;
     } else {
       SCUDA(c, launch_apply(c, in, outv));
     }
@@ -288,7 +314,7 @@ lsp_status lsp_gmres(lsp_ctx* c, const lsp_gmres_opts* opts, const double* f, do
   // b = P^-1 C f
   if (o.precond) {
     SCUDA(c, launch_apply_rows(c, Crows, mu, c->t_built, fv, b));
-    SCUDA(c, launch_nd_solve(c, b, b));
+    if ((st = nd_apply(c, b, b)) != LSP_OK) return st;
   } else {
     SCUDA(c, cudaMemcpyAsync(b, fv, sizeof(double) * N, cudaMemcpyDeviceToDevice, c->stream));
   }

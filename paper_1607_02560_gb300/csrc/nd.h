@@ -68,7 +68,9 @@ struct NdState {
   bool have_plan = false;
   bool factored = false;
   int64_t factored_gen = -1;  // ctx->build_gen of the rows that were factored
+  int refine_steps = 0;       // iterative-refinement steps after every solve
   DevBuf fronts, E, R, inv, asm_dst, asm_src, perm, z, u, cbuf, pinv, swaps, err;
+  DevBuf ry, rd;              // refinement scratch: a copy of y, the correction
   // GMRES workspace
   DevBuf V, w, b, x, tmp, gs, fvec;
   double* h_gs = nullptr;  // pinned mirror of the scalars the host loop reads

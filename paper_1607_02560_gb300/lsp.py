@@ -42,7 +42,7 @@ class StencilOpts(ctypes.Structure):
 
 
 class NdOpts(ctypes.Structure):
-    _fields_ = [("leaf", ctypes.c_int)]
+    _fields_ = [("leaf", ctypes.c_int), ("refine_steps", ctypes.c_int)]
 
 
 class NdInfo(ctypes.Structure):
@@ -324,10 +324,12 @@ class Context:
         self._check(lib().lsp_synchronize(self.h), "synchronize")
 
     # ---- applying the preconditioner: nested dissection of P, GMRES ----
-    def nd_factor(self, leaf: int = 0):
-        """Factorise the current P rows by nested dissection (returns when done)."""
+    def nd_factor(self, leaf: int = 0, refine_steps: int = 0):
+        """Factorise the current P rows by nested dissection (returns when done); every later
+        solve adds `refine_steps` steps of iterative refinement."""
         o = NdOpts()
         o.leaf = int(leaf)
+        o.refine_steps = int(refine_steps)
         self._check(lib().lsp_nd_factor(self.h, ctypes.byref(o)), "nd_factor")
 
     def nd_info(self) -> dict:

@@ -128,10 +128,19 @@ def test_apply_rows_matches_sparse_products(t, leaf):
         assert np.abs(yd.cpu().numpy() - ref).max() <= 32 * U * scale, which
 
 
+def backward_error(P, x, y):
+    return np.abs(P @ x - y).max() / (abs(P).max(axis=1).toarray().max() * 9 * np.abs(x).max()
+                                      + np.abs(y).max())
+
+
 def test_full_size_n1024_solve_backward_error_and_determinism():
-    """The 2D n = 1024 workload (1,048,576 points, local shifts): the whole residual P x - y
-    computed by the oracle's sparse product, and two solves and two factorisations agree bit for
-    bit."""
+    """The 2D n = 1024 workload (1,048,576 points, local shifts, 4 points per wavelength): the
+    whole residual P x - y computed by the oracle's sparse product, and two solves and two
+    factorisations agree bit for bit.
+
+    Pivots are chosen inside each front's E; the long separator lines of this high-frequency
+    problem give ill-conditioned E blocks, so a plain solve has a backward error near 1e-9
+    (measured) while one refinement step brings it to the rounding level."""
     n = 1024
     v = make_workload("helm2d_n1024")
     ctx = ctx_for(v)
@@ -141,20 +150,35 @@ def test_full_size_n1024_solve_backward_error_and_determinism():
     y = np.random.default_rng(1).standard_normal(n * n)
     x1 = gpu_solve(ctx, y)
     P = csr(ctx, "P", n * n)
-    back = np.abs(P @ x1 - y).max() / (abs(P).max(axis=1).toarray().max() * 9 * np.abs(x1).max()
-                                       + np.abs(y).max())
-    print(f"n=1024 backward error {back:.2e}")
-    assert back <= 1e-12
-    x2 = gpu_solve(ctx, y)
-    assert np.array_equal(x1, x2)
-    ctx.nd_factor()
+    b0 = backward_error(P, x1, y)
+    assert b0 <= 1e-7
     assert np.array_equal(gpu_solve(ctx, y), x1)
+    ctx.nd_factor(refine_steps=1)
+    x2 = gpu_solve(ctx, y)
+    b1 = backward_error(P, x2, y)
+    print(f"n=1024 backward error {b0:.2e}, refined {b1:.2e}")
+    assert b1 <= 1e-15
+    ctx.nd_factor(refine_steps=1)
+    assert np.array_equal(gpu_solve(ctx, y), x2)
     # sampled rows, one by one from the exported rows
     rng = np.random.default_rng(2)
     for j in rng.choice(n * n, size=200, replace=False):
         lo, hi = P.indptr[j], P.indptr[j + 1]
-        row = float(np.dot(P.data[lo:hi], x1[P.indices[lo:hi]]))
-        assert abs(row - y[j]) <= 1e-10 * (np.abs(P.data[lo:hi]).sum() * np.abs(x1).max())
+        row = float(np.dot(P.data[lo:hi], x2[P.indices[lo:hi]]))
+        assert abs(row - y[j]) <= 1e-13 * (np.abs(P.data[lo:hi]).sum() * np.abs(x2).max())
+
+
+def test_n512_refined_solve_matches_oracle():
+    """2D n = 512 at 4 points per wavelength against the oracle's sparse-LU solve."""
+    n = 512
+    v = make_workload("helm2d_n1024", n=n)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="local")
+    ctx.nd_factor(refine_steps=1)
+    y = np.random.default_rng(4).standard_normal(n * n)
+    fwd, back, kap = check_solve(csr(ctx, "P", n * n), y, gpu_solve(ctx, y))
+    print(f"n=512 refined: forward {fwd:.2e} (kappa_1 {kap:.2e}), backward {back:.2e}")
 
 
 def test_gmres_counts_match_golden():
@@ -218,6 +242,11 @@ def test_gmres_n256_matches_oracle(policy):
     # the host-buffer call gives the same result
     u_h, res_h = ctx.gmres(f.reshape(-1))
     assert res_h["iterations"] == res["iterations"] and np.array_equal(u_h, u)
+    # a refined preconditioner changes P^-1 by rounding-level amounts only
+    ctx.nd_factor(refine_steps=1)
+    u_r, res_r = ctx.gmres(f.reshape(-1))
+    assert res_r["iterations"] == it
+    assert np.abs(u_r - u_ref.reshape(-1)).max() <= 1e-7 * np.abs(u_ref).max()
     del torch
 
 
@@ -248,6 +277,8 @@ def test_calls_out_of_order_and_unsupported_fail_cleanly():
     for leaf in (3, 6, 64):
         with pytest.raises(LspError, match="ARG"):
             ctx.nd_factor(leaf=leaf)
+    with pytest.raises(LspError, match="ARG"):
+        ctx.nd_factor(refine_steps=5)
     ctx.nd_factor()
     ctx.nd_solve(y, y)
     ctx.build_stencils(policy="local")  # a new build invalidates the factor
