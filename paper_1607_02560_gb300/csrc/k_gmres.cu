@@ -77,8 +77,11 @@ __global__ void k_axpby(double* __restrict__ y, const double* a, const double* x
 // v0 = r / beta with beta = sqrt(gs[kGsNorm]); S = (beta, 0, ...).
 __global__ void k_gmres_start(double* __restrict__ gs, int ld, int restart,
                               const double* __restrict__ r, double* __restrict__ v0, int64_t N) {
+  __shared__ double sinv;
   const double beta = sqrt(gs[kGsNorm]);
-  const double inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  if (threadIdx.x == 0) sinv = beta > 0.0 ? 1.0 / beta : 0.0;  // one division per block
+  __syncthreads();
+  const double inv = sinv;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x)
     v0[i] = r[i] * inv;

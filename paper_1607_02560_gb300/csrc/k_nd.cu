@@ -8,6 +8,7 @@
 //  - the solve: one matrix-vector product per front going up the tree, one coming down.
 // Every reduction runs in a fixed order, so a factorisation and a solve are deterministic.
 #include <math.h>
+#include <stdio.h>
 
 #include "nd.h"
 
@@ -72,6 +73,7 @@ __global__ void __launch_bounds__(256) k_nd_sweep_small(double* __restrict__ fro
   double* rowk = colk + f;
   __shared__ int sperm[kNdSmallFront];
   __shared__ int piv, bad;
+  __shared__ double spiv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
   double* G = fronts + (int64_t)blockIdx.x * f * f;
   for (int e = tid; e < f * f; e += nt) F[e] = G[e];
@@ -96,6 +98,7 @@ __global__ void __launch_bounds__(256) k_nd_sweep_small(double* __restrict__ fro
           atomicOr(err, 1);
         }
         piv = bi < s ? bi : k;
+        spiv = 1.0 / F[piv * f + k];  // the one FP64 division of this pivot
       }
     }
     __syncthreads();
@@ -114,7 +117,7 @@ __global__ void __launch_bounds__(256) k_nd_sweep_small(double* __restrict__ fro
       }
       __syncthreads();
     }
-    const double dinv = 1.0 / F[k * f + k];
+    const double dinv = spiv;
     for (int j = tid; j < f; j += nt) {
       rowk[j] = F[k * f + j] * dinv;
       colk[j] = F[j * f + k];
@@ -143,64 +146,81 @@ constexpr int kSwapInts = 1 + 4 * NP;
 // Part 1, one CTA per front: choose nb pivot rows among positions k..s-1 by partial pivoting
 // on the panel F[k.., K]; record the row exchanges, update perm, write the permuted column
 // block cbuf[x][c] = F[src(x)][k + c] for every row x, and the inverse of the pivot block.
+// The pivot rows come from a trial elimination of the panel in FP32 (one reciprocal per
+// pivot): it only ranks candidate rows by magnitude, while every value the factorisation keeps
+// is computed in FP64 from the original entries (pivot block inverse here, row block and
+// update in parts 2 and 3). An FP64 trial elimination would cost one SM about m nb^2 / 2 FP64
+// FMAs per step on the critical path of the root fronts.
 __global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fronts, int f, int s,
                                                   int k, int nb, int32_t* __restrict__ perm,
                                                   double* __restrict__ cbuf,
                                                   double* __restrict__ pinv,
                                                   int32_t* __restrict__ swaps,
                                                   int32_t* __restrict__ err) {
-  extern __shared__ double sm[];
+  extern __shared__ float smf[];
+  constexpr int PS = NP + 1;                          // odd row stride: no bank conflicts
   const int m = s - k;
-  double* pan = sm;                                   // m x NP
-  uint8_t* used = (uint8_t*)(pan + (size_t)m * NP);   // m
+  float* pan = smf;                                   // m x PS
+  uint8_t* used = (uint8_t*)(pan + (size_t)m * PS);   // m
   __shared__ int sel[NP];
-  __shared__ double wbest[8];
+  __shared__ float wbest[8];
   __shared__ int wbi[8];
   __shared__ int bad, nq;
   __shared__ int dstp[2 * NP], srcp[2 * NP];
   __shared__ double aug[NP][2 * NP];
   __shared__ int gpiv;
+  __shared__ float gpinv;
+  __shared__ double gdinv;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
   const int64_t fid = blockIdx.x;
   const double* F = fronts + fid * f * f;
   for (int i = tid; i < m; i += nt) {
-    for (int c = 0; c < NP; ++c) pan[i * NP + c] = c < nb ? F[(int64_t)(k + i) * f + k + c] : 0.0;
+    const double* Fi = F + (int64_t)(k + i) * f + k;
+    for (int c = 0; c < NP; ++c) pan[i * PS + c] = c < nb ? (float)Fi[c] : 0.0f;
     used[i] = 0;
   }
   if (tid == 0) bad = 0;
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    double best = -1.0;
+    float best = -1.0f;
     int bi = m;
     for (int i = tid; i < m; i += nt) {
       if (used[i]) continue;
-      const double a = fabs(pan[i * NP + j]);
+      const float a = fabsf(pan[i * PS + j]);
       if (a > best) {
         best = a;
         bi = i;
       }
     }
-    warp_argmax(best, bi);
+    for (int off = 16; off > 0; off >>= 1) {
+      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        bi = oi;
+      }
+    }
     if (lane == 0) {
       wbest[warp] = best;
       wbi[warp] = bi;
     }
     __syncthreads();
     if (tid == 0) {
-      double b = wbest[0];
+      float b = wbest[0];
       int ix = wbi[0];
       for (int w = 1; w < nt / 32; ++w)
         if (wbest[w] > b || (wbest[w] == b && wbi[w] < ix)) {
           b = wbest[w];
           ix = wbi[w];
         }
-      if (!(b > 0.0) || !isfinite(b) || ix >= m) {
+      if (!(b > 0.0f) || !isfinite(b) || ix >= m) {
         bad = 1;
         atomicOr(err, 2);
         ix = 0;
       }
       sel[j] = ix;
       used[ix] = 1;
+      gpinv = 1.0f / pan[ix * PS + j];
     }
     __syncthreads();
     if (bad) {  // leave a step that the next kernels read safely (no exchanges)
@@ -208,50 +228,56 @@ __global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fro
       return;
     }
     const int pr = sel[j];
-    const double pv = pan[pr * NP + j];
+    const float ipv = gpinv;
     for (int i = tid; i < m; i += nt) {
       if (used[i]) continue;
-      const double l = pan[i * NP + j] / pv;
-      for (int c = j + 1; c < nb; ++c) pan[i * NP + c] = fma(-l, pan[pr * NP + c], pan[i * NP + c]);
+      const float l = pan[i * PS + j] * ipv;
+      for (int c = j + 1; c < nb; ++c) pan[i * PS + c] = fmaf(-l, pan[pr * PS + c], pan[i * PS + c]);
     }
     __syncthreads();
   }
-  // row exchanges, applied in order: position k + j takes the row chosen j-th
-  if (tid == 0) {
-    int q = 0;
-    for (int j = 0; j < nb; ++j) {
-      const int want = k + sel[j], target = k + j;
-      int qw = -1, qt = -1;
-      for (int a = 0; a < q; ++a) {
-        if (srcp[a] == want) qw = a;
-        if (dstp[a] == target) qt = a;
-      }
-      if (qw < 0) {  // still at its own position
-        for (int a = 0; a < q; ++a)
-          if (dstp[a] == want) qw = a;
-        if (qw < 0) {
-          dstp[q] = want;
-          srcp[q] = want;
-          qw = q++;
-        }
-      }
-      if (qt < 0) {
-        dstp[q] = target;
-        srcp[q] = target;
-        qt = q++;
-      }
-      const int t = srcp[qt];
-      srcp[qt] = srcp[qw];
-      srcp[qw] = t;
+  // row exchanges (warp 0): position k + j takes the row chosen j-th; the rows of K that were
+  // not chosen move, in increasing position order, to the positions the chosen rows left
+  // outside K (taken in choice order)
+  if (warp == 0) {
+    const bool act = lane < nb;
+    const int ps = act ? k + sel[lane] : 0;
+    const bool inK = act && ps < k + nb;
+    const unsigned selK = __reduce_or_sync(0xffffffffu, inK ? 1u << (ps - k) : 0u);
+    const unsigned full = nb >= 32 ? 0xffffffffu : (1u << nb) - 1u;
+    const unsigned displaced = ~selK & full;  // K positions whose rows were not chosen
+    const unsigned outb = __ballot_sync(0xffffffffu, act && !inK);
+    const int rank = __popc(outb & ((1u << lane) - 1u));  // among the chosen rows outside K
+    int dpos = -1;
+    if (act && !inK) {  // the rank-th displaced position of K
+      unsigned mk = displaced;
+      for (int t = 0; t < rank; ++t) mk &= mk - 1u;
+      dpos = k + __ffs(mk) - 1;
     }
-    nq = q;
-    int32_t* sw = swaps + fid * kSwapInts;
-    sw[0] = q;
+    const int nout = __popc(outb);
     int32_t* pf = perm + fid * s;
-    int old[2 * NP];
-    for (int a = 0; a < q; ++a) old[a] = pf[srcp[a]];
-    for (int a = 0; a < q; ++a) {
-      pf[dstp[a]] = old[a];
+    int32_t* sw = swaps + fid * kSwapInts;
+    // entries: lanes 0..nb-1 give (k + j <- ps_j); chosen rows outside K also give (ps_j <- dpos)
+    const int old_sel = act ? pf[ps] : 0;
+    const int old_dis = dpos >= 0 ? pf[dpos] : 0;
+    __syncwarp();
+    if (act) {
+      dstp[lane] = k + lane;
+      srcp[lane] = ps;
+      pf[k + lane] = old_sel;
+    }
+    if (dpos >= 0) {
+      dstp[nb + rank] = ps;
+      srcp[nb + rank] = dpos;
+      pf[ps] = old_dis;
+    }
+    __syncwarp();
+    const int qq = nb + nout;
+    if (lane == 0) {
+      nq = qq;
+      sw[0] = qq;
+    }
+    for (int a = lane; a < qq; a += 32) {
       sw[1 + a] = dstp[a];
       sw[1 + 2 * NP + a] = srcp[a];
     }
@@ -264,11 +290,13 @@ __global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fro
     int src = x;
     for (int a = 0; a < q; ++a)
       if (dstp[a] == x) src = srcp[a];
-    for (int c = 0; c < NP; ++c) cb[(int64_t)x * NP + c] = c < nb ? F[(int64_t)src * f + k + c] : 0.0;
+    const double* Fs = F + (int64_t)src * f + k;
+    double* cx = cb + (int64_t)x * NP;
+    for (int c = 0; c < NP; ++c) cx[c] = c < nb ? Fs[c] : 0.0;
   }
-  // inverse of the pivot block by Gauss-Jordan with partial pivoting: [A | I] -> [I | A^-1]
-  if (tid < NP * 2 * NP) {
-    const int r = tid / (2 * NP), c = tid % (2 * NP);
+  // inverse of the pivot block (FP64) by Gauss-Jordan with partial pivoting: [A | I] -> [I | A^-1]
+  for (int e = tid; e < NP * 2 * NP; e += nt) {
+    const int r = e / (2 * NP), c = e % (2 * NP);
     double v = 0.0;
     if (r < nb) {
       if (c < NP) {
@@ -284,16 +312,19 @@ __global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fro
   }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
-    if (tid == 0) {
+    if (warp == 0) {
+      double b = -1.0;
       int p = j;
-      double b = fabs(aug[j][j]);
-      for (int r = j + 1; r < nb; ++r)
-        if (fabs(aug[r][j]) > b) {
-          b = fabs(aug[r][j]);
-          p = r;
-        }
-      gpiv = p;
-      if (!(b > 0.0)) atomicOr(err, 4);
+      if (lane >= j && lane < nb) {
+        b = fabs(aug[lane][j]);
+        p = lane;
+      }
+      warp_argmax(b, p);
+      if (lane == 0) {
+        gpiv = p;
+        if (!(b > 0.0)) atomicOr(err, 4);
+        gdinv = 1.0 / aug[p][j];  // the one FP64 division of this pivot
+      }
     }
     __syncthreads();
     const int p = gpiv;
@@ -303,26 +334,36 @@ __global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fro
       aug[p][tid] = t;
     }
     __syncthreads();
-    const double d = 1.0 / aug[j][j];
-    double lr = 0.0, pjc = 0.0;
-    const int r = tid / (2 * NP), c = tid % (2 * NP);
-    if (tid < NP * 2 * NP) {
-      lr = aug[r][j];
-      pjc = aug[j][c] * d;
+    const double d = gdinv;
+    double lr[2], pjc[2];
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + h * nt;
+      lr[h] = pjc[h] = 0.0;
+      if (e < NP * 2 * NP) {
+        lr[h] = aug[e / (2 * NP)][j];
+        pjc[h] = aug[j][e % (2 * NP)] * d;
+      }
     }
     __syncthreads();
-    if (tid < NP * 2 * NP && r < nb) aug[r][c] = r == j ? pjc : fma(-lr, pjc, aug[r][c]);
+    for (int h = 0; h < 2; ++h) {
+      const int e = tid + h * nt;
+      if (e < NP * 2 * NP) {
+        const int r = e / (2 * NP), c = e % (2 * NP);
+        if (r < nb) aug[r][c] = r == j ? pjc[h] : fma(-lr[h], pjc[h], aug[r][c]);
+      }
+    }
     __syncthreads();
   }
-  if (tid < NP * NP) {
-    const int r = tid / NP, c = tid % NP;
-    pinv[fid * NP * NP + tid] = (r < nb && c < nb) ? aug[r][NP + c] : 0.0;
+  for (int e = tid; e < NP * NP; e += nt) {
+    const int r = e / NP, c = e % NP;
+    pinv[fid * NP * NP + e] = (r < nb && c < nb) ? aug[r][NP + c] : 0.0;
   }
 }
 
 // Part 2: rows K become A_KK^-1 F[K, j] for the columns j outside K (after applying the row
 // exchanges to those columns), and the column block becomes [A_KK^-1 on K; -cbuf A_KK^-1 off K].
-__global__ void __launch_bounds__(256) k_nd_rowblock(double* __restrict__ fronts, int f, int k,
+constexpr int kRowThreads = 64;  // one column (or row) per thread; small CTAs spread the step
+__global__ void __launch_bounds__(kRowThreads) k_nd_rowblock(double* __restrict__ fronts, int f, int k,
                                                      int nb, int tiles_w,
                                                      const double* __restrict__ cbuf,
                                                      const double* __restrict__ pinv,
@@ -334,7 +375,7 @@ __global__ void __launch_bounds__(256) k_nd_rowblock(double* __restrict__ fronts
   const int64_t fid = blockIdx.y;
   double* F = fronts + fid * f * f;
   const int32_t* sw = swaps + fid * kSwapInts;
-  if (tid < NP * NP) pi[tid / NP][tid % NP] = pinv[fid * NP * NP + tid];
+  for (int e = tid; e < NP * NP; e += blockDim.x) pi[e / NP][e % NP] = pinv[fid * NP * NP + e];
   if (tid == 0) {
     int q0 = sw[0];
     q0 = q0 < 0 || q0 > 2 * NP ? 0 : q0;
@@ -452,7 +493,8 @@ __global__ void __launch_bounds__(256) k_nd_fwd(const double* __restrict__ F, in
                                                 const int32_t* __restrict__ inv, int nchild,
                                                 const double* __restrict__ uc, int rc,
                                                 const double* __restrict__ y,
-                                                double* __restrict__ z, double* __restrict__ u) {
+                                                double* __restrict__ z, double* __restrict__ u,
+                                                int rows) {
   extern __shared__ double wE[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p = blockIdx.y;
@@ -468,8 +510,8 @@ __global__ void __launch_bounds__(256) k_nd_fwd(const double* __restrict__ F, in
   };
   for (int m = tid; m < s; m += blockDim.x) wE[m] = wsum(perm[p * s + m]);
   __syncthreads();
-  const int row0 = blockIdx.x * 64;
-  for (int rr = warp; rr < 64; rr += blockDim.x / 32) {
+  const int row0 = blockIdx.x * rows;
+  for (int rr = warp; rr < rows; rr += blockDim.x / 32) {
     const int i = row0 + rr;
     if (i >= f) break;
     const double* Fi = Fp + (int64_t)i * f;
@@ -490,15 +532,15 @@ __global__ void __launch_bounds__(256) k_nd_bwd(const double* __restrict__ F, in
                                                 const int32_t* __restrict__ E,
                                                 const int32_t* __restrict__ R,
                                                 const double* __restrict__ z,
-                                                double* __restrict__ x) {
+                                                double* __restrict__ x, int rows) {
   extern __shared__ double xR[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p = blockIdx.y;
   const double* Fp = F + p * f * f;
   for (int m = tid; m < r; m += blockDim.x) xR[m] = x[R[p * r + m]];
   __syncthreads();
-  const int row0 = blockIdx.x * 64;
-  for (int rr = warp; rr < 64; rr += blockDim.x / 32) {
+  const int row0 = blockIdx.x * rows;
+  for (int rr = warp; rr < rows; rr += blockDim.x / 32) {
     const int i = row0 + rr;
     if (i >= s) break;
     const double* Fi = Fp + (int64_t)i * f + s;
@@ -506,6 +548,106 @@ __global__ void __launch_bounds__(256) k_nd_bwd(const double* __restrict__ F, in
     for (int m = lane; m < r; m += 32) acc = fma(Fi[m], xR[m], acc);
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if (lane == 0) x[E[p * s + i]] = z[p * s + i] - acc;
+  }
+}
+
+// Copies rows 0..nr-1, columns c0..c0+nc-1 of the f x f front Fp into dst (row stride ld),
+// eight independent loads in flight per thread.
+__device__ __forceinline__ void stage_block(const double* __restrict__ Fp, int f, int c0, int nr,
+                                            int nc, double* __restrict__ dst, int ld) {
+  const int total = nr * nc, nt = blockDim.x;
+  for (int e0 = threadIdx.x; e0 < total; e0 += 8 * nt) {
+    double v[8];
+    int at[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * nt;
+      at[q] = -1;
+      if (e < total) {
+        const int i = e / nc, m = e - i * nc;
+        v[q] = Fp[(int64_t)i * f + c0 + m];
+        at[q] = i * ld + m;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (at[q] >= 0) dst[at[q]] = v[q];
+  }
+}
+
+// Small fronts (f <= kNdSmallFront), one CTA per front: the block the product reads is staged
+// in shared memory with an odd row stride (conflict-free column access), then one thread per
+// row. Same sums in the same order as the warp-per-row kernels would not give; each kernel is
+// deterministic on its own.
+__global__ void __launch_bounds__(128) k_nd_fwd_small(const double* __restrict__ F, int f, int s,
+                                                      int r, const int32_t* __restrict__ E,
+                                                      const int32_t* __restrict__ perm,
+                                                      const int32_t* __restrict__ inv,
+                                                      int nchild, const double* __restrict__ uc,
+                                                      int rc, const double* __restrict__ y,
+                                                      double* __restrict__ z,
+                                                      double* __restrict__ u) {
+  extern __shared__ double sh[];
+  const int ld = s | 1;
+  double* wE = sh;           // s
+  double* Ms = sh + ld;      // f rows of stride ld: F[i][0..s)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t p = blockIdx.x;
+  const double* Fp = F + p * f * f;
+  const int32_t* iv = nchild ? inv + p * f * 2 : nullptr;
+  auto wsum = [&](int i) -> double {
+    double v = i < s ? y[E[p * s + i]] : 0.0;
+    for (int c = 0; c < nchild; ++c) {
+      const int a = iv[i * 2 + c];
+      if (a >= 0) v += uc[(nchild == 1 ? p : 2 * p + c) * rc + a];
+    }
+    return v;
+  };
+  for (int m = tid; m < s; m += blockDim.x) wE[m] = wsum(perm[p * s + m]);
+  stage_block(Fp, f, 0, f, s, Ms, ld);
+  __syncthreads();
+  for (int i = tid; i < f; i += blockDim.x) {
+    const double* Mi = Ms + i * ld;
+    double a0 = 0.0, a1 = 0.0;
+    int m = 0;
+    for (; m + 1 < s; m += 2) {
+      a0 = fma(Mi[m], wE[m], a0);
+      a1 = fma(Mi[m + 1], wE[m + 1], a1);
+    }
+    if (m < s) a0 = fma(Mi[m], wE[m], a0);
+    const double acc = a0 + a1;
+    if (i < s)
+      z[p * s + i] = acc;
+    else
+      u[p * r + (i - s)] = wsum(i) + acc;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_nd_bwd_small(const double* __restrict__ F, int f, int s,
+                                                      int r, const int32_t* __restrict__ E,
+                                                      const int32_t* __restrict__ R,
+                                                      const double* __restrict__ z,
+                                                      double* __restrict__ x) {
+  extern __shared__ double sh[];
+  const int ld = r | 1;
+  double* xR = sh;          // r
+  double* Mb = sh + ld;     // s rows of stride ld: F[i][s..f)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t p = blockIdx.x;
+  const double* Fp = F + p * f * f;
+  for (int m = tid; m < r; m += blockDim.x) xR[m] = x[R[p * r + m]];
+  stage_block(Fp, f, s, s, r, Mb, ld);
+  __syncthreads();
+  for (int i = tid; i < s; i += blockDim.x) {
+    const double* Mi = Mb + i * ld;
+    double a0 = 0.0, a1 = 0.0;
+    int m = 0;
+    for (; m + 1 < r; m += 2) {
+      a0 = fma(Mi[m], xR[m], a0);
+      a1 = fma(Mi[m + 1], xR[m + 1], a1);
+    }
+    if (m < r) a0 = fma(Mi[m], xR[m], a0);
+    x[E[p * s + i]] = z[p * s + i] - (a0 + a1);
   }
 }
 
@@ -546,6 +688,16 @@ __global__ void k_nd_iota(int32_t* __restrict__ perm, int count, int s) {
     perm[e] = (int32_t)(e % s);
 }
 
+// "<stem>@<depth>": per-depth timer names (stable storage for the timer table)
+const char* level_name(const char* stem, int depth) {
+  static char names[7][32][24];
+  const int k = stem[3] == 'f' ? 0 : stem[3] == 'b' ? 1 : stem[3] == 's' ? 2 : stem[3] == 'a' ? 3
+              : stem[3] == 'p' ? 4 : stem[3] == 'r' ? 5 : 6;
+  if (depth < 0 || depth >= 32) return stem;
+  snprintf(names[k][depth], sizeof names[k][depth], "%s@%d", stem, depth);
+  return names[k][depth];
+}
+
 int grid_for(int64_t n, int threads) {
   const int64_t b = (n + threads - 1) / threads;
   return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
@@ -558,7 +710,7 @@ cudaError_t launch_nd_assemble(lsp_ctx* c, int depth, const double* rows) {
   const NdLevel& lv = S.plan.lv[depth];
   double* F = (double*)S.fronts.p + lv.front_off;
   const int64_t total = (int64_t)lv.count * lv.f * lv.f;
-  int t = timer_begin(c, "nd_assemble");
+  int t = timer_begin(c, level_name("nd_asm", depth));
   if (lv.nchild == 0) {
     cudaError_t e = cudaMemsetAsync(F, 0, sizeof(double) * total, c->stream);
     if (e != cudaSuccess) return e;
@@ -583,7 +735,7 @@ cudaError_t launch_nd_sweep(lsp_ctx* c, int depth) {
   int32_t* perm = (int32_t*)S.perm.p + lv.perm_off;
   int32_t* err = (int32_t*)S.err.p;
   if (lv.s == 0) return cudaSuccess;
-  int t = timer_begin(c, "nd_sweep");
+  int t = timer_begin(c, level_name("nd_sweep", depth));
   if (lv.f <= kNdSmallFront) {
     const size_t smem = sizeof(double) * ((size_t)lv.f * lv.f + 2 * lv.f);
     cudaError_t e = cudaFuncSetAttribute(k_nd_sweep_small,
@@ -595,23 +747,29 @@ cudaError_t launch_nd_sweep(lsp_ctx* c, int depth) {
   }
   // blocked steps; perm starts as the identity
   k_nd_iota<<<grid_for((int64_t)lv.count * lv.s, 256), 256, 0, c->stream>>>(perm, lv.count, lv.s);
-  const size_t psmem = sizeof(double) * (size_t)lv.s * NP + (size_t)lv.s + 16;
+  const size_t psmem = sizeof(float) * (size_t)lv.s * (NP + 1) + (size_t)lv.s + 16;
   cudaError_t e =
       cudaFuncSetAttribute(k_nd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
   if (e != cudaSuccess) return e;
-  const int tiles_w = (lv.f + 255) / 256;
-  const int tiles_c = (lv.f + 255) / 256;
+  const int tiles_w = (lv.f + kRowThreads - 1) / kRowThreads;
+  const int tiles_c = (lv.f + kRowThreads - 1) / kRowThreads;
   const int tiles_u = (lv.f + kUT - 1) / kUT;
   for (int k = 0; k < lv.s; k += NP) {
     const int nb = lv.s - k < NP ? lv.s - k : NP;
+    const int t1 = c->timing ? timer_begin(c, level_name("nd_pnl", depth)) : -1;
     k_nd_panel<<<lv.count, 256, psmem, c->stream>>>(F, lv.f, lv.s, k, nb, perm,
                                                     (double*)S.cbuf.p, (double*)S.pinv.p,
                                                     (int32_t*)S.swaps.p, err);
-    k_nd_rowblock<<<dim3(tiles_w + tiles_c, lv.count), 256, 0, c->stream>>>(
+    timer_end(c, t1);
+    const int t2 = c->timing ? timer_begin(c, level_name("nd_row", depth)) : -1;
+    k_nd_rowblock<<<dim3(tiles_w + tiles_c, lv.count), kRowThreads, 0, c->stream>>>(
         F, lv.f, k, nb, tiles_w, (const double*)S.cbuf.p, (const double*)S.pinv.p,
         (const int32_t*)S.swaps.p);
+    timer_end(c, t2);
+    const int t3 = c->timing ? timer_begin(c, level_name("nd_upd", depth)) : -1;
     k_nd_update<<<dim3(tiles_u * tiles_u, lv.count), 256, 0, c->stream>>>(
         F, lv.f, k, nb, tiles_u, (const double*)S.cbuf.p);
+    timer_end(c, t3);
   }
   timer_end(c, t);
   return cudaGetLastError();
@@ -626,29 +784,62 @@ cudaError_t launch_nd_solve(lsp_ctx* c, const double* y, double* x) {
   double* u = (double*)S.u.p;
   const int32_t* E = (const int32_t*)S.E.p;
   const int32_t* R = (const int32_t*)S.R.p;
-  int t = timer_begin(c, "nd_solve");
+  // rows of one front per CTA: 64 where the level has fronts enough to fill the GPU, else 8
+  // (one row per warp) so that the few large fronts near the root still spread over the SMs
+  auto rows_for = [](int count, int nrows) {
+    return (int64_t)count * ((nrows + 63) / 64) >= 8 * 152 ? 64 : 8;
+  };
   for (int d = L - 1; d >= 0; --d) {
     const NdLevel& lv = P.lv[d];
     const NdLevel* cl = lv.nchild ? &P.lv[d + 1] : nullptr;
-    dim3 grid((lv.f + 63) / 64, lv.count);
-    k_nd_fwd<<<grid, 256, sizeof(double) * (lv.s > 0 ? lv.s : 1), c->stream>>>(
-        Fb + lv.front_off, lv.f, lv.s, lv.r, E + lv.E_off, (const int32_t*)S.perm.p + lv.perm_off,
-        lv.nchild ? (const int32_t*)S.inv.p + lv.inv_off : nullptr, lv.nchild,
-        cl ? u + cl->u_off : nullptr, cl ? cl->r : 0, y, z + lv.z_off, u + lv.u_off);
+    const int rows = rows_for(lv.count, lv.f);
+    dim3 grid((lv.f + rows - 1) / rows, lv.count);
+    int t = timer_begin(c, level_name("nd_fwd", d));
+    if (lv.f <= kNdSmallFront) {
+      const size_t sm = sizeof(double) * ((size_t)(lv.s | 1) * (lv.f + 1));
+      k_nd_fwd_small<<<lv.count, 128, sm, c->stream>>>(
+          Fb + lv.front_off, lv.f, lv.s, lv.r, E + lv.E_off,
+          (const int32_t*)S.perm.p + lv.perm_off,
+          lv.nchild ? (const int32_t*)S.inv.p + lv.inv_off : nullptr, lv.nchild,
+          cl ? u + cl->u_off : nullptr, cl ? cl->r : 0, y, z + lv.z_off, u + lv.u_off);
+    } else {
+      k_nd_fwd<<<grid, 256, sizeof(double) * (lv.s > 0 ? lv.s : 1), c->stream>>>(
+          Fb + lv.front_off, lv.f, lv.s, lv.r, E + lv.E_off,
+          (const int32_t*)S.perm.p + lv.perm_off,
+          lv.nchild ? (const int32_t*)S.inv.p + lv.inv_off : nullptr, lv.nchild,
+          cl ? u + cl->u_off : nullptr, cl ? cl->r : 0, y, z + lv.z_off, u + lv.u_off, rows);
+    }
+    timer_end(c, t);
   }
   for (int d = 0; d < L; ++d) {
     const NdLevel& lv = P.lv[d];
-    dim3 grid((lv.s + 63) / 64, lv.count);
-    k_nd_bwd<<<grid, 256, sizeof(double) * (lv.r > 0 ? lv.r : 1), c->stream>>>(
-        Fb + lv.front_off, lv.f, lv.s, lv.r, E + lv.E_off, R + lv.R_off, z + lv.z_off, x);
+    const int rows = rows_for(lv.count, lv.s);
+    dim3 grid((lv.s + rows - 1) / rows, lv.count);
+    int t = timer_begin(c, level_name("nd_bwd", d));
+    if (lv.f <= kNdSmallFront) {
+      const size_t sm = sizeof(double) * ((size_t)(lv.r | 1) * (lv.s + 1));
+      k_nd_bwd_small<<<lv.count, 128, sm, c->stream>>>(Fb + lv.front_off, lv.f, lv.s, lv.r,
+                                                       E + lv.E_off, R + lv.R_off,
+                                                       z + lv.z_off, x);
+    } else {
+      k_nd_bwd<<<grid, 256, sizeof(double) * (lv.r > 0 ? lv.r : 1), c->stream>>>(
+          Fb + lv.front_off, lv.f, lv.s, lv.r, E + lv.E_off, R + lv.R_off, z + lv.z_off, x,
+          rows);
+    }
+    timer_end(c, t);
   }
-  timer_end(c, t);
   return cudaGetLastError();
 }
 
 cudaError_t nd_prepare_kernels(int max_smem) {
+  // (s | 1) (f + 1) or (r | 1) (s + 1) doubles with s, r <= f <= kNdSmallFront
+  const int small = (int)sizeof(double) * ((kNdSmallFront | 1) + 1) * (kNdSmallFront + 1);
   cudaError_t e = cudaFuncSetAttribute(k_nd_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        max_smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_nd_fwd_small, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_nd_bwd_small, cudaFuncAttributeMaxDynamicSharedMemorySize, small);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_nd_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem);
 }

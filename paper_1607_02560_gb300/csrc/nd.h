@@ -28,9 +28,9 @@
 
 namespace lsp {
 
-constexpr int kNdPanel = 8;        // columns eliminated per step in the blocked path
+constexpr int kNdPanel = 16;       // columns eliminated per step in the blocked path
 constexpr int kNdSmallFront = 160; // fronts with f <= this are swept in shared memory
-constexpr int kNdMaxN = 1024;      // the pivot panel of the cross (2n - 1 rows) fits in shared memory
+constexpr int kNdMaxN = 1024;      // the FP32 pivot panel of the cross (2n - 1 rows) fits in shared memory
 
 struct NdLevel {
   int count = 0;       // fronts at this depth

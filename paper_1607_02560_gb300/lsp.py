@@ -387,7 +387,7 @@ class Context:
         self._check(lib().lsp_kernel_timing(self.h, int(bool(enable))), "kernel_timing")
 
     def kernel_times(self) -> dict:
-        cap = 64
+        cap = 512
         names = (ctypes.c_char * 32 * cap)()
         ms = np.zeros(cap)
         launches = np.zeros(cap, dtype=np.int64)
