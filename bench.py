@@ -357,7 +357,7 @@ def run_ours(args):
         out["variants"] = variants(args, torch)
     if not args.no_solve and d == 2:
         out["nd_solve"] = []
-        for ns_ in (256, 512, 1024):
+        for ns_ in (int(x) for x in args.solve_n.split(",") if x):
             try:
                 out["nd_solve"].append(solve_variant(torch, ns_, "paper", fp64_peak,
                                                      peaks["hbm_gbs"]))
@@ -540,6 +540,21 @@ def solve_variant(torch, n: int, policy: str = "paper", fp64_peak: float | None 
     return out
 
 
+def run_solve_only(args):
+    """The nested-dissection / GMRES block alone (one JSON line), for profiling runs."""
+    import torch
+    from paper_1607_02560_gb300 import build as B
+
+    B.build()
+    torch.cuda.set_device(0)
+    peaks, _ = load_peaks()
+    fp64_peak = measure_fp64_peak(torch)
+    out = {"metric": "nested dissection setup / solve", "n_gpus": 1, "nd_solve": []}
+    for n in (int(x) for x in args.solve_n.split(",") if x):
+        out["nd_solve"].append(solve_variant(torch, n, "paper", fp64_peak, peaks["hbm_gbs"]))
+    print(json.dumps(out))
+
+
 def variants(args, torch):
     """The metric's other forms on the same GPU: FP64 vs mixed, 2D n=1024 vs 3D n=64, and the
     paper's shift policy."""
@@ -640,6 +655,10 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-solve", action="store_true",
                     help="skip the nested-dissection / GMRES measurements")
+    ap.add_argument("--solve-n", default="256,512,1024",
+                    help="grid sizes of the nested-dissection / GMRES measurements")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="print only the nested-dissection / GMRES measurements (profiling)")
     ap.add_argument("--no-learned", action="store_true", help="skip training the surrogate")
     ap.add_argument("--n", type=int, default=None, help="rescale the workload's grid (small cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -651,6 +670,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.solve_only:
+        run_solve_only(args)
     else:
         run_ours(args)
 
