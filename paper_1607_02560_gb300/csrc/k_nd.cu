@@ -49,6 +49,16 @@ __global__ void k_nd_scatter(double* __restrict__ F, const double* __restrict__ 
 }
 
 // argmax of |value| over a warp with ties to the smaller index
+__device__ __forceinline__ void warp_argmax_f(float& best, int& bi) {
+  for (int off = 16; off > 0; off >>= 1) {
+    const float ob = __shfl_xor_sync(0xffffffffu, best, off);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      bi = oi;
+    }
+  }
+}
 __device__ __forceinline__ void warp_argmax(double& best, int& bi) {
   for (int off = 16; off > 0; off >>= 1) {
     const double ob = __shfl_xor_sync(0xffffffffu, best, off);
@@ -143,99 +153,124 @@ __global__ void __launch_bounds__(256) k_nd_sweep_small(double* __restrict__ fro
 // 1 + 2 NP + q: after the step, position dst holds the row that was at position src.
 constexpr int kSwapInts = 1 + 4 * NP;
 
+// FP32 value of x for ranking pivot candidates, from the high word of the IEEE double: sign,
+// exponent rebased from 1023 to 127, the top 20 fraction bits (relative error < 2^-20);
+// magnitudes below the FP32 normal range give 0, above it infinity. Integer operations only.
+__device__ __forceinline__ float rank_f32(double x) {
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7ff) - (1023 - 127);
+  const unsigned sign = (unsigned)hi & 0x80000000u;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | (((unsigned)hi & 0xfffffu) << 3));
+}
+
 // Part 1, one CTA per front: choose nb pivot rows among positions k..s-1 by partial pivoting
-// on the panel F[k.., K]; record the row exchanges, update perm, write the permuted column
-// block cbuf[x][c] = F[src(x)][k + c] for every row x, and the inverse of the pivot block.
-// The pivot rows come from a trial elimination of the panel in FP32 (one reciprocal per
-// pivot): it only ranks candidate rows by magnitude, while every value the factorisation keeps
-// is computed in FP64 from the original entries (pivot block inverse here, row block and
-// update in parts 2 and 3). An FP64 trial elimination would cost one SM about m nb^2 / 2 FP64
-// FMAs per step on the critical path of the root fronts.
+// on the panel F[k.., K]; record the row exchanges, update perm, write the column block
+// cbuf[x][c] = F[src(x)][k + c] of the exchanged rows x, and the inverse of the pivot block.
+// The pivot rows come from a trial elimination of the panel in FP32: it only ranks candidate
+// rows by magnitude, while every value the factorisation keeps is FP64, computed from the
+// original entries (the pivot-block inverse here, the row block and the update in parts 2 and
+// 3). Each thread keeps its panel rows (row tid + t * 256, t < kPanelRows) in registers and
+// publishes its best candidate row to shared memory, so a pivot costs one block barrier.
+constexpr int kPanelRows = 8;  // rows per thread: panels of up to 2048 rows (the cross, n = 1024)
 __global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fronts, int f, int s,
                                                   int k, int nb, int32_t* __restrict__ perm,
                                                   double* __restrict__ cbuf,
                                                   double* __restrict__ pinv,
                                                   int32_t* __restrict__ swaps,
                                                   int32_t* __restrict__ err) {
-  extern __shared__ float smf[];
-  constexpr int PS = NP + 1;                          // odd row stride: no bank conflicts
-  const int m = s - k;
-  float* pan = smf;                                   // m x PS
-  uint8_t* used = (uint8_t*)(pan + (size_t)m * PS);   // m
+  constexpr int NT = 256;
+  __shared__ float cand[2][NT][NP + 1];  // each thread's best remaining row, double-buffered
+  __shared__ float wbest[2][8];
+  __shared__ int wbi[2][8];
   __shared__ int sel[NP];
-  __shared__ float wbest[8];
-  __shared__ int wbi[8];
-  __shared__ int bad, nq;
+  __shared__ int nq;
   __shared__ int dstp[2 * NP], srcp[2 * NP];
-  __shared__ double aug[NP][2 * NP];
-  __shared__ int gpiv;
-  __shared__ float gpinv;
-  __shared__ double gdinv;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nt = blockDim.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = s - k;
   const int64_t fid = blockIdx.x;
   const double* F = fronts + fid * f * f;
-  for (int i = tid; i < m; i += nt) {
-    const double* Fi = F + (int64_t)(k + i) * f + k;
-    for (int c = 0; c < NP; ++c) pan[i * PS + c] = c < nb ? (float)Fi[c] : 0.0f;
-    used[i] = 0;
+  float rv[kPanelRows][NP];
+#pragma unroll
+  for (int t = 0; t < kPanelRows; ++t) {
+    const int i = tid + t * NT;
+    const double* Fi = F + (int64_t)(k + (i < m ? i : 0)) * f + k;
+    double v[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) v[c] = (i < m && c < nb) ? Fi[c] : 0.0;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) rv[t][c] = rank_f32(v[c]);
   }
-  if (tid == 0) bad = 0;
-  __syncthreads();
-  for (int j = 0; j < nb; ++j) {
+  unsigned used = 0;  // bit t: row tid + t NT is a pivot row (or does not exist)
+#pragma unroll
+  for (int t = 0; t < kPanelRows; ++t)
+    if (tid + t * NT >= m) used |= 1u << t;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    if (j >= nb) break;
+    // this thread's candidate for pivot j
     float best = -1.0f;
-    int bi = m;
-    for (int i = tid; i < m; i += nt) {
-      if (used[i]) continue;
-      const float a = fabsf(pan[i * PS + j]);
-      if (a > best) {
+    int bt = 0;
+#pragma unroll
+    for (int t = 0; t < kPanelRows; ++t) {
+      const float a = fabsf(rv[t][j]);
+      if (!(used >> t & 1u) && a > best) {
         best = a;
-        bi = i;
+        bt = t;
       }
     }
-    for (int off = 16; off > 0; off >>= 1) {
-      const float ob = __shfl_xor_sync(0xffffffffu, best, off);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        bi = oi;
-      }
+    int bi = best >= 0.0f ? tid + bt * NT : m;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) {
+      if (c < j) continue;
+      float val = rv[0][c];
+#pragma unroll
+      for (int t = 1; t < kPanelRows; ++t)
+        if (t == bt) val = rv[t][c];
+      cand[j & 1][tid][c] = val;
     }
+    warp_argmax_f(best, bi);
     if (lane == 0) {
-      wbest[warp] = best;
-      wbi[warp] = bi;
+      wbest[j & 1][warp] = best;
+      wbi[j & 1][warp] = bi;
     }
     __syncthreads();
-    if (tid == 0) {
-      float b = wbest[0];
-      int ix = wbi[0];
-      for (int w = 1; w < nt / 32; ++w)
-        if (wbest[w] > b || (wbest[w] == b && wbi[w] < ix)) {
-          b = wbest[w];
-          ix = wbi[w];
-        }
-      if (!(b > 0.0f) || !isfinite(b) || ix >= m) {
-        bad = 1;
-        atomicOr(err, 2);
-        ix = 0;
+    float b = wbest[j & 1][0];
+    int pr = wbi[j & 1][0];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) {
+      const float bw = wbest[j & 1][w];
+      const int iw = wbi[j & 1][w];
+      if (bw > b || (bw == b && iw < pr)) {
+        b = bw;
+        pr = iw;
       }
-      sel[j] = ix;
-      used[ix] = 1;
-      gpinv = 1.0f / pan[ix * PS + j];
     }
-    __syncthreads();
-    if (bad) {  // leave a step that the next kernels read safely (no exchanges)
-      if (tid == 0) swaps[fid * kSwapInts] = 0;
+    if (!(b > 0.0f) || !isfinite(b) || pr >= m) {  // uniform: every thread read the same values
+      if (tid == 0) {
+        atomicOr(err, 2);
+        swaps[fid * kSwapInts] = 0;  // the next kernels of the step then exchange nothing
+      }
       return;
     }
-    const int pr = sel[j];
-    const float ipv = gpinv;
-    for (int i = tid; i < m; i += nt) {
-      if (used[i]) continue;
-      const float l = pan[i * PS + j] * ipv;
-      for (int c = j + 1; c < nb; ++c) pan[i * PS + c] = fmaf(-l, pan[pr * PS + c], pan[i * PS + c]);
+    if (tid == 0) sel[j] = pr;
+    const int owner = pr % NT, ot = pr / NT;
+    float pv[NP];  // the pivot row from column j on
+#pragma unroll
+    for (int c = 0; c < NP; ++c) pv[c] = c >= j ? cand[j & 1][owner][c] : 0.0f;
+    if (owner == tid) used |= 1u << ot;
+    const float ipv = 1.0f / pv[j];
+#pragma unroll
+    for (int t = 0; t < kPanelRows; ++t) {
+      if (used >> t & 1u) continue;
+      const float l = rv[t][j] * ipv;
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c > j) rv[t][c] = fmaf(-l, pv[c], rv[t][c]);
     }
-    __syncthreads();
   }
+  __syncthreads();  // sel complete
   // row exchanges (warp 0): position k + j takes the row chosen j-th; the rows of K that were
   // not chosen move, in increasing position order, to the positions the chosen rows left
   // outside K (taken in choice order)
@@ -257,7 +292,6 @@ __global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fro
     const int nout = __popc(outb);
     int32_t* pf = perm + fid * s;
     int32_t* sw = swaps + fid * kSwapInts;
-    // entries: lanes 0..nb-1 give (k + j <- ps_j); chosen rows outside K also give (ps_j <- dpos)
     const int old_sel = act ? pf[ps] : 0;
     const int old_dis = dpos >= 0 ? pf[dpos] : 0;
     __syncwarp();
@@ -284,88 +318,81 @@ __global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fro
   }
   __syncthreads();
   const int q = nq;
-  // the permuted column block
+  // the column block of the exchanged rows (the other rows are read in place by part 2)
   double* cb = cbuf + fid * (int64_t)f * NP;
-  for (int x = tid; x < f; x += nt) {
-    int src = x;
-    for (int a = 0; a < q; ++a)
-      if (dstp[a] == x) src = srcp[a];
-    const double* Fs = F + (int64_t)src * f + k;
-    double* cx = cb + (int64_t)x * NP;
-    for (int c = 0; c < NP; ++c) cx[c] = c < nb ? Fs[c] : 0.0;
+  for (int e = tid; e < q * NP; e += NT) {
+    const int a = e / NP, c = e % NP;
+    cb[(int64_t)dstp[a] * NP + c] = c < nb ? F[(int64_t)srcp[a] * f + k + c] : 0.0;
   }
-  // inverse of the pivot block (FP64) by Gauss-Jordan with partial pivoting: [A | I] -> [I | A^-1]
-  for (int e = tid; e < NP * 2 * NP; e += nt) {
-    const int r = e / (2 * NP), c = e % (2 * NP);
-    double v = 0.0;
-    if (r < nb) {
-      if (c < NP) {
-        int src = k + r;
-        for (int a = 0; a < q; ++a)
-          if (dstp[a] == k + r) src = srcp[a];
-        v = c < nb ? F[(int64_t)src * f + k + c] : 0.0;
-      } else {
-        v = (c - NP) == r ? 1.0 : 0.0;
-      }
-    }
-    aug[r][c] = v;
+  // inverse of the pivot block A (FP64): Gauss-Jordan on [A | I], one element per thread in
+  // each half (rows r = tid / 16, columns c and c + 16), no row exchanges: pivot j is taken in
+  // the unpivoted row p_j of largest |a_pj,j| (integer comparison of magnitude bits), row p_j
+  // is scaled by one reciprocal, column j is eliminated from the other rows. The left block
+  // ends as a permutation with a 1 at (p_j, j), so row j of A^-1 is the right block's row p_j.
+  __shared__ double aug[NP][2 * NP + 1];
+  __shared__ double gd;
+  __shared__ int gp, rowpiv[NP];
+  const int gr = tid / NP, gc = tid % NP;  // 256 threads = 16 rows x 16 column pairs
+  {
+    int src = k + gr;
+    for (int e = 0; e < q; ++e)
+      if (dstp[e] == k + gr) src = srcp[e];
+    aug[gr][gc] = (gr < nb && gc < nb) ? F[(int64_t)src * f + k + gc] : 0.0;
+    aug[gr][NP + gc] = (gr < nb && gc == gr) ? 1.0 : 0.0;
+    if (gc == 0) rowpiv[gr] = gr < nb ? -1 : NP;  // pivot index of the row, -1 while unpivoted
   }
   __syncthreads();
   for (int j = 0; j < nb; ++j) {
     if (warp == 0) {
-      double b = -1.0;
-      int p = j;
-      if (lane >= j && lane < nb) {
-        b = fabs(aug[lane][j]);
-        p = lane;
+      const bool cand_ok = lane < nb && rowpiv[lane] < 0;
+      unsigned long long key =
+          cand_ok ? ((unsigned long long)__double_as_longlong(aug[lane][j]) & 0x7fffffffffffffffull)
+                  : 0ull;
+      int p = lane;
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long ok = __shfl_xor_sync(0xffffffffu, key, off);
+        const int op = __shfl_xor_sync(0xffffffffu, p, off);
+        if (ok > key || (ok == key && op < p)) {
+          key = ok;
+          p = op;
+        }
       }
-      warp_argmax(b, p);
       if (lane == 0) {
-        gpiv = p;
-        if (!(b > 0.0)) atomicOr(err, 4);
-        gdinv = 1.0 / aug[p][j];  // the one FP64 division of this pivot
+        if (key == 0ull || key >= 0x7ff0000000000000ull) atomicOr(err, 4);  // zero, Inf or NaN
+        gp = p;
+        rowpiv[p] = j;
+        gd = 1.0 / aug[p][j];  // the one FP64 division of this pivot
       }
     }
     __syncthreads();
-    const int p = gpiv;
-    if (p != j && tid < 2 * NP) {
-      const double t = aug[j][tid];
-      aug[j][tid] = aug[p][tid];
-      aug[p][tid] = t;
-    }
+    const int p = gp;
+    const double d = gd;
+    const double lr = gr == p ? 0.0 : aug[gr][j];  // multipliers, read before any update
+    const double p0 = aug[p][gc] * d, p1 = aug[p][NP + gc] * d;
     __syncthreads();
-    const double d = gdinv;
-    double lr[2], pjc[2];
-    for (int h = 0; h < 2; ++h) {
-      const int e = tid + h * nt;
-      lr[h] = pjc[h] = 0.0;
-      if (e < NP * 2 * NP) {
-        lr[h] = aug[e / (2 * NP)][j];
-        pjc[h] = aug[j][e % (2 * NP)] * d;
-      }
-    }
-    __syncthreads();
-    for (int h = 0; h < 2; ++h) {
-      const int e = tid + h * nt;
-      if (e < NP * 2 * NP) {
-        const int r = e / (2 * NP), c = e % (2 * NP);
-        if (r < nb) aug[r][c] = r == j ? pjc[h] : fma(-lr[h], pjc[h], aug[r][c]);
-      }
+    if (gr == p) {
+      aug[gr][gc] = p0;
+      aug[gr][NP + gc] = p1;
+    } else {
+      aug[gr][gc] = fma(-lr, p0, aug[gr][gc]);
+      aug[gr][NP + gc] = fma(-lr, p1, aug[gr][NP + gc]);
     }
     __syncthreads();
   }
-  for (int e = tid; e < NP * NP; e += nt) {
-    const int r = e / NP, c = e % NP;
-    pinv[fid * NP * NP + e] = (r < nb && c < nb) ? aug[r][NP + c] : 0.0;
+  {
+    const int jr = rowpiv[gr];
+    if (jr >= 0 && jr < NP) pinv[fid * NP * NP + jr * NP + gc] = gc < nb ? aug[gr][NP + gc] : 0.0;
+    else if (gr >= nb) pinv[fid * NP * NP + gr * NP + gc] = 0.0;
   }
 }
 
 // Part 2: rows K become A_KK^-1 F[K, j] for the columns j outside K (after applying the row
-// exchanges to those columns), and the column block becomes [A_KK^-1 on K; -cbuf A_KK^-1 off K].
+// exchanges to those columns), and the column block becomes [A_KK^-1 on K; -cbuf A_KK^-1 off K];
+// the column tiles also complete cbuf with the rows that the exchanges did not move.
 constexpr int kRowThreads = 64;  // one column (or row) per thread; small CTAs spread the step
 __global__ void __launch_bounds__(kRowThreads) k_nd_rowblock(double* __restrict__ fronts, int f, int k,
                                                      int nb, int tiles_w,
-                                                     const double* __restrict__ cbuf,
+                                                     double* __restrict__ cbuf,
                                                      const double* __restrict__ pinv,
                                                      const int32_t* __restrict__ swaps) {
   __shared__ double pi[NP][NP];
@@ -425,16 +452,29 @@ __global__ void __launch_bounds__(kRowThreads) k_nd_rowblock(double* __restrict_
   } else {
     const int x = (blockIdx.x - tiles_w) * blockDim.x + tid;
     if (x >= f) return;
-    if (x >= k && x < k + nb) {
-      for (int c = 0; c < nb; ++c) F[(int64_t)x * f + k + c] = pi[x - k][c];
-    } else {
-      const double* cx = cbuf + fid * (int64_t)f * NP + (int64_t)x * NP;
-      double cr[NP];
+    bool moved = false;
+    for (int a = 0; a < q; ++a)
+      if (dstp[a] == x) moved = true;
+    double* cx = cbuf + fid * (int64_t)f * NP + (int64_t)x * NP;
+    double* Fx = F + (int64_t)x * f + k;
+    double cr[NP];
+    if (moved) {  // written by part 1 from the row's source position
+#pragma unroll
       for (int mm = 0; mm < NP; ++mm) cr[mm] = cx[mm];
+    } else {      // still in place: this thread is the only reader and writer of F[x][K]
+#pragma unroll
+      for (int mm = 0; mm < NP; ++mm) cr[mm] = mm < nb ? Fx[mm] : 0.0;
+#pragma unroll
+      for (int mm = 0; mm < NP; ++mm) cx[mm] = cr[mm];
+    }
+    if (x >= k && x < k + nb) {
+      for (int c = 0; c < nb; ++c) Fx[c] = pi[x - k][c];
+    } else {
       for (int c = 0; c < nb; ++c) {
         double acc = 0.0;
+#pragma unroll
         for (int mm = 0; mm < NP; ++mm) acc = fma(cr[mm], pi[mm][c], acc);
-        F[(int64_t)x * f + k + c] = -acc;
+        Fx[c] = -acc;
       }
     }
   }
@@ -591,7 +631,7 @@ __global__ void __launch_bounds__(128) k_nd_fwd_small(const double* __restrict__
   const int ld = s | 1;
   double* wE = sh;           // s
   double* Ms = sh + ld;      // f rows of stride ld: F[i][0..s)
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int64_t p = blockIdx.x;
   const double* Fp = F + p * f * f;
   const int32_t* iv = nchild ? inv + p * f * 2 : nullptr;
@@ -632,7 +672,7 @@ __global__ void __launch_bounds__(128) k_nd_bwd_small(const double* __restrict__
   const int ld = r | 1;
   double* xR = sh;          // r
   double* Mb = sh + ld;     // s rows of stride ld: F[i][s..f)
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int64_t p = blockIdx.x;
   const double* Fp = F + p * f * f;
   for (int m = tid; m < r; m += blockDim.x) xR[m] = x[R[p * r + m]];
@@ -763,7 +803,7 @@ cudaError_t launch_nd_sweep(lsp_ctx* c, int depth) {
     timer_end(c, t1);
     const int t2 = c->timing ? timer_begin(c, level_name("nd_row", depth)) : -1;
     k_nd_rowblock<<<dim3(tiles_w + tiles_c, lv.count), kRowThreads, 0, c->stream>>>(
-        F, lv.f, k, nb, tiles_w, (const double*)S.cbuf.p, (const double*)S.pinv.p,
+        F, lv.f, k, nb, tiles_w, (double*)S.cbuf.p, (const double*)S.pinv.p,
         (const int32_t*)S.swaps.p);
     timer_end(c, t2);
     const int t3 = c->timing ? timer_begin(c, level_name("nd_upd", depth)) : -1;
