@@ -355,14 +355,8 @@ def run_ours(args):
         out["config"]["training"] = train_info
     if not args.no_variants:
         out["variants"] = variants(args, torch)
-    if not args.no_solve and d == 2:
-        out["nd_solve"] = []
-        for ns_ in (int(x) for x in args.solve_n.split(",") if x):
-            try:
-                out["nd_solve"].append(solve_variant(torch, ns_, "paper", fp64_peak,
-                                                     peaks["hbm_gbs"]))
-            except Exception as exc:  # must not hide the main line
-                out["nd_solve"].append({"n": ns_, "error": str(exc)[:300]})
+    if not args.no_solve:
+        out["nd_solve"] = solve_block(args, torch, fp64_peak, peaks["hbm_gbs"])
     if ws == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.workload, args.policy, budget_s=args.cpu_budget)
     print(json.dumps(out))
@@ -458,33 +452,36 @@ def learned_variant(torch, workload: str, steps: int = 3000):
 
 
 def solve_variant(torch, n: int, policy: str = "paper", fp64_peak: float | None = None,
-                  hbm_peak: float | None = None):
+                  hbm_peak: float | None = None, d: int = 2):
     """Applying the preconditioner (Sec. 5 tables): nested-dissection setup T_NDsetup, one
-    application T_NDapp, and the GMRES(40) solve to rtol 1e-6 (T_NDsolve, N_iter) on the
-    velocity field of a Gaussian profile at the centre, 4 points per wavelength, n x n grid."""
+    application T_NDapp, and the GMRES(40) solve to rtol 1e-6 (T_NDsolve, N_iter). 2D: the
+    velocity field of a Gaussian profile at the centre, 4 points per wavelength, n x n grid;
+    3D: the Schroedinger-type potential of randomly placed Gaussian wells, n^3 grid."""
     from lsp_inputs import gaussian_source, make_workload
     from paper_1607_02560_gb300 import Context
 
-    v = make_workload("helm2d_n32", n=n)
-    f = gaussian_source(n, 2, 2.0).reshape(-1)
+    wl = "helm2d_n32" if d == 2 else "schr3d_n64"
+    v = make_workload(wl, n=n)
+    f = gaussian_source(n, d, 2.0).reshape(-1)
     stream = torch.cuda.Stream()
-    ctx = Context(2, n, stream=stream)
-    out = {"workload": f"helm2d_n32 rescaled to n={n} (omega/2pi = {n // 4})", "policy": policy,
-           "n": n}
+    ctx = Context(d, n, stream=stream)
+    text = f"(omega/2pi = {n // 4})" if d == 2 else "(max|v| h^2 = 0.6)"
+    out = {"workload": f"{wl} rescaled to n={n} {text}", "policy": policy, "d": d, "n": n}
     with torch.cuda.stream(stream):
         ctx.set_potential(v)
         ctx.build_stencils(policy=policy)
         t0 = time.perf_counter()
         ctx.nd_factor()  # plans the dissection on the host, then factorises
         out["nd_setup_first_call_s"] = time.perf_counter() - t0
+        reps = 3 if out["nd_setup_first_call_s"] < 2.0 else 1
         setup = []
-        for _ in range(3):
+        for _ in range(reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ctx.nd_factor()
             setup.append(time.perf_counter() - t0)
         info = ctx.nd_info()
-        y = torch.from_numpy(np.random.default_rng(0).standard_normal(n * n)).cuda()
+        y = torch.from_numpy(np.random.default_rng(0).standard_normal(v.size)).cuda()
         x = torch.empty_like(y)
         torch.cuda.synchronize()
         for _ in range(3):
@@ -499,7 +496,8 @@ def solve_variant(torch, n: int, policy: str = "paper", fp64_peak: float | None 
         torch.cuda.synchronize()
         app_ms = float(np.median([a.elapsed_time(b) for a, b in evs]))
         ctx.kernel_timing(True)
-        ctx.nd_factor()
+        if reps > 1:
+            ctx.nd_factor()
         for _ in range(5):
             ctx.nd_solve(y, x)
         ctx.synchronize()
@@ -509,7 +507,7 @@ def solve_variant(torch, n: int, policy: str = "paper", fp64_peak: float | None 
         torch.cuda.synchronize()
         ctx.gmres(fd)  # warm
         gm = []
-        for _ in range(3):
+        for _ in range(reps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ud, res = ctx.gmres(fd)
@@ -540,6 +538,18 @@ def solve_variant(torch, n: int, policy: str = "paper", fp64_peak: float | None 
     return out
 
 
+def solve_block(args, torch, fp64_peak, hbm_peak):
+    """The nested-dissection / GMRES measurements at the 2D and 3D sizes asked for."""
+    res = []
+    for d, sizes in ((2, args.solve_n), (3, args.solve_n3)):
+        for n in (int(x) for x in sizes.split(",") if x):
+            try:
+                res.append(solve_variant(torch, n, "paper", fp64_peak, hbm_peak, d=d))
+            except Exception as exc:  # must not hide the main line
+                res.append({"d": d, "n": n, "error": str(exc)[:300]})
+    return res
+
+
 def run_solve_only(args):
     """The nested-dissection / GMRES block alone (one JSON line), for profiling runs."""
     import torch
@@ -549,9 +559,8 @@ def run_solve_only(args):
     torch.cuda.set_device(0)
     peaks, _ = load_peaks()
     fp64_peak = measure_fp64_peak(torch)
-    out = {"metric": "nested dissection setup / solve", "n_gpus": 1, "nd_solve": []}
-    for n in (int(x) for x in args.solve_n.split(",") if x):
-        out["nd_solve"].append(solve_variant(torch, n, "paper", fp64_peak, peaks["hbm_gbs"]))
+    out = {"metric": "nested dissection setup / solve", "n_gpus": 1,
+           "nd_solve": solve_block(args, torch, fp64_peak, peaks["hbm_gbs"])}
     print(json.dumps(out))
 
 
@@ -657,6 +666,8 @@ def main():
                     help="skip the nested-dissection / GMRES measurements")
     ap.add_argument("--solve-n", default="256,512,1024",
                     help="grid sizes of the nested-dissection / GMRES measurements")
+    ap.add_argument("--solve-n3", default="16,32",
+                    help="3D grid sizes of the nested-dissection / GMRES measurements")
     ap.add_argument("--solve-only", action="store_true",
                     help="print only the nested-dissection / GMRES measurements (profiling)")
     ap.add_argument("--no-learned", action="store_true", help="skip training the surrogate")

@@ -261,15 +261,16 @@ lsp_status lsp_apply_operator_noalloc(int d, int n, const double* v_dev, const d
  *
  * P = Q + C diag(v - s) has the sparsity of Q, so P^-1 is applied through a nested-dissection
  * factorisation, and (L + diag v) u = f is solved by GMRES left-preconditioned with P^-1 C.
- * 2D grids only (n a power of two, 4 <= n <= 1024); rows of a t = 1 build, or of a t = 2 build
- * with nd_leaf = b (the t_j rule keeps every row inside the separators of that dissection).
+ * 2D grids (n a power of two, 4 <= n <= 1024) and 3D grids (4 <= n <= 64); rows of a t = 1
+ * build, or of a 2D t = 2 build with nd_leaf = b (the t_j rule keeps every row inside the
+ * separators of that dissection).
  *
- * Elimination tree: the cross {x_0 = 0} U {x_1 = 0} last; before it, the boxes of the remaining
- * open square, each split through its middle grid line (longer side first) down to leaf boxes
- * of at most (b - 1) x (b - 1) points. Every separator is a line x_a = 0 (mod b). Each front
- * (eliminated set E, ring R of ancestors' points) is inverted on E in place with row pivoting
- * inside E; the figure of Sec. 3 groups the separators into edges and vertices instead, with the
- * same leaf boxes and the same separator lines. */
+ * Elimination tree: the root separator {x : some x_a = 0} last; before it, the boxes of the
+ * remaining open square (cube), each split through the middle grid line (plane) of its longest
+ * side down to leaf boxes of at most (b - 1)^d points. Every separator lies on x_a = 0 (mod b).
+ * Each front (eliminated set E, ring R of ancestors' points) is inverted on E in place with row
+ * pivoting inside E; the figure of Sec. 3 groups the separators into edges and vertices
+ * instead, with the same leaf boxes and the same separator lines. */
 typedef struct {
   int leaf;          /* b: power of two in [4, n]. 0: the nd_leaf of a t = 2 build, else 8      */
                      /* (Sec. 5 fixes b = 8)                                                     */
@@ -299,18 +300,20 @@ void lsp_default_nd_opts(lsp_nd_opts* opts);
 /* Factorise the P rows of the last build (stream-ordered on the context stream; returns after
  * the stream has finished, so the call's duration is the setup time T_NDsetup of Sec. 5). The
  * symbolic plan of the dissection is made on the host once per (n, b, row pattern) and kept.
- * Errors: LSP_ERR_STATE before a build; LSP_ERR_UNSUPPORTED for 1D/3D grids, n > 1024 or rows
- * that cross the separators (t = 2 without nd_leaf); LSP_ERR_ARG for a bad b or b != nd_leaf;
+ * Errors: LSP_ERR_STATE before a build; LSP_ERR_UNSUPPORTED for 1D grids, n above the limits
+ * or rows that cross the separators (t = 2 without nd_leaf); LSP_ERR_ARG for a bad b or
+ * b != nd_leaf;
  * LSP_ERR_DEGENERATE when a pivot vanishes (P singular). A later build invalidates the factor. */
 lsp_status lsp_nd_factor(lsp_ctx* ctx, const lsp_nd_opts* opts);
 
-/* Host only (no context, no device): plan the dissection of an n x n grid with leaf b for the
- * rows of a t = 1 build (t = 1) or of a t = 2 build with nd_leaf (t = 2) and report its sizes;
- * the first `cap` depths (0 = the cross) also give their front count and |E|, |R| in count[],
- * s[], r[] (any may be NULL). LSP_ERR_UNSUPPORTED with the reason in err (errcap bytes) when the
- * rows or sizes do not fit; LSP_ERR_ARG for t outside {1, 2} or a NULL info. */
-lsp_status lsp_nd_plan_info(int n, int leaf, int t, int nd_leaf, lsp_nd_info* info, int cap,
-                            int* count, int* s, int* r, char* err, int errcap);
+/* Host only (no context, no device): plan the dissection of the n^d grid (d = 2, 3) with leaf
+ * b for the rows of a t = 1 build (t = 1) or of a 2D t = 2 build with nd_leaf (t = 2) and report
+ * its sizes; the first `cap` depths (0 = the root separator) also give their front count and
+ * |E|, |R| in count[], s[], r[] (any may be NULL). LSP_ERR_UNSUPPORTED with the reason in err
+ * (errcap bytes) when the rows or sizes do not fit; LSP_ERR_ARG for d outside {2, 3}, t outside
+ * {1, 2} or a NULL info. */
+lsp_status lsp_nd_plan_info(int d, int n, int leaf, int t, int nd_leaf, lsp_nd_info* info,
+                            int cap, int* count, int* s, int* r, char* err, int errcap);
 
 /* Sizes and flop counts of the planned dissection. LSP_ERR_STATE if none was planned. */
 lsp_status lsp_nd_get_info(lsp_ctx* ctx, lsp_nd_info* info);

@@ -173,104 +173,17 @@ __device__ __forceinline__ float rank_f32(double x) {
 // original entries (the pivot-block inverse here, the row block and the update in parts 2 and
 // 3). Each thread keeps its panel rows (row tid + t * 256, t < kPanelRows) in registers and
 // publishes its best candidate row to shared memory, so a pivot costs one block barrier.
-constexpr int kPanelRows = 8;  // rows per thread: panels of up to 2048 rows (the cross, n = 1024)
-__global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fronts, int f, int s,
-                                                  int k, int nb, int32_t* __restrict__ perm,
-                                                  double* __restrict__ cbuf,
-                                                  double* __restrict__ pinv,
-                                                  int32_t* __restrict__ swaps,
-                                                  int32_t* __restrict__ err) {
+// Common end of part 1 (after the pivot rows sel[0..nb) are known, block-synchronised):
+// row exchanges, the column block of the exchanged rows, the FP64 pivot-block inverse.
+__device__ __forceinline__ void panel_tail(const double* __restrict__ F, int f, int s, int k,
+                                           int nb, int64_t fid, const int* sel,
+                                           int32_t* __restrict__ perm, double* __restrict__ cbuf,
+                                           double* __restrict__ pinv,
+                                           int32_t* __restrict__ swaps, int32_t* __restrict__ err) {
   constexpr int NT = 256;
-  __shared__ float cand[2][NT][NP + 1];  // each thread's best remaining row, double-buffered
-  __shared__ float wbest[2][8];
-  __shared__ int wbi[2][8];
-  __shared__ int sel[NP];
   __shared__ int nq;
   __shared__ int dstp[2 * NP], srcp[2 * NP];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m = s - k;
-  const int64_t fid = blockIdx.x;
-  const double* F = fronts + fid * f * f;
-  float rv[kPanelRows][NP];
-#pragma unroll
-  for (int t = 0; t < kPanelRows; ++t) {
-    const int i = tid + t * NT;
-    const double* Fi = F + (int64_t)(k + (i < m ? i : 0)) * f + k;
-    double v[NP];
-#pragma unroll
-    for (int c = 0; c < NP; ++c) v[c] = (i < m && c < nb) ? Fi[c] : 0.0;
-#pragma unroll
-    for (int c = 0; c < NP; ++c) rv[t][c] = rank_f32(v[c]);
-  }
-  unsigned used = 0;  // bit t: row tid + t NT is a pivot row (or does not exist)
-#pragma unroll
-  for (int t = 0; t < kPanelRows; ++t)
-    if (tid + t * NT >= m) used |= 1u << t;
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    if (j >= nb) break;
-    // this thread's candidate for pivot j
-    float best = -1.0f;
-    int bt = 0;
-#pragma unroll
-    for (int t = 0; t < kPanelRows; ++t) {
-      const float a = fabsf(rv[t][j]);
-      if (!(used >> t & 1u) && a > best) {
-        best = a;
-        bt = t;
-      }
-    }
-    int bi = best >= 0.0f ? tid + bt * NT : m;
-#pragma unroll
-    for (int c = 0; c < NP; ++c) {
-      if (c < j) continue;
-      float val = rv[0][c];
-#pragma unroll
-      for (int t = 1; t < kPanelRows; ++t)
-        if (t == bt) val = rv[t][c];
-      cand[j & 1][tid][c] = val;
-    }
-    warp_argmax_f(best, bi);
-    if (lane == 0) {
-      wbest[j & 1][warp] = best;
-      wbi[j & 1][warp] = bi;
-    }
-    __syncthreads();
-    float b = wbest[j & 1][0];
-    int pr = wbi[j & 1][0];
-#pragma unroll
-    for (int w = 1; w < NT / 32; ++w) {
-      const float bw = wbest[j & 1][w];
-      const int iw = wbi[j & 1][w];
-      if (bw > b || (bw == b && iw < pr)) {
-        b = bw;
-        pr = iw;
-      }
-    }
-    if (!(b > 0.0f) || !isfinite(b) || pr >= m) {  // uniform: every thread read the same values
-      if (tid == 0) {
-        atomicOr(err, 2);
-        swaps[fid * kSwapInts] = 0;  // the next kernels of the step then exchange nothing
-      }
-      return;
-    }
-    if (tid == 0) sel[j] = pr;
-    const int owner = pr % NT, ot = pr / NT;
-    float pv[NP];  // the pivot row from column j on
-#pragma unroll
-    for (int c = 0; c < NP; ++c) pv[c] = c >= j ? cand[j & 1][owner][c] : 0.0f;
-    if (owner == tid) used |= 1u << ot;
-    const float ipv = 1.0f / pv[j];
-#pragma unroll
-    for (int t = 0; t < kPanelRows; ++t) {
-      if (used >> t & 1u) continue;
-      const float l = rv[t][j] * ipv;
-#pragma unroll
-      for (int c = 0; c < NP; ++c)
-        if (c > j) rv[t][c] = fmaf(-l, pv[c], rv[t][c]);
-    }
-  }
-  __syncthreads();  // sel complete
   // row exchanges (warp 0): position k + j takes the row chosen j-th; the rows of K that were
   // not chosen move, in increasing position order, to the positions the chosen rows left
   // outside K (taken in choice order)
@@ -384,6 +297,214 @@ __global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fro
     if (jr >= 0 && jr < NP) pinv[fid * NP * NP + jr * NP + gc] = gc < nb ? aug[gr][NP + gc] : 0.0;
     else if (gr >= nb) pinv[fid * NP * NP + gr * NP + gc] = 0.0;
   }
+}
+
+constexpr int kPanelRows = 8;  // rows per thread: panels of up to 2048 rows (the cross, n = 1024)
+__global__ void __launch_bounds__(256) k_nd_panel(const double* __restrict__ fronts, int f, int s,
+                                                  int k, int nb, int32_t* __restrict__ perm,
+                                                  double* __restrict__ cbuf,
+                                                  double* __restrict__ pinv,
+                                                  int32_t* __restrict__ swaps,
+                                                  int32_t* __restrict__ err) {
+  constexpr int NT = 256;
+  __shared__ float cand[2][NT][NP + 1];  // each thread's best remaining row, double-buffered
+  __shared__ float wbest[2][8];
+  __shared__ int wbi[2][8];
+  __shared__ int sel[NP];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = s - k;
+  const int64_t fid = blockIdx.x;
+  const double* F = fronts + fid * f * f;
+  float rv[kPanelRows][NP];
+#pragma unroll
+  for (int t = 0; t < kPanelRows; ++t) {
+    const int i = tid + t * NT;
+    const double* Fi = F + (int64_t)(k + (i < m ? i : 0)) * f + k;
+    double v[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) v[c] = (i < m && c < nb) ? Fi[c] : 0.0;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) rv[t][c] = rank_f32(v[c]);
+  }
+  unsigned used = 0;  // bit t: row tid + t NT is a pivot row (or does not exist)
+#pragma unroll
+  for (int t = 0; t < kPanelRows; ++t)
+    if (tid + t * NT >= m) used |= 1u << t;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    if (j >= nb) break;
+    // this thread's candidate for pivot j
+    float best = -1.0f;
+    int bt = 0;
+#pragma unroll
+    for (int t = 0; t < kPanelRows; ++t) {
+      const float a = fabsf(rv[t][j]);
+      if (!(used >> t & 1u) && a > best) {
+        best = a;
+        bt = t;
+      }
+    }
+    int bi = best >= 0.0f ? tid + bt * NT : m;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) {
+      if (c < j) continue;
+      float val = rv[0][c];
+#pragma unroll
+      for (int t = 1; t < kPanelRows; ++t)
+        if (t == bt) val = rv[t][c];
+      cand[j & 1][tid][c] = val;
+    }
+    warp_argmax_f(best, bi);
+    if (lane == 0) {
+      wbest[j & 1][warp] = best;
+      wbi[j & 1][warp] = bi;
+    }
+    __syncthreads();
+    float b = wbest[j & 1][0];
+    int pr = wbi[j & 1][0];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) {
+      const float bw = wbest[j & 1][w];
+      const int iw = wbi[j & 1][w];
+      if (bw > b || (bw == b && iw < pr)) {
+        b = bw;
+        pr = iw;
+      }
+    }
+    if (!(b > 0.0f) || !isfinite(b) || pr >= m) {  // uniform: every thread read the same values
+      if (tid == 0) {
+        atomicOr(err, 2);
+        swaps[fid * kSwapInts] = 0;  // the next kernels of the step then exchange nothing
+      }
+      return;
+    }
+    if (tid == 0) sel[j] = pr;
+    const int owner = pr % NT, ot = pr / NT;
+    float pv[NP];  // the pivot row from column j on
+#pragma unroll
+    for (int c = 0; c < NP; ++c) pv[c] = c >= j ? cand[j & 1][owner][c] : 0.0f;
+    if (owner == tid) used |= 1u << ot;
+    const float ipv = 1.0f / pv[j];
+#pragma unroll
+    for (int t = 0; t < kPanelRows; ++t) {
+      if (used >> t & 1u) continue;
+      const float l = rv[t][j] * ipv;
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c > j) rv[t][c] = fmaf(-l, pv[c], rv[t][c]);
+    }
+  }
+  __syncthreads();  // sel complete
+  panel_tail(F, f, s, k, nb, fid, sel, perm, cbuf, pinv, swaps, err);
+}
+
+// Part 1 for panels of more than kPanelRows * 256 rows (the root planes of 3D grids): the same
+// FP32 trial elimination with the ranking rows in a global scratch (L2-resident) instead of
+// registers; each thread handles rows tid + t * 256, t < 64 (up to 16 384 rows).
+__global__ void __launch_bounds__(256) k_nd_panel_big(const double* __restrict__ fronts, int f,
+                                                      int s, int k, int nb,
+                                                      int32_t* __restrict__ perm,
+                                                      double* __restrict__ cbuf,
+                                                      double* __restrict__ pinv,
+                                                      int32_t* __restrict__ swaps,
+                                                      int32_t* __restrict__ err,
+                                                      float* __restrict__ scratch) {
+  constexpr int NT = 256, PS = NP + 1;
+  __shared__ float cand[2][NT][PS];
+  __shared__ float wbest[2][8];
+  __shared__ int wbi[2][8];
+  __shared__ int sel[NP];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m = s - k;
+  const int64_t fid = blockIdx.x;
+  const double* F = fronts + fid * f * f;
+  float* pan = scratch + fid * (int64_t)s * PS;
+  const int nrows = (m - tid + NT - 1) / NT;  // rows of this thread (<= 64)
+  float best = -1.0f;
+  int bt = 0;
+  for (int t = 0; t < nrows; ++t) {
+    const int i = tid + t * NT;
+    const double* Fi = F + (int64_t)(k + i) * f + k;
+    double v[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) v[c] = c < nb ? Fi[c] : 0.0;
+#pragma unroll
+    for (int c = 0; c < NP; ++c) pan[(int64_t)i * PS + c] = rank_f32(v[c]);
+    const float a = fabsf(rank_f32(v[0]));
+    if (a > best) {
+      best = a;
+      bt = t;
+    }
+  }
+  unsigned long long used = 0;
+  for (int j = 0; j < nb; ++j) {
+    int bi = best >= 0.0f ? tid + bt * NT : m;
+    if (best >= 0.0f) {
+      const float* rowc = pan + (int64_t)bi * PS;
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c >= j) cand[j & 1][tid][c] = rowc[c];
+    }
+    warp_argmax_f(best, bi);
+    if (lane == 0) {
+      wbest[j & 1][warp] = best;
+      wbi[j & 1][warp] = bi;
+    }
+    __syncthreads();
+    float b = wbest[j & 1][0];
+    int pr = wbi[j & 1][0];
+#pragma unroll
+    for (int w = 1; w < NT / 32; ++w) {
+      const float bw = wbest[j & 1][w];
+      const int iw = wbi[j & 1][w];
+      if (bw > b || (bw == b && iw < pr)) {
+        b = bw;
+        pr = iw;
+      }
+    }
+    if (!(b > 0.0f) || !isfinite(b) || pr >= m) {  // uniform
+      if (tid == 0) {
+        atomicOr(err, 2);
+        swaps[fid * kSwapInts] = 0;
+      }
+      return;
+    }
+    if (tid == 0) sel[j] = pr;
+    const int owner = pr % NT;
+    if (owner == tid) used |= 1ull << (pr / NT);
+    float pv[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) pv[c] = c >= j ? cand[j & 1][owner][c] : 0.0f;
+    const float ipv = 1.0f / pv[j];
+    best = -1.0f;
+    bt = 0;
+    for (int t = 0; t < nrows; ++t) {
+      if (used >> t & 1ull) continue;
+      float* row = pan + (int64_t)(tid + t * NT) * PS;
+      float x[NP];
+#pragma unroll
+      for (int c = 0; c < NP; ++c) x[c] = row[c];
+      const float l = x[j] * ipv;
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c > j) x[c] = fmaf(-l, pv[c], x[c]);
+#pragma unroll
+      for (int c = 0; c < NP; ++c)
+        if (c > j) row[c] = x[c];
+      if (j + 1 < nb) {
+        float a = 0.0f;
+#pragma unroll
+        for (int c = 0; c < NP; ++c)
+          if (c == j + 1) a = fabsf(x[c]);
+        if (a > best) {
+          best = a;
+          bt = t;
+        }
+      }
+    }
+  }
+  __syncthreads();  // sel complete
+  panel_tail(F, f, s, k, nb, fid, sel, perm, cbuf, pinv, swaps, err);
 }
 
 // Part 2: rows K become A_KK^-1 F[K, j] for the columns j outside K (after applying the row
@@ -787,19 +908,23 @@ cudaError_t launch_nd_sweep(lsp_ctx* c, int depth) {
   }
   // blocked steps; perm starts as the identity
   k_nd_iota<<<grid_for((int64_t)lv.count * lv.s, 256), 256, 0, c->stream>>>(perm, lv.count, lv.s);
-  const size_t psmem = sizeof(float) * (size_t)lv.s * (NP + 1) + (size_t)lv.s + 16;
-  cudaError_t e =
-      cudaFuncSetAttribute(k_nd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
-  if (e != cudaSuccess) return e;
+  const bool big = lv.s > kPanelRows * 256;
+  if (big && !S.pscratch.p) return cudaErrorInvalidValue;
   const int tiles_w = (lv.f + kRowThreads - 1) / kRowThreads;
   const int tiles_c = (lv.f + kRowThreads - 1) / kRowThreads;
   const int tiles_u = (lv.f + kUT - 1) / kUT;
   for (int k = 0; k < lv.s; k += NP) {
     const int nb = lv.s - k < NP ? lv.s - k : NP;
     const int t1 = c->timing ? timer_begin(c, level_name("nd_pnl", depth)) : -1;
-    k_nd_panel<<<lv.count, 256, psmem, c->stream>>>(F, lv.f, lv.s, k, nb, perm,
-                                                    (double*)S.cbuf.p, (double*)S.pinv.p,
-                                                    (int32_t*)S.swaps.p, err);
+    if (big)
+      k_nd_panel_big<<<lv.count, 256, 0, c->stream>>>(F, lv.f, lv.s, k, nb, perm,
+                                                      (double*)S.cbuf.p, (double*)S.pinv.p,
+                                                      (int32_t*)S.swaps.p, err,
+                                                      (float*)S.pscratch.p);
+    else
+      k_nd_panel<<<lv.count, 256, 0, c->stream>>>(F, lv.f, lv.s, k, nb, perm,
+                                                  (double*)S.cbuf.p, (double*)S.pinv.p,
+                                                  (int32_t*)S.swaps.p, err);
     timer_end(c, t1);
     const int t2 = c->timing ? timer_begin(c, level_name("nd_row", depth)) : -1;
     k_nd_rowblock<<<dim3(tiles_w + tiles_c, lv.count), kRowThreads, 0, c->stream>>>(

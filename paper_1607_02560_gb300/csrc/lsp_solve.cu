@@ -87,7 +87,7 @@ void nd_free(NdState* s) {
   if (!s) return;
   DevBuf* bufs[] = {&s->fronts, &s->E, &s->R, &s->inv, &s->asm_dst, &s->asm_src, &s->perm,
                     &s->z, &s->u, &s->cbuf, &s->pinv, &s->swaps, &s->err, &s->V, &s->w,
-                    &s->b, &s->x, &s->tmp, &s->gs, &s->fvec, &s->ry, &s->rd};
+                    &s->b, &s->x, &s->tmp, &s->gs, &s->fvec, &s->ry, &s->rd, &s->pscratch};
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (s->h_gs) cudaFreeHost(s->h_gs);
@@ -118,8 +118,8 @@ lsp_status lsp_nd_factor(lsp_ctx* c, const lsp_nd_opts* opts) {
   if (!c) return LSP_ERR_ARG;
   cudaGetLastError();
   if (!c->built) return sfail(c, LSP_ERR_STATE, "nd_factor before build_stencils");
-  if (c->geo.d != 2)
-    return sfail(c, LSP_ERR_UNSUPPORTED, "the nested dissection is built for 2D grids");
+  if (c->geo.d == 1)
+    return sfail(c, LSP_ERR_UNSUPPORTED, "the nested dissection is built for 2D and 3D grids");
   int leaf = opts && opts->leaf ? opts->leaf : (c->t_built == 2 ? c->leaf_built : 8);
   if (leaf <= 0) leaf = 8;
   if (leaf < 4 || (leaf & (leaf - 1)) || leaf > c->geo.n)
@@ -133,12 +133,14 @@ lsp_status lsp_nd_factor(lsp_ctx* c, const lsp_nd_opts* opts) {
   NdState& S = *c->nd;
   const int mu = rows_mu(c);
   const NdPlan& P0 = S.plan;
-  if (!S.have_plan || P0.n != c->geo.n || P0.leaf != leaf || P0.t_built != c->t_built ||
+  if (!S.have_plan || P0.d != c->geo.d || P0.n != c->geo.n || P0.leaf != leaf ||
+      P0.t_built != c->t_built ||
       P0.leaf_t != (c->t_built == 2 ? c->leaf_built : 0) || P0.mu != mu) {
     S.have_plan = false;
     S.factored = false;
     const std::string why =
-        build_nd_plan(S.plan, c->geo.n, leaf, c->t_built, c->t_built == 2 ? c->leaf_built : 0, mu);
+        build_nd_plan(S.plan, c->geo.d, c->geo.n, leaf, c->t_built,
+                      c->t_built == 2 ? c->leaf_built : 0, mu);
     if (!why.empty()) return sfail(c, LSP_ERR_UNSUPPORTED, "nested dissection: %s", why.c_str());
     lsp_status st;
     if ((st = upload(c, S.E, S.plan.E)) != LSP_OK) return st;
@@ -147,16 +149,19 @@ lsp_status lsp_nd_factor(lsp_ctx* c, const lsp_nd_opts* opts) {
     if ((st = upload(c, S.asm_dst, S.plan.asm_dst)) != LSP_OK) return st;
     if ((st = upload(c, S.asm_src, S.plan.asm_src)) != LSP_OK) return st;
     const NdPlan& P = S.plan;
-    int64_t cb = 1, pv = 1, sw = 1;
+    int64_t cb = 1, pv = 1, sw = 1, ps = 0;
     int max_sr = 1;
     for (const NdLevel& lv : P.lv) {
       if (lv.f > kNdSmallFront) {
         cb = std::max(cb, (int64_t)lv.count * lv.f * kNdPanel);
         pv = std::max(pv, (int64_t)lv.count * kNdPanel * kNdPanel);
         sw = std::max(sw, (int64_t)lv.count * (1 + 4 * kNdPanel));
+        if (lv.s > kNdPanelRegRows) ps = std::max(ps, (int64_t)lv.count * lv.s * (kNdPanel + 1));
       }
       max_sr = std::max(max_sr, std::max(lv.s, lv.r));
     }
+    if (ps > 0 && !ensure(c, S.pscratch, sizeof(float) * ps))
+      return sfail(c, LSP_ERR_OOM, "nested dissection buffers: %s", c->err.c_str());
     if (!ensure(c, S.fronts, sizeof(double) * P.front_doubles) ||
         !ensure(c, S.perm, sizeof(int32_t) * P.perm_ints) ||
         !ensure(c, S.z, sizeof(double) * P.z_doubles) ||
@@ -202,12 +207,14 @@ static void fill_info(const NdPlan& P, lsp_nd_info* info) {
   info->flops_lu = P.flops_lu;
 }
 
-lsp_status lsp_nd_plan_info(int n, int leaf, int t, int nd_leaf, lsp_nd_info* info, int cap,
-                            int* count, int* s, int* r, char* err, int errcap) {
+lsp_status lsp_nd_plan_info(int d, int n, int leaf, int t, int nd_leaf, lsp_nd_info* info,
+                            int cap, int* count, int* s, int* r, char* err, int errcap) {
   if (err && errcap > 0) err[0] = 0;
-  if (!info || (t != 1 && t != 2) || cap < 0) return LSP_ERR_ARG;
+  if (!info || (t != 1 && t != 2) || (d != 2 && d != 3) || cap < 0) return LSP_ERR_ARG;
   NdPlan P;
-  const std::string why = build_nd_plan(P, n, leaf, t, t == 2 ? nd_leaf : 0, t == 2 ? 25 : 9);
+  const int w = 2 * t + 1;
+  const std::string why =
+      build_nd_plan(P, d, n, leaf, t, t == 2 ? nd_leaf : 0, d == 2 ? w * w : w * w * w);
   if (!why.empty()) {
     if (err && errcap > 0) snprintf(err, (size_t)errcap, "%s", why.c_str());
     return LSP_ERR_UNSUPPORTED;

@@ -30,7 +30,9 @@ namespace lsp {
 
 constexpr int kNdPanel = 16;       // columns eliminated per step in the blocked path
 constexpr int kNdSmallFront = 160; // fronts with f <= this are swept in shared memory
-constexpr int kNdMaxN = 1024;      // the FP32 pivot panel of the cross (2n - 1 rows) fits in shared memory
+constexpr int kNdMaxN = 1024;      // 2D: the cross has 2n - 1 points
+constexpr int kNdMaxN3 = 64;       // 3D: the root planes have 3n^2 - 3n + 1 points (12 097 at 64)
+constexpr int kNdPanelRegRows = 8 * 256;  // panels up to this many rows keep them in registers
 
 struct NdLevel {
   int count = 0;       // fronts at this depth
@@ -45,7 +47,7 @@ struct NdLevel {
 };
 
 struct NdPlan {
-  int n = 0, leaf = 0, mu = 0, t_built = 1, leaf_t = 0;
+  int d = 2, n = 0, leaf = 0, mu = 0, t_built = 1, leaf_t = 0;
   std::vector<NdLevel> lv;  // lv[0]: the cross; lv.back(): the leaves
   // E, R: grid indices of every front's eliminated set and ring, front after front.
   // inv[(front * f + i) * 2 + c]: position of front position i in child c's ring, or -1.
@@ -55,13 +57,13 @@ struct NdPlan {
   double flops_sweep = 0;  // FP64 flops of the partial inversions, 2 s f^2 per front
   double flops_lu = 0;     // multifrontal LU count, 2/3 s^3 + 2 s^2 r + 2 s r^2 per front
   int64_t solve_bytes = 0; // front bytes one solve reads: (f s + s r) * 8 per front
-  int max_f = 0;
+  int max_f = 0, max_s = 0;
 };
 
-// Builds the plan for rows of width mu (t_built = 1: 3 x 3 rows; t_built = 2: 5 x 5 rows, of
-// which point j uses its t_j x t_j core from the leaf-leaf_t rule). Returns "" or the reason
-// the rows or sizes do not fit the dissection.
-std::string build_nd_plan(NdPlan& p, int n, int leaf, int t_built, int leaf_t, int mu);
+// Builds the plan for rows of width mu on the periodic n^d grid (d = 2, 3; t_built = 1: 3^d
+// rows; t_built = 2, 2D only: 5 x 5 rows, of which point j uses its core from the leaf-leaf_t
+// rule). Returns "" or the reason the rows or sizes do not fit the dissection.
+std::string build_nd_plan(NdPlan& p, int d, int n, int leaf, int t_built, int leaf_t, int mu);
 
 struct NdState {
   NdPlan plan;
@@ -71,6 +73,7 @@ struct NdState {
   int refine_steps = 0;       // iterative-refinement steps after every solve
   DevBuf fronts, E, R, inv, asm_dst, asm_src, perm, z, u, cbuf, pinv, swaps, err;
   DevBuf ry, rd;              // refinement scratch: a copy of y, the correction
+  DevBuf pscratch;            // FP32 pivot-ranking rows of panels over 2048 rows
   // GMRES workspace
   DevBuf V, w, b, x, tmp, gs, fvec;
   double* h_gs = nullptr;  // pinned mirror of the scalars the host loop reads

@@ -1,6 +1,7 @@
-// Host planner of the nested dissection of the periodic 2D grid (Sec. 3, Fig. nd; Sec. 4.2):
-// the elimination tree, each front's index sets, the child-to-parent maps and the list of P's
-// entries assembled into each front. Pure host code; the numeric phases are in k_nd.cu.
+// Host planner of the nested dissection of the periodic 2D or 3D grid (Sec. 3, Fig. nd;
+// Sec. 4.2; Table cost): the elimination tree, each front's index sets, the child-to-parent
+// maps and the list of P's entries assembled into each front. Pure host code; the numeric
+// phases are in k_nd.cu.
 #include <algorithm>
 #include <cstring>
 
@@ -10,7 +11,7 @@ namespace lsp {
 namespace {
 
 struct Box {
-  int i0, j0, h, w;  // rows [i0, i0 + h), columns [j0, j0 + w), inside [1, n)^2
+  int lo[3], len[3];  // points lo[a] .. lo[a] + len[a] - 1 on axis a, inside [1, n)^d
   bool cross;
 };
 
@@ -34,44 +35,77 @@ inline int t_point(int x0, int x1, int L) {
 
 }  // namespace
 
-std::string build_nd_plan(NdPlan& P, int n, int leaf, int t_built, int leaf_t, int mu) {
+std::string build_nd_plan(NdPlan& P, int d, int n, int leaf, int t_built, int leaf_t, int mu) {
   P = NdPlan();
+  if (d != 2 && d != 3) return "the dissection is built for 2D and 3D grids";
   if (n < 4 || (n & (n - 1))) return "the dissection needs n a power of two >= 4";
   if (leaf < 4 || (leaf & (leaf - 1)) || leaf > n)
     return "the leaf width b must be a power of two with 4 <= b <= n";
+  if (d == 3 && t_built != 1) return "3D rows must be t = 1 rows";
   if (t_built == 2 && leaf_t <= 0)
     return "t = 2 rows at every point cross the separators: build with nd_leaf = b";
   if (t_built == 2 && leaf_t != leaf)
     return "the leaf width b must equal the nd_leaf of the multi-t build";
-  if ((t_built == 1 && mu != 9) || (t_built == 2 && mu != 25)) return "unexpected row width";
+  const int w1 = 2 * t_built + 1;
+  if (mu != (d == 2 ? w1 * w1 : w1 * w1 * w1)) return "unexpected row width";
   if (t_built == 2 && n < 8) return "t = 2 rows need n >= 8";
-  if (n > kNdMaxN) return "the dissection is built for n <= 1024";
+  if (d == 2 && n > kNdMaxN) return "the dissection is built for n <= 1024 in 2D";
+  if (d == 3 && n > kNdMaxN3) return "the dissection is built for n <= 64 in 3D";
+  P.d = d;
   P.n = n;
   P.leaf = leaf;
   P.mu = mu;
   P.t_built = t_built;
   P.leaf_t = leaf_t;
-  const int64_t N = (int64_t)n * n;
+  const int64_t N = d == 2 ? (int64_t)n * n : (int64_t)n * n * n;
+  auto gidx = [&](const int* x) -> int32_t {
+    int64_t g = 0;
+    for (int a = 0; a < d; ++a) g = g * n + wrapi(x[a], n);
+    return (int32_t)g;
+  };
+  auto coords = [&](int64_t g, int* x) {
+    for (int a = d - 1; a >= 0; --a) {
+      x[a] = (int)(g % n);
+      g /= n;
+    }
+  };
 
-  // ---- the tree, breadth first: children of front k at depth d are 2k, 2k+1 at depth d+1
+  // ---- the tree, breadth first: children of front k at depth e are 2k, 2k+1 at depth e+1.
+  // A box is split through the middle plane of its longest side (the first such axis).
   std::vector<std::vector<Box>> boxes;
-  boxes.push_back({Box{0, 0, 0, 0, true}});
-  boxes.push_back({Box{1, 1, n - 1, n - 1, false}});
-  while (true) {
-    const Box& b0 = boxes.back()[0];
-    if (b0.h <= leaf - 1 && b0.w <= leaf - 1) break;
+  {
+    Box cross{};
+    cross.cross = true;
+    boxes.push_back({cross});
+    Box root{};
+    for (int a = 0; a < d; ++a) {
+      root.lo[a] = 1;
+      root.len[a] = n - 1;
+    }
+    boxes.push_back({root});
+  }
+  auto is_leaf_box = [&](const Box& b) {
+    for (int a = 0; a < d; ++a)
+      if (b.len[a] > leaf - 1) return false;
+    return true;
+  };
+  auto split_axis = [&](const Box& b) {
+    int ax = 0;
+    for (int a = 1; a < d; ++a)
+      if (b.len[a] > b.len[ax]) ax = a;
+    return ax;
+  };
+  while (!is_leaf_box(boxes.back()[0])) {
     std::vector<Box> next;
     next.reserve(boxes.back().size() * 2);
     for (const Box& b : boxes.back()) {
-      if (b.w >= b.h) {
-        const int hw = (b.w - 1) / 2;
-        next.push_back({b.i0, b.j0, b.h, hw, false});
-        next.push_back({b.i0, b.j0 + hw + 1, b.h, hw, false});
-      } else {
-        const int hh = (b.h - 1) / 2;
-        next.push_back({b.i0, b.j0, hh, b.w, false});
-        next.push_back({b.i0 + hh + 1, b.j0, hh, b.w, false});
-      }
+      const int ax = split_axis(b), half = (b.len[ax] - 1) / 2;
+      Box c0 = b, c1 = b;
+      c0.len[ax] = half;
+      c1.len[ax] = half;
+      c1.lo[ax] = b.lo[ax] + half + 1;
+      next.push_back(c0);
+      next.push_back(c1);
     }
     boxes.push_back(std::move(next));
   }
@@ -80,54 +114,72 @@ std::string build_nd_plan(NdPlan& P, int n, int leaf, int t_built, int leaf_t, i
 
   std::vector<int32_t> stamp(N, -1);
   int32_t tag = 0;
+  // points of the box [lo, lo + len) in lexicographic order, optionally only the plane x_ax = c
+  auto for_box = [&](const int* lo, const int* len, auto&& fn) {
+    int x[3] = {0, 0, 0};
+    const int l2 = d == 3 ? len[2] : 1;
+    for (int i = 0; i < len[0]; ++i)
+      for (int j = 0; j < len[1]; ++j)
+        for (int m = 0; m < l2; ++m) {
+          x[0] = lo[0] + i;
+          x[1] = lo[1] + j;
+          if (d == 3) x[2] = lo[2] + m;
+          fn(x);
+        }
+  };
   auto E_of = [&](const Box& b, bool is_leaf, std::vector<int32_t>& out) {
-    if (b.cross) {
-      for (int j = 0; j < n; ++j) out.push_back(j);
-      for (int i = 1; i < n; ++i) out.push_back(i * n);
+    if (b.cross) {  // every point with a zero coordinate, lexicographic
+      int x[3];
+      for (int64_t g = 0; g < N; ++g) {
+        coords(g, x);
+        bool on = false;
+        for (int a = 0; a < d; ++a) on = on || x[a] == 0;
+        if (on) out.push_back((int32_t)g);
+      }
     } else if (is_leaf) {
-      for (int i = b.i0; i < b.i0 + b.h; ++i)
-        for (int j = b.j0; j < b.j0 + b.w; ++j) out.push_back(i * n + j);
-    } else if (b.w >= b.h) {
-      const int jm = b.j0 + (b.w - 1) / 2;
-      for (int i = b.i0; i < b.i0 + b.h; ++i) out.push_back(i * n + jm);
+      for_box(b.lo, b.len, [&](const int* x) { out.push_back(gidx(x)); });
     } else {
-      const int im = b.i0 + (b.h - 1) / 2;
-      for (int j = b.j0; j < b.j0 + b.w; ++j) out.push_back(im * n + j);
+      const int ax = split_axis(b);
+      int lo[3] = {b.lo[0], b.lo[1], d == 3 ? b.lo[2] : 0};
+      int len[3] = {b.len[0], b.len[1], d == 3 ? b.len[2] : 1};
+      lo[ax] = b.lo[ax] + (b.len[ax] - 1) / 2;
+      len[ax] = 1;
+      for_box(lo, len, [&](const int* x) { out.push_back(gidx(x)); });
     }
   };
-  // the ring of a box in row-major order of its bounding rectangle, wrapped, first copy kept
+  // the ring of a box: the points of its enlarged box [lo - 1, lo + len] outside it, wrapped,
+  // in lexicographic order of the enlarged box, first copy kept
   auto R_of = [&](const Box& b, std::vector<int32_t>& out) {
     if (b.cross) return;
     ++tag;
-    auto add = [&](int i, int j) {
-      const int g = wrapi(i, n) * n + wrapi(j, n);
+    int lo[3] = {b.lo[0] - 1, b.lo[1] - 1, d == 3 ? b.lo[2] - 1 : 0};
+    int len[3] = {b.len[0] + 2, b.len[1] + 2, d == 3 ? b.len[2] + 2 : 1};
+    for_box(lo, len, [&](const int* x) {
+      bool inside = true;
+      for (int a = 0; a < d; ++a) inside = inside && x[a] >= b.lo[a] && x[a] < b.lo[a] + b.len[a];
+      if (inside) return;
+      const int32_t g = gidx(x);
       if (stamp[g] == tag) return;
       stamp[g] = tag;
       out.push_back(g);
-    };
-    for (int j = b.j0 - 1; j <= b.j0 + b.w; ++j) add(b.i0 - 1, j);
-    for (int i = b.i0; i < b.i0 + b.h; ++i) {
-      add(i, b.j0 - 1);
-      add(i, b.j0 + b.w);
-    }
-    for (int j = b.j0 - 1; j <= b.j0 + b.w; ++j) add(b.i0 + b.h, j);
+    });
   };
 
-  // ---- index sets, level by level
+  // ---- index sets, depth by depth
   int64_t front_off = 0, perm_off = 0, z_off = 0, u_off = 0, inv_off = 0;
   std::vector<int32_t> e_tmp, r_tmp;
-  for (int d = 0; d < L; ++d) {
-    NdLevel& lv = P.lv[d];
-    const bool is_leaf = d == L - 1;
-    lv.count = (int)boxes[d].size();
-    lv.nchild = is_leaf ? 0 : (d == 0 ? 1 : 2);
+  for (int e = 0; e < L; ++e) {
+    NdLevel& lv = P.lv[e];
+    const bool is_leaf = e == L - 1;
+    lv.count = (int)boxes[e].size();
+    lv.nchild = is_leaf ? 0 : (e == 0 ? 1 : 2);
     lv.E_off = (int64_t)P.E.size();
     lv.R_off = (int64_t)P.R.size();
     for (int k = 0; k < lv.count; ++k) {
       e_tmp.clear();
       r_tmp.clear();
-      E_of(boxes[d][k], is_leaf, e_tmp);
-      R_of(boxes[d][k], r_tmp);
+      E_of(boxes[e][k], is_leaf, e_tmp);
+      R_of(boxes[e][k], r_tmp);
       if (k == 0) {
         lv.s = (int)e_tmp.size();
         lv.r = (int)r_tmp.size();
@@ -155,6 +207,7 @@ std::string build_nd_plan(NdPlan& P, int n, int leaf, int t_built, int leaf_t, i
     P.flops_lu += lv.count * (2.0 / 3.0 * s * s * s + 2.0 * s * s * r + 2.0 * s * r * r);
     P.solve_bytes += (int64_t)lv.count * ((int64_t)lv.f * lv.s + (int64_t)lv.s * lv.r) * 8;
     P.max_f = std::max(P.max_f, lv.f);
+    P.max_s = std::max(P.max_s, lv.s);
   }
   P.front_doubles = front_off;
   P.perm_ints = perm_off;
@@ -165,64 +218,87 @@ std::string build_nd_plan(NdPlan& P, int n, int leaf, int t_built, int leaf_t, i
 
   // ---- assembly lists and child maps
   const int tmax = t_built;
-  auto t_of = [&](int g) { return t_built == 1 ? 1 : t_point(g / n, g % n, leaf_t); };
-  auto a_of = [&](int o0, int o1) {
-    const int w = 2 * t_built + 1;
-    return (o0 + t_built) * w + (o1 + t_built);
+  auto t_of = [&](int32_t g) {
+    if (t_built == 1) return 1;
+    int x[3];
+    coords(g, x);
+    return t_point(x[0], x[1], leaf_t);
   };
+  // offset index in the lexicographic list of [-t_built, t_built]^d (last axis fastest)
+  auto a_of = [&](const int* o) {
+    int a = 0;
+    for (int q = 0; q < d; ++q) a = a * w1 + (o[q] + t_built);
+    return a;
+  };
+  const int nofs = d == 2 ? (2 * tmax + 1) * (2 * tmax + 1)
+                          : (2 * tmax + 1) * (2 * tmax + 1) * (2 * tmax + 1);
   std::vector<int32_t> where(N, -1);
   int64_t emitted = 0;
-  for (int d = 0; d < L; ++d) {
-    NdLevel& lv = P.lv[d];
+  for (int e = 0; e < L; ++e) {
+    NdLevel& lv = P.lv[e];
     lv.asm_off = (int64_t)P.asm_dst.size();
     for (int k = 0; k < lv.count; ++k) {
-      const Box& bx = boxes[d][k];
+      const Box& bx = boxes[e][k];
       const int32_t* Ek = P.E.data() + lv.E_off + (int64_t)k * lv.s;
       const int32_t* Rk = P.R.data() + lv.R_off + (int64_t)k * lv.r;
-      for (int e = 0; e < lv.s; ++e) where[Ek[e]] = e;
+      for (int q = 0; q < lv.s; ++q) where[Ek[q]] = q;
       for (int a = 0; a < lv.r; ++a) where[Rk[a]] = lv.s + a;
       // a point eliminated in this front's subtree before it (inside its box, off E)
-      auto descendant = [&](int g) {
-        if (bx.cross) return where[g] < 0;
-        const int i = g / n, j = g % n;
-        return i >= bx.i0 && i < bx.i0 + bx.h && j >= bx.j0 && j < bx.j0 + bx.w &&
-               where[g] < 0;
+      auto descendant = [&](int32_t g) {
+        if (where[g] >= 0) return false;
+        if (bx.cross) return true;
+        int x[3];
+        coords(g, x);
+        for (int a = 0; a < d; ++a)
+          if (x[a] < bx.lo[a] || x[a] >= bx.lo[a] + bx.len[a]) return false;
+        return true;
       };
       const int64_t base = (int64_t)k * lv.f * lv.f;
-      for (int e = 0; e < lv.s; ++e) {
-        const int g = Ek[e];
-        const int gi = g / n, gj = g % n;
-        // row g of P: entries (g, q) with q in the front
+      for (int q = 0; q < lv.s; ++q) {
+        const int32_t g = Ek[q];
+        int xg[3];
+        coords(g, xg);
         const int tg = t_of(g);
-        for (int o0 = -tg; o0 <= tg; ++o0)
-          for (int o1 = -tg; o1 <= tg; ++o1) {
-            const int q = wrapi(gi + o0, n) * n + wrapi(gj + o1, n);
-            if (where[q] >= 0) {
-              P.asm_dst.push_back((int32_t)(base + (int64_t)e * lv.f + where[q]));
-              P.asm_src.push_back((int32_t)((int64_t)g * mu + a_of(o0, o1)));
+        for (int ao = 0; ao < nofs; ++ao) {
+          int o[3] = {0, 0, 0}, rem = ao;
+          for (int c = d - 1; c >= 0; --c) {
+            o[c] = rem % (2 * tmax + 1) - tmax;
+            rem /= 2 * tmax + 1;
+          }
+          bool in_t = true;
+          for (int c = 0; c < d; ++c) in_t = in_t && std::abs(o[c]) <= tg;
+          int xo[3];
+          // row g of P: entry (g, g + o)
+          if (in_t) {
+            for (int c = 0; c < d; ++c) xo[c] = xg[c] + o[c];
+            const int32_t h = gidx(xo);
+            if (where[h] >= 0) {
+              P.asm_dst.push_back((int32_t)(base + (int64_t)q * lv.f + where[h]));
+              P.asm_src.push_back((int32_t)((int64_t)g * mu + a_of(o)));
               ++emitted;
-            } else if (!descendant(q)) {
+            } else if (!descendant(h)) {
               return "the rows cross a separator of the dissection";
             }
           }
-        // column g of P: entries (q, g) of ring rows q
-        for (int o0 = -tmax; o0 <= tmax; ++o0)
-          for (int o1 = -tmax; o1 <= tmax; ++o1) {
-            const int q = wrapi(gi - o0, n) * n + wrapi(gj - o1, n);
-            const int tq = t_of(q);
-            if (std::abs(o0) > tq || std::abs(o1) > tq) continue;
-            if (where[q] >= lv.s) {
-              P.asm_dst.push_back((int32_t)(base + (int64_t)where[q] * lv.f + e));
-              P.asm_src.push_back((int32_t)((int64_t)q * mu + a_of(o0, o1)));
-              ++emitted;
-            } else if (where[q] < 0 && !descendant(q)) {
-              return "the rows cross a separator of the dissection";
-            }
+          // column g of P: entry (g - o, g) of a ring row g - o whose pattern holds o
+          for (int c = 0; c < d; ++c) xo[c] = xg[c] - o[c];
+          const int32_t h = gidx(xo);
+          const int th = t_of(h);
+          bool in_th = true;
+          for (int c = 0; c < d; ++c) in_th = in_th && std::abs(o[c]) <= th;
+          if (!in_th) continue;
+          if (where[h] >= lv.s) {
+            P.asm_dst.push_back((int32_t)(base + (int64_t)where[h] * lv.f + q));
+            P.asm_src.push_back((int32_t)((int64_t)h * mu + a_of(o)));
+            ++emitted;
+          } else if (where[h] < 0 && !descendant(h)) {
+            return "the rows cross a separator of the dissection";
           }
+        }
       }
       // child ring positions inside this front
       for (int cix = 0; cix < lv.nchild; ++cix) {
-        const NdLevel& cl = P.lv[d + 1];
+        const NdLevel& cl = P.lv[e + 1];
         const int child = lv.nchild == 1 ? k : 2 * k + cix;
         const int32_t* Rc = P.R.data() + cl.R_off + (int64_t)child * cl.r;
         int32_t* inv = P.inv.data() + lv.inv_off + (int64_t)k * lv.f * 2;
@@ -233,7 +309,7 @@ std::string build_nd_plan(NdPlan& P, int n, int leaf, int t_built, int leaf_t, i
           inv[pos * 2 + cix] = a;
         }
       }
-      for (int e = 0; e < lv.s; ++e) where[Ek[e]] = -1;
+      for (int q = 0; q < lv.s; ++q) where[Ek[q]] = -1;
       for (int a = 0; a < lv.r; ++a) where[Rk[a]] = -1;
     }
     lv.asm_n = (int64_t)P.asm_dst.size() - lv.asm_off;
@@ -241,8 +317,10 @@ std::string build_nd_plan(NdPlan& P, int n, int leaf, int t_built, int leaf_t, i
   // every structural entry of P assembled exactly once
   int64_t structural = 0;
   for (int64_t g = 0; g < N; ++g) {
-    const int tg = t_of((int)g);
-    structural += (2 * tg + 1) * (2 * tg + 1);
+    const int tg = t_of((int32_t)g);
+    int64_t c = 1;
+    for (int a = 0; a < d; ++a) c *= 2 * tg + 1;
+    structural += c;
   }
   if (emitted != structural) return "internal: P's entries are not assembled exactly once";
   return "";

@@ -120,8 +120,9 @@ def lib() -> ctypes.CDLL:
         "lsp_nd_factor": (ctypes.c_int, [vp, ctypes.POINTER(NdOpts)]),
         "lsp_nd_get_info": (ctypes.c_int, [vp, ctypes.POINTER(NdInfo)]),
         "lsp_nd_plan_info": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                             ctypes.c_int, ctypes.POINTER(NdInfo), ctypes.c_int,
-                                             vp, vp, vp, ctypes.c_char_p, ctypes.c_int]),
+                                             ctypes.c_int, ctypes.c_int, ctypes.POINTER(NdInfo),
+                                             ctypes.c_int, vp, vp, vp, ctypes.c_char_p,
+                                             ctypes.c_int]),
         "lsp_nd_solve": (ctypes.c_int, [vp, vp, vp]),
         "lsp_apply_rows": (ctypes.c_int, [vp, ctypes.c_char, vp, vp]),
         "lsp_default_gmres_opts": (None, [ctypes.POINTER(GmresOpts)]),
@@ -174,16 +175,16 @@ def apply_operator_noalloc(d: int, n: int, v, u, y, stream=None) -> None:
         raise LspError(st, f"lsp_apply_operator_noalloc(d={d}, n={n}) failed")
 
 
-def nd_plan_info(n: int, leaf: int = 8, t: int = 1, nd_leaf: int = 0) -> dict:
+def nd_plan_info(n: int, leaf: int = 8, t: int = 1, nd_leaf: int = 0, d: int = 2) -> dict:
     """Host-only plan of the nested dissection (lsp_nd_plan_info): sizes, flop counts and the
-    (count, |E|, |R|) of every depth, depth 0 being the cross."""
+    (count, |E|, |R|) of every depth, depth 0 being the root separator."""
     info = NdInfo()
     cap = 64
     cnt = np.zeros(cap, dtype=np.int32)
     s = np.zeros(cap, dtype=np.int32)
     r = np.zeros(cap, dtype=np.int32)
     err = ctypes.create_string_buffer(256)
-    st = lib().lsp_nd_plan_info(n, leaf, t, nd_leaf, ctypes.byref(info), cap, _ptr(cnt),
+    st = lib().lsp_nd_plan_info(d, n, leaf, t, nd_leaf, ctypes.byref(info), cap, _ptr(cnt),
                                 _ptr(s), _ptr(r), err, 256)
     if st != LSP_OK:
         raise LspError(st, err.value.decode())

@@ -73,3 +73,30 @@ def test_cost_grows_like_n_cubed():
 def test_plans_that_do_not_fit_are_refused(args, msg):
     with pytest.raises(lsp.LspError, match=msg):
         lsp.nd_plan_info(*args)
+
+
+def test_3d_n8_leaf4_by_hand():
+    # root: the points with a zero coordinate, 8^3 - 7^3 = 169; root box 7^3 split by its middle
+    # plane x_0 = 4: 49 points, ring = all 169 root points; boxes 3 x 7 x 7 split by x_1 = 4:
+    # 21 points, ring 5 * 8 * 8 - 147 = 173 (the enlarged box wraps in x_1 and x_2); boxes
+    # 3 x 3 x 7 split by x_2 = 4: 9 points, ring 5 * 5 * 8 - 63 = 137; leaves 3^3, ring 5^3 - 27
+    info = lsp.nd_plan_info(8, 4, d=3)
+    assert info["depths"] == [(1, 169, 0), (1, 49, 169), (2, 21, 173), (4, 9, 137), (8, 27, 98)]
+
+
+@pytest.mark.parametrize("n,leaf", [(8, 4), (16, 8), (32, 4)])
+def test_3d_every_point_is_eliminated_once(n, leaf):
+    info = lsp.nd_plan_info(n, leaf, d=3)
+    depths = info["depths"]
+    assert sum(c * s for c, s, _ in depths) == n ** 3
+    assert depths[0] == (1, n ** 3 - (n - 1) ** 3, 0)
+    assert depths[-1][1] == (leaf - 1) ** 3
+    sweep = sum(c * 2.0 * s * (s + r) ** 2 for c, s, r in depths)
+    assert info["flops"] == pytest.approx(sweep, rel=1e-12)
+
+
+def test_3d_limits():
+    with pytest.raises(lsp.LspError, match="n <= 64"):
+        lsp.nd_plan_info(128, 8, d=3)
+    with pytest.raises(lsp.LspError, match="t = 1"):
+        lsp.nd_plan_info(16, 8, t=2, nd_leaf=8, d=3)
