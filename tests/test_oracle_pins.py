@@ -105,7 +105,8 @@ def test_kernel_vector_matches_direct_sum(n, d, m):
 
 @pytest.mark.parametrize("n,d,m,t", [(8, 2, -8, 1), (10, 2, -12, 1), (12, 2, -18, 1),
                                      (8, 2, 3, 1), (6, 3, -5, 1), (8, 3, -9, 1),
-                                     (10, 2, -12, 2), (12, 2, -18, 2), (12, 2, 3, 2)])
+                                     (10, 2, -12, 2), (12, 2, -18, 2), (12, 2, 3, 2),
+                                     (10, 3, -14, 2), (12, 3, -20, 2)])
 def test_gram_identity_and_svd_match_dense(n, d, m, t):
     s = float(O.shift_value(m))
     st = O.stencil_for_shift(n, d, s, t)
