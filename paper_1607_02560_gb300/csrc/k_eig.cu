@@ -1542,7 +1542,10 @@ cudaError_t launch_eig_t(lsp_ctx* c, const int32_t* count, int64_t cap, int meth
 }  // namespace
 
 cudaError_t upload_sym(lsp_ctx* c) {
-  cudaError_t e = cudaMemcpyToSymbol(c_cls, c->geo.cls_of, sizeof(c->geo.cls_of));
+  uint8_t cls[kMaxMu][kMaxMu];  // the t = 1 classes (the geometry holds up to 125 offsets)
+  for (int a = 0; a < kMaxMu; ++a)
+    for (int b = 0; b < kMaxMu; ++b) cls[a][b] = c->geo.cls_of[a][b];
+  cudaError_t e = cudaMemcpyToSymbol(c_cls, cls, sizeof cls);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(c_sym, &c->sym, sizeof(SymBasis));
   if (e != cudaSuccess) return e;

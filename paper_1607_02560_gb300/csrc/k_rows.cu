@@ -127,22 +127,61 @@ __global__ void __launch_bounds__(kThreads) k_colidx(int64_t N, int logn, int32_
     rowptr[j] = j * MU;
 }
 
-// ---- t = 2 rows (2D): 25 columns per point in the lexicographic 5 x 5 offset order ---------
-// t_j at point j = (x0, x1): 2 without a leaf; else min(2, min_a f(x_a mod leaf)) with
-// f(0) = leaf, f(r) = min(r, leaf - r): the largest t whose neighbourhood crosses no separator
-// line of a nested dissection with leaf boxes of width `leaf` (Sec. 4.2).
-__device__ __forceinline__ int t_of_point(int64_t x0, int64_t x1, int leaf) {
+// ---- t = 2 rows (2D and 3D): 5^d columns per point in the lexicographic offset order ------
+// t_j at a point: 2 without a leaf; else min(2, min_a f(x_a mod leaf)) with f(0) = leaf,
+// f(r) = min(r, leaf - r): the largest t whose neighbourhood crosses no separator line (plane)
+// of a nested dissection with leaf boxes of width `leaf` (Sec. 4.2).
+template <int D>
+__device__ __forceinline__ int t_of_point(const int64_t* x, int leaf) {
   if (leaf <= 0) return 2;
   int t = 2;
-  const int r0 = (int)(x0 % leaf), r1 = (int)(x1 % leaf);
-  t = min(t, r0 == 0 ? leaf : min(r0, leaf - r0));
-  t = min(t, r1 == 0 ? leaf : min(r1, leaf - r1));
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const int r = (int)(x[a] % leaf);
+    t = min(t, r == 0 ? leaf : min(r, leaf - r));
+  }
   return t;
 }
 
-// A t_j = 2 point writes alpha2/c2 of its shift in all 25 columns; a t_j = 1 point writes
-// alpha/c of the 3 x 3 stencil in the inner columns (|o_a| <= 1) and zeros in the outer ring.
-template <bool LOCAL>
+template <int D>
+__device__ __forceinline__ void coords_of(int64_t j, int logn, int64_t mask, int64_t* x) {
+#pragma unroll
+  for (int a = D - 1; a >= 0; --a) {
+    x[a] = j & mask;
+    j >>= logn;
+  }
+}
+
+// offsets of the o-th column of a 5^D row, and the index of the same offset in a 3^D row (or
+// -1 when it lies outside [-1, 1]^D)
+template <int D>
+__device__ __forceinline__ int decode5(int o, int* off) {
+  int inner = 0, in3 = 1;
+#pragma unroll
+  for (int a = D - 1; a >= 0; --a) {
+    off[a] = o % 5 - 2;
+    o /= 5;
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    in3 = in3 && off[a] >= -1 && off[a] <= 1;
+    inner = inner * 3 + (off[a] + 1);
+  }
+  return in3 ? inner : -1;
+}
+
+template <int D>
+__device__ __forceinline__ int64_t wrap_index(const int64_t* x, const int* off, int logn,
+                                              int64_t mask) {
+  int64_t g = 0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) g = (g << logn) | ((x[a] + off[a]) & mask);
+  return g;
+}
+
+// A t_j = 2 point writes alpha2/c2 of its shift in all 5^D columns; a t_j = 1 point writes
+// alpha/c of the 3^D stencil in the inner columns (|o_a| <= 1) and zeros elsewhere.
+template <int D, bool LOCAL>
 __global__ void __launch_bounds__(kThreads) k_rows_t2(
     const double* __restrict__ v, int64_t N, int logn, int leaf,
     const int32_t* __restrict__ idx_of, int64_t mlo, int64_t R, int32_t* __restrict__ err,
@@ -150,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_t2(
     const double* __restrict__ alpha1, const double* __restrict__ c1,
     const double* __restrict__ alpha2, const double* __restrict__ c2, double* __restrict__ Q,
     double* __restrict__ C, double* __restrict__ P) {
-  constexpr int MU = 25;
+  constexpr int MU = D == 2 ? 25 : 125, MU1 = D == 2 ? 9 : 27;
   __shared__ int s_idx[kThreads];
   __shared__ int s_t[kThreads];
   __shared__ double s_val[kThreads];
@@ -173,28 +212,30 @@ __global__ void __launch_bounds__(kThreads) k_rows_t2(
       } else {
         idx = nearest_shift(shift_m, ns, x);
       }
+      int64_t xc[D];
+      coords_of<D>(j, logn, mask, xc);
       s_idx[t] = idx;
-      s_t[t] = t_of_point(j >> logn, j & mask, leaf);
+      s_t[t] = t_of_point<D>(xc, leaf);
       s_val[t] = shift_of(__ldg(shift_m + idx));
     }
     __syncthreads();
     const int64_t obase = j0 * MU;
     for (int e = t; e < npts * MU; e += kThreads) {
       const int p = e / MU, o = e - p * MU;
-      const int o0 = o / 5 - 2, o1 = o % 5 - 2;
+      int off[D];
+      const int inner = decode5<D>(o, off);
       const int idx = s_idx[p];
       double a = 0.0, cc = 0.0;
       if (s_t[p] == 2) {
         a = __ldg(alpha2 + (int64_t)idx * MU + o);
         cc = __ldg(c2 + (int64_t)idx * MU + o);
-      } else if (o0 >= -1 && o0 <= 1 && o1 >= -1 && o1 <= 1) {
-        const int b = (o0 + 1) * 3 + (o1 + 1);
-        a = __ldg(alpha1 + (int64_t)idx * 9 + b);
-        cc = __ldg(c1 + (int64_t)idx * 9 + b);
+      } else if (inner >= 0) {
+        a = __ldg(alpha1 + (int64_t)idx * MU1 + inner);
+        cc = __ldg(c1 + (int64_t)idx * MU1 + inner);
       }
-      const int64_t jj = j0 + p;
-      const int64_t nb = (((jj >> logn) + o0) & mask) << logn | (((jj & mask) + o1) & mask);
-      const double vn = __ldg(v + nb);
+      int64_t xc[D];
+      coords_of<D>(j0 + p, logn, mask, xc);
+      const double vn = __ldg(v + wrap_index<D>(xc, off, logn, mask));
       __stcs(Q + obase + e, a);
       __stcs(C + obase + e, cc);
       __stcs(P + obase + e, fma(cc, vn - s_val[p], a));
@@ -203,25 +244,30 @@ __global__ void __launch_bounds__(kThreads) k_rows_t2(
   }
 }
 
-// CSR export of a t = 2 build: row j keeps the (2 t_j + 1)^2 columns of mu_j^{t_j}, in the
-// lexicographic order of its own offsets (the inner 3 x 3 of the 25-wide row when t_j = 1).
+// CSR export of a t = 2 build: row j keeps the (2 t_j + 1)^D columns of mu_j^{t_j}, in the
+// lexicographic order of its own offsets (the inner 3^D of the 5^D-wide row when t_j = 1).
 // rowptr holds the prefix sums of the row lengths.
+template <int D>
 __global__ void __launch_bounds__(kThreads) k_export_t2(const double* __restrict__ rows,
                                                         int64_t N, int logn, int leaf,
                                                         const int64_t* __restrict__ rowptr,
                                                         int32_t* __restrict__ col,
                                                         double* __restrict__ val) {
+  constexpr int MU = D == 2 ? 25 : 125;
   const int64_t mask = ((int64_t)1 << logn) - 1;
-  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < N * 25;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < N * MU;
        e += (int64_t)gridDim.x * kThreads) {
-    const int64_t j = e / 25;
-    const int o = (int)(e - j * 25);
-    const int o0 = o / 5 - 2, o1 = o % 5 - 2;
-    const int tj = t_of_point(j >> logn, j & mask, leaf);
-    if (tj == 1 && (o0 < -1 || o0 > 1 || o1 < -1 || o1 > 1)) continue;
-    const int k = tj == 2 ? o : (o0 + 1) * 3 + (o1 + 1);
+    const int64_t j = e / MU;
+    const int o = (int)(e - j * MU);
+    int off[D];
+    const int inner = decode5<D>(o, off);
+    int64_t xc[D];
+    coords_of<D>(j, logn, mask, xc);
+    const int tj = t_of_point<D>(xc, leaf);
+    if (tj == 1 && inner < 0) continue;
+    const int k = tj == 2 ? o : inner;
     const int64_t pos = rowptr[j] + k;
-    col[pos] = (int32_t)((((j >> logn) + o0) & mask) << logn | (((j & mask) + o1) & mask));
+    col[pos] = (int32_t)wrap_index<D>(xc, off, logn, mask);
     val[pos] = rows[e];
   }
 }
@@ -293,21 +339,33 @@ cudaError_t launch_rows_t2(lsp_ctx* c, int policy, const int32_t* count, int lea
         (const double*)c->alpha2.p, (const double*)c->cst2.p, (double*)c->Q.p, (double*)c->C.p,
         (double*)c->P.p);
   };
-  if (policy == LSP_SHIFT_LOCAL)
-    args(k_rows_t2<true>);
-  else
-    args(k_rows_t2<false>);
+  const bool local = policy == LSP_SHIFT_LOCAL;
+  if (c->geo.d == 2) {
+    if (local)
+      args(k_rows_t2<2, true>);
+    else
+      args(k_rows_t2<2, false>);
+  } else {
+    if (local)
+      args(k_rows_t2<3, true>);
+    else
+      args(k_rows_t2<3, false>);
+  }
   timer_end(c, t);
   return cudaGetLastError();
 }
 
 cudaError_t launch_export_t2(lsp_ctx* c, const double* rows, int leaf, const int64_t* rowptr,
                              int32_t* colidx, double* vals) {
-  const int64_t work = c->geo.N * 25;
+  const int64_t work = c->geo.N * (c->geo.d == 2 ? 25 : 125);
   int64_t b = (work + kThreads - 1) / kThreads;
   if (b > 152 * 16) b = 152 * 16;
-  k_export_t2<<<(int)b, kThreads, 0, c->stream>>>(rows, c->geo.N, log2i(c->geo.n), leaf, rowptr,
-                                                  colidx, vals);
+  if (c->geo.d == 2)
+    k_export_t2<2><<<(int)b, kThreads, 0, c->stream>>>(rows, c->geo.N, log2i(c->geo.n), leaf,
+                                                       rowptr, colidx, vals);
+  else
+    k_export_t2<3><<<(int)b, kThreads, 0, c->stream>>>(rows, c->geo.N, log2i(c->geo.n), leaf,
+                                                       rowptr, colidx, vals);
   return cudaGetLastError();
 }
 

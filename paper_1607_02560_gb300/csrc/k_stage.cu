@@ -68,6 +68,24 @@ struct StageMap<3, 3> {
   }
 };
 
+// Stage 3 for A = 5 (t = 2 in 3D): the 35 sorted triples over {0..4}, the ten of A = 3 first
+// in their order, then those with largest component 3, then 4, each group lexicographic; a
+// triple (a <= b <= c) is (a, class of the pair (b, c) in the stage-2 order of A = 5).
+template <>
+struct StageMap<3, 5> {
+  static constexpr int NCP = 15, NCO = 35;
+  __host__ __device__ static constexpr int a(int c) {
+    constexpr int t[35] = {0, 0, 0, 0, 0, 0, 1, 1, 1, 2, 0, 0, 0, 0, 1, 1, 1, 2,
+                           2, 3, 0, 0, 0, 0, 0, 1, 1, 1, 1, 2, 2, 2, 3, 3, 4};
+    return t[c];
+  }
+  __host__ __device__ static constexpr int r(int c) {
+    constexpr int t[35] = {0, 1, 2, 3, 4,  5,  3,  4,  5,  5,  6,  7,  8,  9,  7,  8,  9, 8,
+                           9, 9, 10, 11, 12, 13, 14, 11, 12, 13, 14, 12, 13, 14, 13, 14, 14};
+    return t[c];
+  }
+};
+
 // R is the arithmetic type: double for the FP64 mode, float for the mixed mode. OUT is the
 // type of the output table (the last stage always writes double g values).
 template <typename R>
@@ -249,11 +267,17 @@ cudaError_t launch_typed(lsp_ctx* c, int d, int k, int t, const int32_t* list,
                          int64_t stride_prev, void* Tout, int64_t lo_out, int64_t stride_out,
                          bool by_index, double scale, const R* X) {
   const R* prev = (const R*)Tprev;
-  if (t == 2) {  // 2D only (validated by the caller): five cosine rows
+  if (t == 2) {  // five cosine rows (2D and 3D)
     if (k == 1)
       return launch_k<1, 5, R, R>(c, list, count, cap, X, prev, lo_prev, stride_prev, (R*)Tout,
                                   lo_out, stride_out, by_index, scale);
-    return launch_k<2, 5, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev,
+    if (k == 2 && d == 3)
+      return launch_k<2, 5, R, R>(c, list, count, cap, X, prev, lo_prev, stride_prev, (R*)Tout,
+                                  lo_out, stride_out, by_index, scale);
+    if (k == 2)
+      return launch_k<2, 5, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev,
+                                       (double*)Tout, lo_out, stride_out, by_index, scale);
+    return launch_k<3, 5, R, double>(c, list, count, cap, X, prev, lo_prev, stride_prev,
                                      (double*)Tout, lo_out, stride_out, by_index, scale);
   }
   if (k == d) {  // last stage: double g values for the eigen step

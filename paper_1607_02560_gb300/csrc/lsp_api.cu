@@ -46,7 +46,10 @@ double shift_host(int64_t m) {
   return a * kPi2;
 }
 
-int ncls_stage(int k) { return k == 1 ? 3 : (k == 2 ? 6 : 10); }
+// Classes of the stage-k table: sorted k-tuples over {0..2t} (t = 1: 3, 6, 10; t = 2: 5, 15, 35).
+int ncls_stage(int k, int t = 1) {
+  return t == 1 ? (k == 1 ? 3 : (k == 2 ? 6 : 10)) : (k == 1 ? 5 : (k == 2 ? 15 : 35));
+}
 
 // Is r = |k|^2 for some k in K = [-n/2, n/2)^d ?  (the eigenvalues of L are 4 pi^2 |k|^2)
 bool is_norm(int64_t r, int d, int half) {
@@ -80,14 +83,20 @@ int pair_index(int a, int b) {
   static const int t[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
   return b <= 2 ? t[a][b] : b * (b + 1) / 2 + a;
 }
+// Class of a sorted triple a <= b <= c of |offset| components: the ten triples over {0,1,2}
+// in the order 000 001 002 011 012 022 111 112 122 222, then (t = 2) the triples with largest
+// component 3 and then 4, each group in lexicographic order, so the classes of t = 1 keep
+// their indices in a t = 2 table (the stage kernels use this order).
 int triple_index(int a, int b, int c) {  // a <= b <= c
   int idx = 0;
-  for (int x = 0; x < 3; ++x)
-    for (int y = x; y < 3; ++y)
-      for (int z = y; z < 3; ++z) {
-        if (x == a && y == b && z == c) return idx;
-        ++idx;
-      }
+  for (int top = 2; top <= 4; ++top)
+    for (int x = 0; x <= top; ++x)
+      for (int y = x; y <= top; ++y)
+        for (int z = y; z <= top; ++z) {
+          if (top > 2 && z != top) continue;  // groups: max <= 2, then max = 3, max = 4
+          if (x == a && y == b && z == c) return idx;
+          ++idx;
+        }
   return -1;
 }
 
@@ -99,7 +108,7 @@ void build_geometry(Geometry& g, int d, int n, int t = 1) {
   g.t = t;
   const int w = 2 * t + 1;
   g.mu = d == 1 ? w : (d == 2 ? w * w : w * w * w);
-  g.ncls = d == 1 ? 2 * t + 1 : (d == 2 ? w * (w + 1) / 2 : 10);
+  g.ncls = d == 1 ? 2 * t + 1 : (d == 2 ? w * (w + 1) / 2 : w * (w + 1) * (w + 2) / 6);
   g.centre = g.mu / 2;
   g.N = 1;
   for (int i = 0; i < d; ++i) g.N *= n;
@@ -396,7 +405,10 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
   if (o.t == 1 || o.nd_leaf > 0)
     CUDA_OK(c, launch_eig(c, counts + 0, cap_s, o.eig_method, o.refine_steps, fp32));
   if (o.t == 2) {
-    CUDA_OK(c, launch_eig_t2(c, counts + 0, cap_s));
+    if (d == 2)
+      CUDA_OK(c, launch_eig_t2(c, counts + 0, cap_s));
+    else
+      CUDA_OK(c, launch_eig_dense3(c, counts + 0, cap_s));
     CUDA_OK(c, launch_rows_t2(c, o.policy, counts + 0, o.nd_leaf));
   } else {
     CUDA_OK(c, launch_rows(c, o.policy, counts + 0));
@@ -430,12 +442,14 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
     delete c;
     return LSP_ERR_STATE;
   }
-  if (d == 2) {  // t = 2 neighbourhoods (2D)
+  if (d == 2) {  // t = 2 neighbourhoods (2D: symmetry-reduced eigen path)
     build_geometry(c->geo2, d, n, 2);
     if (!build_sym_t2(c->sym2, c->geo2)) {
       delete c;
       return LSP_ERR_STATE;
     }
+  } else if (d == 3 && n >= 8) {  // t = 2 neighbourhoods (3D: dense eigen path)
+    build_geometry(c->geo2, d, n, 2);
   }
   lsp_status st = LSP_OK;
   do {
@@ -448,6 +462,10 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
       break;
     }
     if (upload_sym(c) != cudaSuccess) {
+      st = LSP_ERR_CUDA;
+      break;
+    }
+    if (d == 3 && n >= 8 && upload_cls125(c->geo2) != cudaSuccess) {
       st = LSP_ERR_CUDA;
       break;
     }
@@ -583,8 +601,10 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     lsp_default_opts(&o);
   if (!c->have_v) return fail(c, LSP_ERR_STATE, "build_stencils before set_potential");
   if (o.t != 1 && o.t != 2) return fail(c, LSP_ERR_ARG, "t must be 1 or 2");
-  if (o.t == 2 && c->geo.d != 2)
-    return fail(c, LSP_ERR_UNSUPPORTED, "t = 2 neighbourhoods are built in 2D only");
+  if (o.t == 2 && c->geo.d == 1)
+    return fail(c, LSP_ERR_UNSUPPORTED, "t = 2 neighbourhoods are built in 2D and 3D");
+  if (o.t == 2 && c->geo.n < 8)
+    return fail(c, LSP_ERR_UNSUPPORTED, "t = 2 neighbourhoods need n >= 8");
   if (o.nd_leaf < 0 || (o.nd_leaf > 0 && (o.nd_leaf < 2 || c->geo.n % o.nd_leaf != 0)))
     return fail(c, LSP_ERR_ARG, "nd_leaf must be 0 or an even divisor >= 2 of n");
   if (o.t == 2 && o.mode == LSP_LEARNED)
@@ -719,7 +739,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   for (int k = 1; ok && k < d; ++k) {
     const int64_t sz = c->erange[k].size();
     ok = ensure(c, c->eflag[k], round_up(sz, 4096)) && ensure(c, c->elist[k], sizeof(int32_t) * sz) &&
-         ensure(c, c->T[k], sizeof(double) * 2 * (o.t == 2 ? 5 : ncls_stage(k)) * sz);
+         ensure(c, c->T[k], sizeof(double) * 2 * ncls_stage(k, o.t) * sz);
   }
   if (!ok) return LSP_ERR_OOM;
   if (o.policy != LSP_SHIFT_LOCAL) {
@@ -810,11 +830,15 @@ static int built_mu(const lsp_ctx* c) { return c->t_built == 2 ? c->geo2.mu : c-
 
 // t_j of a t = 2 build at point j (2D): 2 everywhere without a leaf, else the largest t <= 2
 // whose neighbourhood crosses no separator line x_a = 0 (mod leaf) (Sec. 4.2).
-static int t_of_point(int64_t j, int n, int leaf) {
+static int t_of_point(int64_t j, int n, int leaf, int d = 2) {
   if (leaf <= 0) return 2;
   int t = 2;
-  const int64_t x[2] = {j / n, j % n};
-  for (int a = 0; a < 2; ++a) {
+  int64_t x[3];
+  for (int a = d - 1; a >= 0; --a) {
+    x[a] = j % n;
+    j /= n;
+  }
+  for (int a = 0; a < d; ++a) {
     const int r = (int)(x[a] % leaf);
     const int f = r == 0 ? leaf : std::min(r, leaf - r);
     t = std::min(t, f);
@@ -852,12 +876,13 @@ lsp_status lsp_export_sparse_rows(lsp_ctx* c, char which, int64_t* rowptr, int32
   cudaGetLastError();
   const int64_t N = c->geo.N;
   if (c->built && c->t_built == 2) {
-    // rows of (2 t_j + 1)^2 entries: the structural zeros of t_j = 1 rows are left out
+    // rows of (2 t_j + 1)^d entries: the structural zeros of t_j = 1 rows are left out
     std::vector<int64_t> ptr(N + 1);
     ptr[0] = 0;
+    const int d = c->geo.d;
     for (int64_t j = 0; j < N; ++j) {
-      const int w = 2 * t_of_point(j, c->geo.n, c->leaf_built) + 1;
-      ptr[j + 1] = ptr[j] + w * w;
+      const int w = 2 * t_of_point(j, c->geo.n, c->leaf_built, d) + 1;
+      ptr[j + 1] = ptr[j] + (d == 2 ? w * w : w * w * w);
     }
     const int64_t nnz = ptr[N];
     if (nnz_out) *nnz_out = nnz;

@@ -23,7 +23,8 @@ constexpr double kPi2 = kPi * kPi;
 constexpr double kQuarterInvPi2 = 0.25 / kPi2;  // for the fast path of the lattice snap
 
 constexpr int kMaxD = 3;
-constexpr int kMaxMu = 27;      // (2t+1)^d: 27 for t = 1, d = 3; 25 for t = 2, d = 2
+constexpr int kMaxMu = 27;      // (2t+1)^d of the symmetry-reduced paths: 27 (t = 1, 3D), 25 (t = 2, 2D)
+constexpr int kMaxMuGeo = 125;  // (2t+1)^d of any neighbourhood: 125 for t = 2 in 3D
 constexpr int kMaxCls = 15;     // sorted |offset| tuples: 10 over {0,1,2}^3, 15 over {0..4}^2
 constexpr int kMaxSymVec = 19;  // symmetry-adapted basis vectors (19 for t = 2, d = 2)
 constexpr int kMaxSymBlk = 6;
@@ -48,8 +49,8 @@ struct Geometry {
   int d, n, t, mu, ncls, centre;
   int64_t N;
   int P;                           // n/2 + 1 frequencies per axis in [0, n/2]
-  int off[kMaxMu][kMaxD];          // mu_0 offsets, lexicographic
-  uint8_t cls_of[kMaxMu][kMaxMu];  // class of o_a - o_b (sorted |components|)
+  int off[kMaxMuGeo][kMaxD];             // mu_0 offsets, lexicographic
+  uint8_t cls_of[kMaxMuGeo][kMaxMuGeo];  // class of o_a - o_b (sorted |components|)
 };
 
 struct Range {
@@ -166,6 +167,8 @@ cudaError_t launch_stage(lsp_ctx* c, int d, int k, int t, const int32_t* list,
                          int64_t stride_prev, void* Tout, int64_t lo_out, int64_t stride_out,
                          bool by_index, bool fp32);
 cudaError_t launch_eig_t2(lsp_ctx* c, const int32_t* count, int64_t cap);
+cudaError_t launch_eig_dense3(lsp_ctx* c, const int32_t* count, int64_t cap);
+cudaError_t upload_cls125(const Geometry& g);
 cudaError_t launch_rows_t2(lsp_ctx* c, int policy, const int32_t* count, int leaf);
 cudaError_t launch_export_t2(lsp_ctx* c, const double* rows, int leaf, const int64_t* rowptr,
                              int32_t* colidx, double* vals);

@@ -20,12 +20,11 @@ inline int wrapi(int a, int n) {
   return a < 0 ? a + n : a;
 }
 
-// t_j of point (x0, x1) for a t = 2 build with leaf width L (Sec. 4.2): the largest t <= 2
-// whose neighbourhood crosses no line x_a = 0 (mod L); a point on a line counts the full width.
-inline int t_point(int x0, int x1, int L) {
+// t_j of point x for a t = 2 build with leaf width L (Sec. 4.2): the largest t <= 2 whose
+// neighbourhood crosses no line (plane) x_a = 0 (mod L); a point on one counts the full width.
+inline int t_point(const int* x, int d, int L) {
   int t = 2;
-  const int x[2] = {x0, x1};
-  for (int a = 0; a < 2; ++a) {
+  for (int a = 0; a < d; ++a) {
     const int rr = x[a] % L;
     const int f = rr == 0 ? L : std::min(rr, L - rr);
     t = std::min(t, f);
@@ -41,7 +40,6 @@ std::string build_nd_plan(NdPlan& P, int d, int n, int leaf, int t_built, int le
   if (n < 4 || (n & (n - 1))) return "the dissection needs n a power of two >= 4";
   if (leaf < 4 || (leaf & (leaf - 1)) || leaf > n)
     return "the leaf width b must be a power of two with 4 <= b <= n";
-  if (d == 3 && t_built != 1) return "3D rows must be t = 1 rows";
   if (t_built == 2 && leaf_t <= 0)
     return "t = 2 rows at every point cross the separators: build with nd_leaf = b";
   if (t_built == 2 && leaf_t != leaf)
@@ -222,7 +220,7 @@ std::string build_nd_plan(NdPlan& P, int d, int n, int leaf, int t_built, int le
     if (t_built == 1) return 1;
     int x[3];
     coords(g, x);
-    return t_point(x[0], x[1], leaf_t);
+    return t_point(x, d, leaf_t);
   };
   // offset index in the lexicographic list of [-t_built, t_built]^d (last axis fastest)
   auto a_of = [&](const int* o) {

@@ -1,6 +1,7 @@
 """Multi-t stencils on the GPU (Sec. 4.2) against the CPU oracle.
 
-* t = 2 (5 x 5 neighbourhoods, 2D) at every point: per-shift alpha, c, lambda_1 and the rows;
+* t = 2 (5 x 5 neighbourhoods in 2D, 5 x 5 x 5 in 3D) at every point: per-shift alpha, c,
+  lambda_1 and the rows;
 * per-point t_j from the nested-dissection geometry (leaf width 8, t_max = 2): the CSR export
   has the oracle's exact pattern (rows of 9 or 25 entries) and its values within the
   tolerances of the FP64 path;
@@ -141,13 +142,74 @@ def test_t2_switches_back_to_t1_and_graph_replay():
     assert ctx.mu == 9 and np.array_equal(ctx.get_rows("Q"), q1)
 
 
+@pytest.mark.parametrize("policy", ["paper", "local"])
+def test_t2_3d_everywhere_matches_oracle(policy):
+    """3D t = 2 (125-point neighbourhoods, 35 classes): per-shift alpha, c and lambda_1 of the
+    dense near-null solve, and the rows, against the oracle."""
+    n, d = 16, 3
+    v = make_workload("schr3d_n64", n=n)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy=policy, t=2)
+    assert ctx.mu == 125
+    tab = ctx.get_shift_table()
+    ref = O.build_stencils(v, policy, t=2)
+    assert np.array_equal(tab["s"], ref["S"])
+    ta_max = tc_max = 0.0
+    for i, s in enumerate(ref["S"]):
+        st, ta, tc = tols(n, d, s, 2)
+        assert np.abs(tab["alpha"][i] - st["alpha"]).max() <= ta, i
+        assert np.abs(tab["c"][i] - st["c"]).max() <= tc, i
+        assert abs(tab["lam"][i, 0] - st["lam1"]) <= 1e-9 * np.abs(st["A"]).max()
+        assert not (tab["flags"][i] & 4)
+        ta_max, tc_max = max(ta_max, ta), max(tc_max, tc)
+    Q, C, P = (ctx.get_rows(k) for k in "QCP")
+    sidx = tab["s_idx"].astype(np.int64)
+    assert np.array_equal(Q, tab["alpha"][sidx]) and np.array_equal(C, tab["c"][sidx])
+    assert np.abs(Q - ref["Q"]).max() <= ta_max
+    assert np.abs(C - ref["C"]).max() <= tc_max
+    vmax = np.abs(v).max() + np.abs(ref["S"]).max()
+    assert np.abs(P - ref["P"]).max() <= ta_max + tc_max * vmax + 1e-13 * np.abs(ref["P"]).max()
+
+
+def test_multi_t_3d_rows_nd_and_gmres_match_oracle():
+    """3D multi-t (t_j from leaf-8 boxes, rows of 27 or 125 entries): the CSR export against the
+    oracle, the nested dissection of these rows, and the GMRES count with them."""
+    n, d = 16, 3
+    v = make_workload("schr3d_n64", n=n)
+    N = n ** d
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="paper", t=2, nd_leaf=8)
+    ref = O.build_stencils_multi(v, "paper", leaf=8, t_max=2)
+    ta_max = tc_max = 0.0
+    for s in ref["S"]:
+        for t in (1, 2):
+            _, ta, tc = tols(n, d, s, t)
+            ta_max, tc_max = max(ta_max, ta), max(tc_max, tc)
+    vmax = np.abs(v).max() + np.abs(ref["S"]).max()
+    for which, tol in (("Q", ta_max), ("C", tc_max),
+                       ("P", ta_max + tc_max * vmax + 1e-13 * np.abs(ref["P"].data).max())):
+        got, want = csr(ctx, which, N), ref[which]
+        assert np.array_equal(got.indptr, want.indptr), which
+        assert np.array_equal(got.indices, want.indices), which
+        assert np.abs(got.data - want.data).max() <= tol, which
+    assert set(np.diff(csr(ctx, "Q", N).indptr).tolist()) == {27, 125}
+    ctx.nd_factor()
+    f = gaussian_source(n, d, 2.0)
+    _, res = ctx.gmres(f.reshape(-1))
+    _, it, _, info = O.gmres_solve(v, f, csr(ctx, "P", N), csr(ctx, "C", N), maxiter=5)
+    print(f"3D multi-t n=16: GPU {res}, oracle {it} iterations")
+    assert info == 0 and res["converged"] == 1 and res["iterations"] == it
+
+
 def test_unsupported_combinations_fail_cleanly():
     from paper_1607_02560_gb300 import LspError
-    v3 = make_workload("schr3d_n64", n=16)
-    ctx3 = ctx_for(v3)
-    ctx3.set_potential(v3)
+    v1 = make_workload("helm1d_n256", n=64)
+    ctx1 = ctx_for(v1)
+    ctx1.set_potential(v1)
     with pytest.raises(LspError, match="UNSUPPORTED"):
-        ctx3.build_stencils(t=2)
+        ctx1.build_stencils(t=2)
     v = make_workload("helm2d_n32")
     ctx = ctx_for(v)
     ctx.set_potential(v)

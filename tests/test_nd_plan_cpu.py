@@ -95,8 +95,11 @@ def test_3d_every_point_is_eliminated_once(n, leaf):
     assert info["flops"] == pytest.approx(sweep, rel=1e-12)
 
 
-def test_3d_limits():
+def test_3d_limits_and_multi_t():
     with pytest.raises(lsp.LspError, match="n <= 64"):
         lsp.nd_plan_info(128, 8, d=3)
-    with pytest.raises(lsp.LspError, match="t = 1"):
-        lsp.nd_plan_info(16, 8, t=2, nd_leaf=8, d=3)
+    with pytest.raises(lsp.LspError, match="cross the separators"):
+        lsp.nd_plan_info(16, 8, t=2, nd_leaf=0, d=3)
+    # 3D multi-t rows (27 or 125 entries by the leaf-8 t_j rule) fit the leaf-8 dissection
+    info = lsp.nd_plan_info(16, 8, t=2, nd_leaf=8, d=3)
+    assert sum(c * s for c, s, _ in info["depths"]) == 16 ** 3
