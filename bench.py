@@ -578,8 +578,7 @@ def variants(args, torch):
         except Exception as exc:  # a variant must not hide the main line
             out.append({"workload": wl, "policy": pol, "mode": mode, "error": str(exc)[:200]})
     # multi-t (Sec. 4.2): t_j from a nested dissection with leaf boxes of width 8, t_max = 2
-    for pol in ("paper", "local"):
-        wl = "helm2d_n1024" if pol == "paper" else "helm2d_n256"
+    for wl, pol in (("helm2d_n1024", "paper"), ("helm2d_n256", "local"), ("schr3d_n64", "local")):
         try:
             out.append(time_config(torch, wl, pol, "fp64", steps=20, warmup=3, t=2, nd_leaf=8))
         except Exception as exc:
