@@ -603,8 +603,11 @@ __global__ void __launch_bounds__(kRowThreads) k_nd_rowblock(double* __restrict_
 
 // Part 3: F[i][j] -= cbuf[i][:] . F[K][j] for every i, j outside K (64 x 64 tiles).
 constexpr int kUT = 64;
+// Columns updated: [col_lo, col_hi) without [skip_lo, skip_hi) (which holds K); the tiles
+// start at col_lo. With look-ahead a step is split into the next panel's columns and the rest.
 __global__ void __launch_bounds__(256) k_nd_update(double* __restrict__ fronts, int f, int k,
-                                                   int nb, int tiles_j,
+                                                   int nb, int tiles_j, int col_lo, int col_hi,
+                                                   int skip_lo, int skip_hi,
                                                    const double* __restrict__ cbuf) {
   __shared__ double cs[kUT][NP + 1];
   __shared__ double ws[NP][kUT];
@@ -612,13 +615,13 @@ __global__ void __launch_bounds__(256) k_nd_update(double* __restrict__ fronts, 
   const int64_t fid = blockIdx.y;
   double* F = fronts + fid * f * f;
   const int ti = blockIdx.x / tiles_j, tj = blockIdx.x % tiles_j;
-  const int i0 = ti * kUT, j0 = tj * kUT;
+  const int i0 = ti * kUT, j0 = col_lo + tj * kUT;
   const double* cb = cbuf + fid * (int64_t)f * NP;
   for (int e = tid; e < kUT * NP; e += blockDim.x) {
     const int r = e / NP, c = e % NP;
     cs[r][c] = (i0 + r < f) ? cb[(int64_t)(i0 + r) * NP + c] : 0.0;
     const int c2 = e / kUT, col = e % kUT;
-    ws[c2][col] = (c2 < nb && j0 + col < f) ? F[(int64_t)(k + c2) * f + j0 + col] : 0.0;
+    ws[c2][col] = (c2 < nb && j0 + col < col_hi) ? F[(int64_t)(k + c2) * f + j0 + col] : 0.0;
   }
   __syncthreads();
   const int ty = tid / 16, tx = tid % 16;
@@ -627,7 +630,7 @@ __global__ void __launch_bounds__(256) k_nd_update(double* __restrict__ fronts, 
   for (int a = 0; a < 4; ++a) {
     const int i = i0 + ty + 16 * a, j = j0 + tx + 16 * a;
     rok[a] = i < f && (i < k || i >= k + nb);
-    cok[a] = j < f && (j < k || j >= k + nb);
+    cok[a] = j < col_hi && (j < skip_lo || j >= skip_hi);
   }
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b)
@@ -913,28 +916,70 @@ cudaError_t launch_nd_sweep(lsp_ctx* c, int depth) {
   const int tiles_w = (lv.f + kRowThreads - 1) / kRowThreads;
   const int tiles_c = (lv.f + kRowThreads - 1) / kRowThreads;
   const int tiles_u = (lv.f + kUT - 1) / kUT;
-  for (int k = 0; k < lv.s; k += NP) {
+  // Look-ahead: once a step's update has reached the next panel's columns, that panel runs on
+  // the side stream while the rest of the update runs here (disjoint columns). The step
+  // buffers (cbuf, pinv, swaps) alternate between two copies. Per-kernel timing keeps one
+  // stream so that every launch is bracketed by its own events.
+  const bool ahead = S.side != nullptr && !c->timing;
+  auto buf = [&](int par, double** cb, double** pv, int32_t** sw) {
+    *cb = (double*)S.cbuf.p + (int64_t)par * S.cbuf_half;
+    *pv = (double*)S.pinv.p + (int64_t)par * S.pinv_half;
+    *sw = (int32_t*)S.swaps.p + (int64_t)par * S.swaps_half;
+  };
+  auto panel = [&](int k, int par, cudaStream_t st) {
+    double *cb, *pv;
+    int32_t* sw;
+    buf(par, &cb, &pv, &sw);
     const int nb = lv.s - k < NP ? lv.s - k : NP;
     const int t1 = c->timing ? timer_begin(c, level_name("nd_pnl", depth)) : -1;
     if (big)
-      k_nd_panel_big<<<lv.count, 256, 0, c->stream>>>(F, lv.f, lv.s, k, nb, perm,
-                                                      (double*)S.cbuf.p, (double*)S.pinv.p,
-                                                      (int32_t*)S.swaps.p, err,
-                                                      (float*)S.pscratch.p);
+      k_nd_panel_big<<<lv.count, 256, 0, st>>>(F, lv.f, lv.s, k, nb, perm, cb, pv, sw, err,
+                                               (float*)S.pscratch.p);
     else
-      k_nd_panel<<<lv.count, 256, 0, c->stream>>>(F, lv.f, lv.s, k, nb, perm,
-                                                  (double*)S.cbuf.p, (double*)S.pinv.p,
-                                                  (int32_t*)S.swaps.p, err);
+      k_nd_panel<<<lv.count, 256, 0, st>>>(F, lv.f, lv.s, k, nb, perm, cb, pv, sw, err);
     timer_end(c, t1);
+  };
+  auto update = [&](int k, int nb, const double* cb, int col_lo, int col_hi, int skip_lo,
+                    int skip_hi) {
+    const int tj = (col_hi - col_lo + kUT - 1) / kUT;
+    const int t3 = c->timing ? timer_begin(c, level_name("nd_upd", depth)) : -1;
+    k_nd_update<<<dim3(tiles_u * tj, lv.count), 256, 0, c->stream>>>(
+        F, lv.f, k, nb, tj, col_lo, col_hi, skip_lo, skip_hi, cb);
+    timer_end(c, t3);
+  };
+  panel(0, 0, c->stream);
+  for (int k = 0, step = 0; k < lv.s; k += NP, ++step) {
+    const int nb = lv.s - k < NP ? lv.s - k : NP;
+    const int par = step & 1;
+    double *cb, *pv;
+    int32_t* sw;
+    buf(par, &cb, &pv, &sw);
+    if (ahead && step > 0) {
+      cudaError_t e = cudaStreamWaitEvent(c->stream, S.ev_panel, 0);
+      if (e != cudaSuccess) return e;
+    }
     const int t2 = c->timing ? timer_begin(c, level_name("nd_row", depth)) : -1;
     k_nd_rowblock<<<dim3(tiles_w + tiles_c, lv.count), kRowThreads, 0, c->stream>>>(
-        F, lv.f, k, nb, tiles_w, (double*)S.cbuf.p, (const double*)S.pinv.p,
-        (const int32_t*)S.swaps.p);
+        F, lv.f, k, nb, tiles_w, cb, pv, sw);
     timer_end(c, t2);
-    const int t3 = c->timing ? timer_begin(c, level_name("nd_upd", depth)) : -1;
-    k_nd_update<<<dim3(tiles_u * tiles_u, lv.count), 256, 0, c->stream>>>(
-        F, lv.f, k, nb, tiles_u, (const double*)S.cbuf.p);
-    timer_end(c, t3);
+    const int kn = k + nb;
+    if (kn >= lv.s) {  // last step: the whole update
+      update(k, nb, cb, 0, lv.f, k, kn);
+    } else if (ahead) {
+      const int nbn = lv.s - kn < NP ? lv.s - kn : NP;
+      update(k, nb, cb, kn, kn + nbn, k, kn);  // the next panel's columns first
+      cudaError_t e = cudaEventRecord(S.ev_cols, c->stream);
+      if (e != cudaSuccess) return e;
+      e = cudaStreamWaitEvent(S.side, S.ev_cols, 0);
+      if (e != cudaSuccess) return e;
+      panel(kn, par ^ 1, S.side);
+      e = cudaEventRecord(S.ev_panel, S.side);
+      if (e != cudaSuccess) return e;
+      update(k, nb, cb, 0, lv.f, k, kn + nbn);  // the rest, beside the panel
+    } else {
+      update(k, nb, cb, 0, lv.f, k, kn);
+      panel(kn, par ^ 1, c->stream);
+    }
   }
   timer_end(c, t);
   return cudaGetLastError();

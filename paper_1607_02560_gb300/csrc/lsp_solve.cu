@@ -91,6 +91,9 @@ void nd_free(NdState* s) {
   for (DevBuf* b : bufs)
     if (b->p) cudaFree(b->p);
   if (s->h_gs) cudaFreeHost(s->h_gs);
+  if (s->ev_cols) cudaEventDestroy(s->ev_cols);
+  if (s->ev_panel) cudaEventDestroy(s->ev_panel);
+  if (s->side) cudaStreamDestroy(s->side);
   delete s;
 }
 
@@ -166,10 +169,21 @@ lsp_status lsp_nd_factor(lsp_ctx* c, const lsp_nd_opts* opts) {
         !ensure(c, S.perm, sizeof(int32_t) * P.perm_ints) ||
         !ensure(c, S.z, sizeof(double) * P.z_doubles) ||
         !ensure(c, S.u, sizeof(double) * (P.u_doubles > 0 ? P.u_doubles : 1)) ||
-        !ensure(c, S.cbuf, sizeof(double) * cb) || !ensure(c, S.pinv, sizeof(double) * pv) ||
-        !ensure(c, S.swaps, sizeof(int32_t) * sw) || !ensure(c, S.err, sizeof(int32_t)))
+        !ensure(c, S.cbuf, sizeof(double) * 2 * cb) ||
+        !ensure(c, S.pinv, sizeof(double) * 2 * pv) ||
+        !ensure(c, S.swaps, sizeof(int32_t) * 2 * sw) || !ensure(c, S.err, sizeof(int32_t)))
       return sfail(c, LSP_ERR_OOM, "nested dissection buffers: %s", c->err.c_str());
-    SCUDA(c, cudaMemsetAsync(S.swaps.p, 0, sizeof(int32_t) * sw, c->stream));
+    S.cbuf_half = cb;
+    S.pinv_half = pv;
+    S.swaps_half = sw;
+    SCUDA(c, cudaMemsetAsync(S.swaps.p, 0, sizeof(int32_t) * 2 * sw, c->stream));
+    if (!S.side) {
+      int least = 0, greatest = 0;
+      SCUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+      SCUDA(c, cudaStreamCreateWithPriority(&S.side, cudaStreamNonBlocking, greatest));
+      SCUDA(c, cudaEventCreateWithFlags(&S.ev_cols, cudaEventDisableTiming));
+      SCUDA(c, cudaEventCreateWithFlags(&S.ev_panel, cudaEventDisableTiming));
+    }
     SCUDA(c, nd_prepare_kernels((int)std::min<int64_t>(sizeof(double) * max_sr + 64, 220 * 1024)));
     S.have_plan = true;
   }

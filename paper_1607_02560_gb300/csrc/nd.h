@@ -74,6 +74,9 @@ struct NdState {
   DevBuf fronts, E, R, inv, asm_dst, asm_src, perm, z, u, cbuf, pinv, swaps, err;
   DevBuf ry, rd;              // refinement scratch: a copy of y, the correction
   DevBuf pscratch;            // FP32 pivot-ranking rows of panels over 2048 rows
+  int64_t cbuf_half = 0, pinv_half = 0, swaps_half = 0;  // the two copies of the step buffers
+  cudaStream_t side = nullptr;  // look-ahead panels (high priority)
+  cudaEvent_t ev_cols = nullptr, ev_panel = nullptr;
   // GMRES workspace
   DevBuf V, w, b, x, tmp, gs, fvec;
   double* h_gs = nullptr;  // pinned mirror of the scalars the host loop reads
