@@ -195,9 +195,12 @@ struct FusedCfg {
   __host__ __device__ static constexpr int64_t OFF(int l) {
     return l == 0 ? 0 : OFF(l - 1) + (int64_t)N(l - 1) * K(l - 1) * 2;
   }
+  // normalisation block (mu_x sig_x mu_y[OUTP] sig_y[OUTP]) padded to 16 bytes, so that the
+  // b / 6 + 1/2 table behind it is read with 16-byte loads
+  static constexpr int NRM = (2 + 2 * OUTP + 3) & ~3;
   static constexpr size_t smem = (size_t)XBUF * XBYTES + kTile * kH * 2 +
                                  (size_t)NBUF * kChunkBytes +
-                                 sizeof(float) * (6 * kH + OUTP + 2 + 2 * OUTP) + 64;
+                                 sizeof(float) * (6 * kH + OUTP + NRM) + 64;
 };
 
 // Fused forward over tiles of 128 rows, persistent (one CTA per SM, tiles strided by the grid).
@@ -222,6 +225,36 @@ struct FusedCfg {
 // (l + 1) % 2 for layer l - 1; epilogue l overwrites H only after the MMAs of layer l (the
 // readers of the previous H) completed. Every wait is bounded (1 s); a timed-out wait sets the
 // error word and makes every thread skip the remaining waits.
+// Two hard-swish outputs h = z * sat(acc / 6 + q), z = acc + b, with the packed FP32
+// instructions of sm_100-family GPUs (add/fma/mul .f32x2 round like their scalar forms; the
+// saturation has no packed form and is applied per lane).
+__device__ __forceinline__ void hswish_x2(uint32_t a0, uint32_t a1, float b0, float b1,
+                                          float q0, float q1, float& h0, float& h1, float& z0,
+                                          float& z1) {
+  uint32_t r0, r1, s0, s1;
+  asm("{\n\t.reg .b64 a, b, q, s, z, t, h;\n\t.reg .f32 t0, t1;\n\t"
+      "mov.b64 a, {%4, %5};\n\t"
+      "mov.b64 b, {%6, %7};\n\t"
+      "mov.b64 q, {%8, %9};\n\t"
+      "mov.b64 s, {%10, %10};\n\t"
+      "add.rn.f32x2 z, a, b;\n\t"
+      "fma.rn.f32x2 t, a, s, q;\n\t"
+      "mov.b64 {t0, t1}, t;\n\t"
+      "cvt.sat.f32.f32 t0, t0;\n\t"
+      "cvt.sat.f32.f32 t1, t1;\n\t"
+      "mov.b64 t, {t0, t1};\n\t"
+      "mul.rn.f32x2 h, z, t;\n\t"
+      "mov.b64 {%0, %1}, h;\n\t"
+      "mov.b64 {%2, %3}, z;\n\t}"
+      : "=r"(r0), "=r"(r1), "=r"(s0), "=r"(s1)
+      : "r"(a0), "r"(a1), "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)),
+        "r"(__float_as_uint(q0)), "r"(__float_as_uint(q1)), "r"(__float_as_uint(1.0f / 6.0f)));
+  h0 = __uint_as_float(r0);
+  h1 = __uint_as_float(r1);
+  z0 = __uint_as_float(s0);
+  z1 = __uint_as_float(s1);
+}
+
 template <int D, int MODE>
 __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
   using Cfg = FusedCfg<D>;
@@ -232,7 +265,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
   uint8_t* Wb = Hs + kTile * kH * 2;                 // NBUF x 16 KiB
   float* bs = reinterpret_cast<float*>(Wb + NBUF * kChunkBytes);  // b1 b2 b3 (3 x 256) + b4
   float* nrm = bs + 3 * kH + OUTP;                   // mu_x sig_x mu_y[OUTP] sig_y[OUTP]
-  float* bq = nrm + 2 + 2 * OUTP;                    // b / 6 + 1/2 of layers 1-3 (3 x 256)
+  float* bq = nrm + Cfg::NRM;                        // b / 6 + 1/2 of layers 1-3 (3 x 256)
   __shared__ __align__(8) uint64_t bar_w[NBUF], bar_f[NBUF], bar_x[2], bar_xf[2], bar_acc[2],
       bar_h[kNPass], bar_done;
   __shared__ uint32_t tslot;
@@ -437,13 +470,19 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
           const uint32_t* rr = r[pass & 1];
           float h[32];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < 32; i += 4) {
             // hard-swish of z = acc + b: z * clamp(z / 6 + 1/2, 0, 1), the clamp argument
-            // formed directly from the accumulator as acc / 6 + (b / 6 + 1/2)
-            const float acc = __uint_as_float(rr[i]);
-            const float z = acc + bl[cb + i];
-            h[i] = z * __saturatef(fmaf(acc, 1.0f / 6.0f, ql[cb + i]));
-            if (MODE == kModeBatch && myrow < p.M) p.Zs[layer][myrow * kH + cb + i] = z;
+            // formed directly from the accumulator as acc / 6 + (b / 6 + 1/2); two columns per
+            // packed FP32 instruction (same rounding as the scalar ones)
+            const float4 b4 = *reinterpret_cast<const float4*>(bl + cb + i);
+            const float4 q4 = *reinterpret_cast<const float4*>(ql + cb + i);
+            float z[4];
+            hswish_x2(rr[i], rr[i + 1], b4.x, b4.y, q4.x, q4.y, h[i], h[i + 1], z[0], z[1]);
+            hswish_x2(rr[i + 2], rr[i + 3], b4.z, b4.w, q4.z, q4.w, h[i + 2], h[i + 3], z[2],
+                      z[3]);
+            if (MODE == kModeBatch && myrow < p.M)
+#pragma unroll
+              for (int u = 0; u < 4; ++u) p.Zs[layer][myrow * kH + cb + i + u] = z[u];
           }
 #pragma unroll
           for (int q8 = 0; q8 < 4; ++q8) {
