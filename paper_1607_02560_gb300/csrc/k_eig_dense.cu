@@ -21,6 +21,7 @@ constexpr int kM = 125;    // |mu_0^2| in 3D
 constexpr int kNC = 35;    // classes
 constexpr int kT = 256;    // threads
 constexpr int kPowerIters = 80;
+constexpr int kDeflIters = 16;  // lambda_2 only decides the degeneracy flag
 
 // the class table of mu_0^2 - mu_0^2 (uint8 [125][125]), copied into shared memory per CTA
 __constant__ uint8_t c_cls125[kM * kM];
@@ -93,16 +94,16 @@ __global__ void __launch_bounds__(kT) k_eig_dense3(const double* __restrict__ gv
     for (int e = tid; e < 2 * kNC; e += kT)
       g[e % 2][e / 2] = gvals[(int64_t)e * cap + i];  // SoA [cls * 2 + f][cap]
     __syncthreads();
-    // ---- A = A1 - Gm Gm^T (upper triangle computed, mirrored) ----
-    for (int e = tid; e < kM * kM; e += kT) {
-      const int a = e / kM, b = e - a * kM;
-      if (a > b) continue;
-      double acc = g[1][cls[a * kM + b]];
+    // ---- A = A1 - Gm Gm^T: row a of Gm in registers of one warp's lanes, entries a <= b ----
+    for (int a = tid >> 5; a < kM; a += kT / 32) {
       const uint8_t* ca = cls + a * kM;
-      const uint8_t* cb = cls + b * kM;
-      for (int k = 0; k < kM; ++k) acc = fma(-g[0][ca[k]], g[0][cb[k]], acc);
-      A[a * kM + b] = acc;
-      A[b * kM + a] = acc;
+      for (int b = a + (tid & 31); b < kM; b += 32) {
+        const uint8_t* cb = cls + b * kM;
+        double acc = g[1][ca[b]];
+        for (int k = 0; k < kM; ++k) acc = fma(-g[0][ca[k]], g[0][cb[k]], acc);
+        A[a * kM + b] = acc;
+        A[b * kM + a] = acc;
+      }
     }
     __syncthreads();
     double tr = 0.0;
@@ -120,14 +121,15 @@ __global__ void __launch_bounds__(kT) k_eig_dense3(const double* __restrict__ gv
         w[j] = A[j * kM + k];         // column k
       }
       __syncthreads();
-      for (int e = tid; e < kM * kM; e += kT) {
-        const int r = e / kM, j = e - r * kM;
-        double val;
-        if (r == k)
-          val = j == k ? dinv : u[j];
-        else
-          val = j == k ? -w[r] * dinv : fma(-w[r], u[j], A[e]);
-        A[e] = val;
+      // one warp per row, lanes over the columns
+      for (int r = tid >> 5; r < kM; r += kT / 32) {
+        double* Ar = A + r * kM;
+        const double wr = w[r];
+        if (r == k) {
+          for (int j = tid & 31; j < kM; j += 32) Ar[j] = j == k ? dinv : u[j];
+        } else {
+          for (int j = tid & 31; j < kM; j += 32) Ar[j] = j == k ? -wr * dinv : fma(-wr, u[j], Ar[j]);
+        }
       }
       __syncthreads();
     }
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(kT) k_eig_dense3(const double* __restrict__ gv
       for (int a = tid; a < kM; a += kT) y[a] *= iy;
       __syncthreads();
     }
-    for (int it = 0; it < 40; ++it) {  // w = B y, projected off alpha before and after
+    for (int it = 0; it < kDeflIters; ++it) {  // w = B y, projected off alpha before and after
       matvec(A, y, w);
       __syncthreads();
       const double pr = dot(x, w, red);
