@@ -168,6 +168,48 @@ def test_full_size_n1024_solve_backward_error_and_determinism():
         assert abs(row - y[j]) <= 1e-13 * (np.abs(P.data[lo:hi]).sum() * np.abs(x2).max())
 
 
+def test_full_size_3d_n64_solve_backward_error():
+    """The 3D n = 64 workload (262 144 points, 24 GB of fronts, a root front of 12 097 points):
+    backward error of a refined solve from the oracle's sparse product, and sampled rows."""
+    n = 64
+    v = make_workload("schr3d_n64")
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="local")
+    ctx.nd_factor(refine_steps=1)
+    y = np.random.default_rng(5).standard_normal(n ** 3)
+    x = gpu_solve(ctx, y)
+    P = csr(ctx, "P", n ** 3)
+    b = backward_error(P, x, y)
+    print(f"3D n=64 refined backward error {b:.2e}")
+    assert b <= 1e-14
+    rng = np.random.default_rng(6)
+    for j in rng.choice(n ** 3, size=200, replace=False):
+        lo, hi = P.indptr[j], P.indptr[j + 1]
+        row = float(np.dot(P.data[lo:hi], x[P.indices[lo:hi]]))
+        assert abs(row - y[j]) <= 1e-13 * (np.abs(P.data[lo:hi]).sum() * np.abs(x).max())
+
+
+@pytest.mark.parametrize("wl", ["helm2d_n1024", "schr3d_n64"])
+def test_full_size_gmres_true_residual(wl):
+    """GMRES at the full workload sizes: converged, and the residual |f - (L + diag v) u| / |f|
+    the library reports equals the oracle's FFT evaluation of the same u."""
+    v = make_workload(wl)
+    n, d = v.shape[0], v.ndim
+    f = gaussian_source(n, d, 2.0)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="paper")
+    ctx.nd_factor()
+    u, res = ctx.gmres(f.reshape(-1))
+    r = f - O.apply_operator(v, u.reshape(v.shape))
+    rel = np.linalg.norm(r) / np.linalg.norm(f)
+    print(f"{wl}: {res}, oracle true residual {rel:.3e}")
+    assert res["converged"] == 1 and res["iterations"] <= 40
+    assert abs(rel - res["resid_true"]) <= 1e-6 * rel + 1e-14
+    assert res["resid_precond"] <= 1e-6
+
+
 def test_n512_refined_solve_matches_oracle():
     """2D n = 512 at 4 points per wavelength against the oracle's sparse-LU solve."""
     n = 512
