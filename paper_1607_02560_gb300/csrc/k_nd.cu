@@ -739,11 +739,11 @@ __device__ __forceinline__ void stage_block(const double* __restrict__ Fp, int f
   }
 }
 
-// Small fronts (f <= kNdSmallFront), one CTA per front: the block the product reads is staged
+// Fronts whose block fits in shared memory, one CTA per front: the block the product reads is staged
 // in shared memory with an odd row stride (conflict-free column access), then one thread per
 // row. Same sums in the same order as the warp-per-row kernels would not give; each kernel is
 // deterministic on its own.
-__global__ void __launch_bounds__(128) k_nd_fwd_small(const double* __restrict__ F, int f, int s,
+__global__ void __launch_bounds__(256) k_nd_fwd_small(const double* __restrict__ F, int f, int s,
                                                       int r, const int32_t* __restrict__ E,
                                                       const int32_t* __restrict__ perm,
                                                       const int32_t* __restrict__ inv,
@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(128) k_nd_fwd_small(const double* __restrict__
   }
 }
 
-__global__ void __launch_bounds__(128) k_nd_bwd_small(const double* __restrict__ F, int f, int s,
+__global__ void __launch_bounds__(256) k_nd_bwd_small(const double* __restrict__ F, int f, int s,
                                                       int r, const int32_t* __restrict__ E,
                                                       const int32_t* __restrict__ R,
                                                       const double* __restrict__ z,
@@ -1005,9 +1005,12 @@ cudaError_t launch_nd_solve(lsp_ctx* c, const double* y, double* x) {
     const int rows = rows_for(lv.count, lv.f);
     dim3 grid((lv.f + rows - 1) / rows, lv.count);
     int t = timer_begin(c, level_name("nd_fwd", d));
-    if (lv.f <= kNdSmallFront) {
-      const size_t sm = sizeof(double) * ((size_t)(lv.s | 1) * (lv.f + 1));
-      k_nd_fwd_small<<<lv.count, 128, sm, c->stream>>>(
+    // one CTA per front with the block staged in shared memory: small fronts, or larger ones
+    // when the depth has fronts enough to fill the GPU (else rows spread over many CTAs)
+    const size_t smf = sizeof(double) * ((size_t)(lv.s | 1) * (lv.f + 1));
+    const bool many = lv.count >= 2 * 152;
+    if (lv.f <= kNdSmallFront || (many && smf <= kNdStagedBytes)) {
+      k_nd_fwd_small<<<lv.count, lv.f <= kNdSmallFront ? 128 : 256, smf, c->stream>>>(
           Fb + lv.front_off, lv.f, lv.s, lv.r, E + lv.E_off,
           (const int32_t*)S.perm.p + lv.perm_off,
           lv.nchild ? (const int32_t*)S.inv.p + lv.inv_off : nullptr, lv.nchild,
@@ -1026,9 +1029,11 @@ cudaError_t launch_nd_solve(lsp_ctx* c, const double* y, double* x) {
     const int rows = rows_for(lv.count, lv.s);
     dim3 grid((lv.s + rows - 1) / rows, lv.count);
     int t = timer_begin(c, level_name("nd_bwd", d));
-    if (lv.f <= kNdSmallFront) {
-      const size_t sm = sizeof(double) * ((size_t)(lv.r | 1) * (lv.s + 1));
-      k_nd_bwd_small<<<lv.count, 128, sm, c->stream>>>(Fb + lv.front_off, lv.f, lv.s, lv.r,
+    const size_t smb = sizeof(double) * ((size_t)(lv.r | 1) * (lv.s + 1));
+    const bool many = lv.count >= 2 * 152;
+    if (lv.f <= kNdSmallFront || (many && smb <= kNdStagedBytes)) {
+      k_nd_bwd_small<<<lv.count, lv.s <= kNdSmallFront ? 128 : 256, smb, c->stream>>>(
+          Fb + lv.front_off, lv.f, lv.s, lv.r,
                                                        E + lv.E_off, R + lv.R_off,
                                                        z + lv.z_off, x);
     } else {
@@ -1042,8 +1047,10 @@ cudaError_t launch_nd_solve(lsp_ctx* c, const double* y, double* x) {
 }
 
 cudaError_t nd_prepare_kernels(int max_smem) {
-  // (s | 1) (f + 1) or (r | 1) (s + 1) doubles with s, r <= f <= kNdSmallFront
-  const int small = (int)sizeof(double) * ((kNdSmallFront | 1) + 1) * (kNdSmallFront + 1);
+  // staged solve kernels: (s | 1) (f + 1) or (r | 1) (s + 1) doubles, with s, r <= f <= 160
+  // for small fronts, and at most kNdStagedBytes for the larger ones
+  const int small_front = (int)sizeof(double) * ((kNdSmallFront | 1) + 1) * (kNdSmallFront + 1);
+  const int small = small_front > (int)kNdStagedBytes ? small_front : (int)kNdStagedBytes;
   cudaError_t e = cudaFuncSetAttribute(k_nd_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        max_smem);
   if (e != cudaSuccess) return e;
