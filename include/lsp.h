@@ -66,7 +66,7 @@ typedef enum {
 
 typedef struct {
   int t;               /* neighbourhood radius t of mu_j^t (Sec. 4.2): 1 (|mu| = 3^d), or 2    */
-                       /* in 2D (|mu| = 25; rows are 25 wide, see nd_leaf)                    */
+                       /* in 2D and 3D (|mu| = 5^d; rows are 5^d wide, see nd_leaf)           */
   int policy;          /* lsp_shift_policy                                                     */
   int nshifts;         /* PAPER: |S| before de-duplication; 0 selects n/16 (2D), n/4 (1D, 3D) */
   const double* shifts;/* LIST: nshifts shift values in host memory, each (4m+2) pi^2          */
@@ -79,8 +79,9 @@ typedef struct {
                        /* crosses no separator line x_a = 0 (mod b) of a nested dissection    */
                        /* with leaf boxes of width b (Sec. 4.2, figure of t choices: along an */
                        /* axis with r = x_a mod b > 0 the bound is min(r, b - r), on a        */
-                       /* separator it is b). Rows stay 25 wide: a t_j = 1 row fills its inner */
-                       /* 3 x 3 columns and holds zeros elsewhere; the CSR export omits them. */
+                       /* separator it is b). Rows stay 5^d wide: a t_j = 1 row fills its     */
+                       /* inner 3^d columns and holds zeros elsewhere; the CSR export omits   */
+                       /* them.                                                                */
 } lsp_stencil_opts;
 
 /* Fill *opts with the defaults: t=1, LOCAL policy, FP64, symmetric eigen-solve, no graph,
@@ -119,11 +120,11 @@ lsp_status lsp_set_potential(lsp_ctx* ctx, const double* v, int v_on_device);
  * Asynchronous on the context stream (except LIST/PAPER/MEAN, which upload a small shift list
  * from pinned host memory). Results stay on the device until read with lsp_get_rows(),
  * lsp_export_sparse_rows() or lsp_get_shift_table(). opts = NULL uses lsp_default_opts().
- * With t = 2 (2D) the same steps run on mu^2 (25 offsets; g_s at offsets up to 4) and, when
+ * With t = 2 the same steps run on mu^2 (5^d offsets; g_s at offsets up to 4) and, when
  * nd_leaf > 0, also on mu^1 for the points with t_j = 1 (Sec. 4.2).
  * Errors: LSP_ERR_STATE without a potential; LSP_ERR_ARG for bad options or an off-lattice
  * LIST shift; LSP_ERR_RESONANT_SHIFT for a LIST shift equal to -4 pi^2 |k|^2 for a k in K;
- * LSP_ERR_UNSUPPORTED for t = 2 in 3D or with the LEARNED mode.
+ * LSP_ERR_UNSUPPORTED for t = 2 in 1D, for n < 8, or with the LEARNED mode.
  */
 lsp_status lsp_build_stencils(lsp_ctx* ctx, const lsp_stencil_opts* opts);
 
@@ -145,7 +146,7 @@ lsp_status lsp_get_rows(lsp_ctx* ctx, char which, double* rows, int on_device);
 /*
  * Export Q, C or P as CSR in host memory: rowptr[n^d + 1] (int64), colidx[nnz] (int32),
  * vals[nnz] (float64), nnz = n^d |mu| (t = 2 builds with nd_leaf > 0: the sum over points
- * of (2 t_j + 1)^2). Column indices of a row follow the mu_j^{t_j} offset order, so they are
+ * of (2 t_j + 1)^d). Column indices of a row follow the mu_j^{t_j} offset order, so they are
  * not sorted where the neighbourhood wraps around the periodic boundary.
  * With rowptr, colidx and vals all NULL only *nnz_out is written (size query). Waits for the
  * copies before returning.
@@ -156,7 +157,7 @@ lsp_status lsp_export_sparse_rows(lsp_ctx* ctx, char which, int64_t* rowptr, int
 /*
  * Read the per-shift table of the last build into host memory (Sec. 4.1: one stencil per
  * shift, shared by every point that uses that shift). *nshifts_out receives |S|. For a t = 2
- * build the table holds the t = 2 stencils (|mu| = 25).
+ * build the table holds the t = 2 stencils (|mu| = 5^d).
  * Any output pointer may be NULL. s[|S|] shift values (increasing), alpha[|S| x |mu|],
  * c[|S| x |mu|], lam[|S| x 2] = (lambda_1, lambda_2) of A, flags[|S|] (LSP_FLAG_* bits),
  * s_idx[n^d] = index into s of each point's shift s_j. Waits before returning.
@@ -262,7 +263,7 @@ lsp_status lsp_apply_operator_noalloc(int d, int n, const double* v_dev, const d
  * P = Q + C diag(v - s) has the sparsity of Q, so P^-1 is applied through a nested-dissection
  * factorisation, and (L + diag v) u = f is solved by GMRES left-preconditioned with P^-1 C.
  * 2D grids (n a power of two, 4 <= n <= 1024) and 3D grids (4 <= n <= 64); rows of a t = 1
- * build, or of a 2D t = 2 build with nd_leaf = b (the t_j rule keeps every row inside the
+ * build, or of a t = 2 build with nd_leaf = b (the t_j rule keeps every row inside the
  * separators of that dissection).
  *
  * Elimination tree: the root separator {x : some x_a = 0} last; before it, the boxes of the
@@ -307,7 +308,7 @@ void lsp_default_nd_opts(lsp_nd_opts* opts);
 lsp_status lsp_nd_factor(lsp_ctx* ctx, const lsp_nd_opts* opts);
 
 /* Host only (no context, no device): plan the dissection of the n^d grid (d = 2, 3) with leaf
- * b for the rows of a t = 1 build (t = 1) or of a 2D t = 2 build with nd_leaf (t = 2) and report
+ * b for the rows of a t = 1 build (t = 1) or of a t = 2 build with nd_leaf (t = 2) and report
  * its sizes; the first `cap` depths (0 = the root separator) also give their front count and
  * |E|, |R| in count[], s[], r[] (any may be NULL). LSP_ERR_UNSUPPORTED with the reason in err
  * (errcap bytes) when the rows or sizes do not fit; LSP_ERR_ARG for d outside {2, 3}, t outside

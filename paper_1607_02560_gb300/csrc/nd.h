@@ -62,8 +62,8 @@ struct NdPlan {
 };
 
 // Builds the plan for rows of width mu on the periodic n^d grid (d = 2, 3; t_built = 1: 3^d
-// rows; t_built = 2, 2D only: 5 x 5 rows, of which point j uses its core from the leaf-leaf_t
-// rule). Returns "" or the reason the rows or sizes do not fit the dissection.
+// rows; t_built = 2: 5^d rows, of which point j uses its core from the leaf-leaf_t rule).
+// Returns "" or the reason the rows or sizes do not fit the dissection.
 std::string build_nd_plan(NdPlan& p, int d, int n, int leaf, int t_built, int leaf_t, int mu);
 
 struct NdState {

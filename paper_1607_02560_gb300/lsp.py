@@ -258,7 +258,7 @@ class Context:
     def build_stencils(self, policy="local", nshifts=0, shifts=None, mode="fp64",
                        refine_steps=0, eig_method="symmetric", use_graph=False, t=1,
                        nd_leaf=0):
-        """Steps a2-a7 (asynchronous on the context stream). t = 2 (2D) builds 25-wide rows;
+        """Steps a2-a7 (asynchronous on the context stream). t = 2 builds 5^d-wide rows;
         nd_leaf > 0 gives each point t_j from a nested dissection with that leaf width."""
         o = StencilOpts()
         o.t = t
