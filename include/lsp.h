@@ -266,9 +266,12 @@ lsp_status lsp_apply_operator_noalloc(int d, int n, const double* v_dev, const d
  * build, or of a t = 2 build with nd_leaf = b (the t_j rule keeps every row inside the
  * separators of that dissection).
  *
- * Elimination tree: the root separator {x : some x_a = 0} last; before it, the boxes of the
- * remaining open square (cube), each split through the middle grid line (plane) of its longest
- * side down to leaf boxes of at most (b - 1)^d points. Every separator lies on x_a = 0 (mod b).
+ * Elimination tree: in 2D (and in 3D with n < 2b) the root separator {x : some x_a = 0} last,
+ * before it the boxes of the remaining open square (cube); in 3D with n >= 2b the plane pairs
+ * {x_a = 0} U {x_a = n/2} of axes 0, 1, 2 at depths 0, 1, 2 (two children per node), before them
+ * the eight open cubes. Each open box is split through the middle grid line (plane) of its
+ * longest side down to leaf boxes of at most (b - 1)^d points. Every separator lies on
+ * x_a = 0 (mod b).
  * Each front (eliminated set E, ring R of ancestors' points) is inverted on E in place with row
  * pivoting inside E; the figure of Sec. 3 groups the separators into edges and vertices
  * instead, with the same leaf boxes and the same separator lines. */

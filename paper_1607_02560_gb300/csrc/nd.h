@@ -3,13 +3,17 @@
 // Fig. nd; Table cost: T_NDsetup, T_NDapp), and the Krylov solve that uses it (Sec. 5: GMRES
 // with restart 40, relative tolerance 1e-6, left-preconditioned by P^-1 C).
 //
-// Elimination tree of the periodic n x n grid (n = 2^p, leaf width b = 2^q):
-//  - depth 0: the cross {x_0 = 0} U {x_1 = 0}; removing it leaves the open square [1, n)^2;
-//  - depth 1..: boxes of (2^k - 1) x (2^l - 1) points, split through their middle line (the
-//    longer side first) into two halves; the separator line is the node's eliminated set;
-//  - leaves: boxes of at most (b - 1) x (b - 1) points, all eliminated at once.
-// Every separator is a grid line x_a = 0 (mod b), so rows whose neighbourhood crosses no such
-// line (t = 1 everywhere, or t_j from the leaf-b rule of Sec. 4.2) keep the dissection exact.
+// Elimination tree of the periodic grid (n = 2^p, leaf width b = 2^q):
+//  - 2D (and 3D with n < 2b): depth 0 is the cross {some x_a = 0}; removing it leaves the open
+//    square (cube) [1, n)^d;
+//  - 3D with n >= 2b: depths 0, 1, 2 open one axis each: a node's points on the plane pair
+//    {x_a = 0} U {x_a = n/2} are its eliminated set, its children the two halves
+//    [1, n/2) and [n/2 + 1, n) along that axis; after three depths the nodes are open cubes;
+//  - then: open boxes of (2^k - 1) points per side, split through their middle line (plane),
+//    the longest side first, into two halves; the separator is the node's eliminated set;
+//  - leaves: boxes of at most (b - 1)^d points, all eliminated at once.
+// Every separator lies on x_a = 0 (mod b), so rows whose neighbourhood crosses no such line
+// (t = 1 everywhere, or t_j from the leaf-b rule of Sec. 4.2) keep the dissection exact.
 //
 // A front holds the eliminated set E (|E| = s) followed by the ring R of its box (|R| = r):
 // the points of ancestors' separators adjacent to the box. Its f x f matrix (f = s + r,
@@ -38,7 +42,7 @@ constexpr int kNdPanelRegRows = 8 * 256;  // panels up to this many rows keep th
 struct NdLevel {
   int count = 0;       // fronts at this depth
   int s = 0, r = 0, f = 0;
-  int nchild = 0;      // children per front: 2, 1 (the cross), 0 (leaves)
+  int nchild = 0;      // children per front: 2, 1 (the cross root), 0 (leaves)
   int64_t front_off = 0;          // doubles into the front buffer (count * f * f)
   int64_t E_off = 0, R_off = 0;   // int32 offsets into E (count * s) and R (count * r)
   int64_t inv_off = 0;            // int32 offset into inv (count * f * 2)
@@ -49,7 +53,7 @@ struct NdLevel {
 
 struct NdPlan {
   int d = 2, n = 0, leaf = 0, mu = 0, t_built = 1, leaf_t = 0;
-  std::vector<NdLevel> lv;  // lv[0]: the cross; lv.back(): the leaves
+  std::vector<NdLevel> lv;  // lv[0]: the root separator; lv.back(): the leaves
   // E, R: grid indices of every front's eliminated set and ring, front after front.
   // inv[(front * f + i) * 2 + c]: position of front position i in child c's ring, or -1.
   // asm_dst / asm_src: P entry rows[src] goes to element dst of its depth's front block.

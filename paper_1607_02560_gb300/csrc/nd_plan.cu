@@ -11,8 +11,9 @@ namespace lsp {
 namespace {
 
 struct Box {
-  int lo[3], len[3];  // points lo[a] .. lo[a] + len[a] - 1 on axis a, inside [1, n)^d
-  bool cross;
+  int lo[3], len[3];  // points lo[a] .. lo[a] + len[a] - 1 on axis a
+  bool cross;         // the 2D (or small 3D) root: every point with a zero coordinate
+  bool per[3];        // axis still periodic: lo = 0, len = n, no end on that axis
 };
 
 inline int wrapi(int a, int n) {
@@ -68,10 +69,29 @@ std::string build_nd_plan(NdPlan& P, int d, int n, int leaf, int t_built, int le
     }
   };
 
-  // ---- the tree, breadth first: children of front k at depth e are 2k, 2k+1 at depth e+1.
-  // A box is split through the middle plane of its longest side (the first such axis).
+  // ---- the tree, breadth first: children of front k at depth e are 2k, 2k+1 at depth e+1
+  // (the cross has one child). The periodic grid is opened first:
+  //  - 2D, or 3D with n < 2b: the root is the cross {some x_a = 0}, its child the open box
+  //    [1, n)^d;
+  //  - 3D with n >= 2b: one axis per depth, the node's points on the plane pair
+  //    {x_a = 0} U {x_a = n/2} (both on multiples of b), children [1, n/2) and [n/2 + 1, n)
+  //    on that axis. The separators are the cross's planes and the first middle planes of the
+  //    open cube, grouped as 2 n^2, 2 x 2 (n/2 - 1) n, 4 x 2 (n/2 - 1)^2 points instead of
+  //    3 n^2 - 3 n + 1, (n - 1)^2, 2 x (n/2 - 1)(n - 1), 4 x (n/2 - 1)^2: the root front
+  //    shrinks from 3 n^2 to 2 n^2 points and one depth of large fronts disappears, about a
+  //    third of the factorisation's flops at n = 64 (in 2D the two groupings cost the same).
+  // An open box is split through the middle plane of its longest side (the first such axis).
   std::vector<std::vector<Box>> boxes;
-  {
+  const bool pairs = d == 3 && n >= 2 * leaf;
+  if (pairs) {
+    Box root{};
+    for (int a = 0; a < d; ++a) {
+      root.lo[a] = 0;
+      root.len[a] = n;
+      root.per[a] = true;
+    }
+    boxes.push_back({root});
+  } else {
     Box cross{};
     cross.cross = true;
     boxes.push_back({cross});
@@ -82,12 +102,20 @@ std::string build_nd_plan(NdPlan& P, int d, int n, int leaf, int t_built, int le
     }
     boxes.push_back({root});
   }
+  auto periodic_axis = [&](const Box& b) {
+    for (int a = 0; a < d; ++a)
+      if (b.per[a]) return a;
+    return -1;
+  };
   auto is_leaf_box = [&](const Box& b) {
+    if (periodic_axis(b) >= 0) return false;
     for (int a = 0; a < d; ++a)
       if (b.len[a] > leaf - 1) return false;
     return true;
   };
   auto split_axis = [&](const Box& b) {
+    const int pa = periodic_axis(b);
+    if (pa >= 0) return pa;
     int ax = 0;
     for (int a = 1; a < d; ++a)
       if (b.len[a] > b.len[ax]) ax = a;
@@ -97,11 +125,19 @@ std::string build_nd_plan(NdPlan& P, int d, int n, int leaf, int t_built, int le
     std::vector<Box> next;
     next.reserve(boxes.back().size() * 2);
     for (const Box& b : boxes.back()) {
-      const int ax = split_axis(b), half = (b.len[ax] - 1) / 2;
+      const int ax = split_axis(b);
       Box c0 = b, c1 = b;
-      c0.len[ax] = half;
-      c1.len[ax] = half;
-      c1.lo[ax] = b.lo[ax] + half + 1;
+      if (b.per[ax]) {
+        c0.per[ax] = c1.per[ax] = false;
+        c0.lo[ax] = 1;
+        c1.lo[ax] = n / 2 + 1;
+        c0.len[ax] = c1.len[ax] = n / 2 - 1;
+      } else {
+        const int half = (b.len[ax] - 1) / 2;
+        c0.len[ax] = half;
+        c1.len[ax] = half;
+        c1.lo[ax] = b.lo[ax] + half + 1;
+      }
       next.push_back(c0);
       next.push_back(c1);
     }
@@ -136,6 +172,15 @@ std::string build_nd_plan(NdPlan& P, int d, int n, int leaf, int t_built, int le
       }
     } else if (is_leaf) {
       for_box(b.lo, b.len, [&](const int* x) { out.push_back(gidx(x)); });
+    } else if (periodic_axis(b) >= 0) {  // the plane pair {x_ax = 0} U {x_ax = n/2}
+      const int ax = periodic_axis(b);
+      int lo[3] = {b.lo[0], b.lo[1], d == 3 ? b.lo[2] : 0};
+      int len[3] = {b.len[0], b.len[1], d == 3 ? b.len[2] : 1};
+      len[ax] = 1;
+      for (int plane : {0, n / 2}) {
+        lo[ax] = plane;
+        for_box(lo, len, [&](const int* x) { out.push_back(gidx(x)); });
+      }
     } else {
       const int ax = split_axis(b);
       int lo[3] = {b.lo[0], b.lo[1], d == 3 ? b.lo[2] : 0};
@@ -145,13 +190,17 @@ std::string build_nd_plan(NdPlan& P, int d, int n, int leaf, int t_built, int le
       for_box(lo, len, [&](const int* x) { out.push_back(gidx(x)); });
     }
   };
-  // the ring of a box: the points of its enlarged box [lo - 1, lo + len] outside it, wrapped,
-  // in lexicographic order of the enlarged box, first copy kept
+  // the ring of a box: the points of its enlarged box [lo - 1, lo + len] (not enlarged along a
+  // periodic axis) outside it, wrapped, in lexicographic order of the enlarged box, first copy
+  // kept
   auto R_of = [&](const Box& b, std::vector<int32_t>& out) {
     if (b.cross) return;
     ++tag;
-    int lo[3] = {b.lo[0] - 1, b.lo[1] - 1, d == 3 ? b.lo[2] - 1 : 0};
-    int len[3] = {b.len[0] + 2, b.len[1] + 2, d == 3 ? b.len[2] + 2 : 1};
+    int lo[3] = {0, 0, 0}, len[3] = {1, 1, 1};
+    for (int a = 0; a < d; ++a) {
+      lo[a] = b.per[a] ? b.lo[a] : b.lo[a] - 1;
+      len[a] = b.per[a] ? b.len[a] : b.len[a] + 2;
+    }
     for_box(lo, len, [&](const int* x) {
       bool inside = true;
       for (int a = 0; a < d; ++a) inside = inside && x[a] >= b.lo[a] && x[a] < b.lo[a] + b.len[a];
@@ -170,7 +219,7 @@ std::string build_nd_plan(NdPlan& P, int d, int n, int leaf, int t_built, int le
     NdLevel& lv = P.lv[e];
     const bool is_leaf = e == L - 1;
     lv.count = (int)boxes[e].size();
-    lv.nchild = is_leaf ? 0 : (e == 0 ? 1 : 2);
+    lv.nchild = is_leaf ? 0 : (boxes[e][0].cross ? 1 : 2);
     lv.E_off = (int64_t)P.E.size();
     lv.R_off = (int64_t)P.R.size();
     for (int k = 0; k < lv.count; ++k) {

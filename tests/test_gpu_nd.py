@@ -169,7 +169,7 @@ def test_full_size_n1024_solve_backward_error_and_determinism():
 
 
 def test_full_size_3d_n64_solve_backward_error():
-    """The 3D n = 64 workload (262 144 points, 24 GB of fronts, a root front of 12 097 points):
+    """The 3D n = 64 workload (262 144 points, 20 GB of fronts, a root front of 8192 points):
     backward error of a refined solve from the oracle's sparse product, and sampled rows."""
     n = 64
     v = make_workload("schr3d_n64")
@@ -294,8 +294,9 @@ def test_gmres_n256_matches_oracle(policy):
 
 @pytest.mark.parametrize("n,leaf", [(8, 4), (8, 8), (16, 4), (16, 8), (32, 8)])
 def test_nd_solve_3d_matches_oracle(n, leaf):
-    """3D (27-point rows): the root planes, plane separators and cubic leaves; n = 32 runs the
-    root's 2977 pivots through the panel kernel for more than 2048 rows."""
+    """3D (27-point rows): plane-pair separators (n >= 2b) or the three-plane root (n = b),
+    middle-plane separators and cubic leaves. Panels of more than 2048 rows (the n = 64 root
+    and its two slab fronts) run in the full-size tests."""
     v = make_workload("schr3d_n64", n=n)
     ctx = ctx_for(v)
     ctx.set_potential(v)

@@ -76,20 +76,37 @@ def test_plans_that_do_not_fit_are_refused(args, msg):
 
 
 def test_3d_n8_leaf4_by_hand():
-    # root: the points with a zero coordinate, 8^3 - 7^3 = 169; root box 7^3 split by its middle
-    # plane x_0 = 4: 49 points, ring = all 169 root points; boxes 3 x 7 x 7 split by x_1 = 4:
-    # 21 points, ring 5 * 8 * 8 - 147 = 173 (the enlarged box wraps in x_1 and x_2); boxes
-    # 3 x 3 x 7 split by x_2 = 4: 9 points, ring 5 * 5 * 8 - 63 = 137; leaves 3^3, ring 5^3 - 27
+    # n >= 2b: the torus is opened one axis per depth by the plane pair {x_a = 0} U {x_a = 4}.
+    # root: 2 * 8^2 = 128 points; slabs [1, 4) x 8 x 8 (two of them): their points on x_1 = 0, 4,
+    # 2 * 3 * 8 = 48, ring = both x_0 planes, 128; bars [1, 4)^2 x 8: their points on x_2 = 0, 4,
+    # 2 * 3 * 3 = 18, ring 5 * 5 * 8 - 3 * 3 * 8 = 128; leaves 3^3, ring 5^3 - 27 = 98
     info = lsp.nd_plan_info(8, 4, d=3)
-    assert info["depths"] == [(1, 169, 0), (1, 49, 169), (2, 21, 173), (4, 9, 137), (8, 27, 98)]
+    assert info["depths"] == [(1, 128, 0), (2, 48, 128), (4, 18, 128), (8, 27, 98)]
+    # flops from the hand-derived sizes: 2 s (s + r)^2 per front
+    sweep = 2.0 * (128 ** 3 + 2 * 48 * 176 ** 2 + 4 * 18 * 146 ** 2 + 8 * 27 * 125 ** 2)
+    assert info["flops"] == pytest.approx(sweep, rel=1e-15)
 
 
-@pytest.mark.parametrize("n,leaf", [(8, 4), (16, 8), (32, 4)])
+def test_3d_n8_leaf8_keeps_the_three_plane_root():
+    # n < 2b: the root is every point with a zero coordinate, 8^3 - 7^3 = 169, and its one child
+    # the open cube 7^3, a single leaf whose ring is the whole root
+    info = lsp.nd_plan_info(8, 8, d=3)
+    assert info["depths"] == [(1, 169, 0), (1, 343, 169)]
+
+
+@pytest.mark.parametrize("n,leaf", [(8, 4), (16, 8), (32, 4), (16, 16)])
 def test_3d_every_point_is_eliminated_once(n, leaf):
     info = lsp.nd_plan_info(n, leaf, d=3)
     depths = info["depths"]
     assert sum(c * s for c, s, _ in depths) == n ** 3
-    assert depths[0] == (1, n ** 3 - (n - 1) ** 3, 0)
+    if n >= 2 * leaf:
+        # plane pairs: 2 n^2, then 2 x 2 (n/2 - 1) n, then 4 x 2 (n/2 - 1)^2, then the open
+        # cubes (n/2 - 1)^3 split by their middle planes
+        h = n // 2 - 1
+        assert depths[:3] == [(1, 2 * n * n, 0), (2, 2 * h * n, 2 * n * n),
+                              (4, 2 * h * h, (h + 2) ** 2 * n - h * h * n)]
+    else:
+        assert depths[0] == (1, n ** 3 - (n - 1) ** 3, 0)
     assert depths[-1][1] == (leaf - 1) ** 3
     sweep = sum(c * 2.0 * s * (s + r) ** 2 for c, s, r in depths)
     assert info["flops"] == pytest.approx(sweep, rel=1e-12)
