@@ -270,19 +270,40 @@ def run_ours(args):
         # ---- end to end through the public API with host buffers ----
         v_pin = torch.empty(v_host.shape, dtype=torch.float64, pin_memory=True)
         v_pin.copy_(torch.from_numpy(v_host))
-        outs = [torch.empty((N, mu), dtype=torch.float64, pin_memory=True).numpy()
-                for _ in range(3)]
+        outs = [[torch.empty((N, mu), dtype=torch.float64, pin_memory=True).numpy()
+                 for _ in range(3)] for _ in range(2)]
+        e2e_steps = max(3, args.steps // 2)
+        # (a) one step at a time: v in, build, the three row blocks out, waited for
         e2e_ms = []
-        for k in range(max(3, args.steps // 2) + 1):
+        for k in range(e2e_steps + 1):
             flush.zero_()
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             ctx.set_potential(v_pin.numpy())
             ctx.build_stencils(policy=args.policy, mode=args.mode, use_graph=True)
-            for which, o in zip("QCP", outs):
+            for which, o in zip("QCP", outs[0]):
                 ctx.get_rows(which, o)
             e2e_ms.append((time.perf_counter() - t1) * 1e3)
         e2e_ms = e2e_ms[1:]
+        # (b) serving loop: step k's rows go to the host (get_rows_async, the library's copy
+        # stream) while step k + 1 builds; two host buffer sets alternate. The L2 flush runs
+        # inside the timed region, and the region ends when the last step's rows have landed.
+        def serve(k):
+            flush.zero_()
+            ctx.set_potential(v_pin.numpy())
+            ctx.build_stencils(policy=args.policy, mode=args.mode, use_graph=True)
+            for which, o in zip("QCP", outs[k & 1]):
+                ctx.get_rows_async(which, o)
+        serve(0)
+        serve(1)
+        ctx.wait_rows()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for k in range(e2e_steps):
+            serve(k)
+        ctx.wait_rows()
+        torch.cuda.synchronize()
+        serve_ms = (time.perf_counter() - t1) * 1e3 / e2e_steps
 
     if rank != 0:
         if ws > 1:
@@ -347,9 +368,16 @@ def run_ours(args):
         "gpu_launches": launches,
         "wall_s_timed_region": wall,
         "clocks": clk,
-        "e2e": {"value": N / (float(np.median(e2e_ms)) * 1e-3), "unit": "stencils/s",
+        "e2e": {"value": N / (serve_ms * 1e-3), "unit": "stencils/s",
                 "h2d_bytes_per_step": int(N * 8), "d2h_bytes_per_step": int(3 * N * mu * 8),
-                "ms_per_step": float(np.median(e2e_ms))},
+                "ms_per_step": serve_ms,
+                "loop": "set_potential from pinned host memory, build, get_rows_async of Q, C, "
+                        "P into pinned host memory (step k's copies overlap step k + 1's "
+                        "build); L2 flush inside the region; ends after the last copy landed",
+                "one_step_at_a_time": {"value": N / (float(np.median(e2e_ms)) * 1e-3),
+                                       "ms_per_step": float(np.median(e2e_ms)),
+                                       "loop": "each step's host copies waited for before "
+                                               "the next step starts (get_rows)"}},
     }
     if train_info is not None:
         out["config"]["training"] = train_info

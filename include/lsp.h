@@ -144,6 +144,24 @@ lsp_status lsp_apply_operator(lsp_ctx* ctx, const double* u_dev, double* y_dev);
 lsp_status lsp_get_rows(lsp_ctx* ctx, char which, double* rows, int on_device);
 
 /*
+ * Start copying the row block of Q, C or P of the last build (layout as lsp_get_rows) into
+ * host memory rows_host, and return without waiting. The block is first copied on the device
+ * (a staging copy, stream-ordered on the context stream after the build); the host copy then
+ * runs on a second stream of the context, so the next set_potential and build may proceed
+ * while it is in flight (a serving loop overlaps step k's host copy with step k + 1's build).
+ * A later call for the same block waits for the previous one's host copy before reusing the
+ * staging copy. rows_host must stay valid and untouched until lsp_wait_rows() returns; page-
+ * locked memory (cudaHostAlloc or cudaHostRegister) is needed for the copy to be asynchronous.
+ * The staging copies take 3 n^d |mu| doubles of device memory, allocated on first use.
+ * Errors: LSP_ERR_ARG (NULL rows_host, bad which), LSP_ERR_STATE before a build,
+ * LSP_ERR_OOM, LSP_ERR_CUDA.
+ */
+lsp_status lsp_get_rows_async(lsp_ctx* ctx, char which, double* rows_host);
+
+/* Wait until every copy started by lsp_get_rows_async() has landed in host memory. */
+lsp_status lsp_wait_rows(lsp_ctx* ctx);
+
+/*
  * Export Q, C or P as CSR in host memory: rowptr[n^d + 1] (int64), colidx[nnz] (int32),
  * vals[nnz] (float64), nnz = n^d |mu| (t = 2 builds with nd_leaf > 0: the sum over points
  * of (2 t_j + 1)^d). Column indices of a row follow the mu_j^{t_j} offset order, so they are

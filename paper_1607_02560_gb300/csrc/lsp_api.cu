@@ -538,6 +538,15 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
 lsp_status lsp_destroy(lsp_ctx* c) {
   if (!c) return LSP_OK;
   cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) {
+    cudaStreamSynchronize(c->copy_stream);
+    cudaStreamDestroy(c->copy_stream);
+  }
+  for (int k = 0; k < 3; ++k) {
+    if (c->stage[k].p) cudaFree(c->stage[k].p);
+    if (c->ev_staged[k]) cudaEventDestroy(c->ev_staged[k]);
+    if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+  }
   DevBuf* bufs[] = {&c->v, &c->stats_part, &c->stats, &c->xtab, &c->xtab32, &c->shift_m, &c->shift_flag,
                     &c->idx_of, &c->counts, &c->wtab, &c->gvals, &c->alpha, &c->cst, &c->lam,
                     &c->sflags, &c->Q, &c->C, &c->P, &c->sidx, &c->colidx, &c->rowptr,
@@ -867,6 +876,42 @@ lsp_status lsp_get_rows(lsp_ctx* c, char which, double* rows, int on_device) {
                              on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              c->stream));
   if (!on_device) CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  return LSP_OK;
+}
+
+lsp_status lsp_get_rows_async(lsp_ctx* c, char which, double* rows) {
+  if (!c) return LSP_ERR_ARG;
+  if (!rows) return fail(c, LSP_ERR_ARG, "rows is NULL");
+  const double* src;
+  lsp_status st = rows_of(c, which, &src);
+  if (st != LSP_OK) return st;
+  const int w = which == 'Q' ? 0 : which == 'C' ? 1 : 2;
+  const size_t bytes = sizeof(double) * built_mu(c) * c->geo.N;
+  if (!c->copy_stream) {
+    CUDA_OK(c, cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+    for (int k = 0; k < 3; ++k) {
+      CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_staged[k], cudaEventDisableTiming));
+      CUDA_OK(c, cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming));
+    }
+  }
+  if (c->stage[w].bytes < bytes) {
+    CUDA_OK(c, cudaStreamSynchronize(c->copy_stream));  // the old staging copy may be in use
+    if (!ensure(c, c->stage[w], bytes)) return LSP_ERR_OOM;
+  }
+  // the staging copy of this block is free again once its previous host copy has landed
+  CUDA_OK(c, cudaStreamWaitEvent(c->stream, c->ev_copied[w], 0));
+  CUDA_OK(c, cudaMemcpyAsync(c->stage[w].p, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  CUDA_OK(c, cudaEventRecord(c->ev_staged[w], c->stream));
+  CUDA_OK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_staged[w], 0));
+  CUDA_OK(c, cudaMemcpyAsync(rows, c->stage[w].p, bytes, cudaMemcpyDeviceToHost,
+                             c->copy_stream));
+  CUDA_OK(c, cudaEventRecord(c->ev_copied[w], c->copy_stream));
+  return LSP_OK;
+}
+
+lsp_status lsp_wait_rows(lsp_ctx* c) {
+  if (!c) return LSP_ERR_ARG;
+  if (c->copy_stream) CUDA_OK(c, cudaStreamSynchronize(c->copy_stream));
   return LSP_OK;
 }
 

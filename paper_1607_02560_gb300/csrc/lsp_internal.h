@@ -119,6 +119,13 @@ struct lsp_ctx {
 
   // rows (a7) and export
   lsp::DevBuf Q, C, P, sidx, colidx, rowptr, expvals;
+  // asynchronous host copies of the rows (lsp_get_rows_async): a device staging copy per block
+  // (Q, C, P), taken on the context stream, is sent to the host on copy_stream, so that the next
+  // build may overwrite the rows while the host copy is still in flight
+  lsp::DevBuf stage[3];
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_staged[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ev_copied[3] = {nullptr, nullptr, nullptr};
 
   // FFT (apply_operator)
   lsp::DevBuf fftbuf, twiddle;

@@ -92,6 +92,8 @@ def lib() -> ctypes.CDLL:
         "lsp_build_stencils": (ctypes.c_int, [vp, ctypes.POINTER(StencilOpts)]),
         "lsp_apply_operator": (ctypes.c_int, [vp, vp, vp]),
         "lsp_get_rows": (ctypes.c_int, [vp, ctypes.c_char, vp, ctypes.c_int]),
+        "lsp_get_rows_async": (ctypes.c_int, [vp, ctypes.c_char, vp]),
+        "lsp_wait_rows": (ctypes.c_int, [vp]),
         "lsp_export_sparse_rows": (ctypes.c_int, [vp, ctypes.c_char, vp, vp, vp, i64p]),
         "lsp_get_shift_table": (ctypes.c_int, [vp, i64p, vp, vp, vp, vp, vp, vp]),
         "lsp_get_sizes": (ctypes.c_int, [vp, i64p, ctypes.POINTER(ctypes.c_int)]),
@@ -222,6 +224,7 @@ class Context:
         lib().lsp_get_sizes(self.h, ctypes.byref(N), ctypes.byref(mu))
         self.N = N.value
         self._keep = None
+        self._pending_rows = []  # host buffers of copies in flight (get_rows_async)
 
     @property
     def mu(self) -> int:
@@ -237,8 +240,9 @@ class Context:
 
     def close(self):
         if getattr(self, "h", None):
-            lib().lsp_destroy(self.h)
+            lib().lsp_destroy(self.h)  # waits for the copies in flight
             self.h = None
+            self._pending_rows = []
 
     def __del__(self):
         try:
@@ -293,6 +297,25 @@ class Context:
         self._check(lib().lsp_get_rows(self.h, which.encode(), _ptr(out), _on_device(out)),
                     "get_rows")
         return out
+
+    def get_rows_async(self, which: str, out):
+        """Start copying the rows of Q, C or P into the host array `out` (numpy array or CPU
+        torch tensor of n^d x |mu| float64; pinned memory for the copy to overlap the next
+        build) and return at once. `out` is kept alive until wait_rows()."""
+        if _on_device(out):
+            raise ValueError("get_rows_async copies into host memory; use get_rows for device")
+        nbytes = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+        if nbytes < 8 * self.N * self.mu:
+            raise ValueError(f"out holds {nbytes} bytes, the rows need {8 * self.N * self.mu}")
+        self._check(lib().lsp_get_rows_async(self.h, which.encode(), _ptr(out)),
+                    "get_rows_async")
+        self._pending_rows.append(out)
+        return out
+
+    def wait_rows(self):
+        """Wait until every copy started by get_rows_async() has landed."""
+        self._check(lib().lsp_wait_rows(self.h), "wait_rows")
+        self._pending_rows.clear()
 
     def export_sparse_rows(self, which: str):
         """(rowptr int64, colidx int32, vals float64) in host memory."""

@@ -44,6 +44,8 @@ def test_null_context_is_rejected(L):
     assert L.lsp_set_potential(None, None, 0) == 1
     assert L.lsp_build_stencils(None, None) == 1
     assert L.lsp_synchronize(None) == 1
+    assert L.lsp_get_rows_async(None, b"Q", None) == 1
+    assert L.lsp_wait_rows(None) == 1
     assert L.lsp_last_error(None) == b"null context"
 
 

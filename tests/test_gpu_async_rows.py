@@ -1,0 +1,87 @@
+"""Asynchronous host copies of the rows (lsp_get_rows_async, lsp_wait_rows).
+
+Copies started after one build and still in flight while the next builds run must deliver the
+rows of their own build: bit for bit the rows a synchronous lsp_get_rows returns right after
+that build (the rows themselves are checked against the oracle in the parity tests).
+"""
+
+import numpy as np
+import pytest
+
+from lsp_inputs import make_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1607_02560_gb300 import build as B
+    B.build()
+
+
+def _pinned(torch, shape):
+    return torch.empty(shape, dtype=torch.float64, pin_memory=True)
+
+
+def test_async_rows_of_consecutive_builds_match_their_own_build():
+    import torch
+    from paper_1607_02560_gb300 import Context
+
+    n = 512
+    vs = [make_workload("helm2d_n1024", seed=s, n=n) for s in (11, 12, 13, 14)]
+    stream = torch.cuda.Stream()
+    ctx = Context(2, n, stream=stream)
+    ref = []
+    for v in vs:
+        ctx.set_potential(v)
+        ctx.build_stencils(policy="local", use_graph=True)
+        ref.append([ctx.get_rows(w) for w in "QCP"])
+    assert not np.array_equal(ref[0][2], ref[1][2])  # a stale copy would be seen
+    outs = [[_pinned(torch, (ctx.N, ctx.mu)) for _ in "QCP"] for _ in vs]
+    for v, o in zip(vs, outs):  # no wait between the steps
+        ctx.set_potential(v)
+        ctx.build_stencils(policy="local", use_graph=True)
+        for w, t in zip("QCP", o):
+            ctx.get_rows_async(w, t)
+    ctx.wait_rows()
+    for r, o in zip(ref, outs):
+        for a, b in zip(r, o):
+            assert np.array_equal(a, b.numpy())
+
+    # wider rows (t = 2, 25 per point) regrow the staging copies; the earlier copies still land
+    first = [_pinned(torch, (ctx.N, ctx.mu)) for _ in "QCP"]
+    for w, t in zip("QCP", first):
+        ctx.get_rows_async(w, t)
+    ctx.build_stencils(policy="paper", t=2, nd_leaf=8)
+    wide = _pinned(torch, (ctx.N, ctx.mu))
+    ctx.get_rows_async("P", wide)
+    ctx.wait_rows()
+    assert ctx.mu == 25
+    assert np.array_equal(wide.numpy(), ctx.get_rows("P"))
+    for a, b in zip(ref[-1], first):
+        assert np.array_equal(a, b.numpy())
+    ctx.close()
+
+
+def test_async_rows_refusals():
+    import torch
+    from paper_1607_02560_gb300 import Context
+    from paper_1607_02560_gb300.lsp import LspError
+
+    v = make_workload("helm2d_n32")
+    ctx = Context(2, 32, stream=torch.cuda.Stream())
+    host = np.empty((ctx.N, ctx.mu))
+    with pytest.raises(LspError):
+        ctx.get_rows_async("Q", host)  # no build yet
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="local")
+    with pytest.raises(ValueError):
+        ctx.get_rows_async("Q", torch.empty((ctx.N, ctx.mu), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        ctx.get_rows_async("Q", np.empty((ctx.N, ctx.mu - 1)))
+    with pytest.raises(LspError):
+        ctx.get_rows_async("X", host)
+    ctx.get_rows_async("C", host)  # pageable memory works too (the copy is not overlapped)
+    ctx.wait_rows()
+    assert np.array_equal(host, ctx.get_rows("C"))
+    ctx.close()
