@@ -27,13 +27,17 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
-// Per-block partial min / max / sum / count of non-finite values, 4 doubles per block.
+// Per-block partial min / max / sum / count of non-finite values, 4 doubles per block. With
+// vcopy, v is also stored there (v read from page-locked host memory over the host link, so
+// the upload and the statistics take one pass and no copy engine).
 __global__ void __launch_bounds__(kThreads) k_stats_partial(const double* __restrict__ v,
-                                                            int64_t N, double* __restrict__ part) {
+                                                            int64_t N, double* __restrict__ part,
+                                                            double* __restrict__ vcopy) {
   double mn = DBL_MAX, mx = -DBL_MAX, sm = 0.0, bad = 0.0;
   for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < N;
        j += (int64_t)gridDim.x * kThreads) {
-    double x = __ldg(v + j);
+    const double x = v[j];
+    if (vcopy) vcopy[j] = x;
     if (!isfinite(x)) {
       bad += 1.0;
       continue;
@@ -73,8 +77,12 @@ __global__ void __launch_bounds__(kThreads) k_stats_partial(const double* __rest
   }
 }
 
+// Reduces the partials to (min, max, sum, non-finite count) in out[0..3], and also in
+// host_out[0..3] (page-locked host memory, device address) when given, so that the host reads
+// them without a copy.
 __global__ void __launch_bounds__(kThreads) k_stats_final(const double* __restrict__ part, int nb,
-                                                          double* __restrict__ out) {
+                                                          double* __restrict__ out,
+                                                          double* __restrict__ host_out) {
   double mn = DBL_MAX, mx = -DBL_MAX, sm = 0.0, bad = 0.0;
   for (int b = threadIdx.x; b < nb; b += kThreads) {
     mn = fmin(mn, part[4 * b + 0]);
@@ -109,6 +117,12 @@ __global__ void __launch_bounds__(kThreads) k_stats_final(const double* __restri
       out[1] = mx;
       out[2] = sm;
       out[3] = bad;
+      if (host_out) {
+        host_out[0] = mn;
+        host_out[1] = mx;
+        host_out[2] = sm;
+        host_out[3] = bad;
+      }
     }
   }
 }
@@ -274,10 +288,11 @@ int grid_for(int64_t work, int per_block = kThreads) {
 
 }  // namespace
 
-cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks) {
+cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks, const double* src) {
   int t = timer_begin(c, "stats");
-  k_stats_partial<<<nblocks, kThreads, 0, c->stream>>>((const double*)c->v.p, c->geo.N,
-                                                        (double*)c->stats_part.p);
+  double* vd = (double*)c->v.p;
+  k_stats_partial<<<nblocks, kThreads, 0, c->stream>>>(src, c->geo.N, (double*)c->stats_part.p,
+                                                        src == vd ? nullptr : vd);
   timer_end(c, t);
   return cudaGetLastError();
 }
@@ -285,7 +300,7 @@ cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks) {
 cudaError_t launch_stats_final(lsp_ctx* c, int nblocks) {
   int t = timer_begin(c, "stats_final");
   k_stats_final<<<1, kThreads, 0, c->stream>>>((const double*)c->stats_part.p, nblocks,
-                                                (double*)c->stats.p);
+                                                (double*)c->stats.p, c->h_stats_dev);
   timer_end(c, t);
   return cudaGetLastError();
 }

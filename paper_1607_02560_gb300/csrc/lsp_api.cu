@@ -461,6 +461,10 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
       st = LSP_ERR_OOM;
       break;
     }
+    if (cudaHostGetDevicePointer((void**)&c->h_stats_dev, c->h_stats, 0) != cudaSuccess) {
+      cudaGetLastError();
+      c->h_stats_dev = nullptr;
+    }
     if (upload_sym(c) != cudaSuccess) {
       st = LSP_ERR_CUDA;
       break;
@@ -574,15 +578,31 @@ lsp_status lsp_set_potential(lsp_ctx* c, const double* v, int v_on_device) {
   if (!v) return fail(c, LSP_ERR_ARG, "v is NULL");
   const int64_t N = c->geo.N;
   if (!ensure(c, c->v, sizeof(double) * N)) return LSP_ERR_OOM;
-  CUDA_OK(c, cudaMemcpyAsync(c->v.p, v, sizeof(double) * N,
-                             v_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                             c->stream));
+  // Page-locked host memory is read by the statistics kernel itself, which also stores v on
+  // the device; pageable host memory and device memory are copied first. Neither the upload
+  // nor the read-back of the statistics then waits behind host copies still in flight on the
+  // copy engines (lsp_get_rows_async of the previous build).
+  const double* src = nullptr;
+  if (!v_on_device) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, v) == cudaSuccess && at.type == cudaMemoryTypeHost &&
+        at.devicePointer)
+      src = (const double*)at.devicePointer;
+    cudaGetLastError();
+  }
+  if (!src) {
+    CUDA_OK(c, cudaMemcpyAsync(c->v.p, v, sizeof(double) * N,
+                               v_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               c->stream));
+    src = (const double*)c->v.p;
+  }
   int nb = (int)std::min<int64_t>(152 * 4, (N + 255) / 256);
   if (!ensure(c, c->stats_part, sizeof(double) * 4 * nb)) return LSP_ERR_OOM;
-  CUDA_OK(c, launch_stats_partial(c, nb));
+  CUDA_OK(c, launch_stats_partial(c, nb, src));
   CUDA_OK(c, launch_stats_final(c, nb));
-  CUDA_OK(c, cudaMemcpyAsync(c->h_stats, c->stats.p, 4 * sizeof(double), cudaMemcpyDeviceToHost,
-                             c->stream));
+  if (!c->h_stats_dev)
+    CUDA_OK(c, cudaMemcpyAsync(c->h_stats, c->stats.p, 4 * sizeof(double),
+                               cudaMemcpyDeviceToHost, c->stream));
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   c->have_v = false;
   c->built = false;

@@ -84,6 +84,7 @@ struct lsp_ctx {
   double vmin = 0, vmax = 0, vmean = 0;
   lsp::DevBuf v, stats_part, stats;
   double* h_stats = nullptr;  // pinned
+  double* h_stats_dev = nullptr;  // its device address (null: read back with a copy)
 
   // cos table X_a(p) = w_p cos(2 pi a p / n), a = 0..4, p = 0..n/2 (FP64 and FP32 copies;
   // t = 1 reads rows 0..2)
@@ -161,7 +162,8 @@ int timer_begin(lsp_ctx* ctx, const char* name);
 void timer_end(lsp_ctx* ctx, int slot);
 
 // ---- launchers; each returns cudaGetLastError() after the launch ----
-cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks);
+// src: c->v itself, or page-locked host memory (device address) that is copied into c->v
+cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks, const double* src);
 cudaError_t launch_stats_final(lsp_ctx* c, int nblocks);
 cudaError_t launch_mark_local(lsp_ctx* c);
 cudaError_t launch_compact(lsp_ctx* c, const uint8_t* flags, int64_t lo, int64_t range,

@@ -85,3 +85,36 @@ def test_async_rows_refusals():
     ctx.wait_rows()
     assert np.array_equal(host, ctx.get_rows("C"))
     ctx.close()
+
+
+def test_pinned_potential_is_read_by_the_statistics_kernel():
+    """Page-locked host v is read by the statistics kernel over the host link (no copy engine):
+    same stored potential, statistics and rows as pageable host v; a NaN is still refused."""
+    import torch
+    from paper_1607_02560_gb300 import Context
+    from paper_1607_02560_gb300.lsp import LspError
+
+    n = 256
+    v = make_workload("helm2d_n1024", seed=21, n=n)
+    ctx = Context(2, n, stream=torch.cuda.Stream())
+    ctx.set_potential(v)  # pageable: copied first
+    ctx.build_stencils(policy="local")
+    rows = [ctx.get_rows(w) for w in "QCP"]
+    u = torch.from_numpy(np.random.default_rng(3).standard_normal(n * n)).cuda()
+    y0 = torch.empty_like(u)
+    ctx.apply_operator(u, y0)
+    ctx.synchronize()
+    pin = torch.empty(v.shape, dtype=torch.float64, pin_memory=True)
+    pin.copy_(torch.from_numpy(v))
+    ctx.set_potential(pin.numpy())
+    ctx.build_stencils(policy="local")
+    for w, r in zip("QCP", rows):
+        assert np.array_equal(ctx.get_rows(w), r)
+    y1 = torch.empty_like(u)
+    ctx.apply_operator(u, y1)  # reads the stored v
+    ctx.synchronize()
+    assert torch.equal(y0, y1)
+    pin[3, 5] = float("nan")
+    with pytest.raises(LspError, match="NaN"):
+        ctx.set_potential(pin.numpy())
+    ctx.close()
