@@ -286,6 +286,26 @@ int grid_for(int64_t work, int per_block = kThreads) {
   return (int)b;
 }
 
+// Zeroes n 32-bit words. A kernel rather than a memset, so that the build never waits behind
+// host copies queued on the copy engines.
+__global__ void __launch_bounds__(kThreads) k_zero_u32(uint32_t* __restrict__ p, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * kThreads + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * kThreads)
+    p[i] = 0u;
+}
+
+// dst[0, n) = src[0, n) (doubles; both 16-byte aligned): pairs by every thread, an odd last
+// element by thread 0.
+__global__ void __launch_bounds__(kThreads) k_copy_f64(const double* __restrict__ src,
+                                                       double* __restrict__ dst, int64_t n) {
+  const int64_t n2 = n / 2;
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+  double2* d2 = reinterpret_cast<double2*>(dst);
+  const int64_t t0 = (int64_t)blockIdx.x * kThreads + threadIdx.x;
+  for (int64_t i = t0; i < n2; i += (int64_t)gridDim.x * kThreads) d2[i] = s2[i];
+  if (t0 == 0 && (n & 1)) dst[n - 1] = src[n - 1];
+}
+
 }  // namespace
 
 cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks, const double* src) {
@@ -293,6 +313,21 @@ cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks, const double* src) {
   double* vd = (double*)c->v.p;
   k_stats_partial<<<nblocks, kThreads, 0, c->stream>>>(src, c->geo.N, (double*)c->stats_part.p,
                                                         src == vd ? nullptr : vd);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_zero(lsp_ctx* c, void* p, size_t bytes) {
+  const int64_t n = (int64_t)(bytes / 4);
+  int t = timer_begin(c, "zero");
+  k_zero_u32<<<grid_for(n), kThreads, 0, c->stream>>>((uint32_t*)p, n);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_f64(lsp_ctx* c, const double* src, double* dst, int64_t n) {
+  int t = timer_begin(c, "copy_rows");
+  k_copy_f64<<<grid_for((n + 1) / 2), kThreads, 0, c->stream>>>(src, dst, n);
   timer_end(c, t);
   return cudaGetLastError();
 }

@@ -353,10 +353,11 @@ lsp_status flush_timers(lsp_ctx* c) {
 lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, bool upload) {
   const int d = c->geo.d;
   int32_t* counts = (int32_t*)c->counts.p;
-  CUDA_OK(c, cudaMemsetAsync(counts + kErrWord, 0, sizeof(int32_t), c->stream));
+  // zeroing by kernels: a memset may be queued behind host copies on the copy engines
+  CUDA_OK(c, launch_zero(c, counts + kErrWord, sizeof(int32_t)));
   if (o.policy == LSP_SHIFT_LOCAL) {
     const int64_t R = c->mrange.size();
-    CUDA_OK(c, cudaMemsetAsync(c->shift_flag.p, 0, round_up(R, 4096), c->stream));
+    CUDA_OK(c, launch_zero(c, c->shift_flag.p, round_up(R, 4096)));
     CUDA_OK(c, launch_mark_local(c));
     CUDA_OK(c, launch_compact(c, (const uint8_t*)c->shift_flag.p, c->mrange.lo, R,
                               (int32_t*)c->shift_m.p, counts + 0, (int32_t*)c->idx_of.p));
@@ -378,7 +379,7 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
       cap = sz;
       continue;
     }
-    CUDA_OK(c, cudaMemsetAsync(c->eflag[k].p, 0, round_up(sz, 4096), c->stream));
+    CUDA_OK(c, launch_zero(c, c->eflag[k].p, round_up(sz, 4096)));
     CUDA_OK(c, launch_mark_stage(c, list, count, cap, c->erange[k].lo, (uint8_t*)c->eflag[k].p));
     CUDA_OK(c, launch_compact(c, (const uint8_t*)c->eflag[k].p, c->erange[k].lo, sz,
                               (int32_t*)c->elist[k].p, counts + (d - k), nullptr));
@@ -656,7 +657,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
           !ensure(c, c->counts, sizeof(int32_t) * 64))
         return LSP_ERR_OOM;
       c->built = false;
-      CUDA_OK(c, cudaMemsetAsync((int32_t*)c->counts.p + kErrWord, 0, sizeof(int32_t), c->stream));
+      CUDA_OK(c, launch_zero(c, (int32_t*)c->counts.p + kErrWord, sizeof(int32_t)));
       CUDA_OK(c, launch_learned_rows(c, c->mlp));
       c->built = true;
       c->built_learned = true;
@@ -920,7 +921,9 @@ lsp_status lsp_get_rows_async(lsp_ctx* c, char which, double* rows) {
   }
   // the staging copy of this block is free again once its previous host copy has landed
   CUDA_OK(c, cudaStreamWaitEvent(c->stream, c->ev_copied[w], 0));
-  CUDA_OK(c, cudaMemcpyAsync(c->stage[w].p, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+  // the staging copy by a kernel: a device-to-device memcpy could queue on the copy engine
+  // behind the host copy of the previous block
+  CUDA_OK(c, launch_copy_f64(c, src, (double*)c->stage[w].p, (int64_t)(bytes / sizeof(double))));
   CUDA_OK(c, cudaEventRecord(c->ev_staged[w], c->stream));
   CUDA_OK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_staged[w], 0));
   CUDA_OK(c, cudaMemcpyAsync(rows, c->stage[w].p, bytes, cudaMemcpyDeviceToHost,

@@ -165,6 +165,10 @@ void timer_end(lsp_ctx* ctx, int slot);
 // src: c->v itself, or page-locked host memory (device address) that is copied into c->v
 cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks, const double* src);
 cudaError_t launch_stats_final(lsp_ctx* c, int nblocks);
+// bytes / 4 words of p set to zero (bytes a multiple of 4, p 4-byte aligned)
+cudaError_t launch_zero(lsp_ctx* c, void* p, size_t bytes);
+// n doubles from src to dst (device, 16-byte aligned)
+cudaError_t launch_copy_f64(lsp_ctx* c, const double* src, double* dst, int64_t n);
 cudaError_t launch_mark_local(lsp_ctx* c);
 cudaError_t launch_compact(lsp_ctx* c, const uint8_t* flags, int64_t lo, int64_t range,
                            int32_t* list, int32_t* count, int32_t* idx_of);
