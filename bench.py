@@ -32,6 +32,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = "local stencils/sec (Q, C, P rows of every grid point, steps a1-a7)"
+
 WORKLOAD_TEXT = {
     "helm2d_n1024": "2D Helmholtz n=1024 (1,048,576 points), 3x3 neighbourhoods, omega=2*pi*256, "
                     "c(x)=1+sum of 64 seeded Gaussians (seed 3)",
@@ -350,7 +352,7 @@ def run_ours(args):
         roof = None
     rows_k = kern.get("rows")
     out = {
-        "metric": "local stencils/sec (Q, C, P rows of every grid point, steps a1-a7)",
+        "metric": METRIC,
         "value": value, "unit": "stencils/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "learned": "bf16+f32"}[args.mode],
@@ -663,8 +665,7 @@ def run_reference(args):
             vals.append(cb)
     value = float(np.median([c["value"] for c in vals]))
     last = vals[-1]
-    out = {"impl": "reference", "metric": "local stencils/sec (Q, C, P rows of every grid "
-                                          "point, steps a1-a7)",
+    out = {"impl": "reference", "metric": METRIC,
            "value": value, "unit": "stencils/s", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": float(np.mean([c["seconds"] for c in vals])) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
