@@ -36,7 +36,7 @@ constexpr int kNdPanel = 16;       // columns eliminated per step in the blocked
 constexpr int kNdSmallFront = 160; // fronts with f <= this are swept in shared memory
 constexpr int kNdStagedBytes = 64 * 1024;  // solve blocks up to this size are staged
 constexpr int kNdMaxN = 1024;      // 2D: the cross has 2n - 1 points
-constexpr int kNdMaxN3 = 64;       // 3D: the root planes have 3n^2 - 3n + 1 points (12 097 at 64)
+constexpr int kNdMaxN3 = 64;       // 3D: the slab fronts have 2 (n/2 - 1) n + 2 n^2 points (12 160 at 64)
 constexpr int kNdPanelRegRows = 8 * 256;  // panels up to this many rows keep them in registers
 
 struct NdLevel {
