@@ -37,7 +37,7 @@ import scipy.sparse.linalg
 
 __all__ = [
     "PI2", "freq_axis", "symbol", "apply_operator", "round_half_away", "snap_index",
-    "shift_value", "paper_shift_list", "default_nshifts", "assign_shifts", "solve_p",
+    "shift_value", "paper_shift_points", "paper_shift_list", "default_nshifts", "assign_shifts", "solve_p",
     "neighbourhood_offsets", "kernel_vectors", "gram_matrix", "near_null",
     "stencil_for_shift", "build_stencils", "rows_to_csr", "sparse_matrices",
     "gmres_solve", "dense_green_matrix", "brute_force_stencil", "sign_fix",
@@ -109,21 +109,27 @@ def default_nshifts(n: int, d: int) -> int:
     return max(2, n // 16 if d == 2 else n // 4)
 
 
-def paper_shift_list(v: np.ndarray, nshifts: int) -> np.ndarray:
-    """S: nshifts points spread evenly over [v_min, v_max], snapped to the lattice, deduped.
+def paper_shift_points(vmin: float, vmax: float, nshifts: int) -> np.ndarray:
+    """The nshifts points spread evenly over [v_min, v_max], before snapping (Sec. 4.1).
 
-    Sec. 4.1 ("Now let us discuss how to choose S"). Returns the sorted lattice indices m.
-    x_i = v_min + i * ((v_max - v_min) / (K - 1)) for i < K-1 and x_{K-1} = v_max.
+    x_i = v_min + i * ((v_max - v_min) / (K - 1)) for i < K-1 and x_{K-1} = v_max; K = 1 gives
+    v_min alone.
     """
-    vmin, vmax = float(v.min()), float(v.max())
     K = int(nshifts)
     if K < 1:
         raise ValueError("nshifts must be >= 1")
     if K == 1:
-        xs = np.array([vmin])
-    else:
-        step = (vmax - vmin) / (K - 1)
-        xs = np.array([vmin + i * step for i in range(K - 1)] + [vmax])
+        return np.array([float(vmin)])
+    step = (float(vmax) - float(vmin)) / (K - 1)
+    return np.array([float(vmin) + i * step for i in range(K - 1)] + [float(vmax)])
+
+
+def paper_shift_list(v: np.ndarray, nshifts: int) -> np.ndarray:
+    """S: nshifts points spread evenly over [v_min, v_max], snapped to the lattice, deduped.
+
+    Sec. 4.1 ("Now let us discuss how to choose S"). Returns the sorted lattice indices m.
+    """
+    xs = paper_shift_points(float(v.min()), float(v.max()), nshifts)
     return np.unique(snap_index(xs))
 
 

@@ -171,6 +171,73 @@ def test_paper_shift_list():
     assert m[0] == O.snap_index(v.min()) and m[-1] == O.snap_index(v.max())
 
 
+def test_paper_shift_points_are_evenly_spaced_with_both_ends():
+    # hand values: K points from v_min to v_max inclusive, spacing (v_max - v_min) / (K - 1)
+    assert O.paper_shift_points(-3.0, 5.0, 5).tolist() == [-3.0, -1.0, 1.0, 3.0, 5.0]
+    assert O.paper_shift_points(10.0, 16.0, 4).tolist() == [10.0, 12.0, 14.0, 16.0]
+    assert O.paper_shift_points(0.0, 1.0, 2).tolist() == [0.0, 1.0]
+    assert O.paper_shift_points(-7.0, 9.0, 1).tolist() == [-7.0]
+
+
+def test_paper_shift_list_interior_after_snapping():
+    # v / pi^2 spans [3.9, 25.9] and K = 5: x / pi^2 = 3.9, 9.4, 14.9, 20.4, 25.9, so
+    # (x / pi^2 - 2) / 4 = 0.475, 1.85, 3.225, 4.6, 5.975 and m = 0, 2, 3, 5, 6
+    v = np.array([[3.9, 10.0], [25.9, 7.0]]) * O.PI2
+    assert O.paper_shift_list(v, 5).tolist() == [0, 2, 3, 5, 6]
+    # v / pi^2 spans [0.1, 9.9] and K = 5: (x / pi^2 - 2) / 4 = -0.475, 0.1375, 0.75, 1.3625,
+    # 1.975, so m = 0, 0, 1, 1, 2, deduplicated to 0, 1, 2
+    v = np.array([0.1, 5.0, 9.9]) * O.PI2
+    assert O.paper_shift_list(v, 5).tolist() == [0, 1, 2]
+
+
+# ---- the sign of the near-null vector (the paper leaves it open; reading: centre > 0) -------
+
+def test_sign_rule_on_hand_vectors():
+    assert O.sign_fix(np.array([0.3, -0.8, 0.1]), 1).tolist() == [-0.3, 0.8, -0.1]
+    assert O.sign_fix(np.array([0.3, 0.8, 0.1]), 1).tolist() == [0.3, 0.8, 0.1]
+    # centre entry below 1e-12: the first entry with |alpha_i| > 1e-12 is made positive
+    assert O.sign_fix(np.array([0.0, -0.6, 1e-13, 0.8]), 2).tolist() == [0.0, 0.6, -1e-13, -0.8]
+    assert O.sign_fix(np.array([1e-13, 0.6, 0.0, -0.8]), 2).tolist() == [1e-13, 0.6, 0.0, -0.8]
+
+
+@pytest.mark.parametrize("n,d,m,t", [(16, 2, -20, 1), (32, 2, -60, 1), (12, 2, -18, 2),
+                                     (8, 3, -9, 1), (10, 3, -14, 2)])
+def test_every_oracle_stencil_has_a_positive_centre(n, d, m, t):
+    st = O.stencil_for_shift(n, d, float(O.shift_value(m)), t)
+    centre = len(O.neighbourhood_offsets(d, t)) // 2
+    assert st["alpha"][centre] > 0
+    # the brute-force SVD vector agrees up to sign, and its sign is fixed the same way
+    alpha_bf, _, _, _ = O.brute_force_stencil(n, d, float(O.shift_value(m)), (0,) * d, t) \
+        if n ** d <= 1000 else (st["alpha"], None, None, None)
+    assert abs(abs(float(alpha_bf @ st["alpha"])) - 1.0) < 1e-9
+    assert alpha_bf[centre] > 0
+
+
+def test_every_oracle_row_has_a_positive_centre():
+    v = make_workload("helm2d_n256", n=32)
+    for pol in ("local", "paper"):
+        st = O.build_stencils(v, pol)
+        assert (st["Q"][:, 4] > 0).all()
+        assert (st["alpha"][:, 4] > 0).all()
+
+
+@pytest.mark.parametrize("mutation", ["spacing_by_K", "flipped_sign_rule"])
+def test_shift_and_sign_pins_catch_planted_mistakes(monkeypatch, mutation):
+    import oracle.lsp_oracle as L
+    if mutation == "spacing_by_K":
+        def bad(vmin, vmax, K):
+            step = (vmax - vmin) / K
+            return np.array([vmin + i * step for i in range(K - 1)] + [vmax])
+        monkeypatch.setattr(L, "paper_shift_points", bad)
+        v = np.array([[3.9, 10.0], [25.9, 7.0]]) * O.PI2
+        assert L.paper_shift_list(v, 5).tolist() != [0, 2, 3, 5, 6]
+    else:
+        orig = L.sign_fix
+        monkeypatch.setattr(L, "sign_fix", lambda a, c: -orig(a, c))
+        st = L.stencil_for_shift(16, 2, float(O.shift_value(-20)))
+        assert not st["alpha"][4] > 0
+
+
 # ---- Sec. 4.1: rows -------------------------------------------------------------------------
 
 def test_constant_potential_gives_identical_rows():
