@@ -1,7 +1,7 @@
 """Benchmark: local stencils/sec of the stencil setup (steps a1-a7) on GB300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload helm2d_n1024]
-                    [--policy local] [--impl ours|reference]
+                    [--policy local] [--mode fp64] [--impl ours|reference] [--detail FILE]
 
 One step = one pass of the whole hot path over the workload's potential, resident in HBM:
 lsp_set_potential (a1: device copy + v_min/v_max/mean) and lsp_build_stencils (a2-a7: shift
@@ -9,12 +9,19 @@ list, per-shift kernel vectors, Gram matrix, near-null vector, and the Q, C, P r
 point). The value is points / second (one stencil = the finished Q, C, P rows of one point).
 L2 is flushed (256 MiB write) before every timed step, outside the step's events.
 
+The last stdout line is the compact result line (a few KB at most). It carries the headline
+(2D n = 1024, per-point shifts, FP64), its roofline, the end-to-end serving loop through the
+C ABI with host buffers, the oracle timed on the host cores (one core and all cores), the
+clocks seen during the timed region, and one summary per form of the metric (FP64, mixed,
+learned at 2D n = 1024 and 3D n = 64). Per-kernel tables, the paper-policy and multi-t
+variants and the preconditioner solve go to the --detail file when one is named.
+
 Under torchrun each rank builds the stencils of its own potential (a different seed): the
 per-point problems are independent, so ranks share nothing (weak scaling, no collective on
 the data path); the step time is the maximum over ranks.
 
---impl reference times the CPU oracle (numpy/scipy FP64) on a bounded sample of the same
-workload on the host cores and extrapolates to the whole workload.
+--impl reference times the CPU oracle (numpy/scipy FP64, as it stands) on a bounded sample of
+the same workload on all host cores and extrapolates to the whole workload.
 """
 
 from __future__ import annotations
@@ -33,6 +40,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "local stencils/sec (Q, C, P rows of every grid point, steps a1-a7)"
+LINE_LIMIT = 4096  # bytes of the result line
 
 WORKLOAD_TEXT = {
     "helm2d_n1024": "2D Helmholtz n=1024 (1,048,576 points), 3x3 neighbourhoods, omega=2*pi*256, "
@@ -44,6 +52,17 @@ WORKLOAD_TEXT = {
     "helm2d_n32": "2D Helmholtz n=32 (1,024 points), 3x3 neighbourhoods, omega=2*pi*8, "
                   "one centred Gaussian bump",
 }
+
+# GB300 unit counts for the ALU-bound kernels (152 SMs, 2070 MHz maximum SM clock): the nominal
+# FP64 rate, 1.25 TFLOP/s, is 2 FP64 FMA per SM per clock (4 flop); FP32 is 128 FMA lanes per SM
+# per clock (256 flop).
+SMS, SM_MAX_MHZ = 152, 2070.0
+FP64_FLOP_PER_SM_CLK, FP32_FLOP_PER_SM_CLK = 4, 256
+
+# DRAM bytes (read + write) per launch from ncu captures (dram__bytes_read.sum +
+# dram__bytes_write.sum), keyed by (kernel, workload, mode); null where no capture of the
+# current kernel exists. The profile named beside each figure holds the command.
+TRAFFIC = {}
 
 
 def dist_info():
@@ -82,6 +101,12 @@ def load_peaks():
             p = json.load(fh)
         return p, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def alu_peak_tflops(fp: str) -> float:
+    """FP64 / FP32 peak from the unit counts at the maximum SM clock (TFLOP/s)."""
+    per = FP64_FLOP_PER_SM_CLK if fp == "fp64" else FP32_FLOP_PER_SM_CLK
+    return per * SMS * SM_MAX_MHZ * 1e6 / 1e12
 
 
 class Clocks:
@@ -153,10 +178,15 @@ def lattice_domain_sizes(m_list: np.ndarray, n: int, d: int) -> list[int]:
 
 
 def kernel_work(name: str, n: int, d: int, N: int, mu: int, sizes: list[int]):
-    """Algorithmic (flops or bytes, unit) of one launch of a kernel, or None."""
+    """Algorithmic (amount, kind) of one launch of a kernel, or None.
+
+    kind: "flop" (FP64 or FP32 ALU, by the build's mode), "tensor_flop" (BF16 tensor cores)
+    or "byte" (HBM)."""
     P = n // 2 + 1
     ncls = {1: 3, 2: 6, 3: 10}
     if name.startswith("stage"):
+        if not sizes:
+            return None
         k = int(name[-1])
         # stage k runs over E_k; sizes lists E_d, E_{d-1}, ..., so E_k = sizes[d - k]
         count = sizes[d - k]
@@ -178,8 +208,50 @@ def kernel_work(name: str, n: int, d: int, N: int, mu: int, sizes: list[int]):
     return None
 
 
-def measure_fp64_peak(torch) -> float:
-    """FP64 GEMM throughput (TFLOP/s) of the library matmul, best of 5, 4096^3."""
+def roofline(name: str, ms_per_launch: float, work, mode: str, peaks: dict,
+             traffic_key=None) -> dict | None:
+    """The roofline object of one kernel: algorithmic work per launch over its mean launch
+    time, against the peak of the unit that bounds it."""
+    if not work or ms_per_launch <= 0:
+        return None
+    amount, kind = work
+    rate = amount / (ms_per_launch * 1e-3)
+    if kind == "tensor_flop":
+        bound, unit, ach, peak = "tensor", "TFLOP/s", rate / 1e12, peaks["bf16_tflops"]
+        src = "bf16_tflops (burst) of measured peaks"
+    elif kind == "flop":
+        fp = "fp32" if mode == "mixed" else "fp64"
+        bound, unit, ach, peak = "alu", "TFLOP/s", rate / 1e12, alu_peak_tflops(fp)
+        src = (f"{fp.upper()} peak from unit counts: {FP64_FLOP_PER_SM_CLK if fp == 'fp64' else FP32_FLOP_PER_SM_CLK}"
+               f" flop/SM/clk x {SMS} SMs x {SM_MAX_MHZ:.0f} MHz")
+    else:
+        bound, unit, ach, peak = "hbm", "GB/s", rate / 1e9, peaks["hbm_gbs"]
+        src = "hbm_gbs of measured peaks"
+    return {"bound": bound, "kernel": name, "achieved": round(ach, 4), "peak": round(peak, 4),
+            "unit": unit, "frac": round(ach / peak, 4),
+            "traffic": TRAFFIC.get(traffic_key) if traffic_key else None,
+            "work_per_launch": amount, "ms_per_launch": round(ms_per_launch, 5),
+            "peak_source": src}
+
+
+def dominant_roofline(ktimes: dict, n: int, d: int, N: int, mu: int, sizes, mode: str,
+                      peaks: dict, workload: str):
+    """Roofline of the kernel with the largest total time among those with a work count."""
+    best = None
+    for name, (ms, cnt) in ktimes.items():
+        w = kernel_work(name, n, d, N, mu, sizes)
+        if w is None:
+            continue
+        if best is None or ms > best[1]:
+            best = (name, ms, cnt, w)
+    if best is None:
+        return None
+    name, ms, cnt, w = best
+    return roofline(name, ms / max(cnt, 1), w, mode, peaks, (name, workload, mode))
+
+
+def measure_fp64_gemm(torch) -> float:
+    """FP64 GEMM throughput (TFLOP/s) of the library matmul, best of 5, 4096^3 (context)."""
     a = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
     b = torch.randn(4096, 4096, dtype=torch.float64, device="cuda")
     best = 0.0
@@ -215,11 +287,13 @@ def run_ours(args):
     v_dev = torch.from_numpy(v_host).to("cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
 
-    mlp = None
-    train_info = None
+    mlps = {}
+    train_info = {}
+    if args.mode == "learned" or not args.no_forms:
+        for dd in ((d,) if args.mode == "learned" and args.no_forms else (2, 3)):
+            mlps[dd], train_info[dd] = train_for(torch, dd, args.learned_steps, stream)
     if args.mode == "learned":
-        mlp, train_info = train_for(torch, args.workload, args.learned_steps, stream)
-        ctx.set_mlp(mlp)
+        ctx.set_mlp(mlps[d])
 
     def step():
         ctx.set_potential(v_dev)
@@ -287,6 +361,7 @@ def run_ours(args):
                 ctx.get_rows(which, o)
             e2e_ms.append((time.perf_counter() - t1) * 1e3)
         e2e_ms = e2e_ms[1:]
+
         # (b) serving loop: step k's rows go to the host (get_rows_async, the library's copy
         # stream) while step k + 1 builds; two host buffer sets alternate. The L2 flush runs
         # inside the timed region, and the region ends when the last step's rows have landed.
@@ -319,99 +394,173 @@ def run_ours(args):
     launches = int(sum(c for _, c in ktimes.values()))
     kern = {}
     for name, (ms, cnt) in ktimes.items():
-        w = kernel_work(name, n, d, N, mu, sizes)
         kern[name] = {"ms_per_launch": ms / max(cnt, 1), "launches": cnt}
-        if w:
-            per = w[0] / (ms / max(cnt, 1) * 1e-3)
-            flops = w[1] in ("flop", "tensor_flop")
-            kern[name]["achieved"] = per / (1e12 if flops else 1e9)
-            kern[name]["unit"] = "TFLOP/s" if flops else "GB/s"
-    dom = max(ktimes.items(), key=lambda kv: kv[1][0])[0]
-    fp64_peak = measure_fp64_peak(torch)
-    w = kernel_work(dom, n, d, N, mu, sizes)
-    if w and w[1] == "tensor_flop":
-        roof = {"bound": "tensor", "kernel": dom, "achieved": kern[dom]["achieved"],
-                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                "frac": kern[dom]["achieved"] / peaks["bf16_tflops"], "traffic": None,
-                "peak_source": f"MEASURED_PEAKS.json bf16_tflops, burst ({peak_src})",
-                "work_per_launch": w[0]}
-    elif w and w[1] == "flop":
-        roof = {"bound": "alu", "kernel": dom, "achieved": kern[dom]["achieved"],
-                "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": kern[dom]["achieved"] / fp64_peak, "traffic": None,
-                "peak_source": "FP64 DGEMM (torch.matmul 4096^3, best of 6) measured in this "
-                               "run; FP64 ALU, nominal 1.25 TFLOP/s on GB300",
-                "work_per_launch": w[0]}
-    elif w:
-        roof = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["achieved"],
-                "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": kern[dom]["achieved"] / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
-                "work_per_launch": w[0]}
-    else:
-        roof = None
-    rows_k = kern.get("rows")
-    out = {
+        r = roofline(name, ms / max(cnt, 1), kernel_work(name, n, d, N, mu, sizes), args.mode,
+                     peaks)
+        if r:
+            kern[name].update(achieved=r["achieved"], unit=r["unit"], frac=r["frac"])
+    roof = dominant_roofline(ktimes, n, d, N, mu, sizes, args.mode, peaks, args.workload)
+    rows_k = ktimes.get("rows")
+    rows_roof = (roofline("rows", rows_k[0] / max(rows_k[1], 1),
+                          kernel_work("rows", n, d, N, mu, sizes), args.mode, peaks,
+                          ("rows", args.workload, args.mode)) if rows_k else None)
+    used = ctx.mode_used()
+    ctx.close()
+    res = {
         "metric": METRIC,
         "value": value, "unit": "stencils/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "f64", "mixed": "f32+f64", "learned": "bf16+f32"}[args.mode],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "mixed": "f32+f64", "learned": "bf16+f32"}[args.mode],
         "data": "synthetic",
-        "config": {"workload": args.workload, "text": WORKLOAD_TEXT.get(args.workload, ""),
-                   "policy": args.policy, "mode": args.mode, "d": d, "n": n, "points": N,
-                   "shifts": ns, "lattice_domains": sizes, "mode_used": ctx.mode_used(),
+        "config": {"workload": args.workload, "policy": args.policy, "mode": args.mode,
+                   "mode_used": used, "d": d, "n": n, "points": N, "shifts": ns,
                    "l2": "flushed before every timed step (256 MiB write), outside the step events",
                    "parallelism": f"replicas x{ws} (independent potentials)"},
         "roofline": roof,
-        "hbm_roofline_rows": ({"achieved": rows_k["achieved"], "peak": peaks["hbm_gbs"],
-                               "frac": rows_k["achieved"] / peaks["hbm_gbs"], "unit": "GB/s"}
-                              if rows_k and "achieved" in rows_k else None),
-        "kernels": kern,
+        "rows_roofline": rows_roof,
         "gpu_launches": launches,
-        "wall_s_timed_region": wall,
+        "wall_s_timed_region": round(wall, 4),
         "clocks": clk,
         "e2e": {"value": N / (serve_ms * 1e-3), "unit": "stencils/s",
                 "h2d_bytes_per_step": int(N * 8), "d2h_bytes_per_step": int(3 * N * mu * 8),
                 "ms_per_step": serve_ms,
-                "loop": "set_potential from pinned host memory, build, get_rows_async of Q, C, "
-                        "P into pinned host memory (step k's copies overlap step k + 1's "
-                        "build); L2 flush inside the region; ends after the last copy landed",
+                "loop": "set_potential from pinned host v, build, get_rows_async of Q, C, P "
+                        "into pinned host memory overlapping the next build; ends when the "
+                        "last rows land",
                 "one_step_at_a_time": {"value": N / (float(np.median(e2e_ms)) * 1e-3),
-                                       "ms_per_step": float(np.median(e2e_ms)),
-                                       "loop": "each step's host copies waited for before "
-                                               "the next step starts (get_rows)"}},
+                                       "ms_per_step": float(np.median(e2e_ms))}},
     }
-    if train_info is not None:
-        out["config"]["training"] = train_info
-    if not args.no_variants:
-        out["variants"] = variants(args, torch)
-    if not args.no_solve:
-        out["nd_solve"] = solve_block(args, torch, fp64_peak, peaks["hbm_gbs"])
+    detail = {"kernels": kern, "lattice_domains": sizes, "peak_source": peak_src,
+              "workload_text": WORKLOAD_TEXT.get(args.workload, "")}
+    if train_info:
+        detail["training"] = {str(k): v for k, v in train_info.items()}
+    if ws == 1 and not args.no_forms:
+        res["forms"], detail["forms"] = forms_block(args, torch, mlps, peaks)
+    if ws == 1 and args.detail:
+        fp64_gemm = measure_fp64_gemm(torch)
+        detail["fp64_gemm_tflops"] = fp64_gemm
+        detail["variants"] = variants(args, torch, peaks)
+        if not args.no_solve:
+            detail["nd_solve"] = solve_block(args, torch, fp64_gemm, peaks["hbm_gbs"])
+    for m in mlps.values():
+        m.close()
     if ws == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.workload, args.policy, budget_s=args.cpu_budget)
-    print(json.dumps(out))
+        res["cpu_baseline"] = cpu_baseline(args.workload, args.policy, args.cpu_budget)
+    if args.detail:
+        detail["result"] = res
+        with open(args.detail, "w") as fh:
+            json.dump(detail, fh, indent=1)
+        res["detail"] = os.path.basename(args.detail)
+    print(contract_line(res), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
+def _r(x, nd=4):
+    """Round to nd significant digits (keeps the result line short)."""
+    if x is None or not isinstance(x, (int, float)) or x == 0 or not np.isfinite(x):
+        return x
+    return float(f"{x:.{nd}g}")
+
+
+def contract_line(res: dict) -> str:
+    """The one-line JSON result: the contract keys, compact, below LINE_LIMIT bytes."""
+    keep_roof = ("bound", "kernel", "achieved", "peak", "unit", "frac", "traffic", "peak_source")
+    out = {k: res[k] for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup",
+                               "ms_per_step", "higher_is_better", "scaling", "vs_baseline",
+                               "dtype", "data", "config") if k in res}
+    out["value"] = _r(out.get("value"), 6)
+    out["ms_per_step"] = _r(out.get("ms_per_step"), 6)
+    if res.get("roofline"):
+        out["roofline"] = {k: (_r(v) if isinstance(v, float) else v)
+                           for k, v in res["roofline"].items() if k in keep_roof}
+    if res.get("rows_roofline"):
+        r = res["rows_roofline"]
+        out["rows_roofline"] = {k: _r(r[k]) for k in ("achieved", "peak", "frac")} | {
+            "unit": r["unit"], "traffic": r.get("traffic")}
+    for k in ("gpu_launches", "clocks"):
+        if k in res:
+            out[k] = res[k]
+    if "e2e" in res:
+        e = res["e2e"]
+        out["e2e"] = {"value": _r(e["value"], 6), "unit": e["unit"],
+                      "h2d_bytes_per_step": e["h2d_bytes_per_step"],
+                      "d2h_bytes_per_step": e["d2h_bytes_per_step"],
+                      "ms_per_step": _r(e["ms_per_step"]), "loop": e.get("loop", "")[:160]}
+        if "one_step_at_a_time" in e:
+            out["e2e"]["one_step_at_a_time"] = _r(e["one_step_at_a_time"]["value"])
+    if "cpu_baseline" in res:
+        c = res["cpu_baseline"]
+        out["cpu_baseline"] = {"value": _r(c["value"]), "unit": c["unit"], "cores": c["cores"],
+                               "kind": c["kind"], "sample": c["sample"][:240]}
+        if c.get("single_core"):
+            s = c["single_core"]
+            out["cpu_baseline"]["single_core"] = {"value": _r(s["value"]), "cores": s["cores"]}
+    if res.get("forms"):
+        out["forms"] = [{k: (_r(v) if isinstance(v, float) else v) for k, v in f.items()}
+                        for f in res["forms"]]
+    for k in ("detail", "impl"):
+        if k in res:
+            out[k] = res[k]
+    line = json.dumps(out, separators=(",", ":"))
+    if len(line.encode()) > LINE_LIMIT:  # drop the optional parts, never the contract keys
+        for k in ("forms", "rows_roofline"):
+            out.pop(k, None)
+            line = json.dumps(out, separators=(",", ":"))
+            if len(line.encode()) <= LINE_LIMIT:
+                break
+    return line
+
+
+FORMS = [("helm2d_n1024", "fp64"), ("helm2d_n1024", "mixed"), ("helm2d_n1024", "learned"),
+         ("schr3d_n64", "fp64"), ("schr3d_n64", "mixed"), ("schr3d_n64", "learned")]
+
+
+def forms_block(args, torch, mlps, peaks):
+    """stencils/s and the dominant kernel's roofline fraction of FP64, mixed and learned at
+    2D n = 1024 and 3D n = 64 (per-point shifts), on the same GPU, same step definition."""
+    short, full = [], []
+    for wl, mode in FORMS:
+        d = 2 if wl.startswith("helm2d") else 3
+        try:
+            r = time_config(torch, wl, args.policy, mode, steps=20, warmup=3, peaks=peaks,
+                            mlp=mlps.get(d) if mode == "learned" else None)
+        except Exception as exc:  # a form must not hide the main line
+            short.append({"workload": wl, "mode": mode, "error": str(exc)[:120]})
+            full.append(short[-1])
+            continue
+        full.append(r)
+        roof = r.get("roofline") or {}
+        s = {"workload": wl, "mode": mode, "mode_used": r["mode_used"], "value": r["value"],
+             "ms": r["ms_per_step"], "kernel": roof.get("kernel"), "bound": roof.get("bound"),
+             "frac": roof.get("frac")}
+        if "quality" in r:
+            s.update(r["quality"])
+        short.append(s)
+    return short, full
+
+
 def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup: int,
-                mlp=None, stream=None, t: int = 1, nd_leaf: int = 0):
+                mlp=None, stream=None, t: int = 1, nd_leaf: int = 0, peaks=None):
     """stencils/s of one configuration (same step, L2 flush and events as the main line)."""
     from lsp_inputs import make_workload
     from paper_1607_02560_gb300 import Context
 
     v = make_workload(workload)
+    d, n, N = v.ndim, v.shape[0], v.size
     stream = stream or torch.cuda.Stream()
-    ctx = Context(v.ndim, v.shape[0], stream=stream)
+    ctx = Context(d, n, stream=stream)
     if mlp is not None:
         ctx.set_mlp(mlp)
     v_dev = torch.from_numpy(v).to("cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    kw = dict(policy=policy, mode=mode, use_graph=True, t=t, nd_leaf=nd_leaf)
     with torch.cuda.stream(stream):
         for _ in range(warmup):
             ctx.set_potential(v_dev)
-            ctx.build_stencils(policy=policy, mode=mode, use_graph=True, t=t, nd_leaf=nd_leaf)
+            ctx.build_stencils(**kw)
         ctx.synchronize()
         tot = 0.0
         for _ in range(steps):
@@ -419,66 +568,67 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             ctx.set_potential(v_dev)
-            ctx.build_stencils(policy=policy, mode=mode, use_graph=True, t=t, nd_leaf=nd_leaf)
+            ctx.build_stencils(**kw)
             e1.record(stream)
             torch.cuda.synchronize()
             tot += e0.elapsed_time(e1)
         used = ctx.mode_used()
-        ns = len(ctx.get_shift_table(with_sidx=False)["s"]) if used != "learned" else None
-        extra = {}
+        m_list, ns = None, None
+        if used != "learned":
+            s = ctx.get_shift_table(with_sidx=False)["s"]
+            ns = len(s)
+            m_list = np.round((s / (np.pi ** 2) - 2) / 4).astype(np.int64)
+        out = {"workload": workload, "policy": policy, "mode": mode, "mode_used": used, "t": t,
+               "nd_leaf": nd_leaf, "value": N * steps / (tot * 1e-3), "unit": "stencils/s",
+               "ms_per_step": tot / steps, "shifts": ns}
         if used == "learned":
             q_learned = ctx.get_rows("Q").copy()
             ctx.build_stencils(policy=policy, mode="fp64")
             err = np.abs(q_learned - ctx.get_rows("Q")).max(axis=1)  # per point
-            extra["max_abs_dalpha_vs_fp64"] = float(err.max())
-            extra["dalpha_vs_fp64_per_point"] = {
-                "p50": float(np.percentile(err, 50)), "p99": float(np.percentile(err, 99)),
-                "p99.9": float(np.percentile(err, 99.9)), "max": float(err.max()),
-                "frac_above_1e-2": float(np.mean(err > 1e-2))}
-            ctx.build_stencils(policy=policy, mode=mode, use_graph=True, t=t, nd_leaf=nd_leaf)
+            out["quality"] = {"dalpha_p50": float(np.percentile(err, 50)),
+                              "dalpha_p99": float(np.percentile(err, 99)),
+                              "dalpha_max": float(err.max())}
+            ctx.build_stencils(**kw)
         ctx.kernel_timing(True)
         for _ in range(5):
             flush.zero_()
             ctx.set_potential(v_dev)
-            ctx.build_stencils(policy=policy, mode=mode, use_graph=True, t=t, nd_leaf=nd_leaf)
+            ctx.build_stencils(**kw)
         ctx.synchronize()
-        kt = {k: round(ms / max(cnt, 1), 4) for k, (ms, cnt) in ctx.kernel_times().items()}
+        kt = ctx.kernel_times()
         ctx.kernel_timing(False)
     ctx.close()
-    out = {"workload": workload, "policy": policy, "mode": mode, "mode_used": used, "t": t,
-           "nd_leaf": nd_leaf,
-           "value": v.size * steps / (tot * 1e-3), "unit": "stencils/s",
-           "ms_per_step": tot / steps, "shifts": ns, "kernel_ms_per_launch": kt}
-    out.update(extra)
+    mu = (2 * t + 1) ** d
+    out["kernel_ms_per_launch"] = {k: round(ms / max(cnt, 1), 4) for k, (ms, cnt) in kt.items()}
+    if peaks is not None and t == 1:
+        sizes = lattice_domain_sizes(m_list, n, d) if m_list is not None else []
+        out["roofline"] = dominant_roofline(kt, n, d, N, mu, sizes, used, peaks, workload)
     return out
 
 
-def train_for(torch, workload: str, steps: int, stream):
-    """Train the surrogate on 16 other seeds (100-115) of the workload."""
+def train_for(torch, d: int, steps: int, stream):
+    """Train the surrogate on training potentials that none of the timed workloads uses: in 2D
+    8 seeds (100-107) of the n = 256 generator and 8 seeds (108-115) of the n = 1024 one, in 3D
+    16 seeds (100-115) of the n = 64 generator."""
     from lsp_inputs import make_workload
     from paper_1607_02560_gb300.learned import train_surrogate
 
-    pots = [make_workload(workload, seed=s) for s in range(100, 116)]
+    if d == 2:
+        pots = ([make_workload("helm2d_n256", seed=s) for s in range(100, 108)]
+                + [make_workload("helm2d_n1024", seed=s) for s in range(108, 116)])
+        seeds = "helm2d_n256 100-107 + helm2d_n1024 108-115"
+    else:
+        pots = [make_workload("schr3d_n64", seed=s) for s in range(100, 116)]
+        seeds = "schr3d_n64 100-115"
     t0 = time.time()
     with torch.cuda.stream(stream):
-        mlp, losses = train_surrogate(pots[0].ndim, pots, samples_per_potential=65536,
-                                      steps=steps, batch=4096, lr=2e-3, stream=stream)
+        mlp, losses = train_surrogate(d, pots, samples_per_potential=65536, steps=steps,
+                                      batch=4096, lr=2e-3, stream=stream)
     torch.cuda.synchronize()
-    info = {"potentials": len(pots), "seeds": "100-115", "pairs": 16 * 65536, "steps": steps,
-            "batch": 4096, "seconds": round(time.time() - t0, 2),
+    info = {"potentials": len(pots), "seeds": seeds, "pairs": len(pots) * 65536,
+            "steps": steps, "batch": 4096, "seconds": round(time.time() - t0, 2),
             "final_loss": float(np.mean(losses[-50:]))}
     return mlp, info
-
-
-def learned_variant(torch, workload: str, steps: int = 3000):
-    """Train the surrogate on 16 other seeds of the workload, then time the learned build."""
-    stream = torch.cuda.Stream()
-    mlp, info = train_for(torch, workload, steps, stream)
-    out = time_config(torch, workload, "local", "learned", steps=20, warmup=3, mlp=mlp,
-                      stream=stream)
-    out["training"] = info
-    mlp.close()
-    return out
 
 
 def solve_variant(torch, n: int, policy: str = "paper", fp64_peak: float | None = None,
@@ -588,23 +738,19 @@ def run_solve_only(args):
     B.build()
     torch.cuda.set_device(0)
     peaks, _ = load_peaks()
-    fp64_peak = measure_fp64_peak(torch)
+    fp64_peak = measure_fp64_gemm(torch)
     out = {"metric": "nested dissection setup / solve", "n_gpus": 1,
            "nd_solve": solve_block(args, torch, fp64_peak, peaks["hbm_gbs"])}
     print(json.dumps(out))
 
 
-def variants(args, torch):
-    """The metric's other forms on the same GPU: FP64 vs mixed, 2D n=1024 vs 3D n=64, and the
-    paper's shift policy."""
+def variants(args, torch, peaks):
+    """The paper's shift policy and multi-t builds on the same GPU (detail file only)."""
     out = []
-    for wl, pol, mode in [("helm2d_n1024", "local", "mixed"), ("schr3d_n64", "local", "fp64"),
-                          ("schr3d_n64", "local", "mixed"), ("helm2d_n1024", "paper", "fp64"),
-                          ("helm2d_n1024", "paper", "mixed")]:
-        if (wl, pol, mode) == (args.workload, args.policy, args.mode):
-            continue
+    for wl, pol, mode in [("helm2d_n1024", "paper", "fp64"), ("helm2d_n1024", "paper", "mixed"),
+                          ("schr3d_n64", "paper", "fp64")]:
         try:
-            out.append(time_config(torch, wl, pol, mode, steps=20, warmup=3))
+            out.append(time_config(torch, wl, pol, mode, steps=20, warmup=3, peaks=peaks))
         except Exception as exc:  # a variant must not hide the main line
             out.append({"workload": wl, "policy": pol, "mode": mode, "error": str(exc)[:200]})
     # multi-t (Sec. 4.2): t_j from a nested dissection with leaf boxes of width 8, t_max = 2
@@ -613,70 +759,166 @@ def variants(args, torch):
             out.append(time_config(torch, wl, pol, "fp64", steps=20, warmup=3, t=2, nd_leaf=8))
         except Exception as exc:
             out.append({"workload": wl, "policy": pol, "t": 2, "error": str(exc)[:200]})
-    if not args.no_learned:
-        for wl in ("helm2d_n1024", "schr3d_n64"):
-            try:
-                out.append(learned_variant(torch, wl, args.learned_steps))
-            except Exception as exc:
-                out.append({"workload": wl, "mode": "learned", "error": str(exc)[:300]})
     return out
 
 
-def cpu_baseline(workload: str, policy: str, budget_s: float = 20.0, step_index: int = 0):
-    """The oracle, as it stands, on the host cores: a sample of shifts plus the row assembly
-    of every point, extrapolated to the workload's full shift list."""
-    import oracle as O
-    from lsp_inputs import make_workload
+# ---- the oracle on the host cores ----------------------------------------------------------
 
-    v = make_workload(workload)
-    n, d = v.shape[0], v.ndim
+def _oracle_shifts(job):
+    """Worker task: the oracle's per-shift stencil (a3-a6) for each shift of the job."""
+    n, d, shifts = job
+    import oracle as O
+
     t0 = time.perf_counter()
-    st = O.build_stencils(v, policy, shift_subset=[0])  # shift list + s_j + row assembly
-    t_rows = time.perf_counter() - t0
-    ns = len(st["S"])
-    rng = np.random.default_rng(100 + step_index)
-    order = rng.permutation(ns)
-    done, t_sh = 0, 0.0
-    while done < ns and (t_sh + t_rows) < budget_s:
-        t1 = time.perf_counter()
-        O.stencil_for_shift(n, d, float(st["S"][order[done]]))
-        t_sh += time.perf_counter() - t1
-        done += 1
-    per_shift = t_sh / max(done, 1)
-    total = t_rows + per_shift * ns
-    return {"value": v.size / total, "unit": "stencils/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} of {ns} shifts (seeded) timed at {per_shift:.3f} s each + "
-                      f"shift assignment and row assembly of all {v.size} points "
-                      f"({t_rows:.2f} s); extrapolated to all shifts"
-                      + ("" if done == ns else " (extrapolated)"),
-            "seconds": t_sh + t_rows}
+    for s in shifts:
+        O.stencil_for_shift(n, d, float(s))
+    return time.perf_counter() - t0
+
+
+class OracleSampler:
+    """The oracle, as it stands, timed on `threads` host processes on a bounded sample.
+
+    The shift list, the per-point shift assignment and the row assembly of every point (the
+    oracle's build_stencils with no shift solved but one) run once in this process; the
+    per-shift solves of a seeded sample of shifts run on `threads` worker processes (started
+    with spawn, one numpy/BLAS thread each), and the wall time per shift extrapolates to the
+    whole shift list."""
+
+    def __init__(self, workload: str, policy: str, threads: int):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        self.workload, self.policy, self.threads = workload, policy, threads
+        self.ex = None
+        if threads > 1:
+            self.ex = cf.ProcessPoolExecutor(max_workers=threads,
+                                             mp_context=mp.get_context("spawn"))
+
+    def close(self):
+        if self.ex is not None:
+            self.ex.shutdown()
+
+    def sample(self, budget_s: float, seed: int = 0) -> dict:
+        import oracle as O
+        from lsp_inputs import make_workload
+
+        v = make_workload(self.workload)
+        n, d = v.shape[0], v.ndim
+        t0 = time.perf_counter()
+        st = O.build_stencils(v, self.policy, shift_subset=[0])  # shift list + s_j + rows
+        t_rows = time.perf_counter() - t0
+        S = st["S"]
+        ns = len(S)
+        order = np.random.default_rng(100 + seed).permutation(ns)
+        done, wall = 0, 0.0
+        if self.ex is None:
+            while done < ns and (done == 0 or wall + t_rows < budget_s):
+                wall += _oracle_shifts((n, d, [S[order[done]]]))
+                done += 1
+        else:
+            per = 2  # shifts per task
+            if seed == 0 or not getattr(self, "_warm", False):  # import the oracle in workers
+                list(self.ex.map(_oracle_shifts, [(n, d, [S[order[0]]])] * self.threads))
+                self._warm = True
+            while done < ns and (done == 0 or wall + t_rows < budget_s):
+                batch = order[done:done + self.threads * per]
+                jobs = [(n, d, [S[i] for i in batch[k:k + per]]) for k in range(0, len(batch), per)]
+                t1 = time.perf_counter()
+                list(self.ex.map(_oracle_shifts, jobs))
+                wall += time.perf_counter() - t1
+                done += len(batch)
+        per_shift = wall / max(done, 1)
+        total = t_rows + per_shift * ns
+        return {"value": v.size / total, "unit": "stencils/s", "cores": self.threads,
+                "kind": "oracle", "seconds": wall + t_rows,
+                "sample": f"{done} of {ns} seeded shifts on {self.threads} process(es), "
+                          f"{per_shift * 1e3:.1f} ms wall per shift, + shift assignment and row "
+                          f"assembly of all {v.size} points ({t_rows:.2f} s, one core); "
+                          + ("all shifts" if done == ns else "extrapolated to all shifts")}
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def thread_env(threads: int = 1) -> dict:
+    """Environment that fixes the numpy/BLAS thread count of a fresh interpreter."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+              "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[k] = str(threads)
+    return env
+
+
+def cpu_baseline(workload: str, policy: str, budget_s: float = 15.0) -> dict:
+    """The oracle on one host core and on all host cores, each in a fresh interpreter whose
+    numpy/BLAS thread count is fixed before numpy loads."""
+    res = {}
+    for label, procs in (("single_core", 1), ("all", host_cores())):
+        cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--cpu-only",
+               "--workload", workload, "--policy", policy, "--cpu-procs", str(procs),
+               "--cpu-budget", str(budget_s)]
+        p = subprocess.run(cmd, env=thread_env(1), capture_output=True, text=True,
+                           timeout=budget_s * 6 + 120)
+        lines = [ln for ln in p.stdout.splitlines() if ln.startswith("{")]
+        if p.returncode != 0 or not lines:
+            res[label] = {"error": (p.stderr or "no output")[-200:]}
+            continue
+        res[label] = json.loads(lines[-1])
+    main = res.get("all", {})
+    if "value" not in main:
+        main = res.get("single_core", {})
+    out = dict(main)
+    if "value" in res.get("single_core", {}) and res["single_core"] is not main:
+        out["single_core"] = res["single_core"]
+    return out
+
+
+def run_cpu_only(args):
+    s = OracleSampler(args.workload, args.policy, args.cpu_procs)
+    try:
+        r = s.sample(args.cpu_budget)
+    finally:
+        s.close()
+    print(json.dumps(r))
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands on all host cores, one bounded sample of the
+    workload per step; rank 0 alone runs and prints."""
     ws, rank, _ = dist_info()
     if rank != 0:
         return
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    if os.environ.get("OMP_NUM_THREADS") != "1":
+        # fix numpy/BLAS threads before numpy loads: re-run this arm in a fresh interpreter
+        p = subprocess.run([sys.executable, *sys.argv], env=thread_env(1))
+        sys.exit(p.returncode)
+    procs = args.cpu_procs or host_cores()
+    sampler = OracleSampler(args.workload, args.policy, procs)
     vals = []
-    budget = max(2.0, args.ref_step_s)
-    for k in range(args.warmup + args.steps):
-        cb = cpu_baseline(args.workload, args.policy, budget_s=budget, step_index=k)
-        if k >= args.warmup:
-            vals.append(cb)
+    try:
+        for k in range(args.warmup + args.steps):
+            cb = sampler.sample(max(0.2, args.ref_step_s), seed=k)
+            if k >= args.warmup:
+                vals.append(cb)
+    finally:
+        sampler.close()
     value = float(np.median([c["value"] for c in vals]))
-    last = vals[-1]
     out = {"impl": "reference", "metric": METRIC,
            "value": value, "unit": "stencils/s", "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": float(np.mean([c["seconds"] for c in vals])) * 1e3,
+           "warmup": args.warmup,
+           "ms_per_step": float(np.mean([c["seconds"] for c in vals])) * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic",
-           "config": {"workload": args.workload, "text": WORKLOAD_TEXT.get(args.workload, ""),
-                      "policy": args.policy, "mode": "fp64"},
-           "cpu_baseline": {"value": value, "unit": "stencils/s", "cores": 1, "kind": "oracle",
-                            "sample": "per step: " + last["sample"]},
+           "config": {"workload": args.workload, "policy": args.policy, "mode": "fp64"},
+           "cpu_baseline": {"value": value, "unit": "stencils/s", "cores": procs,
+                            "kind": "oracle", "sample": "per step: " + vals[-1]["sample"]},
            "e2e": {"value": value, "unit": "stencils/s", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(out))
+    print(json.dumps(out, separators=(",", ":")))
 
 
 def main():
@@ -688,26 +930,33 @@ def main():
     ap.add_argument("--policy", default="local", choices=["local", "paper", "mean"])
     ap.add_argument("--mode", default="fp64", choices=["fp64", "mixed", "learned"])
     ap.add_argument("--learned-steps", type=int, default=3000,
-                    help="training steps of the surrogate (learned mode and variants)")
-    ap.add_argument("--no-variants", action="store_true")
+                    help="training steps of the surrogate (learned mode and forms)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP64 / mixed / learned summaries at 2D n=1024 and 3D n=64")
+    ap.add_argument("--detail", default="",
+                    help="write per-kernel tables, variants and the preconditioner solve here")
     ap.add_argument("--no-solve", action="store_true",
-                    help="skip the nested-dissection / GMRES measurements")
+                    help="skip the nested-dissection / GMRES measurements of --detail")
     ap.add_argument("--solve-n", default="256,512,1024",
                     help="grid sizes of the nested-dissection / GMRES measurements")
     ap.add_argument("--solve-n3", default="16,32",
                     help="3D grid sizes of the nested-dissection / GMRES measurements")
     ap.add_argument("--solve-only", action="store_true",
                     help="print only the nested-dissection / GMRES measurements (profiling)")
-    ap.add_argument("--no-learned", action="store_true", help="skip training the surrogate")
     ap.add_argument("--n", type=int, default=None, help="rescale the workload's grid (small cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
-    ap.add_argument("--ref-step-s", type=float, default=4.0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-only", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-procs", type=int, default=0, help="host processes of the oracle")
+    ap.add_argument("--ref-step-s", type=float, default=3.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.cpu_only:
+        args.cpu_procs = max(1, args.cpu_procs)
+        run_cpu_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.solve_only:
         run_solve_only(args)
