@@ -265,9 +265,10 @@ lsp_status lsp_get_mode_used(const lsp_ctx* ctx, int* mode);
  * values: the potential v, the input u and the output y (y may alias u). d in {2, 3}, n a power
  * of two >= 8, and n^d <= LSP_NOALLOC_MAX_POINTS; larger grids return LSP_ERR_ARG (use a
  * context). The work is issued on cuda_stream (a cudaStream_t; NULL = legacy default stream).
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture. Every call on a device
- * shares the one array: calls whose GPU work may overlap (different streams, no ordering)
+ * Every call looks up the array's device address (cudaGetSymbolAddress) in the current
+ * device's current context; the lookup allocates nothing. The first call in a context also
+ * loads the library's device code there, so make that first call before any stream capture.
+ * Every call on a device shares the one array: calls whose GPU work may overlap (different streams, no ordering)
  * race and give wrong results. Each call overwrites the whole work array before reading it,
  * so nothing needs clearing. Errors: LSP_ERR_ARG for bad sizes or NULL pointers,
  * LSP_ERR_CUDA if the address lookup or a launch fails.

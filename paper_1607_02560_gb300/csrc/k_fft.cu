@@ -37,8 +37,11 @@ __device__ __forceinline__ void fft_line(double2* x, int n, int logn, const doub
 }
 
 // Lines along `axis` (stride S = n^(d-1-axis) between elements); one line per block.
-__global__ void k_fft_axis(double2* __restrict__ Z, const double* __restrict__ u,
-                           const double* __restrict__ v, double* __restrict__ y, int d, int n,
+// u and y may be the same array (y = (L + diag v) u in place): the output pass reads u[g]
+// before it writes y[g], element by element in the same thread, and no other pass reads u
+// after the first one, so neither pointer is declared __restrict__.
+__global__ void k_fft_axis(double2* __restrict__ Z, const double* u,
+                           const double* __restrict__ v, double* y, int d, int n,
                            int logn, int axis, int64_t nlines, const double2* __restrict__ tw,
                            int mode, int fwd_first) {
   extern __shared__ double2 line[];
@@ -86,7 +89,8 @@ __global__ void k_fft_axis(double2* __restrict__ Z, const double* __restrict__ u
       const int64_t g = base + (int64_t)i * S;
       if (mode == kOutput || mode == kAll) {
         const double inv_n = 1.0 / (double)nlines / (double)n;  // 1/N (exact, power of two)
-        y[g] = fma(v[g], u[g], line[i].x * inv_n);
+        const double ug = u[g];
+        y[g] = fma(v[g], ug, line[i].x * inv_n);
       } else {
         Z[g] = line[i];
       }
@@ -150,15 +154,8 @@ namespace {
 
 constexpr int64_t kNoAllocMaxPoints = (int64_t)1 << 20;  // must match LSP_NOALLOC_MAX_POINTS
 constexpr int kNoAllocMaxHalfN = 2048;
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) double2 g_noalloc_work[kNoAllocMaxPoints];
 static __device__ __align__(256) double2 g_noalloc_twiddle[kNoAllocMaxHalfN];
-
-// Host-side copies of the arrays' device addresses, one per device ordinal. The symbol names
-// themselves are host stand-ins, not device addresses, so they are never passed to a kernel.
-double2* g_work_addr[kMaxDevices];
-double2* g_tw_addr[kMaxDevices];
 
 // exp(-2 pi i j / n), j < n/2, with the CUDA math library's sincospi.
 __global__ void k_noalloc_twiddles(double2* __restrict__ tw, int n) {
@@ -182,23 +179,19 @@ extern "C" lsp_status lsp_apply_operator_noalloc(int d, int n, const double* v_d
   for (int i = 0; i < d; ++i) N *= n;
   if (N > kNoAllocMaxPoints) return LSP_ERR_ARG;  // larger grids need the context path
   if (!v_dev || !u_dev || !y_dev) return LSP_ERR_ARG;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LSP_ERR_CUDA;
-  // One-time set-up per device (this device is current): look up the arrays' addresses.
-  if (!g_work_addr[dev] || !g_tw_addr[dev]) {
-    double2* w = nullptr;
-    double2* t = nullptr;
-    if (cudaGetSymbolAddress((void**)&w, g_noalloc_work) != cudaSuccess ||
-        cudaGetSymbolAddress((void**)&t, g_noalloc_twiddle) != cudaSuccess) {
-      cudaGetLastError();
-      return LSP_ERR_CUDA;
-    }
-    g_work_addr[dev] = w;
-    g_tw_addr[dev] = t;
+  // The symbol names are host-side stand-ins, not device addresses, so they are never passed
+  // to a kernel. Their device addresses are looked up on every call, in the current device's
+  // current context: the lookup allocates nothing, and a cached address could outlive a
+  // context that was torn down and created again. The first call in a context loads the
+  // library's device code there, so make it before any stream capture.
+  double2* Z = nullptr;
+  double2* tw = nullptr;
+  if (cudaGetSymbolAddress((void**)&Z, g_noalloc_work) != cudaSuccess ||
+      cudaGetSymbolAddress((void**)&tw, g_noalloc_twiddle) != cudaSuccess) {
+    cudaGetLastError();
+    return LSP_ERR_CUDA;
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
-  double2* Z = g_work_addr[dev];
-  double2* tw = g_tw_addr[dev];
   int logn = 0;
   while ((1 << logn) < n) ++logn;
   const int64_t nlines = N / n;

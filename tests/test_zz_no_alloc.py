@@ -46,6 +46,32 @@ def test_noalloc_apply_matches_context_apply_on_two_calls(name, n):
         assert np.abs(b - O.apply_operator(v, u)).max() <= 1e-13 * scale_of(u), call
 
 
+def test_noalloc_apply_in_place_matches_context_apply():
+    # y may be the same array as u: the result overwrites the input
+    import torch
+    from paper_1607_02560_gb300 import Context, build, lsp
+
+    build.build()
+    n = 128
+    v = make_workload("helm2d_n256", n=n)
+    stream = torch.cuda.Stream()
+    ctx = Context(2, n, stream=stream)
+    ctx.set_potential(v)
+    v_dev = torch.from_numpy(v).cuda()
+    u = np.random.default_rng(5).standard_normal(v.shape)
+    y_ctx = torch.empty(v.shape, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    ctx.apply_operator(torch.from_numpy(u).cuda(), y_ctx)
+    ctx.synchronize()
+    for call in range(2):
+        buf = torch.from_numpy(u).cuda()
+        torch.cuda.synchronize()
+        lsp.apply_operator_noalloc(2, n, v_dev, buf, buf, stream=stream)
+        stream.synchronize()
+        scale = (4 * O.PI2 * 2 * (n / 2) ** 2 + np.abs(v).max()) * np.abs(u).max()
+        assert np.abs(buf.cpu().numpy() - y_ctx.cpu().numpy()).max() <= 1e-13 * scale, call
+
+
 def test_noalloc_rejects_grids_beyond_its_fixed_array():
     import ctypes
     from paper_1607_02560_gb300 import build, lsp
