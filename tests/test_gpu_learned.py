@@ -1,7 +1,8 @@
 """Learned stencils on the GPU (tcgen05 forward/backward, Adam) against the CPU oracles.
 
-* forward and gradients of the network against the numpy FP64 definition (oracle/mlp_oracle),
-  with the same bf16-rounded weights; tolerance set by bf16 activations (about 1e-2 relative);
+* forward and gradients of the network (2D and 3D) against the numpy FP64 definition
+  (oracle/mlp_oracle), with the same bf16-rounded weights, entry by entry; tolerance set by
+  bf16 activations (a few percent of each entry plus a floor for entries that cancel);
 * training lowers the loss;
 * a network trained on eigen-path stencils reproduces them: alpha close to the FP64 path, the
   sparsification residual ||alpha^T G[mu, mu^c]|| within a small factor of the optimum
@@ -64,43 +65,69 @@ def pool_2d(mlp, stream, n=64, seeds=(100, 101), samples=8192):
     return make_pool(mlp, pots, samples, stream)
 
 
-def test_forward_and_gradients_match_oracle(stream):
+def pool_3d(mlp, stream, n=16, seeds=(100, 101), samples=4096):
+    from paper_1607_02560_gb300.learned import make_pool
+    pots = [make_workload("schr3d_n64", seed=s, n=n) for s in seeds]
+    return make_pool(mlp, pots, samples, stream)
+
+
+def close_entrywise(g, ref, rel=5e-2, floor=5e-2):
+    """|g - ref| <= rel |ref| + floor rms(ref), entry by entry. bf16 activations and operands
+    (relative rounding 2^-8 per factor, a few percent through three layers) set rel; the floor
+    covers entries that cancel to near zero. Returns the largest normalised error."""
+    scale = rel * np.abs(ref) + floor * np.sqrt(np.mean(ref ** 2))
+    return float((np.abs(g - ref) / scale).max())
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_forward_and_gradients_match_oracle(stream, d):
     import torch
     from paper_1607_02560_gb300 import Mlp
-    mlp = Mlp(2, seed=5, stream=stream)
-    X, T = pool_2d(mlp, stream)
+    mlp = Mlp(d, seed=5, stream=stream)
+    X, T = (pool_2d if d == 2 else pool_3d)(mlp, stream)
     torch.cuda.synchronize()
     mlp.fit_normalization(X, T, X.shape[0])
     B = 256
     Y = torch.empty((B, mlp.outp), dtype=torch.float32, device="cuda")
     mlp.forward(X[:B], B, Y)
     torch.cuda.synchronize()
-    W, b, norm, K0, OUTP = unpack(mlp.get_params(), 2)
+    W, b, norm, K0, OUTP = unpack(mlp.get_params(), d)
+    nout = mlp.out
     x = normalised_inputs(X[:B].cpu().numpy(), norm, K0)
     y_ref, _ = MO.mlp_forward(x, W, b)
     y = Y.cpu().numpy()
     assert np.abs(y - y_ref).max() <= 2e-2 * max(1.0, np.abs(y_ref).max())
-    # gradients of mean((y - t_norm)^2) over the real outputs
+    # gradients of mean((y - t_norm)^2) over the real outputs, entry by entry
     grads = np.empty(mlp.nweights, dtype=np.float32)
     loss = mlp.train_step(X[:B], T[:B], B, 0.0, apply=False, grads=grads)
-    t = (T[:B].cpu().numpy().astype(np.float64) - norm[2:2 + 18]) / norm[2 + OUTP:2 + OUTP + 18]
+    t = ((T[:B].cpu().numpy().astype(np.float64) - norm[2:2 + nout])
+         / norm[2 + OUTP:2 + OUTP + nout])
     tp = np.zeros((B, OUTP))
-    tp[:, :18] = t
-    # the oracle's loss averages over OUTP columns; rescale to the 18 real outputs
+    tp[:, :nout] = t
+    # the oracle's loss averages over OUTP columns; rescale to the real outputs
     loss_ref, dW, db = MO.mlp_backward(x, tp, W, b)
-    loss_ref *= OUTP / 18
+    loss_ref *= OUTP / nout
     assert abs(loss - loss_ref) <= 3e-2 * loss_ref
     off = 0
+    worst = []
     for layer, (n, k) in enumerate([(256, K0), (256, 256), (256, 256), (OUTP, 256)]):
-        g = grads[off:off + n * k].reshape(n, k)
-        ref = dW[layer] * OUTP / 18
-        rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
-        assert rel < 5e-2, (layer, rel)
+        g = grads[off:off + n * k].reshape(n, k).astype(np.float64)
+        ref = dW[layer] * OUTP / nout
+        if layer == 0:  # input columns past the real features are zero padding on both sides
+            g, ref = g[:, :mlp.nf], ref[:, :mlp.nf]
+        if layer == 3:  # output rows past the real outputs carry no loss
+            g, ref = g[:nout], ref[:nout]
+        ew = close_entrywise(g, ref)
         off += n * k
-        gb = grads[off:off + n]
-        rb = db[layer] * OUTP / 18
-        assert np.linalg.norm(gb - rb) / np.linalg.norm(rb) < 5e-2, layer
+        gb = grads[off:off + n].astype(np.float64)
+        rb = db[layer] * OUTP / nout
+        if layer == 3:
+            gb, rb = gb[:nout], rb[:nout]
+        eb = close_entrywise(gb, rb)
+        worst.append((round(ew, 3), round(eb, 3)))
+        assert ew <= 1.0 and eb <= 1.0, (layer, ew, eb)
         off += n
+    print(f"d={d}: largest entrywise gradient error / tolerance per layer (W, b): {worst}")
 
 
 def test_training_lowers_the_loss(stream):
@@ -168,6 +195,57 @@ def test_learned_stencils_are_judged_by_the_eigen_path(stream, trained_2d_n32):
         gold = json.load(fh)["iterations"]["local/2.0"]
     _, it, res, info = O.gmres_solve(v, gaussian_source(n, 2, 2.0), mats["P"], mats["C"])
     assert info == 0 and it <= gold + 1, (it, gold)
+
+
+@pytest.fixture(scope="module")
+def trained_3d_n16(stream):
+    """A 3D network (5x5x5 patches) trained on eigen-path stencils of 3D n = 16 potentials."""
+    from paper_1607_02560_gb300.learned import train_surrogate
+    pots = [make_workload("schr3d_n64", seed=s, n=16) for s in range(100, 124)]
+    mlp, losses = train_surrogate(3, pots, samples_per_potential=4096, steps=3000, batch=2048,
+                                  lr=2e-3, seed=3, stream=stream)
+    return mlp, losses
+
+
+def test_learned_3d_stencils_are_judged_by_the_eigen_path(stream, trained_3d_n16):
+    """The 3D network on a potential it was not trained on (seed 4): alpha close to the
+    eigen path, the sparsification residual within a small factor of each point's optimum,
+    and the oracle GMRES count within +1 of the eigen path's."""
+    import scipy.sparse
+    from paper_1607_02560_gb300 import Context
+    mlp, losses = trained_3d_n16
+    n, d = 16, 3
+    v = make_workload("schr3d_n64", n=n)
+    ctx = Context(d, n, stream=stream)
+    ctx.set_mlp(mlp)
+    ctx.set_potential(v)
+    ctx.build_stencils(mode="learned")
+    assert ctx.mode_used() == "learned"
+    Ql = ctx.get_rows("Q").copy()
+    ref = O.build_stencils(v, "local")
+    err = np.abs(Ql - ref["Q"]).max()
+    sidx = ref["s_idx"].reshape(-1)
+    worst = 0.0
+    for i, s in enumerate(ref["S"]):
+        st = O.stencil_for_shift(n, d, float(s))
+        pts = np.nonzero(sidx == i)[0]
+        q = Ql[pts]
+        ratio = np.sqrt(np.einsum("pi,ij,pj->p", q, st["A"], q)
+                        / (st["lam1"] * np.einsum("pi,pi->p", q, q)))
+        worst = max(worst, float(ratio.max()))
+    mats = {}
+    for which in "CP":
+        rowptr, colidx, vals = ctx.export_sparse_rows(which)
+        mats[which] = scipy.sparse.csr_matrix((vals, colidx, rowptr), shape=(n ** 3, n ** 3))
+    f = gaussian_source(n, d, 2.0)
+    _, it, _, info = O.gmres_solve(v, f, mats["P"], mats["C"])
+    Pr, Cr = (O.rows_to_csr(ref[k], n, d) for k in "PC")
+    _, it_ref, _, info_ref = O.gmres_solve(v, f, Pr, Cr)
+    print(f"learned 3D n=16: max |d alpha| = {err:.3g}, worst residual / optimum = {worst:.3f}, "
+          f"GMRES {it} vs {it_ref} (eigen path), final loss {np.mean(losses[-50:]):.3g}")
+    assert err < 5e-2
+    assert worst <= 3.0
+    assert info == 0 and info_ref == 0 and it <= it_ref + 1, (it, it_ref)
 
 
 def test_learned_build_falls_back_outside_the_trained_range(stream, trained_2d_n32):

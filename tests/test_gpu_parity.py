@@ -262,8 +262,11 @@ def test_full_size_2d_n1024_sampled():
     for _ in range(2):
         ctx.build_stencils(policy="local", use_graph=True)
     tab = ctx.get_shift_table()
+    # the shifts at v_min and v_max (the ends of the sorted list) and 40 seeded others
     rng = np.random.default_rng(11)
-    sample = sorted(rng.choice(len(tab["s"]), 6, replace=False).tolist()) + [0, len(tab["s"]) - 1]
+    ns = len(tab["s"])
+    sample = sorted(set(rng.choice(np.arange(1, ns - 1), 40, replace=False).tolist())
+                    | {0, ns - 1})
     ref, tols = check_shift_table(tab, v, "local", sample=sample)
     assert check_rows(ctx, v, ref, tols) > 0
     rows_consistent_with_table(ctx, v, tab)
@@ -355,3 +358,39 @@ def test_mixed_mode_full_size_gmres_proxy():
     kap = np.abs(t64["lam"]).max()  # noqa: F841 (kept for the printout)
     print(f"mixed vs fp64 at n=1024: max |d alpha| = {err:.3g}")
     assert err < 1e-2
+
+
+@pytest.mark.parametrize("name,nsample", [("helm2d_n256", 200), ("helm2d_n1024", 24),
+                                          ("schr3d_n64", 0)])
+def test_mixed_mode_full_size_against_the_oracle(name, nsample):
+    """The mixed path at the full sizes of the 2D n = 256, 2D n = 1024 and 3D n = 64
+    workloads, against the FP64 oracle: per shift |d alpha| <= 1e3 u32 kappa (the bound of
+    test_mixed_mode_error_bound), on the shifts at v_min and v_max and a seeded sample of the
+    others (every shift when nsample = 0). Prints the largest |d alpha| / (u32 kappa)."""
+    v = make_workload(name)
+    n, d = v.shape[0], v.ndim
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="local", mode="mixed", use_graph=True)
+    tab = ctx.get_shift_table()
+    ref = O.build_stencils(v, "local", shift_subset=[])
+    assert np.array_equal(tab["s"], ref["S"])
+    assert np.array_equal(tab["s_idx"].reshape(v.shape), ref["s_idx"])
+    ns = len(ref["S"])
+    if nsample and nsample < ns - 2:
+        rng = np.random.default_rng(12)
+        idx = sorted(set(rng.choice(np.arange(1, ns - 1), nsample, replace=False).tolist())
+                     | {0, ns - 1})
+    else:
+        idx = range(ns)
+    worst, worst_abs = 0.0, 0.0
+    for i in idx:
+        st = O.stencil_for_shift(n, d, float(ref["S"][i]))
+        w = np.linalg.eigvalsh(st["A"])
+        kappa = np.abs(w).max() / (w[1] - w[0])
+        err = np.abs(tab["alpha"][i] - st["alpha"]).max()
+        worst = max(worst, err / (U32 * kappa))
+        worst_abs = max(worst_abs, err)
+        assert err <= max(1e-6, 1e3 * U32 * kappa), (i, err, kappa)
+    print(f"mixed {name} full size: {len(idx)} shifts, max |d alpha| = {worst_abs:.3g}, "
+          f"max |d alpha| / (u32 kappa) = {worst:.3g}")
