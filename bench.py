@@ -177,11 +177,12 @@ def lattice_domain_sizes(m_list: np.ndarray, n: int, d: int) -> list[int]:
     return sizes  # [|E_d| = shifts, |E_{d-1}|, ..., |E_1|]
 
 
-def kernel_work(name: str, n: int, d: int, N: int, mu: int, sizes: list[int]):
+def kernel_work(name: str, n: int, d: int, N: int, mu: int, sizes: list[int],
+                mode: str = "fp64"):
     """Algorithmic (amount, kind) of one launch of a kernel, or None.
 
-    kind: "flop" (FP64 or FP32 ALU, by the build's mode), "tensor_flop" (BF16 tensor cores)
-    or "byte" (HBM)."""
+    kind: "flop" (FP64 ALU), "tensor_flop" (BF16 tensor cores), "byte" (HBM) or "l2_byte"
+    (gathers served by L2: the FP32 stages of the mixed mode)."""
     P = n // 2 + 1
     ncls = {1: 3, 2: 6, 3: 10}
     if name.startswith("stage"):
@@ -190,6 +191,13 @@ def kernel_work(name: str, n: int, d: int, N: int, mu: int, sizes: list[int]):
         k = int(name[-1])
         # stage k runs over E_k; sizes lists E_d, E_{d-1}, ..., so E_k = sizes[d - k]
         count = sizes[d - k]
+        if mode == "mixed":
+            # FP32 stages are bound by the gather of the previous table from L2: stage 1 reads
+            # w(l + p^2) for every frequency p in [0, n/2] (4 B each), later stages read both
+            # functions of every class of the previous table at l + p^2 (8 B per class)
+            if k == 1:
+                return count * P * 4, "l2_byte"
+            return count * P * 8 * {2: 3, 3: 6}[k], "l2_byte"
         if k == 1:
             # mirror-paired: per pair 4 add/sub + 6 FMA (16 flops), plus the middle term (12)
             return count * ((n // 4) * 16 + 12), "flop"
@@ -220,10 +228,12 @@ def roofline(name: str, ms_per_launch: float, work, mode: str, peaks: dict,
         bound, unit, ach, peak = "tensor", "TFLOP/s", rate / 1e12, peaks["bf16_tflops"]
         src = "bf16_tflops (burst) of measured peaks"
     elif kind == "flop":
-        fp = "fp32" if mode == "mixed" else "fp64"
-        bound, unit, ach, peak = "alu", "TFLOP/s", rate / 1e12, alu_peak_tflops(fp)
-        src = (f"{fp.upper()} peak from unit counts: {FP64_FLOP_PER_SM_CLK if fp == 'fp64' else FP32_FLOP_PER_SM_CLK}"
-               f" flop/SM/clk x {SMS} SMs x {SM_MAX_MHZ:.0f} MHz")
+        bound, unit, ach, peak = "alu", "TFLOP/s", rate / 1e12, alu_peak_tflops("fp64")
+        src = (f"FP64 peak from unit counts: {FP64_FLOP_PER_SM_CLK} flop/SM/clk x {SMS} SMs x "
+               f"{SM_MAX_MHZ:.0f} MHz")
+    elif kind == "l2_byte":
+        bound, unit, ach, peak = "l2", "GB/s", rate / 1e9, peaks.get("l2_gbs") or float("nan")
+        src = "L2-resident copy (48 MiB, read + write bytes) measured in this run"
     else:
         bound, unit, ach, peak = "hbm", "GB/s", rate / 1e9, peaks["hbm_gbs"]
         src = "hbm_gbs of measured peaks"
@@ -239,7 +249,7 @@ def dominant_roofline(ktimes: dict, n: int, d: int, N: int, mu: int, sizes, mode
     """Roofline of the kernel with the largest total time among those with a work count."""
     best = None
     for name, (ms, cnt) in ktimes.items():
-        w = kernel_work(name, n, d, N, mu, sizes)
+        w = kernel_work(name, n, d, N, mu, sizes, mode)
         if w is None:
             continue
         if best is None or ms > best[1]:
@@ -248,6 +258,21 @@ def dominant_roofline(ktimes: dict, n: int, d: int, N: int, mu: int, sizes, mode
         return None
     name, ms, cnt, w = best
     return roofline(name, ms / max(cnt, 1), w, mode, peaks, (name, workload, mode))
+
+
+def measure_l2_gbs(torch) -> float:
+    """Copy bandwidth of an L2-resident buffer (48 MiB read + 48 MiB written, best of 20)."""
+    a = torch.empty(48 << 20, dtype=torch.uint8, device="cuda").fill_(1)
+    b = torch.empty_like(a)
+    best = 0.0
+    for _ in range(23):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        b.copy_(a)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, 2 * a.numel() / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
 
 
 def measure_fp64_gemm(torch) -> float:
@@ -390,13 +415,14 @@ def run_ours(args):
 
     value = job_throughput(N, args.steps, ws, total_ms)
     peaks, peak_src = load_peaks()
+    peaks = dict(peaks, l2_gbs=measure_l2_gbs(torch))
     sizes = lattice_domain_sizes(m_list, n, d) if m_list is not None else []
     launches = int(sum(c for _, c in ktimes.values()))
     kern = {}
     for name, (ms, cnt) in ktimes.items():
         kern[name] = {"ms_per_launch": ms / max(cnt, 1), "launches": cnt}
-        r = roofline(name, ms / max(cnt, 1), kernel_work(name, n, d, N, mu, sizes), args.mode,
-                     peaks)
+        r = roofline(name, ms / max(cnt, 1), kernel_work(name, n, d, N, mu, sizes, args.mode),
+                     args.mode, peaks)
         if r:
             kern[name].update(achieved=r["achieved"], unit=r["unit"], frac=r["frac"])
     roof = dominant_roofline(ktimes, n, d, N, mu, sizes, args.mode, peaks, args.workload)
@@ -543,7 +569,8 @@ def forms_block(args, torch, mlps, peaks):
 
 
 def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup: int,
-                mlp=None, stream=None, t: int = 1, nd_leaf: int = 0, peaks=None):
+                mlp=None, stream=None, t: int = 1, nd_leaf: int = 0, peaks=None,
+                gmres: bool = True):
     """stencils/s of one configuration (same step, L2 flush and events as the main line)."""
     from lsp_inputs import make_workload
     from paper_1607_02560_gb300 import Context
@@ -582,12 +609,7 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
                "nd_leaf": nd_leaf, "value": N * steps / (tot * 1e-3), "unit": "stencils/s",
                "ms_per_step": tot / steps, "shifts": ns}
         if used == "learned":
-            q_learned = ctx.get_rows("Q").copy()
-            ctx.build_stencils(policy=policy, mode="fp64")
-            err = np.abs(q_learned - ctx.get_rows("Q")).max(axis=1)  # per point
-            out["quality"] = {"dalpha_p50": float(np.percentile(err, 50)),
-                              "dalpha_p99": float(np.percentile(err, 99)),
-                              "dalpha_max": float(err.max())}
+            out["quality"] = learned_quality(torch, ctx, v, v_dev, policy, flush, stream, gmres)
             ctx.build_stencils(**kw)
         ctx.kernel_timing(True)
         for _ in range(5):
@@ -603,6 +625,59 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
     if peaks is not None and t == 1:
         sizes = lattice_domain_sizes(m_list, n, d) if m_list is not None else []
         out["roofline"] = dominant_roofline(kt, n, d, N, mu, sizes, used, peaks, workload)
+    return out
+
+
+GATE_TAU = 2.0  # residual ratio above which a learned stencil takes the eigen path's rows
+
+
+def learned_quality(torch, ctx, v, v_dev, policy: str, flush, stream, gmres: bool = True) -> dict:
+    """What the learned stencils are worth against the eigen path, on this potential:
+    |d alpha| per point against the FP64 build; the per-point residual gate at tau = GATE_TAU
+    (its build time, the fraction of points sent back to the eigen path, and the residual
+    ratio rho = ||alpha^T G[mu, mu^c]|| / sigma_min of the network's stencils); and the GMRES
+    count (the library's nested-dissection factorisation of P and GMRES(40), rtol 1e-6, on a
+    Gaussian point source) with the ungated, gated and FP64 rows."""
+    from lsp_inputs import gaussian_source
+
+    N = v.size
+    ctx.build_stencils(policy=policy, mode="learned")
+    q_learned = ctx.get_rows("Q").copy()
+    ctx.build_stencils(policy=policy, mode="fp64")
+    err = np.abs(q_learned - ctx.get_rows("Q")).max(axis=1)  # per point
+    out = {"dalpha_p50": float(np.percentile(err, 50)), "dalpha_p99": float(np.percentile(err, 99)),
+           "dalpha_max": float(err.max()), "gate_tau": GATE_TAU}
+    kw = dict(policy=policy, mode="learned", learned_gate=GATE_TAU, use_graph=True)
+    for _ in range(3):
+        ctx.build_stencils(**kw)
+    ctx.synchronize()
+    tot, reps = 0.0, 10
+    for _ in range(reps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.set_potential(v_dev)
+        ctx.build_stencils(**kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    nfall, rho = ctx.gate_stats()
+    out.update({"gated_value": N * reps / (tot * 1e-3), "gated_ms": tot / reps,
+                "fallback_frac": nfall / N, "rho_p50": float(np.percentile(rho, 50)),
+                "rho_p99": float(np.percentile(rho, 99)), "rho_max": float(rho.max())})
+    if gmres:
+        f = gaussian_source(v.shape[0], v.ndim, 2.0).reshape(-1)
+        its = {}
+        for tag, bkw in (("gmres_gated", kw), ("gmres_learned", dict(policy=policy, mode="learned")),
+                         ("gmres_fp64", dict(policy=policy, mode="fp64"))):
+            try:
+                ctx.build_stencils(**bkw)
+                ctx.nd_factor()
+                _, res = ctx.gmres(f, max_cycles=25)
+                its[tag] = int(res["iterations"]) if res["converged"] else -int(res["iterations"])
+            except Exception as exc:  # the solve must not hide the timing
+                its[tag] = str(exc)[:80]
+        out.update(its)
     return out
 
 

@@ -82,10 +82,16 @@ typedef struct {
                        /* separator it is b). Rows stay 5^d wide: a t_j = 1 row fills its     */
                        /* inner 3^d columns and holds zeros elsewhere; the CSR export omits   */
                        /* them.                                                                */
+  double learned_gate; /* LEARNED builds only. tau > 0: per-point residual gate. The eigen    */
+                       /* path (a2-a6, FP64) also runs, and every point whose learned alpha   */
+                       /* has rho_j = ||alpha^T G_{s_j}[mu_j, mu_j^c]|| / sigma_min(s_j) > tau */
+                       /* (Sec. 3: sigma_min is the optimum of the sparsification problem)   */
+                       /* gets the eigen path's Q, C, P rows instead (lsp_get_gate_stats).    */
+                       /* 0: no gate (the network's rows as they come).                       */
 } lsp_stencil_opts;
 
 /* Fill *opts with the defaults: t=1, LOCAL policy, FP64, symmetric eigen-solve, no graph,
- * nd_leaf = 0. */
+ * nd_leaf = 0, learned_gate = 0. */
 void lsp_default_opts(lsp_stencil_opts* opts);
 
 /*
@@ -251,6 +257,17 @@ lsp_status lsp_set_mlp(lsp_ctx* ctx, lsp_mlp* m);
  * trained input range falls back to LSP_FP64 (the eigen path).
  */
 lsp_status lsp_get_mode_used(const lsp_ctx* ctx, int* mode);
+/*
+ * Result of the per-point residual gate of the last LEARNED build with learned_gate > 0
+ * (Sec. 3: the residual ||alpha^T G_s[mu, mu^c]|| of a stencil against its optimum, the
+ * smallest singular value). *fallback_points (host) receives how many points took the eigen
+ * path's rows. rho_host (host, N floats, optional) receives each point's ratio
+ * rho_j = sqrt(1 + delta^T (A - lambda_1 I) delta / lambda_1), delta the learned alpha
+ * normalised and sign-matched minus the eigen path's alpha of the point's shift (+inf where
+ * lambda_1 <= 0). The ratio of a fallback point is the learned one that failed the gate.
+ * Synchronises the context's stream. LSP_ERR_STATE if the last build was not gated.
+ */
+lsp_status lsp_get_gate_stats(lsp_ctx* ctx, int64_t* fallback_points, float* rho_host);
 
 /*
  * y = (L + diag(v)) u, like lsp_apply_operator, for callers that cannot allocate device

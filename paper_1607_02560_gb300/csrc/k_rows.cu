@@ -272,6 +272,123 @@ __global__ void __launch_bounds__(kThreads) k_export_t2(const double* __restrict
   }
 }
 
+// ---- the learned-stencil gate (a9) --------------------------------------------------------
+// Class of o_a - o_b for offsets a, b of mu_0^1 (lexicographic, last axis fastest): the sorted
+// |components|, numbered as the stage tables number them (1D: 0 1 2; 2D: 00 01 02 11 12 22;
+// 3D: 000 001 002 011 012 022 111 112 122 222). Compile-time, so that fully unrolled loops
+// index the class values held in registers.
+template <int D>
+__host__ __device__ constexpr int cls1(int a, int b) {
+  if (D == 1) return a - b < 0 ? b - a : a - b;
+  if (D == 2) {
+    const int x0 = a / 3 - b / 3, y0 = a % 3 - b % 3;
+    const int x = x0 < 0 ? -x0 : x0, y = y0 < 0 ? -y0 : y0;
+    const int lo = x < y ? x : y, hi = x < y ? y : x;
+    return lo == 0 ? hi : (lo == 1 ? 2 + hi : 5);
+  }
+  const int p0 = a / 9 - b / 9, q0 = (a / 3) % 3 - (b / 3) % 3, r0 = a % 3 - b % 3;
+  int x = p0 < 0 ? -p0 : p0, y = q0 < 0 ? -q0 : q0, z = r0 < 0 ? -r0 : r0;
+  if (x > y) { const int t = x; x = y; y = t; }
+  if (y > z) { const int t = y; y = z; z = t; }
+  if (x > y) { const int t = x; x = y; y = t; }
+  if (x == 0) return y == 0 ? z : (y == 1 ? 2 + z : 5);
+  if (x == 1) return 6 + (y - 1) + (z - 1);
+  return 9;
+}
+
+// Per point j, with alpha the learned Q row (normalised, sign matched to the eigen path's
+// alpha* of the point's shift s_j) and delta = alpha - alpha*:
+//   ||alpha^T G_s[mu, mu^c]||^2 = alpha^T A alpha = lambda_1 + delta^T (A - lambda_1 I) delta,
+// since A alpha* = lambda_1 alpha* and |alpha| = |alpha*| = 1 (Sec. 3: the optimum of the
+// sparsification problem is the smallest singular value, lambda_1 = sigma_min^2). The ratio
+//   rho_j = ||alpha^T G[mu, mu^c]|| / sigma_min = sqrt(1 + delta^T (A - lambda_1 I) delta / lambda_1)
+// has no cancellation in this form (A - lambda_1 I is positive semidefinite and delta small),
+// so the quadratic form is evaluated in FP32 from the class values of g_s and g_s * g_s
+// (A = A1 - Gm Gm^T, Eq. A). A point with rho_j > tau (or an unusable lambda_1) falls back to
+// the eigen path: its Q, C and P rows are rewritten from alpha*, c* of its shift (a7).
+template <int D, bool LOCAL>
+__global__ void __launch_bounds__(kThreads) k_learned_gate(
+    const double* __restrict__ v, int64_t N, int logn, const int32_t* __restrict__ idx_of,
+    int64_t mlo, int64_t R, const int32_t* __restrict__ shift_m,
+    const int32_t* __restrict__ count, int64_t cap, const double* __restrict__ gvals,
+    const double* __restrict__ alpha, const double* __restrict__ cst,
+    const double* __restrict__ lam, double tau2, double* __restrict__ Q, double* __restrict__ C,
+    double* __restrict__ P, float* __restrict__ rho, int32_t* __restrict__ nfall,
+    int32_t* __restrict__ err) {
+  constexpr int MU = D == 1 ? 3 : (D == 2 ? 9 : 27);
+  constexpr int NC = D == 1 ? 3 : (D == 2 ? 6 : 10);
+  const int64_t mask = ((int64_t)1 << logn) - 1;
+  const int ns = *count;
+  for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * kThreads) {
+    const double x = __ldg(v + j);
+    int idx;
+    if (LOCAL) {
+      const int64_t r = snap_m(x) - mlo;
+      idx = (r >= 0 && r < R) ? __ldg(idx_of + r) : -1;
+      if (idx < 0) {
+        atomicOr(err, 2);
+        idx = 0;
+      }
+    } else {
+      idx = nearest_shift(shift_m, ns, x);
+    }
+    double al[MU], as[MU];
+    double nrm2 = 0.0, dot = 0.0;
+#pragma unroll
+    for (int a = 0; a < MU; ++a) {
+      al[a] = Q[j * MU + a];
+      as[a] = __ldg(alpha + (int64_t)idx * MU + a);
+      nrm2 = fma(al[a], al[a], nrm2);
+      dot = fma(al[a], as[a], dot);
+    }
+    // the residual does not depend on the row's sign: match it to alpha*
+    const double scl = (nrm2 > 0.0 ? 1.0 / sqrt(nrm2) : 0.0) * (dot < 0.0 ? -1.0 : 1.0);
+    float dl[MU];
+    float dd = 0.0f;
+#pragma unroll
+    for (int a = 0; a < MU; ++a) {
+      dl[a] = (float)(fma(al[a], scl, -as[a]));
+      dd = fmaf(dl[a], dl[a], dd);
+    }
+    float g[NC], g2[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      g[c] = (float)__ldg(gvals + (int64_t)(2 * c) * cap + idx);
+      g2[c] = (float)__ldg(gvals + (int64_t)(2 * c + 1) * cap + idx);
+    }
+    float q1 = 0.0f, q2 = 0.0f;  // delta^T A1 delta and |Gm delta|^2
+#pragma unroll
+    for (int b = 0; b < MU; ++b) {
+      float w = 0.0f, u = 0.0f;
+#pragma unroll
+      for (int a = 0; a < MU; ++a) {
+        w = fmaf(g[cls1<D>(a, b)], dl[a], w);
+        u = fmaf(g2[cls1<D>(a, b)], dl[a], u);
+      }
+      q1 = fmaf(dl[b], u, q1);
+      q2 = fmaf(w, w, q2);
+    }
+    const double l1 = __ldg(lam + 2 * (int64_t)idx);
+    const double r2 = 1.0 + ((double)q1 - (double)q2 - l1 * (double)dd) / l1;
+    const bool ok = nrm2 > 0.0 && l1 > 0.0 && r2 <= tau2;  // false for NaN as well
+    rho[j] = (l1 > 0.0 && nrm2 > 0.0 && r2 == r2) ? (float)sqrt(fmax(r2, 1.0)) : INFINITY;
+    if (!ok) {
+      atomicAdd(nfall, 1);
+      const double s = shift_of(__ldg(shift_m + idx));
+#pragma unroll 1
+      for (int a = 0; a < MU; ++a) {
+        const double aa = __ldg(alpha + (int64_t)idx * MU + a);
+        const double cc = __ldg(cst + (int64_t)idx * MU + a);
+        const double vn = __ldg(v + neighbour<D>(j, a, logn, mask));
+        Q[j * MU + a] = aa;
+        C[j * MU + a] = cc;
+        P[j * MU + a] = fma(cc, vn - s, aa);
+      }
+    }
+  }
+}
+
 int log2i(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;
@@ -315,6 +432,32 @@ void dispatch_rows(lsp_ctx* c, int policy, const int32_t* count) {
 cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count) {
   int t = timer_begin(c, "rows");
   dispatch_rows<true, false>(c, policy, count);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_learned_gate(lsp_ctx* c, int policy, const int32_t* count, int64_t cap,
+                                double tau, float* rho, int32_t* nfall) {
+  const int64_t N = c->geo.N;
+  int64_t b = (N + kThreads - 1) / kThreads;
+  if (b > 152 * 16) b = 152 * 16;
+  int t = timer_begin(c, "gate");
+  auto args = [&](auto kern) {
+    kern<<<(int)b, kThreads, 0, c->stream>>>(
+        (const double*)c->v.p, N, log2i(c->geo.n), (const int32_t*)c->idx_of.p, c->mrange.lo,
+        c->mrange.size(), (const int32_t*)c->shift_m.p, count, cap, (const double*)c->gvals.p,
+        (const double*)c->alpha.p, (const double*)c->cst.p, (const double*)c->lam.p, tau * tau,
+        (double*)c->Q.p, (double*)c->C.p, (double*)c->P.p, rho, nfall,
+        (int32_t*)c->counts.p + kErrWord);
+  };
+  const bool local = policy == LSP_SHIFT_LOCAL;
+  if (c->geo.d == 1) {
+    if (local) args(k_learned_gate<1, true>); else args(k_learned_gate<1, false>);
+  } else if (c->geo.d == 2) {
+    if (local) args(k_learned_gate<2, true>); else args(k_learned_gate<2, false>);
+  } else {
+    if (local) args(k_learned_gate<3, true>); else args(k_learned_gate<3, false>);
+  }
   timer_end(c, t);
   return cudaGetLastError();
 }

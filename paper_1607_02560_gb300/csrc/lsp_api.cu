@@ -350,7 +350,8 @@ lsp_status flush_timers(lsp_ctx* c) {
 }
 
 // The launch sequence of steps a2-a7 for the sizes already prepared in the context.
-lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, bool upload) {
+lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, bool upload,
+                       bool rows = true) {
   const int d = c->geo.d;
   int32_t* counts = (int32_t*)c->counts.p;
   // zeroing by kernels: a memset may be queued behind host copies on the copy engines
@@ -411,7 +412,7 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
     else
       CUDA_OK(c, launch_eig_dense3(c, counts + 0, cap_s));
     CUDA_OK(c, launch_rows_t2(c, o.policy, counts + 0, o.nd_leaf));
-  } else {
+  } else if (rows) {
     CUDA_OK(c, launch_rows(c, o.policy, counts + 0));
   }
   return LSP_OK;
@@ -428,6 +429,7 @@ void lsp_default_opts(lsp_stencil_opts* o) {
   o->policy = LSP_SHIFT_LOCAL;
   o->mode = LSP_FP64;
   o->eig_method = LSP_EIG_SYMMETRIC;
+  o->learned_gate = 0.0;
 }
 
 lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
@@ -641,6 +643,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     return fail(c, LSP_ERR_UNSUPPORTED, "learned builds use t = 1 neighbourhoods");
   if (o.mode != LSP_FP64 && o.mode != LSP_MIXED && o.mode != LSP_LEARNED)
     return fail(c, LSP_ERR_ARG, "bad mode %d", o.mode);
+  bool gated = false;
   if (o.mode == LSP_LEARNED) {
     if (!c->mlp) return fail(c, LSP_ERR_STATE, "LEARNED build without a network (lsp_set_mlp)");
     // Gate: the network answers only inside the h^2 v range it was trained on; outside it
@@ -649,7 +652,10 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     if (!mlp_input_range(c->mlp, &lo, &hi)) return fail(c, LSP_ERR_CUDA, "reading the network");
     const double h2 = 1.0 / ((double)c->geo.n * c->geo.n);
     const double margin = 0.02 * ((double)hi - (double)lo);
-    if (c->vmin * h2 >= (double)lo - margin && c->vmax * h2 <= (double)hi + margin) {
+    const bool in_range = c->vmin * h2 >= (double)lo - margin && c->vmax * h2 <= (double)hi + margin;
+    if (in_range && o.learned_gate > 0.0) {
+      gated = true;  // the eigen path runs below without its rows, then the network and the gate
+    } else if (in_range) {
       const int64_t N = c->geo.N;
       const int mu = c->geo.mu;
       if (!ensure(c, c->Q, sizeof(double) * mu * N) || !ensure(c, c->C, sizeof(double) * mu * N) ||
@@ -661,14 +667,16 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
       CUDA_OK(c, launch_learned_rows(c, c->mlp));
       c->built = true;
       c->built_learned = true;
+      c->built_gated = false;
       ++c->build_gen;
       c->mode_used = LSP_LEARNED;
       c->t_built = 1;
       c->leaf_built = 0;
       return LSP_OK;
     }
-    o.mode = LSP_FP64;  // fallback
+    o.mode = LSP_FP64;  // fallback (or the eigen path under the gate)
   }
+  if (!(o.learned_gate >= 0.0)) return fail(c, LSP_ERR_ARG, "learned_gate must be >= 0");
   if (o.policy < 0 || o.policy > 3) return fail(c, LSP_ERR_ARG, "bad policy %d", o.policy);
   if (o.eig_method != LSP_EIG_SYMMETRIC && o.eig_method != LSP_EIG_FULL)
     return fail(c, LSP_ERR_ARG, "bad eig_method %d", o.eig_method);
@@ -809,7 +817,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
                           c->stream != cudaStreamPerThread;
   if (o.use_graph && !c->timing && capturable) {
     std::vector<int64_t> key = {o.policy, o.mode, o.eig_method, o.refine_steps, o.t, o.nd_leaf,
-                                cap_s, c->mrange.lo,
+                                (int64_t)gated, cap_s, c->mrange.lo,
                                 c->mrange.hi, (int64_t)(intptr_t)c->v.p,
                                 (int64_t)(intptr_t)c->Q.p};
     for (int k = 0; k <= d; ++k) key.push_back(c->erange[k].lo);
@@ -820,7 +828,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
       c->graph = nullptr;
       cudaGraph_t g;
       CUDA_OK(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-      st = issue_build(c, o, cap_s, false);
+      st = issue_build(c, o, cap_s, false, !gated);
       cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
       if (st != LSP_OK) return st;
       CUDA_OK(c, ce);
@@ -832,13 +840,23 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     CUDA_OK(c, cudaGraphLaunch(c->graph, c->stream));
     st = LSP_OK;
   } else {
-    st = issue_build(c, o, cap_s, false);
+    st = issue_build(c, o, cap_s, false, !gated);
+  }
+  if (st == LSP_OK && gated) {
+    // the network's rows, then the per-point residual gate against the eigen path's tables
+    if (!ensure(c, c->gate_rho, sizeof(float) * N)) return LSP_ERR_OOM;
+    int32_t* counts = (int32_t*)c->counts.p;
+    CUDA_OK(c, launch_learned_rows(c, c->mlp));
+    CUDA_OK(c, launch_zero(c, counts + kGateWord, sizeof(int32_t)));
+    CUDA_OK(c, launch_learned_gate(c, o.policy, counts + 0, cap_s, o.learned_gate,
+                                   (float*)c->gate_rho.p, counts + kGateWord));
   }
   if (st == LSP_OK) {
     c->built = true;
     ++c->build_gen;
     c->built_learned = false;
-    c->mode_used = o.mode;
+    c->built_gated = gated;
+    c->mode_used = gated ? LSP_LEARNED : o.mode;
     c->t_built = o.t;
     c->leaf_built = o.t == 2 ? o.nd_leaf : 0;
   }
@@ -1052,7 +1070,7 @@ lsp_status lsp_synchronize(lsp_ctx* c) {
   if (!c) return LSP_ERR_ARG;
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   CUDA_OK(c, cudaGetLastError());
-  if (c->built_learned && c->counts.p) {
+  if ((c->built_learned || c->built_gated) && c->counts.p) {
     int32_t e = 0;
     CUDA_OK(c, cudaMemcpy(&e, (int32_t*)c->counts.p + kErrWord, sizeof e, cudaMemcpyDeviceToHost));
     if (e) return fail(c, LSP_ERR_TIMEOUT, "a tensor-core wait gave up (bits %d)", e);
@@ -1065,6 +1083,24 @@ lsp_status lsp_set_mlp(lsp_ctx* c, lsp_mlp* m) {
   if (m && mlp_dim(m) != c->geo.d) return fail(c, LSP_ERR_ARG, "network dimension mismatch");
   if (m) CUDA_OK(c, mlp_sync(m));
   c->mlp = m;
+  return LSP_OK;
+}
+
+lsp_status lsp_get_gate_stats(lsp_ctx* c, int64_t* fallback_points, float* rho_host) {
+  if (!c) return LSP_ERR_ARG;
+  if (!c->built || !c->built_gated)
+    return fail(c, LSP_ERR_STATE, "the last build was not a gated learned build");
+  cudaGetLastError();
+  int32_t head[16];
+  CUDA_OK(c, cudaMemcpyAsync(head, c->counts.p, sizeof(head), cudaMemcpyDeviceToHost, c->stream));
+  if (rho_host)
+    CUDA_OK(c, cudaMemcpyAsync(rho_host, c->gate_rho.p, sizeof(float) * c->geo.N,
+                               cudaMemcpyDeviceToHost, c->stream));
+  CUDA_OK(c, cudaStreamSynchronize(c->stream));
+  if (head[kErrWord] != 0)
+    return fail(c, LSP_ERR_TIMEOUT, "a device wait gave up or a snap disagreed (bits %d)",
+                head[kErrWord]);
+  if (fallback_points) *fallback_points = head[kGateWord];
   return LSP_OK;
 }
 

@@ -31,6 +31,7 @@ constexpr int kMaxSymBlk = 6;
 // counts[] layout: [0] |S|, [1], [2] sizes of the compacted stage domains, [kErrWord] device
 // error bits, [16...] compaction tile scratch.
 constexpr int kErrWord = 15;
+constexpr int kGateWord = 14;  // points the learned-stencil gate sent back to the eigen path
 
 // Symmetry-adapted basis of R^{|mu|} for the hyperoctahedral group acting on mu_0^t:
 // one row of every irreducible representation that occurs. Block b has `dim` basis vectors
@@ -117,6 +118,9 @@ struct lsp_ctx {
 
   // per-shift results (a3-a6); *2: the t = 2 stencils
   lsp::DevBuf gvals, alpha, cst, lam, sflags, alpha2, cst2, lam2, sflags2;
+  // learned-stencil gate: per-point residual ratio of the last gated learned build
+  lsp::DevBuf gate_rho;
+  bool built_gated = false;
 
   // rows (a7) and export
   lsp::DevBuf Q, C, P, sidx, colidx, rowptr, expvals;
@@ -189,6 +193,8 @@ cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int eig_me
                        int refine_steps, bool fp32_gram);
 cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count);
 cudaError_t launch_sidx(lsp_ctx* c, int policy, const int32_t* count);
+cudaError_t launch_learned_gate(lsp_ctx* c, int policy, const int32_t* count, int64_t cap,
+                                double tau, float* rho, int32_t* nfall);
 cudaError_t launch_colidx(lsp_ctx* c);
 cudaError_t launch_apply(lsp_ctx* c, const double* u, double* y);
 void nd_free(NdState* s);

@@ -38,7 +38,8 @@ class StencilOpts(ctypes.Structure):
     _fields_ = [("t", ctypes.c_int), ("policy", ctypes.c_int), ("nshifts", ctypes.c_int),
                 ("shifts", ctypes.POINTER(ctypes.c_double)), ("mode", ctypes.c_int),
                 ("refine_steps", ctypes.c_int), ("eig_method", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("nd_leaf", ctypes.c_int)]
+                ("use_graph", ctypes.c_int), ("nd_leaf", ctypes.c_int),
+                ("learned_gate", ctypes.c_double)]
 
 
 class NdOpts(ctypes.Structure):
@@ -118,6 +119,7 @@ def lib() -> ctypes.CDLL:
         "lsp_mlp_last_error": (ctypes.c_char_p, [vp]),
         "lsp_set_mlp": (ctypes.c_int, [vp, vp]),
         "lsp_get_mode_used": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
+        "lsp_get_gate_stats": (ctypes.c_int, [vp, i64p, vp]),
         "lsp_default_nd_opts": (None, [ctypes.POINTER(NdOpts)]),
         "lsp_nd_factor": (ctypes.c_int, [vp, ctypes.POINTER(NdOpts)]),
         "lsp_nd_get_info": (ctypes.c_int, [vp, ctypes.POINTER(NdInfo)]),
@@ -261,11 +263,14 @@ class Context:
 
     def build_stencils(self, policy="local", nshifts=0, shifts=None, mode="fp64",
                        refine_steps=0, eig_method="symmetric", use_graph=False, t=1,
-                       nd_leaf=0):
+                       nd_leaf=0, learned_gate=0.0):
         """Steps a2-a7 (asynchronous on the context stream). t = 2 builds 5^d-wide rows;
-        nd_leaf > 0 gives each point t_j from a nested dissection with that leaf width."""
+        nd_leaf > 0 gives each point t_j from a nested dissection with that leaf width;
+        learned_gate = tau > 0 checks every learned stencil against its optimum and gives the
+        points above tau the eigen path's rows."""
         o = StencilOpts()
         o.t = t
+        o.learned_gate = float(learned_gate)
         o.nd_leaf = int(nd_leaf)
         o.policy = POLICY[policy] if isinstance(policy, str) else int(policy)
         o.mode = MODE[mode] if isinstance(mode, str) else int(mode)
@@ -406,6 +411,15 @@ class Context:
         m = ctypes.c_int()
         self._check(lib().lsp_get_mode_used(self.h, ctypes.byref(m)), "get_mode_used")
         return {v: k for k, v in MODE.items()}.get(m.value, str(m.value))
+
+    def gate_stats(self, with_rho: bool = True):
+        """(points that fell back to the eigen path, per-point residual ratio or None) of the
+        last gated learned build."""
+        nf = ctypes.c_int64()
+        rho = np.empty(self.N, dtype=np.float32) if with_rho else None
+        self._check(lib().lsp_get_gate_stats(self.h, ctypes.byref(nf), _ptr(rho)),
+                    "get_gate_stats")
+        return int(nf.value), rho
 
     def kernel_timing(self, enable: bool):
         self._check(lib().lsp_kernel_timing(self.h, int(bool(enable))), "kernel_timing")
