@@ -250,6 +250,14 @@ lsp_status lsp_mlp_forward(lsp_mlp* m, const float* X_dev, int64_t batch, float*
 lsp_status lsp_mlp_train_step(lsp_mlp* m, const float* X_dev, const float* T_dev, int64_t batch,
                               float lr, int apply, float* loss_out, float* grads_host);
 const char* lsp_mlp_last_error(const lsp_mlp* m);
+/*
+ * Wall-time limit (ns) of the operand waits inside the network's fused kernel (0: the default,
+ * 1 s). A wait that runs out sets the error word; the kernel then drains its copies and tensor-
+ * core work in flight (those waits keep the 1 s limit), frees its tensor memory and returns, and
+ * lsp_synchronize reports LSP_ERR_TIMEOUT; the context stays usable. The paper has no
+ * counterpart: this exists so that the timeout path can be exercised without a stuck GPU.
+ */
+lsp_status lsp_mlp_set_wait_limit(lsp_mlp* m, uint64_t ns);
 /* Attach a network to a context for LSP_LEARNED builds (NULL detaches). Same d required. */
 lsp_status lsp_set_mlp(lsp_ctx* ctx, lsp_mlp* m);
 /*
@@ -268,6 +276,15 @@ lsp_status lsp_get_mode_used(const lsp_ctx* ctx, int* mode);
  * Synchronises the context's stream. LSP_ERR_STATE if the last build was not gated.
  */
 lsp_status lsp_get_gate_stats(lsp_ctx* ctx, int64_t* fallback_points, float* rho_host);
+
+/*
+ * Allocation-failure injection for tests of the out-of-memory path (the paper has no
+ * counterpart). after >= 0: the library's next `after` device allocations succeed and the one
+ * after them fails as if cudaMalloc had run out of memory, so the call that needed it returns
+ * LSP_ERR_OOM with nothing half-built (the context stays usable once the injection is cleared);
+ * after < 0 clears it. Process-wide; not thread-safe against concurrent library calls.
+ */
+void lsp_inject_alloc_failure(int after);
 
 /*
  * y = (L + diag(v)) u, like lsp_apply_operator, for callers that cannot allocate device

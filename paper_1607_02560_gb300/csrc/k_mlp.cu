@@ -167,6 +167,9 @@ struct FusedParams {
   __nv_bfloat16* Hs[3];
   float* Zs[3];
   int* err;
+  // limit of the pipeline's operand waits (the drain at the end always waits up to 1 s, so
+  // that no copy or MMA is still in flight when the CTA exits)
+  uint64_t wait_ns;
   ChunkPlan plan;
   int64_t bias_off[4], norm_off;
 };
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
   auto wait = [&](uint64_t* bar, uint32_t parity, int bit) {
     if (tc::mbar_test(bar, parity)) return true;  // fast path: already complete
     if (*abort_flag) return false;
-    if (tc::mbar_wait(bar, parity, p.err, bit)) return true;
+    if (tc::mbar_wait(bar, parity, p.err, bit, p.wait_ns)) return true;
     *abort_flag = 1;
     return false;
   };
@@ -916,6 +919,7 @@ struct lsp_mlp {
   cudaStream_t stream = nullptr;
   std::string err;
   lsp::DevBuf params, grads, adam_m, adam_v, tiles, WT[4], W16[4], errflag, loss;
+  uint64_t wait_ns = lsp::tc::kWaitLimitNs;  // operand-wait limit of the fused kernel
   // training workspace
   int64_t cap = 0;
   lsp::DevBuf X16, XT, Xt, Zs[3], Hs[3], HT[3], Y, dY16, dYT, dY32, G, dZ16, dZT, dZ32;
@@ -946,7 +950,7 @@ bool grow(lsp::DevBuf& b, size_t bytes) {
   if (b.p) cudaFree(b.p);
   b.p = nullptr;
   b.bytes = 0;
-  if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+  if (lsp::alloc_should_fail() || cudaMalloc(&b.p, bytes) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
@@ -963,6 +967,7 @@ FusedParams fused_params(lsp_mlp* m) {
   for (int l = 0; l < 4; ++l) p.bias_off[l] = m->L.b[l];
   p.norm_off = m->L.norm;
   p.err = (int*)m->errflag.p;
+  p.wait_ns = m->wait_ns;
   return p;
 }
 
@@ -1285,6 +1290,12 @@ lsp_status lsp_mlp_training_pairs(lsp_ctx* c, lsp_mlp* m, int64_t nsamples, uint
 }
 
 const char* lsp_mlp_last_error(const lsp_mlp* m) { return m ? m->err.c_str() : "null network"; }
+
+lsp_status lsp_mlp_set_wait_limit(lsp_mlp* m, uint64_t ns) {
+  if (!m) return LSP_ERR_ARG;
+  m->wait_ns = ns ? ns : lsp::tc::kWaitLimitNs;
+  return LSP_OK;
+}
 
 }  // extern "C"
 

@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kThreads) k_rows(
         }
       } else
         idx = nearest_shift(shift_m, ns, x);
+      idx = (int)checked(idx, ns, err);
       s_idx[t] = idx;
       s_val[t] = shift_of(__ldg(shift_m + idx));
       if (SIDX) sidx_out[j0 + t] = idx;
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_rows(
         const int idx = s_idx[p];
         const double a = __ldg(alpha + (int64_t)idx * MU + o);
         const double cc = __ldg(cst + (int64_t)idx * MU + o);
-        const double vn = __ldg(v + neighbour<D>(j0 + p, o, logn, mask));
+        const double vn = __ldg(v + checked(neighbour<D>(j0 + p, o, logn, mask), N, err));
         __stcs(Q + obase + e, a);
         __stcs(C + obase + e, cc);
         __stcs(P + obase + e, fma(cc, vn - s_val[p], a));
@@ -212,6 +213,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_t2(
       } else {
         idx = nearest_shift(shift_m, ns, x);
       }
+      idx = (int)checked(idx, ns, err);
       int64_t xc[D];
       coords_of<D>(j, logn, mask, xc);
       s_idx[t] = idx;
@@ -305,7 +307,8 @@ __host__ __device__ constexpr int cls1(int a, int b) {
 // has no cancellation in this form (A - lambda_1 I is positive semidefinite and delta small),
 // so the quadratic form is evaluated in FP32 from the class values of g_s and g_s * g_s
 // (A = A1 - Gm Gm^T, Eq. A). A point with rho_j > tau (or an unusable lambda_1) falls back to
-// the eigen path: its Q, C and P rows are rewritten from alpha*, c* of its shift (a7).
+// the eigen path: its Q, C and P rows are rewritten from alpha*, c* of its shift (a7). A point
+// that passes keeps its learned Q row, and its C and P rows are formed from it in FP64.
 template <int D, bool LOCAL>
 __global__ void __launch_bounds__(kThreads) k_learned_gate(
     const double* __restrict__ v, int64_t N, int logn, const int32_t* __restrict__ idx_of,
@@ -333,6 +336,7 @@ __global__ void __launch_bounds__(kThreads) k_learned_gate(
     } else {
       idx = nearest_shift(shift_m, ns, x);
     }
+    idx = (int)checked(idx, ns, err);
     double al[MU], as[MU];
     double nrm2 = 0.0, dot = 0.0;
 #pragma unroll
@@ -373,7 +377,23 @@ __global__ void __launch_bounds__(kThreads) k_learned_gate(
     const double r2 = 1.0 + ((double)q1 - (double)q2 - l1 * (double)dd) / l1;
     const bool ok = nrm2 > 0.0 && l1 > 0.0 && r2 <= tau2;  // false for NaN as well
     rho[j] = (l1 > 0.0 && nrm2 > 0.0 && r2 == r2) ? (float)sqrt(fmax(r2, 1.0)) : INFINITY;
-    if (!ok) {
+    if (ok) {
+      // the network supplies alpha only: C and P follow from it by the method's formulas,
+      // C[j, mu_j] = Q[j, mu_j] G_s[mu_j, mu_j] and P = Q + C diag(v - s) (Sec. 4.1), in FP64
+      double gd[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) gd[c] = __ldg(gvals + (int64_t)(2 * c) * cap + idx);
+      const double s = shift_of(__ldg(shift_m + idx));
+#pragma unroll
+      for (int b = 0; b < MU; ++b) {
+        double cb = 0.0;
+#pragma unroll
+        for (int a = 0; a < MU; ++a) cb = fma(al[a], gd[cls1<D>(a, b)], cb);
+        const double vn = __ldg(v + neighbour<D>(j, b, logn, mask));
+        C[j * MU + b] = cb;
+        P[j * MU + b] = fma(cb, vn - s, al[b]);
+      }
+    } else {
       atomicAdd(nfall, 1);
       const double s = shift_of(__ldg(shift_m + idx));
 #pragma unroll 1

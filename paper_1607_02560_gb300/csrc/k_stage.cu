@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
                                                     int64_t lo_prev, int64_t stride_prev,
                                                     OUT* __restrict__ Tout, int64_t lo_out,
                                                     int64_t stride_out, int by_index,
-                                                    double scale) {
+                                                    double scale, int32_t* __restrict__ err) {
   using M = StageMap<K, A>;
   extern __shared__ __align__(16) unsigned char xs_raw[];
   R* xs = reinterpret_cast<R*>(xs_raw);  // [A][P]
@@ -203,6 +203,11 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
   for (int64_t idx = (int64_t)blockIdx.x * per_block + sub; idx < cnt;
        idx += (int64_t)gridDim.x * per_block) {
     const int64_t l = list ? (int64_t)__ldg(list + idx) : lo_out + idx;
+    const int64_t pos = by_index ? idx : (l - lo_out);
+    // the previous table is read at l + p^2, p in [0, n/2]; the output at pos
+    if (!checked_range(l - lo_prev, l - lo_prev + (int64_t)(P - 1) * (P - 1), stride_prev, err) ||
+        !checked_range(pos, pos, stride_out, err))
+      continue;
     R acc[M::NCO][2];
 #pragma unroll
     for (int c = 0; c < M::NCO; ++c) acc[c][0] = acc[c][1] = R(0);
@@ -217,7 +222,6 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
           for (int o = 16; o > 0; o >>= 1) acc[c][f] += __shfl_xor_sync(0xffffffffu, acc[c][f], o);
       if (lane != 0) continue;
     }
-    const int64_t pos = by_index ? idx : (l - lo_out);
 #pragma unroll
     for (int c = 0; c < M::NCO; ++c) {
       Tout[(2 * c + 0) * stride_out + pos] = (OUT)((double)acc[c][0] * scale);
@@ -243,7 +247,7 @@ cudaError_t launch_kk(lsp_ctx* c, const int32_t* list, const int32_t* count, int
   if (b > 152 * 16) b = 152 * 16;
   k_stage<K, A, R, OUT, SPLIT><<<(int)b, kThreads, smem, c->stream>>>(
       list, count, P, X, Tprev, lo_prev, stride_prev, Tout, lo_out, stride_out, by_index ? 1 : 0,
-      scale);
+      scale, (int32_t*)c->counts.p + kErrWord);
   return cudaGetLastError();
 }
 

@@ -9,6 +9,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <atomic>
+
 #include "lsp_internal.h"
 
 using namespace lsp;
@@ -286,6 +288,18 @@ bool ensure_tracked(lsp_ctx* c, lsp::DevBuf& b, size_t bytes, int64_t* key) {
 
 namespace lsp {
 
+// Allocation-failure injection (lsp_inject_alloc_failure): allocations left before the one
+// that fails; -1 when off.
+static std::atomic<int> g_alloc_fail_in{-1};
+
+bool alloc_should_fail() {
+  int k = g_alloc_fail_in.load();
+  while (k >= 0) {
+    if (g_alloc_fail_in.compare_exchange_weak(k, k - 1)) return k == 0;
+  }
+  return false;
+}
+
 bool ensure(lsp_ctx* c, DevBuf& b, size_t bytes) {
   if (bytes == 0) bytes = 16;
   if (b.bytes >= bytes) return true;
@@ -294,7 +308,7 @@ bool ensure(lsp_ctx* c, DevBuf& b, size_t bytes) {
   b.p = nullptr;
   b.bytes = 0;
   size_t want = round_up(bytes, 256);
-  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+  if (alloc_should_fail() || cudaMalloc(&b.p, want) != cudaSuccess) {
     cudaGetLastError();
     b.p = nullptr;
     c->err = "device allocation of " + std::to_string(want) + " bytes failed";
@@ -421,6 +435,8 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
 }  // namespace
 
 extern "C" {
+
+void lsp_inject_alloc_failure(int after) { lsp::g_alloc_fail_in.store(after < 0 ? -1 : after); }
 
 void lsp_default_opts(lsp_stencil_opts* o) {
   if (!o) return;
@@ -1070,10 +1086,14 @@ lsp_status lsp_synchronize(lsp_ctx* c) {
   if (!c) return LSP_ERR_ARG;
   CUDA_OK(c, cudaStreamSynchronize(c->stream));
   CUDA_OK(c, cudaGetLastError());
-  if ((c->built_learned || c->built_gated) && c->counts.p) {
+  if (c->built && c->counts.p) {
     int32_t e = 0;
     CUDA_OK(c, cudaMemcpy(&e, (int32_t*)c->counts.p + kErrWord, sizeof e, cudaMemcpyDeviceToHost));
-    if (e) return fail(c, LSP_ERR_TIMEOUT, "a tensor-core wait gave up (bits %d)", e);
+    if (e & kErrBounds)
+      return fail(c, LSP_ERR_STATE, "an index left its array (checked build, bits %d)", e);
+    if (e && (c->built_learned || c->built_gated))
+      return fail(c, LSP_ERR_TIMEOUT, "a tensor-core wait gave up (bits %d)", e);
+    if (e) return fail(c, LSP_ERR_STATE, "device lattice snap disagreed with the host (bits %d)", e);
   }
   return LSP_OK;
 }

@@ -32,6 +32,32 @@ constexpr int kMaxSymBlk = 6;
 // error bits, [16...] compaction tile scratch.
 constexpr int kErrWord = 15;
 constexpr int kGateWord = 14;  // points the learned-stencil gate sent back to the eigen path
+// Bit of the error word set by a checked build (-DLSP_CHECKS) when an index left its array.
+constexpr int kErrBounds = 1 << 10;
+
+#ifdef __CUDACC__
+// Checked builds (-DLSP_CHECKS): an index outside [0, n) is recorded in the error word and
+// replaced by 0, so the access stays inside the array; plain builds compile this away.
+__device__ __forceinline__ int64_t checked(int64_t i, int64_t n, int32_t* err) {
+#ifdef LSP_CHECKS
+  if (i < 0 || i >= n) {
+    atomicOr(err, kErrBounds);
+    return 0;
+  }
+#endif
+  return i;
+}
+// True when [lo, hi] lies inside [0, n) (always true in plain builds); records otherwise.
+__device__ __forceinline__ bool checked_range(int64_t lo, int64_t hi, int64_t n, int32_t* err) {
+#ifdef LSP_CHECKS
+  if (lo < 0 || hi >= n) {
+    atomicOr(err, kErrBounds);
+    return false;
+  }
+#endif
+  return true;
+}
+#endif
 
 // Symmetry-adapted basis of R^{|mu|} for the hyperoctahedral group acting on mu_0^t:
 // one row of every irreducible representation that occurs. Block b has `dim` basis vectors
@@ -162,6 +188,8 @@ namespace lsp {
 
 // ---- host helpers (lsp_api.cu) ----
 bool ensure(lsp_ctx* ctx, DevBuf& b, size_t bytes);
+// True when an injected allocation failure is due (lsp_inject_alloc_failure).
+bool alloc_should_fail();
 int timer_begin(lsp_ctx* ctx, const char* name);
 void timer_end(lsp_ctx* ctx, int slot);
 

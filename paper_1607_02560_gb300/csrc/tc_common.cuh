@@ -71,8 +71,8 @@ __device__ __forceinline__ uint64_t global_ns() {
 // Wait until the phase with the given parity has completed: one non-blocking test, then
 // try_wait with a suspend-time hint (the thread sleeps in hardware until the phase completes or
 // about 2 us pass), so that waiting threads do not flood the shared-memory pipe with polls.
-// After kWaitLimitNs of wall time the wait gives up, records bit `errbit` in *err and returns
-// false.
+// After limit_ns of wall time (default kWaitLimitNs) the wait gives up, records bit `errbit`
+// in *err and returns false.
 __device__ __forceinline__ bool mbar_test(uint64_t* mbar, uint32_t parity) {
   uint32_t done;
   asm volatile(
@@ -83,19 +83,21 @@ __device__ __forceinline__ bool mbar_test(uint64_t* mbar, uint32_t parity) {
       : "memory");
   return done != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int* err, int errbit) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int* err, int errbit,
+                                          uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_test(mbar, parity)) return true;
   const uint64_t t0 = global_ns();
+  const uint32_t hint = limit_ns < 2000u ? (uint32_t)limit_ns : 2000u;  // never past the limit
   for (;;) {
     uint32_t done;
     asm volatile(
         "{\n.reg .pred P1;\nmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2, %3;\n"
         "selp.b32 %0, 1, 0, P1;\n}\n"
         : "=r"(done)
-        : "r"(smem_u32(mbar)), "r"(parity), "r"(2000u)
+        : "r"(smem_u32(mbar)), "r"(parity), "r"(hint)
         : "memory");
     if (done) return true;
-    if (global_ns() - t0 > kWaitLimitNs) break;
+    if (global_ns() - t0 > limit_ns) break;
   }
   atomicOr(err, errbit);
   return false;

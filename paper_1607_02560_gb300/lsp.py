@@ -15,7 +15,8 @@ import re
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "liblsp.so")
+# LSP_LIBRARY selects another build of the library (e.g. the bounds-checked liblsp_checks.so)
+LIB_PATH = os.environ.get("LSP_LIBRARY") or os.path.join(HERE, "liblsp.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "lsp.h")
 
 LSP_OK = 0
@@ -117,6 +118,8 @@ def lib() -> ctypes.CDLL:
         "lsp_mlp_train_step": (ctypes.c_int, [vp, vp, vp, ctypes.c_int64, ctypes.c_float,
                                                ctypes.c_int, ctypes.POINTER(ctypes.c_float), vp]),
         "lsp_mlp_last_error": (ctypes.c_char_p, [vp]),
+        "lsp_mlp_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "lsp_inject_alloc_failure": (None, [ctypes.c_int]),
         "lsp_set_mlp": (ctypes.c_int, [vp, vp]),
         "lsp_get_mode_used": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
         "lsp_get_gate_stats": (ctypes.c_int, [vp, i64p, vp]),
@@ -139,6 +142,12 @@ def lib() -> ctypes.CDLL:
         fn.argtypes = args
     _lib = L
     return L
+
+
+def inject_alloc_failure(after: int) -> None:
+    """The library's next `after` device allocations succeed and the one after them fails
+    (LSP_ERR_OOM); a negative value clears the injection."""
+    lib().lsp_inject_alloc_failure(int(after))
 
 
 def _ptr(a) -> int | None:
@@ -506,6 +515,10 @@ class Mlp:
         self._check(lib().lsp_mlp_train_step(self.h, _ptr(X), _ptr(T), batch, lr, int(apply),
                                              ctypes.byref(loss), _ptr(grads)), "train_step")
         return loss.value
+
+    def set_wait_limit(self, ns: int = 0):
+        """Limit (ns) of the fused kernel's operand waits; 0 restores the default (1 s)."""
+        self._check(lib().lsp_mlp_set_wait_limit(self.h, int(ns)), "set_wait_limit")
 
     def save(self, path: str):
         np.save(path, self.get_params())

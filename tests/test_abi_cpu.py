@@ -5,6 +5,7 @@ CUDA call are exercised.
 """
 
 import ctypes
+import os
 
 import pytest
 
@@ -63,3 +64,20 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".h")):
                 src = open(os.path.join(root, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def test_bounds_checked_kernels_compile():
+    """The -DLSP_CHECKS build (index checks that report through the error word) compiles."""
+    import shutil
+    import subprocess
+    import tempfile
+    from paper_1607_02560_gb300 import build as B
+    if shutil.which("nvcc") is None and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("no nvcc")
+    with tempfile.TemporaryDirectory() as tmp:
+        for name in ("k_rows.cu", "k_stage.cu"):
+            src = os.path.join(B.CSRC, name)
+            cmd = [B.nvcc(), *B.ARCH, *B.FLAGS, "-DLSP_CHECKS", "-c", src, "-o",
+                   os.path.join(tmp, name + ".o")]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            assert r.returncode == 0, r.stderr[-2000:]
