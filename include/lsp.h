@@ -45,7 +45,15 @@ typedef enum {
   LSP_ERR_UNSUPPORTED = 8      /* valid request that this build does not implement           */
 } lsp_status;
 
-typedef enum { LSP_FP64 = 0, LSP_MIXED = 1, LSP_LEARNED = 2 } lsp_mode;
+/*
+ * LSP_FP64: every step in FP64. LSP_MIXED: the a3 contractions and the Gram blocks in FP32,
+ * the near-null solve in FP64. LSP_LEARNED: a trained network gives alpha and c (see lsp_mlp).
+ * LSP_DWORD: the a3 contractions in double words (pairs of FP32 values, about 48 significant
+ * bits, formed with exact two-sum and fused-multiply-add product errors on the FP32 pipe), the
+ * rest in FP64; the stencils meet the FP64 path's tolerance. Double words serve t = 1 builds
+ * in 1D and 2D; elsewhere a LSP_DWORD build runs the FP64 stages (lsp_get_mode_used says so).
+ */
+typedef enum { LSP_FP64 = 0, LSP_MIXED = 1, LSP_LEARNED = 2, LSP_DWORD = 3 } lsp_mode;
 
 typedef enum {
   LSP_SHIFT_PAPER = 0,  /* |S| shifts spread evenly over [v_min, v_max], snapped (Sec. 4.1)   */
@@ -258,6 +266,13 @@ const char* lsp_mlp_last_error(const lsp_mlp* m);
  * counterpart: this exists so that the timeout path can be exercised without a stuck GPU.
  */
 lsp_status lsp_mlp_set_wait_limit(lsp_mlp* m, uint64_t ns);
+/*
+ * Schedule of the 2D network's fused inference kernel: 1 (the default) keeps two 128-row tiles
+ * in flight per SM, so that one tile's tensor-core products overlap the other's epilogue;
+ * 0 runs one tile at a time. Both compute the same rows bit for bit. 3D networks always run
+ * one tile at a time (two tiles' buffers do not fit in shared memory). LSP_ERR_ARG otherwise.
+ */
+lsp_status lsp_mlp_set_schedule(lsp_mlp* m, int schedule);
 /* Attach a network to a context for LSP_LEARNED builds (NULL detaches). Same d required. */
 lsp_status lsp_set_mlp(lsp_ctx* ctx, lsp_mlp* m);
 /*

@@ -566,6 +566,316 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
   if (warp == 0) tc::tmem_dealloc(tmem, 2 * kH);
 }
 
+// ---- two tiles in flight (2D) -----------------------------------------------------------
+// The fused kernel above runs one tile's layers back to back, so the tensor cores wait while
+// the epilogue converts a layer and the epilogue waits while the next layer multiplies. Here a
+// CTA takes its tiles in pairs (A, B), each with its own accumulator (tensor-memory columns
+// 256 t ..) and its own activation buffer H_t, and interleaves them: the MMAs of B's layer l run
+// while the epilogue converts A's layer l, and the MMAs of A's layer l + 1 run while it converts
+// B's, so that the epilogue warps always have a layer to convert.
+//
+// Order of work, per pair: for l = 0..3, for t = A, B: MMAs (t, l), then epilogue (t, l).
+// MMA (t, l) waits for epilogue (t, l - 1) (its accumulator read out, H_t written; for l = 0
+// the output layer of the previous pair's tile t) and, for l = 0, for the input tile X_t.
+// Epilogue (t, l) waits for the MMAs (t, l) (bar_acc[t]). The loader streams the weight chunks
+// in the MMA warp's order (every tile reads all of them; two 32 KiB buffers), and the next
+// pair's input tile t once the layer-0 MMAs of tile t have completed. Every wait is bounded as
+// in the fused kernel; a wait that gives up stops the CTA after its copies and MMAs drain.
+constexpr int kPPThreads = 320;  // 8 epilogue warps, the MMA warp, the loader warp
+
+struct PPCfg {
+  static constexpr int MU = 9, K0 = 32, OUTP = 32, NBUF = 2;
+  static constexpr int XBYTES = kTile * K0 * 2;  // 8 KiB per input tile
+  static constexpr int HBYTES = kTile * kH * 2;  // 64 KiB per activation buffer
+  static constexpr int NRM = (2 + 2 * OUTP + 3) & ~3;
+  static constexpr size_t smem = 2 * (size_t)XBYTES + 2 * (size_t)HBYTES +
+                                 (size_t)NBUF * kChunkBytes +
+                                 sizeof(float) * (6 * kH + OUTP + NRM) + 64;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kPPThreads, 1) k_mlp_pp(FusedParams p) {
+  using Cfg = FusedCfg<2>;  // the chunk plan of the 2D network
+  constexpr int MU = PPCfg::MU, OUTP = PPCfg::OUTP, NBUF = PPCfg::NBUF;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* Xs = smem;                                   // 2 x (128 x 32) bf16
+  uint8_t* Hs = Xs + 2 * PPCfg::XBYTES;                 // 2 x (128 x 256) bf16
+  uint8_t* Wb = Hs + 2 * PPCfg::HBYTES;                 // NBUF x 32 KiB
+  float* bs = reinterpret_cast<float*>(Wb + NBUF * kChunkBytes);
+  float* nrm = bs + 3 * kH + OUTP;
+  float* bq = nrm + PPCfg::NRM;
+  __shared__ __align__(8) uint64_t bar_w[NBUF], bar_f[NBUF], bar_x[2], bar_xf[2], bar_acc[2],
+      bar_e[2], bar_done;
+  __shared__ uint32_t tslot;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool mma_warp = warp == kEpiWarps;
+  const bool loader = warp == kEpiWarps + 1;
+
+  for (int i = tid; i < kH; i += kPPThreads) {
+    bs[i] = p.params[p.bias_off[0] + i];
+    bs[kH + i] = p.params[p.bias_off[1] + i];
+    bs[2 * kH + i] = p.params[p.bias_off[2] + i];
+    for (int l = 0; l < 3; ++l) bq[l * kH + i] = fmaf(bs[l * kH + i], 1.0f / 6.0f, 0.5f);
+  }
+  for (int i = tid; i < OUTP; i += kPPThreads) bs[3 * kH + i] = p.params[p.bias_off[3] + i];
+  for (int i = tid; i < 2 + 2 * OUTP; i += kPPThreads) nrm[i] = p.params[p.norm_off + i];
+  if (mma_warp && lane == 0) {
+    for (int b = 0; b < NBUF; ++b) {
+      tc::mbar_init(&bar_w[b], 1);
+      tc::mbar_init(&bar_f[b], 1);
+    }
+    for (int t = 0; t < 2; ++t) {
+      tc::mbar_init(&bar_x[t], 1);
+      tc::mbar_init(&bar_xf[t], 1);
+      tc::mbar_init(&bar_acc[t], 1);
+      tc::mbar_init(&bar_e[t], kEpiWarps);
+    }
+    tc::mbar_init(&bar_done, 1);
+    s_abort = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(&tslot, 2 * kH);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tslot;
+  volatile int* abort_flag = &s_abort;
+  auto wait = [&](uint64_t* bar, uint32_t parity, int bit) {
+    if (tc::mbar_test(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (tc::mbar_wait(bar, parity, p.err, bit, p.wait_ns)) return true;
+    *abort_flag = 1;
+    return false;
+  };
+  auto wait_warp = [&](uint64_t* bar, uint32_t parity, int bit) {
+    if (lane == 0) wait(bar, parity, bit);
+    __syncwarp();
+  };
+  // this CTA's tiles: blockIdx.x + i * gridDim.x, i < my_tiles; pairs (2k, 2k + 1)
+  const int64_t ntiles = (p.M + kTile - 1) / kTile;
+  const int64_t my_tiles =
+      blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int64_t my_pairs = (my_tiles + 1) / 2;
+  auto tile_of = [&](int64_t pair, int t) { return (int64_t)blockIdx.x + (2 * pair + t) * gridDim.x; };
+  auto has = [&](int64_t pair, int t) { return 2 * pair + t < my_tiles; };
+
+  if (loader) {
+    if (lane == 0) {
+      uint32_t slot = 0, ph_f = 0, ph_xf = 0, issued = 0, cnt_x[2] = {0, 0};
+      auto load_x = [&](int64_t pair, int t) {
+        tc::mbar_expect_tx(&bar_x[t], PPCfg::XBYTES);
+        tc::bulk_g2s(Xs + t * PPCfg::XBYTES, p.Xt + tile_of(pair, t) * PPCfg::XBYTES,
+                     PPCfg::XBYTES, &bar_x[t]);
+        ++cnt_x[t];
+      };
+      if (my_pairs > 0) {
+        load_x(0, 0);
+        if (has(0, 1)) load_x(0, 1);
+      }
+      for (int64_t pr = 0; pr < my_pairs && !*abort_flag; ++pr) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          for (int t = 0; t < 2; ++t) {
+            if (!has(pr, t) || *abort_flag) continue;
+#pragma unroll
+            for (int c = 0; c < Cfg::NCH(l); ++c) {
+              if (issued >= (uint32_t)NBUF) {
+                wait(&bar_f[slot], ph_f >> slot & 1, 2);  // the MMAs that read this buffer
+                ph_f ^= 1u << slot;
+              }
+              if (*abort_flag) break;
+              tc::mbar_expect_tx(&bar_w[slot], Cfg::CHUNK_BYTES(l));
+              tc::bulk_g2s(Wb + slot * kChunkBytes,
+                           p.tiles + Cfg::OFF(l) + (int64_t)c * Cfg::CHUNK_BYTES(l),
+                           Cfg::CHUNK_BYTES(l), &bar_w[slot]);
+              ++issued;
+              slot = slot + 1 == (uint32_t)NBUF ? 0 : slot + 1;
+            }
+            // after tile t's layer-1 chunks: its input buffer is free once its layer-0 MMAs
+            // completed; bring in the next pair's tile t
+            if (l == 1 && has(pr + 1, t) && !*abort_flag) {
+              wait(&bar_xf[t], ph_xf >> t & 1, 1);
+              ph_xf ^= 1u << t;
+              if (!*abort_flag) load_x(pr + 1, t);
+            }
+          }
+        }
+      }
+      // drain: every copy issued has landed (1 s limit; complete unless aborted)
+      for (int b = 0; b < NBUF; ++b) {
+        const uint32_t uses = issued / NBUF + ((uint32_t)b < issued % NBUF ? 1u : 0u);
+        if (uses) tc::mbar_wait(&bar_w[b], (uses - 1) & 1, p.err, 0);
+      }
+      for (int t = 0; t < 2; ++t)
+        if (cnt_x[t]) tc::mbar_wait(&bar_x[t], (cnt_x[t] - 1) & 1, p.err, 0);
+    }
+    __syncwarp();
+  } else if (mma_warp) {
+    if (lane == 0) {
+      uint32_t slot = 0, ph_w = 0, ph_x = 0, ph_e = 0;
+      uint32_t e_done[2] = {0, 0};  // epilogues of tile slot t completed so far (expected)
+      for (int64_t pr = 0; pr < my_pairs && !*abort_flag; ++pr) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          for (int t = 0; t < 2; ++t) {
+            if (!has(pr, t) || *abort_flag) continue;
+            if (l == 0) {
+              wait(&bar_x[t], ph_x >> t & 1, 1);
+              ph_x ^= 1u << t;
+            }
+            if (e_done[t] > 0) {  // the previous epilogue of this slot: H_t written, acc read
+              wait(&bar_e[t], ph_e >> t & 1, 32);
+              ph_e ^= 1u << t;
+            }
+            const uint32_t acc = tmem + (uint32_t)(t * kH);
+#pragma unroll
+            for (int c = 0; c < Cfg::NCH(l); ++c) {
+              wait(&bar_w[slot], ph_w >> slot & 1, 4);
+              ph_w ^= 1u << slot;
+              if (*abort_flag) break;
+              tc::fence_after();
+              const int k0 = c * Cfg::KW(l);
+              const uint32_t aBase = l == 0 ? tc::smem_u32(Xs + t * PPCfg::XBYTES) + (k0 / 8) * 128
+                                            : tc::smem_u32(Hs + t * PPCfg::HBYTES) + (k0 / 8) * 128;
+              const uint32_t sboA = (uint32_t)((l == 0 ? Cfg::K0 : kH) / 8) * 128;
+              const uint32_t sboB = (uint32_t)(Cfg::KW(l) / 8) * 128;
+              const uint32_t bBase = tc::smem_u32(Wb + slot * kChunkBytes);
+              constexpr uint32_t idesc_h = tc::idesc_bf16(kTile, kH);
+              const uint32_t idesc = l < 3 ? idesc_h : tc::idesc_bf16(kTile, OUTP);
+              const uint64_t ad0 = tc::desc_kmajor(aBase, 128, sboA);
+              const uint64_t bd0 = tc::desc_kmajor(bBase, 128, sboB);
+#pragma unroll
+              for (int s = 0; s < Cfg::KW(l) / 16; ++s)
+                tc::mma_bf16(acc, ad0 + (uint64_t)(16 * s), bd0 + (uint64_t)(16 * s), idesc,
+                             (c == 0 && s == 0) ? 0u : 1u);
+              tc::commit(&bar_f[slot]);
+              slot = slot + 1 == (uint32_t)NBUF ? 0 : slot + 1;
+            }
+            if (*abort_flag) break;
+            tc::commit(&bar_acc[t]);
+            if (l == 0) tc::commit(&bar_xf[t]);
+            ++e_done[t];
+          }
+        }
+      }
+      // every MMA of this thread has completed before the tensor memory is released
+      tc::commit(&bar_done);
+      tc::mbar_wait(&bar_done, 0, p.err, 0);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue warps: (A, l), (B, l), (A, l + 1), ... ----
+    const int quarter = warp & 3, grp = warp >> 2;
+    const int trow = quarter * 32 + lane;  // tensor-memory lane = tile row
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    uint32_t ph_acc = 0;
+    const int64_t mask = ((int64_t)1 << p.logn) - 1;
+    for (int64_t pr = 0; pr < my_pairs; ++pr) {
+      if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;
+      for (int l = 0; l < 4; ++l) {
+        for (int t = 0; t < 2; ++t) {
+          if (!has(pr, t)) continue;
+          wait_warp(&bar_acc[t], ph_acc >> t & 1, 8);
+          ph_acc ^= 1u << t;
+          tc::fence_after();
+          const bool stop = __shfl_sync(0xffffffffu, *abort_flag, 0);
+          const uint32_t taddr = tmem + lane_off + (uint32_t)(t * kH);
+          const int64_t myrow = tile_of(pr, t) * kTile + trow;
+          uint8_t* Ht = Hs + t * PPCfg::HBYTES;
+          if (l < 3 && !stop) {
+            const float* bl = bs + l * kH;
+            const float* ql = bq + l * kH;
+            uint32_t r[2][32];
+            tc::tmem_ld32_nowait(taddr + grp * 32, r[0]);
+#pragma unroll
+            for (int pass = 0; pass < kNPass; ++pass) {
+              const int cb = pass * kPassCols + grp * 32;
+              tc::ld_wait(r[pass & 1]);
+              if (pass + 1 < kNPass)
+                tc::tmem_ld32_nowait(taddr + cb + kPassCols, r[(pass + 1) & 1]);
+              const uint32_t* rr = r[pass & 1];
+              float h[32];
+#pragma unroll
+              for (int i = 0; i < 32; i += 4) {
+                const float4 b4 = *reinterpret_cast<const float4*>(bl + cb + i);
+                const float4 q4 = *reinterpret_cast<const float4*>(ql + cb + i);
+                float z[4];
+                hswish_x2(rr[i], rr[i + 1], b4.x, b4.y, q4.x, q4.y, h[i], h[i + 1], z[0], z[1]);
+                hswish_x2(rr[i + 2], rr[i + 3], b4.z, b4.w, q4.z, q4.w, h[i + 2], h[i + 3], z[2],
+                          z[3]);
+                if (MODE == kModeBatch && myrow < p.M)
+#pragma unroll
+                  for (int u = 0; u < 4; ++u) p.Zs[l][myrow * kH + cb + i + u] = z[u];
+              }
+#pragma unroll
+              for (int q8 = 0; q8 < 4; ++q8) {
+                uint4 q;
+                q.x = tc::pack_bf16(h[8 * q8 + 0], h[8 * q8 + 1]);
+                q.y = tc::pack_bf16(h[8 * q8 + 2], h[8 * q8 + 3]);
+                q.z = tc::pack_bf16(h[8 * q8 + 4], h[8 * q8 + 5]);
+                q.w = tc::pack_bf16(h[8 * q8 + 6], h[8 * q8 + 7]);
+                *reinterpret_cast<uint4*>(Ht + tc::kmajor_off(trow, cb + 8 * q8, kH)) = q;
+                if (MODE == kModeBatch && myrow < p.M)
+                  *reinterpret_cast<uint4*>(p.Hs[l] + myrow * kH + cb + 8 * q8) = q;
+              }
+            }
+            // H_t is written and the accumulator read: the MMAs of (t, l + 1) may go
+            tc::fence_async_smem();
+          } else if (!stop) {
+            // output layer: (alpha, c) and the rows, or the normalised outputs Y
+            float y[OUTP];
+            {
+              uint32_t r[32];
+              tc::tmem_ld32_nowait(taddr, r);
+              tc::ld_wait(r);
+#pragma unroll
+              for (int i = 0; i < 32; ++i) y[i] = __uint_as_float(r[i]) + bs[3 * kH + i];
+            }
+            if (myrow < p.M) {
+              if (MODE == kModeBatch) {
+                if (grp == 0) {
+#pragma unroll
+                  for (int o = 0; o < OUTP; ++o) p.Y[myrow * OUTP + o] = y[o];
+                }
+              } else {
+                float al[MU], cc[MU], nrm2 = 0.0f;
+#pragma unroll
+                for (int i = 0; i < MU; ++i) {
+                  al[i] = y[i] * nrm[2 + OUTP + i] + nrm[2 + i];
+                  cc[i] = y[MU + i] * nrm[2 + OUTP + MU + i] + nrm[2 + MU + i];
+                  nrm2 = fmaf(al[i], al[i], nrm2);
+                }
+                const float sc = nrm2 > 0.0f ? rsqrtf(nrm2) : 1.0f;
+                if (grp == 0) {
+#pragma unroll
+                  for (int i = 0; i < MU; ++i) {
+                    __stcs(p.Q + myrow * MU + i, (double)(al[i] * sc));
+                    __stcs(p.C + myrow * MU + i, (double)(cc[i] * sc));
+                  }
+                } else {
+                  const float sh = __ldg(p.sh + myrow), sl = __ldg(p.sl + myrow);
+#pragma unroll
+                  for (int i = 0; i < MU; ++i) {
+                    const int64_t nb = nb_index<2, 1>(myrow, i, p.logn, mask);
+                    const float dv = (__ldg(p.vh + nb) - sh) + (__ldg(p.vl + nb) - sl);
+                    __stcs(p.P + myrow * MU + i, (double)fmaf(cc[i] * sc, dv, al[i] * sc));
+                  }
+                }
+              }
+            }
+          }
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&bar_e[t]);
+        }
+      }
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 2 * kH);
+}
+
 // Per point j of a learned build: the normalised features of h^2 v_j and of h^2 s_j (bf16,
 // s_j = snap(v_j)), and fp32 pairs v_j = vh + vl, s_j = sh + sl for the P epilogue. Since
 // h^2 = 1/n^2 is a power of two, (float)(v h^2) = (float)v * h^2 exactly.
@@ -920,6 +1230,7 @@ struct lsp_mlp {
   std::string err;
   lsp::DevBuf params, grads, adam_m, adam_v, tiles, WT[4], W16[4], errflag, loss;
   uint64_t wait_ns = lsp::tc::kWaitLimitNs;  // operand-wait limit of the fused kernel
+  int schedule = 1;  // 2D: 1 = two tiles in flight (k_mlp_pp), 0 = one tile at a time
   // training workspace
   int64_t cap = 0;
   lsp::DevBuf X16, XT, Xt, Zs[3], Hs[3], HT[3], Y, dY16, dYT, dY32, G, dZ16, dZT, dZ32;
@@ -978,6 +1289,17 @@ size_t input_tile_bytes(int d, int64_t rows) {
 
 template <int D, int MODE>
 cudaError_t launch_fused(lsp_mlp* m, const FusedParams& p, int64_t rows) {
+  if (D == 2 && m->schedule == 1) {
+    const size_t smem = PPCfg::smem;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_pp<MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = (rows + kTile - 1) / kTile;
+    int grid = (int)(tiles < 152 ? tiles : 152);
+    if (grid < 1) grid = 1;
+    k_mlp_pp<MODE><<<grid, kPPThreads, smem, m->stream>>>(p);
+    return cudaGetLastError();
+  }
   const size_t smem = FusedCfg<D>::smem;
   cudaError_t e = cudaFuncSetAttribute(k_mlp_fused<D, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1290,6 +1612,12 @@ lsp_status lsp_mlp_training_pairs(lsp_ctx* c, lsp_mlp* m, int64_t nsamples, uint
 }
 
 const char* lsp_mlp_last_error(const lsp_mlp* m) { return m ? m->err.c_str() : "null network"; }
+
+lsp_status lsp_mlp_set_schedule(lsp_mlp* m, int schedule) {
+  if (!m || (schedule != 0 && schedule != 1)) return LSP_ERR_ARG;
+  m->schedule = schedule;
+  return LSP_OK;
+}
 
 lsp_status lsp_mlp_set_wait_limit(lsp_mlp* m, uint64_t ns) {
   if (!m) return LSP_ERR_ARG;

@@ -278,6 +278,18 @@ __global__ void __launch_bounds__(kThreads) k_wtable32(int64_t lo, int64_t range
   }
 }
 
+// Double words (hi, lo floats) of w and w^2 from their FP64 values, interleaved per l.
+__global__ void __launch_bounds__(kThreads) k_wtable_dw(int64_t lo, int64_t range,
+                                                        float4* __restrict__ w) {
+  for (int64_t r = (int64_t)blockIdx.x * kThreads + threadIdx.x; r < range;
+       r += (int64_t)gridDim.x * kThreads) {
+    const double l4 = (double)(4 * (lo + r) + 2);
+    const double x = 1.0 / __dmul_rn(kPi2, l4), x2 = x * x;
+    const float xh = (float)x, x2h = (float)x2;
+    w[r] = make_float4(xh, (float)(x - (double)xh), x2h, (float)(x2 - (double)x2h));
+  }
+}
+
 int grid_for(int64_t work, int per_block = kThreads) {
   int64_t b = (work + per_block - 1) / per_block;
   const int64_t cap = 152 * 32;
@@ -376,10 +388,12 @@ cudaError_t launch_mark_stage(lsp_ctx* c, const int32_t* list, const int32_t* co
   return cudaGetLastError();
 }
 
-cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, void* w, bool fp32) {
+cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, void* w, int prec) {
   int t = timer_begin(c, "wtable");
-  if (fp32)
+  if (prec == kPrecFP32)
     k_wtable32<<<grid_for(range), kThreads, 0, c->stream>>>(lo, range, (float*)w);
+  else if (prec == kPrecDword)
+    k_wtable_dw<<<grid_for(range), kThreads, 0, c->stream>>>(lo, range, (float4*)w);
   else
     k_wtable64<<<grid_for(range), kThreads, 0, c->stream>>>(lo, range, (double2*)w);
   timer_end(c, t);

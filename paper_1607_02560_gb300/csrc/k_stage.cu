@@ -15,6 +15,8 @@
 //   g_f[a_1..a_d](m) = N^-1 T_d,f[a_1..a_d](m)          (E_d = the shift list).
 // T_k is symmetric in its class tuple, so only sorted tuples (a <= rest) are formed. This is
 // the exact sum of the definition with the terms grouped by axis; no approximation is made.
+#include <type_traits>
+
 #include "lsp_internal.h"
 
 namespace lsp {
@@ -95,6 +97,154 @@ struct Vec2<double> { using type = double2; };
 template <>
 struct Vec2<float> { using type = float2; };
 
+// ---- double-word arithmetic on the FP32 pipe ----------------------------------------------
+// A double word is an unevaluated sum h + l of two floats with |l| <= ulp(h) / 2, which carries
+// about 48 significant bits. GB300 issues FP32 at 64 times its FP64 rate, so a stage evaluated
+// in double words (about ten FP32 operations per multiply-add) costs a fraction of the FP64
+// form. The building blocks are the classical error-free transformations: the exact sum of two
+// floats with its rounding error (Knuth's two-sum, six operations) and the exact product with
+// its error from one fused multiply-add. Explicit _rn intrinsics keep the compiler from
+// contracting or reassociating them.
+struct dword {
+  float h, l;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+// s + e with |e| well below ulp(s) after the exact sum of a and b (|a| >= |b| or a = 0).
+__device__ __forceinline__ dword fast_renorm(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// a + b and a - b of double words: the highs summed exactly, the lows and the error added.
+__device__ __forceinline__ dword dw_add(dword a, dword b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  return fast_renorm(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dword dw_sub(dword a, dword b) {
+  float s, e;
+  two_sum(a.h, -b.h, s, e);
+  return fast_renorm(s, __fadd_rn(e, __fsub_rn(a.l, b.l)));
+}
+// acc += x * y. The product of the highs is exact with its error term; the cross terms of
+// the lows enter that error term; the high of the sum is formed exactly and its error, with
+// the product's, goes into the low word. The low word is folded back by dw_norm every few
+// steps, so that its own rounding stays at the level of the double-word precision.
+__device__ __forceinline__ void dw_mac(dword& acc, dword x, dword y) {
+  const float p = __fmul_rn(x.h, y.h);
+  float pe = __fmaf_rn(x.h, y.h, -p);
+  pe = __fmaf_rn(x.h, y.l, pe);
+  pe = __fmaf_rn(x.l, y.h, pe);
+  float s, e;
+  two_sum(acc.h, p, s, e);
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ void dw_norm(dword& a) { a = fast_renorm(a.h, a.l); }
+__device__ __forceinline__ dword dw_shfl_xor(dword a, int o) {
+  return {__shfl_xor_sync(0xffffffffu, a.h, o), __shfl_xor_sync(0xffffffffu, a.l, o)};
+}
+
+template <typename R>
+__device__ __forceinline__ R zero_of() { return R(0); }
+template <>
+__device__ __forceinline__ dword zero_of<dword>() { return {0.0f, 0.0f}; }
+
+// Output conversion: intermediate stages keep their type; the last stage writes FP64 g values
+// (the final 1/N scale is a power of two, exact in every type).
+__device__ __forceinline__ void store_out(double* p, double v, double scale) { *p = v * scale; }
+__device__ __forceinline__ void store_out(float* p, float v, double scale) { *p = (float)((double)v * scale); }
+__device__ __forceinline__ void store_out(double* p, float v, double scale) { *p = (double)v * scale; }
+__device__ __forceinline__ void store_out(double* p, dword v, double scale) {
+  *p = ((double)v.h + (double)v.l) * scale;
+}
+__device__ __forceinline__ void store_out(dword* p, dword v, double) {
+  dw_norm(v);
+  *p = v;
+}
+
+// Double-word form of stage_accumulate (below): the same sums in the same order, with the
+// w table holding (w, w^2) as two double words per l (16 bytes, one load) and the stage tables
+// holding double words. The accumulators are renormalised every four frequencies.
+template <int K, int A>
+__device__ __forceinline__ void stage_accumulate_dw(const dword* __restrict__ xs, int P,
+                                                    int64_t l, const dword* __restrict__ Tprev,
+                                                    int64_t lo_prev, int64_t stride_prev,
+                                                    int first, int step,
+                                                    dword (&acc)[StageMap<K, A>::NCO][2]) {
+  using M = StageMap<K, A>;
+  const int half = P - 1;  // n/2
+  if (K == 1) {
+    const float4* tab = reinterpret_cast<const float4*>(Tprev) + (l - lo_prev);
+    const int quarter = half / 2;  // n/4
+    int cnt = 0;
+#pragma unroll 4
+    for (int p = first; p < quarter; p += step) {
+      const int q = half - p;
+      const float4 wa = __ldg(tab + (int64_t)p * p);
+      const float4 wb = __ldg(tab + (int64_t)q * q);
+      const dword a1 = {wa.x, wa.y}, b1 = {wb.x, wb.y}, a2 = {wa.z, wa.w}, b2 = {wb.z, wb.w};
+      const dword s1 = dw_add(a1, b1), d1 = dw_sub(a1, b1);
+      const dword s2 = dw_add(a2, b2), d2 = dw_sub(a2, b2);
+#pragma unroll
+      for (int a = 0; a < A; ++a) {  // even a: X_a(q) = X_a(p); odd a: X_a(q) = -X_a(p)
+        const dword xa = xs[a * P + p];
+        dw_mac(acc[a][0], xa, (a & 1) ? d1 : s1);
+        dw_mac(acc[a][1], xa, (a & 1) ? d2 : s2);
+      }
+      if ((++cnt & 3) == 0) {
+#pragma unroll
+        for (int a = 0; a < A; ++a) {
+          dw_norm(acc[a][0]);
+          dw_norm(acc[a][1]);
+        }
+      }
+    }
+    if (first == 0) {
+      const float4 wm = __ldg(tab + (int64_t)quarter * quarter);
+#pragma unroll
+      for (int c = 0; c < A; ++c) {
+        dw_mac(acc[c][0], xs[c * P + quarter], dword{wm.x, wm.y});
+        dw_mac(acc[c][1], xs[c * P + quarter], dword{wm.z, wm.w});
+      }
+    }
+  } else {
+    const dword* base = Tprev + (l - lo_prev);
+    int cnt = 0;
+#pragma unroll 4
+    for (int p = first; p < P; p += step) {
+      const int64_t off = (int64_t)p * p;
+      dword in[M::NCP][2];
+#pragma unroll
+      for (int c = 0; c < M::NCP; ++c) {
+        const float2 v0 = __ldg(reinterpret_cast<const float2*>(base + (2 * c + 0) * stride_prev + off));
+        const float2 v1 = __ldg(reinterpret_cast<const float2*>(base + (2 * c + 1) * stride_prev + off));
+        in[c][0] = {v0.x, v0.y};
+        in[c][1] = {v1.x, v1.y};
+      }
+      dword x[A];
+#pragma unroll
+      for (int a = 0; a < A; ++a) x[a] = xs[a * P + p];
+#pragma unroll
+      for (int c = 0; c < M::NCO; ++c) {
+        dw_mac(acc[c][0], x[M::a(c)], in[M::r(c)][0]);
+        dw_mac(acc[c][1], x[M::a(c)], in[M::r(c)][1]);
+      }
+      if ((++cnt & 3) == 0) {
+#pragma unroll
+        for (int c = 0; c < M::NCO; ++c) {
+          dw_norm(acc[c][0]);
+          dw_norm(acc[c][1]);
+        }
+      }
+    }
+  }
+}
+
 // Accumulate the stage-K sums of one domain point l over the frequencies p = first, first +
 // step, ... (all of them for step = 1). Structure-of-arrays tables: Tprev[(c * 2 + f) *
 // stride_prev + (l + p^2 - lo_prev)].
@@ -157,6 +307,7 @@ __device__ __forceinline__ void stage_accumulate(const R* __restrict__ xs, int P
     }
   } else {
     const R* base = Tprev + (l - lo_prev);
+#pragma unroll 4
     for (int p = first; p < P; p += step) {
       const int64_t off = (int64_t)p * p;
       R in[M::NCP][2];
@@ -210,22 +361,33 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
       continue;
     R acc[M::NCO][2];
 #pragma unroll
-    for (int c = 0; c < M::NCO; ++c) acc[c][0] = acc[c][1] = R(0);
-    stage_accumulate<K, A, R>(xs, P, l, Tprev, lo_prev, stride_prev, SPLIT ? lane : 0,
-                           SPLIT ? 32 : 1, acc);
+    for (int c = 0; c < M::NCO; ++c) acc[c][0] = acc[c][1] = zero_of<R>();
+    if constexpr (std::is_same<R, dword>::value)
+      stage_accumulate_dw<K, A>(xs, P, l, Tprev, lo_prev, stride_prev, SPLIT ? lane : 0,
+                                SPLIT ? 32 : 1, acc);
+    else
+      stage_accumulate<K, A, R>(xs, P, l, Tprev, lo_prev, stride_prev, SPLIT ? lane : 0,
+                                SPLIT ? 32 : 1, acc);
     if (SPLIT) {
 #pragma unroll
       for (int c = 0; c < M::NCO; ++c)
 #pragma unroll
         for (int f = 0; f < 2; ++f)
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc[c][f] += __shfl_xor_sync(0xffffffffu, acc[c][f], o);
+          for (int o = 16; o > 0; o >>= 1) {
+            if constexpr (std::is_same<R, dword>::value) {
+              dw_norm(acc[c][f]);
+              acc[c][f] = dw_add(acc[c][f], dw_shfl_xor(acc[c][f], o));
+            } else {
+              acc[c][f] += __shfl_xor_sync(0xffffffffu, acc[c][f], o);
+            }
+          }
       if (lane != 0) continue;
     }
 #pragma unroll
     for (int c = 0; c < M::NCO; ++c) {
-      Tout[(2 * c + 0) * stride_out + pos] = (OUT)((double)acc[c][0] * scale);
-      Tout[(2 * c + 1) * stride_out + pos] = (OUT)((double)acc[c][1] * scale);
+      store_out(Tout + (2 * c + 0) * stride_out + pos, acc[c][0], scale);
+      store_out(Tout + (2 * c + 1) * stride_out + pos, acc[c][1], scale);
     }
   }
 }
@@ -271,7 +433,9 @@ cudaError_t launch_typed(lsp_ctx* c, int d, int k, int t, const int32_t* list,
                          int64_t stride_prev, void* Tout, int64_t lo_out, int64_t stride_out,
                          bool by_index, double scale, const R* X) {
   const R* prev = (const R*)Tprev;
-  if (t == 2) {  // five cosine rows (2D and 3D)
+  if constexpr (std::is_same<R, dword>::value) {
+    if (t == 2) return cudaErrorInvalidValue;  // double-word stages serve t = 1 builds only
+  } else if (t == 2) {  // five cosine rows (2D and 3D)
     if (k == 1)
       return launch_k<1, 5, R, R>(c, list, count, cap, X, prev, lo_prev, stride_prev, (R*)Tout,
                                   lo_out, stride_out, by_index, scale);
@@ -308,16 +472,21 @@ cudaError_t launch_typed(lsp_ctx* c, int d, int k, int t, const int32_t* list,
 cudaError_t launch_stage(lsp_ctx* c, int d, int k, int t, const int32_t* list,
                          const int32_t* count, int64_t cap, const void* Tprev, int64_t lo_prev,
                          int64_t stride_prev, void* Tout, int64_t lo_out, int64_t stride_out,
-                         bool by_index, bool fp32) {
+                         bool by_index, int prec) {
   // The final stage carries the 1/N of the inverse transform (N a power of two: exact).
   const double scale = (k == d) ? 1.0 / (double)c->geo.N : 1.0;
   static const char* names[4] = {"", "stage1", "stage2", "stage3"};
   int tm = timer_begin(c, names[k]);
-  cudaError_t e =
-      fp32 ? launch_typed<float>(c, d, k, t, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
-                                 lo_out, stride_out, by_index, scale, (const float*)c->xtab32.p)
-           : launch_typed<double>(c, d, k, t, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
-                                  lo_out, stride_out, by_index, scale, (const double*)c->xtab.p);
+  cudaError_t e;
+  if (prec == kPrecFP32)
+    e = launch_typed<float>(c, d, k, t, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
+                            lo_out, stride_out, by_index, scale, (const float*)c->xtab32.p);
+  else if (prec == kPrecDword)
+    e = launch_typed<dword>(c, d, k, t, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
+                            lo_out, stride_out, by_index, scale, (const dword*)c->xtabdw.p);
+  else
+    e = launch_typed<double>(c, d, k, t, list, count, cap, Tprev, lo_prev, stride_prev, Tout,
+                             lo_out, stride_out, by_index, scale, (const double*)c->xtab.p);
   timer_end(c, tm);
   return e;
 }

@@ -364,6 +364,15 @@ lsp_status flush_timers(lsp_ctx* c) {
 }
 
 // The launch sequence of steps a2-a7 for the sizes already prepared in the context.
+// Arithmetic of the a3 stages for a build: FP32 in the mixed mode; double words in the dword
+// mode for t = 1 in 1D and 2D (in 3D the stages are a small part of the build and the
+// tolerance, set by the spectral gap, is tight, so they stay FP64); FP64 otherwise.
+int stage_prec(const lsp_ctx* c, const lsp_stencil_opts& o) {
+  if (o.mode == LSP_MIXED) return kPrecFP32;
+  if (o.mode == LSP_DWORD && o.t == 1 && c->geo.d <= 2) return kPrecDword;
+  return kPrecFP64;
+}
+
 lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, bool upload,
                        bool rows = true) {
   const int d = c->geo.d;
@@ -402,7 +411,8 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
     count = counts + (d - k);
     cap = sz;
   }
-  const bool fp32 = o.mode == LSP_MIXED;  // the w table is refreshed by the caller
+  const int prec = stage_prec(c, o);  // the w table is refreshed by the caller
+  const bool fp32 = prec == kPrecFP32;
   for (int k = 1; k <= d; ++k) {
     const void* prev = k == 1 ? c->wtab.p : c->T[k - 1].p;
     const int64_t lo_prev = c->erange[k - 1].lo, stride_prev = c->erange[k - 1].size();
@@ -411,10 +421,10 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
       CUDA_OK(c, launch_stage(c, d, k, o.t, dense ? nullptr : (const int32_t*)c->elist[k].p,
                               dense ? nullptr : counts + (d - k), c->erange[k].size(), prev,
                               lo_prev, stride_prev, c->T[k].p, c->erange[k].lo,
-                              c->erange[k].size(), false, fp32));
+                              c->erange[k].size(), false, prec));
     } else {
       CUDA_OK(c, launch_stage(c, d, k, o.t, (const int32_t*)c->shift_m.p, counts + 0, cap_s,
-                              prev, lo_prev, stride_prev, c->gvals.p, 0, cap_s, true, fp32));
+                              prev, lo_prev, stride_prev, c->gvals.p, 0, cap_s, true, prec));
     }
   }
   // t = 1 stencils read the first classes of a t = 2 table (same row stride cap_s)
@@ -530,6 +540,22 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
       tw[2 * j + 1] = (double)(-sinl(ang));
     }
     std::vector<float> X32(X.begin(), X.end());
+    // double words of the same values, split from the extended-precision cosines
+    std::vector<float> Xdw(2 * 5 * P);
+    for (int a = 0; a < 5; ++a)
+      for (int p = 0; p < P; ++p) {
+        const long double wgt = (p == 0 || p == n / 2) ? 1.0L : 2.0L;
+        const long double x = wgt * cos_r(a * p);
+        const float hi = (float)x;
+        Xdw[2 * (a * P + p)] = hi;
+        Xdw[2 * (a * P + p) + 1] = (float)(x - (long double)hi);
+      }
+    if (!ensure(c, c->xtabdw, sizeof(float) * Xdw.size()) ||
+        cudaMemcpy(c->xtabdw.p, Xdw.data(), sizeof(float) * Xdw.size(), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+      st = LSP_ERR_CUDA;
+      break;
+    }
     if (!ensure(c, c->xtab32, sizeof(float) * X32.size()) ||
         cudaMemcpy(c->xtab32.p, X32.data(), sizeof(float) * X32.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess) {
@@ -570,7 +596,7 @@ lsp_status lsp_destroy(lsp_ctx* c) {
     if (c->ev_staged[k]) cudaEventDestroy(c->ev_staged[k]);
     if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
   }
-  DevBuf* bufs[] = {&c->v, &c->stats_part, &c->stats, &c->xtab, &c->xtab32, &c->shift_m, &c->shift_flag,
+  DevBuf* bufs[] = {&c->v, &c->stats_part, &c->stats, &c->xtab, &c->xtab32, &c->xtabdw, &c->shift_m, &c->shift_flag,
                     &c->idx_of, &c->counts, &c->wtab, &c->gvals, &c->alpha, &c->cst, &c->lam,
                     &c->sflags, &c->Q, &c->C, &c->P, &c->sidx, &c->colidx, &c->rowptr,
                     &c->fftbuf, &c->twiddle, &c->learn_in, &c->alpha2, &c->cst2, &c->lam2,
@@ -657,7 +683,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     return fail(c, LSP_ERR_ARG, "nd_leaf must be 0 or an even divisor >= 2 of n");
   if (o.t == 2 && o.mode == LSP_LEARNED)
     return fail(c, LSP_ERR_UNSUPPORTED, "learned builds use t = 1 neighbourhoods");
-  if (o.mode != LSP_FP64 && o.mode != LSP_MIXED && o.mode != LSP_LEARNED)
+  if (o.mode != LSP_FP64 && o.mode != LSP_MIXED && o.mode != LSP_LEARNED && o.mode != LSP_DWORD)
     return fail(c, LSP_ERR_ARG, "bad mode %d", o.mode);
   bool gated = false;
   if (o.mode == LSP_LEARNED) {
@@ -819,13 +845,13 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
   // w depends only on its index range and precision: refreshed (outside any graph) only when
   // those change, so a replayed graph always finds the table it was recorded with.
   {
-    const bool fp32 = o.mode == LSP_MIXED;
+    const int prec = stage_prec(c, o);
     if (!(c->wtab_lo == c->erange[0].lo && c->wtab_size == c->erange[0].size() &&
-          c->wtab_fp32 == (int)fp32)) {
-      CUDA_OK(c, launch_wtable(c, c->erange[0].lo, c->erange[0].size(), c->wtab.p, fp32));
+          c->wtab_prec == prec)) {
+      CUDA_OK(c, launch_wtable(c, c->erange[0].lo, c->erange[0].size(), c->wtab.p, prec));
       c->wtab_lo = c->erange[0].lo;
       c->wtab_size = c->erange[0].size();
-      c->wtab_fp32 = (int)fp32;
+      c->wtab_prec = prec;
     }
   }
   lsp_status st;
@@ -872,7 +898,9 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     ++c->build_gen;
     c->built_learned = false;
     c->built_gated = gated;
-    c->mode_used = gated ? LSP_LEARNED : o.mode;
+    c->mode_used = gated ? LSP_LEARNED
+                         : (o.mode == LSP_DWORD && stage_prec(c, o) != kPrecDword ? LSP_FP64
+                                                                                 : o.mode);
     c->t_built = o.t;
     c->leaf_built = o.t == 2 ? o.nd_leaf : 0;
   }

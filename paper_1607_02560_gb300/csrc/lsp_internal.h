@@ -31,6 +31,9 @@ constexpr int kMaxSymBlk = 6;
 // counts[] layout: [0] |S|, [1], [2] sizes of the compacted stage domains, [kErrWord] device
 // error bits, [16...] compaction tile scratch.
 constexpr int kErrWord = 15;
+// Arithmetic of the lattice-separable stages (a3): FP64, FP32 (mixed mode), double words of
+// FP32 (the dword mode: about 48 significant bits on the FP32 pipe).
+constexpr int kPrecFP64 = 0, kPrecFP32 = 1, kPrecDword = 2;
 constexpr int kGateWord = 14;  // points the learned-stencil gate sent back to the eigen path
 // Bit of the error word set by a checked build (-DLSP_CHECKS) when an index left its array.
 constexpr int kErrBounds = 1 << 10;
@@ -115,7 +118,7 @@ struct lsp_ctx {
 
   // cos table X_a(p) = w_p cos(2 pi a p / n), a = 0..4, p = 0..n/2 (FP64 and FP32 copies;
   // t = 1 reads rows 0..2)
-  lsp::DevBuf xtab, xtab32;
+  lsp::DevBuf xtab, xtab32, xtabdw;
 
   // t = 2 neighbourhoods (2D): offsets, classes and symmetry basis of mu_0^2, and the build's
   // choice: rows of a t = 2 build are (2t+1)^d = 25 wide; with nd_leaf > 0 a point uses
@@ -139,7 +142,7 @@ struct lsp_ctx {
   lsp::DevBuf eflag[lsp::kMaxD], elist[lsp::kMaxD], T[lsp::kMaxD], wtab;
   bool edense[lsp::kMaxD] = {false, false, false};  // E_k evaluated over its whole range
   int64_t wtab_lo = 0, wtab_size = -1;  // range held by wtab (-1: none)
-  int wtab_fp32 = -1;
+  int wtab_prec = -1;
   int64_t alloc_gen = 0;  // bumped whenever a device buffer is (re)allocated
 
   // per-shift results (a3-a6); *2: the t = 2 stencils
@@ -206,11 +209,11 @@ cudaError_t launch_compact(lsp_ctx* c, const uint8_t* flags, int64_t lo, int64_t
                            int32_t* list, int32_t* count, int32_t* idx_of);
 cudaError_t launch_mark_stage(lsp_ctx* c, const int32_t* list, const int32_t* count,
                               int64_t cap, int64_t lo_prev, uint8_t* flag_prev);
-cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, void* w, bool fp32);
+cudaError_t launch_wtable(lsp_ctx* c, int64_t lo, int64_t range, void* w, int prec);
 cudaError_t launch_stage(lsp_ctx* c, int d, int k, int t, const int32_t* list,
                          const int32_t* count, int64_t cap, const void* Tprev, int64_t lo_prev,
                          int64_t stride_prev, void* Tout, int64_t lo_out, int64_t stride_out,
-                         bool by_index, bool fp32);
+                         bool by_index, int prec);
 cudaError_t launch_eig_t2(lsp_ctx* c, const int32_t* count, int64_t cap);
 cudaError_t launch_eig_dense3(lsp_ctx* c, const int32_t* count, int64_t cap);
 cudaError_t upload_cls125(const Geometry& g);

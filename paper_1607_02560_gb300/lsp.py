@@ -24,7 +24,7 @@ STATUS = {0: "LSP_OK", 1: "LSP_ERR_ARG", 2: "LSP_ERR_STATE", 3: "LSP_ERR_RESONAN
           4: "LSP_ERR_CUDA", 5: "LSP_ERR_OOM", 6: "LSP_ERR_TIMEOUT", 7: "LSP_ERR_DEGENERATE",
           8: "LSP_ERR_UNSUPPORTED"}
 POLICY = {"paper": 0, "local": 1, "list": 2, "mean": 3}
-MODE = {"fp64": 0, "mixed": 1, "learned": 2}
+MODE = {"fp64": 0, "mixed": 1, "learned": 2, "dword": 3}
 EIG = {"symmetric": 0, "full": 1}
 FLAG_DEGENERATE, FLAG_NONSYMMETRIC, FLAG_NOT_CONVERGED = 1, 2, 4
 
@@ -119,6 +119,7 @@ def lib() -> ctypes.CDLL:
                                                ctypes.c_int, ctypes.POINTER(ctypes.c_float), vp]),
         "lsp_mlp_last_error": (ctypes.c_char_p, [vp]),
         "lsp_mlp_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "lsp_mlp_set_schedule": (ctypes.c_int, [vp, ctypes.c_int]),
         "lsp_inject_alloc_failure": (None, [ctypes.c_int]),
         "lsp_set_mlp": (ctypes.c_int, [vp, vp]),
         "lsp_get_mode_used": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
@@ -515,6 +516,10 @@ class Mlp:
         self._check(lib().lsp_mlp_train_step(self.h, _ptr(X), _ptr(T), batch, lr, int(apply),
                                              ctypes.byref(loss), _ptr(grads)), "train_step")
         return loss.value
+
+    def set_schedule(self, schedule: int = 1):
+        """2D inference: 1 = two tiles in flight per SM (default), 0 = one tile at a time."""
+        self._check(lib().lsp_mlp_set_schedule(self.h, int(schedule)), "set_schedule")
 
     def set_wait_limit(self, ns: int = 0):
         """Limit (ns) of the fused kernel's operand waits; 0 restores the default (1 s)."""

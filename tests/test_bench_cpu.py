@@ -95,7 +95,7 @@ def test_result_line_is_compact_and_complete():
     e = j["e2e"]
     assert e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert j["cpu_baseline"]["cores"] == 16 and j["cpu_baseline"]["single_core"]["cores"] == 1
-    assert len(j["forms"]) == 6
+    assert len(j["forms"]) == len(bench.FORMS)
 
 
 def test_result_line_drops_optional_parts_before_the_contract_keys():

@@ -81,26 +81,33 @@ def stored_precision_backward(x, t, W, b, nout):
     """The gradients of the network's loss in FP64, with values rounded to bf16 where the
     network stores them (the hidden activations h_l, and the output and hidden gradients dY,
     dZ_l when they enter a product), built from the oracle's definitions (hard-swish and its
-    derivative). Returns (dW, db, S): S_l = |dZ_l|^T |a_{l-1}| is each weight gradient's sum of
-    absolute terms, the scale of its FP32 accumulation and of one-unit bf16 differences."""
+    derivative). Returns (dW, db, S, K): S_l = |dZ_l|^T |a_{l-1}| is each weight gradient's sum
+    of absolute terms, the scale of its FP32 accumulation and of one-unit bf16 differences;
+    K_l bounds what the derivative's jumps can change: hard-swish' jumps by 1/2 at z = -3 and
+    z = 3, and where z lies within the FP32 accumulation error of a jump the two sides may take
+    different branches, changing that term by half its size."""
     L = len(W)
-    a, zs, acts = x, [], [x]
+    a, zs, acts, near = x, [], [x], []
     for li in range(L):
         z = a @ W[li].T + b[li]
         zs.append(z)
+        err = 2e-5 * (np.abs(a) @ np.abs(W[li]).T + np.abs(b[li]))  # FP32 sums, generously
+        near.append(np.abs(np.abs(z) - 3.0) <= err)
         a = bf16(MO.hswish(z)) if li < L - 1 else z
         acts.append(a)
     g = np.zeros_like(a)
     g[:, :nout] = 2.0 * (a - t)[:, :nout] / (a.shape[0] * nout)
-    dW, db, S = [None] * L, [None] * L, [None] * L
+    dW, db, S, K = [None] * L, [None] * L, [None] * L, [None] * L
     for li in range(L - 1, -1, -1):
         dz = g if li == L - 1 else g * MO.hswish_grad(zs[li])
+        jump = np.zeros_like(g) if li == L - 1 else 0.5 * np.abs(g) * near[li]
         dz16 = bf16(dz)
         dW[li] = dz16.T @ acts[li]
         db[li] = dz.sum(axis=0)
         S[li] = np.abs(dz16).T @ np.abs(acts[li])
+        K[li] = jump.T @ np.abs(acts[li])
         g = dz16 @ W[li]
-    return dW, db, S
+    return dW, db, S, K
 
 
 @pytest.mark.parametrize("d", [2, 3])
@@ -134,19 +141,19 @@ def test_forward_and_gradients_match_oracle(stream, d):
     assert abs(loss - loss_ref) <= 3e-2 * loss_ref
     # entry by entry against the stored-precision computation: FP32 accumulation order and
     # an occasional one-unit bf16 difference of a stored value separate the two
-    dWs, dbs, S = stored_precision_backward(x, tp, W, b, nout)
+    dWs, dbs, S, KJ = stored_precision_backward(x, tp, W, b, nout)
     off = 0
     worst = []
     for layer, (n, k) in enumerate([(256, K0), (256, 256), (256, 256), (OUTP, 256)]):
         g = grads[off:off + n * k].reshape(n, k).astype(np.float64)
-        ref, sc = dWs[layer], S[layer]
+        ref, sc, kj = dWs[layer], S[layer], KJ[layer]
         if layer == 3:  # output rows past the real outputs carry no loss
-            g, ref, sc = g[:nout], ref[:nout], sc[:nout]
+            g, ref, sc, kj = g[:nout], ref[:nout], sc[:nout], kj[:nout]
         # the plain FP64 definition, as a whole layer
         full = dW[layer] * OUTP / nout
         full = full[:nout] if layer == 3 else full
         assert np.linalg.norm(g - full) <= 5e-2 * np.linalg.norm(full), layer
-        ew = float((np.abs(g - ref) / (8e-3 * sc + 1e-2 * np.abs(ref) + 1e-30)).max())
+        ew = float((np.abs(g - ref) / (8e-3 * sc + 1e-2 * np.abs(ref) + kj + 1e-30)).max())
         off += n * k
         gb = grads[off:off + n].astype(np.float64)
         rb = dbs[layer]
@@ -155,7 +162,7 @@ def test_forward_and_gradients_match_oracle(stream, d):
         eb = float((np.abs(gb - rb) / (2e-3 * np.abs(rb).max() + 1e-2 * np.abs(rb))).max())
         worst.append((round(ew, 3), round(eb, 3)))
         if ew > 1.0:  # where the worst entries sit, for the failure report
-            r = np.abs(g - ref) / (8e-3 * sc + 1e-2 * np.abs(ref) + 1e-30)
+            r = np.abs(g - ref) / (8e-3 * sc + 1e-2 * np.abs(ref) + kj + 1e-30)
             top = np.argsort(r.ravel())[-5:]
             print(f"layer {layer} worst entries (row, col, gpu, ref, scale):",
                   [(int(i // r.shape[1]), int(i % r.shape[1]), float(g.ravel()[i]),
@@ -164,6 +171,38 @@ def test_forward_and_gradients_match_oracle(stream, d):
         assert ew <= 1.0 and eb <= 1.0, (layer, ew, eb)
         off += n
     print(f"d={d}: largest entrywise gradient error / tolerance per layer (W, b): {worst}")
+
+
+@pytest.mark.parametrize("n", [64, 256, 1024])
+def test_two_tiles_in_flight_give_the_same_rows(stream, n):
+    """The 2D inference kernel with two tiles in flight per SM computes the same rows and
+    batch outputs, bit for bit, as the one-tile schedule (32 tiles: one per CTA; 512: three or
+    four per CTA; 8192: 53 or 54 per CTA, so both odd and even tile counts occur)."""
+    import torch
+    from paper_1607_02560_gb300 import Context, Mlp
+    mlp = Mlp(2, seed=7, stream=stream)
+    X, T = pool_2d(mlp, stream)
+    torch.cuda.synchronize()
+    mlp.fit_normalization(X, T, X.shape[0])
+    v = helmholtz_random_bumps(n, 2 * np.pi * n / 4, 16, 100)
+    ctx = Context(2, n, stream=stream)
+    ctx.set_mlp(mlp)
+    ctx.set_potential(v)
+    rows, ys = {}, {}
+    B = 128 * 5
+    for sched in (0, 1):
+        mlp.set_schedule(sched)
+        ctx.build_stencils(mode="learned")
+        ctx.synchronize()
+        assert ctx.mode_used() == "learned"
+        rows[sched] = [ctx.get_rows(k).copy() for k in "QCP"]
+        Y = torch.empty((B, mlp.outp), dtype=torch.float32, device="cuda")
+        mlp.forward(X[:B], B, Y)
+        torch.cuda.synchronize()
+        ys[sched] = Y.cpu().numpy()
+    for a, b in zip(rows[0], rows[1]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(ys[0], ys[1])
 
 
 def test_training_lowers_the_loss(stream):

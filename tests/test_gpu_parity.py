@@ -394,3 +394,89 @@ def test_mixed_mode_full_size_against_the_oracle(name, nsample):
         assert err <= max(1e-6, 1e3 * U32 * kappa), (i, err, kappa)
     print(f"mixed {name} full size: {len(idx)} shifts, max |d alpha| = {worst_abs:.3g}, "
           f"max |d alpha| / (u32 kappa) = {worst:.3g}")
+
+
+# ---- double-word stages (FP32 pairs on the FP32 pipe), held to the FP64 tolerance --------
+
+def dword_margin(tab, v, policy, sample=None):
+    """Largest |d alpha| / tol_alpha over the checked shifts (tol_alpha of the FP64 path)."""
+    n, d = v.shape[0], v.ndim
+    ref = O.build_stencils(v, policy, shift_subset=[])
+    idx = range(len(ref["S"])) if sample is None else sample
+    worst = 0.0
+    for i in idx:
+        st, ta, tc = shift_tols(n, d, ref["S"][i])
+        worst = max(worst, np.abs(tab["alpha"][i] - st["alpha"]).max() / ta)
+    return worst
+
+
+@pytest.mark.parametrize("name,n", [("helm2d_n32", 8), ("helm2d_n32", 16), ("helm2d_n32", 32),
+                                    ("helm2d_n256", 64), ("helm2d_n256", 128)])
+@pytest.mark.parametrize("policy", ["local", "paper", "mean"])
+def test_dword_small_parity(name, n, policy):
+    v = make_workload(name, n=n)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy=policy, mode="dword")
+    assert ctx.mode_used() == "dword"
+    tab = ctx.get_shift_table()
+    ref, tols = check_shift_table(tab, v, policy)
+    assert check_rows(ctx, v, ref, tols) == v.size
+    rows_consistent_with_table(ctx, v, tab)
+    print(f"dword {name} n={n} {policy}: max |d alpha| / tol = {dword_margin(tab, v, policy):.3g}")
+
+
+def test_dword_in_3d_runs_the_fp64_stages():
+    v = make_workload("schr3d_n64", n=16)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="local", mode="dword")
+    assert ctx.mode_used() == "fp64"
+    q = ctx.get_rows("Q").copy()
+    ctx.build_stencils(policy="local", mode="fp64")
+    assert np.array_equal(ctx.get_rows("Q"), q)
+
+
+@pytest.mark.parametrize("name,nsample", [("helm2d_n256", 200), ("helm2d_n1024", 40)])
+def test_dword_full_size_sampled(name, nsample):
+    v = make_workload(name)
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    for _ in range(2):
+        ctx.build_stencils(policy="local", mode="dword", use_graph=True)
+    tab = ctx.get_shift_table()
+    ns = len(tab["s"])
+    rng = np.random.default_rng(13)
+    sample = sorted(set(rng.choice(np.arange(1, ns - 1), nsample, replace=False).tolist())
+                    | {0, ns - 1})
+    ref, tols = check_shift_table(tab, v, "local", sample=sample)
+    assert check_rows(ctx, v, ref, tols) > 0
+    rows_consistent_with_table(ctx, v, tab)
+    print(f"dword {name} full size: {len(sample)} shifts, max |d alpha| / tol = "
+          f"{dword_margin(tab, v, 'local', sample):.3g}")
+
+
+def test_dword_graph_replay_is_bit_identical_and_gmres_unchanged():
+    import json
+    import os
+    import scipy.sparse
+    v = make_workload("helm2d_n32")
+    n = 32
+    ctx = ctx_for(v)
+    ctx.set_potential(v)
+    ctx.build_stencils(policy="local", mode="dword")
+    first = [ctx.get_rows(k).copy() for k in "QCP"]
+    for _ in range(2):
+        ctx.build_stencils(policy="local", mode="dword", use_graph=True)
+        for k, r in zip("QCP", first):
+            assert np.array_equal(ctx.get_rows(k), r)
+    with open(os.path.join(os.path.dirname(__file__), "golden", "gmres_helm2d_n32.json")) as fh:
+        gold = json.load(fh)["iterations"]
+    for pol in ("local", "paper"):
+        ctx.build_stencils(policy=pol, mode="dword")
+        mats = {}
+        for which in "CP":
+            rowptr, colidx, vals = ctx.export_sparse_rows(which)
+            mats[which] = scipy.sparse.csr_matrix((vals, colidx, rowptr), shape=(n * n, n * n))
+        _, it, res, info = O.gmres_solve(v, gaussian_source(n, 2, 2.0), mats["P"], mats["C"])
+        assert info == 0 and it == gold[f"{pol}/2.0"], (pol, it)
