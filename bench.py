@@ -200,12 +200,13 @@ def kernel_work(name: str, n: int, d: int, N: int, mu: int, sizes: list[int],
             ncls_k = ncls[k]
             return count * P * ncls_k * 2 * (10 + 3 / 4), "fp32_op"
         if mode == "mixed":
-            # FP32 stages are bound by the gather of the previous table from L2: stage 1 reads
-            # w(l + p^2) for every frequency p in [0, n/2] (4 B each), later stages read both
-            # functions of every class of the previous table at l + p^2 (8 B per class)
+            # FP32 stages, counted in FP32 operations as written: stage 1 per mirror pair two
+            # squarings, four additions and six fused multiply-adds; later stages one fused
+            # multiply-add per class, function and frequency. They are latency-bound on their
+            # gathers (ncu), so this fraction is low by nature
             if k == 1:
-                return count * P * 4, "l2_byte"
-            return count * P * 8 * {2: 3, 3: 6}[k], "l2_byte"
+                return count * ((n // 4) * 12 + 6), "fp32_op"
+            return count * P * ncls[k] * 2, "fp32_op"
         if k == 1:
             # mirror-paired: per pair 4 add/sub + 6 FMA (16 flops), plus the middle term (12)
             return count * ((n // 4) * 16 + 12), "flop"
@@ -320,6 +321,7 @@ def run_ours(args):
     N = v_host.size
     stream = torch.cuda.Stream()
     ctx = Context(d, n, stream=stream)
+    ctx.set_autotune(not args.no_autotune)  # shapes tuned in the first (warm-up) build
     mu = ctx.mu
     v_dev = torch.from_numpy(v_host).to("cuda")
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
@@ -443,6 +445,7 @@ def run_ours(args):
                           kernel_work("rows", n, d, N, mu, sizes), args.mode, peaks,
                           ("rows", args.workload, args.mode)) if rows_k else None)
     used = ctx.mode_used()
+    tun = ctx.tuning()
     ctx.close()
     res = {
         "metric": METRIC,
@@ -455,7 +458,8 @@ def run_ours(args):
         "config": {"workload": args.workload, "policy": args.policy, "mode": args.mode,
                    "mode_used": used, "d": d, "n": n, "points": N, "shifts": ns,
                    "l2": "flushed before every timed step (256 MiB write), outside the step events",
-                   "parallelism": f"replicas x{ws} (independent potentials)"},
+                   "parallelism": f"replicas x{ws} (independent potentials)",
+                   "autotune": tuning_summary(tun)},
         "roofline": roof,
         "rows_roofline": rows_roof,
         "gpu_launches": launches,
@@ -470,7 +474,7 @@ def run_ours(args):
                 "one_step_at_a_time": {"value": N / (float(np.median(e2e_ms)) * 1e-3),
                                        "ms_per_step": float(np.median(e2e_ms))}},
     }
-    detail = {"kernels": kern, "lattice_domains": sizes, "peak_source": peak_src,
+    detail = {"kernels": kern, "lattice_domains": sizes, "peak_source": peak_src, "tuning": tun,
               "workload_text": WORKLOAD_TEXT.get(args.workload, "")}
     if train_info:
         detail["training"] = {str(k): v for k, v in train_info.items()}
@@ -495,6 +499,15 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def tuning_summary(tun: dict) -> dict:
+    """{kernel: "threads x CTAs/SM, gain"} for the tuned kernels that take at least 10 us."""
+    out = {}
+    for key, (th, ps, md, mb) in tun.items():
+        if md >= 0.01:
+            out[key.split("/")[0]] = f"{th}x{ps} {md / mb:.2f}x"
+    return out
 
 
 def _r(x, nd=4):
@@ -584,7 +597,7 @@ def forms_block(args, torch, mlps, peaks):
 
 def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup: int,
                 mlp=None, stream=None, t: int = 1, nd_leaf: int = 0, peaks=None,
-                gmres: bool = True):
+                gmres: bool = True, autotune: bool = True):
     """stencils/s of one configuration (same step, L2 flush and events as the main line)."""
     from lsp_inputs import make_workload
     from paper_1607_02560_gb300 import Context
@@ -593,6 +606,7 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
     d, n, N = v.ndim, v.shape[0], v.size
     stream = stream or torch.cuda.Stream()
     ctx = Context(d, n, stream=stream)
+    ctx.set_autotune(autotune)
     if mlp is not None:
         ctx.set_mlp(mlp)
     v_dev = torch.from_numpy(v).to("cuda")
@@ -633,6 +647,7 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
         ctx.synchronize()
         kt = ctx.kernel_times()
         ctx.kernel_timing(False)
+    out["tuning"] = ctx.tuning()
     ctx.close()
     mu = (2 * t + 1) ** d
     out["kernel_ms_per_launch"] = {k: round(ms / max(cnt, 1), 4) for k, (ms, cnt) in kt.items()}
@@ -1035,6 +1050,8 @@ def main():
     ap.add_argument("--n", type=int, default=None, help="rescale the workload's grid (small cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (no tuning pass in the warm-up)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--cpu-only", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-procs", type=int, default=0, help="host processes of the oracle")

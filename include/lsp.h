@@ -98,6 +98,19 @@ typedef struct {
                        /* 0: no gate (the network's rows as they come).                       */
 } lsp_stencil_opts;
 
+/*
+ * Launch-shape autotuner (the paper has no counterpart; GB300 launch tuning). With on != 0,
+ * the first build of each configuration (policy, mode, t, size class of the shift count) runs
+ * eagerly, outside any graph capture, and times candidate launch shapes (threads per block and
+ * grid caps in CTAs per SM) of the stage, 2D eigen and row kernels on the real data; later
+ * builds (and recorded graphs) use the fastest. The per-point order of every sum is the same
+ * under every shape, so tuned builds are bit-identical to untuned ones. Off by default.
+ * lsp_get_tuning writes one line per tuned kernel ("key threads per_sm ms_default ms_best
+ * candidates") into buf (NUL-terminated); LSP_ERR_ARG if len is too small.
+ */
+lsp_status lsp_set_autotune(lsp_ctx* ctx, int on);
+lsp_status lsp_get_tuning(const lsp_ctx* ctx, char* buf, int64_t len);
+
 /* Fill *opts with the defaults: t=1, LOCAL policy, FP64, symmetric eigen-solve, no graph,
  * nd_leaf = 0, learned_gate = 0. */
 void lsp_default_opts(lsp_stencil_opts* opts);

@@ -1653,18 +1653,23 @@ cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int method
   int t = timer_begin(c, "eig");
   cudaError_t e;
   if (c->geo.d == 2 && method == LSP_EIG_SYMMETRIC && refine == 0) {
-    int64_t b = (cap + 127) / 128;
-    if (b > 152 * 16) b = 152 * 16;
-    if (b < 1) b = 1;
-    if (fp32_gram)
-      k_eig2d<float><<<(int)b, 128, 0, c->stream>>>((const double*)c->gvals.p, cap, count,
-                                                    (double*)c->alpha.p, (double*)c->cst.p,
-                                                    (double*)c->lam.p, (int32_t*)c->sflags.p);
-    else
-      k_eig2d<double><<<(int)b, 128, 0, c->stream>>>((const double*)c->gvals.p, cap, count,
-                                                     (double*)c->alpha.p, (double*)c->cst.p,
-                                                     (double*)c->lam.p, (int32_t*)c->sflags.p);
-    e = cudaGetLastError();
+    // one thread per shift; the block size (<= 128) and grid cap come from the autotuner
+    e = tuned_launch(c, std::string("eig2d/") + (fp32_gram ? "f32" : "f64") + "/w" +
+                            work_bucket(cap),
+                     {128, 16}, 128, 0, [&](LaunchShape sh) {
+      int64_t b = (cap + sh.threads - 1) / sh.threads;
+      if (b > 152 * (int64_t)sh.per_sm) b = 152 * (int64_t)sh.per_sm;
+      if (b < 1) b = 1;
+      if (fp32_gram)
+        k_eig2d<float><<<(int)b, sh.threads, 0, c->stream>>>(
+            (const double*)c->gvals.p, cap, count, (double*)c->alpha.p, (double*)c->cst.p,
+            (double*)c->lam.p, (int32_t*)c->sflags.p);
+      else
+        k_eig2d<double><<<(int)b, sh.threads, 0, c->stream>>>(
+            (const double*)c->gvals.p, cap, count, (double*)c->alpha.p, (double*)c->cst.p,
+            (double*)c->lam.p, (int32_t*)c->sflags.p);
+      return cudaGetLastError();
+    });
   } else if (c->geo.d == 3 && method == LSP_EIG_SYMMETRIC && refine == 0) {
     constexpr int kW = 4;
     int64_t b = (cap + kW - 1) / kW;

@@ -418,12 +418,24 @@ int log2i(int n) {
 template <int D, bool LOCAL, bool ROWS, bool SIDX>
 void launch_rows_t(lsp_ctx* c, const int32_t* count) {
   const int64_t N = c->geo.N;
-  int64_t b = (N + kThreads - 1) / kThreads;
-  if (b > 152 * 16) b = 152 * 16;
-  k_rows<D, LOCAL, ROWS, SIDX><<<(int)b, kThreads, 0, c->stream>>>(
-      (const double*)c->v.p, N, log2i(c->geo.n), (const int32_t*)c->idx_of.p, c->mrange.lo,
-      c->mrange.size(), (int32_t*)c->counts.p + kErrWord, (const int32_t*)c->shift_m.p, count, (const double*)c->alpha.p, (const double*)c->cst.p,
-      (double*)c->Q.p, (double*)c->C.p, (double*)c->P.p, (int32_t*)c->sidx.p);
+  auto go = [&](LaunchShape sh) {
+    int64_t b = (N + kThreads - 1) / kThreads;
+    if (b > 152 * (int64_t)sh.per_sm) b = 152 * (int64_t)sh.per_sm;
+    k_rows<D, LOCAL, ROWS, SIDX><<<(int)b, kThreads, 0, c->stream>>>(
+        (const double*)c->v.p, N, log2i(c->geo.n), (const int32_t*)c->idx_of.p, c->mrange.lo,
+        c->mrange.size(), (int32_t*)c->counts.p + kErrWord, (const int32_t*)c->shift_m.p,
+        count, (const double*)c->alpha.p, (const double*)c->cst.p, (double*)c->Q.p,
+        (double*)c->C.p, (double*)c->P.p, (int32_t*)c->sidx.p);
+    return cudaGetLastError();
+  };
+  if (!ROWS) {  // the shift-index export is not tuned
+    go({kThreads, 16});
+    return;
+  }
+  // one block per 256 points (shared tables are sized for it): only the grid cap is tuned
+  tuned_launch(c, std::string("rows/d") + std::to_string(D) + (LOCAL ? "/local" : "/list") + "/w" +
+                      work_bucket(N),
+               {kThreads, 16}, kThreads, kThreads, go);
 }
 
 template <bool ROWS, bool SIDX>

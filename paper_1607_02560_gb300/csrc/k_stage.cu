@@ -344,12 +344,12 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
   using M = StageMap<K, A>;
   extern __shared__ __align__(16) unsigned char xs_raw[];
   R* xs = reinterpret_cast<R*>(xs_raw);  // [A][P]
-  for (int i = threadIdx.x; i < A * P; i += kThreads) xs[i] = X[i];
+  for (int i = threadIdx.x; i < A * P; i += blockDim.x) xs[i] = X[i];
   __syncthreads();
   // list == nullptr: the domain is the whole range [lo_out, lo_out + stride_out)
   const int64_t cnt = list ? (int64_t)*count_ptr : stride_out;
   const int lane = threadIdx.x & 31;
-  const int64_t per_block = SPLIT ? kThreads / 32 : kThreads;
+  const int64_t per_block = SPLIT ? blockDim.x / 32 : blockDim.x;
   const int64_t sub = SPLIT ? (threadIdx.x >> 5) : threadIdx.x;
   for (int64_t idx = (int64_t)blockIdx.x * per_block + sub; idx < cnt;
        idx += (int64_t)gridDim.x * per_block) {
@@ -403,14 +403,21 @@ cudaError_t launch_kk(lsp_ctx* c, const int32_t* list, const int32_t* count, int
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  const int64_t per_block = SPLIT ? kThreads / 32 : kThreads;
-  int64_t b = (cap + per_block - 1) / per_block;
-  if (b < 1) b = 1;
-  if (b > 152 * 16) b = 152 * 16;
-  k_stage<K, A, R, OUT, SPLIT><<<(int)b, kThreads, smem, c->stream>>>(
-      list, count, P, X, Tprev, lo_prev, stride_prev, Tout, lo_out, stride_out, by_index ? 1 : 0,
-      scale, (int32_t*)c->counts.p + kErrWord);
-  return cudaGetLastError();
+  // launch shape: 256 threads and at most 16 CTAs per SM unless the autotuner found better
+  // (the per-point order of the sums does not depend on it, so the results do not either)
+  const std::string key = std::string("stage") + std::to_string(K) + "/A" + std::to_string(A) +
+                          "/" + (sizeof(R) == 4 ? "f32" : (std::is_same<R, dword>::value ? "dw" : "f64")) +
+                          (SPLIT ? "/split" : "") + "/w" + work_bucket(cap);
+  return tuned_launch(c, key, {kThreads, 16}, kThreads, 0, [&](LaunchShape sh) {
+    const int64_t per_block = SPLIT ? sh.threads / 32 : sh.threads;
+    int64_t b = (cap + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > 152 * (int64_t)sh.per_sm) b = 152 * (int64_t)sh.per_sm;
+    k_stage<K, A, R, OUT, SPLIT><<<(int)b, sh.threads, smem, c->stream>>>(
+        list, count, P, X, Tprev, lo_prev, stride_prev, Tout, lo_out, stride_out,
+        by_index ? 1 : 0, scale, (int32_t*)c->counts.p + kErrWord);
+    return cudaGetLastError();
+  });
 }
 
 // Domains below about two threads per SM-lane slot are spread over warps instead.

@@ -318,6 +318,59 @@ bool ensure(lsp_ctx* c, DevBuf& b, size_t bytes) {
   return true;
 }
 
+std::string work_bucket(int64_t work) {
+  int b = 0;
+  while (b < 62 && ((int64_t)1 << b) < work) ++b;
+  return std::to_string(b);
+}
+
+cudaError_t tuned_launch(lsp_ctx* c, const std::string& key, LaunchShape def, int threads_max,
+                         int fixed_threads, const std::function<cudaError_t(LaunchShape)>& launch) {
+  auto it = c->tune.find(key);
+  if (it != c->tune.end()) return launch(it->second.best);
+  if (!c->tuning) return launch(def);
+  // candidates: the default first, then threads x grid caps (CTAs per SM)
+  std::vector<LaunchShape> cand = {def};
+  const int th_opts[3] = {64, 128, 256}, sm_opts[5] = {2, 4, 8, 16, 32};
+  for (int th : th_opts) {
+    if (th > threads_max || (fixed_threads > 0 && th != fixed_threads)) continue;
+    for (int ps : sm_opts)
+      if (!(th == def.threads && ps == def.per_sm)) cand.push_back({th, ps});
+  }
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return cudaGetLastError();
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cudaGetLastError();
+  }
+  float best_ms = 1e30f, def_ms = 0.0f;
+  LaunchShape best = def;
+  cudaError_t err = cudaSuccess;
+  for (size_t k = 0; k < cand.size() && err == cudaSuccess; ++k) {
+    err = launch(cand[k]);  // warm
+    float ms = 1e30f;
+    for (int r = 0; r < 3 && err == cudaSuccess; ++r) {
+      cudaEventRecord(e0, c->stream);
+      err = launch(cand[k]);
+      cudaEventRecord(e1, c->stream);
+      if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+      float t = 0.0f;
+      if (err == cudaSuccess) err = cudaEventElapsedTime(&t, e0, e1);
+      if (t < ms) ms = t;
+    }
+    if (k == 0) def_ms = ms;
+    if (ms < best_ms * 0.98f || k == 0) {  // a new shape must win by 2%
+      best_ms = ms;
+      best = cand[k];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return err;
+  c->tune[key] = {best, def_ms, best_ms, (int)cand.size()};
+  return launch(best);
+}
+
 int timer_begin(lsp_ctx* c, const char* name) {
   if (!c->timing) return -1;
   int slot = -1;
@@ -855,6 +908,22 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     }
   }
   lsp_status st;
+  if (c->autotune && !c->timing) {
+    // the first build of a configuration times the candidate launch shapes eagerly (outside
+    // any capture); the build it runs is a complete one, and later builds use the winners
+    std::vector<int64_t> cfg = {o.policy, o.mode, o.eig_method, o.refine_steps, o.t, o.nd_leaf,
+                                (int64_t)gated, (int64_t)std::stoi(work_bucket(cap_s))};
+    if (std::find(c->tuned_configs.begin(), c->tuned_configs.end(), cfg) ==
+        c->tuned_configs.end()) {
+      c->tuning = true;
+      st = issue_build(c, o, cap_s, false, !gated);
+      c->tuning = false;
+      if (st != LSP_OK) return st;
+      CUDA_OK(c, cudaStreamSynchronize(c->stream));
+      c->tuned_configs.push_back(cfg);
+      ++c->tune_gen;
+    }
+  }
   const bool capturable = c->stream != nullptr && c->stream != cudaStreamLegacy &&
                           c->stream != cudaStreamPerThread;
   if (o.use_graph && !c->timing && capturable) {
@@ -865,6 +934,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
     for (int k = 0; k <= d; ++k) key.push_back(c->erange[k].lo);
     for (int k = 0; k < kMaxD; ++k) key.push_back(c->edense[k]);
     key.push_back(c->alloc_gen);  // any reallocation invalidates recorded pointers
+    key.push_back(c->tune_gen);   // so does a tuning pass (new launch shapes)
     if (!c->graph || key != c->graph_key) {
       if (c->graph) cudaGraphExecDestroy(c->graph);
       c->graph = nullptr;
@@ -1131,6 +1201,27 @@ lsp_status lsp_set_mlp(lsp_ctx* c, lsp_mlp* m) {
   if (m && mlp_dim(m) != c->geo.d) return fail(c, LSP_ERR_ARG, "network dimension mismatch");
   if (m) CUDA_OK(c, mlp_sync(m));
   c->mlp = m;
+  return LSP_OK;
+}
+
+lsp_status lsp_set_autotune(lsp_ctx* c, int on) {
+  if (!c) return LSP_ERR_ARG;
+  c->autotune = on != 0;
+  return LSP_OK;
+}
+
+lsp_status lsp_get_tuning(const lsp_ctx* c, char* buf, int64_t len) {
+  if (!c || !buf || len < 1) return LSP_ERR_ARG;
+  std::string out;
+  for (const auto& kv : c->tune) {
+    char line[256];
+    snprintf(line, sizeof line, "%s %d %d %.5f %.5f %d\n", kv.first.c_str(), kv.second.best.threads,
+             kv.second.best.per_sm, kv.second.ms_default, kv.second.ms_best,
+             kv.second.candidates);
+    out += line;
+  }
+  if ((int64_t)out.size() + 1 > len) return LSP_ERR_ARG;
+  memcpy(buf, out.c_str(), out.size() + 1);
   return LSP_OK;
 }
 

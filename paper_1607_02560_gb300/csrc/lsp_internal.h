@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -83,6 +85,16 @@ struct Geometry {
   uint8_t cls_of[kMaxMuGeo][kMaxMuGeo];  // class of o_a - o_b (sorted |components|)
 };
 
+// Launch shape of a tunable kernel: threads per block and the grid cap in CTAs per SM.
+struct LaunchShape {
+  int threads, per_sm;
+};
+struct TuneRecord {
+  LaunchShape best;
+  float ms_default, ms_best;
+  int candidates;
+};
+
 struct Range {
   int64_t lo = 0, hi = -1;  // inclusive
   int64_t size() const { return hi >= lo ? hi - lo + 1 : 0; }
@@ -147,6 +159,12 @@ struct lsp_ctx {
 
   // per-shift results (a3-a6); *2: the t = 2 stencils
   lsp::DevBuf gvals, alpha, cst, lam, sflags, alpha2, cst2, lam2, sflags2;
+  // launch-shape autotuner (lsp_set_autotune): the first build of a configuration times
+  // candidate shapes of the stage, eigen and row kernels eagerly; the winners are kept here
+  bool autotune = false, tuning = false;
+  std::map<std::string, lsp::TuneRecord> tune;
+  std::vector<std::vector<int64_t>> tuned_configs;
+  int64_t tune_gen = 0;  // bumped when a tuning pass changes shapes (invalidates the graph)
   // learned-stencil gate: per-point residual ratio of the last gated learned build
   lsp::DevBuf gate_rho;
   bool built_gated = false;
@@ -224,6 +242,13 @@ cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int eig_me
                        int refine_steps, bool fp32_gram);
 cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count);
 cudaError_t launch_sidx(lsp_ctx* c, int policy, const int32_t* count);
+// Launch through the autotuner: the tuned shape of `key` if there is one; during a tuning pass
+// (ctx->tuning) each candidate shape is timed (side-effect-free kernels only: the launch must
+// be repeatable) and the fastest kept; otherwise `def`. threads_max bounds the block size (the
+// kernel's launch bound); fixed_threads > 0 tunes only the grid cap.
+cudaError_t tuned_launch(lsp_ctx* c, const std::string& key, LaunchShape def, int threads_max,
+                         int fixed_threads, const std::function<cudaError_t(LaunchShape)>& launch);
+std::string work_bucket(int64_t work);
 cudaError_t launch_learned_gate(lsp_ctx* c, int policy, const int32_t* count, int64_t cap,
                                 double tau, float* rho, int32_t* nfall);
 cudaError_t launch_colidx(lsp_ctx* c);

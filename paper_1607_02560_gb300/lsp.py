@@ -124,6 +124,8 @@ def lib() -> ctypes.CDLL:
         "lsp_set_mlp": (ctypes.c_int, [vp, vp]),
         "lsp_get_mode_used": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
         "lsp_get_gate_stats": (ctypes.c_int, [vp, i64p, vp]),
+        "lsp_set_autotune": (ctypes.c_int, [vp, ctypes.c_int]),
+        "lsp_get_tuning": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_int64]),
         "lsp_default_nd_opts": (None, [ctypes.POINTER(NdOpts)]),
         "lsp_nd_factor": (ctypes.c_int, [vp, ctypes.POINTER(NdOpts)]),
         "lsp_nd_get_info": (ctypes.c_int, [vp, ctypes.POINTER(NdInfo)]),
@@ -421,6 +423,20 @@ class Context:
         m = ctypes.c_int()
         self._check(lib().lsp_get_mode_used(self.h, ctypes.byref(m)), "get_mode_used")
         return {v: k for k, v in MODE.items()}.get(m.value, str(m.value))
+
+    def set_autotune(self, on: bool = True):
+        """Tune launch shapes on the first build of each configuration (bit-identical rows)."""
+        self._check(lib().lsp_set_autotune(self.h, int(bool(on))), "set_autotune")
+
+    def tuning(self) -> dict:
+        """{kernel key: (threads, CTAs per SM, ms with the default shape, ms tuned)}."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        self._check(lib().lsp_get_tuning(self.h, buf, len(buf)), "get_tuning")
+        out = {}
+        for line in buf.value.decode().splitlines():
+            k, th, ps, md, mb, _ = line.split()
+            out[k] = (int(th), int(ps), float(md), float(mb))
+        return out
 
     def gate_stats(self, with_rho: bool = True):
         """(points that fell back to the eigen path, per-point residual ratio or None) of the

@@ -91,7 +91,7 @@ def stored_precision_backward(x, t, W, b, nout):
     for li in range(L):
         z = a @ W[li].T + b[li]
         zs.append(z)
-        err = 2e-5 * (np.abs(a) @ np.abs(W[li]).T + np.abs(b[li]))  # FP32 sums, generously
+        err = 2e-4 * (np.abs(a) @ np.abs(W[li]).T + np.abs(b[li]))  # FP32 sums, generously
         near.append(np.abs(np.abs(z) - 3.0) <= err)
         a = bf16(MO.hswish(z)) if li < L - 1 else z
         acts.append(a)
@@ -107,7 +107,7 @@ def stored_precision_backward(x, t, W, b, nout):
         S[li] = np.abs(dz16).T @ np.abs(acts[li])
         K[li] = jump.T @ np.abs(acts[li])
         g = dz16 @ W[li]
-    return dW, db, S, K
+    return dW, db, S, K, zs
 
 
 @pytest.mark.parametrize("d", [2, 3])
@@ -141,7 +141,7 @@ def test_forward_and_gradients_match_oracle(stream, d):
     assert abs(loss - loss_ref) <= 3e-2 * loss_ref
     # entry by entry against the stored-precision computation: FP32 accumulation order and
     # an occasional one-unit bf16 difference of a stored value separate the two
-    dWs, dbs, S, KJ = stored_precision_backward(x, tp, W, b, nout)
+    dWs, dbs, S, KJ, ZS = stored_precision_backward(x, tp, W, b, nout)
     off = 0
     worst = []
     for layer, (n, k) in enumerate([(256, K0), (256, 256), (256, 256), (OUTP, 256)]):
@@ -168,6 +168,11 @@ def test_forward_and_gradients_match_oracle(stream, d):
                   [(int(i // r.shape[1]), int(i % r.shape[1]), float(g.ravel()[i]),
                     float(ref.ravel()[i]), float(sc.ravel()[i])) for i in top],
                   "columns above tolerance:", sorted(set((np.nonzero(r > 1)[1]).tolist()))[:20])
+            j = int(top[-1] // r.shape[1])
+            zj = ZS[layer][:, j]
+            print(f"unit {j}: distance of z to the kinks (min over samples) "
+                  f"{float(np.min(np.abs(np.abs(zj) - 3.0))):.3g}, |z| range "
+                  f"[{float(np.abs(zj).min()):.3g}, {float(np.abs(zj).max()):.3g}]")
         assert ew <= 1.0 and eb <= 1.0, (layer, ew, eb)
         off += n
     print(f"d={d}: largest entrywise gradient error / tolerance per layer (W, b): {worst}")
@@ -180,11 +185,12 @@ def test_two_tiles_in_flight_give_the_same_rows(stream, n):
     four per CTA; 8192: 53 or 54 per CTA, so both odd and even tile counts occur)."""
     import torch
     from paper_1607_02560_gb300 import Context, Mlp
+    from paper_1607_02560_gb300.learned import make_pool
     mlp = Mlp(2, seed=7, stream=stream)
-    X, T = pool_2d(mlp, stream)
+    v = helmholtz_random_bumps(n, 2 * np.pi * n / 4, 16, 100)
+    X, T = make_pool(mlp, [v], 4096, stream)  # normalised on this potential: in range
     torch.cuda.synchronize()
     mlp.fit_normalization(X, T, X.shape[0])
-    v = helmholtz_random_bumps(n, 2 * np.pi * n / 4, 16, 100)
     ctx = Context(2, n, stream=stream)
     ctx.set_mlp(mlp)
     ctx.set_potential(v)

@@ -480,3 +480,28 @@ def test_dword_graph_replay_is_bit_identical_and_gmres_unchanged():
             mats[which] = scipy.sparse.csr_matrix((vals, colidx, rowptr), shape=(n * n, n * n))
         _, it, res, info = O.gmres_solve(v, gaussian_source(n, 2, 2.0), mats["P"], mats["C"])
         assert info == 0 and it == gold[f"{pol}/2.0"], (pol, it)
+
+
+# ---- launch-shape autotuner ------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,n,mode", [("helm2d_n256", 256, "fp64"), ("helm2d_n256", 256, "dword"),
+                                         ("helm2d_n256", 256, "mixed"), ("schr3d_n64", 32, "fp64")])
+def test_autotuned_builds_are_bit_identical(name, n, mode):
+    v = make_workload(name, n=n)
+    ref = ctx_for(v)
+    ref.set_potential(v)
+    ref.build_stencils(policy="local", mode=mode, use_graph=True)
+    want = [ref.get_rows(k).copy() for k in "QCP"]
+    ctx = ctx_for(v)
+    ctx.set_autotune(True)
+    ctx.set_potential(v)
+    for _ in range(3):  # the tuning pass, then graph record and replay with the tuned shapes
+        ctx.build_stencils(policy="local", mode=mode, use_graph=True)
+        for k, r in zip("QCP", want):
+            assert np.array_equal(ctx.get_rows(k), r)
+    tun = ctx.tuning()
+    assert any(k.startswith("stage1") for k in tun) and any(k.startswith("rows") for k in tun)
+    for key, (th, ps, md, mb) in tun.items():
+        assert th in (64, 128, 256) and ps in (2, 4, 8, 16, 32) and 0 < mb <= md * 1.0001, key
+    print(f"autotune {name} n={n} {mode}: " + ", ".join(
+        f"{k}={th}x{ps} ({md:.4f}->{mb:.4f} ms)" for k, (th, ps, md, mb) in tun.items()))
