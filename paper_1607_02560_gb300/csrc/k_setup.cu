@@ -30,9 +30,8 @@ __device__ __forceinline__ double warp_sum(double x) {
 // Per-block partial min / max / sum / count of non-finite values, 4 doubles per block. With
 // vcopy, v is also stored there (v read from page-locked host memory over the host link, so
 // the upload and the statistics take one pass and no copy engine).
-__global__ void __launch_bounds__(kThreads) k_stats_partial(const double* __restrict__ v,
-                                                            int64_t N, double* __restrict__ part,
-                                                            double* __restrict__ vcopy) {
+__device__ void stats_partial(const double* __restrict__ v, int64_t N, double* __restrict__ part,
+                              double* __restrict__ vcopy) {
   double mn = DBL_MAX, mx = -DBL_MAX, sm = 0.0, bad = 0.0;
   for (int64_t j = (int64_t)blockIdx.x * kThreads + threadIdx.x; j < N;
        j += (int64_t)gridDim.x * kThreads) {
@@ -79,10 +78,9 @@ __global__ void __launch_bounds__(kThreads) k_stats_partial(const double* __rest
 
 // Reduces the partials to (min, max, sum, non-finite count) in out[0..3], and also in
 // host_out[0..3] (page-locked host memory, device address) when given, so that the host reads
-// them without a copy.
-__global__ void __launch_bounds__(kThreads) k_stats_final(const double* __restrict__ part, int nb,
-                                                          double* __restrict__ out,
-                                                          double* __restrict__ host_out) {
+// them without a copy. The partials are taken in block order, so the sum does not depend on
+// which block finished last.
+__device__ void stats_final(const double* part, int nb, double* out, double* host_out) {
   double mn = DBL_MAX, mx = -DBL_MAX, sm = 0.0, bad = 0.0;
   for (int b = threadIdx.x; b < nb; b += kThreads) {
     mn = fmin(mn, part[4 * b + 0]);
@@ -125,6 +123,26 @@ __global__ void __launch_bounds__(kThreads) k_stats_final(const double* __restri
       }
     }
   }
+}
+
+// One launch: every block writes its partial, and the block that finishes last (a ticket
+// counter, reset by that block for the next call) reduces them all.
+__global__ void __launch_bounds__(kThreads) k_stats(const double* __restrict__ v, int64_t N,
+                                                    double* __restrict__ part,
+                                                    double* __restrict__ vcopy,
+                                                    double* __restrict__ out,
+                                                    double* __restrict__ host_out,
+                                                    unsigned int* __restrict__ ticket) {
+  stats_partial(v, N, part, vcopy);
+  __shared__ bool last;
+  __threadfence();  // this block's partial is visible before its ticket is taken
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  stats_final(part, gridDim.x, out, host_out);
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // Lattice index of the resonance-free shift (4m+2) pi^2 nearest to x (Sec. 4.1); halves away
@@ -320,11 +338,13 @@ __global__ void __launch_bounds__(kThreads) k_copy_f64(const double* __restrict_
 
 }  // namespace
 
-cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks, const double* src) {
+cudaError_t launch_stats(lsp_ctx* c, int nblocks, const double* src) {
   int t = timer_begin(c, "stats");
   double* vd = (double*)c->v.p;
-  k_stats_partial<<<nblocks, kThreads, 0, c->stream>>>(src, c->geo.N, (double*)c->stats_part.p,
-                                                        src == vd ? nullptr : vd);
+  double* st = (double*)c->stats.p;
+  k_stats<<<nblocks, kThreads, 0, c->stream>>>(src, c->geo.N, (double*)c->stats_part.p,
+                                               src == vd ? nullptr : vd, st, c->h_stats_dev,
+                                               (unsigned int*)(st + 4));
   timer_end(c, t);
   return cudaGetLastError();
 }
@@ -340,14 +360,6 @@ cudaError_t launch_zero(lsp_ctx* c, void* p, size_t bytes) {
 cudaError_t launch_copy_f64(lsp_ctx* c, const double* src, double* dst, int64_t n) {
   int t = timer_begin(c, "copy_rows");
   k_copy_f64<<<grid_for((n + 1) / 2), kThreads, 0, c->stream>>>(src, dst, n);
-  timer_end(c, t);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_stats_final(lsp_ctx* c, int nblocks) {
-  int t = timer_begin(c, "stats_final");
-  k_stats_final<<<1, kThreads, 0, c->stream>>>((const double*)c->stats_part.p, nblocks,
-                                                (double*)c->stats.p, c->h_stats_dev);
   timer_end(c, t);
   return cudaGetLastError();
 }

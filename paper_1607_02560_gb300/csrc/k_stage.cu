@@ -328,11 +328,14 @@ __device__ __forceinline__ void stage_accumulate(const R* __restrict__ xs, int P
   }
 }
 
-// One thread per domain point (SPLIT = false), or one warp per domain point with the lanes
-// splitting the frequencies and a shuffle reduction at the end (SPLIT = true, used when the
-// domain is too small to fill the GPU, e.g. a few dozen shifts). Output: Tout[(c * 2 + f) *
-// stride_out + pos], pos = index in the list (by_index) or l - lo_out.
-template <int K, int A, typename R, typename OUT, bool SPLIT>
+// LANES threads per domain point: one (a large domain fills the GPU by itself), four (a
+// domain of a few hundred thousand points, e.g. the shift list of the per-point policy at 2D
+// n = 1024, which one thread per point would leave at a third of the SM's thread slots), or a
+// whole warp (a few dozen shifts). The lanes of a group split the frequencies (lane r takes
+// p = r, r + LANES, ...) and a shuffle reduction combines them; the order of every sum depends
+// only on LANES, which the domain size fixes, not on the launch shape. Output:
+// Tout[(c * 2 + f) * stride_out + pos], pos = index in the list (by_index) or l - lo_out.
+template <int K, int A, typename R, typename OUT, int LANES>
 __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ list,
                                                     const int32_t* __restrict__ count_ptr, int P,
                                                     const R* __restrict__ X,
@@ -348,9 +351,9 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
   __syncthreads();
   // list == nullptr: the domain is the whole range [lo_out, lo_out + stride_out)
   const int64_t cnt = list ? (int64_t)*count_ptr : stride_out;
-  const int lane = threadIdx.x & 31;
-  const int64_t per_block = SPLIT ? blockDim.x / 32 : blockDim.x;
-  const int64_t sub = SPLIT ? (threadIdx.x >> 5) : threadIdx.x;
+  const int lane = threadIdx.x % LANES;
+  const int64_t per_block = blockDim.x / LANES;
+  const int64_t sub = threadIdx.x / LANES;
   for (int64_t idx = (int64_t)blockIdx.x * per_block + sub; idx < cnt;
        idx += (int64_t)gridDim.x * per_block) {
     const int64_t l = list ? (int64_t)__ldg(list + idx) : lo_out + idx;
@@ -363,18 +366,18 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
 #pragma unroll
     for (int c = 0; c < M::NCO; ++c) acc[c][0] = acc[c][1] = zero_of<R>();
     if constexpr (std::is_same<R, dword>::value)
-      stage_accumulate_dw<K, A>(xs, P, l, Tprev, lo_prev, stride_prev, SPLIT ? lane : 0,
-                                SPLIT ? 32 : 1, acc);
+      stage_accumulate_dw<K, A>(xs, P, l, Tprev, lo_prev, stride_prev, lane, LANES, acc);
     else
-      stage_accumulate<K, A, R>(xs, P, l, Tprev, lo_prev, stride_prev, SPLIT ? lane : 0,
-                                SPLIT ? 32 : 1, acc);
-    if (SPLIT) {
+      stage_accumulate<K, A, R>(xs, P, l, Tprev, lo_prev, stride_prev, lane, LANES, acc);
+    if (LANES > 1) {
+      // the LANES consecutive lanes of a group hold one point; xor offsets below LANES stay
+      // inside the group (LANES divides 32 and every lane of the warp takes part)
 #pragma unroll
       for (int c = 0; c < M::NCO; ++c)
 #pragma unroll
         for (int f = 0; f < 2; ++f)
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
+          for (int o = LANES / 2; o > 0; o >>= 1) {
             if constexpr (std::is_same<R, dword>::value) {
               dw_norm(acc[c][f]);
               acc[c][f] = dw_add(acc[c][f], dw_shfl_xor(acc[c][f], o));
@@ -392,14 +395,14 @@ __global__ void __launch_bounds__(kThreads) k_stage(const int32_t* __restrict__ 
   }
 }
 
-template <int K, int A, typename R, typename OUT, bool SPLIT>
+template <int K, int A, typename R, typename OUT, int LANES>
 cudaError_t launch_kk(lsp_ctx* c, const int32_t* list, const int32_t* count, int64_t cap,
                       const R* X, const R* Tprev, int64_t lo_prev, int64_t stride_prev, OUT* Tout,
                       int64_t lo_out, int64_t stride_out, bool by_index, double scale) {
   const int P = c->geo.P;
   const size_t smem = sizeof(R) * A * P;
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_stage<K, A, R, OUT, SPLIT>,
+    cudaError_t e = cudaFuncSetAttribute(k_stage<K, A, R, OUT, LANES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
@@ -407,31 +410,35 @@ cudaError_t launch_kk(lsp_ctx* c, const int32_t* list, const int32_t* count, int
   // (the per-point order of the sums does not depend on it, so the results do not either)
   const std::string key = std::string("stage") + std::to_string(K) + "/A" + std::to_string(A) +
                           "/" + (sizeof(R) == 4 ? "f32" : (std::is_same<R, dword>::value ? "dw" : "f64")) +
-                          (SPLIT ? "/split" : "") + "/w" + work_bucket(cap);
+                          "/lanes" + std::to_string(LANES) + "/w" + work_bucket(cap);
   return tuned_launch(c, key, {kThreads, 16}, kThreads, 0, [&](LaunchShape sh) {
-    const int64_t per_block = SPLIT ? sh.threads / 32 : sh.threads;
+    const int64_t per_block = sh.threads / LANES;
     int64_t b = (cap + per_block - 1) / per_block;
     if (b < 1) b = 1;
     if (b > 152 * (int64_t)sh.per_sm) b = 152 * (int64_t)sh.per_sm;
-    k_stage<K, A, R, OUT, SPLIT><<<(int)b, sh.threads, smem, c->stream>>>(
+    k_stage<K, A, R, OUT, LANES><<<(int)b, sh.threads, smem, c->stream>>>(
         list, count, P, X, Tprev, lo_prev, stride_prev, Tout, lo_out, stride_out,
         by_index ? 1 : 0, scale, (int32_t*)c->counts.p + kErrWord);
     return cudaGetLastError();
   });
 }
 
-// Domains below about two threads per SM-lane slot are spread over warps instead.
-constexpr int64_t kSplitBelow = 152 * 256;
+// A domain below two threads per SM thread slot of the GPU (152 x 2048) shares each point
+// among lanes: a warp per point below 152 x 256 points, four lanes per point above.
+constexpr int64_t kWarpBelow = 152 * 256, kQuadBelow = 152 * 2048;
 
 template <int K, int A, typename R, typename OUT>
 cudaError_t launch_k(lsp_ctx* c, const int32_t* list, const int32_t* count, int64_t cap,
                      const R* X, const R* Tprev, int64_t lo_prev, int64_t stride_prev, OUT* Tout,
                      int64_t lo_out, int64_t stride_out, bool by_index, double scale) {
-  if (cap < kSplitBelow)
-    return launch_kk<K, A, R, OUT, true>(c, list, count, cap, X, Tprev, lo_prev, stride_prev,
-                                         Tout, lo_out, stride_out, by_index, scale);
-  return launch_kk<K, A, R, OUT, false>(c, list, count, cap, X, Tprev, lo_prev, stride_prev, Tout,
-                                        lo_out, stride_out, by_index, scale);
+  if (cap < kWarpBelow)
+    return launch_kk<K, A, R, OUT, 32>(c, list, count, cap, X, Tprev, lo_prev, stride_prev,
+                                       Tout, lo_out, stride_out, by_index, scale);
+  if (cap < kQuadBelow)
+    return launch_kk<K, A, R, OUT, 4>(c, list, count, cap, X, Tprev, lo_prev, stride_prev, Tout,
+                                      lo_out, stride_out, by_index, scale);
+  return launch_kk<K, A, R, OUT, 1>(c, list, count, cap, X, Tprev, lo_prev, stride_prev, Tout,
+                                    lo_out, stride_out, by_index, scale);
 }
 
 template <typename R>

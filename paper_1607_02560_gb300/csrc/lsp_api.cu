@@ -621,7 +621,8 @@ lsp_status lsp_create(int d, int n, void* cuda_stream, lsp_ctx** out) {
       st = LSP_ERR_OOM;
       break;
     }
-    if (cudaMemcpy(c->xtab.p, X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice) !=
+    if (cudaMemset(c->stats.p, 0, 8 * sizeof(double)) != cudaSuccess ||  // zero ticket
+        cudaMemcpy(c->xtab.p, X.data(), sizeof(double) * X.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(c->twiddle.p, tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice) !=
             cudaSuccess) {
@@ -696,8 +697,7 @@ lsp_status lsp_set_potential(lsp_ctx* c, const double* v, int v_on_device) {
   }
   int nb = (int)std::min<int64_t>(152 * 4, (N + 255) / 256);
   if (!ensure(c, c->stats_part, sizeof(double) * 4 * nb)) return LSP_ERR_OOM;
-  CUDA_OK(c, launch_stats_partial(c, nb, src));
-  CUDA_OK(c, launch_stats_final(c, nb));
+  CUDA_OK(c, launch_stats(c, nb, src));
   if (!c->h_stats_dev)
     CUDA_OK(c, cudaMemcpyAsync(c->h_stats, c->stats.p, 4 * sizeof(double),
                                cudaMemcpyDeviceToHost, c->stream));

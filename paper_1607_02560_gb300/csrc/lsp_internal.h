@@ -216,8 +216,9 @@ void timer_end(lsp_ctx* ctx, int slot);
 
 // ---- launchers; each returns cudaGetLastError() after the launch ----
 // src: c->v itself, or page-locked host memory (device address) that is copied into c->v
-cudaError_t launch_stats_partial(lsp_ctx* c, int nblocks, const double* src);
-cudaError_t launch_stats_final(lsp_ctx* c, int nblocks);
+// v_min, v_max, sum and the count of non-finite values of v in stats[0..3] (one launch; the
+// ticket of its last block lives in stats[4] and is zero between calls).
+cudaError_t launch_stats(lsp_ctx* c, int nblocks, const double* src);
 // bytes / 4 words of p set to zero (bytes a multiple of 4, p 4-byte aligned)
 cudaError_t launch_zero(lsp_ctx* c, void* p, size_t bytes);
 // n doubles from src to dst (device, 16-byte aligned)
