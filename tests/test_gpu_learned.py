@@ -77,37 +77,39 @@ def bf16(a):
         torch.float64).numpy()
 
 
-def stored_precision_backward(x, t, W, b, nout):
+def stored_precision_backward(x, t, W, b, nout, y_gpu=None):
     """The gradients of the network's loss in FP64, with values rounded to bf16 where the
     network stores them (the hidden activations h_l, and the output and hidden gradients dY,
     dZ_l when they enter a product), built from the oracle's definitions (hard-swish and its
-    derivative). Returns (dW, db, S, K): S_l = |dZ_l|^T |a_{l-1}| is each weight gradient's sum
-    of absolute terms, the scale of its FP32 accumulation and of one-unit bf16 differences;
-    K_l bounds what the derivative's jumps can change: hard-swish' jumps by 1/2 at z = -3 and
-    z = 3, and where z lies within the FP32 accumulation error of a jump the two sides may take
-    different branches, changing that term by half its size."""
+    derivative). Returns (dW, db, S, K):
+    - S_l = |dZ_l|^T |a_{l-1}|, each weight gradient's sum of absolute terms: the scale of its
+      FP32 accumulation and of one-unit bf16 differences;
+    - K_l, the absolute terms of the samples whose outputs y_gpu (the GPU's own forward)
+      already differ from this computation beyond FP32 accumulation: for them a stored bf16
+      activation rounded the other way on the GPU (a value next to a rounding boundary), so
+      every term of theirs may differ; doubled, as a bound on both sides."""
     L = len(W)
-    a, zs, acts, near = x, [], [x], []
+    a, zs, acts = x, [], [x]
     for li in range(L):
         z = a @ W[li].T + b[li]
         zs.append(z)
-        err = 2e-4 * (np.abs(a) @ np.abs(W[li]).T + np.abs(b[li]))  # FP32 sums, generously
-        near.append(np.abs(np.abs(z) - 3.0) <= err)
         a = bf16(MO.hswish(z)) if li < L - 1 else z
         acts.append(a)
+    flag = np.zeros(a.shape[0], dtype=bool)
+    if y_gpu is not None:
+        flag = np.abs(y_gpu - a).max(axis=1) > 1e-5 * np.abs(a).max()
     g = np.zeros_like(a)
     g[:, :nout] = 2.0 * (a - t)[:, :nout] / (a.shape[0] * nout)
     dW, db, S, K = [None] * L, [None] * L, [None] * L, [None] * L
     for li in range(L - 1, -1, -1):
         dz = g if li == L - 1 else g * MO.hswish_grad(zs[li])
-        jump = np.zeros_like(g) if li == L - 1 else 0.5 * np.abs(g) * near[li]
         dz16 = bf16(dz)
         dW[li] = dz16.T @ acts[li]
         db[li] = dz.sum(axis=0)
         S[li] = np.abs(dz16).T @ np.abs(acts[li])
-        K[li] = jump.T @ np.abs(acts[li])
+        K[li] = 2.0 * (np.abs(dz16) * flag[:, None]).T @ np.abs(acts[li])
         g = dz16 @ W[li]
-    return dW, db, S, K, zs
+    return dW, db, S, K, flag
 
 
 @pytest.mark.parametrize("d", [2, 3])
@@ -141,7 +143,7 @@ def test_forward_and_gradients_match_oracle(stream, d):
     assert abs(loss - loss_ref) <= 3e-2 * loss_ref
     # entry by entry against the stored-precision computation: FP32 accumulation order and
     # an occasional one-unit bf16 difference of a stored value separate the two
-    dWs, dbs, S, KJ, ZS = stored_precision_backward(x, tp, W, b, nout)
+    dWs, dbs, S, KJ, flagged = stored_precision_backward(x, tp, W, b, nout, y_gpu=y)
     off = 0
     worst = []
     for layer, (n, k) in enumerate([(256, K0), (256, 256), (256, 256), (OUTP, 256)]):
@@ -159,7 +161,8 @@ def test_forward_and_gradients_match_oracle(stream, d):
         rb = dbs[layer]
         if layer == 3:
             gb, rb = gb[:nout], rb[:nout]
-        eb = float((np.abs(gb - rb) / (2e-3 * np.abs(rb).max() + 1e-2 * np.abs(rb))).max())
+        eb = float((np.abs(gb - rb) / (2e-3 * np.abs(rb).max() + 1e-2 * np.abs(rb)
+                                       + 2.0 * np.abs(rb).max() * flagged.mean())).max())
         worst.append((round(ew, 3), round(eb, 3)))
         if ew > 1.0:  # where the worst entries sit, for the failure report
             r = np.abs(g - ref) / (8e-3 * sc + 1e-2 * np.abs(ref) + kj + 1e-30)
@@ -168,14 +171,12 @@ def test_forward_and_gradients_match_oracle(stream, d):
                   [(int(i // r.shape[1]), int(i % r.shape[1]), float(g.ravel()[i]),
                     float(ref.ravel()[i]), float(sc.ravel()[i])) for i in top],
                   "columns above tolerance:", sorted(set((np.nonzero(r > 1)[1]).tolist()))[:20])
-            j = int(top[-1] // r.shape[1])
-            zj = ZS[layer][:, j]
-            print(f"unit {j}: distance of z to the kinks (min over samples) "
-                  f"{float(np.min(np.abs(np.abs(zj) - 3.0))):.3g}, |z| range "
-                  f"[{float(np.abs(zj).min()):.3g}, {float(np.abs(zj).max()):.3g}]")
+            print("samples whose outputs differ:", np.nonzero(flagged)[0])
         assert ew <= 1.0 and eb <= 1.0, (layer, ew, eb)
         off += n
-    print(f"d={d}: largest entrywise gradient error / tolerance per layer (W, b): {worst}")
+    print(f"d={d}: largest entrywise gradient error / tolerance per layer (W, b): {worst}; "
+          f"{int(flagged.sum())} of {B} samples' outputs differ beyond FP32 accumulation")
+    assert flagged.sum() <= B // 16  # a few boundary cases, not a systematic difference
 
 
 @pytest.mark.parametrize("n", [64, 256, 1024])
