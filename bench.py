@@ -62,7 +62,11 @@ FP64_FLOP_PER_SM_CLK, FP32_FLOP_PER_SM_CLK = 4, 256
 # DRAM bytes (read + write) per launch from ncu captures (dram__bytes_read.sum +
 # dram__bytes_write.sum), keyed by (kernel, workload, mode); null where no capture of the
 # current kernel exists. The profile named beside each figure holds the command.
-TRAFFIC = {}
+TRAFFIC = {
+    # profiles/stencil_build_fp64_helm2d_n1024.md: k_stage<1, 3, double, double, 1>, four
+    # launches at 2D n = 1024 (per-point shifts): 11.1-11.3 MB read, 0 written
+    ("stage1", "helm2d_n1024", "fp64"): 11.2e6,
+}
 
 
 def dist_info():
