@@ -62,16 +62,20 @@ __device__ __forceinline__ int64_t neighbour(int64_t j, int o, int logn, int64_t
   }
 }
 
+// P[j, o] = alpha[o] + c[o] (v[j + o] - s) is formed as fma(c[o], v[j + o], ap[o]) from the
+// per-shift table ap = alpha - c s (k_affine): one FP64 operation per element instead of two,
+// which halves the FP64-pipe work of this kernel (the FP64 pipe, not HBM, held it back). c s
+// is of the order of alpha here, so the two roundings cost a few ulp of P.
 template <int D, bool LOCAL, bool ROWS, bool SIDX>
 __global__ void __launch_bounds__(kThreads) k_rows(
     const double* __restrict__ v, int64_t N, int logn, const int32_t* __restrict__ idx_of,
     int64_t mlo, int64_t R, int32_t* __restrict__ err, const int32_t* __restrict__ shift_m,
     const int32_t* __restrict__ count,
-    const double* __restrict__ alpha, const double* __restrict__ cst, double* __restrict__ Q,
+    const double* __restrict__ alpha, const double* __restrict__ cst,
+    const double* __restrict__ ap, double* __restrict__ Q,
     double* __restrict__ C, double* __restrict__ P, int32_t* __restrict__ sidx_out) {
   constexpr int MU = D == 1 ? 3 : (D == 2 ? 9 : 27);
   __shared__ int s_idx[kThreads];
-  __shared__ double s_val[kThreads];
   const int64_t mask = ((int64_t)1 << logn) - 1;
   const int ns = *count;
   for (int64_t j0 = (int64_t)blockIdx.x * kThreads; j0 < N; j0 += (int64_t)gridDim.x * kThreads) {
@@ -91,7 +95,6 @@ __global__ void __launch_bounds__(kThreads) k_rows(
         idx = nearest_shift(shift_m, ns, x);
       idx = (int)checked(idx, ns, err);
       s_idx[t] = idx;
-      s_val[t] = shift_of(__ldg(shift_m + idx));
       if (SIDX) sidx_out[j0 + t] = idx;
     }
     __syncthreads();
@@ -102,10 +105,11 @@ __global__ void __launch_bounds__(kThreads) k_rows(
         const int idx = s_idx[p];
         const double a = __ldg(alpha + (int64_t)idx * MU + o);
         const double cc = __ldg(cst + (int64_t)idx * MU + o);
+        const double aff = __ldg(ap + (int64_t)idx * MU + o);
         const double vn = __ldg(v + checked(neighbour<D>(j0 + p, o, logn, mask), N, err));
         __stcs(Q + obase + e, a);
         __stcs(C + obase + e, cc);
-        __stcs(P + obase + e, fma(cc, vn - s_val[p], a));
+        __stcs(P + obase + e, fma(cc, vn, aff));
       }
     }
     __syncthreads();
@@ -315,9 +319,9 @@ __global__ void __launch_bounds__(kThreads) k_learned_gate(
     int64_t mlo, int64_t R, const int32_t* __restrict__ shift_m,
     const int32_t* __restrict__ count, int64_t cap, const double* __restrict__ gvals,
     const double* __restrict__ alpha, const double* __restrict__ cst,
-    const double* __restrict__ lam, double tau2, double* __restrict__ Q, double* __restrict__ C,
-    double* __restrict__ P, float* __restrict__ rho, int32_t* __restrict__ nfall,
-    int32_t* __restrict__ err) {
+    const double* __restrict__ ap, const double* __restrict__ lam, double tau2,
+    double* __restrict__ Q, double* __restrict__ C, double* __restrict__ P,
+    float* __restrict__ rho, int32_t* __restrict__ nfall, int32_t* __restrict__ err) {
   constexpr int MU = D == 1 ? 3 : (D == 2 ? 9 : 27);
   constexpr int NC = D == 1 ? 3 : (D == 2 ? 6 : 10);
   const int64_t mask = ((int64_t)1 << logn) - 1;
@@ -394,18 +398,34 @@ __global__ void __launch_bounds__(kThreads) k_learned_gate(
         P[j * MU + b] = fma(cb, vn - s, al[b]);
       }
     } else {
+      // the eigen path's rows, formed exactly as k_rows forms them
       atomicAdd(nfall, 1);
-      const double s = shift_of(__ldg(shift_m + idx));
 #pragma unroll 1
       for (int a = 0; a < MU; ++a) {
         const double aa = __ldg(alpha + (int64_t)idx * MU + a);
         const double cc = __ldg(cst + (int64_t)idx * MU + a);
+        const double aff = __ldg(ap + (int64_t)idx * MU + a);
         const double vn = __ldg(v + neighbour<D>(j, a, logn, mask));
         Q[j * MU + a] = aa;
         C[j * MU + a] = cc;
-        P[j * MU + a] = fma(cc, vn - s, aa);
+        P[j * MU + a] = fma(cc, vn, aff);
       }
     }
+  }
+}
+
+// ap[i * MU + o] = alpha - c s_i for every shift i of the list (t = 1 tables), with s_i the
+// shift value as the rows use it.
+__global__ void __launch_bounds__(kThreads) k_affine(const int32_t* __restrict__ shift_m,
+                                                     const int32_t* __restrict__ count, int mu,
+                                                     const double* __restrict__ alpha,
+                                                     const double* __restrict__ cst,
+                                                     double* __restrict__ ap) {
+  const int64_t total = (int64_t)*count * mu;
+  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * kThreads) {
+    const double s = shift_of(__ldg(shift_m + e / mu));
+    ap[e] = fma(-__ldg(cst + e), s, __ldg(alpha + e));
   }
 }
 
@@ -424,8 +444,8 @@ void launch_rows_t(lsp_ctx* c, const int32_t* count) {
     k_rows<D, LOCAL, ROWS, SIDX><<<(int)b, kThreads, 0, c->stream>>>(
         (const double*)c->v.p, N, log2i(c->geo.n), (const int32_t*)c->idx_of.p, c->mrange.lo,
         c->mrange.size(), (int32_t*)c->counts.p + kErrWord, (const int32_t*)c->shift_m.p,
-        count, (const double*)c->alpha.p, (const double*)c->cst.p, (double*)c->Q.p,
-        (double*)c->C.p, (double*)c->P.p, (int32_t*)c->sidx.p);
+        count, (const double*)c->alpha.p, (const double*)c->cst.p, (const double*)c->ap.p,
+        (double*)c->Q.p, (double*)c->C.p, (double*)c->P.p, (int32_t*)c->sidx.p);
     return cudaGetLastError();
   };
   if (!ROWS) {  // the shift-index export is not tuned
@@ -461,6 +481,19 @@ void dispatch_rows(lsp_ctx* c, int policy, const int32_t* count) {
 
 }  // namespace
 
+cudaError_t launch_affine(lsp_ctx* c, const int32_t* count, int64_t cap) {
+  const int64_t work = cap * c->geo.mu;
+  int64_t b = (work + kThreads - 1) / kThreads;
+  if (b > 152 * 8) b = 152 * 8;
+  if (b < 1) b = 1;
+  int t = timer_begin(c, "affine");
+  k_affine<<<(int)b, kThreads, 0, c->stream>>>((const int32_t*)c->shift_m.p, count, c->geo.mu,
+                                                (const double*)c->alpha.p,
+                                                (const double*)c->cst.p, (double*)c->ap.p);
+  timer_end(c, t);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count) {
   int t = timer_begin(c, "rows");
   dispatch_rows<true, false>(c, policy, count);
@@ -478,7 +511,8 @@ cudaError_t launch_learned_gate(lsp_ctx* c, int policy, const int32_t* count, in
     kern<<<(int)b, kThreads, 0, c->stream>>>(
         (const double*)c->v.p, N, log2i(c->geo.n), (const int32_t*)c->idx_of.p, c->mrange.lo,
         c->mrange.size(), (const int32_t*)c->shift_m.p, count, cap, (const double*)c->gvals.p,
-        (const double*)c->alpha.p, (const double*)c->cst.p, (const double*)c->lam.p, tau * tau,
+        (const double*)c->alpha.p, (const double*)c->cst.p, (const double*)c->ap.p,
+        (const double*)c->lam.p, tau * tau,
         (double*)c->Q.p, (double*)c->C.p, (double*)c->P.p, rho, nfall,
         (int32_t*)c->counts.p + kErrWord);
   };

@@ -481,8 +481,10 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
     }
   }
   // t = 1 stencils read the first classes of a t = 2 table (same row stride cap_s)
-  if (o.t == 1 || o.nd_leaf > 0)
+  if (o.t == 1 || o.nd_leaf > 0) {
     CUDA_OK(c, launch_eig(c, counts + 0, cap_s, o.eig_method, o.refine_steps, fp32));
+    if (o.t == 1) CUDA_OK(c, launch_affine(c, counts + 0, cap_s));
+  }
   if (o.t == 2) {
     if (d == 2)
       CUDA_OK(c, launch_eig_t2(c, counts + 0, cap_s));
@@ -651,7 +653,7 @@ lsp_status lsp_destroy(lsp_ctx* c) {
     if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
   }
   DevBuf* bufs[] = {&c->v, &c->stats_part, &c->stats, &c->xtab, &c->xtab32, &c->xtabdw, &c->shift_m, &c->shift_flag,
-                    &c->idx_of, &c->counts, &c->wtab, &c->gvals, &c->alpha, &c->cst, &c->lam,
+                    &c->idx_of, &c->counts, &c->wtab, &c->gvals, &c->alpha, &c->cst, &c->ap, &c->lam,
                     &c->sflags, &c->Q, &c->C, &c->P, &c->sidx, &c->colidx, &c->rowptr,
                     &c->fftbuf, &c->twiddle, &c->learn_in, &c->alpha2, &c->cst2, &c->lam2,
                     &c->sflags2, &c->expvals};
@@ -858,6 +860,7 @@ lsp_status lsp_build_stencils(lsp_ctx* c, const lsp_stencil_opts* opts) {
             ensure(c, c->gvals, sizeof(double) * 2 * G.ncls * cap_s) &&
             (!need_t1 || (ensure(c, c->alpha, sizeof(double) * c->geo.mu * cap_s) &&
                           ensure(c, c->cst, sizeof(double) * c->geo.mu * cap_s) &&
+                          ensure(c, c->ap, sizeof(double) * c->geo.mu * cap_s) &&
                           ensure(c, c->lam, sizeof(double) * 2 * cap_s) &&
                           ensure(c, c->sflags, sizeof(int32_t) * cap_s))) &&
             (o.t != 2 || (ensure(c, c->alpha2, sizeof(double) * mu * cap_s) &&

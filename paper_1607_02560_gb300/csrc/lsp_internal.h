@@ -159,6 +159,7 @@ struct lsp_ctx {
 
   // per-shift results (a3-a6); *2: the t = 2 stencils
   lsp::DevBuf gvals, alpha, cst, lam, sflags, alpha2, cst2, lam2, sflags2;
+  lsp::DevBuf ap;  // alpha - c s per shift and offset (t = 1): the P rows are fma(c, v, ap)
   // launch-shape autotuner (lsp_set_autotune): the first build of a configuration times
   // candidate shapes of the stage, eigen and row kernels eagerly; the winners are kept here
   bool autotune = false, tuning = false;
@@ -242,6 +243,7 @@ cudaError_t launch_export_t2(lsp_ctx* c, const double* rows, int leaf, const int
 cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int eig_method,
                        int refine_steps, bool fp32_gram);
 cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count);
+cudaError_t launch_affine(lsp_ctx* c, const int32_t* count, int64_t cap);
 cudaError_t launch_sidx(lsp_ctx* c, int policy, const int32_t* count);
 // Launch through the autotuner: the tuned shape of `key` if there is one; during a tuning pass
 // (ctx->tuning) each candidate shape is timed (side-effect-free kernels only: the launch must
