@@ -661,7 +661,7 @@ def time_config(torch, workload: str, policy: str, mode: str, steps: int, warmup
     return out
 
 
-GATE_TAU = 1.1  # residual ratio above which a learned stencil takes the eigen path's rows
+GATE_TAU = 1.003  # residual ratio above which a learned stencil takes the eigen path's rows
 
 
 def learned_quality(torch, ctx, v, v_dev, policy: str, flush, stream, gmres: bool = True) -> dict:

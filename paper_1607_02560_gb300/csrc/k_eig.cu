@@ -377,7 +377,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
                                                     double* __restrict__ alpha_out,
                                                     double* __restrict__ c_out,
                                                     double* __restrict__ lam_out,
-                                                    int32_t* __restrict__ flags_out) {
+                                                    int32_t* __restrict__ flags_out,
+                                                    const int32_t* __restrict__ shift_m,
+                                                    double* __restrict__ ap_out) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   BlockTables<MU>& tb = *reinterpret_cast<BlockTables<MU>*>(smraw);
@@ -510,6 +512,8 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig(const double* __restrict__ g
       for (int a = 0; a < MU; ++a) s = fma(sm.g[2 * tb.cls[a][lane]], sm.alpha[a], s);
       alpha_out[i * MU + lane] = sm.alpha[lane];
       c_out[i * MU + lane] = s;
+      // P rows are fma(c, v, alpha - c s_i) (see k_rows)
+      ap_out[i * MU + lane] = fma(-s, lattice_shift(__ldg(shift_m + i)), sm.alpha[lane]);
     }
     if (lane == 0) {
       lam_out[2 * i + 0] = lam1;
@@ -589,7 +593,9 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig3d(const double* __restrict__
                                                       double* __restrict__ alpha_out,
                                                       double* __restrict__ c_out,
                                                       double* __restrict__ lam_out,
-                                                      int32_t* __restrict__ flags_out) {
+                                                      int32_t* __restrict__ flags_out,
+                                                      const int32_t* __restrict__ shift_m,
+                                                      double* __restrict__ ap_out) {
   constexpr int MU = 27, NCLS = 10, NENT = 24, CENTRE = 13;
   __shared__ double s_coef[NENT][NCLS];
   __shared__ double s_u[kMaxSymVec][MU];
@@ -840,6 +846,7 @@ __global__ void __launch_bounds__(WARPS * 32) k_eig3d(const double* __restrict__
     if (lane < MU) {
       alpha_out[i * MU + lane] = av;
       c_out[i * MU + lane] = cv;
+      ap_out[i * MU + lane] = fma(-cv, lattice_shift(__ldg(shift_m + i)), av);
     }
     if (lane == 0) {
       lam_out[2 * i + 0] = lam1;
@@ -1340,7 +1347,9 @@ __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals,
                                                double* __restrict__ alpha_out,
                                                double* __restrict__ c_out,
                                                double* __restrict__ lam_out,
-                                               int32_t* __restrict__ flags_out) {
+                                               int32_t* __restrict__ flags_out,
+                                               const int32_t* __restrict__ shift_m,
+                                               double* __restrict__ ap_out) {
   const int64_t cnt = *count;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -1510,10 +1519,13 @@ __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals,
         if (ref == 0.0 && fabs(al[a]) > 1e-12) ref = al[a];
     }
     const double sg = ref < 0 ? -1.0 : 1.0;
+    const double si = lattice_shift(__ldg(shift_m + i));
 #pragma unroll
     for (int a = 0; a < 9; ++a) {
-      alpha_out[i * 9 + a] = sg * al[a];
-      c_out[i * 9 + a] = sg * cv[a];
+      const double aa = sg * al[a], ca = sg * cv[a];
+      alpha_out[i * 9 + a] = aa;
+      c_out[i * 9 + a] = ca;
+      ap_out[i * 9 + a] = fma(-ca, si, aa);  // P rows are fma(c, v, alpha - c s_i)
     }
     lam_out[2 * i + 0] = best;
     lam_out[2 * i + 1] = lam2;
@@ -1535,7 +1547,8 @@ cudaError_t launch_eig_t(lsp_ctx* c, const int32_t* count, int64_t cap, int meth
   if (b < 1) b = 1;
   k_eig<MU, NCLS, WARPS><<<(int)b, WARPS * 32, smem, c->stream>>>(
       (const double*)c->gvals.p, cap, count, method, refine, (double*)c->alpha.p,
-      (double*)c->cst.p, (double*)c->lam.p, (int32_t*)c->sflags.p);
+      (double*)c->cst.p, (double*)c->lam.p, (int32_t*)c->sflags.p,
+      (const int32_t*)c->shift_m.p, (double*)c->ap.p);
   return cudaGetLastError();
 }
 
@@ -1663,11 +1676,13 @@ cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int method
       if (fp32_gram)
         k_eig2d<float><<<(int)b, sh.threads, 0, c->stream>>>(
             (const double*)c->gvals.p, cap, count, (double*)c->alpha.p, (double*)c->cst.p,
-            (double*)c->lam.p, (int32_t*)c->sflags.p);
+            (double*)c->lam.p, (int32_t*)c->sflags.p, (const int32_t*)c->shift_m.p,
+            (double*)c->ap.p);
       else
         k_eig2d<double><<<(int)b, sh.threads, 0, c->stream>>>(
             (const double*)c->gvals.p, cap, count, (double*)c->alpha.p, (double*)c->cst.p,
-            (double*)c->lam.p, (int32_t*)c->sflags.p);
+            (double*)c->lam.p, (int32_t*)c->sflags.p, (const int32_t*)c->shift_m.p,
+            (double*)c->ap.p);
       return cudaGetLastError();
     });
   } else if (c->geo.d == 3 && method == LSP_EIG_SYMMETRIC && refine == 0) {
@@ -1677,7 +1692,9 @@ cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int method
     if (b < 1) b = 1;
     k_eig3d<kW><<<(int)b, kW * 32, 0, c->stream>>>((const double*)c->gvals.p, cap, count,
                                                    (double*)c->alpha.p, (double*)c->cst.p,
-                                                   (double*)c->lam.p, (int32_t*)c->sflags.p);
+                                                   (double*)c->lam.p, (int32_t*)c->sflags.p,
+                                                   (const int32_t*)c->shift_m.p,
+                                                   (double*)c->ap.p);
     e = cudaGetLastError();
   } else {
     e = c->geo.d == 1   ? launch_eig_t<3, 3, 8>(c, count, cap, method, refine)

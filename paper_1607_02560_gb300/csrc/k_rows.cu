@@ -23,9 +23,7 @@ __device__ __forceinline__ int64_t snap_m(double x) {
   const double y = __dmul_rn(__dsub_rn(__ddiv_rn(x, kPi2), 2.0), 0.25);
   return (int64_t)round(y);
 }
-__device__ __forceinline__ double shift_of(int64_t m) {
-  return __dmul_rn((double)(4 * m + 2), kPi2);
-}
+__device__ __forceinline__ double shift_of(int64_t m) { return lattice_shift(m); }
 
 // Index in the sorted list S (given by lattice indices) of the shift nearest to x; ties go to
 // the smaller shift. |s - x| is monotone on each side of x, so only the two shifts around the
@@ -63,7 +61,8 @@ __device__ __forceinline__ int64_t neighbour(int64_t j, int o, int logn, int64_t
 }
 
 // P[j, o] = alpha[o] + c[o] (v[j + o] - s) is formed as fma(c[o], v[j + o], ap[o]) from the
-// per-shift table ap = alpha - c s (k_affine): one FP64 operation per element instead of two,
+// per-shift table ap = alpha - c s (written by the eigen kernels with alpha and c): one FP64
+// operation per element instead of two,
 // which halves the FP64-pipe work of this kernel (the FP64 pipe, not HBM, held it back). c s
 // is of the order of alpha here, so the two roundings cost a few ulp of P.
 template <int D, bool LOCAL, bool ROWS, bool SIDX>
@@ -414,21 +413,6 @@ __global__ void __launch_bounds__(kThreads) k_learned_gate(
   }
 }
 
-// ap[i * MU + o] = alpha - c s_i for every shift i of the list (t = 1 tables), with s_i the
-// shift value as the rows use it.
-__global__ void __launch_bounds__(kThreads) k_affine(const int32_t* __restrict__ shift_m,
-                                                     const int32_t* __restrict__ count, int mu,
-                                                     const double* __restrict__ alpha,
-                                                     const double* __restrict__ cst,
-                                                     double* __restrict__ ap) {
-  const int64_t total = (int64_t)*count * mu;
-  for (int64_t e = (int64_t)blockIdx.x * kThreads + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * kThreads) {
-    const double s = shift_of(__ldg(shift_m + e / mu));
-    ap[e] = fma(-__ldg(cst + e), s, __ldg(alpha + e));
-  }
-}
-
 int log2i(int n) {
   int l = 0;
   while ((1 << l) < n) ++l;
@@ -480,19 +464,6 @@ void dispatch_rows(lsp_ctx* c, int policy, const int32_t* count) {
 }
 
 }  // namespace
-
-cudaError_t launch_affine(lsp_ctx* c, const int32_t* count, int64_t cap) {
-  const int64_t work = cap * c->geo.mu;
-  int64_t b = (work + kThreads - 1) / kThreads;
-  if (b > 152 * 8) b = 152 * 8;
-  if (b < 1) b = 1;
-  int t = timer_begin(c, "affine");
-  k_affine<<<(int)b, kThreads, 0, c->stream>>>((const int32_t*)c->shift_m.p, count, c->geo.mu,
-                                                (const double*)c->alpha.p,
-                                                (const double*)c->cst.p, (double*)c->ap.p);
-  timer_end(c, t);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count) {
   int t = timer_begin(c, "rows");

@@ -481,10 +481,9 @@ lsp_status issue_build(lsp_ctx* c, const lsp_stencil_opts& o, int64_t cap_s, boo
     }
   }
   // t = 1 stencils read the first classes of a t = 2 table (same row stride cap_s)
-  if (o.t == 1 || o.nd_leaf > 0) {
+  // the eigen kernels also write ap = alpha - c s per shift for the P rows
+  if (o.t == 1 || o.nd_leaf > 0)
     CUDA_OK(c, launch_eig(c, counts + 0, cap_s, o.eig_method, o.refine_steps, fp32));
-    if (o.t == 1) CUDA_OK(c, launch_affine(c, counts + 0, cap_s));
-  }
   if (o.t == 2) {
     if (d == 2)
       CUDA_OK(c, launch_eig_t2(c, counts + 0, cap_s));

@@ -41,6 +41,11 @@ constexpr int kGateWord = 14;  // points the learned-stencil gate sent back to t
 constexpr int kErrBounds = 1 << 10;
 
 #ifdef __CUDACC__
+// The lattice shift s = (4m + 2) pi^2 (Sec. 4.1), evaluated identically wherever a kernel needs
+// it (round-to-nearest product, no contraction).
+__device__ __forceinline__ double lattice_shift(int64_t m) {
+  return __dmul_rn((double)(4 * m + 2), kPi2);
+}
 // Checked builds (-DLSP_CHECKS): an index outside [0, n) is recorded in the error word and
 // replaced by 0, so the access stays inside the array; plain builds compile this away.
 __device__ __forceinline__ int64_t checked(int64_t i, int64_t n, int32_t* err) {
@@ -243,7 +248,6 @@ cudaError_t launch_export_t2(lsp_ctx* c, const double* rows, int leaf, const int
 cudaError_t launch_eig(lsp_ctx* c, const int32_t* count, int64_t cap, int eig_method,
                        int refine_steps, bool fp32_gram);
 cudaError_t launch_rows(lsp_ctx* c, int policy, const int32_t* count);
-cudaError_t launch_affine(lsp_ctx* c, const int32_t* count, int64_t cap);
 cudaError_t launch_sidx(lsp_ctx* c, int policy, const int32_t* count);
 // Launch through the autotuner: the tuned shape of `key` if there is one; during a tuning pass
 // (ctx->tuning) each candidate shape is timed (side-effect-free kernels only: the launch must
