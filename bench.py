@@ -336,6 +336,8 @@ def run_ours(args):
         for dd in ((d,) if args.mode == "learned" and args.no_forms else (2, 3)):
             mlps[dd], train_info[dd] = train_for(torch, dd, args.learned_steps, stream)
     if args.mode == "learned":
+        if args.mlp_schedule is not None:
+            mlps[d].set_schedule(args.mlp_schedule)
         ctx.set_mlp(mlps[d])
 
     def step():
@@ -1039,6 +1041,8 @@ def main():
     ap.add_argument("--mode", default="fp64", choices=["fp64", "dword", "mixed", "learned"])
     ap.add_argument("--learned-steps", type=int, default=3000,
                     help="training steps of the surrogate (learned mode and forms)")
+    ap.add_argument("--mlp-schedule", type=int, default=None, choices=[0, 1],
+                    help="2D network kernel: 1 = two tiles in flight (default), 0 = one tile")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP64 / mixed / learned summaries at 2D n=1024 and 3D n=64")
     ap.add_argument("--detail", default="",

@@ -231,8 +231,8 @@ lsp_status lsp_kernel_times(lsp_ctx* ctx, int cap, char (*names)[32], double* ms
  * A multilayer perceptron maps the 5^d patch of h^2 v around a point and the point's snapped
  * shift h^2 s_j (normalised) to that point's (alpha, c); it is trained on the stencils the
  * eigen path (Sec. 4.1-4.2) produces.
- * Layers: (5^d+1 -> 256), (256 -> 256), (256 -> 256) with hard-swish z clamp(z+3,0,6)/6, then
- * (256 -> 2|mu|); bf16 weights,
+ * Layers: (5^d+1 -> 256), (256 -> 256), (256 -> 256) with ReLU max(z, 0), then (256 -> 2|mu|);
+ * bf16 weights and hidden activations,
  * fp32 accumulation on the tensor cores, fp32 master weights and Adam. In a LEARNED build the
  * rows are Q = alpha / |alpha|, C = c / |alpha|, P = Q + C .* (v[mu_j] - s_j), s_j = snap(v_j).
  */

@@ -5,7 +5,7 @@ imports it. The paper has no learned component: this network is a surrogate trai
 paper's own stencils (Sec. 4.1, 4.2), so its oracle is the textbook definition of a
 multilayer perceptron, written out in numpy:
 
-    z_l = a_{l-1} W_l^T + b_l,   a_l = hswish(z_l) = z_l * clamp(z_l + 3, 0, 6) / 6   (hidden),
+    z_l = a_{l-1} W_l^T + b_l,   a_l = relu(z_l) = max(z_l, 0)   (hidden),
     y   = a_{L-1} W_L^T + b_L,   loss = mean over the batch and the outputs of (y - t)^2,
 
 with the gradients of that loss by the chain rule. Weights enter as float64 copies of the
@@ -22,19 +22,19 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["hswish", "hswish_grad", "mlp_forward", "mlp_backward", "patches",
+__all__ = ["relu", "relu_grad", "mlp_forward", "mlp_backward", "patches",
            "finite_difference"]
 
 
-def hswish(z):
-    """Hard-swish activation z * clamp(z + 3, 0, 6) / 6."""
-    return z * np.clip(z + 3.0, 0.0, 6.0) / 6.0
+def relu(z):
+    """The ReLU activation max(z, 0)."""
+    return np.maximum(z, 0.0)
 
 
-def hswish_grad(z):
-    """Its derivative: 0 below -3, (2z + 3) / 6 on [-3, 3], 1 above 3."""
+def relu_grad(z):
+    """Its derivative: 1 where z > 0, else 0 (0 at z = 0)."""
     z = np.asarray(z, dtype=np.float64)
-    return np.where(z < -3.0, 0.0, np.where(z > 3.0, 1.0, (2.0 * z + 3.0) / 6.0))
+    return (z > 0.0).astype(np.float64)
 
 
 def mlp_forward(x: np.ndarray, weights: list, biases: list):
@@ -45,7 +45,7 @@ def mlp_forward(x: np.ndarray, weights: list, biases: list):
     for li, (W, b) in enumerate(zip(weights, biases)):
         z = a @ np.asarray(W, np.float64).T + np.asarray(b, np.float64)
         zs.append(z)
-        a = hswish(z) if li < L - 1 else z
+        a = relu(z) if li < L - 1 else z
         acts.append(a)
     return a, (zs, acts)
 
@@ -59,7 +59,7 @@ def mlp_backward(x, t, weights, biases):
     L = len(weights)
     dWs, dbs = [None] * L, [None] * L
     for li in range(L - 1, -1, -1):
-        dz = g if li == L - 1 else g * hswish_grad(zs[li])
+        dz = g if li == L - 1 else g * relu_grad(zs[li])
         dWs[li] = dz.T @ acts[li]
         dbs[li] = dz.sum(axis=0)
         g = dz @ np.asarray(weights[li], np.float64)

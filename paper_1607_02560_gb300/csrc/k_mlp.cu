@@ -7,7 +7,7 @@
 //        (h^2 s_j - mu_x) / sigma_x with s_j = snap(v_j), zero-padded to K0. The stencil of the
 //        method depends on v_j only through the snapped shift s_j (a step function of v_j), so
 //        s_j is given to the network directly; the patch lets it use the neighbourhood too.
-//   z1 = x W1^T + b1, h1 = a(z1);  z2, h2;  z3, h3 (hidden width 256), a = hard-swish
+//   z1 = x W1^T + b1, h1 = a(z1);  z2, h2;  z3, h3 (hidden width 256), a = ReLU
 //   y  = h3 W4^T + b4;  (alpha, c) = y * sigma_y + mu_y;  alpha /= |alpha|, c scaled alike
 //   rows: Q = alpha, C = c, P = alpha + c .* (v[mu_j] - s_j), s_j = snap(v_j)   (Sec. 4.1)
 //
@@ -114,10 +114,8 @@ ChunkPlan plan_for(const Dims& m) {
   return p;
 }
 
-// Derivative of the hard-swish activation z * clamp(z + 3, 0, 6) / 6.
-__device__ __forceinline__ float act_grad(float z) {
-  return z < -3.0f ? 0.0f : (z > 3.0f ? 1.0f : (2.0f * z + 3.0f) * (1.0f / 6.0f));
-}
+// Derivative of the ReLU activation max(z, 0) (0 at z = 0).
+__device__ __forceinline__ float act_grad(float z) { return z > 0.0f ? 1.0f : 0.0f; }
 
 __device__ __forceinline__ int64_t snap_m(double x) {
   const double yf = fma(x, kQuarterInvPi2, -0.5);
@@ -199,11 +197,11 @@ struct FusedCfg {
     return l == 0 ? 0 : OFF(l - 1) + (int64_t)N(l - 1) * K(l - 1) * 2;
   }
   // normalisation block (mu_x sig_x mu_y[OUTP] sig_y[OUTP]) padded to 16 bytes, so that the
-  // b / 6 + 1/2 table behind it is read with 16-byte loads
+  // arrays behind it keep their 16-byte alignment
   static constexpr int NRM = (2 + 2 * OUTP + 3) & ~3;
   static constexpr size_t smem = (size_t)XBUF * XBYTES + kTile * kH * 2 +
                                  (size_t)NBUF * kChunkBytes +
-                                 sizeof(float) * (6 * kH + OUTP + NRM) + 64;
+                                 sizeof(float) * (3 * kH + OUTP + NRM) + 64;
 };
 
 // Fused forward over tiles of 128 rows, persistent (one CTA per SM, tiles strided by the grid).
@@ -228,34 +226,24 @@ struct FusedCfg {
 // (l + 1) % 2 for layer l - 1; epilogue l overwrites H only after the MMAs of layer l (the
 // readers of the previous H) completed. Every wait is bounded (1 s); a timed-out wait sets the
 // error word and makes every thread skip the remaining waits.
-// Two hard-swish outputs h = z * sat(acc / 6 + q), z = acc + b, with the packed FP32
-// instructions of sm_100-family GPUs (add/fma/mul .f32x2 round like their scalar forms; the
-// saturation has no packed form and is applied per lane).
-__device__ __forceinline__ void hswish_x2(uint32_t a0, uint32_t a1, float b0, float b1,
-                                          float q0, float q1, float& h0, float& h1, float& z0,
-                                          float& z1) {
-  uint32_t r0, r1, s0, s1;
-  asm("{\n\t.reg .b64 a, b, q, s, z, t, h;\n\t.reg .f32 t0, t1;\n\t"
-      "mov.b64 a, {%4, %5};\n\t"
-      "mov.b64 b, {%6, %7};\n\t"
-      "mov.b64 q, {%8, %9};\n\t"
-      "mov.b64 s, {%10, %10};\n\t"
+// Two columns of the hidden-layer epilogue: z = acc + b with one packed FP32 addition (it
+// rounds like the scalar one), then ReLU and the conversion to bf16 in one instruction,
+// packed as the next layer's operand wants it (column 2i in the low half). Returns the packed
+// pair; z0, z1 receive z (kept for the backward pass in batch mode).
+__device__ __forceinline__ uint32_t relu_bf16x2(uint32_t a0, uint32_t a1, float b0, float b1,
+                                                float& z0, float& z1) {
+  uint32_t h, r0, r1;
+  asm("{\n\t.reg .b64 a, b, z;\n\t"
+      "mov.b64 a, {%3, %4};\n\t"
+      "mov.b64 b, {%5, %6};\n\t"
       "add.rn.f32x2 z, a, b;\n\t"
-      "fma.rn.f32x2 t, a, s, q;\n\t"
-      "mov.b64 {t0, t1}, t;\n\t"
-      "cvt.sat.f32.f32 t0, t0;\n\t"
-      "cvt.sat.f32.f32 t1, t1;\n\t"
-      "mov.b64 t, {t0, t1};\n\t"
-      "mul.rn.f32x2 h, z, t;\n\t"
-      "mov.b64 {%0, %1}, h;\n\t"
-      "mov.b64 {%2, %3}, z;\n\t}"
-      : "=r"(r0), "=r"(r1), "=r"(s0), "=r"(s1)
-      : "r"(a0), "r"(a1), "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)),
-        "r"(__float_as_uint(q0)), "r"(__float_as_uint(q1)), "r"(__float_as_uint(1.0f / 6.0f)));
-  h0 = __uint_as_float(r0);
-  h1 = __uint_as_float(r1);
-  z0 = __uint_as_float(s0);
-  z1 = __uint_as_float(s1);
+      "mov.b64 {%1, %2}, z;\n\t"
+      "cvt.rn.relu.bf16x2.f32 %0, %2, %1;\n\t}"
+      : "=r"(h), "=r"(r0), "=r"(r1)
+      : "r"(a0), "r"(a1), "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)));
+  z0 = __uint_as_float(r0);
+  z1 = __uint_as_float(r1);
+  return h;
 }
 
 template <int D, int MODE>
@@ -268,7 +256,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
   uint8_t* Wb = Hs + kTile * kH * 2;                 // NBUF x 16 KiB
   float* bs = reinterpret_cast<float*>(Wb + NBUF * kChunkBytes);  // b1 b2 b3 (3 x 256) + b4
   float* nrm = bs + 3 * kH + OUTP;                   // mu_x sig_x mu_y[OUTP] sig_y[OUTP]
-  float* bq = nrm + Cfg::NRM;                        // b / 6 + 1/2 of layers 1-3 (3 x 256)
   __shared__ __align__(8) uint64_t bar_w[NBUF], bar_f[NBUF], bar_x[2], bar_xf[2], bar_acc[2],
       bar_h[kNPass], bar_done;
   __shared__ uint32_t tslot;
@@ -281,7 +268,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
     bs[i] = p.params[p.bias_off[0] + i];
     bs[kH + i] = p.params[p.bias_off[1] + i];
     bs[2 * kH + i] = p.params[p.bias_off[2] + i];
-    for (int l = 0; l < 3; ++l) bq[l * kH + i] = fmaf(bs[l * kH + i], 1.0f / 6.0f, 0.5f);
   }
   for (int i = tid; i < OUTP; i += kFusedThreads) bs[3 * kH + i] = p.params[p.bias_off[3] + i];
   for (int i = tid; i < 2 + 2 * OUTP; i += kFusedThreads) nrm[i] = p.params[p.norm_off + i];
@@ -461,7 +447,6 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
         tc::fence_after();
         const uint32_t taddr = tmem + lane_off + (uint32_t)(a * kH);
         const float* bl = bs + layer * kH;
-        const float* ql = bq + layer * kH;
         uint32_t r[2][32];
         tc::tmem_ld32_nowait(taddr + grp * 32, r[0]);
 #pragma unroll
@@ -471,32 +456,25 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
           if (pass + 1 < kNPass)
             tc::tmem_ld32_nowait(taddr + cb + kPassCols, r[(pass + 1) & 1]);
           const uint32_t* rr = r[pass & 1];
-          float h[32];
-#pragma unroll
-          for (int i = 0; i < 32; i += 4) {
-            // hard-swish of z = acc + b: z * clamp(z / 6 + 1/2, 0, 1), the clamp argument
-            // formed directly from the accumulator as acc / 6 + (b / 6 + 1/2); two columns per
-            // packed FP32 instruction (same rounding as the scalar ones)
-            const float4 b4 = *reinterpret_cast<const float4*>(bl + cb + i);
-            const float4 q4 = *reinterpret_cast<const float4*>(ql + cb + i);
-            float z[4];
-            hswish_x2(rr[i], rr[i + 1], b4.x, b4.y, q4.x, q4.y, h[i], h[i + 1], z[0], z[1]);
-            hswish_x2(rr[i + 2], rr[i + 3], b4.z, b4.w, q4.z, q4.w, h[i + 2], h[i + 3], z[2],
-                      z[3]);
-            if (MODE == kModeBatch && myrow < p.M)
-#pragma unroll
-              for (int u = 0; u < 4; ++u) p.Zs[layer][myrow * kH + cb + i + u] = z[u];
-          }
 #pragma unroll
           for (int q8 = 0; q8 < 4; ++q8) {
+            // ReLU of z = acc + b, eight columns: two bias loads, four packed additions, four
+            // converting ReLUs into bf16 pairs, one 16-byte store
+            const int i = 8 * q8;
+            const float4 b0 = *reinterpret_cast<const float4*>(bl + cb + i);
+            const float4 b1 = *reinterpret_cast<const float4*>(bl + cb + i + 4);
+            float z[8];
             uint4 q;
-            q.x = tc::pack_bf16(h[8 * q8 + 0], h[8 * q8 + 1]);
-            q.y = tc::pack_bf16(h[8 * q8 + 2], h[8 * q8 + 3]);
-            q.z = tc::pack_bf16(h[8 * q8 + 4], h[8 * q8 + 5]);
-            q.w = tc::pack_bf16(h[8 * q8 + 6], h[8 * q8 + 7]);
-            *reinterpret_cast<uint4*>(Hs + tc::kmajor_off(trow, cb + 8 * q8, kH)) = q;
-            if (MODE == kModeBatch && myrow < p.M)
-              *reinterpret_cast<uint4*>(p.Hs[layer] + myrow * kH + cb + 8 * q8) = q;
+            q.x = relu_bf16x2(rr[i + 0], rr[i + 1], b0.x, b0.y, z[0], z[1]);
+            q.y = relu_bf16x2(rr[i + 2], rr[i + 3], b0.z, b0.w, z[2], z[3]);
+            q.z = relu_bf16x2(rr[i + 4], rr[i + 5], b1.x, b1.y, z[4], z[5]);
+            q.w = relu_bf16x2(rr[i + 6], rr[i + 7], b1.z, b1.w, z[6], z[7]);
+            *reinterpret_cast<uint4*>(Hs + tc::kmajor_off(trow, cb + i, kH)) = q;
+            if (MODE == kModeBatch && myrow < p.M) {
+#pragma unroll
+              for (int u = 0; u < 8; ++u) p.Zs[layer][myrow * kH + cb + i + u] = z[u];
+              *reinterpret_cast<uint4*>(p.Hs[layer] + myrow * kH + cb + i) = q;
+            }
           }
           // this warp's part of the pass is written: make it visible to the tensor cores
           tc::fence_async_smem();
@@ -590,7 +568,7 @@ struct PPCfg {
   static constexpr int NRM = (2 + 2 * OUTP + 3) & ~3;
   static constexpr size_t smem = 2 * (size_t)XBYTES + 2 * (size_t)HBYTES +
                                  (size_t)NBUF * kChunkBytes +
-                                 sizeof(float) * (6 * kH + OUTP + NRM) + 64;
+                                 sizeof(float) * (3 * kH + OUTP + NRM) + 64;
 };
 
 template <int MODE>
@@ -603,7 +581,6 @@ __global__ void __launch_bounds__(kPPThreads, 1) k_mlp_pp(FusedParams p) {
   uint8_t* Wb = Hs + 2 * PPCfg::HBYTES;                 // NBUF x 32 KiB
   float* bs = reinterpret_cast<float*>(Wb + NBUF * kChunkBytes);
   float* nrm = bs + 3 * kH + OUTP;
-  float* bq = nrm + PPCfg::NRM;
   __shared__ __align__(8) uint64_t bar_w[NBUF], bar_f[NBUF], bar_x[2], bar_xf[2], bar_acc[2],
       bar_e[2], bar_done;
   __shared__ uint32_t tslot;
@@ -616,7 +593,6 @@ __global__ void __launch_bounds__(kPPThreads, 1) k_mlp_pp(FusedParams p) {
     bs[i] = p.params[p.bias_off[0] + i];
     bs[kH + i] = p.params[p.bias_off[1] + i];
     bs[2 * kH + i] = p.params[p.bias_off[2] + i];
-    for (int l = 0; l < 3; ++l) bq[l * kH + i] = fmaf(bs[l * kH + i], 1.0f / 6.0f, 0.5f);
   }
   for (int i = tid; i < OUTP; i += kPPThreads) bs[3 * kH + i] = p.params[p.bias_off[3] + i];
   for (int i = tid; i < 2 + 2 * OUTP; i += kPPThreads) nrm[i] = p.params[p.norm_off + i];
@@ -784,7 +760,6 @@ __global__ void __launch_bounds__(kPPThreads, 1) k_mlp_pp(FusedParams p) {
           uint8_t* Ht = Hs + t * PPCfg::HBYTES;
           if (l < 3 && !stop) {
             const float* bl = bs + l * kH;
-            const float* ql = bq + l * kH;
             uint32_t r[2][32];
             tc::tmem_ld32_nowait(taddr + grp * 32, r[0]);
 #pragma unroll
@@ -794,29 +769,23 @@ __global__ void __launch_bounds__(kPPThreads, 1) k_mlp_pp(FusedParams p) {
               if (pass + 1 < kNPass)
                 tc::tmem_ld32_nowait(taddr + cb + kPassCols, r[(pass + 1) & 1]);
               const uint32_t* rr = r[pass & 1];
-              float h[32];
-#pragma unroll
-              for (int i = 0; i < 32; i += 4) {
-                const float4 b4 = *reinterpret_cast<const float4*>(bl + cb + i);
-                const float4 q4 = *reinterpret_cast<const float4*>(ql + cb + i);
-                float z[4];
-                hswish_x2(rr[i], rr[i + 1], b4.x, b4.y, q4.x, q4.y, h[i], h[i + 1], z[0], z[1]);
-                hswish_x2(rr[i + 2], rr[i + 3], b4.z, b4.w, q4.z, q4.w, h[i + 2], h[i + 3], z[2],
-                          z[3]);
-                if (MODE == kModeBatch && myrow < p.M)
-#pragma unroll
-                  for (int u = 0; u < 4; ++u) p.Zs[l][myrow * kH + cb + i + u] = z[u];
-              }
 #pragma unroll
               for (int q8 = 0; q8 < 4; ++q8) {
+                const int i = 8 * q8;
+                const float4 b0 = *reinterpret_cast<const float4*>(bl + cb + i);
+                const float4 b1 = *reinterpret_cast<const float4*>(bl + cb + i + 4);
+                float z[8];
                 uint4 q;
-                q.x = tc::pack_bf16(h[8 * q8 + 0], h[8 * q8 + 1]);
-                q.y = tc::pack_bf16(h[8 * q8 + 2], h[8 * q8 + 3]);
-                q.z = tc::pack_bf16(h[8 * q8 + 4], h[8 * q8 + 5]);
-                q.w = tc::pack_bf16(h[8 * q8 + 6], h[8 * q8 + 7]);
-                *reinterpret_cast<uint4*>(Ht + tc::kmajor_off(trow, cb + 8 * q8, kH)) = q;
-                if (MODE == kModeBatch && myrow < p.M)
-                  *reinterpret_cast<uint4*>(p.Hs[l] + myrow * kH + cb + 8 * q8) = q;
+                q.x = relu_bf16x2(rr[i + 0], rr[i + 1], b0.x, b0.y, z[0], z[1]);
+                q.y = relu_bf16x2(rr[i + 2], rr[i + 3], b0.z, b0.w, z[2], z[3]);
+                q.z = relu_bf16x2(rr[i + 4], rr[i + 5], b1.x, b1.y, z[4], z[5]);
+                q.w = relu_bf16x2(rr[i + 6], rr[i + 7], b1.z, b1.w, z[6], z[7]);
+                *reinterpret_cast<uint4*>(Ht + tc::kmajor_off(trow, cb + i, kH)) = q;
+                if (MODE == kModeBatch && myrow < p.M) {
+#pragma unroll
+                  for (int u = 0; u < 8; ++u) p.Zs[l][myrow * kH + cb + i + u] = z[u];
+                  *reinterpret_cast<uint4*>(p.Hs[l] + myrow * kH + cb + i) = q;
+                }
               }
             }
             // H_t is written and the accumulator read: the MMAs of (t, l + 1) may go

@@ -80,20 +80,24 @@ def bf16(a):
 def stored_precision_backward(x, t, W, b, nout, y_gpu=None):
     """The gradients of the network's loss in FP64, with values rounded to bf16 where the
     network stores them (the hidden activations h_l, and the output and hidden gradients dY,
-    dZ_l when they enter a product), built from the oracle's definitions (hard-swish and its
-    derivative). Returns (dW, db, S, K):
+    dZ_l when they enter a product), built from the oracle's definitions (ReLU and its
+    derivative). Returns (dW, db, S, K, flagged):
     - S_l = |dZ_l|^T |a_{l-1}|, each weight gradient's sum of absolute terms: the scale of its
       FP32 accumulation and of one-unit bf16 differences;
-    - K_l, the absolute terms of the samples whose outputs y_gpu (the GPU's own forward)
-      already differ from this computation beyond FP32 accumulation: for them a stored bf16
-      activation rounded the other way on the GPU (a value next to a rounding boundary), so
-      every term of theirs may differ; doubled, as a bound on both sides."""
+    - K_l bounds two kinds of whole-term differences. (1) Samples whose outputs y_gpu (the
+      GPU's own forward) already differ from this computation beyond FP32 accumulation: for
+      them a stored bf16 activation rounded the other way on the GPU (a value next to a
+      rounding boundary), so every term of theirs may differ; doubled, as a bound on both
+      sides. (2) Units whose z lies within the FP32 accumulation error of ReLU's kink at 0:
+      the derivative (0 or 1) may differ there, so that term may differ by its full size."""
     L = len(W)
-    a, zs, acts = x, [], [x]
+    a, zs, acts, near = x, [], [x], []
     for li in range(L):
         z = a @ W[li].T + b[li]
         zs.append(z)
-        a = bf16(MO.hswish(z)) if li < L - 1 else z
+        err = 2e-5 * (np.abs(a) @ np.abs(W[li]).T + np.abs(b[li]))  # FP32 sums, generously
+        near.append(np.abs(z) <= err)
+        a = bf16(MO.relu(z)) if li < L - 1 else z
         acts.append(a)
     flag = np.zeros(a.shape[0], dtype=bool)
     if y_gpu is not None:
@@ -102,12 +106,13 @@ def stored_precision_backward(x, t, W, b, nout, y_gpu=None):
     g[:, :nout] = 2.0 * (a - t)[:, :nout] / (a.shape[0] * nout)
     dW, db, S, K = [None] * L, [None] * L, [None] * L, [None] * L
     for li in range(L - 1, -1, -1):
-        dz = g if li == L - 1 else g * MO.hswish_grad(zs[li])
+        dz = g if li == L - 1 else g * MO.relu_grad(zs[li])
+        kink = np.zeros_like(g) if li == L - 1 else np.abs(g) * near[li]
         dz16 = bf16(dz)
         dW[li] = dz16.T @ acts[li]
         db[li] = dz.sum(axis=0)
         S[li] = np.abs(dz16).T @ np.abs(acts[li])
-        K[li] = 2.0 * (np.abs(dz16) * flag[:, None]).T @ np.abs(acts[li])
+        K[li] = (2.0 * np.abs(dz16) * flag[:, None] + kink).T @ np.abs(acts[li])
         g = dz16 @ W[li]
     return dW, db, S, K, flag
 

@@ -1,6 +1,6 @@
 """Pins of the learned-stencil network's CPU oracle (no GPU): chain-rule gradients against
-central finite differences, hard-swish against its closed form, a hand-computed tiny network,
-and the patch layout."""
+central finite differences, ReLU against its closed form, a hand-computed tiny network, and
+the patch layout."""
 
 import numpy as np
 import pytest
@@ -8,24 +8,28 @@ import pytest
 from oracle import mlp_oracle as M
 
 
-def test_hswish_closed_form_and_derivative():
-    z = np.linspace(-6, 6, 101) + 0.0123  # off the kinks at -3 and 3
-    ref = np.where(z < -3, 0.0, np.where(z > 3, z, z * (z + 3) / 6))
-    assert np.allclose(M.hswish(z), ref, rtol=0, atol=1e-15)
+def test_relu_closed_form_and_derivative():
+    z = np.linspace(-6, 6, 101) + 0.0123  # off the kink at 0
+    assert np.array_equal(M.relu(z), np.where(z > 0, z, 0.0))
     h = 1e-6
-    fd = (M.hswish(z + h) - M.hswish(z - h)) / (2 * h)
-    assert np.abs(fd - M.hswish_grad(z)).max() < 1e-8
-    assert M.hswish(0.0) == 0.0 and abs(M.hswish_grad(0.0) - 0.5) < 1e-15
+    fd = (M.relu(z + h) - M.relu(z - h)) / (2 * h)
+    assert np.abs(fd - M.relu_grad(z)).max() < 1e-8
+    assert M.relu(0.0) == 0.0 and M.relu_grad(0.0) == 0.0 and M.relu_grad(1e-300) == 1.0
 
 
 def test_tiny_network_by_hand():
-    # one input, one hidden unit, one output: y = w2 * hswish(w1 x + b1) + b2
+    # one input, two hidden units (one active, one not), one output:
+    # y = w2 . relu(W1 x + b1) + b2
     x = np.array([[0.5]])
-    W = [np.array([[2.0]]), np.array([[-3.0]])]
-    b = [np.array([0.25]), np.array([1.0])]
+    W = [np.array([[2.0], [-4.0]]), np.array([[-3.0, 5.0]])]
+    b = [np.array([0.25, 1.0]), np.array([1.0])]
     y, _ = M.mlp_forward(x, W, b)
-    z = 2.0 * 0.5 + 0.25
-    assert abs(y[0, 0] - (-3.0 * z * (z + 3) / 6 + 1.0)) < 1e-15
+    # z = (1.25, -1.0): relu -> (1.25, 0); y = -3 * 1.25 + 5 * 0 + 1
+    assert abs(y[0, 0] - (-3.0 * 1.25 + 1.0)) < 1e-15
+    loss, dW, db = M.mlp_backward(x, np.array([[0.0]]), W, b)
+    g = 2.0 * y[0, 0]  # d loss / d y for one sample, one output
+    assert abs(dW[1][0, 0] - g * 1.25) < 1e-14 and dW[1][0, 1] == 0.0
+    assert abs(dW[0][0, 0] - g * -3.0 * 0.5) < 1e-14 and dW[0][1, 0] == 0.0
 
 
 @pytest.mark.parametrize("seed", [0, 1])
