@@ -35,7 +35,17 @@ namespace {
 constexpr int kH = 256;         // hidden width
 constexpr int kTile = 128;      // rows per tile (MMA M)
 constexpr int kChunkK = 64;     // K width of a GEMM staging chunk (training)
-constexpr int kChunkBytes = 32768;  // largest streamed weight chunk (fused kernel)
+// Largest streamed weight chunk of the inference kernels. The weights are packed chunk by chunk
+// (plan_for); a chunk of an N-wide layer covers K = kChunkBytes / (2 N) inputs.
+#ifndef LSP_MLP_CHUNK_BYTES
+#define LSP_MLP_CHUNK_BYTES 32768
+#endif
+constexpr int kChunkBytes = LSP_MLP_CHUNK_BYTES;
+static_assert(kChunkBytes >= 8192 && (kChunkBytes & (kChunkBytes - 1)) == 0,
+              "a chunk holds at least one K step of 16 of a 256-wide layer");
+// shared memory for weight chunks: one tile in flight (2D, 3D), two tiles in flight (2D)
+constexpr int kWBuf2D = 131072, kWBuf3D = 98304, kWBufPP = 65536;
+constexpr int kMaxChunks = 64;
 constexpr int kFusedThreads = 320;  // fused kernel: 8 epilogue warps, MMA warp, loader warp
 
 struct Dims {
@@ -85,11 +95,11 @@ Layout layout_for(const Dims& m) {
 // the same plan at compile time (FusedCfg).
 struct ChunkPlan {
   int n;
-  int64_t off[40];   // bytes into the tile buffer
-  int kw[40];        // K width of the chunk
-  int nrows[40];     // N of the chunk (= the layer's output width)
-  int layer[40];
-  int k0[40];
+  int64_t off[kMaxChunks];   // bytes into the tile buffer
+  int kw[kMaxChunks];        // K width of the chunk
+  int nrows[kMaxChunks];     // N of the chunk (= the layer's output width)
+  int layer[kMaxChunks];
+  int k0[kMaxChunks];
   int64_t total_bytes;
 };
 ChunkPlan plan_for(const Dims& m) {
@@ -183,7 +193,7 @@ struct FusedCfg {
   static constexpr int K0 = D == 2 ? 32 : 128;
   static constexpr int OUTP = D == 2 ? 32 : 64;
   static constexpr int XBUF = D == 2 ? 2 : 1;  // input-tile buffers
-  static constexpr int NBUF = D == 2 ? 4 : 3;  // weight-chunk buffers of 32 KiB
+  static constexpr int NBUF = (D == 2 ? kWBuf2D : kWBuf3D) / kChunkBytes;  // weight buffers
   static constexpr int XBYTES = kTile * K0 * 2;
   // the chunk plan of plan_for(), at compile time
   __host__ __device__ static constexpr int N(int l) { return l < 3 ? kH : OUTP; }
@@ -203,6 +213,26 @@ struct FusedCfg {
                                  (size_t)NBUF * kChunkBytes +
                                  sizeof(float) * (3 * kH + OUTP + NRM) + 64;
 };
+template <int D>
+constexpr int chunk_count() {
+  return FusedCfg<D>::NCH(0) + FusedCfg<D>::NCH(1) + FusedCfg<D>::NCH(2) + FusedCfg<D>::NCH(3);
+}
+static_assert(chunk_count<2>() <= kMaxChunks && chunk_count<3>() <= kMaxChunks,
+              "the chunk plan must fit ChunkPlan");
+
+// float -> double on the integer pipe (the FP64 pipe, which the hardware conversion uses, is
+// narrow on this GPU): the 8-bit exponent is rebased from bias 127 to bias 1023 (255 to 2047
+// for infinities and NaN, whose payload moves along) and the 23-bit fraction becomes the top
+// of the 52-bit one. Exact for normal numbers, zeros, infinities and NaN; subnormal inputs
+// (|x| < 2^-126) give a zero of the same sign.
+__device__ __forceinline__ double f2d_int(float x) {
+  const uint32_t f = __float_as_uint(x), a = f & 0x7FFFFFFFu;
+  const uint32_t bias = a >= 0x7F800000u ? (1792u << 20) : (896u << 20);
+  const bool sub = a < 0x00800000u;
+  const uint32_t hi = (sub ? 0u : (a >> 3) + bias) | (f & 0x80000000u);
+  const uint32_t lo = sub ? 0u : f << 29;
+  return __hiloint2double((int)hi, (int)lo);
+}
 
 // Fused forward over tiles of 128 rows, persistent (one CTA per SM, tiles strided by the grid).
 //
@@ -391,7 +421,8 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
                 ph_x ^= 1u << xb;
               }
             } else {
-              const int need = (k0 + Cfg::KW(l)) / kPassCols;
+              // the passes that cover this chunk's K columns (a chunk may end inside a pass)
+              const int need = (k0 + Cfg::KW(l) + kPassCols - 1) / kPassCols;
               for (; waited < need; ++waited) {
                 wait(&bar_h[waited], ph_h >> waited & 1, 32);
                 ph_h ^= 1u << waited;
@@ -484,6 +515,21 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
         }
       }
       // ---- layer 3: the outputs (accumulator 1) ----
+      // rows mode, group 1, 2D: the fp32 pairs of s_j and of v at the stencil offsets, loaded
+      // while the layer-3 MMAs run (in 3D the 56 values cost more registers than they save)
+      float pf_sh = 0.f, pf_sl = 0.f, pf_vh[MU], pf_vl[MU];
+#pragma unroll
+      for (int i = 0; i < MU; ++i) pf_vh[i] = pf_vl[i] = 0.f;
+      if (D == 2 && MODE == kModeRows && grp == 1 && myrow < p.M) {
+        pf_sh = __ldg(p.sh + myrow);
+        pf_sl = __ldg(p.sl + myrow);
+#pragma unroll
+        for (int i = 0; i < MU; ++i) {
+          const int64_t nb = nb_index<D, 1>(myrow, i, p.logn, mask);
+          pf_vh[i] = __ldg(p.vh + nb);
+          pf_vl[i] = __ldg(p.vl + nb);
+        }
+      }
       wait_warp(&bar_acc[1], ph_acc[1], 8);
       ph_acc[1] ^= 1;
       tc::fence_after();
@@ -527,12 +573,20 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
           } else {
             // v[mu_j] - s_j from the fp32 pairs: the difference of the high parts is exact
             // when v and s_j are within a factor of two of each other (the usual case)
-            const float sh = __ldg(p.sh + myrow), sl = __ldg(p.sl + myrow);
+            if (D == 3 && myrow < p.M) {
+              pf_sh = __ldg(p.sh + myrow);
+              pf_sl = __ldg(p.sl + myrow);
+#pragma unroll
+              for (int i = 0; i < MU; ++i) {
+                const int64_t nb = nb_index<D, 1>(myrow, i, p.logn, mask);
+                pf_vh[i] = __ldg(p.vh + nb);
+                pf_vl[i] = __ldg(p.vl + nb);
+              }
+            }
 #pragma unroll
             for (int i = 0; i < MU; ++i) {
-              const int64_t nb = nb_index<D, 1>(myrow, i, p.logn, mask);
-              const float dv = (__ldg(p.vh + nb) - sh) + (__ldg(p.vl + nb) - sl);
-              __stcs(p.P + myrow * MU + i, (double)fmaf(cc[i] * sc, dv, al[i] * sc));
+              const float dv = (pf_vh[i] - pf_sh) + (pf_vl[i] - pf_sl);
+              __stcs(p.P + myrow * MU + i, (double)(fmaf(cc[i] * sc, dv, al[i] * sc)));
             }
           }
         }
@@ -562,7 +616,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) k_mlp_fused(FusedParams p) {
 constexpr int kPPThreads = 320;  // 8 epilogue warps, the MMA warp, the loader warp
 
 struct PPCfg {
-  static constexpr int MU = 9, K0 = 32, OUTP = 32, NBUF = 2;
+  static constexpr int MU = 9, K0 = 32, OUTP = 32, NBUF = kWBufPP / kChunkBytes;
   static constexpr int XBYTES = kTile * K0 * 2;  // 8 KiB per input tile
   static constexpr int HBYTES = kTile * kH * 2;  // 64 KiB per activation buffer
   static constexpr int NRM = (2 + 2 * OUTP + 3) & ~3;
@@ -746,11 +800,37 @@ __global__ void __launch_bounds__(kPPThreads, 1) k_mlp_pp(FusedParams p) {
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     uint32_t ph_acc = 0;
     const int64_t mask = ((int64_t)1 << p.logn) - 1;
+    // rows mode, warps of group 1: the fp32 pairs of s_j and of v at the stencil offsets that
+    // P = alpha + c (v - s_j) needs, loaded one layer ahead (set a: tile A, set b: tile B)
+    float a_sh = 0.f, a_sl = 0.f, a_vh[MU], a_vl[MU], b_sh = 0.f, b_sl = 0.f, b_vh[MU], b_vl[MU];
+#pragma unroll
+    for (int i = 0; i < MU; ++i) a_vh[i] = a_vl[i] = b_vh[i] = b_vl[i] = 0.f;
+    auto prefetch = [&](int64_t row, float& sh, float& sl, float (&vh)[MU], float (&vl)[MU]) {
+      if (row >= p.M) return;
+      sh = __ldg(p.sh + row);
+      sl = __ldg(p.sl + row);
+#pragma unroll
+      for (int i = 0; i < MU; ++i) {
+        const int64_t nb = nb_index<2, 1>(row, i, p.logn, mask);
+        vh[i] = __ldg(p.vh + nb);
+        vl[i] = __ldg(p.vl + nb);
+      }
+    };
     for (int64_t pr = 0; pr < my_pairs; ++pr) {
       if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;
       for (int l = 0; l < 4; ++l) {
         for (int t = 0; t < 2; ++t) {
           if (!has(pr, t)) continue;
+          if (MODE == kModeRows && grp == 1) {
+            if (l == 2 && t == 1) {
+              prefetch(tile_of(pr, 0) * kTile + trow, a_sh, a_sl, a_vh, a_vl);
+            } else if (l == 3 && t == 0) {
+              if (has(pr, 1))
+                prefetch(tile_of(pr, 1) * kTile + trow, b_sh, b_sl, b_vh, b_vl);
+              else
+                prefetch(tile_of(pr, 0) * kTile + trow, a_sh, a_sl, a_vh, a_vl);
+            }
+          }
           wait_warp(&bar_acc[t], ph_acc >> t & 1, 8);
           ph_acc ^= 1u << t;
           tc::fence_after();
@@ -800,35 +880,71 @@ __global__ void __launch_bounds__(kPPThreads, 1) k_mlp_pp(FusedParams p) {
 #pragma unroll
               for (int i = 0; i < 32; ++i) y[i] = __uint_as_float(r[i]) + bs[3 * kH + i];
             }
-            if (myrow < p.M) {
-              if (MODE == kModeBatch) {
-                if (grp == 0) {
+            if (MODE == kModeBatch) {
+              if (grp == 0 && myrow < p.M) {
 #pragma unroll
-                  for (int o = 0; o < OUTP; ++o) p.Y[myrow * OUTP + o] = y[o];
-                }
-              } else {
-                float al[MU], cc[MU], nrm2 = 0.0f;
+                for (int o = 0; o < OUTP; ++o) p.Y[myrow * OUTP + o] = y[o];
+              }
+            } else {
+              // de-normalise, unit-normalise alpha (c scaled alike: P^-1 C is invariant)
+              float al[MU], cc[MU], nrm2 = 0.0f;
+#pragma unroll
+              for (int i = 0; i < MU; ++i) {
+                al[i] = y[i] * nrm[2 + OUTP + i] + nrm[2 + i];
+                cc[i] = y[MU + i] * nrm[2 + OUTP + MU + i] + nrm[2 + MU + i];
+                nrm2 = fmaf(al[i], al[i], nrm2);
+              }
+              const float sc = nrm2 > 0.0f ? rsqrtf(nrm2) : 1.0f;
+              // This warp's 32 rows of Q and C (group 0) or of P (group 1) are contiguous
+              // blocks of 32 x MU doubles in global memory. When all 32 rows exist they are
+              // staged in H_t (free: the layer-3 MMAs that read it have completed, and the
+              // next writes to it follow this epilogue's arrival) and leave by one bulk copy
+              // per block; otherwise each row is stored directly.
+              constexpr int BLK = 32 * MU * 8;
+              const int64_t wrow0 = tile_of(pr, t) * kTile + quarter * 32;
+              const bool full = wrow0 + 32 <= p.M;
+              double* stg = reinterpret_cast<double*>(Ht + (grp == 0 ? quarter : 8 + quarter) * BLK);
+              if (grp == 0) {
 #pragma unroll
                 for (int i = 0; i < MU; ++i) {
-                  al[i] = y[i] * nrm[2 + OUTP + i] + nrm[2 + i];
-                  cc[i] = y[MU + i] * nrm[2 + OUTP + MU + i] + nrm[2 + MU + i];
-                  nrm2 = fmaf(al[i], al[i], nrm2);
+                  // Q and C convert on the integer pipe while group 1 converts P on the FP64
+                  // pipe: the two pipes run side by side
+                  const double qv = f2d_int(al[i] * sc), cv = f2d_int(cc[i] * sc);
+                  if (full) {
+                    stg[lane * MU + i] = qv;
+                    stg[4 * BLK / 8 + lane * MU + i] = cv;
+                  } else if (myrow < p.M) {
+                    __stcs(p.Q + myrow * MU + i, qv);
+                    __stcs(p.C + myrow * MU + i, cv);
+                  }
                 }
-                const float sc = nrm2 > 0.0f ? rsqrtf(nrm2) : 1.0f;
-                if (grp == 0) {
+              } else {
+                // v[mu_j] - s_j from the fp32 pairs: the difference of the high parts is exact
+                // when v and s_j are within a factor of two of each other (the usual case)
+                const float sh = t == 0 ? a_sh : b_sh, sl = t == 0 ? a_sl : b_sl;
 #pragma unroll
-                  for (int i = 0; i < MU; ++i) {
-                    __stcs(p.Q + myrow * MU + i, (double)(al[i] * sc));
-                    __stcs(p.C + myrow * MU + i, (double)(cc[i] * sc));
+                for (int i = 0; i < MU; ++i) {
+                  const float dv = ((t == 0 ? a_vh[i] : b_vh[i]) - sh) +
+                                   ((t == 0 ? a_vl[i] : b_vl[i]) - sl);
+                  const double pv = (double)(fmaf(cc[i] * sc, dv, al[i] * sc));
+                  if (full)
+                    stg[lane * MU + i] = pv;
+                  else if (myrow < p.M)
+                    __stcs(p.P + myrow * MU + i, pv);
+                }
+              }
+              if (full) {
+                tc::fence_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                  if (grp == 0) {
+                    tc::bulk_s2g(p.Q + wrow0 * MU, stg, BLK);
+                    tc::bulk_s2g(p.C + wrow0 * MU, stg + 4 * BLK / 8, BLK);
+                  } else {
+                    tc::bulk_s2g(p.P + wrow0 * MU, stg, BLK);
                   }
-                } else {
-                  const float sh = __ldg(p.sh + myrow), sl = __ldg(p.sl + myrow);
-#pragma unroll
-                  for (int i = 0; i < MU; ++i) {
-                    const int64_t nb = nb_index<2, 1>(myrow, i, p.logn, mask);
-                    const float dv = (__ldg(p.vh + nb) - sh) + (__ldg(p.vl + nb) - sl);
-                    __stcs(p.P + myrow * MU + i, (double)fmaf(cc[i] * sc, dv, al[i] * sc));
-                  }
+                  tc::bulk_commit();
+                  tc::bulk_wait_read();  // H_t may be written again once every warp arrived
                 }
               }
             }
@@ -839,6 +955,7 @@ __global__ void __launch_bounds__(kPPThreads, 1) k_mlp_pp(FusedParams p) {
         }
       }
     }
+    if (lane == 0) tc::bulk_wait_all();  // this warp's row stores have landed
   }
   tc::fence_before();
   __syncthreads();
