@@ -1041,8 +1041,9 @@ def main():
     ap.add_argument("--mode", default="fp64", choices=["fp64", "dword", "mixed", "learned"])
     ap.add_argument("--learned-steps", type=int, default=3000,
                     help="training steps of the surrogate (learned mode and forms)")
-    ap.add_argument("--mlp-schedule", type=int, default=None, choices=[0, 1],
-                    help="2D network kernel: 1 = two tiles in flight (default), 0 = one tile")
+    ap.add_argument("--mlp-schedule", type=int, default=None, choices=[0, 1, 2],
+                    help="2D network kernel: 1 = two tiles in flight (default), 0 = one tile, "
+                         "2 = two 256-row tiles on a CTA pair")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP64 / mixed / learned summaries at 2D n=1024 and 3D n=64")
     ap.add_argument("--detail", default="",

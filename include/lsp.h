@@ -282,8 +282,12 @@ lsp_status lsp_mlp_set_wait_limit(lsp_mlp* m, uint64_t ns);
 /*
  * Schedule of the 2D network's fused inference kernel: 1 (the default) keeps two 128-row tiles
  * in flight per SM, so that one tile's tensor-core products overlap the other's epilogue;
- * 0 runs one tile at a time. Both compute the same rows bit for bit. 3D networks always run
- * one tile at a time (two tiles' buffers do not fit in shared memory). LSP_ERR_ARG otherwise.
+ * 0 runs one tile at a time; 2 runs the two-tile schedule on pairs of SMs (a two-CTA cluster
+ * with 256-row tensor-core products, each CTA holding half of every weight chunk) for the
+ * rows of a build, and schedule 1 for training batches. All three compute the same rows bit
+ * for bit; schedule 2 measured slower than 1 and is kept for comparison. 3D networks always
+ * run one tile at a time (two tiles' buffers do not fit in shared memory). LSP_ERR_ARG for any
+ * other value.
  */
 lsp_status lsp_mlp_set_schedule(lsp_mlp* m, int schedule);
 /* Attach a network to a context for LSP_LEARNED builds (NULL detaches). Same d required. */

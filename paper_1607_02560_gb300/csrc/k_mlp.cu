@@ -962,6 +962,414 @@ __global__ void __launch_bounds__(kPPThreads, 1) k_mlp_pp(FusedParams p) {
   if (warp == 0) tc::tmem_dealloc(tmem, 2 * kH);
 }
 
+// ---- two tiles in flight on a CTA pair (2D, cta_group::2) ----------------------------------
+// The two-tile schedule above streams every weight chunk into every CTA through two 32 KiB
+// buffers, and a chunk takes ~1.1k cycles from its copy to its arrival, against ~0.5k cycles of
+// MMA for the chunk before it, so the MMAs stall at every buffer reuse. Here a cluster of two
+// CTAs (one TPC) runs the same schedule on super-tiles of 256 rows with M = 256 MMAs: each CTA
+// holds its 128 rows (input tile, activations, accumulator rows) and HALF of every weight chunk
+// (N/2 rows of the K-major chunk, 16 KiB), so the same 64 KiB give four chunk buffers (three
+// chunks of lead) and each SM streams half the weight bytes.
+//
+// The even CTA (rank 0) issues every MMA and commit; commits arrive in both CTAs (bar_f: a
+// buffer may be refilled; bar_acc: an accumulator is ready; bar_xf: an input buffer is free;
+// bar_done). Operands of the odd CTA are reported to the even one: its MMA warp forwards the
+// arrival of each of its weight halves (bar_wp) and input tiles (bar_xp), and every epilogue
+// warp of both CTAs arrives on the even CTA's bar_e (16 arrivals). Both CTAs walk the same
+// sequence of super-tiles, so the weight stream stays in step. Every wait is bounded; a CTA
+// that gives up stops arriving, and its partner's waits then run out too.
+//
+// Measured on GB300 (2D n = 1024): 0.47 ms against 0.36 ms for the one-CTA two-tile kernel, with
+// bit-identical rows. The weight stalls are gone, but the pair MMAs of a chunk take ~700 cycles
+// instead of ~500, and the cluster-scope arrivals lengthen every epilogue by ~1k cycles
+// (forwarding them through one thread instead made it 0.50 ms). Selectable as schedule 2.
+constexpr int kPP2Half = kChunkBytes / 2;
+
+struct PP2Cfg {
+  static constexpr int NBUF = kWBufPP / kPP2Half;  // half-chunk buffers
+};
+
+template <int MODE>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPPThreads, 1) k_mlp_pp2(FusedParams p) {
+  using Cfg = FusedCfg<2>;
+  constexpr int MU = PPCfg::MU, OUTP = PPCfg::OUTP, NBUF = PP2Cfg::NBUF;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t* Xs = smem;                    // 2 x (128 x 32) bf16: this CTA's rows of tiles A, B
+  uint8_t* Hs = Xs + 2 * PPCfg::XBYTES;  // 2 x (128 x 256) bf16
+  uint8_t* Wb = Hs + 2 * PPCfg::HBYTES;  // NBUF x 16 KiB: this CTA's half of each chunk
+  float* bs = reinterpret_cast<float*>(Wb + NBUF * kPP2Half);
+  float* nrm = bs + 3 * kH + OUTP;
+  __shared__ __align__(8) uint64_t bar_w[NBUF], bar_wp[NBUF], bar_f[NBUF], bar_x[2], bar_xp[2],
+      bar_xf[2], bar_acc[2], bar_e[2], bar_done;
+  __shared__ uint32_t tslot;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool mma_warp = warp == kEpiWarps;
+  const bool loader = warp == kEpiWarps + 1;
+  const uint32_t rank = tc::cluster_rank();
+
+  for (int i = tid; i < kH; i += kPPThreads) {
+    bs[i] = p.params[p.bias_off[0] + i];
+    bs[kH + i] = p.params[p.bias_off[1] + i];
+    bs[2 * kH + i] = p.params[p.bias_off[2] + i];
+  }
+  for (int i = tid; i < OUTP; i += kPPThreads) bs[3 * kH + i] = p.params[p.bias_off[3] + i];
+  for (int i = tid; i < 2 + 2 * OUTP; i += kPPThreads) nrm[i] = p.params[p.norm_off + i];
+  if (mma_warp && lane == 0) {
+    for (int b = 0; b < NBUF; ++b) {
+      tc::mbar_init(&bar_w[b], 1);
+      tc::mbar_init(&bar_wp[b], 1);
+      tc::mbar_init(&bar_f[b], 1);
+    }
+    for (int t = 0; t < 2; ++t) {
+      tc::mbar_init(&bar_x[t], 1);
+      tc::mbar_init(&bar_xp[t], 1);
+      tc::mbar_init(&bar_xf[t], 1);
+      tc::mbar_init(&bar_acc[t], 1);
+      tc::mbar_init(&bar_e[t], 2 * kEpiWarps);
+    }
+    tc::mbar_init(&bar_done, 1);
+    s_abort = 0;
+  }
+  if (warp == 0) tc::tmem_alloc_pair(&tslot, 2 * kH);
+  tc::fence_before();
+  __syncthreads();
+  // both CTAs' barriers are initialised before either CTA arrives on the other's
+  tc::cluster_sync();
+  tc::fence_after();
+  const uint32_t tmem = tslot;
+  volatile int* abort_flag = &s_abort;
+  auto wait = [&](uint64_t* bar, uint32_t parity, int bit) {
+    if (tc::mbar_test_cluster(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (tc::mbar_wait_cluster(bar, parity, p.err, bit, p.wait_ns)) return true;
+    *abort_flag = 1;
+    return false;
+  };
+  auto wait_warp = [&](uint64_t* bar, uint32_t parity, int bit) {
+    if (lane == 0) wait(bar, parity, bit);
+    __syncwarp();
+  };
+  // super-tiles of 256 rows: the pair handles cl + i * ncl, i < my_super, in pairs (A, B);
+  // this CTA's rows of super-tile s are the 128-row tile 2 s + rank
+  const int64_t ntiles = (p.M + kTile - 1) / kTile;
+  const int64_t nsuper = (ntiles + 1) / 2;
+  const int64_t cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int64_t my_super = cl < nsuper ? (nsuper - 1 - cl) / ncl + 1 : 0;
+  const int64_t my_pairs = (my_super + 1) / 2;
+  auto tile_of = [&](int64_t pair, int t) {
+    return 2 * (cl + (2 * pair + t) * ncl) + (int64_t)rank;
+  };
+  auto has = [&](int64_t pair, int t) { return 2 * pair + t < my_super; };
+
+  if (loader) {
+    if (lane == 0) {
+      uint32_t slot = 0, ph_f = 0, ph_xf = 0, issued = 0, cnt_x[2] = {0, 0};
+      auto load_x = [&](int64_t pair, int t) {
+        tc::mbar_expect_tx(&bar_x[t], PPCfg::XBYTES);
+        tc::bulk_g2s(Xs + t * PPCfg::XBYTES, p.Xt + tile_of(pair, t) * PPCfg::XBYTES,
+                     PPCfg::XBYTES, &bar_x[t]);
+        ++cnt_x[t];
+      };
+      if (my_pairs > 0) {
+        load_x(0, 0);
+        if (has(0, 1)) load_x(0, 1);
+      }
+      for (int64_t pr = 0; pr < my_pairs && !*abort_flag; ++pr) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          for (int t = 0; t < 2; ++t) {
+            if (!has(pr, t) || *abort_flag) continue;
+#pragma unroll
+            for (int c = 0; c < Cfg::NCH(l); ++c) {
+              if (issued >= (uint32_t)NBUF) {
+                wait(&bar_f[slot], ph_f >> slot & 1, 2);  // the pair MMAs that read it
+                ph_f ^= 1u << slot;
+              }
+              if (*abort_flag) break;
+              const int half = Cfg::CHUNK_BYTES(l) / 2;
+              tc::mbar_expect_tx(&bar_w[slot], half);
+              tc::bulk_g2s(Wb + slot * kPP2Half,
+                           p.tiles + Cfg::OFF(l) + (int64_t)c * Cfg::CHUNK_BYTES(l) +
+                               (int64_t)rank * half,
+                           half, &bar_w[slot]);
+              ++issued;
+              slot = slot + 1 == (uint32_t)NBUF ? 0 : slot + 1;
+            }
+            if (l == 1 && has(pr + 1, t) && !*abort_flag) {
+              wait(&bar_xf[t], ph_xf >> t & 1, 1);
+              ph_xf ^= 1u << t;
+              if (!*abort_flag) load_x(pr + 1, t);
+            }
+          }
+        }
+      }
+      for (int b = 0; b < NBUF; ++b) {
+        const uint32_t uses = issued / NBUF + ((uint32_t)b < issued % NBUF ? 1u : 0u);
+        if (uses) tc::mbar_wait(&bar_w[b], (uses - 1) & 1, p.err, 0);
+      }
+      for (int t = 0; t < 2; ++t)
+        if (cnt_x[t]) tc::mbar_wait(&bar_x[t], (cnt_x[t] - 1) & 1, p.err, 0);
+    }
+    __syncwarp();
+  } else if (mma_warp && rank != 0) {
+    // ---- odd CTA: forward the arrival of its operands to the even CTA ----
+    if (lane == 0) {
+      uint32_t slot = 0, ph_w = 0, ph_x = 0;
+      for (int64_t pr = 0; pr < my_pairs && !*abort_flag; ++pr) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          for (int t = 0; t < 2; ++t) {
+            if (!has(pr, t) || *abort_flag) continue;
+            if (l == 0) {
+              if (!wait(&bar_x[t], ph_x >> t & 1, 1)) break;
+              ph_x ^= 1u << t;
+              tc::mbar_arrive_cluster(&bar_xp[t], 0);
+            }
+#pragma unroll
+            for (int c = 0; c < Cfg::NCH(l); ++c) {
+              if (!wait(&bar_w[slot], ph_w >> slot & 1, 4)) break;
+              ph_w ^= 1u << slot;
+              tc::mbar_arrive_cluster(&bar_wp[slot], 0);
+              slot = slot + 1 == (uint32_t)NBUF ? 0 : slot + 1;
+            }
+          }
+        }
+      }
+      // the even CTA's last commit: every pair MMA (which reads this CTA's shared memory and
+      // writes its tensor memory) has completed
+      tc::mbar_wait(&bar_done, 0, p.err, 0);
+    }
+    __syncwarp();
+  } else if (mma_warp) {
+    // ---- even CTA: every MMA of the pair ----
+    if (lane == 0) {
+      uint32_t slot = 0, ph_w = 0, ph_x = 0, ph_e = 0;
+      uint32_t e_done[2] = {0, 0};
+      for (int64_t pr = 0; pr < my_pairs && !*abort_flag; ++pr) {
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          for (int t = 0; t < 2; ++t) {
+            if (!has(pr, t) || *abort_flag) continue;
+            if (l == 0) {
+              wait(&bar_x[t], ph_x >> t & 1, 1);
+              wait(&bar_xp[t], ph_x >> t & 1, 1);
+              ph_x ^= 1u << t;
+            }
+            if (e_done[t] > 0) {  // both CTAs' epilogues of this slot: H_t written, acc read
+              wait(&bar_e[t], ph_e >> t & 1, 32);
+              ph_e ^= 1u << t;
+            }
+            const uint32_t acc = tmem + (uint32_t)(t * kH);
+#pragma unroll
+            for (int c = 0; c < Cfg::NCH(l); ++c) {
+              wait(&bar_w[slot], ph_w >> slot & 1, 4);
+              wait(&bar_wp[slot], ph_w >> slot & 1, 4);
+              ph_w ^= 1u << slot;
+              if (*abort_flag) break;
+              tc::fence_after();
+              const int k0 = c * Cfg::KW(l);
+              const uint32_t aBase = l == 0 ? tc::smem_u32(Xs + t * PPCfg::XBYTES) + (k0 / 8) * 128
+                                            : tc::smem_u32(Hs + t * PPCfg::HBYTES) + (k0 / 8) * 128;
+              const uint32_t sboA = (uint32_t)((l == 0 ? Cfg::K0 : kH) / 8) * 128;
+              const uint32_t sboB = (uint32_t)(Cfg::KW(l) / 8) * 128;
+              const uint32_t bBase = tc::smem_u32(Wb + slot * kPP2Half);
+              constexpr uint32_t idesc_h = tc::idesc_bf16(2 * kTile, kH);
+              const uint32_t idesc = l < 3 ? idesc_h : tc::idesc_bf16(2 * kTile, OUTP);
+              const uint64_t ad0 = tc::desc_kmajor(aBase, 128, sboA);
+              const uint64_t bd0 = tc::desc_kmajor(bBase, 128, sboB);
+#pragma unroll
+              for (int s = 0; s < Cfg::KW(l) / 16; ++s)
+                tc::mma_bf16_pair(acc, ad0 + (uint64_t)(16 * s), bd0 + (uint64_t)(16 * s), idesc,
+                                  (c == 0 && s == 0) ? 0u : 1u);
+              tc::commit_pair(&bar_f[slot]);
+              slot = slot + 1 == (uint32_t)NBUF ? 0 : slot + 1;
+            }
+            if (*abort_flag) break;
+            tc::commit_pair(&bar_acc[t]);
+            if (l == 0) tc::commit_pair(&bar_xf[t]);
+            ++e_done[t];
+          }
+        }
+      }
+      tc::commit_pair(&bar_done);
+      tc::mbar_wait(&bar_done, 0, p.err, 0);
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue warps: (A, l), (B, l), (A, l + 1), ... ----
+    const int quarter = warp & 3, grp = warp >> 2;
+    const int trow = quarter * 32 + lane;  // tensor-memory lane = tile row
+    const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    uint32_t ph_acc = 0;
+    const int64_t mask = ((int64_t)1 << p.logn) - 1;
+    // rows mode, warps of group 1: the fp32 pairs of s_j and of v at the stencil offsets that
+    // P = alpha + c (v - s_j) needs, loaded one layer ahead (set a: tile A, set b: tile B)
+    float a_sh = 0.f, a_sl = 0.f, a_vh[MU], a_vl[MU], b_sh = 0.f, b_sl = 0.f, b_vh[MU], b_vl[MU];
+#pragma unroll
+    for (int i = 0; i < MU; ++i) a_vh[i] = a_vl[i] = b_vh[i] = b_vl[i] = 0.f;
+    auto prefetch = [&](int64_t row, float& sh, float& sl, float (&vh)[MU], float (&vl)[MU]) {
+      if (row >= p.M) return;
+      sh = __ldg(p.sh + row);
+      sl = __ldg(p.sl + row);
+#pragma unroll
+      for (int i = 0; i < MU; ++i) {
+        const int64_t nb = nb_index<2, 1>(row, i, p.logn, mask);
+        vh[i] = __ldg(p.vh + nb);
+        vl[i] = __ldg(p.vl + nb);
+      }
+    };
+    for (int64_t pr = 0; pr < my_pairs; ++pr) {
+      if (__shfl_sync(0xffffffffu, *abort_flag, 0)) break;
+      for (int l = 0; l < 4; ++l) {
+        for (int t = 0; t < 2; ++t) {
+          if (!has(pr, t)) continue;
+          if (MODE == kModeRows && grp == 1) {
+            if (l == 2 && t == 1) {
+              prefetch(tile_of(pr, 0) * kTile + trow, a_sh, a_sl, a_vh, a_vl);
+            } else if (l == 3 && t == 0) {
+              if (has(pr, 1))
+                prefetch(tile_of(pr, 1) * kTile + trow, b_sh, b_sl, b_vh, b_vl);
+              else
+                prefetch(tile_of(pr, 0) * kTile + trow, a_sh, a_sl, a_vh, a_vl);
+            }
+          }
+          wait_warp(&bar_acc[t], ph_acc >> t & 1, 8);
+          ph_acc ^= 1u << t;
+          tc::fence_after();
+          const bool stop = __shfl_sync(0xffffffffu, *abort_flag, 0);
+          const uint32_t taddr = tmem + lane_off + (uint32_t)(t * kH);
+          const int64_t myrow = tile_of(pr, t) * kTile + trow;
+          uint8_t* Ht = Hs + t * PPCfg::HBYTES;
+          if (l < 3 && !stop) {
+            const float* bl = bs + l * kH;
+            uint32_t r[2][32];
+            tc::tmem_ld32_nowait(taddr + grp * 32, r[0]);
+#pragma unroll
+            for (int pass = 0; pass < kNPass; ++pass) {
+              const int cb = pass * kPassCols + grp * 32;
+              tc::ld_wait(r[pass & 1]);
+              if (pass + 1 < kNPass)
+                tc::tmem_ld32_nowait(taddr + cb + kPassCols, r[(pass + 1) & 1]);
+              const uint32_t* rr = r[pass & 1];
+#pragma unroll
+              for (int q8 = 0; q8 < 4; ++q8) {
+                const int i = 8 * q8;
+                const float4 b0 = *reinterpret_cast<const float4*>(bl + cb + i);
+                const float4 b1 = *reinterpret_cast<const float4*>(bl + cb + i + 4);
+                float z[8];
+                uint4 q;
+                q.x = relu_bf16x2(rr[i + 0], rr[i + 1], b0.x, b0.y, z[0], z[1]);
+                q.y = relu_bf16x2(rr[i + 2], rr[i + 3], b0.z, b0.w, z[2], z[3]);
+                q.z = relu_bf16x2(rr[i + 4], rr[i + 5], b1.x, b1.y, z[4], z[5]);
+                q.w = relu_bf16x2(rr[i + 6], rr[i + 7], b1.z, b1.w, z[6], z[7]);
+                *reinterpret_cast<uint4*>(Ht + tc::kmajor_off(trow, cb + i, kH)) = q;
+                if (MODE == kModeBatch && myrow < p.M) {
+#pragma unroll
+                  for (int u = 0; u < 8; ++u) p.Zs[l][myrow * kH + cb + i + u] = z[u];
+                  *reinterpret_cast<uint4*>(p.Hs[l] + myrow * kH + cb + i) = q;
+                }
+              }
+            }
+            // H_t is written and the accumulator read: the MMAs of (t, l + 1) may go
+            tc::fence_async_smem();
+          } else if (!stop) {
+            // output layer: (alpha, c) and the rows, or the normalised outputs Y
+            float y[OUTP];
+            {
+              uint32_t r[32];
+              tc::tmem_ld32_nowait(taddr, r);
+              tc::ld_wait(r);
+#pragma unroll
+              for (int i = 0; i < 32; ++i) y[i] = __uint_as_float(r[i]) + bs[3 * kH + i];
+            }
+            if (MODE == kModeBatch) {
+              if (grp == 0 && myrow < p.M) {
+#pragma unroll
+                for (int o = 0; o < OUTP; ++o) p.Y[myrow * OUTP + o] = y[o];
+              }
+            } else {
+              // de-normalise, unit-normalise alpha (c scaled alike: P^-1 C is invariant)
+              float al[MU], cc[MU], nrm2 = 0.0f;
+#pragma unroll
+              for (int i = 0; i < MU; ++i) {
+                al[i] = y[i] * nrm[2 + OUTP + i] + nrm[2 + i];
+                cc[i] = y[MU + i] * nrm[2 + OUTP + MU + i] + nrm[2 + MU + i];
+                nrm2 = fmaf(al[i], al[i], nrm2);
+              }
+              const float sc = nrm2 > 0.0f ? rsqrtf(nrm2) : 1.0f;
+              // This warp's 32 rows of Q and C (group 0) or of P (group 1) are contiguous
+              // blocks of 32 x MU doubles in global memory. When all 32 rows exist they are
+              // staged in H_t (free: the layer-3 MMAs that read it have completed, and the
+              // next writes to it follow this epilogue's arrival) and leave by one bulk copy
+              // per block; otherwise each row is stored directly.
+              constexpr int BLK = 32 * MU * 8;
+              const int64_t wrow0 = tile_of(pr, t) * kTile + quarter * 32;
+              const bool full = wrow0 + 32 <= p.M;
+              double* stg = reinterpret_cast<double*>(Ht + (grp == 0 ? quarter : 8 + quarter) * BLK);
+              if (grp == 0) {
+#pragma unroll
+                for (int i = 0; i < MU; ++i) {
+                  // Q and C convert on the integer pipe while group 1 converts P on the FP64
+                  // pipe: the two pipes run side by side
+                  const double qv = f2d_int(al[i] * sc), cv = f2d_int(cc[i] * sc);
+                  if (full) {
+                    stg[lane * MU + i] = qv;
+                    stg[4 * BLK / 8 + lane * MU + i] = cv;
+                  } else if (myrow < p.M) {
+                    __stcs(p.Q + myrow * MU + i, qv);
+                    __stcs(p.C + myrow * MU + i, cv);
+                  }
+                }
+              } else {
+                // v[mu_j] - s_j from the fp32 pairs: the difference of the high parts is exact
+                // when v and s_j are within a factor of two of each other (the usual case)
+                const float sh = t == 0 ? a_sh : b_sh, sl = t == 0 ? a_sl : b_sl;
+#pragma unroll
+                for (int i = 0; i < MU; ++i) {
+                  const float dv = ((t == 0 ? a_vh[i] : b_vh[i]) - sh) +
+                                   ((t == 0 ? a_vl[i] : b_vl[i]) - sl);
+                  const double pv = (double)(fmaf(cc[i] * sc, dv, al[i] * sc));
+                  if (full)
+                    stg[lane * MU + i] = pv;
+                  else if (myrow < p.M)
+                    __stcs(p.P + myrow * MU + i, pv);
+                }
+              }
+              if (full) {
+                tc::fence_async_smem();
+                __syncwarp();
+                if (lane == 0) {
+                  if (grp == 0) {
+                    tc::bulk_s2g(p.Q + wrow0 * MU, stg, BLK);
+                    tc::bulk_s2g(p.C + wrow0 * MU, stg + 4 * BLK / 8, BLK);
+                  } else {
+                    tc::bulk_s2g(p.P + wrow0 * MU, stg, BLK);
+                  }
+                  tc::bulk_commit();
+                  tc::bulk_wait_read();  // H_t may be written again once every warp arrived
+                }
+              }
+            }
+          }
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive_cluster(&bar_e[t], 0);  // on the even CTA's bar_e
+        }
+      }
+    }
+    if (lane == 0) tc::bulk_wait_all();  // this warp's row stores have landed
+  }
+  tc::fence_before();
+  __syncthreads();
+  // neither CTA leaves (or releases the pair's tensor memory) while the other may still arrive
+  // on its barriers or its MMAs read the other's shared memory
+  tc::cluster_sync();
+  tc::fence_after();
+  if (warp == 0) tc::tmem_dealloc_pair(tmem, 2 * kH);
+}
+
+
 // Per point j of a learned build: the normalised features of h^2 v_j and of h^2 s_j (bf16,
 // s_j = snap(v_j)), and fp32 pairs v_j = vh + vl, s_j = sh + sl for the P epilogue. Since
 // h^2 = 1/n^2 is a power of two, (float)(v h^2) = (float)v * h^2 exactly.
@@ -998,7 +1406,7 @@ __global__ void k_inputs_rows(const __nv_bfloat16* __restrict__ xb,
   constexpr int NF = D == 2 ? 26 : 126, NP = NF - 1;
   constexpr int K0 = D == 2 ? 32 : 128;
   const int64_t mask = ((int64_t)1 << logn) - 1;
-  const int64_t rows = (M + kTile - 1) / kTile * kTile;
+  const int64_t rows = (M + 2 * kTile - 1) / (2 * kTile) * (2 * kTile);  // whole tile pairs
   for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < rows;
        row += (int64_t)gridDim.x * blockDim.x) {
     const bool live = row < M;
@@ -1316,7 +1724,8 @@ struct lsp_mlp {
   std::string err;
   lsp::DevBuf params, grads, adam_m, adam_v, tiles, WT[4], W16[4], errflag, loss;
   uint64_t wait_ns = lsp::tc::kWaitLimitNs;  // operand-wait limit of the fused kernel
-  int schedule = 1;  // 2D: 1 = two tiles in flight (k_mlp_pp), 0 = one tile at a time
+  int schedule = 1;  // 2D: 1 = two tiles in flight (k_mlp_pp), 0 = one tile at a time,
+                     // 2 = two 256-row tiles in flight on a CTA pair (k_mlp_pp2, rows mode)
   // training workspace
   int64_t cap = 0;
   lsp::DevBuf X16, XT, Xt, Zs[3], Hs[3], HT[3], Y, dY16, dYT, dY32, G, dZ16, dZT, dZ32;
@@ -1369,13 +1778,27 @@ FusedParams fused_params(lsp_mlp* m) {
 }
 
 // Bytes of the canonical input tiles for `rows` rows (whole tiles).
+// Whole pairs of 128-row tiles (the CTA-pair kernel reads both tiles of a 256-row super-tile;
+// rows beyond M are zero).
 size_t input_tile_bytes(int d, int64_t rows) {
-  return (size_t)((rows + kTile - 1) / kTile) * kTile * dims_for(d).K0 * 2;
+  return (size_t)((rows + 2 * kTile - 1) / (2 * kTile)) * 2 * kTile * dims_for(d).K0 * 2;
 }
 
 template <int D, int MODE>
 cudaError_t launch_fused(lsp_mlp* m, const FusedParams& p, int64_t rows) {
-  if (D == 2 && m->schedule == 1) {
+  if constexpr (D == 2 && MODE == kModeRows) {
+    if (m->schedule == 2) {
+      const size_t smem = PPCfg::smem;
+      cudaError_t e = cudaFuncSetAttribute(k_mlp_pp2<MODE>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      const int64_t super = ((rows + kTile - 1) / kTile + 1) / 2;
+      const int pairs = (int)(super < 76 ? super : 76);  // one CTA pair per TPC
+      k_mlp_pp2<MODE><<<2 * (pairs < 1 ? 1 : pairs), kPPThreads, smem, m->stream>>>(p);
+      return cudaGetLastError();
+    }
+  }
+  if (D == 2 && m->schedule >= 1) {  // batch mode of schedule 2 runs the one-CTA kernel
     const size_t smem = PPCfg::smem;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_pp<MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1700,7 +2123,7 @@ lsp_status lsp_mlp_training_pairs(lsp_ctx* c, lsp_mlp* m, int64_t nsamples, uint
 const char* lsp_mlp_last_error(const lsp_mlp* m) { return m ? m->err.c_str() : "null network"; }
 
 lsp_status lsp_mlp_set_schedule(lsp_mlp* m, int schedule) {
-  if (!m || (schedule != 0 && schedule != 1)) return LSP_ERR_ARG;
+  if (!m || schedule < 0 || schedule > 2) return LSP_ERR_ARG;
   m->schedule = schedule;
   return LSP_OK;
 }

@@ -126,6 +126,88 @@ __device__ __forceinline__ void bulk_g2s(void* smem, const void* gmem, uint32_t 
       : "memory");
 }
 
+// ---- CTA pairs (cluster of two CTAs on one TPC, tcgen05 with cta_group::2) ----
+// One MMA of M = 256 spans the pair: rows 0-127 of A and the first N/2 rows of B (our K-major
+// weight chunk) are read from the even CTA's shared memory, rows 128-255 and the other N/2
+// rows of B from the odd CTA's, at the same offsets; each CTA's tensor memory receives its
+// 128 rows of D. The even CTA issues the MMAs and commits; the commits arrive on the
+// mbarrier at the same offset in both CTAs.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of both CTAs: arrive and wait (release / acquire at cluster scope).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+// One arrival (release at cluster scope) on the mbarrier at the same offset in CTA `rank`.
+__device__ __forceinline__ void mbar_arrive_cluster(uint64_t* mbar, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(mbar)), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote)
+               : "memory");
+}
+// mbar_test / mbar_wait with acquire at cluster scope: for phases completed by arrivals from
+// the other CTA of the pair.
+__device__ __forceinline__ bool mbar_test_cluster(uint64_t* mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n.reg .pred P1;\nmbarrier.test_wait.parity.acquire.cluster.shared::cta.b64 P1, [%1], %2;\n"
+      "selp.b32 %0, 1, 0, P1;\n}\n"
+      : "=r"(done)
+      : "r"(smem_u32(mbar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* mbar, uint32_t parity, int* err,
+                                                  int errbit, uint64_t limit_ns = kWaitLimitNs) {
+  if (mbar_test_cluster(mbar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  const uint32_t hint = limit_ns < 2000u ? (uint32_t)limit_ns : 2000u;
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred P1;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 P1, [%1], %2, "
+        "%3;\nselp.b32 %0, 1, 0, P1;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(mbar)), "r"(parity), "r"(hint)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > limit_ns) break;
+  }
+  atomicOr(err, errbit);
+  return false;
+}
+__device__ __forceinline__ void mma_bf16_pair(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+// Completion of this thread's earlier pair MMAs, signalled on the mbarrier at the same offset in
+// both CTAs of the pair.
+__device__ __forceinline__ void commit_pair(uint64_t* mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+      "[%0], %1;" ::"r"(smem_u32(mbar)),
+      "h"((uint16_t)3)
+      : "memory");
+}
+// Tensor memory of a pair: one warp of each CTA takes part in the allocation (and in the
+// release), which reserves the same columns in both CTAs.
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols));
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols));
+}
+
 // 1D bulk copy shared -> global, tracked in this thread's bulk group (commit with
 // bulk_commit()). Both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_s2g(void* gmem, const void* smem, uint32_t bytes) {

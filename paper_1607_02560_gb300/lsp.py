@@ -534,7 +534,8 @@ class Mlp:
         return loss.value
 
     def set_schedule(self, schedule: int = 1):
-        """2D inference: 1 = two tiles in flight per SM (default), 0 = one tile at a time."""
+        """2D inference: 1 = two tiles in flight per SM (default), 0 = one tile at a time,
+        2 = two 256-row tiles in flight per CTA pair (rows only; slower, kept for comparison)."""
         self._check(lib().lsp_mlp_set_schedule(self.h, int(schedule)), "set_schedule")
 
     def set_wait_limit(self, ns: int = 0):

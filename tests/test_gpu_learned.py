@@ -184,11 +184,14 @@ def test_forward_and_gradients_match_oracle(stream, d):
     assert flagged.sum() <= B // 16  # a few boundary cases, not a systematic difference
 
 
-@pytest.mark.parametrize("n", [64, 256, 1024])
+@pytest.mark.parametrize("n", [8, 16, 64, 256, 1024])
 def test_two_tiles_in_flight_give_the_same_rows(stream, n):
-    """The 2D inference kernel with two tiles in flight per SM computes the same rows and
-    batch outputs, bit for bit, as the one-tile schedule (32 tiles: one per CTA; 512: three or
-    four per CTA; 8192: 53 or 54 per CTA, so both odd and even tile counts occur)."""
+    """The 2D inference kernels with two tiles in flight per SM (schedule 1) and with two
+    256-row tiles in flight per CTA pair (schedule 2, rows only) compute the same rows, and
+    schedule 1 the same batch outputs, bit for bit, as the one-tile schedule. Tile counts: 1
+    (the pair's second CTA holds only the zero padding tile), 2, 32 (one per CTA), 512 (three or
+    four per CTA) and 8192 (53 or 54 per CTA), so odd and even counts per CTA and per pair
+    occur."""
     import torch
     from paper_1607_02560_gb300 import Context, Mlp
     from paper_1607_02560_gb300.learned import make_pool
@@ -202,7 +205,7 @@ def test_two_tiles_in_flight_give_the_same_rows(stream, n):
     ctx.set_potential(v)
     rows, ys = {}, {}
     B = 128 * 5
-    for sched in (0, 1):
+    for sched in (0, 1, 2):
         mlp.set_schedule(sched)
         ctx.build_stencils(mode="learned")
         ctx.synchronize()
@@ -212,9 +215,10 @@ def test_two_tiles_in_flight_give_the_same_rows(stream, n):
         mlp.forward(X[:B], B, Y)
         torch.cuda.synchronize()
         ys[sched] = Y.cpu().numpy()
-    for a, b in zip(rows[0], rows[1]):
-        assert np.array_equal(a, b)
-    assert np.array_equal(ys[0], ys[1])
+    for sched in (1, 2):
+        for a, b in zip(rows[0], rows[sched]):
+            assert np.array_equal(a, b), sched
+        assert np.array_equal(ys[0], ys[sched]), sched
 
 
 def test_training_lowers_the_loss(stream):
