@@ -696,7 +696,9 @@ lsp_status lsp_set_potential(lsp_ctx* c, const double* v, int v_on_device) {
                                c->stream));
     src = (const double*)c->v.p;
   }
-  int nb = (int)std::min<int64_t>(152 * 4, (N + 255) / 256);
+  // one block per SM: fewer partials for the last block to reduce (measured 20 -> 16 us in 3D
+  // n = 64, 29 -> 23 us in 2D n = 1024 against four per SM)
+  int nb = (int)std::min<int64_t>(152, (N + 255) / 256);
   if (!ensure(c, c->stats_part, sizeof(double) * 4 * nb)) return LSP_ERR_OOM;
   CUDA_OK(c, launch_stats(c, nb, src));
   if (!c->h_stats_dev)
