@@ -1327,6 +1327,16 @@ __device__ __forceinline__ GT b_entry(const GT (&g2)[6], const GT (&wi)[9], cons
   return s - t;
 }
 
+// 2^-ilogb(x) for x > 0: the power of two that scales x into [1, 2). For a normal x whose
+// reciprocal power is normal (biased exponent field ef in 1..2045) it is built from the
+// exponent field with integer operations, 2^(1023 - ef + 1023) as a bit pattern, which keeps
+// the FP64 pipe (narrow on this GPU) free; other x take the library functions.
+__device__ __forceinline__ double pow2_neg_ilogb(double x) {
+  const int ef = (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+  if (ef >= 1 && ef <= 2045) return __longlong_as_double((long long)(2046 - ef) << 52);
+  return exp2((double)(-ilogb(x)));
+}
+
 // Eigenvalues of the symmetric 2 x 2 [[a, b], [b, c]], smaller one first; the small one as
 // det / large avoids cancellation.
 __device__ __forceinline__ void eig2(double a, double b, double c, double& lo, double& hi) {
@@ -1407,7 +1417,7 @@ __global__ void __launch_bounds__(128) k_eig2d(const double* __restrict__ gvals,
       const double y2 = a02 * x0 + a12 * x1 + a22 * x2;
       // renormalise by a power of two (exact) to stay clear of under/overflow
       const double mx = fmax(fabs(y0), fmax(fabs(y1), fabs(y2)));
-      const double p2 = mx > 0 ? exp2((double)(-ilogb(mx))) : 1.0;
+      const double p2 = mx > 0 ? pow2_neg_ilogb(mx) : 1.0;
       x0 = y0 * p2;
       x1 = y1 * p2;
       x2 = y2 * p2;
