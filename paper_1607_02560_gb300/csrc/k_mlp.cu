@@ -1412,6 +1412,16 @@ __global__ void k_inputs_rows(const __nv_bfloat16* __restrict__ xb,
     const bool live = row < M;
     uint8_t* tile = Xt + (row / kTile) * (int64_t)(kTile * K0 * 2);
     const int r = (int)(row % kTile);
+    // the five wrapped coordinates of each axis at offsets -2..2, already shifted into place:
+    // the index of patch offset k (lexicographic, as nb_index<D, 2>) is then two ORs
+    int64_t Y[D][5];
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      const int sh = (D - 1 - a) * logn;
+      const int64_t xa = (row >> sh) & mask;
+#pragma unroll
+      for (int o = 0; o < 5; ++o) Y[a][o] = ((xa + o - 2) & mask) << sh;
+    }
 #pragma unroll
     for (int k8 = 0; k8 < K0; k8 += 8) {
       __nv_bfloat16 f[8];
@@ -1419,7 +1429,11 @@ __global__ void k_inputs_rows(const __nv_bfloat16* __restrict__ xb,
       for (int i = 0; i < 8; ++i) {
         const int k = k8 + i;
         __nv_bfloat16 x = __float2bfloat16(0.0f);
-        if (live && k < NP) x = xb[nb_index<D, 2>(row, k, logn, mask)];
+        if (live && k < NP) {
+          const int64_t nb = D == 2 ? (Y[0][(k / 5) % 5] | Y[D - 1][k % 5])
+                                    : (Y[0][(k / 25) % 5] | Y[D - 2][(k / 5) % 5] | Y[D - 1][k % 5]);
+          x = xb[nb];
+        }
         if (live && k == NP) x = sb[row];
         f[i] = x;
       }
